@@ -1,0 +1,212 @@
+"""CPU oracle for the ensemble ODE/SDE solver -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference legs
+may import this package.  The product package never imports it and shares no code with it.
+
+The arithmetic lives in ``ens_oracle.cpp`` (plain C++, FP64, with an FP32 mode), built on demand
+into ``liboracle.so`` next to this file; ``mlp.py`` holds the NumPy oracle of the surrogate
+network.  This module only marshals NumPy arrays into the C functions.
+
+Identifiers (the same numbers as the public C-ABI, by documentation):
+  rhs:  1 Lorenz (D=3, P=3: sigma, rho, beta), 2 Robertson (D=3, P=3: k1, k2, k3),
+        3 geometric Brownian motion (D=1, P=2: mu, sigma)
+  alg:  1 Tsit5 fixed, 2 Tsit5 adaptive, 3 RK4, 4 Rosenbrock23, 5 Euler-Maruyama
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ens_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+RHS = {"lorenz": 1, "robertson": 2, "gbm": 3}
+ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5}
+DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2)}
+STATUS = {"ok": 0, "maxiters": 1, "dt_min": 2, "nonfinite": 3}
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with the host compiler (no FMA contraction, portable flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+               "-o", tmp, _SRC]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.oracle_solve.restype = ctypes.c_int
+            L.oracle_solve.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_longlong,
+                dp, ctypes.POINTER(ctypes.c_byte), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+            L.oracle_step.restype = ctypes.c_int
+            L.oracle_step.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, dp, dp]
+            L.oracle_tsit5_tableau.restype = None
+            L.oracle_tsit5_tableau.argtypes = [dp, dp, dp, dp]
+            L.oracle_rhs.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
+            L.oracle_jac.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp, dp]
+            L.oracle_lu_solve.argtypes = [ctypes.c_int, dp, dp, dp]
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            L.oracle_philox4x32_10.restype = None
+            L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.oracle_normals.restype = None
+            L.oracle_normals.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.c_longlong,
+                                         ctypes.c_int, dp]
+            L.oracle_tsit5_fixed_grad.restype = ctypes.c_int
+            L.oracle_tsit5_fixed_grad.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, dp,
+                                                  ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def default_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)))
+
+
+def solve(rhs, alg, params, u0, tspan, *, dt=0.0, abstol=1e-6, reltol=1e-3, dt0=0.0,
+          maxiters=1_000_000, saveat=None, seed=0, index_offset=0, precision="f64",
+          nthreads=None):
+    """Solve an ensemble.  params [N,P], u0 [N,D], tspan [N,2] (row-major, float64).
+
+    precision "f32" runs the same algorithms in float arithmetic on the given (already
+    float-representable) inputs.  Returns (out [N,S,D] or [N,D], status [N], stats [N,3]).
+    """
+    rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    alg_id = ALG[alg] if isinstance(alg, str) else int(alg)
+    D, P = DIMS[rhs_id]
+    params = _f64(params).reshape(-1, P)
+    N = params.shape[0]
+    u0 = _f64(u0).reshape(N, D)
+    tspan = _f64(tspan).reshape(N, 2)
+    sv = None if saveat is None else _f64(saveat).reshape(-1)
+    S = 1 if sv is None or sv.size == 0 else sv.size
+    out = np.empty((N, S, D), np.float64)
+    status = np.empty(N, np.int8)
+    stats = np.empty((N, 3), np.int64)
+    nt = default_threads() if nthreads is None else int(nthreads)
+    rc = lib().oracle_solve(
+        rhs_id, alg_id, 0 if precision == "f64" else 1, 0, N, _dp(params), _dp(u0), _dp(tspan),
+        float(dt), float(abstol), float(reltol), float(dt0), int(maxiters),
+        _dp(sv) if sv is not None and sv.size else None, 0 if sv is None else int(sv.size),
+        int(seed), int(index_offset), _dp(out),
+        status.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)),
+        stats.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), nt)
+    if rc != 0:
+        raise ValueError("oracle_solve rejected its arguments")
+    if sv is None or sv.size == 0:
+        out = out[:, 0, :]
+    return out, status, stats
+
+
+def step(rhs, alg, u, p, t, h, z=0.0):
+    """One step of a method; returns (u_new, err)."""
+    rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    alg_id = ALG[alg] if isinstance(alg, str) else int(alg)
+    D, _ = DIMS[rhs_id]
+    u = _f64(u)
+    p = _f64(p)
+    unew = np.empty(D)
+    err = np.empty(D)
+    if lib().oracle_step(rhs_id, alg_id, _dp(u), _dp(p), float(t), float(h), float(z), _dp(unew),
+                         _dp(err)) != 0:
+        raise ValueError("bad step arguments")
+    return unew, err
+
+
+def tsit5_tableau():
+    c = np.empty(7)
+    A = np.empty((7, 7))
+    b = np.empty(7)
+    bh = np.empty(7)
+    lib().oracle_tsit5_tableau(_dp(c), _dp(A), _dp(b), _dp(bh))
+    return c, A, b, bh
+
+
+def rhs_eval(rhs, u, p, t=0.0):
+    rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    D, _ = DIMS[rhs_id]
+    du = np.empty(D)
+    lib().oracle_rhs(rhs_id, _dp(_f64(u)), _dp(_f64(p)), float(t), _dp(du))
+    return du
+
+
+def jacobians(rhs, u, p, t=0.0):
+    rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    D, P = DIMS[rhs_id]
+    Ju = np.empty((D, D))
+    Jp = np.empty((D, P))
+    lib().oracle_jac(rhs_id, _dp(_f64(u)), _dp(_f64(p)), float(t), _dp(Ju), _dp(Jp))
+    return Ju, Jp
+
+
+def lu_solve(W, b):
+    W = _f64(W)
+    D = W.shape[0]
+    x = np.empty(D)
+    lib().oracle_lu_solve(D, _dp(W), _dp(_f64(b)), _dp(x))
+    return x
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty(4, np.uint32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib().oracle_philox4x32_10(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p),
+                               out.ctypes.data_as(u32p))
+    return out
+
+
+def normals(seed, traj, n, fp64=False):
+    out = np.empty(int(n))
+    lib().oracle_normals(int(seed), int(traj), int(n), 1 if fp64 else 0, _dp(out))
+    return out
+
+
+def tsit5_fixed_grad(rhs, params, u0, tspan, dt, grad_out, nthreads=None):
+    """Exact gradient of the fixed-step Tsit5 map by forward tangents.
+
+    Returns (grad_p [N,P], grad_u0 [N,D], u_final [N,D])."""
+    rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    D, P = DIMS[rhs_id]
+    params = _f64(params).reshape(-1, P)
+    N = params.shape[0]
+    u0 = _f64(u0).reshape(N, D)
+    tspan = _f64(tspan).reshape(N, 2)
+    go = _f64(grad_out).reshape(N, D)
+    gp = np.empty((N, P))
+    gu = np.empty((N, D))
+    uf = np.empty((N, D))
+    nt = default_threads() if nthreads is None else int(nthreads)
+    rc = lib().oracle_tsit5_fixed_grad(rhs_id, N, _dp(params), _dp(u0), _dp(tspan), float(dt),
+                                       _dp(go), _dp(gp), _dp(gu), _dp(uf), nt)
+    if rc != 0:
+        raise ValueError("bad arguments")
+    return gp, gu, uf

@@ -1,0 +1,813 @@
+// ens_oracle.cpp -- plain, slow, obviously-correct CPU oracle for the ensemble solver.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call this file;
+// only tests/, the smoke check in __graft_entry__ and bench.py's CPU-baseline / reference
+// legs use it.  It shares no source, header, table or constant with the CUDA path.
+//
+// What it computes (arXiv 2304.06835, "Automated Translation and Accelerated Solving of
+// Differential Equations on Multiple GPU Platforms"):
+//   * the ensemble problem: N independent copies of du/dt = f(u,p,t), one (p_j, u0_j, tspan_j)
+//     per trajectory (Sec. 5.1.1, the U / P / F matrices);
+//   * explicit Runge-Kutta steps from a tableau {A,b,c} (Sec. 3.1, the k_s / u_{n+1} equations),
+//     here Tsitouras' 5(4) pair (GPUTsit5, Sec. 5.2.1) and the classic RK4;
+//   * the embedded error estimate, the scaled error ratio q and PI step control
+//     (Sec. 3.1, the q equation and h_new = eta q_{n-1}^{beta2} q_n^{beta1} h);
+//   * the Rosenbrock method (Sec. 3.2.1, the s-stage Rosenbrock formulas), as the
+//     Shampine-Reichelt order-2(3) Rosenbrock-W pair named by GPURosenbrock23 (Sec. 5.2.1);
+//   * Euler-Maruyama for dX = a dt + b dW, dW ~ N(0,dt) (Sec. 3.3, the SDE definition; GPUEM);
+//   * the benchmark models: Lorenz (Appendix, Lorenz problem), Robertson (Appendix, Robertson
+//     equation) and the linear asset-price SDE / geometric Brownian motion (Appendix, linear SDE).
+//
+// Readings where the paper is silent (every one is listed in the design notes):
+//   * Tsit5 coefficients: Tsitouras (2011), Comput. Math. Appl. 62, table of the 5(4) pair.
+//   * error norm: root-mean-square over the D components (Hairer-Norsett-Wanner I, II.4).
+//   * accept iff q <= 1;  PI constants eta=0.9, beta1=0.7/k, beta2=0.4/k (k=5 Tsit5, k=3 R23),
+//     fac clamped to [0.2,10], reject factor max(0.2, eta q^{-1/k}), q_{n-1} starts at 1e-4 and is
+//     max(q,1e-4) after an accept, q guarded below by 1e-10.
+//   * automatic first step: Hairer-Norsett-Wanner I, II.4 starting step size algorithm.
+//   * Rosenbrock23: d = 1/(2+sqrt2), e32 = 6+sqrt2 (Shampine & Reichelt 1997, ode23s).
+//   * random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = seed,
+//     counter = (draw index lo, hi, trajectory index lo, hi); uniforms ((x>>8)+0.5)*2^-24 (FP32)
+//     or ((x0:x1 >> 11)+0.5)*2^-53 (FP64); Box-Muller normals.
+//
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared -pthread (see oracle/__init__.py).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <thread>
+#include <vector>
+
+namespace {
+
+// ----------------------------------------------------------------------------------------------
+// identifiers (values match the public C-ABI enumeration by documentation, not by a shared header)
+enum { RHS_LORENZ = 1, RHS_ROBERTSON = 2, RHS_GBM = 3 };
+enum { ALG_TSIT5_FIXED = 1, ALG_TSIT5_ADAPTIVE = 2, ALG_RK4 = 3, ALG_ROS23 = 4, ALG_EM = 5 };
+enum { ST_OK = 0, ST_MAXITERS = 1, ST_DT_MIN = 2, ST_NONFINITE = 3 };
+enum { LAYOUT_ROWMAJOR = 0, LAYOUT_SOA = 1 };
+
+// ----------------------------------------------------------------------------------------------
+// Models (Appendix: Lorenz, Robertson, linear SDE).  f(u,p,t) and the Jacobians df/du, df/dp.
+struct Model {
+  int D, P;
+};
+
+Model model_of(int rhs) {
+  switch (rhs) {
+    case RHS_LORENZ: return {3, 3};
+    case RHS_ROBERTSON: return {3, 3};
+    case RHS_GBM: return {1, 2};
+  }
+  return {0, 0};
+}
+
+// Lorenz: p = (sigma, rho, beta); the paper writes beta as gamma.
+template <class T>
+void f_lorenz(const T* u, const T* p, T /*t*/, T* du) {
+  const T sigma = p[0], rho = p[1], beta = p[2];
+  du[0] = sigma * (u[1] - u[0]);
+  du[1] = rho * u[0] - u[1] - u[0] * u[2];
+  du[2] = u[0] * u[1] - beta * u[2];
+}
+
+// Robertson: p = (k1, k2, k3) with k1 on y1, k2 on y2^2, k3 on y2*y3.
+template <class T>
+void f_robertson(const T* u, const T* p, T /*t*/, T* du) {
+  const T k1 = p[0], k2 = p[1], k3 = p[2];
+  du[0] = -k1 * u[0] + k3 * u[1] * u[2];
+  du[1] = k1 * u[0] - k3 * u[1] * u[2] - k2 * u[1] * u[1];
+  du[2] = k2 * u[1] * u[1];
+}
+
+// Geometric Brownian motion drift a(X) = mu X (diffusion b(X) = sigma X below); p = (mu, sigma).
+template <class T>
+void f_gbm(const T* u, const T* p, T /*t*/, T* du) {
+  du[0] = p[0] * u[0];
+}
+
+template <class T>
+void g_gbm(const T* u, const T* p, T /*t*/, T* gu) {
+  gu[0] = p[1] * u[0];
+}
+
+template <class T>
+void rhs(int id, const T* u, const T* p, T t, T* du) {
+  if (id == RHS_LORENZ) f_lorenz(u, p, t, du);
+  else if (id == RHS_ROBERTSON) f_robertson(u, p, t, du);
+  else f_gbm(u, p, t, du);
+}
+
+// J[i*D+j] = d f_i / d u_j
+template <class T>
+void jac_u(int id, const T* u, const T* p, T /*t*/, T* J) {
+  if (id == RHS_LORENZ) {
+    const T sigma = p[0], rho = p[1], beta = p[2];
+    J[0] = -sigma; J[1] = sigma; J[2] = 0;
+    J[3] = rho - u[2]; J[4] = -1; J[5] = -u[0];
+    J[6] = u[1]; J[7] = u[0]; J[8] = -beta;
+  } else if (id == RHS_ROBERTSON) {
+    const T k1 = p[0], k2 = p[1], k3 = p[2];
+    J[0] = -k1; J[1] = k3 * u[2]; J[2] = k3 * u[1];
+    J[3] = k1; J[4] = -k3 * u[2] - 2 * k2 * u[1]; J[5] = -k3 * u[1];
+    J[6] = 0; J[7] = 2 * k2 * u[1]; J[8] = 0;
+  } else {
+    J[0] = p[0];
+  }
+}
+
+// Jp[i*P+m] = d f_i / d p_m
+template <class T>
+void jac_p(int id, const T* u, const T* /*p*/, T /*t*/, T* Jp) {
+  if (id == RHS_LORENZ) {
+    Jp[0] = u[1] - u[0]; Jp[1] = 0; Jp[2] = 0;
+    Jp[3] = 0; Jp[4] = u[0]; Jp[5] = 0;
+    Jp[6] = 0; Jp[7] = 0; Jp[8] = -u[2];
+  } else if (id == RHS_ROBERTSON) {
+    Jp[0] = -u[0]; Jp[1] = 0; Jp[2] = u[1] * u[2];
+    Jp[3] = u[0]; Jp[4] = -u[1] * u[1]; Jp[5] = -u[1] * u[2];
+    Jp[6] = 0; Jp[7] = u[1] * u[1]; Jp[8] = 0;
+  } else {
+    Jp[0] = u[0]; Jp[1] = 0;
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Tsitouras 5(4) tableau (Tsitouras 2011).  Stage 7 is the FSAL stage: row 7 of A equals b.
+// bhat is the embedded 4th-order weight vector; the error estimate is h * sum (b_i - bhat_i) k_i.
+const double TS_C[7] = {0.0, 0.161, 0.327, 0.9, 0.9800255409045097, 1.0, 1.0};
+const double TS_A[7][7] = {
+    {0, 0, 0, 0, 0, 0, 0},
+    {0.161, 0, 0, 0, 0, 0, 0},
+    {-0.008480655492356989, 0.335480655492357, 0, 0, 0, 0, 0},
+    {2.897153057105493, -6.359448489975075, 4.3622954328695815, 0, 0, 0, 0},
+    {5.325864828439257, -11.748883564062828, 7.4955393428898365, -0.09249506636175525, 0, 0, 0},
+    {5.86145544294642, -12.92096931784711, 8.159367898576159, -0.071584973281401,
+     -0.028269050394068383, 0, 0},
+    {0.09646076681806523, 0.01, 0.4798896504144996, 1.379008574103742, -3.290069515436081,
+     2.324710524099774, 0},
+};
+const double TS_B[7] = {0.09646076681806523, 0.01, 0.4798896504144996, 1.379008574103742,
+                        -3.290069515436081, 2.324710524099774, 0.0};
+const double TS_BHAT[7] = {0.09468075576583945, 0.009183565540343254, 0.4877705284247616,
+                           1.234297566930479, -2.7077123499835256, 1.866628418170587,
+                           0.015151515151515152};
+
+// Controller constants (readings listed in the file header).
+const double ETA = 0.9;
+const double FAC_MIN = 0.2, FAC_MAX = 10.0;
+const double QOLD_INIT = 1e-4, Q_FLOOR = 1e-10;
+
+template <class T>
+struct Prec;
+template <>
+struct Prec<double> {
+  static constexpr double dtmin_factor = 1e-14;
+};
+template <>
+struct Prec<float> {
+  static constexpr double dtmin_factor = 1e-9;
+};
+const double STOP_EPS = 1e-12;  // a remainder this small (relative) counts as having arrived
+
+// ----------------------------------------------------------------------------------------------
+// Time accumulator.  FP64: plain sum.  FP32: Neumaier-compensated (t = hi + lo).
+template <class T>
+struct Clock {
+  T hi, lo;
+  void set(T v) { hi = v; lo = 0; }
+  T value() const { return hi + lo; }
+  T remaining(T stop) const { return (stop - hi) - lo; }
+  void add(T h) {
+    T s = hi + h;
+    if (std::fabs(hi) >= std::fabs(h)) lo += (hi - s) + h;
+    else lo += (h - s) + hi;
+    hi = s;
+  }
+};
+template <>
+struct Clock<double> {
+  double hi;
+  void set(double v) { hi = v; }
+  double value() const { return hi; }
+  double remaining(double stop) const { return stop - hi; }
+  void add(double h) { hi += h; }
+};
+
+template <class T>
+bool finite_all(const T* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+// scaled RMS norm  sqrt( (1/D) sum_j (x_j / sc_j)^2 )
+template <class T>
+T rms_scaled(const T* x, const T* sc, int D) {
+  T s = 0;
+  for (int j = 0; j < D; ++j) {
+    T r = x[j] / sc[j];
+    s += r * r;
+  }
+  return std::sqrt(s / T(D));
+}
+
+// ----------------------------------------------------------------------------------------------
+// One Tsit5 step of size h from (u,t) with k1 = f(u,t) given.  Fills unew, err (= h sum btilde k),
+// k7 = f(unew, t+h).  Stage formula: U_i = u + h sum_j a_ij k_j, k_i = f(U_i, t + c_i h).
+template <class T>
+void tsit5_step(int id, int D, const T* u, const T* p, T t, T h, const T* k1, T* unew, T* err,
+                T* k7) {
+  T k[7][8];
+  T U[8];
+  for (int j = 0; j < D; ++j) k[0][j] = k1[j];
+  for (int i = 1; i < 7; ++i) {
+    for (int j = 0; j < D; ++j) {
+      T s = 0;
+      for (int m = 0; m < i; ++m) s += T(TS_A[i][m]) * k[m][j];
+      U[j] = u[j] + h * s;
+    }
+    rhs<T>(id, U, p, t + T(TS_C[i]) * h, k[i]);
+  }
+  // u_{n+1} = u_n + h sum b_i k_i  (b_7 = 0)
+  for (int j = 0; j < D; ++j) {
+    T s = 0;
+    for (int m = 0; m < 7; ++m) s += T(TS_B[m]) * k[m][j];
+    unew[j] = u[j] + h * s;
+  }
+  // E = u~ - u_{n+1} = h sum (bhat_i - b_i) k_i
+  for (int j = 0; j < D; ++j) {
+    T s = 0;
+    for (int m = 0; m < 7; ++m) s += T(TS_BHAT[m] - TS_B[m]) * k[m][j];
+    err[j] = h * s;
+    k7[j] = k[6][j];
+  }
+}
+
+template <class T>
+void rk4_step(int id, int D, const T* u, const T* p, T t, T h, T* unew) {
+  T k1[8], k2[8], k3[8], k4[8], U[8];
+  rhs<T>(id, u, p, t, k1);
+  for (int j = 0; j < D; ++j) U[j] = u[j] + (h / 2) * k1[j];
+  rhs<T>(id, U, p, t + h / 2, k2);
+  for (int j = 0; j < D; ++j) U[j] = u[j] + (h / 2) * k2[j];
+  rhs<T>(id, U, p, t + h / 2, k3);
+  for (int j = 0; j < D; ++j) U[j] = u[j] + h * k3[j];
+  rhs<T>(id, U, p, t + h, k4);
+  for (int j = 0; j < D; ++j) unew[j] = u[j] + (h / 6) * (k1[j] + 2 * k2[j] + 2 * k3[j] + k4[j]);
+}
+
+// ---- dense LU with partial pivoting (ties -> lowest row index), then forward/back substitution.
+template <class T>
+void lu_factor(int D, T* W, int* piv) {
+  for (int c = 0; c < D; ++c) {
+    int best = c;
+    for (int r = c + 1; r < D; ++r)
+      if (std::fabs(W[r * D + c]) > std::fabs(W[best * D + c])) best = r;
+    piv[c] = best;
+    if (best != c)
+      for (int j = 0; j < D; ++j) std::swap(W[c * D + j], W[best * D + j]);
+    for (int r = c + 1; r < D; ++r) {
+      W[r * D + c] /= W[c * D + c];
+      for (int j = c + 1; j < D; ++j) W[r * D + j] -= W[r * D + c] * W[c * D + j];
+    }
+  }
+}
+
+template <class T>
+void lu_solve(int D, const T* LU, const int* piv, const T* b, T* x) {
+  T y[8];
+  for (int j = 0; j < D; ++j) y[j] = b[j];
+  for (int c = 0; c < D; ++c) std::swap(y[c], y[piv[c]]);
+  for (int r = 0; r < D; ++r)
+    for (int j = 0; j < r; ++j) y[r] -= LU[r * D + j] * y[j];
+  for (int r = D - 1; r >= 0; --r) {
+    for (int j = r + 1; j < D; ++j) y[r] -= LU[r * D + j] * y[j];
+    y[r] /= LU[r * D + r];
+  }
+  for (int j = 0; j < D; ++j) x[j] = y[j];
+}
+
+// One Rosenbrock23 (ode23s) step from (u,t) with f0 = f(u,t).  W = I - h d J.
+// Fills unew, err = h/6 (k1 - 2 k2 + k3), f2 = f(unew, t+h).  All models here are autonomous,
+// so df/dt = 0 and the h d T terms vanish.
+template <class T>
+void ros23_step(int id, int D, const T* u, const T* p, T t, T h, const T* f0, T* unew, T* err,
+                T* f2) {
+  const T d = T(1.0 / (2.0 + std::sqrt(2.0)));
+  const T e32 = T(6.0 + std::sqrt(2.0));
+  T J[64], W[64];
+  int piv[8];
+  jac_u<T>(id, u, p, t, J);
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) W[r * D + c] = (r == c ? T(1) : T(0)) - h * d * J[r * D + c];
+  lu_factor<T>(D, W, piv);
+  T k1[8], k2[8], k3[8], f1[8], U[8], rhs_v[8] = {};
+  lu_solve<T>(D, W, piv, f0, k1);  // k1 = W^{-1} (f0 + h d T), T = 0
+  for (int j = 0; j < D; ++j) U[j] = u[j] + (h / 2) * k1[j];
+  rhs<T>(id, U, p, t + h / 2, f1);
+  for (int j = 0; j < D; ++j) rhs_v[j] = f1[j] - k1[j];
+  lu_solve<T>(D, W, piv, rhs_v, k2);
+  for (int j = 0; j < D; ++j) k2[j] += k1[j];  // k2 = W^{-1}(f1 - k1) + k1
+  for (int j = 0; j < D; ++j) unew[j] = u[j] + h * k2[j];
+  rhs<T>(id, unew, p, t + h, f2);
+  for (int j = 0; j < D; ++j) rhs_v[j] = f2[j] - e32 * (k2[j] - f1[j]) - 2 * (k1[j] - f0[j]);
+  lu_solve<T>(D, W, piv, rhs_v, k3);
+  for (int j = 0; j < D; ++j) err[j] = (h / 6) * (k1[j] - 2 * k2[j] + k3[j]);
+}
+
+// ----------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 Philox S-box with a Weyl key
+// schedule.  Round: (c0,c1,c2,c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)).
+void philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint64_t p0 = uint64_t(M0) * uint64_t(c[0]);
+    uint64_t p1 = uint64_t(M1) * uint64_t(c[2]);
+    uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0);
+    uint32_t hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+  }
+  for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+// Standard normal number `k` of trajectory stream `traj` (fp64: 2 normals per Philox call,
+// fp32: 4 normals per call).  Computed in double from exact uniforms.
+double normal_draw(uint64_t seed, uint64_t traj, uint64_t k, bool fp64) {
+  const double PI = 3.14159265358979323846;
+  uint64_t call = fp64 ? (k >> 1) : (k >> 2);
+  uint32_t ctr[4] = {uint32_t(call), uint32_t(call >> 32), uint32_t(traj), uint32_t(traj >> 32)};
+  uint32_t key[2] = {uint32_t(seed), uint32_t(seed >> 32)};
+  uint32_t x[4];
+  philox(ctr, key, x);
+  double ua, ub;
+  int which;
+  if (fp64) {
+    uint64_t a = (uint64_t(x[0]) << 32) | x[1];
+    uint64_t b = (uint64_t(x[2]) << 32) | x[3];
+    ua = (double(a >> 11) + 0.5) * std::ldexp(1.0, -53);
+    ub = (double(b >> 11) + 0.5) * std::ldexp(1.0, -53);
+    which = int(k & 1);
+  } else {
+    int pair = int((k & 3) >> 1);
+    ua = (double(x[2 * pair] >> 8) + 0.5) * std::ldexp(1.0, -24);
+    ub = (double(x[2 * pair + 1] >> 8) + 0.5) * std::ldexp(1.0, -24);
+    which = int(k & 1);
+  }
+  double r = std::sqrt(-2.0 * std::log(ua));
+  return which == 0 ? r * std::cos(2.0 * PI * ub) : r * std::sin(2.0 * PI * ub);
+}
+
+// ----------------------------------------------------------------------------------------------
+struct Opts {
+  int rhs, alg, D, P;
+  double dt, abstol, reltol, dt0;
+  long long maxiters;
+  const double* saveat;
+  int n_save;
+  unsigned long long seed;
+  long long index_offset;
+};
+
+// Hairer-Norsett-Wanner I, II.4: starting step size for an order-p method.
+template <class T>
+T initial_step(const Opts& o, const T* u0, const T* p, T t0, const T* f0, int order,
+               long long* fevals) {
+  const int D = o.D;
+  T sc[8], tmp[8], u1[8], f1[8];
+  for (int j = 0; j < D; ++j) sc[j] = T(o.abstol) + T(o.reltol) * std::fabs(u0[j]);
+  T d0 = rms_scaled(u0, sc, D);
+  T d1 = rms_scaled(f0, sc, D);
+  T h0 = (d0 < T(1e-5) || d1 < T(1e-5)) ? T(1e-6) : T(0.01) * d0 / d1;
+  for (int j = 0; j < D; ++j) u1[j] = u0[j] + h0 * f0[j];
+  rhs<T>(o.rhs, u1, p, t0 + h0, f1);
+  *fevals += 1;
+  for (int j = 0; j < D; ++j) tmp[j] = f1[j] - f0[j];
+  T d2 = rms_scaled(tmp, sc, D) / h0;
+  T dm = std::max(d1, d2);
+  T h1 = (dm <= T(1e-15)) ? std::max(T(1e-6), h0 * T(1e-3))
+                          : std::pow(T(0.01) / dm, T(1.0 / (order + 1)));
+  return std::min(T(100) * h0, h1);
+}
+
+template <class T>
+struct Traj {
+  const Opts* o;
+  T u[8], p[8];
+  T t0, tf;
+  T* out;  // [S or 1][D] row-major scratch owned by the caller
+  int S;
+  signed char status;
+  long long accepted, rejected, fevals;
+};
+
+template <class T>
+void fill_nan(T* v, int n) {
+  for (int i = 0; i < n; ++i) v[i] = std::numeric_limits<T>::quiet_NaN();
+}
+
+// ---- fixed-step drivers (Tsit5 fixed, RK4, Euler-Maruyama) ------------------------------------
+// n = ceil((tf - t0)/dt - 1e-12); steps 0..n-2 use h = dt, the last uses tf - (t0 + (n-1) dt);
+// step k starts at t_k = t0 + k dt.  A save time s is recorded after step
+// k_s = ceil((s - t0)/dt - 1e-12) (clamped to [0, n]); save times outside [t0, tf] give NaN.
+template <class T>
+void solve_fixed(Traj<T>& tr, uint64_t traj_index) {
+  const Opts& o = *tr.o;
+  const int D = o.D;
+  const double t0 = double(tr.t0), tf = double(tr.tf), dt = o.dt;
+  long long n = (tf > t0) ? (long long)std::ceil((tf - t0) / dt - 1e-12) : 0;
+  if (n < 0) n = 0;
+  long long nrun = std::min(n, o.maxiters);
+  const T h_reg = T(dt);
+  const T h_last = n > 0 ? T(tf - (t0 + double(n - 1) * dt)) : T(0);
+  const int S = o.n_save;  // number of save times (0: final state only)
+  const bool save_mode = o.n_save > 0;
+  auto ks_of = [&](int si) -> long long {
+    double s = o.saveat[si];
+    if (s < t0 || s > tf) return -1;
+    long long ks = (s <= t0) ? 0 : (long long)std::ceil((s - t0) / dt - 1e-12);
+    return std::min(std::max(ks, 0LL), n);
+  };
+  if (save_mode) fill_nan(tr.out, S * D);
+  int si = 0;
+  auto record_saves = [&](long long step_count) {
+    while (si < S) {
+      long long ks = ks_of(si);
+      if (ks < 0) { ++si; continue; }
+      if (ks != step_count) break;
+      for (int j = 0; j < D; ++j) tr.out[si * D + j] = tr.u[j];
+      ++si;
+    }
+  };
+  if (save_mode) record_saves(0);
+  T k1[8];
+  if (o.alg == ALG_TSIT5_FIXED) {
+    rhs<T>(o.rhs, tr.u, tr.p, tr.t0, k1);
+    tr.fevals += 1;
+  }
+  for (long long k = 0; k < nrun; ++k) {
+    const T h = (k == n - 1) ? h_last : h_reg;
+    const T tk = T(t0) + T(k) * T(dt);
+    T unew[8];
+    if (o.alg == ALG_TSIT5_FIXED) {
+      T err[8], k7[8];
+      tsit5_step<T>(o.rhs, D, tr.u, tr.p, tk, h, k1, unew, err, k7);
+      for (int j = 0; j < D; ++j) k1[j] = k7[j];
+      tr.fevals += 6;
+    } else if (o.alg == ALG_RK4) {
+      rk4_step<T>(o.rhs, D, tr.u, tr.p, tk, h, unew);
+      tr.fevals += 4;
+    } else {  // Euler-Maruyama: X_{k+1} = X_k + a(X_k) h + b(X_k) sqrt(h) Z_k
+      T a[8], b[8];
+      f_gbm<T>(tr.u, tr.p, tk, a);
+      g_gbm<T>(tr.u, tr.p, tk, b);
+      tr.fevals += 1;
+      const bool fp64 = sizeof(T) == 8;
+      T z = T(normal_draw(o.seed, traj_index, uint64_t(k), fp64));
+      T sq = std::sqrt(h);
+      for (int j = 0; j < D; ++j) unew[j] = tr.u[j] + a[j] * h + b[j] * sq * z;
+    }
+    for (int j = 0; j < D; ++j) tr.u[j] = unew[j];
+    tr.accepted += 1;
+    if (save_mode) record_saves(k + 1);
+  }
+  if (nrun < n) tr.status = ST_MAXITERS;
+  else if (!finite_all(tr.u, D)) tr.status = ST_NONFINITE;
+  if (!save_mode)
+    for (int j = 0; j < D; ++j) tr.out[j] = tr.u[j];
+}
+
+// ---- adaptive drivers (Tsit5 with PI control, Rosenbrock23) -----------------------------------
+template <class T>
+void solve_adaptive(Traj<T>& tr) {
+  const Opts& o = *tr.o;
+  const int D = o.D;
+  const bool is_r23 = (o.alg == ALG_ROS23);
+  const int k_ord = is_r23 ? 3 : 5;  // exponent denominators of the controller
+  const T beta1 = T(0.7 / k_ord), beta2 = T(0.4 / k_ord), rej_exp = T(1.0 / k_ord);
+  const T atol = T(o.abstol), rtol = T(o.reltol);
+  const int S = o.n_save;  // number of save times (0: final state only)
+  const bool save_mode = o.n_save > 0;
+  if (save_mode) fill_nan(tr.out, S * D);
+
+  Clock<T> clk;
+  clk.set(tr.t0);
+  int si = 0;
+  // skip save times before t0
+  while (si < S && T(o.saveat[si]) < tr.t0) ++si;
+
+  T fcur[8];  // k1 (Tsit5) or f0 (R23): f at the current state
+  rhs<T>(o.rhs, tr.u, tr.p, tr.t0, fcur);
+  tr.fevals += 1;
+  T h;
+  if (o.dt0 > 0) h = T(o.dt0);
+  else h = initial_step<T>(o, tr.u, tr.p, tr.t0, fcur, is_r23 ? 2 : 5, &tr.fevals);
+  T qold = T(QOLD_INIT);
+  long long attempts = 0;
+
+  for (;;) {
+    const bool stop_is_save = (si < S && T(o.saveat[si]) < tr.tf);
+    const T stop = stop_is_save ? T(o.saveat[si]) : tr.tf;
+    const T rem = clk.remaining(stop);
+    if (rem <= T(STOP_EPS) * std::max(T(1), std::fabs(stop))) {
+      clk.set(stop);
+      if (stop_is_save) {
+        for (int j = 0; j < D; ++j) tr.out[si * D + j] = tr.u[j];
+        ++si;
+        continue;
+      }
+      // reached tf: record every remaining save time equal to tf
+      while (si < S && T(o.saveat[si]) == tr.tf) {
+        for (int j = 0; j < D; ++j) tr.out[si * D + j] = tr.u[j];
+        ++si;
+      }
+      break;
+    }
+    if (attempts >= o.maxiters) { tr.status = ST_MAXITERS; break; }
+    const bool last = (h >= rem);
+    const T hs = last ? rem : h;
+    const T tnow = clk.value();
+    if (hs < T(Prec<T>::dtmin_factor) * std::max(T(1), std::fabs(tnow))) {
+      tr.status = ST_DT_MIN;
+      break;
+    }
+    T unew[8], err[8], fnew[8];
+    if (is_r23) {
+      ros23_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew);
+      tr.fevals += 2;
+    } else {
+      tsit5_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew);
+      tr.fevals += 6;
+    }
+    ++attempts;
+    // q = || E / (atol + rtol max(|u(t)|, |u(t+h)|)) ||  (RMS norm)
+    T sc[8];
+    for (int j = 0; j < D; ++j)
+      sc[j] = atol + rtol * std::max(std::fabs(tr.u[j]), std::fabs(unew[j]));
+    const T q = rms_scaled(err, sc, D);
+    if (!std::isfinite(q) || !finite_all(unew, D)) { tr.status = ST_NONFINITE; break; }
+    if (q <= T(1)) {
+      const T qg = std::max(q, T(Q_FLOOR));
+      T fac = T(ETA) * std::pow(qg, -beta1) * std::pow(qold, beta2);
+      fac = std::min(T(FAC_MAX), std::max(T(FAC_MIN), fac));
+      qold = std::max(q, T(QOLD_INIT));
+      for (int j = 0; j < D; ++j) { tr.u[j] = unew[j]; fcur[j] = fnew[j]; }
+      if (last) clk.set(stop);
+      else clk.add(hs);
+      tr.accepted += 1;
+      h = hs * fac;
+    } else {
+      const T qg = std::max(q, T(Q_FLOOR));
+      const T fac = std::max(T(FAC_MIN), T(ETA) * std::pow(qg, -rej_exp));
+      tr.rejected += 1;
+      h = hs * fac;
+    }
+  }
+  if (!save_mode)
+    for (int j = 0; j < D; ++j) tr.out[j] = tr.u[j];
+}
+
+// index helpers for the two supported layouts
+inline long long idx_in(int layout, long long i, int k, long long N, int width) {
+  return layout == LAYOUT_SOA ? (long long)k * N + i : i * width + k;
+}
+inline long long idx_out(int layout, long long i, int s, int k, long long N, int S, int D) {
+  return layout == LAYOUT_SOA ? ((long long)s * D + k) * N + i : (i * S + s) * (long long)D + k;
+}
+
+template <class T>
+void solve_range(const Opts& o, int layout, long long N, long long i0, long long i1,
+                 const double* params, const double* u0, const double* tspan, double* out,
+                 signed char* status, long long* stats) {
+  const int D = o.D, P = o.P;
+  const int S = o.n_save > 0 ? o.n_save : 1;
+  std::vector<T> buf(size_t(S) * D);
+  for (long long i = i0; i < i1; ++i) {
+    Traj<T> tr;
+    tr.o = &o;
+    for (int k = 0; k < P; ++k) tr.p[k] = T(params[idx_in(layout, i, k, N, P)]);
+    for (int k = 0; k < D; ++k) tr.u[k] = T(u0[idx_in(layout, i, k, N, D)]);
+    tr.t0 = T(tspan[idx_in(layout, i, 0, N, 2)]);
+    tr.tf = T(tspan[idx_in(layout, i, 1, N, 2)]);
+    tr.out = buf.data();
+    tr.S = S;
+    tr.status = ST_OK;
+    tr.accepted = tr.rejected = tr.fevals = 0;
+    if (o.alg == ALG_TSIT5_ADAPTIVE || o.alg == ALG_ROS23) solve_adaptive<T>(tr);
+    else solve_fixed<T>(tr, uint64_t(o.index_offset + i));
+    for (int s = 0; s < S; ++s)
+      for (int k = 0; k < D; ++k) out[idx_out(layout, i, s, k, N, S, D)] = double(buf[s * D + k]);
+    if (status) status[i] = tr.status;
+    if (stats) {
+      stats[i * 3 + 0] = tr.accepted;
+      stats[i * 3 + 1] = tr.rejected;
+      stats[i * 3 + 2] = tr.fevals;
+    }
+  }
+}
+
+template <class F>
+void parallel_for(long long N, int nthreads, F&& fn) {
+  if (nthreads <= 1 || N < 2) {
+    fn(0LL, N);
+    return;
+  }
+  std::vector<std::thread> th;
+  // interleaved chunks of 64 so that slow and fast trajectories spread over the threads
+  const long long chunk = 64;
+  const long long nchunks = (N + chunk - 1) / chunk;
+  for (int w = 0; w < nthreads; ++w) {
+    th.emplace_back([&, w]() {
+      for (long long c = w; c < nchunks; c += nthreads) {
+        long long a = c * chunk, b = std::min(N, a + chunk);
+        fn(a, b);
+      }
+    });
+  }
+  for (auto& t : th) t.join();
+}
+
+}  // namespace
+
+// ================================================================================================
+extern "C" {
+
+// Solve N trajectories.  All arrays are host double arrays; `layout` 0 = row-major
+// (params[N][P], u0[N][D], tspan[N][2], out[N][S][D]), 1 = structure of arrays
+// (params[P][N], u0[D][N], tspan[2][N], out[S][D][N]).  `precision` 0 = FP64, 1 = FP32 mode
+// (inputs rounded to float first by the caller; arithmetic in float, time compensated).
+// stats[N][3] = accepted, rejected, f-evaluations.  Returns 0, or -1 on bad arguments.
+int oracle_solve(int rhs_id, int alg, int precision, int layout, long long N,
+                 const double* params, const double* u0, const double* tspan, double dt,
+                 double abstol, double reltol, double dt0, long long maxiters,
+                 const double* saveat, int n_save, unsigned long long seed,
+                 long long index_offset, double* out, signed char* status, long long* stats,
+                 int nthreads) {
+  Model m = model_of(rhs_id);
+  if (m.D == 0 || N < 0 || alg < 1 || alg > 5) return -1;
+  if (alg == ALG_EM && rhs_id != RHS_GBM) return -1;
+  Opts o{rhs_id, alg, m.D, m.P, dt, abstol, reltol, dt0, maxiters, saveat, n_save, seed,
+         index_offset};
+  parallel_for(N, nthreads, [&](long long a, long long b) {
+    if (precision == 0)
+      solve_range<double>(o, layout, N, a, b, params, u0, tspan, out, status, stats);
+    else
+      solve_range<float>(o, layout, N, a, b, params, u0, tspan, out, status, stats);
+  });
+  return 0;
+}
+
+// One step of a method (for convergence-order and stability pins).  alg: 1 Tsit5, 3 RK4,
+// 4 Rosenbrock23, 5 Euler-Maruyama with the given normal z.  err (Tsit5/R23) may be NULL.
+int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t, double h,
+                double z, double* unew, double* err) {
+  Model m = model_of(rhs_id);
+  if (m.D == 0) return -1;
+  double e[8] = {0}, fx[8], k1[8];
+  if (alg == ALG_TSIT5_FIXED || alg == ALG_TSIT5_ADAPTIVE) {
+    rhs<double>(rhs_id, u, p, t, k1);
+    tsit5_step<double>(rhs_id, m.D, u, p, t, h, k1, unew, e, fx);
+  } else if (alg == ALG_RK4) {
+    rk4_step<double>(rhs_id, m.D, u, p, t, h, unew);
+  } else if (alg == ALG_ROS23) {
+    rhs<double>(rhs_id, u, p, t, k1);
+    ros23_step<double>(rhs_id, m.D, u, p, t, h, k1, unew, e, fx);
+  } else if (alg == ALG_EM) {
+    if (rhs_id != RHS_GBM) return -1;
+    double a[8], b[8];
+    f_gbm<double>(u, p, t, a);
+    g_gbm<double>(u, p, t, b);
+    for (int j = 0; j < m.D; ++j) unew[j] = u[j] + a[j] * h + b[j] * std::sqrt(h) * z;
+  } else {
+    return -1;
+  }
+  if (err)
+    for (int j = 0; j < m.D; ++j) err[j] = e[j];
+  return 0;
+}
+
+void oracle_tsit5_tableau(double* c, double* A, double* b, double* bhat) {
+  for (int i = 0; i < 7; ++i) {
+    c[i] = TS_C[i];
+    b[i] = TS_B[i];
+    bhat[i] = TS_BHAT[i];
+    for (int j = 0; j < 7; ++j) A[i * 7 + j] = TS_A[i][j];
+  }
+}
+
+int oracle_rhs(int rhs_id, const double* u, const double* p, double t, double* du) {
+  if (model_of(rhs_id).D == 0) return -1;
+  rhs<double>(rhs_id, u, p, t, du);
+  return 0;
+}
+
+int oracle_jac(int rhs_id, const double* u, const double* p, double t, double* Ju, double* Jp) {
+  if (model_of(rhs_id).D == 0) return -1;
+  if (Ju) jac_u<double>(rhs_id, u, p, t, Ju);
+  if (Jp) jac_p<double>(rhs_id, u, p, t, Jp);
+  return 0;
+}
+
+// Solve W x = b by the oracle's LU (for the linear-algebra pin).
+int oracle_lu_solve(int D, const double* W, const double* b, double* x) {
+  if (D < 1 || D > 8) return -1;
+  double LU[64];
+  int piv[8];
+  std::memcpy(LU, W, sizeof(double) * D * D);
+  lu_factor<double>(D, LU, piv);
+  lu_solve<double>(D, LU, piv, b, x);
+  return 0;
+}
+
+void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  philox(ctr, key, out);
+}
+
+// normals z_0..z_{n-1} of the stream of trajectory `traj`
+void oracle_normals(unsigned long long seed, unsigned long long traj, long long n, int fp64,
+                    double* out) {
+  for (long long k = 0; k < n; ++k) out[k] = normal_draw(seed, traj, uint64_t(k), fp64 != 0);
+}
+
+// Exact gradient of the discrete fixed-step Tsit5 map (FP64) by forward-mode tangents.
+// For each trajectory i: g_p[i][m] = sum_k grad_out[i][k] d u_k(tf) / d p_m,
+// g_u0[i][j] = sum_k grad_out[i][k] d u_k(tf) / d u0_j.  Row-major arrays.
+// Tangent recursion (chain rule through every stage): dU_i = du + h sum_j a_ij dk_j,
+// dk_i = f_u(U_i) dU_i + f_p(U_i) dtheta.
+int oracle_tsit5_fixed_grad(int rhs_id, long long N, const double* params, const double* u0,
+                            const double* tspan, double dt, const double* grad_out,
+                            double* g_p, double* g_u0, double* u_final, int nthreads) {
+  Model m = model_of(rhs_id);
+  if (m.D == 0) return -1;
+  const int D = m.D, P = m.P, M = m.P + m.D;
+  parallel_for(N, nthreads, [&](long long a, long long bnd) {
+    for (long long i = a; i < bnd; ++i) {
+      double u[8], p[8], du[8][16];  // du[j][m] = d u_j / d theta_m
+      for (int k = 0; k < P; ++k) p[k] = params[i * P + k];
+      for (int k = 0; k < D; ++k) u[k] = u0[i * D + k];
+      for (int j = 0; j < D; ++j)
+        for (int mm = 0; mm < M; ++mm) du[j][mm] = (mm == P + j) ? 1.0 : 0.0;
+      const double t0 = tspan[i * 2], tf = tspan[i * 2 + 1];
+      long long n = (tf > t0) ? (long long)std::ceil((tf - t0) / dt - 1e-12) : 0;
+      const double h_last = n > 0 ? tf - (t0 + double(n - 1) * dt) : 0.0;
+      for (long long s = 0; s < n; ++s) {
+        const double h = (s == n - 1) ? h_last : dt;
+        const double t = t0 + double(s) * dt;
+        double k[7][8], dk[7][8][16], U[8], dU[8][16], Ju[64], Jp[64];
+        for (int st = 0; st < 7; ++st) {
+          for (int j = 0; j < D; ++j) {
+            double acc = 0;
+            for (int q = 0; q < st; ++q) acc += TS_A[st][q] * k[q][j];
+            U[j] = u[j] + h * acc;
+            for (int mm = 0; mm < M; ++mm) {
+              double dacc = 0;
+              for (int q = 0; q < st; ++q) dacc += TS_A[st][q] * dk[q][j][mm];
+              dU[j][mm] = du[j][mm] + h * dacc;
+            }
+          }
+          rhs<double>(rhs_id, U, p, t + TS_C[st] * h, k[st]);
+          jac_u<double>(rhs_id, U, p, t + TS_C[st] * h, Ju);
+          jac_p<double>(rhs_id, U, p, t + TS_C[st] * h, Jp);
+          for (int j = 0; j < D; ++j)
+            for (int mm = 0; mm < M; ++mm) {
+              double v = (mm < P) ? Jp[j * P + mm] : 0.0;
+              for (int q = 0; q < D; ++q) v += Ju[j * D + q] * dU[q][mm];
+              dk[st][j][mm] = v;
+            }
+        }
+        for (int j = 0; j < D; ++j) {
+          double acc = 0;
+          for (int q = 0; q < 7; ++q) acc += TS_B[q] * k[q][j];
+          double unew = u[j] + h * acc;
+          for (int mm = 0; mm < M; ++mm) {
+            double dacc = 0;
+            for (int q = 0; q < 7; ++q) dacc += TS_B[q] * dk[q][j][mm];
+            du[j][mm] = du[j][mm] + h * dacc;
+          }
+          u[j] = unew;
+        }
+      }
+      for (int mm = 0; mm < M; ++mm) {
+        double g = 0;
+        for (int j = 0; j < D; ++j) g += grad_out[i * D + j] * du[j][mm];
+        if (mm < P) g_p[i * P + mm] = g;
+        else g_u0[i * D + (mm - P)] = g;
+      }
+      if (u_final)
+        for (int j = 0; j < D; ++j) u_final[i * D + j] = u[j];
+    }
+  });
+  return 0;
+}
+
+}  // extern "C"
