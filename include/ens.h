@@ -1,0 +1,156 @@
+/*
+ * ens.h -- C ABI of the GB300 ensemble ODE/SDE solver (libens.so).
+ *
+ * The operation: solve N independent copies of one small differential equation
+ *     du/dt = f(u, p, t),  u(t0) = u0            (ODE, arXiv 2304.06835 Sec. 3.1)
+ *     dX = a(X,t) dt + b(X,t) dW                  (SDE, Sec. 3.3)
+ * each with its own parameters p_j, initial state u0_j and time span [t0_j, tf_j]
+ * (the ensemble problem of Sec. 5.1.1: the U, P and F matrices).  One GPU thread integrates
+ * one trajectory with the whole step loop in registers (EnsembleGPUKernel, Sec. 5.2,
+ * the one-thread-per-trajectory kernel listing).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: ENS_OK or an ENS_E* code.  On error nothing was launched and
+ *     ens_last_error() returns a message (thread-local, valid until the next call).
+ *   - Array pointers passed to ens_solve* / ens_adjoint / ens_mlp_* are DEVICE pointers
+ *     owned by the caller, except where a parameter says HOST.  The library never frees
+ *     or allocates caller memory; it allocates only its own small scratch (queue counters,
+ *     adjoint replay buffers, staging for ens_solve_host), owned by the handle and freed
+ *     by ens_destroy.
+ *   - Calls are asynchronous on `cuda_stream` (a cudaStream_t, NULL = legacy default
+ *     stream) unless stated otherwise.  Calls that share a handle must be ordered on one
+ *     stream (they share the handle's scratch).
+ *   - Per-trajectory numerical failures do not fail a call: they go to status[i].
+ *   - N = 0 is a no-op that returns ENS_OK.
+ */
+#ifndef ENS_H_
+#define ENS_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ens_handle ens_handle;
+
+/* return codes */
+enum { ENS_OK = 0, ENS_EINVAL = 1, ENS_ENOTSUP = 2, ENS_ECUDA = 3, ENS_ENOMEM = 4 };
+
+/* right-hand sides compiled into the library (Appendix models):
+ *   LORENZ    D=3 P=3  p=(sigma, rho, beta)   f = (sigma(y2-y1), y1(rho-y3)-y2, y1 y2 - beta y3)
+ *             (Appendix, Lorenz problem; the paper writes beta as gamma)
+ *   ROBERTSON D=3 P=3  p=(k1, k2, k3)         f = (-k1 y1 + k3 y2 y3, k1 y1 - k3 y2 y3 - k2 y2^2,
+ *                                                   k2 y2^2)   (Appendix, Robertson equation)
+ *   GBM       D=1 P=2  p=(mu, sigma)          a = mu X, b = sigma X   (Appendix, linear SDE);
+ *             ODE algorithms integrate the drift only (u' = mu u). */
+enum { ENS_RHS_LORENZ = 1, ENS_RHS_ROBERTSON = 2, ENS_RHS_GBM = 3 };
+
+/* algorithms:
+ *   TSIT5_FIXED    Tsitouras 5(4) pair, fixed step dt (GPUTsit5, Sec. 5.2.1; RK step Sec. 3.1)
+ *   TSIT5_ADAPTIVE same with the embedded error estimate, scaled RMS ratio q and PI control
+ *                  h_new = eta q_{n-1}^{beta2} q_n^{beta1} h (Sec. 3.1)
+ *   RK4            classic 4-stage Runge-Kutta, fixed step (explicit RK family, Sec. 3.1)
+ *   ROS23          Rosenbrock23, the Shampine-Reichelt 2(3) Rosenbrock-W pair with a 3x3 LU of
+ *                  W = I - h d J held in registers (GPURosenbrock23, Sec. 5.2.1; Sec. 3.2.1)
+ *   EM             Euler-Maruyama, fixed step, diagonal noise (GPUEM, Sec. 5.2.2; Sec. 3.3) */
+enum { ENS_TSIT5_FIXED = 1, ENS_TSIT5_ADAPTIVE = 2, ENS_RK4 = 3, ENS_ROS23 = 4, ENS_EM = 5 };
+
+/* element type of every floating-point array of a call */
+enum { ENS_F32 = 0, ENS_F64 = 1 };
+
+/* array layouts (the paper's n x N state matrix U is the SOA layout, Sec. 5.1.1):
+ *   ROWMAJOR  params[N][P], u0[N][D], tspan[N][2], out[N][S][D]
+ *   SOA       params[P][N], u0[D][N], tspan[2][N], out[S][D][N]  (coalesced) */
+enum { ENS_LAYOUT_ROWMAJOR = 0, ENS_LAYOUT_SOA = 1 };
+
+/* per-trajectory status codes written to status[i] */
+enum { ENS_TRAJ_OK = 0, ENS_TRAJ_MAXITERS = 1, ENS_TRAJ_DT_MIN = 2, ENS_TRAJ_NONFINITE = 3 };
+
+/* scheduling of trajectories onto threads */
+enum {
+  ENS_SCHED_AUTO = 0,       /* adaptive algorithms: PERSISTENT; fixed-step: DIRECT */
+  ENS_SCHED_DIRECT = 1,     /* thread i integrates trajectories i, i+grid, ... */
+  ENS_SCHED_PERSISTENT = 2  /* resident grid; a lane that finishes fetches the next trajectory
+                               from an atomic queue (per-lane refill) */
+};
+
+#define ENS_MAX_SAVE 256
+
+typedef struct {
+  int alg;                /* ENS_TSIT5_FIXED ... ENS_EM */
+  int dtype;              /* ENS_F32 / ENS_F64 */
+  int layout;             /* ENS_LAYOUT_* */
+  double dt;              /* fixed-step size (TSIT5_FIXED, RK4, EM), > 0 */
+  double abstol, reltol;  /* adaptive tolerances; abstol >= 1e-30, reltol >= 0 */
+  double dt0;             /* adaptive first step; <= 0: Hairer-Norsett-Wanner starting step */
+  long long maxiters;     /* per-trajectory cap on step attempts (>= 1) */
+  const double* saveat;   /* HOST array of n_save ascending times, copied during the call;
+                             NULL/0: only the final state is written (S = 1) */
+  int n_save;             /* 0 .. ENS_MAX_SAVE */
+  unsigned long long seed;   /* SDE: Philox4x32-10 key */
+  long long index_offset;    /* SDE: trajectory i draws from stream index_offset + i */
+  int schedule;           /* ENS_SCHED_* */
+  int block;              /* threads per block; 0 = tuned / default */
+  int tpt;                /* trajectories per thread (1, 2 or 4); 0 = tuned / default */
+} ens_opts;
+
+/* Fill *o with defaults: TSIT5_ADAPTIVE, F32, SOA, abstol=reltol=1e-6, maxiters=1e6, auto. */
+void ens_opts_default(ens_opts* o);
+
+/* Create a solver handle for right-hand side `rhs_id` with state dimension D and parameter
+ * count P (ENS_EINVAL unless they match the model).  Binds to the current CUDA device. */
+int ens_create(ens_handle** h, int rhs_id, int D, int P);
+
+/* Destroy a handle and free its scratch.  Waits for work the handle launched to finish. */
+int ens_destroy(ens_handle* h);
+
+/* Solve N trajectories (Sec. 5.1.1 ensemble problem; algorithms above).
+ *   params, u0, tspan : device arrays in opts->dtype and opts->layout (read only)
+ *   out               : device array [N][S][D] (layout) written with the state at each save
+ *                       time (S = n_save) or the final state (S = 1).  Save times outside
+ *                       [t0, tf] of a trajectory, or after a failure, are written as NaN.
+ *                       Adaptive methods step exactly onto save times; fixed-step methods
+ *                       record after step ceil((s - t0)/dt - 1e-12).
+ *   status            : device int8 [N] (ENS_TRAJ_*) or NULL
+ *   stats             : device int32 [3][N] = accepted steps, rejected steps, f evaluations,
+ *                       or NULL
+ * Validation (ENS_EINVAL): null arrays, N < 0, unsupported (rhs, alg) pair (EM needs GBM),
+ * dt <= 0 for fixed-step, tolerances out of range, n_save > ENS_MAX_SAVE or unsorted. */
+int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, const void* tspan,
+              const ens_opts* opts, void* out, signed char* status, int* stats,
+              void* cuda_stream);
+
+/* Same as ens_solve with HOST arrays (pageable or pinned): copies inputs to the device,
+ * solves, copies out/status/stats back and synchronises the stream before returning
+ * (the paper's high-level path that passes the problem to the GPU and returns the result
+ * to the CPU, Sec. 6.1). */
+int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u0,
+                   const void* tspan, const ens_opts* opts, void* out, signed char* status,
+                   int* stats, void* cuda_stream);
+
+/* Raw Philox4x32-10 words (Salmon et al. SC'11) of the SDE streams: for trajectory
+ * j < n_traj and call c < n_calls, out[(c*4 + w)*n_traj + j] = word w of
+ * Philox(counter = (c lo, c hi, (index_offset+j) lo, hi), key = (seed lo, seed hi)).
+ * Device array out; used to check the generator bit-exactly. */
+int ens_philox4x32_10(unsigned long long seed, long long index_offset, long long n_traj,
+                      long long n_calls, unsigned int* out, void* cuda_stream);
+
+/* The standard normals Z_k (k < n_per) that drive Euler-Maruyama step k of trajectory j:
+ * out[k*n_traj + j] in `dtype` (F32: 4 normals per Philox call, F64: 2).  Box-Muller of the
+ * uniforms ((x>>9)+0.5)*2^-23 (F32) or ((x0:x1 >> 12)+0.5)*2^-52 (F64),
+ * exact and inside (0,1). */
+int ens_normals(unsigned long long seed, long long index_offset, long long n_traj,
+                long long n_per, int dtype, void* out, void* cuda_stream);
+
+/* Measurement aid (no counterpart in the paper): times `blocks` x `threads` threads that each
+ * run 8 independent FMA chains for 16*iters steps in `dtype`, synchronising the stream, and
+ * writes the achieved FMA instructions per second (lane-level) to *ops_per_s.  Used to
+ * measure the FP32 / FP64 FMA-pipe rate that bounds the solver. */
+int ens_probe_fma(int dtype, long long iters, int blocks, int threads, double* ops_per_s,
+                  void* cuda_stream);
+
+const char* ens_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENS_H_ */

@@ -27,8 +27,8 @@
 //   * automatic first step: Hairer-Norsett-Wanner I, II.4 starting step size algorithm.
 //   * Rosenbrock23: d = 1/(2+sqrt2), e32 = 6+sqrt2 (Shampine & Reichelt 1997, ode23s).
 //   * random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = seed,
-//     counter = (draw index lo, hi, trajectory index lo, hi); uniforms ((x>>8)+0.5)*2^-24 (FP32)
-//     or ((x0:x1 >> 11)+0.5)*2^-53 (FP64); Box-Muller normals.
+//     counter = (draw index lo, hi, trajectory index lo, hi); uniforms ((x>>9)+0.5)*2^-23 (FP32)
+//     or ((x0:x1 >> 12)+0.5)*2^-52 (FP64), both exact and inside (0,1); Box-Muller normals.
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared -pthread (see oracle/__init__.py).
 
@@ -355,13 +355,13 @@ double normal_draw(uint64_t seed, uint64_t traj, uint64_t k, bool fp64) {
   if (fp64) {
     uint64_t a = (uint64_t(x[0]) << 32) | x[1];
     uint64_t b = (uint64_t(x[2]) << 32) | x[3];
-    ua = (double(a >> 11) + 0.5) * std::ldexp(1.0, -53);
-    ub = (double(b >> 11) + 0.5) * std::ldexp(1.0, -53);
+    ua = (double(a >> 12) + 0.5) * std::ldexp(1.0, -52);
+    ub = (double(b >> 12) + 0.5) * std::ldexp(1.0, -52);
     which = int(k & 1);
   } else {
     int pair = int((k & 3) >> 1);
-    ua = (double(x[2 * pair] >> 8) + 0.5) * std::ldexp(1.0, -24);
-    ub = (double(x[2 * pair + 1] >> 8) + 0.5) * std::ldexp(1.0, -24);
+    ua = (double(x[2 * pair] >> 9) + 0.5) * std::ldexp(1.0, -23);
+    ub = (double(x[2 * pair + 1] >> 9) + 0.5) * std::ldexp(1.0, -23);
     which = int(k & 1);
   }
   double r = std::sqrt(-2.0 * std::log(ua));
@@ -555,7 +555,8 @@ void solve_adaptive(Traj<T>& tr) {
     for (int j = 0; j < D; ++j)
       sc[j] = atol + rtol * std::max(std::fabs(tr.u[j]), std::fabs(unew[j]));
     const T q = rms_scaled(err, sc, D);
-    if (!std::isfinite(q) || !finite_all(unew, D)) { tr.status = ST_NONFINITE; break; }
+    // NONFINITE: u_{n+1} has a NaN/Inf component or q is NaN; q = +Inf is an ordinary reject.
+    if (std::isnan(q) || !finite_all(unew, D)) { tr.status = ST_NONFINITE; break; }
     if (q <= T(1)) {
       const T qg = std::max(q, T(Q_FLOOR));
       T fac = T(ETA) * std::pow(qg, -beta1) * std::pow(qold, beta2);

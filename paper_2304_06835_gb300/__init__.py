@@ -1,0 +1,9 @@
+"""GB300-native ensemble ODE/SDE solver (arXiv 2304.06835's data-parallel hot path).
+
+The compute path is libens.so (hand-written CUDA for sm_103a behind a C ABI, include/ens.h);
+this package only marshals torch tensors into it.
+"""
+from ._lib import EnsError, lib  # noqa: F401
+from .solver import EnsembleSolver, make_opts, normals, philox_words  # noqa: F401
+
+__all__ = ["EnsembleSolver", "EnsError", "make_opts", "normals", "philox_words", "lib"]

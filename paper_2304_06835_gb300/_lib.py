@@ -1,0 +1,90 @@
+"""ctypes binding of libens.so: argument marshalling only (see include/ens.h).
+
+Every computation runs in the library's CUDA kernels.  If libens.so is missing this module
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libens.so")
+
+ENS_OK, ENS_EINVAL, ENS_ENOTSUP, ENS_ECUDA, ENS_ENOMEM = 0, 1, 2, 3, 4
+RHS = {"lorenz": 1, "robertson": 2, "gbm": 3}
+DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2)}
+ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5}
+F32, F64 = 0, 1
+LAYOUT = {"rowmajor": 0, "soa": 1}
+SCHED = {"auto": 0, "direct": 1, "persistent": 2}
+MAX_SAVE = 256
+STATUS = {0: "ok", 1: "maxiters", 2: "dt_min", 3: "nonfinite"}
+
+
+class EnsOpts(ctypes.Structure):
+    _fields_ = [
+        ("alg", ctypes.c_int), ("dtype", ctypes.c_int), ("layout", ctypes.c_int),
+        ("dt", ctypes.c_double), ("abstol", ctypes.c_double), ("reltol", ctypes.c_double),
+        ("dt0", ctypes.c_double), ("maxiters", ctypes.c_longlong),
+        ("saveat", ctypes.POINTER(ctypes.c_double)), ("n_save", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong), ("index_offset", ctypes.c_longlong),
+        ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
+    ]
+
+
+class EnsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("ens error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP = ctypes.c_void_p
+_LL = ctypes.c_longlong
+_INT = ctypes.c_int
+_ULL = ctypes.c_ulonglong
+
+SIGNATURES = {
+    "ens_opts_default": (None, [ctypes.POINTER(EnsOpts)]),
+    "ens_create": (_INT, [ctypes.POINTER(_VP), _INT, _INT, _INT]),
+    "ens_destroy": (_INT, [_VP]),
+    "ens_solve": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP, _VP]),
+    "ens_solve_host": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP,
+                              _VP]),
+    "ens_philox4x32_10": (_INT, [_ULL, _LL, _LL, _LL, _VP, _VP]),
+    "ens_normals": (_INT, [_ULL, _LL, _LL, _LL, _INT, _VP, _VP]),
+    "ens_probe_fma": (_INT, [_INT, _LL, _INT, _INT, ctypes.POINTER(ctypes.c_double), _VP]),
+    "ens_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libens.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libens.so is not built: run paper_2304_06835_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != ENS_OK:
+        msg = lib().ens_last_error()
+        raise EnsError(rc, msg.decode() if msg else "")
+
+
+def exported_symbols():
+    return [n for n in SIGNATURES if getattr(lib(), n, None) is not None]

@@ -1,0 +1,415 @@
+// abi.cu -- the extern "C" surface of libens.so: handles, validation, dispatch and the random
+// stream kernels.  Declarations and their contracts are in include/ens.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "ens_device.cuh"
+#include "ens_internal.h"
+
+namespace ens {
+cudaError_t dispatch_f32_lorenz(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                                cudaFuncAttributes*, int*);
+cudaError_t dispatch_f32_robertson(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                                   cudaFuncAttributes*, int*);
+cudaError_t dispatch_f32_gbm(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                             cudaFuncAttributes*, int*);
+cudaError_t dispatch_f64_lorenz(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                                cudaFuncAttributes*, int*);
+cudaError_t dispatch_f64_robertson(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                                   cudaFuncAttributes*, int*);
+cudaError_t dispatch_f64_gbm(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                             cudaFuncAttributes*, int*);
+
+typedef cudaError_t (*DispatchFn)(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                                  cudaFuncAttributes*, int*);
+
+static DispatchFn table(int rhs_id, int dtype) {
+  static const DispatchFn t[2][3] = {
+      {dispatch_f32_lorenz, dispatch_f32_robertson, dispatch_f32_gbm},
+      {dispatch_f64_lorenz, dispatch_f64_robertson, dispatch_f64_gbm}};
+  if (rhs_id < 1 || rhs_id > 3 || (dtype != ENS_F32 && dtype != ENS_F64)) return nullptr;
+  return t[dtype][rhs_id - 1];
+}
+
+cudaError_t launch_solve(int rhs_id, int alg, int dtype, const SolveArgs& a,
+                         const LaunchCfg& cfg, cudaStream_t stream, bool* supported) {
+  DispatchFn f = table(rhs_id, dtype);
+  if (!f) {
+    *supported = false;
+    return cudaSuccess;
+  }
+  return f(alg, &a, cfg, stream, supported, nullptr, nullptr);
+}
+
+cudaError_t solve_kernel_attrs(int rhs_id, int alg, int dtype, const LaunchCfg& cfg,
+                               cudaFuncAttributes* attr, int* bps) {
+  DispatchFn f = table(rhs_id, dtype);
+  bool sup = false;
+  if (!f) return cudaErrorInvalidValue;
+  cudaError_t e = f(alg, nullptr, cfg, 0, &sup, attr, bps);
+  if (!sup) return cudaErrorInvalidValue;
+  return e;
+}
+
+// ---- random streams --------------------------------------------------------------------------
+__global__ void k_philox(unsigned long long seed, long long off, long long n_traj,
+                         long long n_calls, unsigned int* out) {
+  const long long total = n_traj * n_calls;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long j = g % n_traj, c = g / n_traj;
+    const uint4 x = Philox::call(seed, (unsigned long long)(off + j), (unsigned long long)c);
+    out[(c * 4 + 0) * n_traj + j] = x.x;
+    out[(c * 4 + 1) * n_traj + j] = x.y;
+    out[(c * 4 + 2) * n_traj + j] = x.z;
+    out[(c * 4 + 3) * n_traj + j] = x.w;
+  }
+}
+
+template <class T>
+__global__ void k_normals(unsigned long long seed, long long off, long long n_traj,
+                          long long n_per, T* out) {
+  constexpr int PC = Normals<T>::per_call;
+  const long long n_calls = (n_per + PC - 1) / PC;
+  const long long total = n_traj * n_calls;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long j = g % n_traj, c = g / n_traj;
+    T z[PC];
+    Normals<T>::draw(Philox::call(seed, (unsigned long long)(off + j), (unsigned long long)c), z);
+#pragma unroll
+    for (int w = 0; w < PC; ++w) {
+      const long long k = c * PC + w;
+      if (k < n_per) out[k * n_traj + j] = z[w];
+    }
+  }
+}
+
+cudaError_t launch_philox(unsigned long long seed, long long off, long long n_traj,
+                          long long n_calls, unsigned int* out, cudaStream_t s) {
+  const long long total = n_traj * n_calls;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 1 << 20);
+  k_philox<<<grid, 256, 0, s>>>(seed, off, n_traj, n_calls, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normals(unsigned long long seed, long long off, long long n_traj,
+                           long long n_per, int dtype, void* out, cudaStream_t s) {
+  const int pc = dtype == ENS_F32 ? 4 : 2;
+  const long long total = n_traj * ((n_per + pc - 1) / pc);
+  const int grid = (int)std::min<long long>((total + 255) / 256, 1 << 20);
+  if (dtype == ENS_F32) k_normals<float><<<grid, 256, 0, s>>>(seed, off, n_traj, n_per, (float*)out);
+  else k_normals<double><<<grid, 256, 0, s>>>(seed, off, n_traj, n_per, (double*)out);
+  return cudaGetLastError();
+}
+
+// ---- FMA-pipe rate probe: 8 independent FMA chains per thread, ITER iterations ----------------
+template <class T>
+__global__ void k_fma_probe(long long iters, T seed, T* sink) {
+  T a0 = seed + T(threadIdx.x), a1 = a0 + T(1), a2 = a0 + T(2), a3 = a0 + T(3);
+  T a4 = a0 + T(4), a5 = a0 + T(5), a6 = a0 + T(6), a7 = a0 + T(7);
+  const T m = T(0.999999), c = T(1e-7);
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      a0 = M<T>::fma(a0, m, c); a1 = M<T>::fma(a1, m, c); a2 = M<T>::fma(a2, m, c);
+      a3 = M<T>::fma(a3, m, c); a4 = M<T>::fma(a4, m, c); a5 = M<T>::fma(a5, m, c);
+      a6 = M<T>::fma(a6, m, c); a7 = M<T>::fma(a7, m, c);
+    }
+  }
+  const T r = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+  if (r == T(-12345)) sink[0] = r;  // keeps the chains alive
+}
+
+cudaError_t probe_fma(int dtype, long long iters, int blocks, int threads, double* ops_per_s,
+                      cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  void* sink = nullptr;
+  cudaError_t e = cudaMalloc(&sink, 64);
+  if (e != cudaSuccess) return e;
+  // warm-up launch, then the timed one
+  for (int rep = 0; rep < 2; ++rep) {
+    if (rep == 1) cudaEventRecord(e0, s);
+    if (dtype == ENS_F32) k_fma_probe<float><<<blocks, threads, 0, s>>>(iters, 1.f, (float*)sink);
+    else k_fma_probe<double><<<blocks, threads, 0, s>>>(iters, 1.0, (double*)sink);
+  }
+  cudaEventRecord(e1, s);
+  e = cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  *ops_per_s = double(blocks) * threads * iters * 16.0 * 8.0 / (ms * 1e-3);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+}  // namespace ens
+
+// =================================================================================================
+using namespace ens;
+
+struct ens_handle {
+  int rhs_id, D, P;
+  int device;
+  int num_sms;
+  unsigned long long* queue;  // persistent-schedule counter (device)
+  // staging for ens_solve_host
+  void* stage;
+  size_t stage_bytes;
+  std::mutex mu;
+};
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(ENS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool model_dims(int rhs_id, int* D, int* P) {
+  switch (rhs_id) {
+    case ENS_RHS_LORENZ: *D = 3; *P = 3; return true;
+    case ENS_RHS_ROBERTSON: *D = 3; *P = 3; return true;
+    case ENS_RHS_GBM: *D = 1; *P = 2; return true;
+  }
+  return false;
+}
+
+bool is_fixed(int alg) { return alg == ENS_TSIT5_FIXED || alg == ENS_RK4 || alg == ENS_EM; }
+
+int validate(const ens_handle* h, long long N, const void* params, const void* u0,
+             const void* tspan, const ens_opts* o, const void* out) {
+  if (!h) return fail(ENS_EINVAL, "null handle");
+  if (!o) return fail(ENS_EINVAL, "null options");
+  if (N < 0) return fail(ENS_EINVAL, "N < 0");
+  if (o->alg < ENS_TSIT5_FIXED || o->alg > ENS_EM) return fail(ENS_EINVAL, "unknown algorithm");
+  if (o->dtype != ENS_F32 && o->dtype != ENS_F64) return fail(ENS_EINVAL, "unknown dtype");
+  if (o->layout != ENS_LAYOUT_ROWMAJOR && o->layout != ENS_LAYOUT_SOA)
+    return fail(ENS_EINVAL, "unknown layout");
+  if (o->alg == ENS_EM && h->rhs_id != ENS_RHS_GBM)
+    return fail(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM)");
+  if (is_fixed(o->alg) && !(o->dt > 0) ) return fail(ENS_EINVAL, "fixed-step methods need dt > 0");
+  if (is_fixed(o->alg) && !std::isfinite(o->dt)) return fail(ENS_EINVAL, "dt not finite");
+  if (!is_fixed(o->alg)) {
+    if (!(o->abstol >= 1e-30) || !std::isfinite(o->abstol))
+      return fail(ENS_EINVAL, "abstol must be in [1e-30, inf)");
+    if (!(o->reltol >= 0) || !std::isfinite(o->reltol))
+      return fail(ENS_EINVAL, "reltol must be >= 0");
+    if (!std::isfinite(o->dt0)) return fail(ENS_EINVAL, "dt0 not finite");
+  }
+  if (o->maxiters < 1) return fail(ENS_EINVAL, "maxiters must be >= 1");
+  if (o->maxiters > 2000000000LL) return fail(ENS_EINVAL, "maxiters must be <= 2e9");
+  if (o->n_save < 0 || o->n_save > ENS_MAX_SAVE)
+    return fail(ENS_EINVAL, "n_save out of range [0, ENS_MAX_SAVE]");
+  if (o->n_save > 0) {
+    if (!o->saveat) return fail(ENS_EINVAL, "saveat is NULL with n_save > 0");
+    for (int i = 0; i < o->n_save; ++i) {
+      if (!std::isfinite(o->saveat[i])) return fail(ENS_EINVAL, "saveat not finite");
+      if (i > 0 && o->saveat[i] < o->saveat[i - 1]) return fail(ENS_EINVAL, "saveat not sorted");
+    }
+  }
+  if (o->schedule < ENS_SCHED_AUTO || o->schedule > ENS_SCHED_PERSISTENT)
+    return fail(ENS_EINVAL, "unknown schedule");
+  if (o->block != 0 && (o->block < 32 || o->block > 1024 || o->block % 32 != 0))
+    return fail(ENS_EINVAL, "block must be 0 or a multiple of 32 in [32, 1024]");
+  if (o->tpt != 0 && o->tpt != 1 && o->tpt != 2 && o->tpt != 4)
+    return fail(ENS_EINVAL, "tpt must be 0, 1, 2 or 4");
+  if (N > 0 && (!params || !u0 || !tspan || !out)) return fail(ENS_EINVAL, "null array");
+  return ENS_OK;
+}
+
+void fill_args(SolveArgs* a, long long N, const void* params, const void* u0, const void* tspan,
+               const ens_opts* o, void* out, signed char* status, int* stats,
+               unsigned long long* queue) {
+  std::memset(a, 0, sizeof(*a));
+  a->N = N;
+  a->params = params;
+  a->u0 = u0;
+  a->tspan = tspan;
+  a->out = out;
+  a->status = status;
+  a->stats = stats;
+  a->layout = o->layout;
+  a->n_save = o->n_save;
+  a->dt = o->dt;
+  a->abstol = o->abstol;
+  a->reltol = o->reltol;
+  a->dt0 = o->dt0;
+  a->maxiters = o->maxiters;
+  a->seed = o->seed;
+  a->index_offset = o->index_offset;
+  a->queue = queue;
+  for (int i = 0; i < o->n_save; ++i) a->saveat[i] = o->saveat[i];
+}
+
+LaunchCfg resolve_cfg(const ens_handle* h, const ens_opts* o) {
+  LaunchCfg c;
+  c.schedule = o->schedule;
+  if (c.schedule == ENS_SCHED_AUTO)
+    c.schedule = is_fixed(o->alg) ? ENS_SCHED_DIRECT : ENS_SCHED_PERSISTENT;
+  c.block = o->block ? o->block : 128;
+  c.tpt = o->tpt ? o->tpt : 1;
+  c.num_sms = h->num_sms;
+  return c;
+}
+
+size_t elem_size(int dtype) { return dtype == ENS_F32 ? 4 : 8; }
+
+}  // namespace
+
+extern "C" {
+
+void ens_opts_default(ens_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->alg = ENS_TSIT5_ADAPTIVE;
+  o->dtype = ENS_F32;
+  o->layout = ENS_LAYOUT_SOA;
+  o->abstol = 1e-6;
+  o->reltol = 1e-6;
+  o->maxiters = 1000000;
+  o->schedule = ENS_SCHED_AUTO;
+}
+
+const char* ens_last_error(void) { return g_err.c_str(); }
+
+int ens_create(ens_handle** out, int rhs_id, int D, int P) {
+  if (!out) return fail(ENS_EINVAL, "null output pointer");
+  *out = nullptr;
+  int d, p;
+  if (!model_dims(rhs_id, &d, &p)) return fail(ENS_EINVAL, "unknown rhs_id");
+  if (D != d || P != p) return fail(ENS_EINVAL, "D/P do not match the model");
+  ens_handle* h = new ens_handle();
+  h->rhs_id = rhs_id;
+  h->D = D;
+  h->P = P;
+  h->stage = nullptr;
+  h->stage_bytes = 0;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->queue, 256);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "ens_create");
+  }
+  *out = h;
+  return ENS_OK;
+}
+
+int ens_destroy(ens_handle* h) {
+  if (!h) return ENS_OK;
+  cudaDeviceSynchronize();
+  cudaFree(h->queue);
+  if (h->stage) cudaFree(h->stage);
+  delete h;
+  return ENS_OK;
+}
+
+int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, const void* tspan,
+              const ens_opts* o, void* out, signed char* status, int* stats, void* stream) {
+  int rc = validate(h, N, params, u0, tspan, o, out);
+  if (rc) return rc;
+  if (N == 0) return ENS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  LaunchCfg cfg = resolve_cfg(h, o);
+  SolveArgs a;
+  fill_args(&a, N, params, u0, tspan, o, out, status, stats, h->queue);
+  if (cfg.schedule == ENS_SCHED_PERSISTENT) {
+    cudaError_t e = cudaMemsetAsync(h->queue, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+  }
+  bool sup = false;
+  cudaError_t e = launch_solve(h->rhs_id, o->alg, o->dtype, a, cfg, s, &sup);
+  if (!sup) return fail(ENS_ENOTSUP, "algorithm not available for this model");
+  if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+  return ENS_OK;
+}
+
+int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u0,
+                   const void* tspan, const ens_opts* o, void* out, signed char* status,
+                   int* stats, void* stream) {
+  int rc = validate(h, N, params, u0, tspan, o, out);
+  if (rc) return rc;
+  if (N == 0) return ENS_OK;
+  std::lock_guard<std::mutex> lock(h->mu);
+  const size_t es = elem_size(o->dtype);
+  const int S = o->n_save > 0 ? o->n_save : 1;
+  const size_t b_p = es * N * h->P, b_u = es * N * h->D, b_t = es * N * 2;
+  const size_t b_o = es * N * (size_t)S * h->D, b_s = status ? N : 0;
+  const size_t b_st = stats ? sizeof(int) * 3 * N : 0;
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t total = up(b_p) + up(b_u) + up(b_t) + up(b_o) + up(b_s) + up(b_st);
+  if (total > h->stage_bytes) {
+    if (h->stage) cudaFree(h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->stage, total);
+    if (e != cudaSuccess) return fail(ENS_ENOMEM, "staging allocation failed");
+    h->stage_bytes = total;
+  }
+  char* base = (char*)h->stage;
+  char* dp = base;
+  char* du = dp + up(b_p);
+  char* dt = du + up(b_u);
+  char* dout = dt + up(b_t);
+  char* dst = dout + up(b_o);
+  char* dstats = dst + up(b_s);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(dp, params, b_p, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(du, u0, b_u, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tspan, b_t, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  rc = ens_solve(h, N, dp, du, dt, o, dout, status ? (signed char*)dst : nullptr,
+                 stats ? (int*)dstats : nullptr, stream);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(out, dout, b_o, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, dst, b_s, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && stats) e = cudaMemcpyAsync(stats, dstats, b_st, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  return ENS_OK;
+}
+
+int ens_philox4x32_10(unsigned long long seed, long long index_offset, long long n_traj,
+                      long long n_calls, unsigned int* out, void* stream) {
+  if (n_traj < 0 || n_calls < 0) return fail(ENS_EINVAL, "negative size");
+  if (n_traj == 0 || n_calls == 0) return ENS_OK;
+  if (!out) return fail(ENS_EINVAL, "null output");
+  cudaError_t e = launch_philox(seed, index_offset, n_traj, n_calls, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? ENS_OK : cuda_fail(e, "philox launch");
+}
+
+int ens_normals(unsigned long long seed, long long index_offset, long long n_traj,
+                long long n_per, int dtype, void* out, void* stream) {
+  if (n_traj < 0 || n_per < 0) return fail(ENS_EINVAL, "negative size");
+  if (dtype != ENS_F32 && dtype != ENS_F64) return fail(ENS_EINVAL, "unknown dtype");
+  if (n_traj == 0 || n_per == 0) return ENS_OK;
+  if (!out) return fail(ENS_EINVAL, "null output");
+  cudaError_t e = launch_normals(seed, index_offset, n_traj, n_per, dtype, out,
+                                 (cudaStream_t)stream);
+  return e == cudaSuccess ? ENS_OK : cuda_fail(e, "normals launch");
+}
+
+int ens_probe_fma(int dtype, long long iters, int blocks, int threads, double* ops_per_s,
+                  void* stream) {
+  if (dtype != ENS_F32 && dtype != ENS_F64) return fail(ENS_EINVAL, "unknown dtype");
+  if (iters < 1 || blocks < 1 || threads < 32 || threads > 1024 || !ops_per_s)
+    return fail(ENS_EINVAL, "bad probe arguments");
+  cudaError_t e = probe_fma(dtype, iters, blocks, threads, ops_per_s, (cudaStream_t)stream);
+  return e == cudaSuccess ? ENS_OK : cuda_fail(e, "probe");
+}
+
+}  // extern "C"

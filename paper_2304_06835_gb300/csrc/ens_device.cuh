@@ -1,0 +1,423 @@
+// ens_device.cuh -- device-side building blocks of the ensemble solver (sm_103a).
+//
+// Everything here runs inside one thread and keeps its state in registers: the models'
+// right-hand sides and Jacobians (Appendix: Lorenz, Robertson, linear SDE), the Tsit5 / RK4 /
+// Rosenbrock23 / Euler-Maruyama steps (Sec. 3.1, 3.2.1, 3.3), the in-register LU of the
+// Rosenbrock matrix (Sec. 5.1.3 batched LU, fused per thread) and Philox4x32-10.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include <cuda_runtime.h>
+
+namespace ens {
+
+// ------------------------------------------------------------------------------------------
+// precision helpers
+template <class T>
+struct M;
+
+template <>
+struct M<float> {
+  static __device__ __forceinline__ float fma(float a, float b, float c) {
+    return __fmaf_rn(a, b, c);
+  }
+  static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
+  static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
+  static __device__ __forceinline__ float min(float a, float b) { return fminf(a, b); }
+  static __device__ __forceinline__ float sqrt(float a) { return sqrtf(a); }
+  static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+  static __device__ __forceinline__ bool finite(float a) { return isfinite(a); }
+  static constexpr double dtmin_factor = 1e-9;
+};
+
+template <>
+struct M<double> {
+  static __device__ __forceinline__ double fma(double a, double b, double c) {
+    return __fma_rn(a, b, c);
+  }
+  static __device__ __forceinline__ double abs(double a) { return fabs(a); }
+  static __device__ __forceinline__ double max(double a, double b) { return fmax(a, b); }
+  static __device__ __forceinline__ double min(double a, double b) { return fmin(a, b); }
+  static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
+  static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+  static __device__ __forceinline__ bool finite(double a) { return isfinite(a); }
+  static constexpr double dtmin_factor = 1e-14;
+};
+
+// ------------------------------------------------------------------------------------------
+// Models.  f = du/dt (drift for SDEs), g = diagonal diffusion, jac = df/du (row-major D x D),
+// vjp_u = (df/du)^T w, vjp_p = (df/dp)^T w.
+
+template <class T>
+struct Lorenz {
+  static constexpr int D = 3, P = 3;
+  static constexpr bool autonomous = true, has_noise = false;
+  static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) {
+    du[0] = p[0] * (u[1] - u[0]);                  // sigma (y2 - y1)
+    du[1] = M<T>::fma(u[0], p[1] - u[2], -u[1]);   // y1 (rho - y3) - y2
+    du[2] = M<T>::fma(u[0], u[1], -(p[2] * u[2])); // y1 y2 - beta y3
+  }
+  static __device__ __forceinline__ void jac(const T* u, const T* p, T, T* J) {
+    J[0] = -p[0]; J[1] = p[0]; J[2] = T(0);
+    J[3] = p[1] - u[2]; J[4] = T(-1); J[5] = -u[0];
+    J[6] = u[1]; J[7] = u[0]; J[8] = -p[2];
+  }
+  static __device__ __forceinline__ void vjp_u(const T* u, const T* p, T, const T* w, T* o) {
+    o[0] = M<T>::fma(-p[0], w[0], M<T>::fma(p[1] - u[2], w[1], u[1] * w[2]));
+    o[1] = M<T>::fma(p[0], w[0], M<T>::fma(u[0], w[2], -w[1]));
+    o[2] = M<T>::fma(-u[0], w[1], -(p[2] * w[2]));
+  }
+  static __device__ __forceinline__ void vjp_p(const T* u, const T*, T, const T* w, T* o) {
+    o[0] = (u[1] - u[0]) * w[0];
+    o[1] = u[0] * w[1];
+    o[2] = -u[2] * w[2];
+  }
+};
+
+template <class T>
+struct Robertson {
+  static constexpr int D = 3, P = 3;
+  static constexpr bool autonomous = true, has_noise = false;
+  static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) {
+    const T r1 = p[0] * u[0];           // k1 y1
+    const T r2 = p[1] * u[1] * u[1];    // k2 y2^2
+    const T r3 = p[2] * u[1] * u[2];    // k3 y2 y3
+    du[0] = r3 - r1;
+    du[1] = (r1 - r3) - r2;
+    du[2] = r2;
+  }
+  static __device__ __forceinline__ void jac(const T* u, const T* p, T, T* J) {
+    const T k3y3 = p[2] * u[2], k3y2 = p[2] * u[1], k2y2x2 = T(2) * p[1] * u[1];
+    J[0] = -p[0]; J[1] = k3y3; J[2] = k3y2;
+    J[3] = p[0]; J[4] = -k3y3 - k2y2x2; J[5] = -k3y2;
+    J[6] = T(0); J[7] = k2y2x2; J[8] = T(0);
+  }
+  static __device__ __forceinline__ void vjp_u(const T* u, const T* p, T, const T* w, T* o) {
+    const T k3y3 = p[2] * u[2], k3y2 = p[2] * u[1], k2y2x2 = T(2) * p[1] * u[1];
+    o[0] = p[0] * (w[1] - w[0]);
+    o[1] = M<T>::fma(k3y3, w[0] - w[1], k2y2x2 * (w[2] - w[1]));
+    o[2] = k3y2 * (w[0] - w[1]);
+  }
+  static __device__ __forceinline__ void vjp_p(const T* u, const T*, T, const T* w, T* o) {
+    o[0] = u[0] * (w[1] - w[0]);
+    o[1] = u[1] * u[1] * (w[2] - w[1]);
+    o[2] = u[1] * u[2] * (w[0] - w[1]);
+  }
+};
+
+template <class T>
+struct GBM {
+  static constexpr int D = 1, P = 2;
+  static constexpr bool autonomous = true, has_noise = true;
+  static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) { du[0] = p[0] * u[0]; }
+  static __device__ __forceinline__ void g(const T* u, const T* p, T, T* gu) { gu[0] = p[1] * u[0]; }
+  static __device__ __forceinline__ void jac(const T*, const T* p, T, T* J) { J[0] = p[0]; }
+  static __device__ __forceinline__ void vjp_u(const T*, const T* p, T, const T* w, T* o) {
+    o[0] = p[0] * w[0];
+  }
+  static __device__ __forceinline__ void vjp_p(const T* u, const T*, T, const T* w, T* o) {
+    o[0] = u[0] * w[0];
+    o[1] = T(0);
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// Tsitouras 5(4) coefficients (Tsitouras 2011; GPUTsit5, Sec. 5.2.1).  BT_i = bhat_i - b_i.
+struct Ts5 {
+  static constexpr double c2 = 0.161, c3 = 0.327, c4 = 0.9, c5 = 0.9800255409045097;
+  static constexpr double a21 = 0.161;
+  static constexpr double a31 = -0.008480655492356989, a32 = 0.335480655492357;
+  static constexpr double a41 = 2.897153057105493, a42 = -6.359448489975075,
+                          a43 = 4.3622954328695815;
+  static constexpr double a51 = 5.325864828439257, a52 = -11.748883564062828,
+                          a53 = 7.4955393428898365, a54 = -0.09249506636175525;
+  static constexpr double a61 = 5.86145544294642, a62 = -12.92096931784711,
+                          a63 = 8.159367898576159, a64 = -0.071584973281401,
+                          a65 = -0.028269050394068383;
+  static constexpr double a71 = 0.09646076681806523, a72 = 0.01, a73 = 0.4798896504144996,
+                          a74 = 1.379008574103742, a75 = -3.290069515436081,
+                          a76 = 2.324710524099774;
+  static constexpr double bt1 = 0.09468075576583945 - a71, bt2 = 0.009183565540343254 - a72,
+                          bt3 = 0.4877705284247616 - a73, bt4 = 1.234297566930479 - a74,
+                          bt5 = -2.7077123499835256 - a75, bt6 = 1.866628418170587 - a76,
+                          bt7 = 0.015151515151515152;
+};
+
+// One Tsit5 step: U_i = u + h sum_j a_ij k_j, k_i = f(U_i, t + c_i h) (Sec. 3.1); stage 7 is
+// u_{n+1} itself (FSAL) and k7 = f(u_{n+1}).  With WANT_ERR, es = sum_j (bhat_j - b_j) k_j
+// (the error estimate is h * es).
+template <class RHS, class T, bool WANT_ERR>
+__device__ __forceinline__ void tsit5_step(const T* u, const T* p, T t, T h, const T* k1,
+                                           T* unew, T* es, T* k7) {
+  constexpr int D = RHS::D;
+  typedef M<T> m;
+  T U[D], k2[D], k3[D], k4[D], k5[D], k6[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) U[j] = m::fma(h, T(Ts5::a21) * k1[j], u[j]);
+  RHS::f(U, p, t + T(Ts5::c2) * h, k2);
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    U[j] = m::fma(h, m::fma(T(Ts5::a32), k2[j], T(Ts5::a31) * k1[j]), u[j]);
+  RHS::f(U, p, t + T(Ts5::c3) * h, k3);
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    U[j] = m::fma(h, m::fma(T(Ts5::a43), k3[j], m::fma(T(Ts5::a42), k2[j], T(Ts5::a41) * k1[j])),
+                  u[j]);
+  RHS::f(U, p, t + T(Ts5::c4) * h, k4);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    T s = T(Ts5::a51) * k1[j];
+    s = m::fma(T(Ts5::a52), k2[j], s);
+    s = m::fma(T(Ts5::a53), k3[j], s);
+    s = m::fma(T(Ts5::a54), k4[j], s);
+    U[j] = m::fma(h, s, u[j]);
+  }
+  RHS::f(U, p, t + T(Ts5::c5) * h, k5);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    T s = T(Ts5::a61) * k1[j];
+    s = m::fma(T(Ts5::a62), k2[j], s);
+    s = m::fma(T(Ts5::a63), k3[j], s);
+    s = m::fma(T(Ts5::a64), k4[j], s);
+    s = m::fma(T(Ts5::a65), k5[j], s);
+    U[j] = m::fma(h, s, u[j]);
+  }
+  RHS::f(U, p, t + h, k6);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    T s = T(Ts5::a71) * k1[j];
+    s = m::fma(T(Ts5::a72), k2[j], s);
+    s = m::fma(T(Ts5::a73), k3[j], s);
+    s = m::fma(T(Ts5::a74), k4[j], s);
+    s = m::fma(T(Ts5::a75), k5[j], s);
+    s = m::fma(T(Ts5::a76), k6[j], s);
+    unew[j] = m::fma(h, s, u[j]);
+  }
+  RHS::f(unew, p, t + h, k7);
+  if (WANT_ERR) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      T s = T(Ts5::bt1) * k1[j];
+      s = m::fma(T(Ts5::bt2), k2[j], s);
+      s = m::fma(T(Ts5::bt3), k3[j], s);
+      s = m::fma(T(Ts5::bt4), k4[j], s);
+      s = m::fma(T(Ts5::bt5), k5[j], s);
+      s = m::fma(T(Ts5::bt6), k6[j], s);
+      s = m::fma(T(Ts5::bt7), k7[j], s);
+      es[j] = s;
+    }
+  }
+}
+
+// Classic RK4 step.
+template <class RHS, class T>
+__device__ __forceinline__ void rk4_step(const T* u, const T* p, T t, T h, T* unew) {
+  constexpr int D = RHS::D;
+  typedef M<T> m;
+  T k1[D], k2[D], k3[D], k4[D], U[D];
+  const T hh = T(0.5) * h;
+  RHS::f(u, p, t, k1);
+#pragma unroll
+  for (int j = 0; j < D; ++j) U[j] = m::fma(hh, k1[j], u[j]);
+  RHS::f(U, p, t + hh, k2);
+#pragma unroll
+  for (int j = 0; j < D; ++j) U[j] = m::fma(hh, k2[j], u[j]);
+  RHS::f(U, p, t + hh, k3);
+#pragma unroll
+  for (int j = 0; j < D; ++j) U[j] = m::fma(h, k3[j], u[j]);
+  RHS::f(U, p, t + h, k4);
+  const T h6 = h * T(1.0 / 6.0);
+#pragma unroll
+  for (int j = 0; j < D; ++j) unew[j] = m::fma(h6, (k1[j] + k4[j]) + T(2) * (k2[j] + k3[j]), u[j]);
+}
+
+// ------------------------------------------------------------------------------------------
+// Dense LU with partial pivoting, small D, fully unrolled; the row exchanges are done with
+// selects so that no lane branches.  Ties keep the lower row (strict > comparison).
+template <class T, int D>
+struct LU {
+  T a[D][D];          // L (unit, strictly lower) and U (upper; diagonal stored as reciprocal)
+  bool sw[D][D];      // sw[c][r]: rows c and r were exchanged for column c (at most one r)
+
+  __device__ __forceinline__ void factor(T (&W)[D][D]) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      // pivot: the first row of largest |W[r][c]|, r >= c; then exchange it with row c
+      T big = M<T>::abs(W[c][c]);
+      int best = c;
+#pragma unroll
+      for (int r = c + 1; r < D; ++r) {
+        const T v = M<T>::abs(W[r][c]);
+        const bool g = v > big;
+        big = g ? v : big;
+        best = g ? r : best;
+      }
+#pragma unroll
+      for (int r = c + 1; r < D; ++r) {
+        const bool x = (best == r);
+        sw[c][r] = x;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const T wc = W[c][j], wr = W[r][j];
+          W[c][j] = x ? wr : wc;
+          W[r][j] = x ? wc : wr;
+        }
+      }
+      const T inv = M<T>::rcp(W[c][c]);
+      W[c][c] = inv;
+#pragma unroll
+      for (int r = c + 1; r < D; ++r) {
+        const T l = W[r][c] * inv;
+        W[r][c] = l;
+#pragma unroll
+        for (int j = c + 1; j < D; ++j) W[r][j] = M<T>::fma(-l, W[c][j], W[r][j]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int j = 0; j < D; ++j) a[r][j] = W[r][j];
+  }
+
+  // x = W^{-1} b
+  __device__ __forceinline__ void solve(const T* b, T* x) const {
+    T y[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) y[r] = b[r];
+    // apply the row exchanges in elimination order, then forward substitution with unit L
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+#pragma unroll
+      for (int r = c + 1; r < D; ++r) {
+        const T yc = y[c], yr = y[r];
+        y[c] = sw[c][r] ? yr : yc;
+        y[r] = sw[c][r] ? yc : yr;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int j = 0; j < r; ++j) y[r] = M<T>::fma(-a[r][j], y[j], y[r]);
+#pragma unroll
+    for (int r = D - 1; r >= 0; --r) {
+      T v = y[r];
+#pragma unroll
+      for (int j = r + 1; j < D; ++j) v = M<T>::fma(-a[r][j], x[j], v);
+      x[r] = v * a[r][r];
+    }
+  }
+};
+
+// One Rosenbrock23 (ode23s) step from (u, t) with f0 = f(u, t); W = I - h d J:
+//   k1 = W^-1 f0,  f1 = f(u + h/2 k1),  k2 = W^-1 (f1 - k1) + k1,  u_{n+1} = u + h k2,
+//   f2 = f(u_{n+1}),  k3 = W^-1 (f2 - e32 (k2 - f1) - 2 (k1 - f0)),  err = h/6 (k1 - 2 k2 + k3).
+// Autonomous models only (df/dt = 0).  Writes es = (k1 - 2 k2 + k3)/6 (err = h * es).
+template <class RHS, class T>
+__device__ __forceinline__ void ros23_step(const T* u, const T* p, T t, T h, const T* f0, T* unew,
+                                           T* es, T* f2) {
+  static_assert(RHS::autonomous, "Rosenbrock23 here assumes df/dt = 0");
+  constexpr int D = RHS::D;
+  typedef M<T> m;
+  const T d = T(0.29289321881345247559915563789515);   // 1 / (2 + sqrt 2)
+  const T e32 = T(7.4142135623730950488016887242097);  // 6 + sqrt 2
+  T Jf[D * D];
+  RHS::jac(u, p, t, Jf);
+  T W[D][D];
+  const T hd = h * d;
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) W[r][c] = m::fma(-hd, Jf[r * D + c], (r == c) ? T(1) : T(0));
+  LU<T, D> lu;
+  lu.factor(W);
+  T k1[D], k2[D], k3[D], f1[D], U[D], v[D];
+  lu.solve(f0, k1);
+  const T hh = T(0.5) * h;
+#pragma unroll
+  for (int j = 0; j < D; ++j) U[j] = m::fma(hh, k1[j], u[j]);
+  RHS::f(U, p, t + hh, f1);
+#pragma unroll
+  for (int j = 0; j < D; ++j) v[j] = f1[j] - k1[j];
+  lu.solve(v, k2);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    k2[j] += k1[j];
+    unew[j] = m::fma(h, k2[j], u[j]);
+  }
+  RHS::f(unew, p, t + h, f2);
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    v[j] = m::fma(-e32, k2[j] - f1[j], m::fma(T(-2), k1[j] - f0[j], f2[j]));
+  lu.solve(v, k3);
+#pragma unroll
+  for (int j = 0; j < D; ++j) es[j] = (m::fma(T(-2), k2[j], k1[j]) + k3[j]) * T(1.0 / 6.0);
+}
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+struct Philox {
+  static __device__ __forceinline__ uint4 gen(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      if (r > 0) {
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+      }
+      const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+      const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+      c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+  }
+  static __device__ __forceinline__ uint4 call(unsigned long long seed, unsigned long long traj,
+                                               unsigned long long idx) {
+    return gen(make_uint4(uint32_t(idx), uint32_t(idx >> 32), uint32_t(traj),
+                          uint32_t(traj >> 32)),
+               make_uint2(uint32_t(seed), uint32_t(seed >> 32)));
+  }
+};
+
+// Normals from one Philox call: 4 in FP32, 2 in FP64 (Box-Muller of exact uniforms).
+template <class T>
+struct Normals;
+
+template <>
+struct Normals<float> {
+  static constexpr int per_call = 4;
+  static __device__ __forceinline__ float uni(uint32_t x) {
+    // ((x >> 9) + 0.5) * 2^-23: exact in float, inside (0, 1)
+    return __fmaf_rn(__uint2float_rn(x >> 9), 1.1920928955078125e-07f, 5.9604644775390625e-08f);
+  }
+  static __device__ __forceinline__ void draw(uint4 x, float* z) {
+    float s, c;
+    float r = sqrtf(-2.0f * logf(uni(x.x)));
+    sincospif(2.0f * uni(x.y), &s, &c);
+    z[0] = r * c;
+    z[1] = r * s;
+    r = sqrtf(-2.0f * logf(uni(x.z)));
+    sincospif(2.0f * uni(x.w), &s, &c);
+    z[2] = r * c;
+    z[3] = r * s;
+  }
+};
+
+template <>
+struct Normals<double> {
+  static constexpr int per_call = 2;
+  static __device__ __forceinline__ double uni(uint32_t hi, uint32_t lo) {
+    const unsigned long long v = ((unsigned long long)hi << 32) | lo;
+    // ((v >> 12) + 0.5) * 2^-52: exact in double, inside (0, 1)
+    return __fma_rn(__ull2double_rn(v >> 12), 2.220446049250313e-16, 1.1102230246251565e-16);
+  }
+  static __device__ __forceinline__ void draw(uint4 x, double* z) {
+    double s, c;
+    const double r = ::sqrt(-2.0 * ::log(uni(x.x, x.y)));
+    sincospi(2.0 * uni(x.z, x.w), &s, &c);
+    z[0] = r * c;
+    z[1] = r * s;
+  }
+};
+
+}  // namespace ens

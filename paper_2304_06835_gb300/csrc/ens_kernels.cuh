@@ -1,0 +1,440 @@
+// ens_kernels.cuh -- per-trajectory integrators and the fused ensemble kernels.
+//
+// One thread integrates one trajectory with the whole step loop in registers (the
+// EnsembleGPUKernel design, Sec. 5.2 and its kernel listing: init, then step until t = tf,
+// saving values).  Two schedules:
+//   * direct:     thread i owns trajectories i, i + grid, ...
+//   * persistent: a resident grid; whenever a lane finishes a trajectory it takes the next
+//                 index from an atomic queue (warp-aggregated atomicAdd), so lanes of a warp
+//                 whose trajectories need different step counts stay busy (the divergence
+//                 of adaptive stepping noted in Sec. 6.4).  TPT slots per thread give ILP.
+#pragma once
+
+#include "ens_device.cuh"
+#include "ens_internal.h"
+
+namespace ens {
+
+constexpr double kStopEps = 1e-12;    // remainder counted as having arrived (relative)
+constexpr double kEta = 0.9;          // PI safety factor
+constexpr float kLog2QoldInit = -13.287712379549449f;  // log2(1e-4)
+
+// ------------------------------------------------------------------------------------------
+// time accumulator: plain in FP64; Neumaier-compensated pair in FP32
+template <class T>
+struct Clock {
+  T hi, lo;
+  __device__ __forceinline__ void set(T v) { hi = v; lo = T(0); }
+  __device__ __forceinline__ T value() const { return hi + lo; }
+  __device__ __forceinline__ T remaining(T stop) const { return (stop - hi) - lo; }
+  __device__ __forceinline__ void add(T h) {
+    const T s = hi + h;
+    const T c = (fabsf(hi) >= fabsf(h)) ? ((hi - s) + h) : ((h - s) + hi);
+    lo += c;
+    hi = s;
+  }
+};
+template <>
+struct Clock<double> {
+  double hi;
+  __device__ __forceinline__ void set(double v) { hi = v; }
+  __device__ __forceinline__ double value() const { return hi; }
+  __device__ __forceinline__ double remaining(double stop) const { return stop - hi; }
+  __device__ __forceinline__ void add(double h) { hi += h; }
+};
+
+// ------------------------------------------------------------------------------------------
+// global-memory indexing for the two layouts
+__device__ __forceinline__ long long in_idx(int layout, long long i, int k, long long N, int w) {
+  return layout == ENS_LAYOUT_SOA ? (long long)k * N + i : i * w + k;
+}
+__device__ __forceinline__ long long out_idx(int layout, long long i, int s, int k, long long N,
+                                             int S, int D) {
+  return layout == ENS_LAYOUT_SOA ? ((long long)s * D + k) * N + i
+                                  : (i * S + s) * (long long)D + k;
+}
+
+template <class T>
+__device__ __forceinline__ T ldg(const void* base, long long idx) {
+  return __ldg(static_cast<const T*>(base) + idx);
+}
+
+template <class T>
+__device__ __forceinline__ T nan_of();
+template <>
+__device__ __forceinline__ float nan_of<float>() { return __int_as_float(0x7fc00000); }
+template <>
+__device__ __forceinline__ double nan_of<double>() {
+  return __longlong_as_double(0x7ff8000000000000LL);
+}
+
+template <class RHS, class T>
+__device__ __forceinline__ void load_problem(const SolveArgs& a, long long i, T* p, T* u, T& t0,
+                                             T& tf) {
+#pragma unroll
+  for (int k = 0; k < RHS::P; ++k) p[k] = ldg<T>(a.params, in_idx(a.layout, i, k, a.N, RHS::P));
+#pragma unroll
+  for (int k = 0; k < RHS::D; ++k) u[k] = ldg<T>(a.u0, in_idx(a.layout, i, k, a.N, RHS::D));
+  t0 = ldg<T>(a.tspan, in_idx(a.layout, i, 0, a.N, 2));
+  tf = ldg<T>(a.tspan, in_idx(a.layout, i, 1, a.N, 2));
+}
+
+template <class RHS, class T>
+__device__ __forceinline__ void write_slot(const SolveArgs& a, long long i, int s, const T* v) {
+  const int S = a.n_save > 0 ? a.n_save : 1;
+  T* o = static_cast<T*>(a.out);
+#pragma unroll
+  for (int k = 0; k < RHS::D; ++k) o[out_idx(a.layout, i, s, k, a.N, S, RHS::D)] = v[k];
+}
+
+template <class RHS, class T>
+__device__ __forceinline__ void write_nan_slot(const SolveArgs& a, long long i, int s) {
+  T v[RHS::D];
+#pragma unroll
+  for (int k = 0; k < RHS::D; ++k) v[k] = nan_of<T>();
+  write_slot<RHS, T>(a, i, s, v);
+}
+
+__device__ __forceinline__ void write_stats(const SolveArgs& a, long long i, signed char st,
+                                            int acc, int rej, int fev) {
+  if (a.status) a.status[i] = st;
+  if (a.stats) {
+    a.stats[i] = acc;
+    a.stats[a.N + i] = rej;
+    a.stats[2 * a.N + i] = fev;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T rms_scaled(const T* x, const T* sc, int D) {
+  T s = T(0);
+  for (int j = 0; j < D; ++j) {
+    const T r = x[j] / sc[j];
+    s = M<T>::fma(r, r, s);
+  }
+  return M<T>::sqrt(s / T(D));
+}
+
+// ------------------------------------------------------------------------------------------
+// Adaptive integrators: Tsit5 with PI control (Sec. 3.1) and Rosenbrock23 (Sec. 3.2.1).
+enum { METH_TSIT5 = 0, METH_ROS23 = 1 };
+
+template <class RHS, class T, int METH>
+struct Adaptive {
+  static constexpr int D = RHS::D, P = RHS::P;
+  // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k
+  static constexpr float kOrd = (METH == METH_TSIT5) ? 5.f : 3.f;
+  static constexpr int kInitOrder = (METH == METH_TSIT5) ? 5 : 2;
+  static constexpr int kFevPerAttempt = (METH == METH_TSIT5) ? 6 : 2;
+
+  T u[D], fk[D], p[P];
+  Clock<T> t;
+  T tf, h;
+  float lq;  // log2 q_{n-1}
+  int attempts, rejected, si, fev0;
+  signed char st;
+  long long idx;
+
+  __device__ __forceinline__ void init(long long i, const SolveArgs& a) {
+    idx = i;
+    T t0;
+    load_problem<RHS, T>(a, i, p, u, t0, tf);
+    t.set(t0);
+    RHS::f(u, p, t0, fk);
+    fev0 = 1;
+    if (a.dt0 > 0) {
+      h = T(a.dt0);
+    } else {
+      h = initial_step(a, t0);
+      fev0 = 2;
+    }
+    lq = kLog2QoldInit;
+    attempts = 0;
+    rejected = 0;
+    st = ENS_TRAJ_OK;
+    si = 0;
+    while (si < a.n_save && T(a.saveat[si]) < t0) {
+      write_nan_slot<RHS, T>(a, idx, si);
+      ++si;
+    }
+  }
+
+  // Hairer-Norsett-Wanner I, II.4: starting step size
+  __device__ __forceinline__ T initial_step(const SolveArgs& a, T t0) {
+    T sc[D], tmp[D], u1[D], f1[D];
+    const T atol = T(a.abstol), rtol = T(a.reltol);
+    for (int j = 0; j < D; ++j) sc[j] = atol + rtol * M<T>::abs(u[j]);
+    const T d0 = rms_scaled(u, sc, D);
+    const T d1 = rms_scaled(fk, sc, D);
+    const T h0 = (d0 < T(1e-5) || d1 < T(1e-5)) ? T(1e-6) : T(0.01) * d0 / d1;
+    for (int j = 0; j < D; ++j) u1[j] = u[j] + h0 * fk[j];
+    RHS::f(u1, p, t0 + h0, f1);
+    for (int j = 0; j < D; ++j) tmp[j] = f1[j] - fk[j];
+    const T d2 = rms_scaled(tmp, sc, D) / h0;
+    const T dm = M<T>::max(d1, d2);
+    const T h1 = (dm <= T(1e-15)) ? M<T>::max(T(1e-6), h0 * T(1e-3))
+                                  : T(pow(double(T(0.01) / dm), 1.0 / (kInitOrder + 1)));
+    return M<T>::min(T(100) * h0, h1);
+  }
+
+  // one attempt; returns true when the trajectory is finished
+  __device__ __forceinline__ bool advance(const SolveArgs& a) {
+    T stop, rem;
+    for (;;) {
+      const bool stop_is_save = si < a.n_save && T(a.saveat[si]) < tf;
+      stop = stop_is_save ? T(a.saveat[si]) : tf;
+      rem = t.remaining(stop);
+      if (rem > T(kStopEps) * M<T>::max(T(1), M<T>::abs(stop))) break;
+      t.set(stop);
+      if (stop_is_save) {
+        write_slot<RHS, T>(a, idx, si, u);
+        ++si;
+        continue;
+      }
+      while (si < a.n_save && T(a.saveat[si]) == tf) {
+        write_slot<RHS, T>(a, idx, si, u);
+        ++si;
+      }
+      return true;
+    }
+    if (attempts >= a.maxiters) {
+      st = ENS_TRAJ_MAXITERS;
+      return true;
+    }
+    const bool last = h >= rem;
+    const T hs = last ? rem : h;
+    const T tnow = t.value();
+    if (hs < T(M<T>::dtmin_factor) * M<T>::max(T(1), M<T>::abs(tnow))) {
+      st = ENS_TRAJ_DT_MIN;
+      return true;
+    }
+    T unew[D], es[D], fnew[D];
+    if (METH == METH_TSIT5) tsit5_step<RHS, T, true>(u, p, tnow, hs, fk, unew, es, fnew);
+    else ros23_step<RHS, T>(u, p, tnow, hs, fk, unew, es, fnew);
+    ++attempts;
+    // q^2 = (1/D) sum_j (E_j / (atol + rtol max(|u_j|, |unew_j|)))^2 with E_j = h es_j.
+    // The ratios are formed in FP32 for both precisions (E itself is accumulated in T).
+    const T atol = T(a.abstol), rtol = T(a.reltol);
+    float r2 = 0.f;
+    bool fin = true;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const T sc = M<T>::fma(rtol, M<T>::max(M<T>::abs(u[j]), M<T>::abs(unew[j])), atol);
+      const float r = __fdividef(float(hs * es[j]), float(sc));
+      r2 = __fmaf_rn(r, r, r2);
+      fin = fin && M<T>::finite(unew[j]);
+    }
+    const float q2 = r2 * (1.f / float(D));
+    if (!fin || isnan(q2)) {
+      st = ENS_TRAJ_NONFINITE;
+      return true;
+    }
+    const bool accept = q2 <= 1.f;
+    // PI control: accept fac = eta q_n^{-beta1} q_{n-1}^{beta2} in [0.2, 10];
+    // reject fac = max(0.2, eta q_n^{-1/k}).  Exponentials in log2 form (q guarded at 1e-10).
+    const float L = __log2f(fmaxf(q2, 1e-20f));  // log2 q^2
+    const float e = accept ? __fmaf_rn(-0.35f / kOrd, L, (0.4f / kOrd) * lq) : (-0.5f / kOrd) * L;
+    float fac = float(kEta) * exp2f(e);
+    fac = fminf(accept ? 10.f : 1.f, fmaxf(0.2f, fac));
+    if (accept) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        u[j] = unew[j];
+        fk[j] = fnew[j];
+      }
+      if (last) t.set(stop);
+      else t.add(hs);
+      lq = fmaxf(0.5f * L, kLog2QoldInit);
+    } else {
+      ++rejected;
+    }
+    h = hs * T(fac);
+    return false;
+  }
+
+  __device__ __forceinline__ void finish(const SolveArgs& a) {
+    if (a.n_save == 0) write_slot<RHS, T>(a, idx, 0, u);
+    for (; si < a.n_save; ++si) write_nan_slot<RHS, T>(a, idx, si);
+    write_stats(a, idx, st, attempts - rejected, rejected, fev0 + kFevPerAttempt * attempts);
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// Fixed-step integrators: Tsit5, RK4 and Euler-Maruyama.
+// n = ceil((tf - t0)/dt - 1e-12) steps; h = dt except the last, h = tf - (t0 + (n-1) dt).
+enum { METH_FIX_TSIT5 = 0, METH_FIX_RK4 = 1, METH_FIX_EM = 2 };
+
+template <class RHS, class T, int METH>
+struct Fixed {
+  static constexpr int D = RHS::D, P = RHS::P;
+  static constexpr int kSub = (METH == METH_FIX_EM) ? Normals<T>::per_call : 1;
+
+  T u[D], fk[D], p[P];
+  T h_reg, h_last, t0f;
+  double t0, tf;
+  long long n, nrun, k, next_ks;
+  int si;
+  long long idx;
+
+  __device__ __forceinline__ long long ks_of(const SolveArgs& a, int s) const {
+    const double sv = a.saveat[s];
+    if (sv < t0 || sv > tf) return -1;
+    long long ks = (sv <= t0) ? 0 : (long long)ceil((sv - t0) / a.dt - 1e-12);
+    return ks < 0 ? 0 : (ks > n ? n : ks);
+  }
+
+  __device__ __forceinline__ void advance_saves(const SolveArgs& a) {
+    // record every save whose step index has been reached; NaN for out-of-range ones
+    while (si < a.n_save) {
+      if (next_ks < 0) {
+        write_nan_slot<RHS, T>(a, idx, si);
+      } else if (next_ks == k) {
+        write_slot<RHS, T>(a, idx, si, u);
+      } else {
+        break;
+      }
+      ++si;
+      if (si < a.n_save) next_ks = ks_of(a, si);
+    }
+  }
+
+  __device__ __forceinline__ void init(long long i, const SolveArgs& a) {
+    idx = i;
+    T t0t, tft;
+    load_problem<RHS, T>(a, i, p, u, t0t, tft);
+    t0f = t0t;
+    t0 = double(t0t);
+    tf = double(tft);
+    n = (tf > t0) ? (long long)ceil((tf - t0) / a.dt - 1e-12) : 0;
+    if (n < 0) n = 0;
+    nrun = n < a.maxiters ? n : a.maxiters;
+    h_reg = T(a.dt);
+    h_last = n > 0 ? T(tf - (t0 + double(n - 1) * a.dt)) : T(0);
+    k = 0;
+    if (METH == METH_FIX_TSIT5) RHS::f(u, p, t0t, fk);
+    si = 0;
+    if (a.n_save > 0) {
+      next_ks = ks_of(a, 0);
+      advance_saves(a);
+    }
+  }
+
+  __device__ __forceinline__ void one_step(const SolveArgs& a, const T* z, int sub) {
+    const T h = (k == n - 1) ? h_last : h_reg;
+    const T tk = T(METH == METH_FIX_EM || !RHS::autonomous ? t0f + T(k) * h_reg : T(0));
+    T unew[D];
+    if (METH == METH_FIX_TSIT5) {
+      T k7[D];
+      tsit5_step<RHS, T, false>(u, p, tk, h, fk, unew, nullptr, k7);
+#pragma unroll
+      for (int j = 0; j < D; ++j) fk[j] = k7[j];
+    } else if (METH == METH_FIX_RK4) {
+      rk4_step<RHS, T>(u, p, tk, h, unew);
+    } else {
+      em_step(u, p, tk, h, z[sub], unew);
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) u[j] = unew[j];
+    ++k;
+    if (a.n_save > 0) advance_saves(a);
+  }
+
+  template <class R = RHS>
+  __device__ __forceinline__ typename std::enable_if<R::has_noise>::type em_step(
+      const T* uu, const T* pp, T tk, T h, T z, T* unew) {
+    T dr[D], df[D];
+    RHS::f(uu, pp, tk, dr);
+    RHS::g(uu, pp, tk, df);
+    const T sq = M<T>::sqrt(h);
+#pragma unroll
+    for (int j = 0; j < D; ++j) unew[j] = M<T>::fma(df[j] * sq, z, M<T>::fma(dr[j], h, uu[j]));
+  }
+  template <class R = RHS>
+  __device__ __forceinline__ typename std::enable_if<!R::has_noise>::type em_step(
+      const T*, const T*, T, T, T, T*) {}
+
+  __device__ __forceinline__ bool advance(const SolveArgs& a) {
+    if (k >= nrun) return true;
+    if (METH == METH_FIX_EM) {
+      T z[Normals<T>::per_call];
+      const uint4 x = Philox::call(a.seed, (unsigned long long)(a.index_offset + idx),
+                                   (unsigned long long)(k / kSub));
+      Normals<T>::draw(x, z);
+#pragma unroll
+      for (int sub = 0; sub < kSub; ++sub)
+        if (k < nrun) one_step(a, z, sub);
+    } else {
+      one_step(a, nullptr, 0);
+    }
+    return k >= nrun;
+  }
+
+  __device__ __forceinline__ void finish(const SolveArgs& a) {
+    signed char st = ENS_TRAJ_OK;
+    bool fin = true;
+#pragma unroll
+    for (int j = 0; j < D; ++j) fin = fin && M<T>::finite(u[j]);
+    if (nrun < n) st = ENS_TRAJ_MAXITERS;
+    else if (!fin) st = ENS_TRAJ_NONFINITE;
+    if (a.n_save == 0) write_slot<RHS, T>(a, idx, 0, u);
+    for (; si < a.n_save; ++si) write_nan_slot<RHS, T>(a, idx, si);
+    const int fev = METH == METH_FIX_TSIT5 ? int(1 + 6 * k) : METH == METH_FIX_RK4 ? int(4 * k)
+                                                                                  : int(k);
+    write_stats(a, idx, st, int(k), 0, fev);
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// schedules
+__device__ __forceinline__ long long queue_next(unsigned long long* q) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  const int rank = __popc(mask & ((1u << lane) - 1u));
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(q, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return (long long)(base + (unsigned long long)rank);
+}
+
+template <class I>
+__global__ void k_direct(const SolveArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
+    I s;
+    s.init(i, a);
+    while (!s.advance(a)) {
+    }
+    s.finish(a);
+  }
+}
+
+template <class I, int TPT>
+__global__ void k_persistent(const SolveArgs a) {
+  I s[TPT];
+  bool act[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const long long i = queue_next(a.queue);
+    act[q] = i < a.N;
+    if (act[q]) s[q].init(i, a);
+  }
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      if (act[q]) {
+        if (s[q].advance(a)) {
+          s[q].finish(a);
+          const long long i = queue_next(a.queue);
+          act[q] = i < a.N;
+          if (act[q]) s[q].init(i, a);
+        }
+      }
+      any = any || act[q];
+    }
+    if (!any) break;
+  }
+}
+
+}  // namespace ens

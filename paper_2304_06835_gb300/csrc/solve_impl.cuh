@@ -1,0 +1,96 @@
+// solve_impl.cuh -- instantiation of the solve kernels for one (model, precision) pair and
+// their launch configuration.  Included by the solve_<precision>_<model>.cu units.
+#pragma once
+
+#include <algorithm>
+
+#include "ens_kernels.cuh"
+
+namespace ens {
+
+template <class I, int TPT>
+cudaError_t persistent_grid(const LaunchCfg& cfg, int* grid) {
+  int bps = 0;
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent<I, TPT>, cfg.block, 0);
+  if (e != cudaSuccess) return e;
+  *grid = std::max(1, bps) * cfg.num_sms;
+  return cudaSuccess;
+}
+
+template <class I, int TPT>
+cudaError_t launch_persistent(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
+  int grid = 0;
+  cudaError_t e = persistent_grid<I, TPT>(cfg, &grid);
+  if (e != cudaSuccess) return e;
+  // never more resident threads than trajectory slots needed
+  const long long need = (a.N + (long long)TPT * cfg.block - 1) / ((long long)TPT * cfg.block);
+  grid = (int)std::min<long long>(grid, std::max<long long>(1, need));
+  k_persistent<I, TPT><<<grid, cfg.block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class I>
+cudaError_t launch_integ(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
+  if (cfg.schedule == ENS_SCHED_DIRECT) {
+    const long long blocks = (a.N + cfg.block - 1) / cfg.block;
+    const int grid = (int)std::min<long long>(blocks, 1LL << 30);
+    k_direct<I><<<grid, cfg.block, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  switch (cfg.tpt) {
+    case 1: return launch_persistent<I, 1>(a, cfg, s);
+    case 2: return launch_persistent<I, 2>(a, cfg, s);
+    case 4: return launch_persistent<I, 4>(a, cfg, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class I>
+cudaError_t attrs_integ(const LaunchCfg& cfg, cudaFuncAttributes* attr, int* bps) {
+  const void* fn = nullptr;
+  if (cfg.schedule == ENS_SCHED_DIRECT) fn = (const void*)k_direct<I>;
+  else if (cfg.tpt == 1) fn = (const void*)k_persistent<I, 1>;
+  else if (cfg.tpt == 2) fn = (const void*)k_persistent<I, 2>;
+  else if (cfg.tpt == 4) fn = (const void*)k_persistent<I, 4>;
+  else return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncGetAttributes(attr, fn);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, cfg.block, 0);
+}
+
+template <class I>
+cudaError_t run_integ(const SolveArgs* a, const LaunchCfg& cfg, cudaStream_t s,
+                      cudaFuncAttributes* attr, int* bps) {
+  return attr ? attrs_integ<I>(cfg, attr, bps) : launch_integ<I>(*a, cfg, s);
+}
+
+// Dispatch on the algorithm for one model: launch (attr == nullptr) or report attributes.
+template <class RHS, class T>
+cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cudaStream_t s,
+                           bool* supported, cudaFuncAttributes* attr, int* bps) {
+  *supported = true;
+  switch (alg) {
+    case ENS_TSIT5_FIXED: return run_integ<Fixed<RHS, T, METH_FIX_TSIT5>>(a, cfg, s, attr, bps);
+    case ENS_TSIT5_ADAPTIVE: return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps);
+    case ENS_RK4: return run_integ<Fixed<RHS, T, METH_FIX_RK4>>(a, cfg, s, attr, bps);
+    case ENS_ROS23: return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps);
+    case ENS_EM:
+      if constexpr (RHS::has_noise) {
+        return run_integ<Fixed<RHS, T, METH_FIX_EM>>(a, cfg, s, attr, bps);
+      }
+      break;
+  }
+  *supported = false;
+  return cudaSuccess;
+}
+
+}  // namespace ens
+
+#define ENS_INSTANTIATE_MODEL(FN, MODEL, T)                                                 \
+  namespace ens {                                                                           \
+  cudaError_t FN(int alg, const SolveArgs* a, const LaunchCfg& cfg, cudaStream_t s,         \
+                 bool* supported, cudaFuncAttributes* attr, int* bps) {                     \
+    return dispatch_model<MODEL<T>, T>(alg, a, cfg, s, supported, attr, bps);               \
+  }                                                                                         \
+  }

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, trajectory by
+trajectory, on the same seeded inputs.
+
+Tolerances (state-vector relative error e = max_j |u_j - ref_j| / max(max_j |ref_j|, 1)):
+  fixed-step FP64 e <= 1e-12; FP32 e <= 1e-5 (against the FP64 oracle on the float inputs);
+  adaptive: |u - u_ref| <= 10 (abstol + reltol |u_ref|) per component against a tol-1e-12 FP64
+  oracle reference, plus algorithmic parity against the oracle at the same tolerance;
+  Philox words bit-exact; normals within a few ulp.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, dt=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dt, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().double().numpy()
+
+
+def normwise(out, ref):
+    out = out.reshape(out.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    return np.abs(out - ref).max(axis=1) / np.maximum(np.abs(ref).max(axis=1), 1.0)
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2304_06835_gb300 import EnsembleSolver
+    return {k: EnsembleSolver(k) for k in ("lorenz", "robertson", "gbm")}
+
+
+# ----------------------------------------------------------------------------- fixed step
+@pytest.mark.parametrize("alg", ["tsit5_fixed", "rk4"])
+def test_fixed_lorenz_sweep_fp64(S, alg):
+    P, U, T = workloads.lorenz_sweep(1024)
+    ref, _, rst = oracle.solve("lorenz", alg, P, U, T, dt=1e-3)
+    out, st, stats = S["lorenz"].solve(dev(P), dev(U), dev(T), alg=alg, dt=1e-3, want_stats=True)
+    assert normwise(host(out), ref).max() <= 1e-12
+    assert int(st.abs().sum()) == 0
+    np.testing.assert_array_equal(stats.cpu().numpy().T, rst.astype(np.int32))
+
+
+@pytest.mark.parametrize("alg", ["tsit5_fixed", "rk4"])
+def test_fixed_lorenz_sweep_fp32(S, alg):
+    P, U, T = workloads.lorenz_sweep(1024)
+    P, U, T = f32(P), f32(U), f32(T)
+    ref, _, _ = oracle.solve("lorenz", alg, P, U, T, dt=1e-3)
+    out, _, _ = S["lorenz"].solve(dev(P, torch.float32), dev(U, torch.float32),
+                                  dev(T, torch.float32), alg=alg, dt=1e-3)
+    assert normwise(host(out), ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("N", [1, 31, 33, 1000, 4097])
+def test_ragged_sizes_and_layouts_and_schedules(S, N):
+    P, U, T = workloads.lorenz_random(N, seed=N, t1=0.5)
+    ref, _, _ = oracle.solve("lorenz", "tsit5_fixed", P, U, T, dt=1e-3)
+    s = S["lorenz"]
+    outs = []
+    for layout in ("rowmajor", "soa"):
+        for sched, tpt in (("direct", 0), ("persistent", 1), ("persistent", 2), ("persistent", 4)):
+            if layout == "soa":
+                o, _, _ = s.solve(dev(P.T.copy()), dev(U.T.copy()), dev(T.T.copy()),
+                                  alg="tsit5_fixed", dt=1e-3, layout="soa", schedule=sched, tpt=tpt)
+                o = host(o).T
+            else:
+                o, _, _ = s.solve(dev(P), dev(U), dev(T), alg="tsit5_fixed", dt=1e-3,
+                                  schedule=sched, tpt=tpt)
+                o = host(o)
+            outs.append(o)
+    for o in outs:
+        np.testing.assert_array_equal(o, outs[0])  # schedule/layout change no arithmetic
+    assert normwise(outs[0], ref).max() <= 1e-12
+
+
+def test_empty_ensemble(S):
+    z = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    out, st, _ = S["lorenz"].solve(z, z, torch.empty((0, 2), dtype=torch.float64, device="cuda"),
+                                   alg="tsit5_fixed", dt=1e-3)
+    assert out.shape == (0, 3)
+
+
+def test_fixed_saveat(S):
+    P, U, T = workloads.lorenz_sweep(64)
+    sv = [-1.0, 0.0, 0.25, 0.5, 0.7505, 1.0, 2.0]
+    ref, _, _ = oracle.solve("lorenz", "tsit5_fixed", P, U, T, dt=1e-3, saveat=sv)
+    out, _, _ = S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5_fixed", dt=1e-3, saveat=sv)
+    o = host(out)
+    assert np.array_equal(np.isnan(o), np.isnan(ref))
+    ok = ~np.isnan(ref[:, :, 0])
+    assert normwise(o[ok], ref[ok]).max() <= 1e-12
+
+
+# ----------------------------------------------------------------------------- adaptive
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-8), (torch.float32, 1e-5)])
+def test_adaptive_tsit5_within_10x_tol_of_reference(S, dtype, tol):
+    P, U, T = workloads.lorenz_random(2048, seed=21, t1=1.0)
+    if dtype == torch.float32:
+        P = f32(P)
+    ref, _, _ = oracle.solve("lorenz", "tsit5", P, U, T, abstol=1e-12, reltol=1e-12)
+    out, st, _ = S["lorenz"].solve(dev(P, dtype), dev(U, dtype), dev(T, dtype), alg="tsit5",
+                                   abstol=tol, reltol=tol)
+    o = host(out)
+    assert int(st.abs().sum()) == 0
+    assert np.all(np.abs(o - ref) <= 10 * (tol + tol * np.abs(ref)))
+
+
+def test_adaptive_tsit5_nonchaotic_t10(S):
+    P, U, T = workloads.lorenz_random(4096, seed=22, t1=10.0)
+    keep = P[:, 1] < 10.0
+    P, U, T = P[keep], U[keep], T[keep]
+    ref, _, _ = oracle.solve("lorenz", "tsit5", P, U, T, abstol=1e-12, reltol=1e-12)
+    out, _, _ = S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5", abstol=1e-8, reltol=1e-8)
+    o = host(out)
+    assert np.all(np.abs(o - ref) <= 10 * (1e-8 + 1e-8 * np.abs(ref)))
+
+
+def test_adaptive_tsit5_algorithmic_parity_fp64(S):
+    """Same tolerance on both sides over [0,10] (chaotic for large rho): trajectories whose
+    accept/reject counts agree must agree to 1e-9; counts must agree on >= 99%."""
+    P, U, T = workloads.lorenz_random(2048, seed=23, t1=10.0)
+    ref, _, rst = oracle.solve("lorenz", "tsit5", P, U, T, abstol=1e-8, reltol=1e-8)
+    out, st, stats = S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5", abstol=1e-8,
+                                       reltol=1e-8, want_stats=True)
+    o = host(out)
+    gs = stats.cpu().numpy().T
+    same = np.all(gs[:, :2] == rst[:, :2], axis=1)
+    assert same.mean() >= 0.99, same.mean()
+    assert normwise(o[same], ref[same]).max() <= 1e-9
+    assert np.all(gs[same, 2] == rst[same, 2])
+
+
+def test_adaptive_tsit5_saveat(S):
+    P, U, T = workloads.lorenz_random(256, seed=24, t1=1.0)
+    sv = [0.0, 0.1, 0.33, 0.5, 1.0, 1.5]
+    ref, _, _ = oracle.solve("lorenz", "tsit5", P, U, T, abstol=1e-12, reltol=1e-12, saveat=sv)
+    out, _, _ = S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5", abstol=1e-8, reltol=1e-8,
+                                  saveat=sv)
+    o = host(out)
+    assert np.array_equal(np.isnan(o), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert np.all(np.abs(o[ok] - ref[ok]) <= 10 * (1e-8 + 1e-8 * np.abs(ref[ok])))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_rosenbrock23_robertson(S, dtype):
+    P, U, T = workloads.robertson_random(512, seed=31)
+    if dtype == torch.float32:
+        P = f32(P)
+        tol = dict(abstol=1e-8, reltol=1e-4)
+    else:
+        tol = dict(abstol=1e-6, reltol=1e-6)
+    sv = np.logspace(-4, 5, 10)
+    prec = "f64" if dtype == torch.float64 else "f32"
+    ref, rstat_, rst = oracle.solve("robertson", "ros23", P, U, T, dt0=1e-4, saveat=sv,
+                                    precision=prec, **tol)
+    out, st, stats = S["robertson"].solve(dev(P, dtype), dev(U, dtype), dev(T, dtype), alg="ros23",
+                                          dt0=1e-4, saveat=sv, want_stats=True, **tol)
+    o = host(out)
+    assert int(st.abs().sum()) == 0
+    gs = stats.cpu().numpy().T
+    same = np.all(gs[:, :2] == rst[:, :2], axis=1)
+    assert same.mean() >= 0.95
+    # algorithmic parity on identical step sequences
+    lim = 1e-9 if dtype == torch.float64 else 2e-3
+    e = np.abs(o - ref) / np.maximum(np.abs(ref), 1e-3)
+    assert e[same].max() <= lim, e[same].max()
+    # accuracy against the oracle at 1e-12 (itself pinned to scipy Radau)
+    if dtype == torch.float64:
+        fine, _, _ = oracle.solve("robertson", "ros23", P[:64], U[:64], T[:64], abstol=1e-12,
+                                  reltol=1e-12, dt0=1e-8, saveat=sv)
+        assert np.all(np.abs(o[:64] - fine) <= 10 * (1e-6 + 1e-6 * np.abs(fine)))
+        mass = o.sum(axis=2)
+        assert np.abs(mass - 1).max() < 1e-10
+
+
+# ----------------------------------------------------------------------------- SDE
+def test_philox_words_bit_exact():
+    from paper_2304_06835_gb300 import philox_words
+    seed = 0xDEADBEEF12345
+    w = philox_words(seed, 37, 5, index_offset=1000).cpu().numpy().astype(np.uint32)
+    for j in (0, 1, 36):
+        for c in (0, 4):
+            tr = 1000 + j
+            ref = oracle.philox4x32_10([c, 0, tr, 0], [seed & 0xFFFFFFFF, seed >> 32])
+            np.testing.assert_array_equal(w[c, :, j], ref)
+    # known-answer vector: counter 0, key 0
+    w0 = philox_words(0, 1, 1).cpu().numpy().astype(np.uint32)[0, :, 0]
+    assert [int(x) for x in w0] == [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_normals_match_oracle(dtype):
+    from paper_2304_06835_gb300 import normals
+    z = normals(77, 16, 33, dtype=dtype, index_offset=5).cpu().double().numpy()
+    for j in range(16):
+        ref = oracle.normals(77, 5 + j, 33, fp64=dtype == torch.float64)
+        tol = 1e-14 if dtype == torch.float64 else 2e-6
+        np.testing.assert_allclose(z[:, j], ref, rtol=tol, atol=tol)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_em_gbm_matches_oracle(S, dtype):
+    P, U, T = workloads.gbm_random(4096, seed=41)
+    if dtype == torch.float32:
+        P = f32(P)
+    ref, _, _ = oracle.solve("gbm", "em", P, U, T, dt=1e-3, seed=123, index_offset=7,
+                             precision="f64")
+    out, st, stats = S["gbm"].solve(dev(P, dtype), dev(U, dtype), dev(T, dtype), alg="em",
+                                    dt=1e-3, seed=123, index_offset=7, want_stats=True)
+    o = host(out)
+    lim = 1e-12 if dtype == torch.float64 else 1e-5
+    assert normwise(o, ref).max() <= lim
+    assert np.all(stats.cpu().numpy()[0] == 1000)
+
+
+# ----------------------------------------------------------------------------- status, host API
+def test_status_codes(S):
+    P, U, T = workloads.lorenz_random(64, seed=51, t1=10.0)
+    P[3, 0] = np.nan
+    out, st, stats = S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5", abstol=1e-8,
+                                       reltol=1e-8, want_stats=True)
+    ref, rst, rstats = oracle.solve("lorenz", "tsit5", P, U, T, abstol=1e-8, reltol=1e-8)
+    s = st.cpu().numpy()
+    assert s[3] == 3 and np.all(np.delete(s, 3) == 0)
+    out, st, stats = S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5", abstol=1e-8,
+                                       reltol=1e-8, maxiters=10, want_stats=True)
+    s = st.cpu().numpy()
+    assert np.all(np.delete(s, 3) == 1)
+    g = stats.cpu().numpy()
+    assert np.all(np.delete(g[0] + g[1], 3) == 10)
+    # t0 == tf: no steps, u0 back
+    Tz = np.zeros_like(T)
+    out, st, stats = S["lorenz"].solve(dev(P), dev(U), dev(Tz), alg="tsit5", want_stats=True)
+    np.testing.assert_array_equal(host(out)[:3], U[:3])
+
+
+def test_invalid_arguments_raise(S):
+    from paper_2304_06835_gb300 import EnsError
+    P, U, T = workloads.lorenz_sweep(8)
+    with pytest.raises(EnsError):
+        S["lorenz"].solve(dev(P), dev(U), dev(T), alg="em", dt=1e-3)  # no noise in Lorenz
+    with pytest.raises(EnsError):
+        S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5_fixed", dt=0.0)
+    with pytest.raises(EnsError):
+        S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5", saveat=[0.5, 0.2])
+
+
+def test_solve_host_matches_device(S):
+    P, U, T = workloads.lorenz_random(3000, seed=61, t1=1.0)
+    a, st_a, sa = S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5", abstol=1e-8,
+                                    reltol=1e-8, want_stats=True)
+    b, st_b, sb = S["lorenz"].solve_host(P, U, T, alg="tsit5", abstol=1e-8, reltol=1e-8,
+                                         want_stats=True)
+    np.testing.assert_array_equal(host(a), b)
+    np.testing.assert_array_equal(sa.cpu().numpy(), sb)

@@ -59,8 +59,8 @@ def test_uniform_mapping_is_box_muller_of_philox_words():
     Philox call; check the Box-Muller identity z0^2 + z1^2 = -2 ln u0 on those words."""
     seed, tr = 0x1234_5678_9ABC, 5
     x = oracle.philox4x32_10([0, 0, tr, 0], [seed & 0xFFFFFFFF, seed >> 32])
-    u0 = ((int(x[0]) >> 8) + 0.5) * 2.0**-24
+    u0 = ((int(x[0]) >> 9) + 0.5) * 2.0**-23
     z = oracle.normals(seed, tr, 4)
     assert abs(z[0] ** 2 + z[1] ** 2 - (-2 * np.log(u0))) < 1e-12
-    u2 = ((int(x[2]) >> 8) + 0.5) * 2.0**-24
+    u2 = ((int(x[2]) >> 9) + 0.5) * 2.0**-23
     assert abs(z[2] ** 2 + z[3] ** 2 - (-2 * np.log(u2))) < 1e-12
