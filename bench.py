@@ -170,6 +170,44 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line))
 
 
+def e2e_rate(args, w, P, U, T, solver, stream, kw):
+    """Trajectories/s through ens_solve_host: pinned host inputs copied to the device, the
+    solve, and the outputs (final state + status) copied back, all inside the timed region."""
+    import ctypes
+
+    import torch
+
+    import paper_2304_06835_gb300 as ens
+    from paper_2304_06835_gb300 import _lib
+    N = w["N"]
+    npdt = np.float32 if w["dtype"] == "f32" else np.float64
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=npdt)).pin_memory()
+    Pp, Up, Tp = pin(P.T), pin(U.T), pin(T.T)
+    D = U.shape[1]
+    outp = torch.empty((D, N), dtype=Pp.dtype).pin_memory()
+    stp = torch.empty(N, dtype=torch.int8).pin_memory()
+    o, keep = ens.make_opts(w["alg"], _lib.F32 if w["dtype"] == "f32" else _lib.F64, "soa",
+                            schedule=args.schedule, block=args.block, tpt=args.tpt,
+                            refill_min=args.refill, **kw)
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def host_step():
+        _lib.check(_lib.lib().ens_solve_host(solver.handle, N, Pp.data_ptr(), Up.data_ptr(),
+                                             Tp.data_ptr(), ctypes.byref(o), outp.data_ptr(),
+                                             stp.data_ptr(), None, sptr))
+    host_step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        host_step()
+    el = (time.perf_counter() - t0) / steps
+    es = np.dtype(npdt).itemsize
+    return {"value": N / el, "unit": "trajectories/s",
+            "h2d_bytes_per_step": int(N * es * (P.shape[1] + D + 2)),
+            "d2h_bytes_per_step": int(N * es * D + N)}
+
+
 # ------------------------------------------------------------------------------- GPU leg
 def main():
     ap = argparse.ArgumentParser()
@@ -180,11 +218,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--tpt", type=int, default=0)
+    ap.add_argument("--refill", type=int, default=0, help="persistent refill batch (0 = default)")
     ap.add_argument("--schedule", default="auto")
+    ap.add_argument("--n", type=int, default=0, help="override N (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--probe", action="store_true", help="also measure FP32/FP64 FMA rates")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.n:
+        w["N"] = args.n
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -219,7 +262,8 @@ def main():
 
     def step():
         solver.solve(Pd, Ud, Td, alg=w["alg"], layout="soa", out=out, status=status, stats=stats,
-                     schedule=args.schedule, block=args.block, tpt=args.tpt, want_stats=True, **kw)
+                     schedule=args.schedule, block=args.block, tpt=args.tpt,
+                     refill_min=args.refill, want_stats=True, **kw)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -261,33 +305,9 @@ def main():
     bound = "alu"
 
     # e2e: the same solve through the C ABI with host buffers (copies inside the timed region)
-    Ph = np.ascontiguousarray(P.T, dtype=np.float32 if w["dtype"] == "f32" else np.float64)
-    Uh = np.ascontiguousarray(U.T, dtype=Ph.dtype)
-    Th = np.ascontiguousarray(T.T, dtype=Ph.dtype)
-    import ctypes
-    pin = lambda a: torch.from_numpy(a).pin_memory()
-    Pp, Up, Tp = pin(Ph), pin(Uh), pin(Th)
-    outp = torch.empty((D, N), dtype=dt_t).pin_memory()
-    stp = torch.empty(N, dtype=torch.int8).pin_memory()
-    o, keep = ens.make_opts(w["alg"], _lib.F32 if w["dtype"] == "f32" else _lib.F64, "soa",
-                            schedule=args.schedule, block=args.block, tpt=args.tpt, **kw)
-    e2e_steps = max(1, min(args.steps, 5))
-    sptr = ctypes.c_void_p(stream.cuda_stream)
-
-    def host_step():
-        _lib.check(_lib.lib().ens_solve_host(solver.handle, N, Pp.data_ptr(), Up.data_ptr(),
-                                             Tp.data_ptr(), ctypes.byref(o), outp.data_ptr(),
-                                             stp.data_ptr(), None, sptr))
-    host_step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        host_step()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    es = Ph.itemsize
-    h2d = N * es * (Pd.shape[0] + Ud.shape[0] + 2)
-    d2h = N * es * D + N
-
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_rate(args, w, P, U, T, solver, stream, kw)
     line = {
         "metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * launch_s,
@@ -297,7 +317,7 @@ def main():
                    "tspan": [0.0, w["t1"]], **{k: w[k] for k in ("tol", "dt", "dt0") if k in w},
                    "layout": "soa", "l2": "flushed between steps (256 MB write outside events)",
                    "parallelism": "dp%d" % world, "block": args.block, "tpt": args.tpt,
-                   "schedule": args.schedule},
+                   "schedule": args.schedule, "refill_min": args.refill},
         "wall_s": wall,
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak_max,
                      "unit": "T FP32-FMA-pipe instr/s", "frac": achieved / peak_max,
@@ -308,8 +328,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": args.steps,
         "trajectories_ok": ok,
-        "e2e": {"value": N / e2e_s, "unit": "trajectories/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "e2e": e2e,
     }
     if args.probe:
         import ctypes as C

@@ -91,6 +91,9 @@ typedef struct {
   int schedule;           /* ENS_SCHED_* */
   int block;              /* threads per block; 0 = tuned / default */
   int tpt;                /* trajectories per thread (1, 2 or 4); 0 = tuned / default */
+  int refill_min;         /* persistent schedule: a warp refills its idle lanes once at least
+                             this many are idle (1..32; 0 = default).  Batching refills trades
+                             idle lanes for fewer divergent refill passes. */
 } ens_opts;
 
 /* Fill *o with defaults: TSIT5_ADAPTIVE, F32, SOA, abstol=reltol=1e-6, maxiters=1e6, auto. */

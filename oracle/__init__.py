@@ -96,7 +96,8 @@ def solve(rhs, alg, params, u0, tspan, *, dt=0.0, abstol=1e-6, reltol=1e-3, dt0=
     """Solve an ensemble.  params [N,P], u0 [N,D], tspan [N,2] (row-major, float64).
 
     precision "f32" runs the same algorithms in float arithmetic on the given (already
-    float-representable) inputs.  Returns (out [N,S,D] or [N,D], status [N], stats [N,3]).
+    float-representable) inputs; "f64_f32stream" is FP64 arithmetic driven by the FP32 normal
+    stream (4 normals per Philox call).  Returns (out [N,S,D] or [N,D], status [N], stats [N,3]).
     """
     rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
     alg_id = ALG[alg] if isinstance(alg, str) else int(alg)
@@ -112,7 +113,7 @@ def solve(rhs, alg, params, u0, tspan, *, dt=0.0, abstol=1e-6, reltol=1e-3, dt0=
     stats = np.empty((N, 3), np.int64)
     nt = default_threads() if nthreads is None else int(nthreads)
     rc = lib().oracle_solve(
-        rhs_id, alg_id, 0 if precision == "f64" else 1, 0, N, _dp(params), _dp(u0), _dp(tspan),
+        rhs_id, alg_id, {"f64": 0, "f32": 1, "f64_f32stream": 2}[precision], 0, N, _dp(params), _dp(u0), _dp(tspan),
         float(dt), float(abstol), float(reltol), float(dt0), int(maxiters),
         _dp(sv) if sv is not None and sv.size else None, 0 if sv is None else int(sv.size),
         int(seed), int(index_offset), _dp(out),

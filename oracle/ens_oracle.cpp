@@ -377,6 +377,7 @@ struct Opts {
   int n_save;
   unsigned long long seed;
   long long index_offset;
+  bool stream_fp64;  // normals from the FP64 stream (2 per Philox call) or the FP32 one (4)
 };
 
 // Hairer-Norsett-Wanner I, II.4: starting step size for an order-p method.
@@ -472,8 +473,7 @@ void solve_fixed(Traj<T>& tr, uint64_t traj_index) {
       f_gbm<T>(tr.u, tr.p, tk, a);
       g_gbm<T>(tr.u, tr.p, tk, b);
       tr.fevals += 1;
-      const bool fp64 = sizeof(T) == 8;
-      T z = T(normal_draw(o.seed, traj_index, uint64_t(k), fp64));
+      T z = T(normal_draw(o.seed, traj_index, uint64_t(k), o.stream_fp64));
       T sq = std::sqrt(h);
       for (int j = 0; j < D; ++j) unew[j] = tr.u[j] + a[j] * h + b[j] * sq * z;
     }
@@ -646,7 +646,8 @@ extern "C" {
 // Solve N trajectories.  All arrays are host double arrays; `layout` 0 = row-major
 // (params[N][P], u0[N][D], tspan[N][2], out[N][S][D]), 1 = structure of arrays
 // (params[P][N], u0[D][N], tspan[2][N], out[S][D][N]).  `precision` 0 = FP64, 1 = FP32 mode
-// (inputs rounded to float first by the caller; arithmetic in float, time compensated).
+// (inputs rounded to float first by the caller; arithmetic in float, time compensated),
+// 2 = FP64 arithmetic driven by the FP32 normal stream (the reference for FP32 SDE paths).
 // stats[N][3] = accepted, rejected, f-evaluations.  Returns 0, or -1 on bad arguments.
 int oracle_solve(int rhs_id, int alg, int precision, int layout, long long N,
                  const double* params, const double* u0, const double* tspan, double dt,
@@ -657,10 +658,11 @@ int oracle_solve(int rhs_id, int alg, int precision, int layout, long long N,
   Model m = model_of(rhs_id);
   if (m.D == 0 || N < 0 || alg < 1 || alg > 5) return -1;
   if (alg == ALG_EM && rhs_id != RHS_GBM) return -1;
+  if (precision < 0 || precision > 2) return -1;
   Opts o{rhs_id, alg, m.D, m.P, dt, abstol, reltol, dt0, maxiters, saveat, n_save, seed,
-         index_offset};
+         index_offset, precision == 0};
   parallel_for(N, nthreads, [&](long long a, long long b) {
-    if (precision == 0)
+    if (precision != 1)
       solve_range<double>(o, layout, N, a, b, params, u0, tspan, out, status, stats);
     else
       solve_range<float>(o, layout, N, a, b, params, u0, tspan, out, status, stats);

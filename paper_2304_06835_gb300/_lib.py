@@ -31,6 +31,7 @@ class EnsOpts(ctypes.Structure):
         ("saveat", ctypes.POINTER(ctypes.c_double)), ("n_save", ctypes.c_int),
         ("seed", ctypes.c_ulonglong), ("index_offset", ctypes.c_longlong),
         ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
+        ("refill_min", ctypes.c_int),
     ]
 
 

@@ -226,6 +226,8 @@ int validate(const ens_handle* h, long long N, const void* params, const void* u
     return fail(ENS_EINVAL, "block must be 0 or a multiple of 32 in [32, 1024]");
   if (o->tpt != 0 && o->tpt != 1 && o->tpt != 2 && o->tpt != 4)
     return fail(ENS_EINVAL, "tpt must be 0, 1, 2 or 4");
+  if (o->refill_min < 0 || o->refill_min > 32)
+    return fail(ENS_EINVAL, "refill_min must be in [0, 32]");
   if (N > 0 && (!params || !u0 || !tspan || !out)) return fail(ENS_EINVAL, "null array");
   return ENS_OK;
 }
@@ -248,6 +250,8 @@ void fill_args(SolveArgs* a, long long N, const void* params, const void* u0, co
   a->reltol = o->reltol;
   a->dt0 = o->dt0;
   a->maxiters = o->maxiters;
+  a->maxiters_i = (int)o->maxiters;
+  a->refill_min = o->refill_min > 0 ? (o->refill_min > 32 ? 32 : o->refill_min) : 4;
   a->seed = o->seed;
   a->index_offset = o->index_offset;
   a->queue = queue;

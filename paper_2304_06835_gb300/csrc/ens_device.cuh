@@ -15,6 +15,17 @@ namespace ens {
 
 // ------------------------------------------------------------------------------------------
 // precision helpers
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <class T>
 struct M;
 
@@ -28,6 +39,12 @@ struct M<float> {
   static __device__ __forceinline__ float min(float a, float b) { return fminf(a, b); }
   static __device__ __forceinline__ float sqrt(float a) { return sqrtf(a); }
   static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+  static __device__ __forceinline__ float pow(float a, float b) { return powf(a, b); }
+  // approximate forms for heuristics (controller, starting step): MUFU ex2 / lg2
+  static __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float fast_pow(float a, float b) {
+    return ex2_approx(b * lg2_approx(a));
+  }
   static __device__ __forceinline__ bool finite(float a) { return isfinite(a); }
   static constexpr double dtmin_factor = 1e-9;
 };
@@ -42,6 +59,9 @@ struct M<double> {
   static __device__ __forceinline__ double min(double a, double b) { return fmin(a, b); }
   static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
   static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+  static __device__ __forceinline__ double pow(double a, double b) { return ::pow(a, b); }
+  static __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double fast_pow(double a, double b) { return ::pow(a, b); }
   static __device__ __forceinline__ bool finite(double a) { return isfinite(a); }
   static constexpr double dtmin_factor = 1e-14;
 };

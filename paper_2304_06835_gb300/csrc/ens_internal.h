@@ -20,6 +20,8 @@ struct SolveArgs {
   int n_save;
   double dt, abstol, reltol, dt0;
   long long maxiters;
+  int maxiters_i;   // the same cap as an int (validated <= 2e9)
+  int refill_min;   // persistent schedule: refill a warp's idle lanes once this many are idle
   unsigned long long seed;
   long long index_offset;
   unsigned long long* queue;  // persistent-schedule counter (device), zeroed before launch

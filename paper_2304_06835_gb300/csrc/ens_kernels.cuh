@@ -130,10 +130,18 @@ struct Adaptive {
   T u[D], fk[D], p[P];
   Clock<T> t;
   T tf, h;
-  float lq;  // log2 q_{n-1}
+  T stop, stop_thr;   // next stop (a save time before tf, or tf) and its arrival threshold
+  float lq;           // log2 q_{n-1}
   int attempts, rejected, si, fev0;
   signed char st;
+  bool stop_is_save;
   long long idx;
+
+  __device__ __forceinline__ void set_stop(const SolveArgs& a) {
+    stop_is_save = si < a.n_save && T(a.saveat[si]) < tf;
+    stop = stop_is_save ? T(a.saveat[si]) : tf;
+    stop_thr = T(kStopEps) * M<T>::max(T(1), M<T>::abs(stop));
+  }
 
   __device__ __forceinline__ void init(long long i, const SolveArgs& a) {
     idx = i;
@@ -157,47 +165,57 @@ struct Adaptive {
       write_nan_slot<RHS, T>(a, idx, si);
       ++si;
     }
+    set_stop(a);
   }
 
-  // Hairer-Norsett-Wanner I, II.4: starting step size
+  // Hairer-Norsett-Wanner I, II.4: starting step size (a heuristic: the FP32 solve forms it
+  // with fast division and MUFU-based pow)
   __device__ __forceinline__ T initial_step(const SolveArgs& a, T t0) {
-    T sc[D], tmp[D], u1[D], f1[D];
+    T sc[D], u1[D], f1[D];
     const T atol = T(a.abstol), rtol = T(a.reltol);
-    for (int j = 0; j < D; ++j) sc[j] = atol + rtol * M<T>::abs(u[j]);
-    const T d0 = rms_scaled(u, sc, D);
-    const T d1 = rms_scaled(fk, sc, D);
-    const T h0 = (d0 < T(1e-5) || d1 < T(1e-5)) ? T(1e-6) : T(0.01) * d0 / d1;
-    for (int j = 0; j < D; ++j) u1[j] = u[j] + h0 * fk[j];
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      sc[j] = M<T>::fast_div(T(1), M<T>::fma(rtol, M<T>::abs(u[j]), atol));
+      s0 = M<T>::fma(u[j] * sc[j], u[j] * sc[j], s0);
+      s1 = M<T>::fma(fk[j] * sc[j], fk[j] * sc[j], s1);
+    }
+    const T d0 = M<T>::sqrt(s0 * T(1.0 / D)), d1 = M<T>::sqrt(s1 * T(1.0 / D));
+    const T h0 = (d0 < T(1e-5) || d1 < T(1e-5)) ? T(1e-6) : T(0.01) * M<T>::fast_div(d0, d1);
+#pragma unroll
+    for (int j = 0; j < D; ++j) u1[j] = M<T>::fma(h0, fk[j], u[j]);
     RHS::f(u1, p, t0 + h0, f1);
-    for (int j = 0; j < D; ++j) tmp[j] = f1[j] - fk[j];
-    const T d2 = rms_scaled(tmp, sc, D) / h0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const T v = (f1[j] - fk[j]) * sc[j];
+      s2 = M<T>::fma(v, v, s2);
+    }
+    const T d2 = M<T>::fast_div(M<T>::sqrt(s2 * T(1.0 / D)), h0);
     const T dm = M<T>::max(d1, d2);
     const T h1 = (dm <= T(1e-15)) ? M<T>::max(T(1e-6), h0 * T(1e-3))
-                                  : T(pow(double(T(0.01) / dm), 1.0 / (kInitOrder + 1)));
+                                  : M<T>::fast_pow(M<T>::fast_div(T(0.01), dm),
+                                                   T(1.0 / (kInitOrder + 1)));
     return M<T>::min(T(100) * h0, h1);
   }
 
   // one attempt; returns true when the trajectory is finished
   __device__ __forceinline__ bool advance(const SolveArgs& a) {
-    T stop, rem;
-    for (;;) {
-      const bool stop_is_save = si < a.n_save && T(a.saveat[si]) < tf;
-      stop = stop_is_save ? T(a.saveat[si]) : tf;
-      rem = t.remaining(stop);
-      if (rem > T(kStopEps) * M<T>::max(T(1), M<T>::abs(stop))) break;
+    T rem = t.remaining(stop);
+    while (rem <= stop_thr) {  // arrived at the stop
       t.set(stop);
-      if (stop_is_save) {
-        write_slot<RHS, T>(a, idx, si, u);
-        ++si;
-        continue;
+      if (!stop_is_save) {
+        while (si < a.n_save && T(a.saveat[si]) == tf) {
+          write_slot<RHS, T>(a, idx, si, u);
+          ++si;
+        }
+        return true;
       }
-      while (si < a.n_save && T(a.saveat[si]) == tf) {
-        write_slot<RHS, T>(a, idx, si, u);
-        ++si;
-      }
-      return true;
+      write_slot<RHS, T>(a, idx, si, u);
+      ++si;
+      set_stop(a);
+      rem = t.remaining(stop);
     }
-    if (attempts >= a.maxiters) {
+    if (attempts >= a.maxiters_i) {
       st = ENS_TRAJ_MAXITERS;
       return true;
     }
@@ -232,9 +250,9 @@ struct Adaptive {
     const bool accept = q2 <= 1.f;
     // PI control: accept fac = eta q_n^{-beta1} q_{n-1}^{beta2} in [0.2, 10];
     // reject fac = max(0.2, eta q_n^{-1/k}).  Exponentials in log2 form (q guarded at 1e-10).
-    const float L = __log2f(fmaxf(q2, 1e-20f));  // log2 q^2
+    const float L = lg2_approx(fmaxf(q2, 1e-20f));  // log2 q^2
     const float e = accept ? __fmaf_rn(-0.35f / kOrd, L, (0.4f / kOrd) * lq) : (-0.5f / kOrd) * L;
-    float fac = float(kEta) * exp2f(e);
+    float fac = float(kEta) * ex2_approx(e);
     fac = fminf(accept ? 10.f : 1.f, fmaxf(0.2f, fac));
     if (accept) {
 #pragma unroll
@@ -346,8 +364,9 @@ struct Fixed {
     RHS::f(uu, pp, tk, dr);
     RHS::g(uu, pp, tk, df);
     const T sq = M<T>::sqrt(h);
+    // increment first (a h + b sqrt(h) Z), then one rounding at the scale of X
 #pragma unroll
-    for (int j = 0; j < D; ++j) unew[j] = M<T>::fma(df[j] * sq, z, M<T>::fma(dr[j], h, uu[j]));
+    for (int j = 0; j < D; ++j) unew[j] = uu[j] + M<T>::fma(dr[j], h, (df[j] * sq) * z);
   }
   template <class R = RHS>
   __device__ __forceinline__ typename std::enable_if<!R::has_noise>::type em_step(
@@ -409,31 +428,51 @@ __global__ void k_direct(const SolveArgs a) {
   }
 }
 
+// Persistent schedule.  Every lane of a warp stays in the loop until the whole warp is done,
+// so warp-wide votes are safe.  A lane that finishes its trajectory writes it out and idles;
+// once at least a.refill_min lanes of the warp are idle (or all are), the idle lanes fetch
+// the next indices together (one warp-aggregated atomic) and initialise in one divergent
+// pass instead of one pass per finishing lane.
 template <class I, int TPT>
 __global__ void k_persistent(const SolveArgs a) {
   I s[TPT];
   bool act[TPT];
+  bool drained = false;  // warp-uniform: a fetch has come back past the end of the queue
 #pragma unroll
   for (int q = 0; q < TPT; ++q) {
     const long long i = queue_next(a.queue);
     act[q] = i < a.N;
     if (act[q]) s[q].init(i, a);
   }
+  drained = __any_sync(0xffffffffu, !act[TPT - 1]);
   for (;;) {
-    bool any = false;
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
-      if (act[q]) {
-        if (s[q].advance(a)) {
-          s[q].finish(a);
-          const long long i = queue_next(a.queue);
-          act[q] = i < a.N;
-          if (act[q]) s[q].init(i, a);
+      if (act[q] && s[q].advance(a)) {
+        s[q].finish(a);
+        act[q] = false;
+      }
+    }
+    if (!drained) {
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) {
+        const unsigned idle = __ballot_sync(0xffffffffu, !act[q]);
+        if (__popc(idle) >= a.refill_min) {
+          bool got = true;
+          if (!act[q]) {
+            const long long i = queue_next(a.queue);
+            act[q] = i < a.N;
+            got = act[q];
+            if (act[q]) s[q].init(i, a);
+          }
+          drained = drained || __any_sync(0xffffffffu, !got);
         }
       }
-      any = any || act[q];
     }
-    if (!any) break;
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) any = any || act[q];
+    if (!__any_sync(0xffffffffu, any)) break;
   }
 }
 
