@@ -188,7 +188,7 @@ def e2e_rate(args, w, P, U, T, solver, stream, kw):
     stp = torch.empty(N, dtype=torch.int8).pin_memory()
     o, keep = ens.make_opts(w["alg"], _lib.F32 if w["dtype"] == "f32" else _lib.F64, "soa",
                             schedule=args.schedule, block=args.block, tpt=args.tpt,
-                            refill_min=args.refill, **kw)
+                            refill_min=args.refill, order=args.order, **kw)
     sptr = ctypes.c_void_p(stream.cuda_stream)
 
     def host_step():
@@ -219,6 +219,7 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--tpt", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0, help="persistent refill batch (0 = default)")
+    ap.add_argument("--order", default="auto", choices=["auto", "index", "cost"])
     ap.add_argument("--schedule", default="auto")
     ap.add_argument("--n", type=int, default=0, help="override N (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -263,7 +264,7 @@ def main():
     def step():
         solver.solve(Pd, Ud, Td, alg=w["alg"], layout="soa", out=out, status=status, stats=stats,
                      schedule=args.schedule, block=args.block, tpt=args.tpt,
-                     refill_min=args.refill, want_stats=True, **kw)
+                     refill_min=args.refill, order=args.order, want_stats=True, **kw)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -317,7 +318,8 @@ def main():
                    "tspan": [0.0, w["t1"]], **{k: w[k] for k in ("tol", "dt", "dt0") if k in w},
                    "layout": "soa", "l2": "flushed between steps (256 MB write outside events)",
                    "parallelism": "dp%d" % world, "block": args.block, "tpt": args.tpt,
-                   "schedule": args.schedule, "refill_min": args.refill},
+                   "schedule": args.schedule, "refill_min": args.refill,
+                   "order": args.order},
         "wall_s": wall,
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak_max,
                      "unit": "T FP32-FMA-pipe instr/s", "frac": achieved / peak_max,

@@ -73,6 +73,15 @@ enum {
                                from an atomic queue (per-lane refill) */
 };
 
+/* order in which the persistent schedule hands out trajectories */
+enum {
+  ENS_ORDER_AUTO = 0,   /* adaptive algorithms: COST; fixed-step: INDEX */
+  ENS_ORDER_INDEX = 1,  /* 0, 1, 2, ... */
+  ENS_ORDER_COST = 2    /* longest expected work first: key (tf - t0) / h0 with h0 the
+                           Hairer-Norsett-Wanner starting step (adaptive) or dt (fixed),
+                           counting-sorted on the device into 1024 log-spaced buckets */
+};
+
 #define ENS_MAX_SAVE 256
 
 typedef struct {
@@ -94,6 +103,7 @@ typedef struct {
   int refill_min;         /* persistent schedule: a warp refills its idle lanes once at least
                              this many are idle (1..32; 0 = default).  Batching refills trades
                              idle lanes for fewer divergent refill passes. */
+  int order;              /* ENS_ORDER_* (persistent schedule only) */
 } ens_opts;
 
 /* Fill *o with defaults: TSIT5_ADAPTIVE, F32, SOA, abstol=reltol=1e-6, maxiters=1e6, auto. */

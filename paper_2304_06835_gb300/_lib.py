@@ -19,6 +19,7 @@ ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5}
 F32, F64 = 0, 1
 LAYOUT = {"rowmajor": 0, "soa": 1}
 SCHED = {"auto": 0, "direct": 1, "persistent": 2}
+ORDER = {"auto": 0, "index": 1, "cost": 2}
 MAX_SAVE = 256
 STATUS = {0: "ok", 1: "maxiters", 2: "dt_min", 3: "nonfinite"}
 
@@ -31,7 +32,7 @@ class EnsOpts(ctypes.Structure):
         ("saveat", ctypes.POINTER(ctypes.c_double)), ("n_save", ctypes.c_int),
         ("seed", ctypes.c_ulonglong), ("index_offset", ctypes.c_longlong),
         ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
-        ("refill_min", ctypes.c_int),
+        ("refill_min", ctypes.c_int), ("order", ctypes.c_int),
     ]
 
 

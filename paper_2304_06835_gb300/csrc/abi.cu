@@ -12,20 +12,20 @@
 
 namespace ens {
 cudaError_t dispatch_f32_lorenz(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
-                                cudaFuncAttributes*, int*);
+                                cudaFuncAttributes*, int*, CostScratch*);
 cudaError_t dispatch_f32_robertson(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
-                                   cudaFuncAttributes*, int*);
+                                   cudaFuncAttributes*, int*, CostScratch*);
 cudaError_t dispatch_f32_gbm(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
-                             cudaFuncAttributes*, int*);
+                             cudaFuncAttributes*, int*, CostScratch*);
 cudaError_t dispatch_f64_lorenz(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
-                                cudaFuncAttributes*, int*);
+                                cudaFuncAttributes*, int*, CostScratch*);
 cudaError_t dispatch_f64_robertson(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
-                                   cudaFuncAttributes*, int*);
+                                   cudaFuncAttributes*, int*, CostScratch*);
 cudaError_t dispatch_f64_gbm(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
-                             cudaFuncAttributes*, int*);
+                             cudaFuncAttributes*, int*, CostScratch*);
 
 typedef cudaError_t (*DispatchFn)(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
-                                  cudaFuncAttributes*, int*);
+                                  cudaFuncAttributes*, int*, CostScratch*);
 
 static DispatchFn table(int rhs_id, int dtype) {
   static const DispatchFn t[2][3] = {
@@ -42,17 +42,61 @@ cudaError_t launch_solve(int rhs_id, int alg, int dtype, const SolveArgs& a,
     *supported = false;
     return cudaSuccess;
   }
-  return f(alg, &a, cfg, stream, supported, nullptr, nullptr);
+  return f(alg, &a, cfg, stream, supported, nullptr, nullptr, nullptr);
 }
 
-cudaError_t solve_kernel_attrs(int rhs_id, int alg, int dtype, const LaunchCfg& cfg,
-                               cudaFuncAttributes* attr, int* bps) {
+// exclusive scan of the kCostBuckets totals in place (one block of kCostBuckets threads)
+__global__ void k_cost_scan(unsigned int* tot) {
+  __shared__ unsigned int sh[kCostBuckets];
+  const int t = threadIdx.x;
+  sh[t] = tot[t];
+  __syncthreads();
+  for (int off = 1; off < kCostBuckets; off <<= 1) {
+    const unsigned int v = t >= off ? sh[t - off] : 0u;
+    __syncthreads();
+    sh[t] += v;
+    __syncthreads();
+  }
+  tot[t] = t ? sh[t - 1] : 0u;
+}
+
+__global__ void k_cost_scatter(long long N, long long chunk, const unsigned short* bucket,
+                               unsigned int* cursor, int* order) {
+  __shared__ unsigned int base[kCostBuckets];
+  for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) base[b] = 0u;
+  __syncthreads();
+  const long long lo = (long long)blockIdx.x * chunk;
+  const long long hi = lo + chunk < N ? lo + chunk : N;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&base[bucket[i]], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x)
+    if (base[b]) base[b] = atomicAdd(&cursor[b], base[b]);  // this block's range in bucket b
+  __syncthreads();
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const unsigned int pos = atomicAdd(&base[bucket[i]], 1u);
+    order[pos] = (int)i;
+  }
+}
+
+cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a,
+                              unsigned short* bucket, unsigned int* hist, int* order,
+                              cudaStream_t stream) {
   DispatchFn f = table(rhs_id, dtype);
-  bool sup = false;
   if (!f) return cudaErrorInvalidValue;
-  cudaError_t e = f(alg, nullptr, cfg, 0, &sup, attr, bps);
-  if (!sup) return cudaErrorInvalidValue;
-  return e;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kCostBuckets, stream);
+  if (e != cudaSuccess) return e;
+  CostScratch cs;
+  cs.bucket = bucket;
+  cs.hist = hist;
+  cs.blocks = (int)std::min<long long>(kCostBlocks, std::max<long long>(1, (a.N + 1023) / 1024));
+  cs.chunk = (a.N + cs.blocks - 1) / cs.blocks;
+  LaunchCfg cfg{};
+  bool sup = false;
+  e = f(alg, &a, cfg, stream, &sup, nullptr, nullptr, &cs);
+  if (e != cudaSuccess || !sup) return sup ? e : cudaErrorInvalidValue;
+  k_cost_scan<<<1, kCostBuckets, 0, stream>>>(hist);
+  k_cost_scatter<<<cs.blocks, 256, 0, stream>>>(a.N, cs.chunk, bucket, hist, order);
+  return cudaGetLastError();
 }
 
 // ---- random streams --------------------------------------------------------------------------
@@ -160,6 +204,11 @@ struct ens_handle {
   int device;
   int num_sms;
   unsigned long long* queue;  // persistent-schedule counter (device)
+  // longest-expected-first ordering scratch, grown on demand
+  int* order;
+  unsigned short* bucket;
+  unsigned int* hist;
+  long long order_cap;
   // staging for ens_solve_host
   void* stage;
   size_t stage_bytes;
@@ -228,6 +277,8 @@ int validate(const ens_handle* h, long long N, const void* params, const void* u
     return fail(ENS_EINVAL, "tpt must be 0, 1, 2 or 4");
   if (o->refill_min < 0 || o->refill_min > 32)
     return fail(ENS_EINVAL, "refill_min must be in [0, 32]");
+  if (o->order < ENS_ORDER_AUTO || o->order > ENS_ORDER_COST)
+    return fail(ENS_EINVAL, "unknown order");
   if (N > 0 && (!params || !u0 || !tspan || !out)) return fail(ENS_EINVAL, "null array");
   return ENS_OK;
 }
@@ -251,6 +302,9 @@ void fill_args(SolveArgs* a, long long N, const void* params, const void* u0, co
   a->dt0 = o->dt0;
   a->maxiters = o->maxiters;
   a->maxiters_i = (int)o->maxiters;
+  a->abstol_f = (float)o->abstol;
+  a->reltol_f = (float)o->reltol;
+  a->dt0_f = (float)o->dt0;
   a->refill_min = o->refill_min > 0 ? (o->refill_min > 32 ? 32 : o->refill_min) : 4;
   a->seed = o->seed;
   a->index_offset = o->index_offset;
@@ -301,10 +355,15 @@ int ens_create(ens_handle** out, int rhs_id, int D, int P) {
   h->P = P;
   h->stage = nullptr;
   h->stage_bytes = 0;
+  h->order = nullptr;
+  h->bucket = nullptr;
+  h->hist = nullptr;
+  h->order_cap = 0;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->queue, 256);
+  if (e == cudaSuccess) e = cudaMalloc(&h->hist, sizeof(unsigned int) * kCostBuckets);
   if (e != cudaSuccess) {
     delete h;
     return cuda_fail(e, "ens_create");
@@ -317,6 +376,9 @@ int ens_destroy(ens_handle* h) {
   if (!h) return ENS_OK;
   cudaDeviceSynchronize();
   cudaFree(h->queue);
+  cudaFree(h->hist);
+  if (h->order) cudaFree(h->order);
+  if (h->bucket) cudaFree(h->bucket);
   if (h->stage) cudaFree(h->stage);
   delete h;
   return ENS_OK;
@@ -332,6 +394,25 @@ int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, co
   SolveArgs a;
   fill_args(&a, N, params, u0, tspan, o, out, status, stats, h->queue);
   if (cfg.schedule == ENS_SCHED_PERSISTENT) {
+    const bool cost = o->order == ENS_ORDER_COST ||
+                      (o->order == ENS_ORDER_AUTO && !is_fixed(o->alg));
+    if (cost && N <= 0x7fffffffLL) {
+      if (N > h->order_cap) {
+        cudaFree(h->order);
+        cudaFree(h->bucket);
+        h->order = nullptr;
+        h->bucket = nullptr;
+        h->order_cap = 0;
+        cudaError_t e1 = cudaMalloc(&h->order, sizeof(int) * N);
+        cudaError_t e2 = cudaMalloc(&h->bucket, sizeof(unsigned short) * N);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ENS_ENOMEM, "order scratch");
+        h->order_cap = N;
+      }
+      cudaError_t e = launch_cost_order(h->rhs_id, o->alg, o->dtype, a, h->bucket, h->hist,
+                                        h->order, s);
+      if (e != cudaSuccess) return cuda_fail(e, "cost ordering");
+      a.order = h->order;
+    }
     cudaError_t e = cudaMemsetAsync(h->queue, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
   }

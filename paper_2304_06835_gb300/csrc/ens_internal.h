@@ -21,11 +21,20 @@ struct SolveArgs {
   double dt, abstol, reltol, dt0;
   long long maxiters;
   int maxiters_i;   // the same cap as an int (validated <= 2e9)
+  float abstol_f, reltol_f, dt0_f;  // FP32 copies (an FP32 solve never converts in its loop)
   int refill_min;   // persistent schedule: refill a warp's idle lanes once this many are idle
   unsigned long long seed;
   long long index_offset;
   unsigned long long* queue;  // persistent-schedule counter (device), zeroed before launch
+  const int* order;           // persistent schedule: queue slot -> trajectory index (or null)
   double saveat[ENS_MAX_SAVE];
+};
+
+struct CostScratch {
+  unsigned short* bucket;  // [N]
+  unsigned int* hist;      // [kCostBuckets] bucket totals, then cursors
+  int blocks;              // G <= kCostBlocks
+  long long chunk;         // trajectories per block
 };
 
 struct LaunchCfg {
@@ -35,10 +44,19 @@ struct LaunchCfg {
   int num_sms;
 };
 
-// Launch one solve; returns the CUDA error of the launch.  Implemented per precision in
-// solve_f32.cu / solve_f64.cu.
+// Launch one solve; returns the CUDA error of the launch.  Implemented per (precision, model)
+// in the solve_<precision>_<model>.cu units.
 cudaError_t launch_solve(int rhs_id, int alg, int dtype, const SolveArgs& a,
                          const LaunchCfg& cfg, cudaStream_t stream, bool* supported);
+
+// Longest-expected-first ordering for the persistent schedule: fills order[0..N) with the
+// trajectory indices sorted by decreasing cost key (counting sort over kCostBuckets
+// log-spaced buckets).  bucket: [N] scratch, hist: [kCostBuckets] scratch.
+constexpr int kCostBuckets = 1024;
+constexpr int kCostBlocks = 256;
+cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a,
+                              unsigned short* bucket, unsigned int* hist, int* order,
+                              cudaStream_t stream);
 
 // Register / shared-memory attributes of the kernel a launch would use (for tuning).
 cudaError_t solve_kernel_attrs(int rhs_id, int alg, int dtype, const LaunchCfg& cfg,

@@ -33,6 +33,10 @@ struct Clock {
     lo += c;
     hi = s;
   }
+  __device__ __forceinline__ void snap(bool cond, T v) {
+    hi = cond ? v : hi;
+    lo = cond ? T(0) : lo;
+  }
 };
 template <>
 struct Clock<double> {
@@ -41,6 +45,7 @@ struct Clock<double> {
   __device__ __forceinline__ double value() const { return hi; }
   __device__ __forceinline__ double remaining(double stop) const { return stop - hi; }
   __device__ __forceinline__ void add(double h) { hi += h; }
+  __device__ __forceinline__ void snap(bool cond, double v) { hi = cond ? v : hi; }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -105,6 +110,20 @@ __device__ __forceinline__ void write_stats(const SolveArgs& a, long long i, sig
   }
 }
 
+// tolerances / first step in the solve's precision (FP32 solves read the FP32 copies)
+template <class T>
+struct Tol {
+  static __device__ __forceinline__ T abstol(const SolveArgs& a) { return T(a.abstol); }
+  static __device__ __forceinline__ T reltol(const SolveArgs& a) { return T(a.reltol); }
+  static __device__ __forceinline__ T dt0(const SolveArgs& a) { return T(a.dt0); }
+};
+template <>
+struct Tol<float> {
+  static __device__ __forceinline__ float abstol(const SolveArgs& a) { return a.abstol_f; }
+  static __device__ __forceinline__ float reltol(const SolveArgs& a) { return a.reltol_f; }
+  static __device__ __forceinline__ float dt0(const SolveArgs& a) { return a.dt0_f; }
+};
+
 template <class T>
 __device__ __forceinline__ T rms_scaled(const T* x, const T* sc, int D) {
   T s = T(0);
@@ -133,8 +152,8 @@ struct Adaptive {
   T stop, stop_thr;   // next stop (a save time before tf, or tf) and its arrival threshold
   float lq;           // log2 q_{n-1}
   int attempts, rejected, si, fev0;
-  signed char st;
-  bool stop_is_save;
+  int st;             // ENS_TRAJ_* (int, not char: no byte packing in the loop)
+  int stop_is_save;
   long long idx;
 
   __device__ __forceinline__ void set_stop(const SolveArgs& a) {
@@ -150,8 +169,8 @@ struct Adaptive {
     t.set(t0);
     RHS::f(u, p, t0, fk);
     fev0 = 1;
-    if (a.dt0 > 0) {
-      h = T(a.dt0);
+    if (Tol<T>::dt0(a) > T(0)) {
+      h = Tol<T>::dt0(a);
     } else {
       h = initial_step(a, t0);
       fev0 = 2;
@@ -172,7 +191,7 @@ struct Adaptive {
   // with fast division and MUFU-based pow)
   __device__ __forceinline__ T initial_step(const SolveArgs& a, T t0) {
     T sc[D], u1[D], f1[D];
-    const T atol = T(a.abstol), rtol = T(a.reltol);
+    const T atol = Tol<T>::abstol(a), rtol = Tol<T>::reltol(a);
     T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -198,41 +217,38 @@ struct Adaptive {
     return M<T>::min(T(100) * h0, h1);
   }
 
-  // one attempt; returns true when the trajectory is finished
+  // one attempt; returns true when the trajectory is finished.  The common path has no
+  // data-dependent branch: the rare exits are merged into one test and accept/reject is
+  // applied with selects.
   __device__ __forceinline__ bool advance(const SolveArgs& a) {
     T rem = t.remaining(stop);
-    while (rem <= stop_thr) {  // arrived at the stop
-      t.set(stop);
-      if (!stop_is_save) {
-        while (si < a.n_save && T(a.saveat[si]) == tf) {
-          write_slot<RHS, T>(a, idx, si, u);
-          ++si;
+    if (rem <= stop_thr) {  // arrived at the stop
+      do {
+        t.set(stop);
+        if (!stop_is_save) {
+          while (si < a.n_save && T(a.saveat[si]) == tf) {
+            write_slot<RHS, T>(a, idx, si, u);
+            ++si;
+          }
+          return true;
         }
-        return true;
-      }
-      write_slot<RHS, T>(a, idx, si, u);
-      ++si;
-      set_stop(a);
-      rem = t.remaining(stop);
-    }
-    if (attempts >= a.maxiters_i) {
-      st = ENS_TRAJ_MAXITERS;
-      return true;
+        write_slot<RHS, T>(a, idx, si, u);
+        ++si;
+        set_stop(a);
+        rem = t.remaining(stop);
+      } while (rem <= stop_thr);
     }
     const bool last = h >= rem;
     const T hs = last ? rem : h;
     const T tnow = t.value();
-    if (hs < T(M<T>::dtmin_factor) * M<T>::max(T(1), M<T>::abs(tnow))) {
-      st = ENS_TRAJ_DT_MIN;
-      return true;
-    }
+    const bool capped = attempts >= a.maxiters_i;
+    const bool tiny = hs < T(M<T>::dtmin_factor) * M<T>::max(T(1), M<T>::abs(tnow));
     T unew[D], es[D], fnew[D];
     if (METH == METH_TSIT5) tsit5_step<RHS, T, true>(u, p, tnow, hs, fk, unew, es, fnew);
     else ros23_step<RHS, T>(u, p, tnow, hs, fk, unew, es, fnew);
-    ++attempts;
     // q^2 = (1/D) sum_j (E_j / (atol + rtol max(|u_j|, |unew_j|)))^2 with E_j = h es_j.
     // The ratios are formed in FP32 for both precisions (E itself is accumulated in T).
-    const T atol = T(a.abstol), rtol = T(a.reltol);
+    const T atol = Tol<T>::abstol(a), rtol = Tol<T>::reltol(a);
     float r2 = 0.f;
     bool fin = true;
 #pragma unroll
@@ -243,29 +259,28 @@ struct Adaptive {
       fin = fin && M<T>::finite(unew[j]);
     }
     const float q2 = r2 * (1.f / float(D));
-    if (!fin || isnan(q2)) {
-      st = ENS_TRAJ_NONFINITE;
+    if (capped || tiny || !fin || isnan(q2)) {
+      // priority as the checks would run in sequence: cap, step too small, non-finite attempt
+      st = capped ? ENS_TRAJ_MAXITERS : (tiny ? ENS_TRAJ_DT_MIN : ENS_TRAJ_NONFINITE);
+      attempts += (capped || tiny) ? 0 : 1;
       return true;
     }
-    const bool accept = q2 <= 1.f;
+    ++attempts;
+    const bool acc = q2 <= 1.f;
     // PI control: accept fac = eta q_n^{-beta1} q_{n-1}^{beta2} in [0.2, 10];
     // reject fac = max(0.2, eta q_n^{-1/k}).  Exponentials in log2 form (q guarded at 1e-10).
     const float L = lg2_approx(fmaxf(q2, 1e-20f));  // log2 q^2
-    const float e = accept ? __fmaf_rn(-0.35f / kOrd, L, (0.4f / kOrd) * lq) : (-0.5f / kOrd) * L;
-    float fac = float(kEta) * ex2_approx(e);
-    fac = fminf(accept ? 10.f : 1.f, fmaxf(0.2f, fac));
-    if (accept) {
+    const float e = acc ? __fmaf_rn(-0.35f / kOrd, L, (0.4f / kOrd) * lq) : (-0.5f / kOrd) * L;
+    const float fac = fminf(acc ? 10.f : 1.f, fmaxf(0.2f, float(kEta) * ex2_approx(e)));
 #pragma unroll
-      for (int j = 0; j < D; ++j) {
-        u[j] = unew[j];
-        fk[j] = fnew[j];
-      }
-      if (last) t.set(stop);
-      else t.add(hs);
-      lq = fmaxf(0.5f * L, kLog2QoldInit);
-    } else {
-      ++rejected;
+    for (int j = 0; j < D; ++j) {
+      u[j] = acc ? unew[j] : u[j];
+      fk[j] = acc ? fnew[j] : fk[j];
     }
+    t.add(acc ? hs : T(0));
+    t.snap(acc && last, stop);
+    lq = acc ? fmaxf(0.5f * L, kLog2QoldInit) : lq;
+    rejected += acc ? 0 : 1;
     h = hs * T(fac);
     return false;
   }
@@ -274,6 +289,17 @@ struct Adaptive {
     if (a.n_save == 0) write_slot<RHS, T>(a, idx, 0, u);
     for (; si < a.n_save; ++si) write_nan_slot<RHS, T>(a, idx, si);
     write_stats(a, idx, st, attempts - rejected, rejected, fev0 + kFevPerAttempt * attempts);
+  }
+
+  // expected work of trajectory i: (tf - t0) / (starting step), the number of steps a solve
+  // that kept the Hairer-Norsett-Wanner starting step would take
+  static __device__ __forceinline__ float cost_key(const SolveArgs& a, long long i) {
+    Adaptive s;
+    T t0;
+    load_problem<RHS, T>(a, i, s.p, s.u, t0, s.tf);
+    RHS::f(s.u, s.p, t0, s.fk);
+    const T h0 = s.initial_step(a, t0);
+    return float(s.tf - t0) / float(h0);
   }
 };
 
@@ -401,6 +427,13 @@ struct Fixed {
                                                                                   : int(k);
     write_stats(a, idx, st, int(k), 0, fev);
   }
+
+  // expected work: the number of fixed steps
+  static __device__ __forceinline__ float cost_key(const SolveArgs& a, long long i) {
+    const double t0 = double(ldg<T>(a.tspan, in_idx(a.layout, i, 0, a.N, 2)));
+    const double tf = double(ldg<T>(a.tspan, in_idx(a.layout, i, 1, a.N, 2)));
+    return float((tf - t0) / a.dt);
+  }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -428,6 +461,41 @@ __global__ void k_direct(const SolveArgs a) {
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Longest-expected-first ordering: a counting sort of log2 cost keys (32 buckets per octave).
+// Block b of G owns trajectories [b*C, min((b+1)*C, N)).  Pass 1 computes each key's bucket
+// and adds the block's histogram into the bucket totals; a 1024-entry scan turns the totals
+// into bucket cursors; pass 2 reserves one contiguous range per (block, bucket) with a single
+// atomic and scatters with shared-memory atomics.  (Order inside a bucket is arbitrary: the
+// result of every trajectory does not depend on the order.)
+__device__ __forceinline__ int cost_bucket(float key) {
+  int b = (int)(log2f(fmaxf(key, 1.f)) * 32.f);  // NaN keys land in the cheapest bucket
+  b = b < 0 ? 0 : (b > kCostBuckets - 1 ? kCostBuckets - 1 : b);
+  return kCostBuckets - 1 - b;  // ascending bucket = descending cost
+}
+
+template <class I>
+__global__ void k_cost_keys(const SolveArgs a, long long chunk, unsigned short* bucket,
+                            unsigned int* tot) {
+  __shared__ unsigned int sh[kCostBuckets];
+  for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) sh[b] = 0u;
+  __syncthreads();
+  const long long lo = (long long)blockIdx.x * chunk;
+  const long long hi = lo + chunk < a.N ? lo + chunk : a.N;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const int b = cost_bucket(I::cost_key(a, i));
+    bucket[i] = (unsigned short)b;
+    atomicAdd(&sh[b], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x)
+    if (sh[b]) atomicAdd(&tot[b], sh[b]);
+}
+
+__global__ void k_cost_scan(unsigned int* tot);
+__global__ void k_cost_scatter(long long N, long long chunk, const unsigned short* bucket,
+                               unsigned int* cursor, int* order);
+
 // Persistent schedule.  Every lane of a warp stays in the loop until the whole warp is done,
 // so warp-wide votes are safe.  A lane that finishes its trajectory writes it out and idles;
 // once at least a.refill_min lanes of the warp are idle (or all are), the idle lanes fetch
@@ -437,42 +505,41 @@ template <class I, int TPT>
 __global__ void k_persistent(const SolveArgs a) {
   I s[TPT];
   bool act[TPT];
-  bool drained = false;  // warp-uniform: a fetch has come back past the end of the queue
 #pragma unroll
   for (int q = 0; q < TPT; ++q) {
     const long long i = queue_next(a.queue);
     act[q] = i < a.N;
-    if (act[q]) s[q].init(i, a);
+    if (act[q]) s[q].init(a.order ? (long long)__ldg(a.order + i) : i, a);
   }
-  drained = __any_sync(0xffffffffu, !act[TPT - 1]);
+  bool drained = __any_sync(0xffffffffu, !act[TPT - 1]);  // warp-uniform
   for (;;) {
+    unsigned busy = 0u;
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       if (act[q] && s[q].advance(a)) {
         s[q].finish(a);
         act[q] = false;
       }
+      busy |= __ballot_sync(0xffffffffu, act[q]);
     }
-    if (!drained) {
+    if (drained) {
+      if (busy == 0u) break;
+      continue;
+    }
 #pragma unroll
-      for (int q = 0; q < TPT; ++q) {
-        const unsigned idle = __ballot_sync(0xffffffffu, !act[q]);
-        if (__popc(idle) >= a.refill_min) {
-          bool got = true;
-          if (!act[q]) {
-            const long long i = queue_next(a.queue);
-            act[q] = i < a.N;
-            got = act[q];
-            if (act[q]) s[q].init(i, a);
-          }
-          drained = drained || __any_sync(0xffffffffu, !got);
+    for (int q = 0; q < TPT; ++q) {
+      const unsigned idle = __ballot_sync(0xffffffffu, !act[q]);
+      if (__popc(idle) >= a.refill_min) {
+        bool got = true;
+        if (!act[q]) {
+          const long long i = queue_next(a.queue);
+          act[q] = i < a.N;
+          got = act[q];
+          if (act[q]) s[q].init(a.order ? (long long)__ldg(a.order + i) : i, a);
         }
+        drained = drained || __any_sync(0xffffffffu, !got);
       }
     }
-    bool any = false;
-#pragma unroll
-    for (int q = 0; q < TPT; ++q) any = any || act[q];
-    if (!__any_sync(0xffffffffu, any)) break;
   }
 }
 

@@ -60,24 +60,32 @@ cudaError_t attrs_integ(const LaunchCfg& cfg, cudaFuncAttributes* attr, int* bps
 }
 
 template <class I>
+cudaError_t cost_keys_integ(const SolveArgs& a, CostScratch* cs, cudaStream_t s) {
+  k_cost_keys<I><<<cs->blocks, 256, 0, s>>>(a, cs->chunk, cs->bucket, cs->hist);
+  return cudaGetLastError();
+}
+
+template <class I>
 cudaError_t run_integ(const SolveArgs* a, const LaunchCfg& cfg, cudaStream_t s,
-                      cudaFuncAttributes* attr, int* bps) {
+                      cudaFuncAttributes* attr, int* bps, CostScratch* cs) {
+  if (cs) return cost_keys_integ<I>(*a, cs, s);
   return attr ? attrs_integ<I>(cfg, attr, bps) : launch_integ<I>(*a, cfg, s);
 }
 
 // Dispatch on the algorithm for one model: launch (attr == nullptr) or report attributes.
 template <class RHS, class T>
 cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cudaStream_t s,
-                           bool* supported, cudaFuncAttributes* attr, int* bps) {
+                           bool* supported, cudaFuncAttributes* attr, int* bps,
+                           CostScratch* cs) {
   *supported = true;
   switch (alg) {
-    case ENS_TSIT5_FIXED: return run_integ<Fixed<RHS, T, METH_FIX_TSIT5>>(a, cfg, s, attr, bps);
-    case ENS_TSIT5_ADAPTIVE: return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps);
-    case ENS_RK4: return run_integ<Fixed<RHS, T, METH_FIX_RK4>>(a, cfg, s, attr, bps);
-    case ENS_ROS23: return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps);
+    case ENS_TSIT5_FIXED: return run_integ<Fixed<RHS, T, METH_FIX_TSIT5>>(a, cfg, s, attr, bps, cs);
+    case ENS_TSIT5_ADAPTIVE: return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps, cs);
+    case ENS_RK4: return run_integ<Fixed<RHS, T, METH_FIX_RK4>>(a, cfg, s, attr, bps, cs);
+    case ENS_ROS23: return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps, cs);
     case ENS_EM:
       if constexpr (RHS::has_noise) {
-        return run_integ<Fixed<RHS, T, METH_FIX_EM>>(a, cfg, s, attr, bps);
+        return run_integ<Fixed<RHS, T, METH_FIX_EM>>(a, cfg, s, attr, bps, cs);
       }
       break;
   }
@@ -90,7 +98,7 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
 #define ENS_INSTANTIATE_MODEL(FN, MODEL, T)                                                 \
   namespace ens {                                                                           \
   cudaError_t FN(int alg, const SolveArgs* a, const LaunchCfg& cfg, cudaStream_t s,         \
-                 bool* supported, cudaFuncAttributes* attr, int* bps) {                     \
-    return dispatch_model<MODEL<T>, T>(alg, a, cfg, s, supported, attr, bps);               \
+                 bool* supported, cudaFuncAttributes* attr, int* bps, CostScratch* cs) {    \
+    return dispatch_model<MODEL<T>, T>(alg, a, cfg, s, supported, attr, bps, cs);           \
   }                                                                                         \
   }

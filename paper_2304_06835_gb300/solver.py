@@ -22,7 +22,7 @@ _NP_DT = {np.dtype(np.float32): _lib.F32, np.dtype(np.float64): _lib.F64}
 
 def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-6, reltol=1e-6,
               dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
-              schedule="auto", block=0, tpt=0, refill_min=0):
+              schedule="auto", block=0, tpt=0, refill_min=0, order="auto"):
     o = _lib.EnsOpts()
     _lib.lib().ens_opts_default(ctypes.byref(o))
     o.alg = _lib.ALG[alg] if isinstance(alg, str) else int(alg)
@@ -44,6 +44,7 @@ def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-
     o.block = int(block)
     o.tpt = int(tpt)
     o.refill_min = int(refill_min)
+    o.order = _lib.ORDER[order] if isinstance(order, str) else int(order)
     return o, keep
 
 
@@ -85,8 +86,8 @@ class EnsembleSolver:
 
     def solve(self, params, u0, tspan, alg="tsit5", *, layout="rowmajor", dt=0.0, abstol=1e-6,
               reltol=1e-6, dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
-              schedule="auto", block=0, tpt=0, refill_min=0, want_status=True, want_stats=False,
-              out=None, status=None, stats=None, stream=None):
+              schedule="auto", block=0, tpt=0, refill_min=0, order="auto", want_status=True,
+              want_stats=False, out=None, status=None, stats=None, stream=None):
         if not (params.is_cuda and u0.is_cuda and tspan.is_cuda):
             raise ValueError("params, u0 and tspan must be CUDA tensors")
         if params.dtype not in _TORCH_DT or u0.dtype != params.dtype or tspan.dtype != params.dtype:
@@ -107,7 +108,7 @@ class EnsembleSolver:
         if want_stats and stats is None:
             stats = torch.empty((3, N), dtype=torch.int32, device=dev)
         o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, dt, abstol, reltol, dt0, maxiters,
-                            saveat, seed, index_offset, schedule, block, tpt, refill_min)
+                            saveat, seed, index_offset, schedule, block, tpt, refill_min, order)
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
         _lib.check(_lib.lib().ens_solve(self._h, N, _ptr(params), _ptr(u0), _ptr(tspan),
                                         ctypes.byref(o), _ptr(out), _ptr(status), _ptr(stats),

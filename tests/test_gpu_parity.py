@@ -70,19 +70,43 @@ def test_ragged_sizes_and_layouts_and_schedules(S, N):
     s = S["lorenz"]
     outs = []
     for layout in ("rowmajor", "soa"):
-        for sched, tpt in (("direct", 0), ("persistent", 1), ("persistent", 2), ("persistent", 4)):
+        for sched, tpt, order in (("direct", 0, "auto"), ("persistent", 1, "index"),
+                                  ("persistent", 2, "index"), ("persistent", 4, "index"),
+                                  ("persistent", 1, "cost")):
             if layout == "soa":
                 o, _, _ = s.solve(dev(P.T.copy()), dev(U.T.copy()), dev(T.T.copy()),
-                                  alg="tsit5_fixed", dt=1e-3, layout="soa", schedule=sched, tpt=tpt)
+                                  alg="tsit5_fixed", dt=1e-3, layout="soa", schedule=sched, tpt=tpt,
+                                  order=order)
                 o = host(o).T
             else:
                 o, _, _ = s.solve(dev(P), dev(U), dev(T), alg="tsit5_fixed", dt=1e-3,
-                                  schedule=sched, tpt=tpt)
+                                  schedule=sched, tpt=tpt, order=order)
                 o = host(o)
             outs.append(o)
     for o in outs:
         np.testing.assert_array_equal(o, outs[0])  # schedule/layout change no arithmetic
     assert normwise(outs[0], ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 37, 5000])
+def test_adaptive_schedules_and_orders_agree(S, N):
+    """Per-trajectory arithmetic does not depend on schedule, order, TPT or refill batching."""
+    P, U, T = workloads.lorenz_random(N, seed=100 + N, t1=2.0)
+    T[:, 1] = np.random.default_rng(N).uniform(0.1, 3.0, N)  # uneven lengths
+    s = S["lorenz"]
+    ref = None
+    for kw in (dict(schedule="direct"), dict(schedule="persistent", order="index"),
+               dict(schedule="persistent", order="cost"), dict(schedule="persistent", tpt=2),
+               dict(schedule="persistent", refill_min=1), dict(schedule="persistent", refill_min=32)):
+        o, st, stats = s.solve(dev(P, torch.float32), dev(U, torch.float32),
+                               dev(T, torch.float32), alg="tsit5", abstol=1e-6, reltol=1e-6,
+                               want_stats=True, **kw)
+        cur = (host(o), st.cpu().numpy(), stats.cpu().numpy())
+        if ref is None:
+            ref = cur
+        else:
+            for x, y in zip(cur, ref):
+                np.testing.assert_array_equal(x, y)
 
 
 def test_empty_ensemble(S):
