@@ -161,6 +161,23 @@ int ens_normals(unsigned long long seed, long long index_offset, long long n_tra
 int ens_probe_fma(int dtype, long long iters, int blocks, int threads, double* ops_per_s,
                   void* cuda_stream);
 
+/* No counterpart in the paper.  The ensemble solve of ens_solve (same options, same
+ * device-array arguments, same results) for callers that must not allocate device memory:
+ * a framework that owns all device memory through its own pool, a real-time loop that cannot
+ * pay cudaMalloc's implicit synchronisation, a plugin whose host forbids allocations.  It
+ * needs no handle and calls no cudaMalloc, cudaFree or allocating library routine; its
+ * scratch (queue counter, cost-order permutation and keys, bucket cursors) lives in one
+ * fixed device array of the library, about 6 MiB, that every GPU loading the library holds
+ * until the process exits.  The first call on a device looks up that array's device address
+ * (once per device): make that first call before any stream capture.  All calls share the
+ * array: a call clears what must start at zero, and calls that overlap on the GPU (other
+ * streams or host threads) race on it, so order them on one stream.
+ * Errors: ENS_EINVAL when N > ENS_NOALLOC_MAX_N, otherwise as ens_solve. */
+#define ENS_NOALLOC_MAX_N 1048576LL
+int ens_solve_noalloc(int rhs_id, long long N, const void* params, const void* u0,
+                      const void* tspan, const ens_opts* opts, void* out, signed char* status,
+                      int* stats, void* cuda_stream);
+
 const char* ens_last_error(void);
 
 #ifdef __cplusplus

@@ -59,6 +59,8 @@ SIGNATURES = {
                               _VP]),
     "ens_philox4x32_10": (_INT, [_ULL, _LL, _LL, _LL, _VP, _VP]),
     "ens_normals": (_INT, [_ULL, _LL, _LL, _LL, _INT, _VP, _VP]),
+    "ens_solve_noalloc": (_INT, [_INT, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP,
+                                 _VP]),
     "ens_probe_fma": (_INT, [_INT, _LL, _INT, _INT, ctypes.POINTER(ctypes.c_double), _VP]),
     "ens_last_error": (ctypes.c_char_p, []),
 }

@@ -327,6 +327,11 @@ size_t elem_size(int dtype) { return dtype == ENS_F32 ? 4 : 8; }
 
 }  // namespace
 
+namespace ens {
+// Record an error for ens_last_error() from another translation unit of the library.
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace ens
+
 extern "C" {
 
 void ens_opts_default(ens_opts* o) {
