@@ -7,6 +7,11 @@ ensemble solve.  Metric: trajectories per second (whole job, all ranks).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
+Other workloads (--workload): lorenz_adaptive_f64, lorenz_fixed_f32, robertson_ros23_f64,
+lorenz_adjoint_f64 (forward with checkpoints + discrete adjoint, N = 65,536, 1000 fixed Tsit5
+steps, FP64), uneven_batch_f32 (500k Lorenz tf~U[1,100] + 200k Robertson + 300k GBM in one
+CUDA-graph launch, FP32).
+
 Under torchrun (N > 1) every rank solves its own N-trajectory shard (weak scaling, no
 collective on the data path); the timing is the max over ranks.
 """
@@ -30,29 +35,52 @@ import workloads  # noqa: E402
 METRIC = "Lorenz Tsit5 trajectories/s at N=1M, % FMA peak; surrogate vs solver at stated err"
 SMS = 152
 FP32_LANES = 128
+FP64_LANES = 2          # GB300: FP64 is 1/64 of the FP32 lane rate (nominal 1.25 TFLOP/s)
 SM_MAX_MHZ = 2070.0
 
-# Algorithmic FP32 work per adaptive Tsit5 attempt on Lorenz (FMA-pipe instructions):
-# stage combinations 81, six f evaluations 36, error estimate 21, scaled RMS norm 19,
-# PI-controller arithmetic 3  -> 160 (selects, compares and clamps are not counted).
-OPS_PER_ATTEMPT = {"tsit5": 160, "tsit5_fixed": 117, "rk4": 48, "ros23": 140, "em": 25}
+# Algorithmic work, in FMA-pipe instructions (FFMA/FADD/FMUL or their FP64 forms) per unit,
+# counted from the operation model of each step (selects, compares and clamps not counted):
+#   adaptive Tsit5 attempt on Lorenz: stage combinations 81, six f evaluations 36, error
+#     estimate 21, scaled RMS norm 19, PI-controller arithmetic 3 -> 160;
+#   fixed Tsit5 step: stage combinations 81 + six f evaluations 36 -> 117;
+#   adjoint step (Tsit5, Lorenz): forward with checkpoints 117, replay 117, transposed step
+#     189 (six VJP pairs 6 x 18, stage-adjoint sums 45 + 15, seeds 21) -> 423.
+OPS_PER_ATTEMPT = {"tsit5": 160, "tsit5_fixed": 117, "rk4": 48, "ros23": 140, "em": 25,
+                   "adjoint": 423}
 
 WORKLOADS = {
-    # name: (model, alg, dtype, N, t1, tol / dt)
-    "lorenz_adaptive_f32": dict(rhs="lorenz", alg="tsit5", dtype="f32", N=1 << 20, t1=10.0,
-                                tol=1e-5),
-    "lorenz_adaptive_f64": dict(rhs="lorenz", alg="tsit5", dtype="f64", N=1 << 20, t1=10.0,
-                                tol=1e-8),
-    "lorenz_fixed_f32": dict(rhs="lorenz", alg="tsit5_fixed", dtype="f32", N=1 << 20, t1=1.0,
-                             dt=1e-3),
-    "robertson_ros23_f64": dict(rhs="robertson", alg="ros23", dtype="f64", N=1 << 18, t1=1e5,
-                                tol=1e-6, dt0=1e-4),
+    # name: model, algorithm, precision, N, tspan end, tolerance / step, default timed steps
+    "lorenz_adaptive_f32": dict(kind="solve", rhs="lorenz", alg="tsit5", dtype="f32", N=1 << 20,
+                                t1=10.0, tol=1e-5, steps=1000),
+    "lorenz_adaptive_f64": dict(kind="solve", rhs="lorenz", alg="tsit5", dtype="f64", N=1 << 20,
+                                t1=10.0, tol=1e-8, steps=5),
+    "lorenz_fixed_f32": dict(kind="solve", rhs="lorenz", alg="tsit5_fixed", dtype="f32",
+                             N=1 << 20, t1=1.0, dt=1e-3, steps=300),
+    "robertson_ros23_f64": dict(kind="solve", rhs="robertson", alg="ros23", dtype="f64",
+                                N=1 << 18, t1=1e5, tol=1e-6, dt0=1e-4, steps=20),
+    "lorenz_adjoint_f64": dict(kind="adjoint", rhs="lorenz", alg="tsit5_fixed", dtype="f64",
+                               N=65536, t1=1.0, dt=1e-3, every=64, steps=30),
+    "uneven_batch_f32": dict(kind="batch", rhs="mixed", alg="tsit5+ros23+em", dtype="f32",
+                             N=1_000_000, t1=100.0, steps=100),
 }
+
+# the uneven batch: 500k Lorenz (adaptive Tsit5, tf ~ U[1,100]), 200k Robertson
+# (Rosenbrock23, abstol 1e-8, reltol 1e-4, dt0 1e-4), 300k GBM (Euler-Maruyama, dt 1e-3)
+BATCH_PARTS = (("lorenz", "tsit5", 500_000, dict(abstol=1e-5, reltol=1e-5)),
+               ("robertson", "ros23", 200_000, dict(abstol=1e-8, reltol=1e-4, dt0=1e-4)),
+               ("gbm", "em", 300_000, dict(dt=1e-3, seed=12345)))
+
+
+def batch_inputs(rank=0):
+    b = workloads.uneven_batch(*(n for _, _, n, _ in BATCH_PARTS), seed=4 + 1000 * rank)
+    return [b[name] for name, _, _, _ in BATCH_PARTS]
 
 
 def inputs_for(w, rank=0):
     N = w["N"]
-    if w["rhs"] == "lorenz":
+    if w["kind"] == "adjoint":
+        P, U, T = workloads.lorenz_random(N, seed=5 + 1000 * rank, t1=w["t1"])
+    elif w["rhs"] == "lorenz":
         if w["alg"] == "tsit5_fixed":
             P, U, T = workloads.lorenz_sweep(N, t1=w["t1"])
         else:
@@ -88,7 +116,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -96,7 +124,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.3)
+        time.sleep(0.15)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -122,37 +150,72 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- oracle leg
-def oracle_rate(w, budget_s=12.0):
-    """Oracle (CPU, FP64, as it stands) on a bounded prefix of the same workload."""
+def _oracle_run(w, P, U, T, n, nt, G=None):
     import oracle
-    P, U, T = inputs_for(w)
-    kw = solve_kwargs(w)
+    if w["kind"] == "batch":  # the same share of every part: n of the N trajectories
+        for (name, alg, nk, kw), (Pk, Uk, Tk) in zip(BATCH_PARTS, P):
+            m = max(1, int(round(n * nk / w["N"])))
+            oracle.solve(name, alg, Pk[:m], Uk[:m], Tk[:m], nthreads=nt, **kw)
+        return
+    if w["kind"] == "adjoint":
+        oracle.fixed_grad(w["rhs"], w["alg"], P[:n], U[:n], T[:n], w["dt"], G[:n], nthreads=nt)
+    else:
+        oracle.solve(w["rhs"], w["alg"], P[:n], U[:n], T[:n], nthreads=nt, **solve_kwargs(w))
+
+
+def oracle_rate(w, budget_s=12.0):
+    """The oracle (CPU, FP64, as it stands) on a bounded sample of the same workload: a prefix
+    of the inputs, repeated when the whole workload takes less than the budget."""
+    import oracle
+    if w["kind"] == "batch":
+        P, U, T = batch_inputs(), None, None
+    else:
+        P, U, T = inputs_for(w)
+    G = workloads.adjoint_targets(w["N"], seed=5) if w["kind"] == "adjoint" else None
     nt = oracle.default_threads()
-    n = min(w["N"], 4 * nt)
-    t0 = time.perf_counter()
-    oracle.solve(w["rhs"], w["alg"], P[:n], U[:n], T[:n], nthreads=nt, **kw)
-    dt = time.perf_counter() - t0
+    n = min(w["N"], 64 * nt)
+    while True:
+        t0 = time.perf_counter()
+        _oracle_run(w, P, U, T, n, nt, G)
+        dt = time.perf_counter() - t0
+        if dt > 0.5 or n == w["N"]:
+            break
+        n = min(w["N"], n * 4)
     n2 = int(min(w["N"], max(n, n * budget_s / max(dt, 1e-3))))
+    reps = max(1, int(round(budget_s / max(dt * n2 / n, 1e-3)))) if n2 == w["N"] else 1
     t0 = time.perf_counter()
-    oracle.solve(w["rhs"], w["alg"], P[:n2], U[:n2], T[:n2], nthreads=nt, **kw)
-    dt = time.perf_counter() - t0
-    return n2 / dt, n2, nt, dt
+    for _ in range(reps):
+        _oracle_run(w, P, U, T, n2, nt, G)
+    el = time.perf_counter() - t0
+    sample = ("%d pass(es) over the first %d of the %d trajectories (%.1f s)"
+              % (reps, n2, w["N"], el))
+    return n2 * reps / el, sample, nt
 
 
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
     import oracle
-    P, U, T = inputs_for(w)
-    kw = solve_kwargs(w)
+    if w["kind"] == "batch":
+        P, U, T = batch_inputs(), None, None
+    else:
+        P, U, T = inputs_for(w)
+    G = workloads.adjoint_targets(w["N"], seed=5) if w["kind"] == "adjoint" else None
     nt = oracle.default_threads()
-    rate, n, _, _ = oracle_rate(w, budget_s=4.0)
-    n = max(1, int(rate * 3.0))  # each step ~3 s of CPU work
+    n = min(w["N"], 64 * nt)
+    while True:  # size each step to ~3 s of CPU work
+        t0 = time.perf_counter()
+        _oracle_run(w, P, U, T, n, nt, G)
+        dt = time.perf_counter() - t0
+        if dt > 0.3 or n == w["N"]:
+            break
+        n = min(w["N"], n * 4)
+    n = max(1, min(w["N"], int(n * 3.0 / max(dt, 1e-3))))
     for _ in range(args.warmup):
-        oracle.solve(w["rhs"], w["alg"], P[:n], U[:n], T[:n], nthreads=nt, **kw)
+        _oracle_run(w, P, U, T, n, nt, G)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.solve(w["rhs"], w["alg"], P[:n], U[:n], T[:n], nthreads=nt, **kw)
+        _oracle_run(w, P, U, T, n, nt, G)
     el = time.perf_counter() - t0
     v = n * args.steps / el
     line = {
@@ -170,49 +233,254 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line))
 
 
-def e2e_rate(args, w, P, U, T, solver, stream, kw):
-    """Trajectories/s through ens_solve_host: pinned host inputs copied to the device, the
-    solve, and the outputs (final state + status) copied back, all inside the timed region."""
-    import ctypes
+# ------------------------------------------------------------------------------- GPU legs
+class SolveRunner:
+    """One step = one ensemble solve through ens_solve (inputs resident in HBM)."""
 
-    import torch
+    def __init__(self, args, w, rank, dev):
+        import torch
 
-    import paper_2304_06835_gb300 as ens
-    from paper_2304_06835_gb300 import _lib
-    N = w["N"]
-    npdt = np.float32 if w["dtype"] == "f32" else np.float64
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=npdt)).pin_memory()
-    Pp, Up, Tp = pin(P.T), pin(U.T), pin(T.T)
-    D = U.shape[1]
-    outp = torch.empty((D, N), dtype=Pp.dtype).pin_memory()
-    stp = torch.empty(N, dtype=torch.int8).pin_memory()
-    o, keep = ens.make_opts(w["alg"], _lib.F32 if w["dtype"] == "f32" else _lib.F64, "soa",
-                            schedule=args.schedule, block=args.block, tpt=args.tpt,
-                            refill_min=args.refill, order=args.order, **kw)
-    sptr = ctypes.c_void_p(stream.cuda_stream)
+        import paper_2304_06835_gb300 as ens
+        self.args, self.w, self.dev = args, w, dev
+        self.dt_t = torch.float32 if w["dtype"] == "f32" else torch.float64
+        self.P, self.U, self.T = inputs_for(w, rank)
+        N = w["N"]
+        t = lambda a: torch.tensor(a.T.copy(), dtype=self.dt_t, device=dev)
+        self.Pd, self.Ud, self.Td = t(self.P), t(self.U), t(self.T)
+        D = self.U.shape[1]
+        self.out = torch.empty((D, N), dtype=self.dt_t, device=dev)
+        self.status = torch.empty(N, dtype=torch.int8, device=dev)
+        self.stats = torch.empty((3, N), dtype=torch.int32, device=dev)
+        self.solver = ens.EnsembleSolver(w["rhs"])
+        self.kw = solve_kwargs(w)
+        fixed = w["alg"] in ("tsit5_fixed", "rk4", "em")
+        sched = args.schedule if args.schedule != "auto" else ("direct" if fixed else "persistent")
+        order = args.order if args.order != "auto" else ("index" if fixed else "cost")
+        # kernels of one solve: the integrator, plus key / scan / scatter for the cost order
+        self.launches_per_step = 1 + (3 if sched == "persistent" and order == "cost" else 0)
 
-    def host_step():
-        _lib.check(_lib.lib().ens_solve_host(solver.handle, N, Pp.data_ptr(), Up.data_ptr(),
-                                             Tp.data_ptr(), ctypes.byref(o), outp.data_ptr(),
-                                             stp.data_ptr(), None, sptr))
-    host_step()
-    torch.cuda.synchronize()
-    steps = max(1, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(steps):
+    def step(self):
+        a = self.args
+        self.solver.solve(self.Pd, self.Ud, self.Td, alg=self.w["alg"], layout="soa",
+                          out=self.out, status=self.status, stats=self.stats,
+                          schedule=a.schedule, block=a.block, tpt=a.tpt, refill_min=a.refill,
+                          order=a.order, want_stats=True, **self.kw)
+
+    def work(self):
+        st = self.stats.cpu().numpy().astype(np.int64)
+        attempts = int(st[0].sum() + st[1].sum())
+        ok = int((self.status.cpu().numpy() == 0).sum())
+        return attempts * OPS_PER_ATTEMPT[self.w["alg"]], {
+            "attempts_per_launch": attempts, "ops_per_attempt": OPS_PER_ATTEMPT[self.w["alg"]],
+            "trajectories_ok": ok}
+
+    def e2e(self, stream):
+        """Trajectories/s through ens_solve_host: pinned host inputs copied to the device, the
+        solve, and the outputs (final state + status) copied back, inside the timed region."""
+        import ctypes
+
+        import torch
+
+        import paper_2304_06835_gb300 as ens
+        from paper_2304_06835_gb300 import _lib
+        w, a = self.w, self.args
+        N = w["N"]
+        npdt = np.float32 if w["dtype"] == "f32" else np.float64
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=npdt)).pin_memory()
+        Pp, Up, Tp = pin(self.P.T), pin(self.U.T), pin(self.T.T)
+        D = self.U.shape[1]
+        outp = torch.empty((D, N), dtype=Pp.dtype).pin_memory()
+        stp = torch.empty(N, dtype=torch.int8).pin_memory()
+        o, keep = ens.make_opts(w["alg"], _lib.F32 if w["dtype"] == "f32" else _lib.F64, "soa",
+                                schedule=a.schedule, block=a.block, tpt=a.tpt,
+                                refill_min=a.refill, order=a.order, **self.kw)
+        sptr = ctypes.c_void_p(stream.cuda_stream)
+
+        def host_step():
+            _lib.check(_lib.lib().ens_solve_host(self.solver.handle, N, Pp.data_ptr(),
+                                                 Up.data_ptr(), Tp.data_ptr(), ctypes.byref(o),
+                                                 outp.data_ptr(), stp.data_ptr(), None, sptr))
         host_step()
-    el = (time.perf_counter() - t0) / steps
-    es = np.dtype(npdt).itemsize
-    return {"value": N / el, "unit": "trajectories/s",
-            "h2d_bytes_per_step": int(N * es * (P.shape[1] + D + 2)),
-            "d2h_bytes_per_step": int(N * es * D + N)}
+        torch.cuda.synchronize()
+        steps = max(3, min(a.steps, 20))
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            host_step()
+        el = (time.perf_counter() - t0) / steps
+        es = np.dtype(npdt).itemsize
+        del keep
+        return {"value": N / el, "unit": "trajectories/s",
+                "h2d_bytes_per_step": int(N * es * (self.P.shape[1] + D + 2)),
+                "d2h_bytes_per_step": int(N * es * D + N)}
 
 
-# ------------------------------------------------------------------------------- GPU leg
+class AdjointRunner:
+    """One step = the gradient of L = sum_i ||u_i(tf) - target_i||^2 w.r.t. (p_i, u0_i):
+    ens_adjoint_forward (fixed Tsit5 with checkpoints), the loss gradient 2 (u - target), and
+    ens_adjoint (replay + transposed steps)."""
+
+    def __init__(self, args, w, rank, dev):
+        import torch
+
+        import paper_2304_06835_gb300 as ens
+        self.args, self.w, self.dev = args, w, dev
+        self.P, self.U, self.T = inputs_for(w, rank)
+        self.tgt = workloads.adjoint_targets(w["N"], seed=5 + 1000 * rank)
+        t = lambda a: torch.tensor(a.T.copy(), dtype=torch.float64, device=dev)
+        self.Pd, self.Ud, self.Td, self.tg = t(self.P), t(self.U), t(self.T), t(self.tgt)
+        self.solver = ens.EnsembleSolver(w["rhs"])
+        self.n = int(np.ceil((w["t1"] - 0.0) / w["dt"] - 1e-12))
+        self.out, self.ckpt, self.status, _ = self.solver.adjoint_forward(
+            self.Pd, self.Ud, self.Td, w["alg"], dt=w["dt"], layout="soa", max_steps=self.n,
+            checkpoint_every=w["every"])
+        self.gp = torch.empty_like(self.Pd)
+        self.gu = torch.empty_like(self.Ud)
+        self.G = torch.empty_like(self.out)
+        self.launches_per_step = 2
+
+    def step(self):
+        import torch
+        w = self.w
+        self.solver.adjoint_forward(self.Pd, self.Ud, self.Td, w["alg"], dt=w["dt"],
+                                    layout="soa", max_steps=self.n, checkpoint_every=w["every"],
+                                    out=self.out, ckpt=self.ckpt, status=self.status)
+        torch.sub(self.out, self.tg, out=self.G).mul_(2.0)
+        self.solver.adjoint(self.Pd, self.Ud, self.Td, self.G, w["alg"], dt=w["dt"],
+                            layout="soa", max_steps=self.n, checkpoint_every=w["every"],
+                            ckpt=self.ckpt, grad_p=self.gp, grad_u0=self.gu)
+
+    def work(self):
+        ok = int((self.status.cpu().numpy() == 0).sum())
+        steps = self.w["N"] * self.n
+        return steps * OPS_PER_ATTEMPT["adjoint"], {
+            "steps_per_launch": steps, "ops_per_step": OPS_PER_ATTEMPT["adjoint"],
+            "trajectories_ok": ok}
+
+    def e2e(self, stream):
+        """Gradient evaluations/s with host inputs: pinned params/u0/tspan/targets copied in,
+        forward + adjoint, gradients copied back, inside the timed region."""
+        import torch
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).pin_memory()
+        hp, hu, ht, hg = pin(self.P), pin(self.U), pin(self.T), pin(self.tgt)
+        ogp = torch.empty_like(hp).pin_memory()
+        ogu = torch.empty_like(hu).pin_memory()
+
+        def host_step():
+            self.Pd.copy_(hp, non_blocking=True)
+            self.Ud.copy_(hu, non_blocking=True)
+            self.Td.copy_(ht, non_blocking=True)
+            self.tg.copy_(hg, non_blocking=True)
+            self.step()
+            ogp.copy_(self.gp, non_blocking=True)
+            ogu.copy_(self.gu, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        host_step()
+        steps = max(3, min(self.args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            host_step()
+        el = (time.perf_counter() - t0) / steps
+        N = self.w["N"]
+        return {"value": N / el, "unit": "trajectories/s",
+                "h2d_bytes_per_step": int(8 * N * (3 + 3 + 2 + 3)),
+                "d2h_bytes_per_step": int(8 * N * (3 + 3))}
+
+
+class BatchRunner:
+    """One step = one ens_batch_run of the uneven batch (a single CUDA-graph launch that runs
+    the three sub-problems as concurrent persistent kernels, launch shapes autotuned)."""
+
+    def __init__(self, args, w, rank, dev):
+        import torch
+
+        import paper_2304_06835_gb300 as ens
+        self.args, self.w, self.dev = args, w, dev
+        self.parts = batch_inputs(rank)
+        t = lambda a: torch.tensor(a.T.copy(), dtype=torch.float32, device=dev)
+        self.items = []
+        for (name, alg, n, kw), (P, U, T) in zip(BATCH_PARTS, self.parts):
+            self.items.append(dict(rhs=name, params=t(P), u0=t(U), tspan=t(T), alg=alg,
+                                   **kw))
+        self.plan = ens.EnsembleBatch(self.items, graph=True, autotune=True)
+        self.launches_per_step = sum(
+            1 + (3 if a == "tsit5" or a == "ros23" else 0) for _, a, _, _ in BATCH_PARTS)
+
+    def step(self):
+        self.plan.run()
+
+    def compare(self, steps):
+        """Device time per batch of the same items (a) as separate launches one after another
+        on one stream, (b) as one graph launch, both with the tuned shapes."""
+        import torch
+
+        import paper_2304_06835_gb300 as ens
+        serial = ens.EnsembleBatch(self.items, graph=False, serial=True)
+        res = {}
+        for name, plan in (("separate_launches_ms", serial), ("graph_ms", self.plan)):
+            plan.run()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(steps):
+                plan.run()
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / steps
+        serial.close()
+        res["items_alone_ms"] = [round(i["tuned_ms"], 4) for i in self.plan.info()]
+        res["launch_shapes"] = [(i["block"], i["tpt"]) for i in self.plan.info()]
+        return res
+
+    def work(self):
+        ops, att, ok = 0, [], 0
+        for (name, alg, n, kw), (o, st, stats) in zip(BATCH_PARTS, self.plan.outputs):
+            sts = stats.cpu().numpy().astype(np.int64)
+            a = int(sts[0].sum() + sts[1].sum())
+            att.append(a)
+            ops += a * OPS_PER_ATTEMPT[alg]
+            ok += int((st.cpu().numpy() == 0).sum())
+        return ops, {"attempts_per_launch": att,
+                     "ops_per_attempt": [OPS_PER_ATTEMPT[a] for _, a, _, _ in BATCH_PARTS],
+                     "trajectories_ok": ok, **self.compare(10)}
+
+    def e2e(self, stream):
+        """Trajectories/s with host inputs: pinned inputs of all three parts copied in, one
+        graph launch, final states and status copied back, inside the timed region."""
+        import torch
+        pins = []
+        for (P, U, T), it in zip(self.parts, self.items):
+            pins.append([(torch.from_numpy(np.ascontiguousarray(a.T, dtype=np.float32))
+                          .pin_memory(), it[k]) for a, k in ((P, "params"), (U, "u0"),
+                                                             (T, "tspan"))])
+        outs = [(torch.empty_like(o, device="cpu").pin_memory(),
+                 torch.empty_like(st, device="cpu").pin_memory(), o, st)
+                for o, st, _ in self.plan.outputs]
+        h2d = sum(h.numel() * 4 for p in pins for h, _ in p)
+        d2h = sum(ho.numel() * 4 + hs.numel() for ho, hs, _, _ in outs)
+
+        def host_step():
+            for p in pins:
+                for h, d in p:
+                    d.copy_(h, non_blocking=True)
+            self.plan.run()
+            for ho, hs, o, st in outs:
+                ho.copy_(o, non_blocking=True)
+                hs.copy_(st, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        host_step()
+        steps = max(3, min(self.args.steps, 20))
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            host_step()
+        el = (time.perf_counter() - t0) / steps
+        return {"value": self.w["N"] / el, "unit": "trajectories/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (0: workload default)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="lorenz_adaptive_f32", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -229,6 +497,8 @@ def main():
     w = dict(WORKLOADS[args.workload])
     if args.n:
         w["N"] = args.n
+    if args.steps <= 0:
+        args.steps = w["steps"]
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -242,32 +512,17 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    import paper_2304_06835_gb300 as ens
     from paper_2304_06835_gb300 import _lib
 
-    dt_t = torch.float32 if w["dtype"] == "f32" else torch.float64
-    P, U, T = inputs_for(w, rank)
-    N = w["N"]
     dev = torch.device("cuda", local)
-    Pd = torch.tensor(P.T.copy(), dtype=dt_t, device=dev)
-    Ud = torch.tensor(U.T.copy(), dtype=dt_t, device=dev)
-    Td = torch.tensor(T.T.copy(), dtype=dt_t, device=dev)
-    D = U.shape[1]
-    out = torch.empty((D, N), dtype=dt_t, device=dev)
-    status = torch.empty(N, dtype=torch.int8, device=dev)
-    stats = torch.empty((3, N), dtype=torch.int32, device=dev)
+    runner = {"adjoint": AdjointRunner, "batch": BatchRunner,
+              "solve": SolveRunner}[w["kind"]](args, w, rank, dev)
+    N = w["N"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
-    solver = ens.EnsembleSolver(w["rhs"])
-    kw = solve_kwargs(w)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        solver.solve(Pd, Ud, Td, alg=w["alg"], layout="soa", out=out, status=status, stats=stats,
-                     schedule=args.schedule, block=args.block, tpt=args.tpt,
-                     refill_min=args.refill, order=args.order, want_stats=True, **kw)
-
     for _ in range(max(3, args.warmup)):
-        step()
+        runner.step()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -277,9 +532,9 @@ def main():
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for i in range(args.steps):
-        flush.fill_(i & 0xFF)  # L2 flush between timed solves (outside the events)
+        flush.fill_(i & 0xFF)  # L2 flush between timed steps (outside the events)
         ev[i][0].record(stream)
-        step()
+        runner.step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -294,42 +549,35 @@ def main():
         tot_s = float(t.item())
     value = N * world * args.steps / tot_s
 
-    st = stats.cpu().numpy().astype(np.int64)
-    attempts = int(st[0].sum() + st[1].sum())
-    ok = int((status.cpu().numpy() == 0).sum())
-    ops = attempts * OPS_PER_ATTEMPT[w["alg"]]
+    ops, extra = runner.work()
     launch_s = tot_s / args.steps
     achieved = ops / launch_s / 1e12
-    peak_max = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    lanes = FP32_LANES if w["dtype"] == "f32" else FP64_LANES
+    peak_max = SMS * lanes * SM_MAX_MHZ * 1e6 / 1e12
     sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
-    peak_clk = SMS * FP32_LANES * sm_mhz * 1e6 / 1e12
-    bound = "alu"
+    peak_clk = SMS * lanes * sm_mhz * 1e6 / 1e12
+    pipe = "FP32" if w["dtype"] == "f32" else "FP64"
 
-    # e2e: the same solve through the C ABI with host buffers (copies inside the timed region)
-    e2e = None
-    if not args.no_e2e:
-        e2e = e2e_rate(args, w, P, U, T, solver, stream, kw)
+    e2e = None if args.no_e2e else runner.e2e(stream)
+    cfg = {"workload": args.workload, "model": w["rhs"], "alg": w["alg"], "N": N,
+           "tspan": [0.0, w["t1"]], **{k: w[k] for k in ("tol", "dt", "dt0", "every") if k in w},
+           "layout": "soa", "l2": "flushed between steps (256 MB write outside events)",
+           "parallelism": "dp%d" % world}
+    if w["kind"] == "solve":
+        cfg.update({"block": args.block, "tpt": args.tpt, "schedule": args.schedule,
+                    "refill_min": args.refill, "order": args.order})
     line = {
         "metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * launch_s,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"],
-        "data": "synthetic",
-        "config": {"workload": args.workload, "model": w["rhs"], "alg": w["alg"], "N": N,
-                   "tspan": [0.0, w["t1"]], **{k: w[k] for k in ("tol", "dt", "dt0") if k in w},
-                   "layout": "soa", "l2": "flushed between steps (256 MB write outside events)",
-                   "parallelism": "dp%d" % world, "block": args.block, "tpt": args.tpt,
-                   "schedule": args.schedule, "refill_min": args.refill,
-                   "order": args.order},
-        "wall_s": wall,
-        "roofline": {"bound": bound, "achieved": achieved, "peak": peak_max,
-                     "unit": "T FP32-FMA-pipe instr/s", "frac": achieved / peak_max,
+        "data": "synthetic", "config": cfg, "wall_s": wall,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_max,
+                     "unit": "T %s-FMA-pipe instr/s" % pipe, "frac": achieved / peak_max,
                      "frac_at_sampled_clock": achieved / peak_clk, "traffic": None,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (derived)",
-                     "ops_per_attempt": OPS_PER_ATTEMPT[w["alg"]],
-                     "attempts_per_launch": attempts},
+                     "peak_basis": "152 SMs x %d %s lanes x 2070 MHz (derived)" % (lanes, pipe),
+                     **extra},
         "clocks": clocks,
-        "gpu_launches": args.steps,
-        "trajectories_ok": ok,
+        "gpu_launches": args.steps * runner.launches_per_step,
         "e2e": e2e,
     }
     if args.probe:
@@ -339,11 +587,10 @@ def main():
             iters = 20000 if code == _lib.F32 else 400
             _lib.check(_lib.lib().ens_probe_fma(code, iters, SMS * 8, 256, C.byref(r), None))
             line.setdefault("probe", {})[dt_name + "_fma_per_s"] = r.value
-    if rank == 0 and not args.no_cpu_baseline:
-        rate, n, nt, el = oracle_rate(w)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sample, nt = oracle_rate(w)
         line["cpu_baseline"] = {"value": rate, "unit": "trajectories/s", "cores": nt,
-                                "kind": "oracle",
-                                "sample": "first %d of the %d trajectories (%.1f s)" % (n, N, el)}
+                                "kind": "oracle", "sample": sample}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:

@@ -140,6 +140,102 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
                    const void* tspan, const ens_opts* opts, void* out, signed char* status,
                    int* stats, void* cuda_stream);
 
+/* Launch-shape autotuner (the occupancy tuning the paper leaves to KernelAbstractions,
+ * Sec. 5.1): runs the solve of ens_solve (same arguments, outputs really written) with every
+ * candidate launch shape -- block in {64, 128, 256, 512}, and for the persistent schedule
+ * trajectories per thread in {1, 2}; a nonzero opts->block / opts->tpt pins that value --
+ * timing each (one warm-up, best of two), and records the fastest in a process-wide cache
+ * keyed by (model, algorithm, dtype, layout, floor(log2 N), saveat or not, SM count).  Later
+ * ens_solve / ens_batch_create calls with block = tpt = 0 use the cached shape.  Returns it in
+ * *block / *tpt and its time in *best_ms.  Synchronises the stream. */
+int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
+                 const void* tspan, const ens_opts* opts, void* out, signed char* status,
+                 int* stats, void* cuda_stream, int* block, int* tpt, float* best_ms);
+
+/* Batched ensembles: several sub-problems (different models, methods, sizes and time spans)
+ * solved by one call -- the uneven-work case of Sec. 6.4 (trajectories whose step counts
+ * differ) widened to mixed stiff / non-stiff / stochastic work.  A plan validates the items,
+ * optionally autotunes each one, allocates its scratch and, with ENS_BATCH_GRAPH, captures the
+ * whole batch into one CUDA graph: the items run as concurrent persistent (or direct) kernels
+ * on forked streams, longest measured item first, joined back onto the caller's stream.
+ * Flags:
+ *   ENS_BATCH_GRAPH     capture into a CUDA graph; ens_batch_run is one graph launch
+ *   ENS_BATCH_AUTOTUNE  run ens_autotune's search on every item during creation (the items'
+ *                       outputs are written by the trial solves)
+ *   ENS_BATCH_SERIAL    no concurrency: the items run one after another on the caller stream
+ * Each item's opts are those of ens_solve; saveat is copied at creation.  The plan keeps the
+ * item pointers: ens_batch_run re-solves whatever the input arrays hold at that time. */
+#define ENS_BATCH_MAX_ITEMS 16
+enum { ENS_BATCH_GRAPH = 1, ENS_BATCH_AUTOTUNE = 2, ENS_BATCH_SERIAL = 4 };
+
+typedef struct {
+  int rhs_id;               /* ENS_RHS_* */
+  long long N;
+  const void* params;       /* device arrays as for ens_solve */
+  const void* u0;
+  const void* tspan;
+  void* out;
+  signed char* status;      /* or NULL */
+  int* stats;               /* or NULL */
+  ens_opts opts;
+} ens_batch_item;
+
+typedef struct {
+  int schedule, block, tpt; /* launch shape the plan uses */
+  float tuned_ms;           /* autotuned solve time of the item alone (0 if not tuned) */
+  int launch_position;      /* position in the launch order (-1: empty item) */
+  int graph;                /* 1 if the plan runs as a CUDA graph */
+} ens_batch_item_info;
+
+typedef struct ens_batch ens_batch;
+
+/* Create a plan (may synchronise cuda_stream: autotuning and graph capture do). */
+int ens_batch_create(ens_batch** b, const ens_batch_item* items, int n_items, int flags,
+                     void* cuda_stream);
+/* Solve every item (asynchronous on cuda_stream). */
+int ens_batch_run(ens_batch* b, void* cuda_stream);
+int ens_batch_info(const ens_batch* b, int item, ens_batch_item_info* info);
+/* Waits for the device, then frees the plan. */
+int ens_batch_destroy(ens_batch* b);
+
+/* Discrete adjoint of a fixed-step explicit Runge-Kutta solve (TSIT5_FIXED or RK4).
+ * The paper differentiates through its solvers with automatic differentiation (Sec. 6.5);
+ * here the reverse mode of the step map of Sec. 3.1 (U_i = u_n + h sum_j a_ij k_j,
+ * k_i = f(U_i, p), u_{n+1} = u_n + h sum_i b_i k_i) is written out: per step, with
+ * lambda = dL/du_{n+1}, the stage adjoints kbar_i = h b_i lambda + h sum_{l>i} a_li Ubar_l,
+ * Ubar_i = f_u(U_i)^T kbar_i, dL/dp += f_p(U_i)^T kbar_i, dL/du_n = lambda + sum_i Ubar_i.
+ * The result is the exact gradient of the discrete map (not of the ODE), up to rounding.
+ *
+ * Checkpointing: u is stored every `checkpoint_every` = K steps; the reverse pass replays
+ * each K-step segment from its checkpoint, storing the stage inputs, then transposes it.
+ *   max_steps  : upper bound on any trajectory's step count n = ceil((tf - t0)/dt - 1e-12).
+ *                Trajectories with more steps get status MAXITERS, NaN state and gradients.
+ *   ckpt       : device array of ens_adjoint_ckpt_elems(N, D, max_steps, K) elements of
+ *                opts->dtype, laid out [C][D][N], C = ceil(max_steps / K).
+ * Options used: alg, dtype, layout, dt (others ignored).  Arrays follow opts->layout like
+ * ens_solve: params [N][P], u0 [N][D], tspan [N][2], out / grad_out / grad_u0 [N][D],
+ * grad_p [N][P] (ROWMAJOR) or their transposes (SOA).  Asynchronous on cuda_stream.
+ * Errors: ENS_EINVAL for another algorithm, dt <= 0, max_steps < 1, K < 1, null arrays;
+ * ENS_ENOMEM when the handle's scratch cannot be allocated. */
+
+/* Elements of the checkpoint array (C * D * N), or -1 for invalid arguments. */
+long long ens_adjoint_ckpt_elems(long long N, int D, long long max_steps, int checkpoint_every);
+
+/* Forward pass with checkpoints: writes out = u(tf) (or skips it if out is NULL), ckpt, and
+ * status (OK or MAXITERS; NULL allowed). */
+int ens_adjoint_forward(ens_handle* h, long long N, const void* params, const void* u0,
+                        const void* tspan, const ens_opts* opts, long long max_steps,
+                        int checkpoint_every, void* out, void* ckpt, signed char* status,
+                        void* cuda_stream);
+
+/* Reverse pass: grad_out = dL/du(tf) in; grad_p = dL/dp and grad_u0 = dL/du0 out.  ckpt is
+ * the array written by ens_adjoint_forward with the same arguments, or NULL, in which case
+ * the forward pass runs first into handle-owned scratch.  The handle also owns the segment
+ * buffer of K * S * D * N elements (S = 6 stages for TSIT5_FIXED, 4 for RK4). */
+int ens_adjoint(ens_handle* h, long long N, const void* params, const void* u0, const void* tspan,
+                const ens_opts* opts, long long max_steps, int checkpoint_every, const void* ckpt,
+                const void* grad_out, void* grad_p, void* grad_u0, void* cuda_stream);
+
 /* Raw Philox4x32-10 words (Salmon et al. SC'11) of the SDE streams: for trajectory
  * j < n_traj and call c < n_calls, out[(c*4 + w)*n_traj + j] = word w of
  * Philox(counter = (c lo, c hi, (index_offset+j) lo, hi), key = (seed lo, seed hi)).

@@ -4,8 +4,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / r
 may import this package.  The product package never imports it and shares no code with it.
 
 The arithmetic lives in ``ens_oracle.cpp`` (plain C++, FP64, with an FP32 mode), built on demand
-into ``liboracle.so`` next to this file; ``mlp.py`` holds the NumPy oracle of the surrogate
-network.  This module only marshals NumPy arrays into the C functions.
+into ``liboracle.so`` next to this file.  This module only marshals NumPy arrays into the C
+functions.
 
 Identifiers (the same numbers as the public C-ABI, by documentation):
   rhs:  1 Lorenz (D=3, P=3: sigma, rho, beta), 2 Robertson (D=3, P=3: k1, k2, k3),
@@ -74,6 +74,9 @@ def lib():
             L.oracle_tsit5_fixed_grad.restype = ctypes.c_int
             L.oracle_tsit5_fixed_grad.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, dp,
                                                   ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
+            L.oracle_fixed_grad.restype = ctypes.c_int
+            L.oracle_fixed_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, dp, dp,
+                                            dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
             _lib = L
     return _lib
 
@@ -195,7 +198,14 @@ def tsit5_fixed_grad(rhs, params, u0, tspan, dt, grad_out, nthreads=None):
     """Exact gradient of the fixed-step Tsit5 map by forward tangents.
 
     Returns (grad_p [N,P], grad_u0 [N,D], u_final [N,D])."""
+    return fixed_grad(rhs, "tsit5_fixed", params, u0, tspan, dt, grad_out, nthreads)
+
+
+def fixed_grad(rhs, alg, params, u0, tspan, dt, grad_out, nthreads=None):
+    """Exact gradient of a fixed-step explicit RK map ("tsit5_fixed" or "rk4") by forward
+    tangents: grad_out [N,D] = dL/du(tf).  Returns (grad_p [N,P], grad_u0 [N,D], u_final [N,D])."""
     rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    alg_id = ALG[alg] if isinstance(alg, str) else int(alg)
     D, P = DIMS[rhs_id]
     params = _f64(params).reshape(-1, P)
     N = params.shape[0]
@@ -206,8 +216,8 @@ def tsit5_fixed_grad(rhs, params, u0, tspan, dt, grad_out, nthreads=None):
     gu = np.empty((N, D))
     uf = np.empty((N, D))
     nt = default_threads() if nthreads is None else int(nthreads)
-    rc = lib().oracle_tsit5_fixed_grad(rhs_id, N, _dp(params), _dp(u0), _dp(tspan), float(dt),
-                                       _dp(go), _dp(gp), _dp(gu), _dp(uf), nt)
+    rc = lib().oracle_fixed_grad(rhs_id, alg_id, N, _dp(params), _dp(u0), _dp(tspan), float(dt),
+                                 _dp(go), _dp(gp), _dp(gu), _dp(uf), nt)
     if rc != 0:
         raise ValueError("bad arguments")
     return gp, gu, uf

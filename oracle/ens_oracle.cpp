@@ -742,14 +742,41 @@ void oracle_normals(unsigned long long seed, unsigned long long traj, long long 
   for (long long k = 0; k < n; ++k) out[k] = normal_draw(seed, traj, uint64_t(k), fp64 != 0);
 }
 
-// Exact gradient of the discrete fixed-step Tsit5 map (FP64) by forward-mode tangents.
+// Classic RK4 as an explicit tableau (used by the tangent gradient below; the forward solver
+// above steps RK4 with the textbook formula).
+const double RK4_C[4] = {0.0, 0.5, 0.5, 1.0};
+const double RK4_A[4][4] = {{0, 0, 0, 0}, {0.5, 0, 0, 0}, {0, 0.5, 0, 0}, {0, 0, 1.0, 0}};
+const double RK4_B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+
+// Exact gradient of a discrete fixed-step explicit Runge-Kutta map (FP64) by forward-mode
+// tangents: alg 1 = Tsit5 (7-stage tableau, b_7 = 0), alg 3 = RK4.
 // For each trajectory i: g_p[i][m] = sum_k grad_out[i][k] d u_k(tf) / d p_m,
 // g_u0[i][j] = sum_k grad_out[i][k] d u_k(tf) / d u0_j.  Row-major arrays.
-// Tangent recursion (chain rule through every stage): dU_i = du + h sum_j a_ij dk_j,
-// dk_i = f_u(U_i) dU_i + f_p(U_i) dtheta.
-int oracle_tsit5_fixed_grad(int rhs_id, long long N, const double* params, const double* u0,
-                            const double* tspan, double dt, const double* grad_out,
-                            double* g_p, double* g_u0, double* u_final, int nthreads) {
+// Tangent recursion (chain rule through every stage, Sec. 3.1 stage equations):
+// dU_i = du + h sum_j a_ij dk_j,  dk_i = f_u(U_i) dU_i + f_p(U_i) dtheta,
+// du_{n+1} = du_n + h sum_i b_i dk_i.
+int oracle_fixed_grad(int rhs_id, int alg_id, long long N, const double* params,
+                      const double* u0, const double* tspan, double dt, const double* grad_out,
+                      double* g_p, double* g_u0, double* u_final, int nthreads) {
+  int S = 0;
+  const double* TC = nullptr;
+  const double* TB = nullptr;
+  double TA[7][7] = {};
+  if (alg_id == ALG_TSIT5_FIXED) {
+    S = 7;
+    TC = TS_C;
+    TB = TS_B;
+    for (int r = 0; r < 7; ++r)
+      for (int q = 0; q < 7; ++q) TA[r][q] = TS_A[r][q];
+  } else if (alg_id == ALG_RK4) {
+    S = 4;
+    TC = RK4_C;
+    TB = RK4_B;
+    for (int r = 0; r < 4; ++r)
+      for (int q = 0; q < 4; ++q) TA[r][q] = RK4_A[r][q];
+  } else {
+    return -1;
+  }
   Model m = model_of(rhs_id);
   if (m.D == 0) return -1;
   const int D = m.D, P = m.P, M = m.P + m.D;
@@ -767,20 +794,20 @@ int oracle_tsit5_fixed_grad(int rhs_id, long long N, const double* params, const
         const double h = (s == n - 1) ? h_last : dt;
         const double t = t0 + double(s) * dt;
         double k[7][8], dk[7][8][16], U[8], dU[8][16], Ju[64], Jp[64];
-        for (int st = 0; st < 7; ++st) {
+        for (int st = 0; st < S; ++st) {
           for (int j = 0; j < D; ++j) {
             double acc = 0;
-            for (int q = 0; q < st; ++q) acc += TS_A[st][q] * k[q][j];
+            for (int q = 0; q < st; ++q) acc += TA[st][q] * k[q][j];
             U[j] = u[j] + h * acc;
             for (int mm = 0; mm < M; ++mm) {
               double dacc = 0;
-              for (int q = 0; q < st; ++q) dacc += TS_A[st][q] * dk[q][j][mm];
+              for (int q = 0; q < st; ++q) dacc += TA[st][q] * dk[q][j][mm];
               dU[j][mm] = du[j][mm] + h * dacc;
             }
           }
-          rhs<double>(rhs_id, U, p, t + TS_C[st] * h, k[st]);
-          jac_u<double>(rhs_id, U, p, t + TS_C[st] * h, Ju);
-          jac_p<double>(rhs_id, U, p, t + TS_C[st] * h, Jp);
+          rhs<double>(rhs_id, U, p, t + TC[st] * h, k[st]);
+          jac_u<double>(rhs_id, U, p, t + TC[st] * h, Ju);
+          jac_p<double>(rhs_id, U, p, t + TC[st] * h, Jp);
           for (int j = 0; j < D; ++j)
             for (int mm = 0; mm < M; ++mm) {
               double v = (mm < P) ? Jp[j * P + mm] : 0.0;
@@ -790,11 +817,11 @@ int oracle_tsit5_fixed_grad(int rhs_id, long long N, const double* params, const
         }
         for (int j = 0; j < D; ++j) {
           double acc = 0;
-          for (int q = 0; q < 7; ++q) acc += TS_B[q] * k[q][j];
+          for (int q = 0; q < S; ++q) acc += TB[q] * k[q][j];
           double unew = u[j] + h * acc;
           for (int mm = 0; mm < M; ++mm) {
             double dacc = 0;
-            for (int q = 0; q < 7; ++q) dacc += TS_B[q] * dk[q][j][mm];
+            for (int q = 0; q < S; ++q) dacc += TB[q] * dk[q][j][mm];
             du[j][mm] = du[j][mm] + h * dacc;
           }
           u[j] = unew;
@@ -811,6 +838,13 @@ int oracle_tsit5_fixed_grad(int rhs_id, long long N, const double* params, const
     }
   });
   return 0;
+}
+
+int oracle_tsit5_fixed_grad(int rhs_id, long long N, const double* params, const double* u0,
+                            const double* tspan, double dt, const double* grad_out,
+                            double* g_p, double* g_u0, double* u_final, int nthreads) {
+  return oracle_fixed_grad(rhs_id, ALG_TSIT5_FIXED, N, params, u0, tspan, dt, grad_out, g_p,
+                           g_u0, u_final, nthreads);
 }
 
 }  // extern "C"

@@ -36,6 +36,25 @@ class EnsOpts(ctypes.Structure):
     ]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [
+        ("rhs_id", ctypes.c_int), ("N", ctypes.c_longlong), ("params", ctypes.c_void_p),
+        ("u0", ctypes.c_void_p), ("tspan", ctypes.c_void_p), ("out", ctypes.c_void_p),
+        ("status", ctypes.c_void_p), ("stats", ctypes.c_void_p), ("opts", EnsOpts),
+    ]
+
+
+class BatchItemInfo(ctypes.Structure):
+    _fields_ = [
+        ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
+        ("tuned_ms", ctypes.c_float), ("launch_position", ctypes.c_int), ("graph", ctypes.c_int),
+    ]
+
+
+BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_SERIAL = 1, 2, 4
+BATCH_MAX_ITEMS = 16
+
+
 class EnsError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("ens error %d: %s" % (code, msg))
@@ -61,6 +80,18 @@ SIGNATURES = {
     "ens_normals": (_INT, [_ULL, _LL, _LL, _LL, _INT, _VP, _VP]),
     "ens_solve_noalloc": (_INT, [_INT, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP,
                                  _VP]),
+    "ens_autotune": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP, _VP,
+                            ctypes.POINTER(_INT), ctypes.POINTER(_INT),
+                            ctypes.POINTER(ctypes.c_float)]),
+    "ens_batch_create": (_INT, [ctypes.POINTER(_VP), ctypes.POINTER(BatchItem), _INT, _INT, _VP]),
+    "ens_batch_run": (_INT, [_VP, _VP]),
+    "ens_batch_info": (_INT, [_VP, _INT, ctypes.POINTER(BatchItemInfo)]),
+    "ens_batch_destroy": (_INT, [_VP]),
+    "ens_adjoint_ckpt_elems": (_LL, [_LL, _INT, _LL, _INT]),
+    "ens_adjoint_forward": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _LL, _INT,
+                                   _VP, _VP, _VP, _VP]),
+    "ens_adjoint": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _LL, _INT, _VP, _VP,
+                           _VP, _VP, _VP]),
     "ens_probe_fma": (_INT, [_INT, _LL, _INT, _INT, ctypes.POINTER(ctypes.c_double), _VP]),
     "ens_last_error": (ctypes.c_char_p, []),
 }

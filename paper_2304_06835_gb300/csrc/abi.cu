@@ -212,6 +212,11 @@ struct ens_handle {
   // staging for ens_solve_host
   void* stage;
   size_t stage_bytes;
+  // discrete adjoint: one segment of stage inputs, and checkpoints when the caller gives none
+  void* adj_seg;
+  size_t adj_seg_bytes;
+  void* adj_ckpt;
+  size_t adj_ckpt_bytes;
   std::mutex mu;
 };
 
@@ -238,16 +243,15 @@ bool model_dims(int rhs_id, int* D, int* P) {
 
 bool is_fixed(int alg) { return alg == ENS_TSIT5_FIXED || alg == ENS_RK4 || alg == ENS_EM; }
 
-int validate(const ens_handle* h, long long N, const void* params, const void* u0,
-             const void* tspan, const ens_opts* o, const void* out) {
-  if (!h) return fail(ENS_EINVAL, "null handle");
+int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
+                  const void* tspan, const ens_opts* o, const void* out) {
   if (!o) return fail(ENS_EINVAL, "null options");
   if (N < 0) return fail(ENS_EINVAL, "N < 0");
   if (o->alg < ENS_TSIT5_FIXED || o->alg > ENS_EM) return fail(ENS_EINVAL, "unknown algorithm");
   if (o->dtype != ENS_F32 && o->dtype != ENS_F64) return fail(ENS_EINVAL, "unknown dtype");
   if (o->layout != ENS_LAYOUT_ROWMAJOR && o->layout != ENS_LAYOUT_SOA)
     return fail(ENS_EINVAL, "unknown layout");
-  if (o->alg == ENS_EM && h->rhs_id != ENS_RHS_GBM)
+  if (o->alg == ENS_EM && rhs_id != ENS_RHS_GBM)
     return fail(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM)");
   if (is_fixed(o->alg) && !(o->dt > 0) ) return fail(ENS_EINVAL, "fixed-step methods need dt > 0");
   if (is_fixed(o->alg) && !std::isfinite(o->dt)) return fail(ENS_EINVAL, "dt not finite");
@@ -283,6 +287,12 @@ int validate(const ens_handle* h, long long N, const void* params, const void* u
   return ENS_OK;
 }
 
+int validate(const ens_handle* h, long long N, const void* params, const void* u0,
+             const void* tspan, const ens_opts* o, const void* out) {
+  if (!h) return fail(ENS_EINVAL, "null handle");
+  return validate_opts(h->rhs_id, N, params, u0, tspan, o, out);
+}
+
 void fill_args(SolveArgs* a, long long N, const void* params, const void* u0, const void* tspan,
                const ens_opts* o, void* out, signed char* status, int* stats,
                unsigned long long* queue) {
@@ -312,24 +322,102 @@ void fill_args(SolveArgs* a, long long N, const void* params, const void* u0, co
   for (int i = 0; i < o->n_save; ++i) a->saveat[i] = o->saveat[i];
 }
 
-LaunchCfg resolve_cfg(const ens_handle* h, const ens_opts* o) {
-  LaunchCfg c;
-  c.schedule = o->schedule;
-  if (c.schedule == ENS_SCHED_AUTO)
-    c.schedule = is_fixed(o->alg) ? ENS_SCHED_DIRECT : ENS_SCHED_PERSISTENT;
-  c.block = o->block ? o->block : 128;
-  c.tpt = o->tpt ? o->tpt : 1;
-  c.num_sms = h->num_sms;
-  return c;
+LaunchCfg resolve_cfg(const ens_handle* h, long long N, const ens_opts* o) {
+  return resolve_launch(h->rhs_id, N, o, h->num_sms);
 }
 
 size_t elem_size(int dtype) { return dtype == ENS_F32 ? 4 : 8; }
+
+// grow a handle-owned device buffer to at least `bytes`
+bool grow(void** buf, size_t* cap, size_t bytes) {
+  if (bytes <= *cap) return true;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (cudaMalloc(buf, bytes) != cudaSuccess) {
+    *buf = nullptr;
+    return false;
+  }
+  *cap = bytes;
+  return true;
+}
+
+int validate_adjoint(const ens_handle* h, long long N, const void* params, const void* u0,
+                     const void* tspan, const ens_opts* o, long long max_steps, int every) {
+  if (!h) return fail(ENS_EINVAL, "null handle");
+  if (!o) return fail(ENS_EINVAL, "null options");
+  if (N < 0) return fail(ENS_EINVAL, "N < 0");
+  if (o->alg != ENS_TSIT5_FIXED && o->alg != ENS_RK4)
+    return fail(ENS_EINVAL, "the adjoint needs a fixed-step explicit method (TSIT5_FIXED or RK4)");
+  if (o->dtype != ENS_F32 && o->dtype != ENS_F64) return fail(ENS_EINVAL, "unknown dtype");
+  if (o->layout != ENS_LAYOUT_ROWMAJOR && o->layout != ENS_LAYOUT_SOA)
+    return fail(ENS_EINVAL, "unknown layout");
+  if (!(o->dt > 0) || !std::isfinite(o->dt)) return fail(ENS_EINVAL, "dt must be finite and > 0");
+  if (max_steps < 1 || max_steps > (1LL << 40)) return fail(ENS_EINVAL, "max_steps out of range");
+  if (every < 1 || every > (1 << 20)) return fail(ENS_EINVAL, "checkpoint_every out of range");
+  if (N > 0 && (!params || !u0 || !tspan)) return fail(ENS_EINVAL, "null array");
+  return ENS_OK;
+}
+
+AdjArgs adj_args(const ens_handle* h, long long N, const void* params, const void* u0,
+                 const void* tspan, const ens_opts* o, long long max_steps, int every) {
+  AdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.N = N;
+  a.params = params;
+  a.u0 = u0;
+  a.tspan = tspan;
+  a.layout = o->layout;
+  a.dt = o->dt;
+  a.max_steps = max_steps;
+  a.K = every;
+  (void)h;
+  return a;
+}
+
+long long ckpt_slots(long long max_steps, int every) { return (max_steps + every - 1) / every; }
 
 }  // namespace
 
 namespace ens {
 // Record an error for ens_last_error() from another translation unit of the library.
 int set_last_error(int code, const char* msg) { return fail(code, msg); }
+
+int validate_problem(int rhs_id, long long N, const void* params, const void* u0,
+                     const void* tspan, const ens_opts* o, const void* out) {
+  int D, P;
+  if (!model_dims(rhs_id, &D, &P)) return fail(ENS_EINVAL, "unknown rhs_id");
+  return validate_opts(rhs_id, N, params, u0, tspan, o, out);
+}
+
+void fill_solve_args(SolveArgs* a, long long N, const void* params, const void* u0,
+                     const void* tspan, const ens_opts* o, void* out, signed char* status,
+                     int* stats) {
+  fill_args(a, N, params, u0, tspan, o, out, status, stats, nullptr);
+}
+
+bool uses_cost_order(const ens_opts* o, const LaunchCfg& cfg) {
+  return cfg.schedule == ENS_SCHED_PERSISTENT &&
+         (o->order == ENS_ORDER_COST || (o->order == ENS_ORDER_AUTO && !is_fixed(o->alg)));
+}
+
+cudaError_t enqueue_solve(int rhs_id, const ens_opts* o, SolveArgs a, const LaunchCfg& cfg,
+                          const SolveScratch& sc, cudaStream_t s, bool* supported) {
+  *supported = true;
+  a.queue = sc.queue;
+  a.order = nullptr;
+  if (cfg.schedule == ENS_SCHED_PERSISTENT) {
+    if (uses_cost_order(o, cfg) && a.N <= 0x7fffffffLL && sc.order) {
+      cudaError_t e = launch_cost_order(rhs_id, o->alg, o->dtype, a, sc.bucket, sc.hist,
+                                        sc.order, s);
+      if (e != cudaSuccess) return e;
+      a.order = sc.order;
+    }
+    cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_solve(rhs_id, o->alg, o->dtype, a, cfg, s, supported);
+}
 }  // namespace ens
 
 extern "C" {
@@ -364,6 +452,10 @@ int ens_create(ens_handle** out, int rhs_id, int D, int P) {
   h->bucket = nullptr;
   h->hist = nullptr;
   h->order_cap = 0;
+  h->adj_seg = nullptr;
+  h->adj_seg_bytes = 0;
+  h->adj_ckpt = nullptr;
+  h->adj_ckpt_bytes = 0;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -385,6 +477,8 @@ int ens_destroy(ens_handle* h) {
   if (h->order) cudaFree(h->order);
   if (h->bucket) cudaFree(h->bucket);
   if (h->stage) cudaFree(h->stage);
+  if (h->adj_seg) cudaFree(h->adj_seg);
+  if (h->adj_ckpt) cudaFree(h->adj_ckpt);
   delete h;
   return ENS_OK;
 }
@@ -395,36 +489,59 @@ int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, co
   if (rc) return rc;
   if (N == 0) return ENS_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  LaunchCfg cfg = resolve_cfg(h, o);
+  LaunchCfg cfg = resolve_cfg(h, N, o);
   SolveArgs a;
   fill_args(&a, N, params, u0, tspan, o, out, status, stats, h->queue);
-  if (cfg.schedule == ENS_SCHED_PERSISTENT) {
-    const bool cost = o->order == ENS_ORDER_COST ||
-                      (o->order == ENS_ORDER_AUTO && !is_fixed(o->alg));
-    if (cost && N <= 0x7fffffffLL) {
-      if (N > h->order_cap) {
-        cudaFree(h->order);
-        cudaFree(h->bucket);
-        h->order = nullptr;
-        h->bucket = nullptr;
-        h->order_cap = 0;
-        cudaError_t e1 = cudaMalloc(&h->order, sizeof(int) * N);
-        cudaError_t e2 = cudaMalloc(&h->bucket, sizeof(unsigned short) * N);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ENS_ENOMEM, "order scratch");
-        h->order_cap = N;
-      }
-      cudaError_t e = launch_cost_order(h->rhs_id, o->alg, o->dtype, a, h->bucket, h->hist,
-                                        h->order, s);
-      if (e != cudaSuccess) return cuda_fail(e, "cost ordering");
-      a.order = h->order;
+  SolveScratch sc{h->queue, nullptr, nullptr, h->hist};
+  if (uses_cost_order(o, cfg) && N <= 0x7fffffffLL) {
+    if (N > h->order_cap) {
+      cudaFree(h->order);
+      cudaFree(h->bucket);
+      h->order = nullptr;
+      h->bucket = nullptr;
+      h->order_cap = 0;
+      cudaError_t e1 = cudaMalloc(&h->order, sizeof(int) * N);
+      cudaError_t e2 = cudaMalloc(&h->bucket, sizeof(unsigned short) * N);
+      if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ENS_ENOMEM, "order scratch");
+      h->order_cap = N;
     }
-    cudaError_t e = cudaMemsetAsync(h->queue, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    sc.order = h->order;
+    sc.bucket = h->bucket;
   }
   bool sup = false;
-  cudaError_t e = launch_solve(h->rhs_id, o->alg, o->dtype, a, cfg, s, &sup);
+  cudaError_t e = enqueue_solve(h->rhs_id, o, a, cfg, sc, s, &sup);
   if (!sup) return fail(ENS_ENOTSUP, "algorithm not available for this model");
   if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+  return ENS_OK;
+}
+
+int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
+                 const void* tspan, const ens_opts* o, void* out, signed char* status,
+                 int* stats, void* stream, int* block, int* tpt, float* best_ms) {
+  int rc = validate(h, N, params, u0, tspan, o, out);
+  if (rc) return rc;
+  if (!block || !tpt || !best_ms) return fail(ENS_EINVAL, "null result pointer");
+  if (N == 0) return fail(ENS_EINVAL, "nothing to tune (N = 0)");
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (N <= 0x7fffffffLL && N > h->order_cap) {
+    cudaFree(h->order);
+    cudaFree(h->bucket);
+    h->order = nullptr;
+    h->bucket = nullptr;
+    h->order_cap = 0;
+    cudaError_t e1 = cudaMalloc(&h->order, sizeof(int) * N);
+    cudaError_t e2 = cudaMalloc(&h->bucket, sizeof(unsigned short) * N);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ENS_ENOMEM, "order scratch");
+    h->order_cap = N;
+  }
+  SolveArgs a;
+  fill_args(&a, N, params, u0, tspan, o, out, status, stats, h->queue);
+  SolveScratch sc{h->queue, N <= 0x7fffffffLL ? h->order : nullptr, h->bucket, h->hist};
+  LaunchCfg best;
+  rc = tune_problem(h->rhs_id, o, a, sc, h->num_sms, (cudaStream_t)stream, &best, best_ms);
+  if (rc) return rc;
+  *block = best.block;
+  *tpt = best.tpt;
   return ENS_OK;
 }
 
@@ -470,6 +587,71 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
   if (e == cudaSuccess && stats) e = cudaMemcpyAsync(stats, dstats, b_st, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  return ENS_OK;
+}
+
+long long ens_adjoint_ckpt_elems(long long N, int D, long long max_steps, int checkpoint_every) {
+  if (N < 0 || D < 1 || max_steps < 1 || checkpoint_every < 1) return -1;
+  return ckpt_slots(max_steps, checkpoint_every) * D * N;
+}
+
+int ens_adjoint_forward(ens_handle* h, long long N, const void* params, const void* u0,
+                        const void* tspan, const ens_opts* o, long long max_steps,
+                        int checkpoint_every, void* out, void* ckpt, signed char* status,
+                        void* stream) {
+  int rc = validate_adjoint(h, N, params, u0, tspan, o, max_steps, checkpoint_every);
+  if (rc) return rc;
+  if (N == 0) return ENS_OK;
+  if (!ckpt) return fail(ENS_EINVAL, "null checkpoint array");
+  AdjArgs a = adj_args(h, N, params, u0, tspan, o, max_steps, checkpoint_every);
+  a.out = out;
+  a.ckpt = ckpt;
+  a.status = status;
+  bool sup = false;
+  cudaError_t e = launch_adjoint(0, h->rhs_id, o->alg, o->dtype, a, (cudaStream_t)stream, &sup);
+  if (!sup) return fail(ENS_ENOTSUP, "adjoint not available for this model / method");
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint forward launch");
+  return ENS_OK;
+}
+
+int ens_adjoint(ens_handle* h, long long N, const void* params, const void* u0, const void* tspan,
+                const ens_opts* o, long long max_steps, int checkpoint_every, const void* ckpt,
+                const void* grad_out, void* grad_p, void* grad_u0, void* stream) {
+  int rc = validate_adjoint(h, N, params, u0, tspan, o, max_steps, checkpoint_every);
+  if (rc) return rc;
+  if (N == 0) return ENS_OK;
+  if (!grad_out || !grad_p || !grad_u0) return fail(ENS_EINVAL, "null gradient array");
+  std::lock_guard<std::mutex> lock(h->mu);
+  const size_t es = elem_size(o->dtype);
+  const int S = adjoint_stages(o->alg);
+  const long long K = std::min<long long>(checkpoint_every, max_steps);
+  const double seg_bytes = double(K) * S * h->D * double(N) * es;
+  if (seg_bytes > 64e9) return fail(ENS_ENOMEM, "adjoint segment buffer would exceed 64 GB");
+  if (!grow(&h->adj_seg, &h->adj_seg_bytes, (size_t)seg_bytes))
+    return fail(ENS_ENOMEM, "adjoint segment buffer");
+  AdjArgs a = adj_args(h, N, params, u0, tspan, o, max_steps, checkpoint_every);
+  a.seg = h->adj_seg;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool sup = false;
+  cudaError_t e = cudaSuccess;
+  if (ckpt) {
+    a.ckpt = const_cast<void*>(ckpt);
+  } else {
+    const double ck_bytes = double(ckpt_slots(max_steps, checkpoint_every)) * h->D * N * es;
+    if (ck_bytes > 64e9) return fail(ENS_ENOMEM, "adjoint checkpoints would exceed 64 GB");
+    if (!grow(&h->adj_ckpt, &h->adj_ckpt_bytes, (size_t)ck_bytes))
+      return fail(ENS_ENOMEM, "adjoint checkpoint buffer");
+    a.ckpt = h->adj_ckpt;
+    e = launch_adjoint(0, h->rhs_id, o->alg, o->dtype, a, s, &sup);
+    if (!sup) return fail(ENS_ENOTSUP, "adjoint not available for this model / method");
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint forward launch");
+  }
+  a.grad_out = grad_out;
+  a.grad_p = grad_p;
+  a.grad_u0 = grad_u0;
+  e = launch_adjoint(1, h->rhs_id, o->alg, o->dtype, a, s, &sup);
+  if (!sup) return fail(ENS_ENOTSUP, "adjoint not available for this model / method");
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   return ENS_OK;
 }
 

@@ -1,0 +1,349 @@
+// batch.cu -- launch-shape autotuner and batched (mixed-model) ensembles under one CUDA graph.
+//
+// Uneven ensembles make lanes of a warp finish at different times (adaptive stepping, Sec.
+// 6.4; mixed stiff / non-stiff / SDE work).  Within one (model, method) the persistent
+// schedule refills idle lanes; across models the batch runs one persistent kernel per
+// sub-problem, each with its own register budget, on forked streams captured into a single
+// CUDA graph, so one graph launch solves the whole batch and a kernel's tail overlaps with
+// the next kernels instead of leaving SMs idle between separate launches.  The autotuner
+// times candidate block sizes and trajectories-per-thread on the caller's own inputs (the
+// kernel-occupancy tuning the paper leaves to KernelAbstractions, Sec. 5.1) and remembers
+// the winner per (model, method, precision, layout, size class, SM count).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "ens_internal.h"
+
+namespace ens {
+
+namespace {
+
+bool fixed_method(int alg) { return alg == ENS_TSIT5_FIXED || alg == ENS_RK4 || alg == ENS_EM; }
+
+typedef std::tuple<int, int, int, int, int, int, int> TuneKey;
+std::map<TuneKey, LaunchCfg> g_tuned;
+std::mutex g_tuned_mu;
+
+TuneKey tune_key(int rhs_id, long long N, const ens_opts* o, int sms) {
+  int nbits = 0;
+  while (nbits < 62 && (1LL << (nbits + 1)) <= N) ++nbits;  // size class floor(log2 N)
+  return TuneKey(rhs_id, o->alg, o->dtype, o->layout, nbits, o->n_save > 0 ? 1 : 0, sms);
+}
+
+LaunchCfg default_launch(const ens_opts* o, int sms) {
+  LaunchCfg c;
+  c.schedule = o->schedule;
+  if (c.schedule == ENS_SCHED_AUTO)
+    c.schedule = fixed_method(o->alg) ? ENS_SCHED_DIRECT : ENS_SCHED_PERSISTENT;
+  c.block = o->block ? o->block : 128;
+  c.tpt = o->tpt ? o->tpt : 1;
+  c.num_sms = sms;
+  return c;
+}
+
+}  // namespace
+
+LaunchCfg resolve_launch(int rhs_id, long long N, const ens_opts* o, int num_sms) {
+  LaunchCfg c = default_launch(o, num_sms);
+  if (o->block == 0 && o->tpt == 0) {
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    auto it = g_tuned.find(tune_key(rhs_id, N, o, num_sms));
+    if (it != g_tuned.end() && (o->schedule == ENS_SCHED_AUTO ||
+                                o->schedule == it->second.schedule)) {
+      c = it->second;
+      c.num_sms = num_sms;
+    }
+  }
+  return c;
+}
+
+// Time every candidate launch shape of one solve (the solve really runs and writes its
+// outputs) and record the fastest in the tuning cache.  Synchronises the stream.
+int tune_problem(int rhs_id, const ens_opts* o, const SolveArgs& a, const SolveScratch& sc,
+                 int sms, cudaStream_t s, LaunchCfg* best, float* best_ms) {
+  const LaunchCfg base = default_launch(o, sms);
+  std::vector<LaunchCfg> cand;
+  const int blocks[] = {64, 128, 256, 512};
+  for (int b : blocks) {
+    if (o->block && b != o->block) continue;
+    if (base.schedule == ENS_SCHED_DIRECT) {
+      LaunchCfg c = base;
+      c.block = b;
+      c.tpt = 1;
+      cand.push_back(c);
+    } else {
+      for (int t : {1, 2}) {
+        if (o->tpt && t != o->tpt) continue;
+        LaunchCfg c = base;
+        c.block = b;
+        c.tpt = t;
+        cand.push_back(c);
+      }
+    }
+  }
+  if (cand.empty()) cand.push_back(base);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return set_last_error(ENS_ECUDA, "event create");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_last_error(ENS_ECUDA, "event create");
+  }
+  int rc = ENS_OK;
+  float bms = 1e30f;
+  LaunchCfg bc = base;
+  for (const LaunchCfg& c : cand) {
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3 && rc == ENS_OK; ++rep) {  // one warm-up, two timed runs
+      bool sup = false;
+      cudaEventRecord(e0, s);
+      cudaError_t e = enqueue_solve(rhs_id, o, a, c, sc, s, &sup);
+      cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (!sup) rc = set_last_error(ENS_ENOTSUP, "algorithm not available for this model");
+      else if (e != cudaSuccess) rc = set_last_error(ENS_ECUDA, cudaGetErrorString(e));
+      float ms = 0.f;
+      if (rc == ENS_OK && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        tmin = std::min(tmin, ms);
+    }
+    if (rc != ENS_OK) break;
+    if (tmin < bms) {
+      bms = tmin;
+      bc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != ENS_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    g_tuned[tune_key(rhs_id, a.N, o, sms)] = bc;
+  }
+  *best = bc;
+  *best_ms = bms;
+  return ENS_OK;
+}
+
+}  // namespace ens
+
+using namespace ens;
+
+// ============================================================================ batch plans
+struct ens_batch {
+  struct Item {
+    int rhs_id;
+    ens_opts o;
+    SolveArgs a;
+    LaunchCfg cfg;
+    SolveScratch sc;
+    float tuned_ms;
+    cudaStream_t st;
+    cudaEvent_t done;
+  };
+  std::vector<Item> items;
+  std::vector<int> order;  // launch order (longest measured first when tuned)
+  void* scratch;
+  cudaStream_t cap;
+  cudaEvent_t fork;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int flags;
+  int device;
+};
+
+namespace {
+
+int batch_fail(ens_batch* b, int code, const char* msg);
+
+cudaError_t enqueue_batch(ens_batch* b, cudaStream_t s, bool* sup) {
+  *sup = true;
+  if (b->flags & ENS_BATCH_SERIAL) {
+    for (int i : b->order) {
+      ens_batch::Item& it = b->items[i];
+      cudaError_t e = enqueue_solve(it.rhs_id, &it.o, it.a, it.cfg, it.sc, s, sup);
+      if (e != cudaSuccess || !*sup) return e;
+    }
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaEventRecord(b->fork, s);
+  for (int i : b->order) {
+    if (e != cudaSuccess) return e;
+    ens_batch::Item& it = b->items[i];
+    e = cudaStreamWaitEvent(it.st, b->fork, 0);
+    if (e == cudaSuccess) e = enqueue_solve(it.rhs_id, &it.o, it.a, it.cfg, it.sc, it.st, sup);
+    if (!*sup) return e;
+    if (e == cudaSuccess) e = cudaEventRecord(it.done, it.st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, it.done, 0);
+  }
+  return e;
+}
+
+void batch_free(ens_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto& it : b->items) {
+    if (it.st) cudaStreamDestroy(it.st);
+    if (it.done) cudaEventDestroy(it.done);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->scratch) cudaFree(b->scratch);
+  delete b;
+}
+
+int batch_fail(ens_batch* b, int code, const char* msg) {
+  batch_free(b);
+  return set_last_error(code, msg);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, int flags,
+                     void* cuda_stream) {
+  if (!out) return set_last_error(ENS_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (n_items < 1 || n_items > ENS_BATCH_MAX_ITEMS || !items)
+    return set_last_error(ENS_EINVAL, "n_items must be in [1, ENS_BATCH_MAX_ITEMS]");
+  if (flags & ~(ENS_BATCH_GRAPH | ENS_BATCH_AUTOTUNE | ENS_BATCH_SERIAL))
+    return set_last_error(ENS_EINVAL, "unknown flags");
+  for (int i = 0; i < n_items; ++i) {
+    const ens_batch_item& it = items[i];
+    int rc = validate_problem(it.rhs_id, it.N, it.params, it.u0, it.tspan, &it.opts, it.out);
+    if (rc) return rc;
+  }
+  ens_batch* b = new ens_batch();
+  b->scratch = nullptr;
+  b->cap = nullptr;
+  b->fork = nullptr;
+  b->graph = nullptr;
+  b->exec = nullptr;
+  b->flags = flags;
+  int sms = 0;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e));
+  // one scratch block: per item a 256-byte queue slot, the bucket cursors, order and keys
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  std::vector<size_t> off(n_items);
+  size_t total = 0;
+  for (int i = 0; i < n_items; ++i) {
+    off[i] = total;
+    const long long N = items[i].N;
+    total += 256 + up(4 * (size_t)kCostBuckets) + up(4 * (size_t)N) + up(2 * (size_t)N);
+  }
+  if (cudaMalloc(&b->scratch, total) != cudaSuccess)
+    return batch_fail(b, ENS_ENOMEM, "batch scratch");
+  b->items.resize(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const ens_batch_item& src = items[i];
+    ens_batch::Item& it = b->items[i];
+    std::memset(&it, 0, sizeof(it));
+    it.rhs_id = src.rhs_id;
+    it.o = src.opts;
+    fill_solve_args(&it.a, src.N, src.params, src.u0, src.tspan, &src.opts, src.out, src.status,
+                    src.stats);
+    it.o.saveat = nullptr;  // the save times now live in it.a (copied); the plan keeps no
+                            // pointer into the caller's host memory
+    it.cfg = resolve_launch(src.rhs_id, src.N, &src.opts, sms);
+    char* base = (char*)b->scratch + off[i];
+    it.sc.queue = (unsigned long long*)base;
+    it.sc.hist = (unsigned int*)(base + 256);
+    it.sc.order = (int*)(base + 256 + up(4 * (size_t)kCostBuckets));
+    it.sc.bucket = (unsigned short*)(base + 256 + up(4 * (size_t)kCostBuckets) +
+                                     up(4 * (size_t)src.N));
+    if (cudaStreamCreateWithFlags(&it.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming) != cudaSuccess)
+      return batch_fail(b, ENS_ECUDA, "stream / event creation");
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return batch_fail(b, ENS_ECUDA, "stream / event creation");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (flags & ENS_BATCH_AUTOTUNE) {
+    for (int i = 0; i < n_items; ++i) {
+      ens_batch::Item& it = b->items[i];
+      if (it.a.N == 0) continue;
+      // the trial solves need the save times in the options only for the cache key
+      ens_opts o = items[i].opts;
+      int rc = tune_problem(it.rhs_id, &o, it.a, it.sc, sms, s, &it.cfg, &it.tuned_ms);
+      if (rc) {
+        batch_free(b);
+        return rc;
+      }
+    }
+  }
+  b->order.resize(n_items);
+  for (int i = 0; i < n_items; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+    return b->items[x].tuned_ms > b->items[y].tuned_ms;  // longest first (ties: input order)
+  });
+  // items with no trajectories launch nothing
+  b->order.erase(std::remove_if(b->order.begin(), b->order.end(),
+                                [&](int i) { return b->items[i].a.N == 0; }),
+                 b->order.end());
+  if (flags & ENS_BATCH_GRAPH) {
+    // wait for the tuning runs (and any caller work on s) before capturing on a private stream
+    if (cudaStreamSynchronize(s) != cudaSuccess) return batch_fail(b, ENS_ECUDA, "sync");
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e));
+    bool sup = true;
+    cudaError_t e1 = enqueue_batch(b, b->cap, &sup);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    b->graph = g;
+    if (!sup) return batch_fail(b, ENS_ENOTSUP, "algorithm not available for this model");
+    if (e1 != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e1));
+    if (e != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e));
+  }
+  *out = b;
+  return ENS_OK;
+}
+
+int ens_batch_run(ens_batch* b, void* cuda_stream) {
+  if (!b) return set_last_error(ENS_EINVAL, "null batch");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e;
+  if (b->exec) {
+    e = cudaGraphLaunch(b->exec, s);
+  } else {
+    bool sup = true;
+    e = enqueue_batch(b, s, &sup);
+    if (!sup) return set_last_error(ENS_ENOTSUP, "algorithm not available for this model");
+  }
+  if (e != cudaSuccess) return set_last_error(ENS_ECUDA, cudaGetErrorString(e));
+  return ENS_OK;
+}
+
+int ens_batch_info(const ens_batch* b, int item, ens_batch_item_info* info) {
+  if (!b || !info) return set_last_error(ENS_EINVAL, "null argument");
+  if (item < 0 || item >= (int)b->items.size()) return set_last_error(ENS_EINVAL, "bad item");
+  const ens_batch::Item& it = b->items[item];
+  info->schedule = it.cfg.schedule;
+  info->block = it.cfg.block;
+  info->tpt = it.cfg.tpt;
+  info->tuned_ms = it.tuned_ms;
+  int pos = -1;
+  for (size_t k = 0; k < b->order.size(); ++k)
+    if (b->order[k] == item) pos = (int)k;
+  info->launch_position = pos;
+  info->graph = b->exec != nullptr;
+  return ENS_OK;
+}
+
+int ens_batch_destroy(ens_batch* b) {
+  if (!b) return ENS_OK;
+  cudaDeviceSynchronize();
+  batch_free(b);
+  return ENS_OK;
+}
+
+}  // extern "C"

@@ -30,6 +30,31 @@ struct SolveArgs {
   double saveat[ENS_MAX_SAVE];
 };
 
+// Arguments of the discrete-adjoint kernels (fixed-step explicit RK, one thread per trajectory).
+struct AdjArgs {
+  long long N;
+  const void* params;
+  const void* u0;
+  const void* tspan;
+  int layout;
+  double dt;
+  long long max_steps;   // capacity: every trajectory's step count must be <= max_steps
+  int K;                 // checkpoint interval (steps)
+  void* out;             // forward: final state [N][D] (layout) or null
+  void* ckpt;            // [C][D][N] checkpoints u_{cK}, C = ceil(max_steps / K)
+  const void* grad_out;  // [N][D] (layout) dL/du(tf)
+  void* grad_p;          // [N][P] (layout)
+  void* grad_u0;         // [N][D] (layout)
+  signed char* status;   // [N] or null
+  void* seg;             // [K][S][D][N] stage inputs of one segment (S stages of the method)
+};
+
+// Discrete adjoint: which = 0 forward with checkpoints, 1 reverse pass.  alg is
+// ENS_TSIT5_FIXED or ENS_RK4.  Implemented in adjoint.cu.
+cudaError_t launch_adjoint(int which, int rhs_id, int alg, int dtype, const AdjArgs& a,
+                           cudaStream_t stream, bool* supported);
+int adjoint_stages(int alg);  // stages whose inputs the reverse pass stores (0: unsupported)
+
 struct CostScratch {
   unsigned short* bucket;  // [N]
   unsigned int* hist;      // [kCostBuckets] bucket totals, then cursors
@@ -57,6 +82,34 @@ constexpr int kCostBlocks = 256;
 cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a,
                               unsigned short* bucket, unsigned int* hist, int* order,
                               cudaStream_t stream);
+
+// Device scratch of one persistent solve: the queue counter, and for the longest-first order
+// the permutation [N], bucket keys [N] and the kCostBuckets bucket cursors.
+struct SolveScratch {
+  unsigned long long* queue;
+  int* order;               // null: index order
+  unsigned short* bucket;
+  unsigned int* hist;
+};
+
+// Shared pieces of the solve entry points (abi.cu).
+int validate_problem(int rhs_id, long long N, const void* params, const void* u0,
+                     const void* tspan, const ens_opts* o, const void* out);
+void fill_solve_args(SolveArgs* a, long long N, const void* params, const void* u0,
+                     const void* tspan, const ens_opts* o, void* out, signed char* status,
+                     int* stats);
+bool uses_cost_order(const ens_opts* o, const LaunchCfg& cfg);
+// enqueue one solve on stream s: [cost order], queue reset, integrator kernel
+cudaError_t enqueue_solve(int rhs_id, const ens_opts* o, SolveArgs a, const LaunchCfg& cfg,
+                          const SolveScratch& sc, cudaStream_t s, bool* supported);
+// launch shape of a solve: explicit options, else the autotuner's cache, else the defaults
+// (persistent 128 x 1 for adaptive methods, direct 128 for fixed-step ones)
+LaunchCfg resolve_launch(int rhs_id, long long N, const ens_opts* o, int num_sms);
+int set_last_error(int code, const char* msg);
+// Autotuner (batch.cu): time the candidate launch shapes of one solve on its own inputs and
+// remember the fastest for resolve_launch; synchronises the stream.
+int tune_problem(int rhs_id, const ens_opts* o, const SolveArgs& a, const SolveScratch& sc,
+                 int sms, cudaStream_t s, LaunchCfg* best, float* best_ms);
 
 // Register / shared-memory attributes of the kernel a launch would use (for tuning).
 cudaError_t solve_kernel_attrs(int rhs_id, int alg, int dtype, const LaunchCfg& cfg,

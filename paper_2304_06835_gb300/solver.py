@@ -116,6 +116,104 @@ class EnsembleSolver:
         del keep
         return out, status, stats
 
+    def autotune(self, params, u0, tspan, alg="tsit5", *, layout="rowmajor", out=None,
+                 status=None, stats=None, stream=None, **kw):
+        """Time the candidate launch shapes on these inputs (the solve really runs) and cache
+        the fastest for later solves with block = tpt = 0.  Returns (block, tpt, ms)."""
+        N = params.shape[0] if layout == "rowmajor" else params.shape[-1]
+        saveat = kw.get("saveat")
+        saved = saveat is not None and len(saveat) > 0
+        S = len(saveat) if saved else 1
+        so = self._shapes(N, S, layout, saved)[3]
+        dev = params.device
+        if out is None:
+            out = torch.empty(so, dtype=params.dtype, device=dev)
+        o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, **kw)
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+        b, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _lib.check(_lib.lib().ens_autotune(self._h, N, _ptr(params), _ptr(u0), _ptr(tspan),
+                                           ctypes.byref(o), _ptr(out), _ptr(status), _ptr(stats),
+                                           ctypes.c_void_p(s), ctypes.byref(b), ctypes.byref(t),
+                                           ctypes.byref(ms)))
+        del keep
+        return b.value, t.value, ms.value
+
+    # --------------------------------------------------------------- discrete adjoint
+    def _adj_common(self, params, u0, tspan, layout):
+        if not (params.is_cuda and u0.is_cuda and tspan.is_cuda):
+            raise ValueError("params, u0 and tspan must be CUDA tensors")
+        if params.dtype not in _TORCH_DT or u0.dtype != params.dtype or tspan.dtype != params.dtype:
+            raise ValueError("params, u0, tspan must share dtype float32 or float64")
+        N = params.shape[0] if layout == "rowmajor" else params.shape[-1]
+        sp, su, st, so = self._shapes(N, 1, layout, False)
+        for name, t, shp in (("params", params, sp), ("u0", u0, su), ("tspan", tspan, st)):
+            if tuple(t.shape) != shp or not t.is_contiguous():
+                raise ValueError("%s must be contiguous with shape %s, got %s"
+                                 % (name, shp, tuple(t.shape)))
+        return N, so
+
+    @staticmethod
+    def max_steps_of(tspan, dt, layout="rowmajor"):
+        """Largest fixed-step count over the ensemble (reads tspan back to the host)."""
+        span = (tspan[:, 1] - tspan[:, 0]) if layout == "rowmajor" else (tspan[1] - tspan[0])
+        if span.numel() == 0:
+            return 1
+        return max(1, int(np.ceil(float(span.double().max().item()) / dt - 1e-12)))
+
+    def ckpt_elems(self, N, max_steps, checkpoint_every=64):
+        return int(_lib.lib().ens_adjoint_ckpt_elems(N, self.D, int(max_steps),
+                                                     int(checkpoint_every)))
+
+    def adjoint_forward(self, params, u0, tspan, alg="tsit5_fixed", *, dt, layout="rowmajor",
+                        max_steps=None, checkpoint_every=64, out=None, ckpt=None, status=None,
+                        stream=None):
+        """Fixed-step solve that also stores checkpoints for `adjoint`.  Returns (out, ckpt,
+        status, max_steps)."""
+        N, so = self._adj_common(params, u0, tspan, layout)
+        if max_steps is None:
+            max_steps = self.max_steps_of(tspan, dt, layout)
+        dev = params.device
+        if out is None:
+            out = torch.empty(so, dtype=params.dtype, device=dev)
+        if ckpt is None:
+            ckpt = torch.empty(max(1, self.ckpt_elems(N, max_steps, checkpoint_every)),
+                               dtype=params.dtype, device=dev)
+        if status is None:
+            status = torch.empty(N, dtype=torch.int8, device=dev)
+        o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, dt=dt)
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+        _lib.check(_lib.lib().ens_adjoint_forward(
+            self._h, N, _ptr(params), _ptr(u0), _ptr(tspan), ctypes.byref(o), int(max_steps),
+            int(checkpoint_every), _ptr(out), _ptr(ckpt), _ptr(status), ctypes.c_void_p(s)))
+        del keep
+        return out, ckpt, status, max_steps
+
+    def adjoint(self, params, u0, tspan, grad_out, alg="tsit5_fixed", *, dt, layout="rowmajor",
+                max_steps=None, checkpoint_every=64, ckpt=None, grad_p=None, grad_u0=None,
+                stream=None):
+        """dL/dp and dL/du0 of the fixed-step map given grad_out = dL/du(tf).  With ckpt=None
+        the forward pass is rerun inside the library."""
+        N, so = self._adj_common(params, u0, tspan, layout)
+        if tuple(grad_out.shape) != so or grad_out.dtype != params.dtype or not grad_out.is_cuda:
+            raise ValueError("grad_out must be a CUDA tensor of shape %s and dtype %s"
+                             % (so, params.dtype))
+        grad_out = grad_out.contiguous()
+        if max_steps is None:
+            max_steps = self.max_steps_of(tspan, dt, layout)
+        dev = params.device
+        if grad_p is None:
+            grad_p = torch.empty_like(params)
+        if grad_u0 is None:
+            grad_u0 = torch.empty_like(u0)
+        o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, dt=dt)
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+        _lib.check(_lib.lib().ens_adjoint(
+            self._h, N, _ptr(params), _ptr(u0), _ptr(tspan), ctypes.byref(o), int(max_steps),
+            int(checkpoint_every), _ptr(ckpt), _ptr(grad_out), _ptr(grad_p), _ptr(grad_u0),
+            ctypes.c_void_p(s)))
+        del keep
+        return grad_p, grad_u0
+
     def solve_host(self, params, u0, tspan, alg="tsit5", *, layout="rowmajor", want_stats=False,
                    stream=None, **kw):
         """NumPy (host) arrays in and out; the library copies to and from the device."""
@@ -158,3 +256,93 @@ def normals(seed, n_traj, n_per, dtype=torch.float32, index_offset=0, device="cu
     _lib.check(_lib.lib().ens_normals(int(seed), int(index_offset), int(n_traj), int(n_per),
                                       _TORCH_DT[dtype], _ptr(out), ctypes.c_void_p(s)))
     return out
+
+
+class EnsembleBatch:
+    """Several sub-problems solved by one call (one CUDA graph launch with graph=True).
+
+    items: list of dicts with keys rhs ("lorenz" / "robertson" / "gbm"), params, u0, tspan
+    (CUDA tensors, one dtype per item), alg, layout (default "soa") and any ens_solve option
+    (dt, abstol, reltol, dt0, maxiters, saveat, seed, index_offset, ...).  Outputs are
+    allocated here: ``batch.outputs[i] = (out, status, stats)``.
+    """
+
+    def __init__(self, items, *, graph=True, autotune=False, serial=False, want_stats=True,
+                 stream=None):
+        if not items or len(items) > _lib.BATCH_MAX_ITEMS:
+            raise ValueError("1 .. %d items" % _lib.BATCH_MAX_ITEMS)
+        arr = (_lib.BatchItem * len(items))()
+        self.outputs, self._keep = [], []
+        dev = None
+        for k, it in enumerate(items):
+            rhs_id = _lib.RHS[it["rhs"]]
+            D, P = _lib.DIMS[rhs_id]
+            params, u0, tspan = it["params"], it["u0"], it["tspan"]
+            layout = it.get("layout", "soa")
+            if params.dtype not in _TORCH_DT or u0.dtype != params.dtype or \
+                    tspan.dtype != params.dtype:
+                raise ValueError("item %d: params, u0, tspan must share float32/float64" % k)
+            N = params.shape[0] if layout == "rowmajor" else params.shape[-1]
+            saveat = it.get("saveat")
+            saved = saveat is not None and len(saveat) > 0
+            S = len(saveat) if saved else 1
+            shp = ((N, P), (N, D), (N, 2)) if layout == "rowmajor" else ((P, N), (D, N), (2, N))
+            for name, t, sh in zip(("params", "u0", "tspan"), (params, u0, tspan), shp):
+                if tuple(t.shape) != sh or not t.is_contiguous() or not t.is_cuda:
+                    raise ValueError("item %d: %s must be a contiguous CUDA tensor %s"
+                                     % (k, name, sh))
+            dev = params.device
+            so = ((N, S, D) if saved else (N, D)) if layout == "rowmajor" else \
+                ((S, D, N) if saved else (D, N))
+            out = torch.empty(so, dtype=params.dtype, device=dev)
+            status = torch.empty(N, dtype=torch.int8, device=dev)
+            stats = torch.empty((3, N), dtype=torch.int32, device=dev) if want_stats else None
+            kw = {k2: v for k2, v in it.items()
+                  if k2 not in ("rhs", "params", "u0", "tspan", "alg", "layout")}
+            o, keep = make_opts(it.get("alg", "tsit5"), _TORCH_DT[params.dtype], layout, **kw)
+            arr[k].rhs_id = rhs_id
+            arr[k].N = N
+            arr[k].params, arr[k].u0, arr[k].tspan = (params.data_ptr(), u0.data_ptr(),
+                                                      tspan.data_ptr())
+            arr[k].out = out.data_ptr()
+            arr[k].status = status.data_ptr()
+            arr[k].stats = stats.data_ptr() if stats is not None else None
+            arr[k].opts = o
+            self.outputs.append((out, status, stats))
+            self._keep.append((params, u0, tspan, keep))
+        flags = (_lib.BATCH_GRAPH if graph else 0) | (_lib.BATCH_AUTOTUNE if autotune else 0) | \
+            (_lib.BATCH_SERIAL if serial else 0)
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+        h = ctypes.c_void_p()
+        _lib.check(_lib.lib().ens_batch_create(ctypes.byref(h), arr, len(items), flags,
+                                               ctypes.c_void_p(s)))
+        self._h = h
+        self._items = arr
+        self.device = dev
+
+    def run(self, stream=None):
+        s = torch.cuda.current_stream(self.device).cuda_stream if stream is None \
+            else stream.cuda_stream
+        _lib.check(_lib.lib().ens_batch_run(self._h, ctypes.c_void_p(s)))
+        return self.outputs
+
+    def info(self):
+        res = []
+        for k in range(len(self.outputs)):
+            inf = _lib.BatchItemInfo()
+            _lib.check(_lib.lib().ens_batch_info(self._h, k, ctypes.byref(inf)))
+            res.append({"schedule": inf.schedule, "block": inf.block, "tpt": inf.tpt,
+                        "tuned_ms": inf.tuned_ms, "launch_position": inf.launch_position,
+                        "graph": bool(inf.graph)})
+        return res
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().ens_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -51,19 +51,23 @@ def test_em_uses_stream_of_its_index():
     assert abs(one[0, 0] - (1 + mu * 1e-3 + s * np.sqrt(1e-3) * z0)) < 1e-15
 
 
-def test_tangent_gradient_matches_central_differences():
+@pytest.mark.parametrize("alg", ["tsit5_fixed", "rk4"])
+def test_tangent_gradient_matches_central_differences(alg):
     P, U, T = workloads.lorenz_random(6, seed=5, t1=1.0)
     U = U + np.random.default_rng(3).normal(0, 1, U.shape)
     tgt = workloads.adjoint_targets(6)
     dt = 1e-2
 
     def loss(Pv, Uv):
-        out, _, _ = oracle.solve("lorenz", "tsit5_fixed", Pv, Uv, T, dt=dt)
+        out, _, _ = oracle.solve("lorenz", alg, Pv, Uv, T, dt=dt)
         return ((out - tgt) ** 2).sum(axis=1)
 
-    out, _, _ = oracle.solve("lorenz", "tsit5_fixed", P, U, T, dt=dt)
-    gp, gu, uf = oracle.tsit5_fixed_grad("lorenz", P, U, T, dt, 2 * (out - tgt))
-    np.testing.assert_array_equal(uf, out)
+    out, _, _ = oracle.solve("lorenz", alg, P, U, T, dt=dt)
+    gp, gu, uf = oracle.fixed_grad("lorenz", alg, P, U, T, dt, 2 * (out - tgt))
+    if alg == "tsit5_fixed":
+        np.testing.assert_array_equal(uf, out)
+    else:
+        np.testing.assert_allclose(uf, out, rtol=1e-13, atol=1e-13)
     hh = 1e-6
     for m in range(3):
         e = np.zeros_like(P)
@@ -89,3 +93,15 @@ def test_tangent_gradient_linear_closed_form():
     assert abs(gu[0, 0] - R(z) ** n) < 1e-13
     assert abs(gp[0, 0] - n * h * Rp * R(z) ** (n - 1) * u0) < 1e-8
     assert gp[0, 1] == 0.0
+
+
+def test_tangent_gradient_rk4_linear_closed_form():
+    """RK4 on u' = mu u: R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, so du(1)/du0 = R^n and
+    du(1)/dmu = n h R'(z) R^{n-1} u0 with R'(z) = 1 + z + z^2/2 + z^3/6."""
+    mu, h, n, u0 = -0.8, 0.01, 100, 1.3
+    z = h * mu
+    R = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    Rp = 1 + z + z * z / 2 + z ** 3 / 6
+    gp, gu, _ = oracle.fixed_grad("gbm", "rk4", [[mu, 0.2]], [[u0]], [[0.0, 1.0]], h, [[1.0]])
+    assert abs(gu[0, 0] - R ** n) < 1e-13
+    assert abs(gp[0, 0] - n * h * Rp * R ** (n - 1) * u0) < 1e-12
