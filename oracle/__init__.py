@@ -4,8 +4,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / r
 may import this package.  The product package never imports it and shares no code with it.
 
 The arithmetic lives in ``ens_oracle.cpp`` (plain C++, FP64, with an FP32 mode), built on demand
-into ``liboracle.so`` next to this file.  This module only marshals NumPy arrays into the C
-functions.
+into ``liboracle.so`` next to this file; ``mlp.py`` holds the NumPy oracle of the surrogate
+network.  This module only marshals NumPy arrays into the C functions.
 
 Identifiers (the same numbers as the public C-ABI, by documentation):
   rhs:  1 Lorenz (D=3, P=3: sigma, rho, beta), 2 Robertson (D=3, P=3: k1, k2, k3),
