@@ -236,6 +236,55 @@ int ens_adjoint(ens_handle* h, long long N, const void* params, const void* u0, 
                 const ens_opts* opts, long long max_steps, int checkpoint_every, const void* ckpt,
                 const void* grad_out, void* grad_p, void* grad_u0, void* cuda_stream);
 
+/* Learned surrogate (no counterpart in the paper: an addition to the ensemble method).
+ * A multilayer perceptron with widths 6 -> 256 -> 256 -> 256 -> 3 and exact-erf GELU maps a
+ * Lorenz problem x = (sigma, rho, beta, u0_1, u0_2, u0_3) to its state u(tf); `members`
+ * independently initialised copies form an ensemble whose disagreement gates a fallback to
+ * the solver.  BF16 operands, FP32 accumulation, every product on the tcgen05 tensor cores:
+ *   x_n = bf16(2 (x - lo)/(hi - lo) - 1),  Z_l = H_{l-1} W_l^T + b_l,  H_l = bf16(gelu(Z_l)),
+ *   y = Z_4 * y_std + y_mean.
+ * Parameters per member: FP32, flat in the order W_1 [256][6], b_1 [256], W_2 [256][256],
+ * b_2, W_3 [256][256], b_3, W_4 [3][256], b_4 [3] (ens_mlp_n_params() = 134,147 values).
+ * Arrays are device arrays; x [B][6] and y [B][3] FP32 row-major.  Calls are asynchronous
+ * unless stated; calls on one network share its workspace and must be ordered on one stream.
+ * A wait for the tensor cores that exceeds one second sets an error flag that ens_mlp_check
+ * reports (the results of that call are then invalid). */
+typedef struct ens_mlp ens_mlp;
+long long ens_mlp_n_params(void);
+/* box: HOST [6][2] (lo, hi) of the inputs, used to normalise x and by the gate.  batch_max:
+ * rows of the workspace (a multiple of 128); longer forward calls are processed in chunks.
+ * Parameters are drawn uniform in +-1/sqrt(fan_in) from Philox4x32-10 keyed by `seed`.
+ * Synchronises the stream. */
+int ens_mlp_create(ens_mlp** m, int members, long long batch_max, const double* box,
+                   unsigned long long seed, void* cuda_stream);
+int ens_mlp_destroy(ens_mlp* m);
+/* output de-standardisation y = z * y_std + y_mean (HOST arrays of 3); synchronises. */
+int ens_mlp_set_scaling(ens_mlp* m, const double* y_mean, const double* y_std, void* cuda_stream);
+/* copy member's FP32 parameters to `get` and/or replace them from `set` (device, n_params) */
+int ens_mlp_params(ens_mlp* m, int member, float* get, const float* set, void* cuda_stream);
+/* Forward + backward of one member on a minibatch (B <= batch_max): the gradient of the mean
+ * squared error on standardised targets, L = sum (z - (y - y_mean)/y_std)^2 / (3B), is kept
+ * for ens_mlp_adam and copied to `grad` (n_params, or NULL); the loss to *loss (device
+ * double, or NULL).  Row b of the minibatch is x[idx[b]], y[idx[b]] when idx (device int64
+ * [B]) is given, else x[b], y[b]. */
+int ens_mlp_grad(ens_mlp* m, int member, long long B, const float* x, const float* y,
+                 const long long* idx, float* grad, double* loss, void* cuda_stream);
+/* One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8, step count t >= 1) of one
+ * member with the gradient of the last ens_mlp_grad call. */
+int ens_mlp_adam(ens_mlp* m, int member, float lr, int t, void* cuda_stream);
+/* Inference: y [E'][B][3] for member (E' = 1) or all members (member = -1, E' = members). */
+int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* y,
+                    void* cuda_stream);
+/* Gate: y_mean [B][3] = mean over the members of y_members [members][B][3] (NULL to skip);
+ * fallback[b] = 1 when x_b leaves the box or the largest per-component population standard
+ * deviation over the members exceeds tau; *n_fallback (device, or NULL) is incremented by the
+ * number of fallbacks. */
+int ens_mlp_gate(ens_mlp* m, long long B, const float* x, const float* y_members, float tau,
+                 float* y_mean, unsigned char* fallback, unsigned long long* n_fallback,
+                 void* cuda_stream);
+/* Synchronise the stream and report a tensor-core wait timeout of an earlier call. */
+int ens_mlp_check(ens_mlp* m, void* cuda_stream);
+
 /* Raw Philox4x32-10 words (Salmon et al. SC'11) of the SDE streams: for trajectory
  * j < n_traj and call c < n_calls, out[(c*4 + w)*n_traj + j] = word w of
  * Philox(counter = (c lo, c hi, (index_offset+j) lo, hi), key = (seed lo, seed hi)).

@@ -92,6 +92,18 @@ SIGNATURES = {
                                    _VP, _VP, _VP, _VP]),
     "ens_adjoint": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _LL, _INT, _VP, _VP,
                            _VP, _VP, _VP]),
+    "ens_mlp_n_params": (_LL, []),
+    "ens_mlp_create": (_INT, [ctypes.POINTER(_VP), _INT, _LL, ctypes.POINTER(ctypes.c_double), _ULL,
+                              _VP]),
+    "ens_mlp_destroy": (_INT, [_VP]),
+    "ens_mlp_set_scaling": (_INT, [_VP, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), _VP]),
+    "ens_mlp_params": (_INT, [_VP, _INT, _VP, _VP, _VP]),
+    "ens_mlp_grad": (_INT, [_VP, _INT, _LL, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ens_mlp_adam": (_INT, [_VP, _INT, ctypes.c_float, _INT, _VP]),
+    "ens_mlp_forward": (_INT, [_VP, _INT, _LL, _VP, _VP, _VP]),
+    "ens_mlp_gate": (_INT, [_VP, _LL, _VP, _VP, ctypes.c_float, _VP, _VP, _VP, _VP]),
+    "ens_mlp_check": (_INT, [_VP, _VP]),
     "ens_probe_fma": (_INT, [_INT, _LL, _INT, _INT, ctypes.POINTER(ctypes.c_double), _VP]),
     "ens_last_error": (ctypes.c_char_p, []),
 }

@@ -1,0 +1,844 @@
+// mlp.cu -- the learned surrogate: a BF16 multilayer perceptron on the tcgen05 tensor cores.
+//
+// Not in the paper (an addition to the ensemble method): the network maps a Lorenz problem
+// x = (sigma, rho, beta, u0) to the state u(tf) and is trained on solver output.  Widths
+// 6 -> 256 -> 256 -> 256 -> 3, exact-erf GELU, BF16 operands with FP32 accumulation:
+//   x_n = bf16(2 (x - lo)/(hi - lo) - 1),  Z_l = H_{l-1} W_l^T + b_l,  H_l = bf16(gelu(Z_l)),
+//   y = Z_4 * y_std + y_mean.
+// Training minimises the mean squared error on standardised targets with Adam; the backward
+// pass is  dZ_4 = bf16(2 (Z_4 - t)/(3B)),  dW_l = dZ_l^T H_{l-1},  db_l = sum_b dZ_l,
+// dZ_{l-1} = bf16((dZ_l W_l) * gelu'(Z_{l-1})).
+//
+// Every matrix product runs in one kernel, k_gemm: a CTA owns a 128-row tile of the output
+// and BN columns; K is walked in 64-wide stages loaded by cp.async into the no-swizzle
+// core-matrix layout (double-buffered), one thread issues tcgen05.mma (M = 128, N = BN,
+// K = 16 per instruction) into an FP32 accumulator in tensor memory, and the epilogue reads it
+// back with tcgen05.ld and applies bias / GELU / GELU' / affine output in registers.  The
+// weight gradients contract over the batch with both operands MN-major (no transposed
+// copies), split over K into deterministic partial sums.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include <cuda_bf16.h>
+
+#include "ens_device.cuh"
+#include "ens_internal.h"
+#include "umma.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+namespace ens {
+namespace mlp {
+
+constexpr int PAD_IN = 16, PAD_OUT = 16, HID = 256;
+// flat FP32 parameter layout: W_1 [256][6], b_1, W_2 [256][256], b_2, W_3, b_3, W_4 [3][256], b_4
+constexpr long long OFF_W1 = 0, OFF_B1 = OFF_W1 + 256 * 6;
+constexpr long long OFF_W2 = OFF_B1 + 256, OFF_B2 = OFF_W2 + 256 * 256;
+constexpr long long OFF_W3 = OFF_B2 + 256, OFF_B3 = OFF_W3 + 256 * 256;
+constexpr long long OFF_W4 = OFF_B3 + 256, OFF_B4 = OFF_W4 + 3 * 256;
+constexpr long long NP = OFF_B4 + 3;          // 134,147 parameters per member
+// padded BF16 weights per member: W1b [256][16], W2b [256][256], W3b [256][256], W4b [16][256]
+constexpr long long WB1 = 0, WB2 = WB1 + 256 * 16, WB3 = WB2 + 256 * 256, WB4 = WB3 + 256 * 256;
+constexpr long long NWB = WB4 + 16 * 256;
+// padded FP32 biases per member: b1 [256], b2 [256], b3 [256], b4 [16]
+constexpr long long BB1 = 0, BB2 = 256, BB3 = 512, BB4 = 768, NBB = 784;
+
+// ------------------------------------------------------------------------------ GEMM kernel
+enum { EPI_AFFINE = 0, EPI_GELU_FWD = 1, EPI_GELU_BWD = 2, EPI_PARTIAL = 3 };
+
+struct GemmArgs {
+  int M, N, K;             // C[M][N] = sum_k A(m,k) B(n,k)
+  const bf16* A;
+  long long lda;
+  int a_mn;                // 0: A(m,k) = A[m*lda + k]; 1: A(m,k) = A[k*lda + m]
+  const bf16* B;
+  long long ldb;
+  int b_mn;                // 0: B(n,k) = B[n*ldb + k]; 1: B(n,k) = B[k*ldb + n]
+  int epi;
+  const float* bias;       // [N] or null
+  const float* scale;      // EPI_AFFINE: [N] or null (1)
+  const float* shift;      // EPI_AFFINE: [N] or null (0)
+  const float* aux;        // EPI_GELU_BWD: Z [M][ldaux]
+  long long ldaux;
+  float* out_f32;          // EPI_AFFINE / EPI_PARTIAL / (EPI_GELU_FWD: Z, optional)
+  long long ldo;
+  long long split_stride;  // EPI_PARTIAL: elements between the partial sums of splits
+  bf16* out_bf16;          // EPI_GELU_FWD: H; EPI_GELU_BWD: dZ
+  long long ldob;
+  int k_chunk;             // split-K: CTA z covers K range [z*k_chunk, (z+1)*k_chunk)
+  int* err;                // set to 1 when a wait for the tensor cores times out
+};
+
+constexpr int BM = 128, BK = 64, NTHREADS = 128;
+
+__device__ __forceinline__ float gelu_f(float z) {
+  return 0.5f * z * (1.f + erff(z * 0.70710678118654752440f));
+}
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752440f)) +
+         z * 0.39894228040143267794f * expf(-0.5f * z * z);
+}
+
+template <int BN>
+struct Tile {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int SMEM = 2 * STAGE + 1024;  // + alignment slack
+  static constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
+  // K-major: core matrices along K adjacent (128 B), 8-row groups BK/8 * 128 = 1024 B apart
+  static constexpr uint32_t KM_LBO = 128, KM_SBO = (BK / 8) * 128;
+  // MN-major: core matrices along MN adjacent (128 B), 8-k groups (rows/8)*128 B apart
+  static constexpr uint32_t A_MN_LBO = (BM / 8) * 128, B_MN_LBO = (BN / 8) * 128, MN_SBO = 128;
+};
+
+template <int BN>
+__device__ __forceinline__ void load_stage(const GemmArgs& g, unsigned char* sA, unsigned char* sB,
+                                           int m0, int n0, int k0, int kend) {
+  typedef Tile<BN> TL;
+  const int tid = threadIdx.x;
+  const uint32_t a = umma::smem_addr(sA), b = umma::smem_addr(sB);
+  if (!g.a_mn) {
+    for (int c = tid; c < BM * (BK / 8); c += NTHREADS) {
+      const int m = c >> 3, kc = c & 7, gm = m0 + m, gk = k0 + kc * 8;
+      const bool ok = gm < g.M && gk < kend;
+      const bf16* src = ok ? g.A + (long long)gm * g.lda + gk : g.A;
+      umma::cp_async16(a + (m >> 3) * TL::KM_SBO + kc * 128 + (m & 7) * 16, src, ok ? 16 : 0);
+    }
+  } else {
+    for (int c = tid; c < BK * (BM / 8); c += NTHREADS) {
+      const int k = c / (BM / 8), mc = c % (BM / 8), gk = k0 + k, gm = m0 + mc * 8;
+      const bool ok = gk < kend && gm < g.M;
+      const bf16* src = ok ? g.A + (long long)gk * g.lda + gm : g.A;
+      umma::cp_async16(a + (k >> 3) * TL::A_MN_LBO + mc * 128 + (k & 7) * 16, src, ok ? 16 : 0);
+    }
+  }
+  if (!g.b_mn) {
+    for (int c = tid; c < BN * (BK / 8); c += NTHREADS) {
+      const int n = c >> 3, kc = c & 7, gn = n0 + n, gk = k0 + kc * 8;
+      const bool ok = gn < g.N && gk < kend;
+      const bf16* src = ok ? g.B + (long long)gn * g.ldb + gk : g.B;
+      umma::cp_async16(b + (n >> 3) * TL::KM_SBO + kc * 128 + (n & 7) * 16, src, ok ? 16 : 0);
+    }
+  } else {
+    for (int c = tid; c < BK * (BN / 8); c += NTHREADS) {
+      const int k = c / (BN / 8), nc = c % (BN / 8), gk = k0 + k, gn = n0 + nc * 8;
+      const bool ok = gk < kend && gn < g.N;
+      const bf16* src = ok ? g.B + (long long)gk * g.ldb + gn : g.B;
+      umma::cp_async16(b + (k >> 3) * TL::B_MN_LBO + nc * 128 + (k & 7) * 16, src, ok ? 16 : 0);
+    }
+  }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS) k_gemm(const GemmArgs g) {
+  typedef Tile<BN> TL;
+  extern __shared__ unsigned char smraw[];
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t tslot;
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * g.k_chunk;
+  const int kend = min(g.K, kbeg + g.k_chunk);
+  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+
+  if (tid == 0) {
+    umma::mbar_init(&bar[0], 1);
+    umma::mbar_init(&bar[1], 1);
+    umma::mbar_init_fence();
+  }
+  if (warp == 0) umma::tmem_alloc<TL::TCOLS>(&tslot);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tacc = tslot;
+  const uint32_t idesc = umma::idesc_bf16(BM, BN, g.a_mn, g.b_mn);
+
+  bool ok = true;
+  if (nk > 0) {
+    load_stage<BN>(g, sm, sm + TL::A_BYTES, m0, n0, kbeg, kend);
+    umma::cp_async_commit();
+  }
+  for (int kt = 0; kt < nk && ok; ++kt) {
+    const int s = kt & 1;
+    if (kt + 1 < nk) {
+      if (kt >= 1) ok = umma::mbar_wait(&bar[s ^ 1], ((kt - 1) >> 1) & 1);
+      if (!ok) break;
+      unsigned char* st = sm + (s ^ 1) * TL::STAGE;
+      load_stage<BN>(g, st, st + TL::A_BYTES, m0, n0, kbeg + (kt + 1) * BK, kend);
+      umma::cp_async_commit();
+      umma::cp_async_wait<1>();
+    } else {
+      umma::cp_async_wait<0>();
+    }
+    umma::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      umma::fence_after();
+      const uint32_t a = umma::smem_addr(sm + s * TL::STAGE);
+      const uint32_t b = a + TL::A_BYTES;
+      const int k0 = kbeg + kt * BK;
+      const int steps = min(BK / 16, (kend - k0 + 15) / 16);
+      for (int j = 0; j < steps; ++j) {
+        const uint64_t ad = g.a_mn ? umma::desc(a + j * 2 * TL::A_MN_LBO, TL::A_MN_LBO, TL::MN_SBO)
+                                   : umma::desc(a + j * 256, TL::KM_LBO, TL::KM_SBO);
+        const uint64_t bd = g.b_mn ? umma::desc(b + j * 2 * TL::B_MN_LBO, TL::B_MN_LBO, TL::MN_SBO)
+                                   : umma::desc(b + j * 256, TL::KM_LBO, TL::KM_SBO);
+        umma::mma_bf16(tacc, ad, bd, idesc, (kt > 0 || j > 0) ? 1u : 0u);
+      }
+      umma::mma_commit(&bar[s]);
+    }
+  }
+  if (nk > 0 && ok) ok = umma::mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+  if (!ok) {
+    if (tid == 0) atomicExch(g.err, 1);
+    umma::cp_async_wait<0>();
+    // give any MMA still in flight a bounded chance to finish before the memory goes away
+    if (nk > 0) umma::mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, 100000000ull);
+  }
+  umma::fence_after();
+
+  // epilogue: warp w holds rows m0 + 32 w + lane, 16 columns per tcgen05.ld
+  const int row = m0 + warp * 32 + lane;
+  const bool live = ok && row < g.M;
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    uint32_t r[16];
+    if (nk > 0) {
+      umma::tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + c0, r);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) r[j] = 0u;
+    }
+    if (!live) continue;
+    const int nb = n0 + c0;
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+    if (g.epi == EPI_PARTIAL) {
+      float* o = g.out_f32 + (long long)blockIdx.z * g.split_stride + (long long)row * g.ldo + nb;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (nb + j < g.N) o[j] = v[j];
+      continue;
+    }
+    if (g.bias) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (nb + j < g.N) v[j] += __ldg(g.bias + nb + j);
+    }
+    if (g.epi == EPI_AFFINE) {
+      float* o = g.out_f32 + (long long)row * g.ldo + nb;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (nb + j < g.N) {
+          const float sc = g.scale ? __ldg(g.scale + nb + j) : 1.f;
+          const float sh = g.shift ? __ldg(g.shift + nb + j) : 0.f;
+          o[j] = fmaf(v[j], sc, sh);
+        }
+    } else if (g.epi == EPI_GELU_FWD) {
+      if (g.out_f32) {
+        float* o = g.out_f32 + (long long)row * g.ldo + nb;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (nb + j < g.N) o[j] = v[j];
+      }
+      bf16* o = g.out_bf16 + (long long)row * g.ldob + nb;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (nb + j < g.N) o[j] = __float2bfloat16_rn(gelu_f(v[j]));
+    } else {  // EPI_GELU_BWD
+      const float* z = g.aux + (long long)row * g.ldaux + nb;
+      bf16* o = g.out_bf16 + (long long)row * g.ldob + nb;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (nb + j < g.N) o[j] = __float2bfloat16_rn(v[j] * gelu_grad_f(__ldg(z + j)));
+    }
+  }
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    umma::fence_after();
+    umma::tmem_dealloc<TL::TCOLS>(tacc);
+  }
+}
+
+// ------------------------------------------------------------------------------ small kernels
+struct Box {
+  float lo[6], inv[6];  // inv = 2 / (hi - lo)
+  float hi[6];
+};
+
+// x_n = bf16(2 (x - lo)/(hi - lo) - 1), columns 6..15 zero; row b reads x[idx[b]] when an
+// index array is given (minibatch gather)
+__global__ void k_input(long long B, const float* __restrict__ x, const long long* __restrict__ idx,
+                        Box box, bf16* __restrict__ xn) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * PAD_IN) return;
+  const long long b = i / PAD_IN;
+  const long long r = idx ? idx[b] : b;
+  const int c = (int)(i % PAD_IN);
+  float v = 0.f;
+  if (c < 6) v = (x[r * 6 + c] - box.lo[c]) * box.inv[c] - 1.f;
+  xn[i] = __float2bfloat16_rn(v);
+}
+
+// loss partial sums and dZ_4 = bf16(2 (z - t) / (3 B)); t = (y - mean)/std
+__global__ void k_loss(long long B, const float* __restrict__ z4, const float* __restrict__ y,
+                       const long long* __restrict__ idx, const float* __restrict__ mean,
+                       const float* __restrict__ stdv, bf16* __restrict__ dz4, double* loss) {
+  __shared__ double red[256];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (i < B * PAD_OUT) {
+    const long long b = i / PAD_OUT;
+    const int c = (int)(i % PAD_OUT);
+    float d = 0.f;
+    if (c < 3) {
+      const long long row = idx ? idx[b] : b;
+      const float t = (y[row * 3 + c] - mean[c]) / stdv[c];
+      const float r = z4[b * PAD_OUT + c] - t;
+      acc = (double)r * r;
+      d = 2.f * r / (3.f * (float)B);
+    }
+    dz4[i] = __float2bfloat16_rn(d);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) atomicAdd(loss, red[0] / (3.0 * (double)B));
+}
+
+// column sums of a bf16 matrix [rows][ld] over a chunk of rows: part[chunk][c]
+__global__ void k_colsum(long long rows, int ncols, long long ld, const bf16* __restrict__ a,
+                         long long chunk, float* __restrict__ part) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  const long long r0 = (long long)blockIdx.y * chunk;
+  const long long r1 = min(rows, r0 + chunk);
+  float s = 0.f;
+  for (long long r = r0; r < r1; ++r) s += __bfloat162float(a[r * ld + c]);
+  part[(long long)blockIdx.y * ncols + c] = s;
+}
+
+// out[r * out_ld + c] = sum_s part[s * stride + r * ld + c]   (r < rows, c < cols)
+__global__ void k_reduce(int S, long long stride, int rows, int cols, long long ld,
+                         const float* __restrict__ part, float* __restrict__ out, long long out_ld) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)rows * cols) return;
+  const int r = (int)(i / cols), c = (int)(i % cols);
+  float s = 0.f;
+  for (int k = 0; k < S; ++k) s += part[k * stride + (long long)r * ld + c];
+  out[(long long)r * out_ld + c] = s;
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
+__global__ void k_adam(long long n, float* __restrict__ p, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 padded weights and padded FP32 biases of one member from its FP32 parameters
+__global__ void k_refresh(const float* __restrict__ p, bf16* __restrict__ wb, float* __restrict__ bb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < NWB) {
+    float v = 0.f;
+    if (i < WB2) {
+      const long long r = i / 16, c = i % 16;
+      v = c < 6 ? p[OFF_W1 + r * 6 + c] : 0.f;
+    } else if (i < WB3) {
+      v = p[OFF_W2 + (i - WB2)];
+    } else if (i < WB4) {
+      v = p[OFF_W3 + (i - WB3)];
+    } else {
+      const long long r = (i - WB4) / 256, c = (i - WB4) % 256;
+      v = r < 3 ? p[OFF_W4 + r * 256 + c] : 0.f;
+    }
+    wb[i] = __float2bfloat16_rn(v);
+  }
+  if (i < NBB) {
+    float v;
+    if (i < BB2) v = p[OFF_B1 + i];
+    else if (i < BB3) v = p[OFF_B2 + (i - BB2)];
+    else if (i < BB4) v = p[OFF_B3 + (i - BB3)];
+    else v = (i - BB4) < 3 ? p[OFF_B4 + (i - BB4)] : 0.f;
+    bb[i] = v;
+  }
+}
+
+// Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for every weight and bias, from Philox4x32-10
+// (counter = (parameter index, member, 0x4D4C5000), key = seed).
+__global__ void k_init(long long n, int member, unsigned long long seed, float* __restrict__ p) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 x = Philox::gen(make_uint4((uint32_t)i, (uint32_t)(i >> 32), (uint32_t)member,
+                                         0x4D4C5000u),
+                              make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const float u = ((float)(x.x >> 8) + 0.5f) * 5.9604644775390625e-08f;  // (0, 1)
+  const int fan_in = i < OFF_W2 ? 6 : 256;
+  p[i] = (2.f * u - 1.f) * rsqrtf((float)fan_in);
+}
+
+// mean and population standard deviation over the members; fallback when the input leaves
+// the training box or max_j std_j > tau
+__global__ void k_gate(long long B, int E, const float* __restrict__ x,
+                       const float* __restrict__ ym, Box box, float tau, float* __restrict__ mean,
+                       unsigned char* __restrict__ fb, unsigned long long* n_fb) {
+  const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool f = false;
+  if (b < B) {
+    bool out = false;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float v = x[b * 6 + c];
+      out = out || !(v >= box.lo[c] && v <= box.hi[c]);
+    }
+    float smax = 0.f;
+    for (int j = 0; j < 3; ++j) {
+      float s = 0.f;
+      for (int e = 0; e < E; ++e) s += ym[((long long)e * B + b) * 3 + j];
+      const float mu = s / (float)E;
+      float q = 0.f;
+      for (int e = 0; e < E; ++e) {
+        const float d = ym[((long long)e * B + b) * 3 + j] - mu;
+        q += d * d;
+      }
+      smax = fmaxf(smax, sqrtf(q / (float)E));
+      if (mean) mean[b * 3 + j] = mu;
+    }
+    f = out || !(smax <= tau);
+    fb[b] = f ? 1 : 0;
+  }
+  const unsigned cnt = __popc(__ballot_sync(0xffffffffu, f));
+  if ((threadIdx.x & 31) == 0 && cnt && n_fb) atomicAdd(n_fb, (unsigned long long)cnt);
+}
+
+}  // namespace mlp
+}  // namespace ens
+
+using namespace ens;
+using namespace ens::mlp;
+
+// ============================================================================ the C ABI
+struct ens_mlp {
+  int E;
+  long long bmax;
+  int splits_max;
+  Box box;
+  float* p;       // [E][NP]
+  float* am;      // [E][NP]
+  float* av;      // [E][NP]
+  float* g;       // [NP] gradient of the last ens_mlp_grad
+  bf16* wb;       // [E][NWB]
+  float* bb;      // [E][NBB]
+  float* ystat;   // [6]: y_mean[3], y_std[3]
+  float* one3;    // [6]: ones[3], zeros[3] (identity affine for training)
+  bf16* xn;       // [bmax][16]
+  float* z[3];    // [bmax][256]
+  bf16* h[3];     // [bmax][256]
+  float* z4;      // [bmax][16]
+  bf16* dz4;      // [bmax][16]
+  bf16* dz[2];    // [bmax][256]
+  float* part;    // [splits_max][256][256]
+  double* loss;
+  int* err;
+  void* block;    // single allocation holding everything above
+};
+
+namespace {
+
+int mfail(int code, const char* msg) { return set_last_error(code, msg); }
+
+cudaError_t gemm(const GemmArgs& g0, int splits, cudaStream_t s) {
+  GemmArgs g = g0;
+  if (g.k_chunk <= 0) g.k_chunk = g.K;
+  const dim3 grid((g.M + BM - 1) / BM, 1, splits);
+  cudaError_t e;
+  if (g.N <= 16) {
+    e = cudaFuncSetAttribute(k_gemm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tile<16>::SMEM);
+    if (e != cudaSuccess) return e;
+    k_gemm<16><<<grid, NTHREADS, Tile<16>::SMEM, s>>>(g);
+  } else {
+    e = cudaFuncSetAttribute(k_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tile<256>::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 gr = grid;
+    gr.y = (g.N + 255) / 256;
+    k_gemm<256><<<gr, NTHREADS, Tile<256>::SMEM, s>>>(g);
+  }
+  return cudaGetLastError();
+}
+
+GemmArgs gemm_args(const ens_mlp* m) {
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.err = m->err;
+  return g;
+}
+
+unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// forward of one member on rows [0, B) of the workspace (x already normalised into xn);
+// keep = store the pre-activations for the backward pass; y (if not null) gets the
+// de-standardised output [B][3]
+cudaError_t forward_member(ens_mlp* m, int e, long long B, bool keep, float* y, long long ldy,
+                           cudaStream_t s) {
+  const bf16* W = m->wb + (long long)e * NWB;
+  const float* bias = m->bb + (long long)e * NBB;
+  const bf16* in = m->xn;
+  long long ldin = PAD_IN;
+  const long long woff[3] = {WB1, WB2, WB3};
+  const long long boff[3] = {BB1, BB2, BB3};
+  for (int l = 0; l < 3; ++l) {
+    GemmArgs g = gemm_args(m);
+    g.M = (int)B;
+    g.N = HID;
+    g.K = l == 0 ? PAD_IN : HID;
+    g.A = in;
+    g.lda = ldin;
+    g.B = W + woff[l];
+    g.ldb = l == 0 ? PAD_IN : HID;
+    g.epi = EPI_GELU_FWD;
+    g.bias = bias + boff[l];
+    g.out_f32 = keep ? m->z[l] : nullptr;
+    g.ldo = HID;
+    g.out_bf16 = m->h[l];
+    g.ldob = HID;
+    cudaError_t err = gemm(g, 1, s);
+    if (err != cudaSuccess) return err;
+    in = m->h[l];
+    ldin = HID;
+  }
+  GemmArgs g = gemm_args(m);
+  g.M = (int)B;
+  g.N = y ? 3 : PAD_OUT;
+  g.K = HID;
+  g.A = m->h[2];
+  g.lda = HID;
+  g.B = W + WB4;
+  g.ldb = HID;
+  g.epi = EPI_AFFINE;
+  g.bias = bias + BB4;
+  g.scale = y ? m->ystat + 3 : nullptr;
+  g.shift = y ? m->ystat : nullptr;
+  g.out_f32 = y ? y : m->z4;
+  g.ldo = y ? ldy : PAD_OUT;
+  return gemm(g, 1, s);
+}
+
+// weight gradient dW = dZ^T H over the batch (both operands MN-major), split over K
+cudaError_t wgrad(ens_mlp* m, long long B, const bf16* dz, int ldz, int Mrows, const bf16* h,
+                  int ldh, int Ncols, float* out, int out_rows, int out_cols, cudaStream_t s) {
+  int chunk = (int)std::max<long long>(BK, ((B + m->splits_max - 1) / m->splits_max + BK - 1) /
+                                               BK * BK);
+  const int splits = (int)((B + chunk - 1) / chunk);
+  GemmArgs g = gemm_args(m);
+  g.M = Mrows;
+  g.N = Ncols;
+  g.K = (int)B;
+  g.A = dz;
+  g.lda = ldz;
+  g.a_mn = 1;
+  g.B = h;
+  g.ldb = ldh;
+  g.b_mn = 1;
+  g.epi = EPI_PARTIAL;
+  g.out_f32 = m->part;
+  g.ldo = Ncols;
+  g.split_stride = (long long)Mrows * Ncols;
+  g.k_chunk = chunk;
+  cudaError_t e = gemm(g, splits, s);
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)out_rows * out_cols;
+  k_reduce<<<blocks_for(n), 256, 0, s>>>(splits, (long long)Mrows * Ncols, out_rows, out_cols,
+                                         Ncols, m->part, out, out_cols);
+  return cudaGetLastError();
+}
+
+cudaError_t bias_grad(ens_mlp* m, long long B, const bf16* dz, int ld, int ncols, float* out,
+                      cudaStream_t s) {
+  const long long chunk = 256;
+  const int nchunk = (int)((B + chunk - 1) / chunk);
+  // the partial column sums reuse the split-K buffer (after the weight gradient is reduced)
+  k_colsum<<<dim3((ncols + 255) / 256, nchunk), 256, 0, s>>>(B, ncols, ld, dz, chunk, m->part);
+  k_reduce<<<blocks_for(ncols), 256, 0, s>>>(nchunk, ncols, 1, ncols, ncols, m->part, out, ncols);
+  return cudaGetLastError();
+}
+
+Box make_box(const double* box) {
+  Box b;
+  for (int c = 0; c < 6; ++c) {
+    b.lo[c] = (float)box[2 * c];
+    b.hi[c] = (float)box[2 * c + 1];
+    b.inv[c] = (float)(2.0 / (box[2 * c + 1] - box[2 * c]));
+  }
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+long long ens_mlp_n_params(void) { return NP; }
+
+int ens_mlp_create(ens_mlp** out, int members, long long batch_max, const double* box,
+                   unsigned long long seed, void* cuda_stream) {
+  if (!out) return mfail(ENS_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (members < 1 || members > 16) return mfail(ENS_EINVAL, "members must be in [1, 16]");
+  if (batch_max < 128 || batch_max > (1LL << 24) || batch_max % 128)
+    return mfail(ENS_EINVAL, "batch_max must be a multiple of 128 in [128, 2^24]");
+  if (!box) return mfail(ENS_EINVAL, "null box");
+  for (int c = 0; c < 6; ++c)
+    if (!(box[2 * c + 1] > box[2 * c]) || !std::isfinite(box[2 * c]) ||
+        !std::isfinite(box[2 * c + 1]))
+      return mfail(ENS_EINVAL, "box must have finite lo < hi in every input");
+  ens_mlp* m = new ens_mlp();
+  std::memset(m, 0, sizeof(*m));
+  m->E = members;
+  m->bmax = batch_max;
+  m->splits_max = 64;
+  m->box = make_box(box);
+  const long long E = members, Bm = batch_max;
+  auto up = [](long long x) { return (x + 255) & ~255LL; };
+  long long off = 0;
+  long long o_p = off; off += up(4 * E * NP);
+  long long o_am = off; off += up(4 * E * NP);
+  long long o_av = off; off += up(4 * E * NP);
+  long long o_g = off; off += up(4 * NP);
+  long long o_wb = off; off += up(2 * E * NWB);
+  long long o_bb = off; off += up(4 * E * NBB);
+  long long o_ys = off; off += up(4 * 6);
+  long long o_one = off; off += up(4 * 6);
+  long long o_xn = off; off += up(2 * Bm * PAD_IN);
+  long long o_z[3], o_h[3];
+  for (int l = 0; l < 3; ++l) { o_z[l] = off; off += up(4 * Bm * HID); }
+  for (int l = 0; l < 3; ++l) { o_h[l] = off; off += up(2 * Bm * HID); }
+  long long o_z4 = off; off += up(4 * Bm * PAD_OUT);
+  long long o_dz4 = off; off += up(2 * Bm * PAD_OUT);
+  long long o_dz[2];
+  for (int l = 0; l < 2; ++l) { o_dz[l] = off; off += up(2 * Bm * HID); }
+  const long long part_elems = std::max<long long>((long long)m->splits_max * HID * HID,
+                                                   (Bm / 256 + 1) * HID);
+  long long o_part = off; off += up(4 * part_elems);
+  long long o_loss = off; off += up(8);
+  long long o_err = off; off += up(4);
+  if (cudaMalloc(&m->block, off) != cudaSuccess) {
+    delete m;
+    return mfail(ENS_ENOMEM, "surrogate network memory");
+  }
+  char* b = (char*)m->block;
+  m->p = (float*)(b + o_p);
+  m->am = (float*)(b + o_am);
+  m->av = (float*)(b + o_av);
+  m->g = (float*)(b + o_g);
+  m->wb = (bf16*)(b + o_wb);
+  m->bb = (float*)(b + o_bb);
+  m->ystat = (float*)(b + o_ys);
+  m->one3 = (float*)(b + o_one);
+  m->xn = (bf16*)(b + o_xn);
+  for (int l = 0; l < 3; ++l) {
+    m->z[l] = (float*)(b + o_z[l]);
+    m->h[l] = (bf16*)(b + o_h[l]);
+  }
+  m->z4 = (float*)(b + o_z4);
+  m->dz4 = (bf16*)(b + o_dz4);
+  for (int l = 0; l < 2; ++l) m->dz[l] = (bf16*)(b + o_dz[l]);
+  m->part = (float*)(b + o_part);
+  m->loss = (double*)(b + o_loss);
+  m->err = (int*)(b + o_err);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const float ys[6] = {0.f, 0.f, 0.f, 1.f, 1.f, 1.f};
+  cudaError_t e = cudaMemcpyAsync(m->ystat, ys, sizeof(ys), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->one3, ys, sizeof(ys), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->am, 0, 4 * E * NP, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->av, 0, 4 * E * NP, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, 4, s);
+  for (int k = 0; k < members && e == cudaSuccess; ++k) {
+    k_init<<<blocks_for(NP), 256, 0, s>>>(NP, k, seed, m->p + k * NP);
+    k_refresh<<<blocks_for(NWB), 256, 0, s>>>(m->p + k * NP, m->wb + k * NWB, m->bb + k * NBB);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host arrays above are stack memory
+  if (e != cudaSuccess) {
+    cudaFree(m->block);
+    delete m;
+    return mfail(ENS_ECUDA, cudaGetErrorString(e));
+  }
+  *out = m;
+  return ENS_OK;
+}
+
+int ens_mlp_destroy(ens_mlp* m) {
+  if (!m) return ENS_OK;
+  cudaDeviceSynchronize();
+  cudaFree(m->block);
+  delete m;
+  return ENS_OK;
+}
+
+int ens_mlp_set_scaling(ens_mlp* m, const double* y_mean, const double* y_std, void* stream) {
+  if (!m || !y_mean || !y_std) return mfail(ENS_EINVAL, "null argument");
+  float ys[6];
+  for (int j = 0; j < 3; ++j) {
+    if (!(y_std[j] > 0) || !std::isfinite(y_std[j]) || !std::isfinite(y_mean[j]))
+      return mfail(ENS_EINVAL, "y_std must be finite and > 0");
+    ys[j] = (float)y_mean[j];
+    ys[3 + j] = (float)y_std[j];
+  }
+  cudaError_t e = cudaMemcpyAsync(m->ystat, ys, sizeof(ys), cudaMemcpyHostToDevice,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
+}
+
+int ens_mlp_params(ens_mlp* m, int member, float* get, const float* set, void* stream) {
+  if (!m) return mfail(ENS_EINVAL, "null network");
+  if (member < 0 || member >= m->E) return mfail(ENS_EINVAL, "member out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  float* p = m->p + (long long)member * NP;
+  cudaError_t e = cudaSuccess;
+  if (get) e = cudaMemcpyAsync(get, p, 4 * NP, cudaMemcpyDeviceToDevice, s);
+  if (set && e == cudaSuccess) {
+    e = cudaMemcpyAsync(p, set, 4 * NP, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+      k_refresh<<<blocks_for(NWB), 256, 0, s>>>(p, m->wb + member * NWB, m->bb + member * NBB);
+      e = cudaGetLastError();
+    }
+  }
+  return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
+}
+
+int ens_mlp_grad(ens_mlp* m, int member, long long B, const float* x, const float* y,
+                 const long long* idx, float* grad, double* loss, void* stream) {
+  if (!m) return mfail(ENS_EINVAL, "null network");
+  if (member < 0 || member >= m->E) return mfail(ENS_EINVAL, "member out of range");
+  if (B < 1 || B > m->bmax) return mfail(ENS_EINVAL, "B must be in [1, batch_max]");
+  if (!x || !y) return mfail(ENS_EINVAL, "null array");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int e_ = member;
+  const bf16* W = m->wb + (long long)e_ * NWB;
+  cudaError_t e = cudaMemsetAsync(m->loss, 0, 8, s);
+  k_input<<<blocks_for(B * PAD_IN), 256, 0, s>>>(B, x, idx, m->box, m->xn);
+  if (e == cudaSuccess) e = forward_member(m, e_, B, true, nullptr, 0, s);
+  if (e == cudaSuccess) {
+    k_loss<<<blocks_for(B * PAD_OUT), 256, 0, s>>>(B, m->z4, y, idx, m->ystat, m->ystat + 3,
+                                                   m->dz4, m->loss);
+    e = cudaGetLastError();
+  }
+  float* G = m->g;
+  // layer 4: dW4 = dZ4^T H3 (rows 0..2), db4, dZ3 = (dZ4 W4) * gelu'(Z3)
+  if (e == cudaSuccess) e = wgrad(m, B, m->dz4, PAD_OUT, PAD_OUT, m->h[2], HID, HID,
+                                  G + OFF_W4, 3, HID, s);
+  if (e == cudaSuccess) e = bias_grad(m, B, m->dz4, PAD_OUT, 3, G + OFF_B4, s);
+  const bf16* dzl = m->dz4;
+  int lddz = PAD_OUT;
+  const long long woff[4] = {WB1, WB2, WB3, WB4};
+  const long long goffW[3] = {OFF_W1, OFF_W2, OFF_W3};
+  const long long goffB[3] = {OFF_B1, OFF_B2, OFF_B3};
+  for (int l = 2; l >= 0 && e == cudaSuccess; --l) {
+    // dZ_l = (dZ_{l+1} W_{l+1}) * gelu'(Z_l): A = dZ_{l+1} (K-major), B(n,k) = W_{l+1}[k][n]
+    bf16* dzn = m->dz[l & 1];
+    GemmArgs g = gemm_args(m);
+    g.M = (int)B;
+    g.N = HID;
+    g.K = lddz;
+    g.A = dzl;
+    g.lda = lddz;
+    g.B = W + woff[l + 1];
+    g.ldb = HID;
+    g.b_mn = 1;
+    g.epi = EPI_GELU_BWD;
+    g.aux = m->z[l];
+    g.ldaux = HID;
+    g.out_bf16 = dzn;
+    g.ldob = HID;
+    e = gemm(g, 1, s);
+    // dW_l = dZ_l^T H_{l-1}, db_l
+    const bf16* hin = l == 0 ? m->xn : m->h[l - 1];
+    const int ldh = l == 0 ? PAD_IN : HID;
+    const int ncol = l == 0 ? PAD_IN : HID;
+    if (e == cudaSuccess)
+      e = wgrad(m, B, dzn, HID, HID, hin, ldh, ncol, G + goffW[l], HID, l == 0 ? 6 : HID, s);
+    if (e == cudaSuccess) e = bias_grad(m, B, dzn, HID, HID, G + goffB[l], s);
+    dzl = dzn;
+    lddz = HID;
+  }
+  if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, G, 4 * NP, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, m->loss, 8, cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
+}
+
+int ens_mlp_adam(ens_mlp* m, int member, float lr, int t, void* stream) {
+  if (!m) return mfail(ENS_EINVAL, "null network");
+  if (member < 0 || member >= m->E) return mfail(ENS_EINVAL, "member out of range");
+  if (t < 1 || !(lr >= 0)) return mfail(ENS_EINVAL, "t must be >= 1 and lr >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = (float)(1.0 - std::pow(0.9, t)), c2 = (float)(1.0 - std::pow(0.999, t));
+  const long long o = (long long)member * NP;
+  k_adam<<<blocks_for(NP), 256, 0, s>>>(NP, m->p + o, m->g, m->am + o, m->av + o, lr, b1, b2,
+                                        1e-8f, c1, c2);
+  k_refresh<<<blocks_for(NWB), 256, 0, s>>>(m->p + o, m->wb + member * NWB, m->bb + member * NBB);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
+}
+
+int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* y, void* stream) {
+  if (!m) return mfail(ENS_EINVAL, "null network");
+  if (member < -1 || member >= m->E) return mfail(ENS_EINVAL, "member out of range");
+  if (B < 0) return mfail(ENS_EINVAL, "B < 0");
+  if (B == 0) return ENS_OK;
+  if (!x || !y) return mfail(ENS_EINVAL, "null array");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int e0 = member < 0 ? 0 : member, e1 = member < 0 ? m->E : member + 1;
+  cudaError_t e = cudaSuccess;
+  for (long long b0 = 0; b0 < B && e == cudaSuccess; b0 += m->bmax) {
+    const long long nb = std::min(m->bmax, B - b0);
+    k_input<<<blocks_for(nb * PAD_IN), 256, 0, s>>>(nb, x + b0 * 6, nullptr, m->box, m->xn);
+    e = cudaGetLastError();
+    for (int k = e0; k < e1 && e == cudaSuccess; ++k)
+      e = forward_member(m, k, nb, false, y + ((long long)(k - e0) * B + b0) * 3, 3, s);
+  }
+  return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
+}
+
+int ens_mlp_gate(ens_mlp* m, long long B, const float* x, const float* y_members, float tau,
+                 float* y_mean, unsigned char* fallback, unsigned long long* n_fallback,
+                 void* stream) {
+  if (!m) return mfail(ENS_EINVAL, "null network");
+  if (B < 0) return mfail(ENS_EINVAL, "B < 0");
+  if (B == 0) return ENS_OK;
+  if (!x || !y_members || !fallback) return mfail(ENS_EINVAL, "null array");
+  k_gate<<<blocks_for(B), 256, 0, (cudaStream_t)stream>>>(B, m->E, x, y_members, m->box, tau,
+                                                          y_mean, fallback, n_fallback);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
+}
+
+int ens_mlp_check(ens_mlp* m, void* stream) {
+  if (!m) return mfail(ENS_EINVAL, "null network");
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, m->err, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return mfail(ENS_ECUDA, cudaGetErrorString(e));
+  if (h) return mfail(ENS_ECUDA, "a tensor-core wait timed out (results invalid)");
+  return ENS_OK;
+}
+
+}  // extern "C"
