@@ -104,6 +104,9 @@ typedef struct {
                              this many are idle (1..32; 0 = default).  Batching refills trades
                              idle lanes for fewer divergent refill passes. */
   int order;              /* ENS_ORDER_* (persistent schedule only) */
+  int blocks_per_sm;      /* persistent schedule: resident blocks per SM (0 = as many as fit).
+                             Fewer resident lanes each take more trajectories from the queue,
+                             which shortens the drain at the end of the queue. */
 } ens_opts;
 
 /* Fill *o with defaults: TSIT5_ADAPTIVE, F32, SOA, abstol=reltol=1e-6, maxiters=1e6, auto. */
@@ -143,14 +146,17 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
 /* Launch-shape autotuner (the occupancy tuning the paper leaves to KernelAbstractions,
  * Sec. 5.1): runs the solve of ens_solve (same arguments, outputs really written) with every
  * candidate launch shape -- block in {64, 128, 256, 512}, and for the persistent schedule
- * trajectories per thread in {1, 2}; a nonzero opts->block / opts->tpt pins that value --
+ * trajectories per thread in {1, 2} and resident blocks per SM in {all that fit, 3/4, 1/2 of
+ * that}; a nonzero opts->block / opts->tpt / opts->blocks_per_sm pins that value --
  * timing each (one warm-up, best of two), and records the fastest in a process-wide cache
  * keyed by (model, algorithm, dtype, layout, floor(log2 N), saveat or not, SM count).  Later
- * ens_solve / ens_batch_create calls with block = tpt = 0 use the cached shape.  Returns it in
- * *block / *tpt and its time in *best_ms.  Synchronises the stream. */
+ * ens_solve / ens_batch_create calls with block = tpt = blocks_per_sm = 0 use the cached
+ * shape.  Returns it in *block / *tpt / *blocks_per_sm (> 0 a cap, 0 all that fit, < 0 that
+ * many quarters of the blocks that fit) and its time in *best_ms.  Synchronises the stream. */
 int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
                  const void* tspan, const ens_opts* opts, void* out, signed char* status,
-                 int* stats, void* cuda_stream, int* block, int* tpt, float* best_ms);
+                 int* stats, void* cuda_stream, int* block, int* tpt, int* blocks_per_sm,
+                 float* best_ms);
 
 /* Batched ensembles: several sub-problems (different models, methods, sizes and time spans)
  * solved by one call -- the uneven-work case of Sec. 6.4 (trajectories whose step counts
@@ -182,6 +188,7 @@ typedef struct {
 
 typedef struct {
   int schedule, block, tpt; /* launch shape the plan uses */
+  int blocks_per_sm;        /* persistent: > 0 a cap, 0 all that fit, < 0 that fraction x 4 */
   float tuned_ms;           /* autotuned solve time of the item alone (0 if not tuned) */
   int launch_position;      /* position in the launch order (-1: empty item) */
   int graph;                /* 1 if the plan runs as a CUDA graph */
@@ -240,7 +247,9 @@ int ens_adjoint(ens_handle* h, long long N, const void* params, const void* u0, 
  * A multilayer perceptron with widths 6 -> 256 -> 256 -> 256 -> 3 and exact-erf GELU maps a
  * Lorenz problem x = (sigma, rho, beta, u0_1, u0_2, u0_3) to its state u(tf); `members`
  * independently initialised copies form an ensemble whose disagreement gates a fallback to
- * the solver.  BF16 operands, FP32 accumulation, every product on the tcgen05 tensor cores:
+ * the solver.  BF16 operands, FP32 accumulation, every product on the tcgen05 tensor cores
+ * (gelu(z) = z Phi(z), the exact erf form, with erf evaluated by Abramowitz & Stegun 7.1.26,
+ * absolute error <= 1.5e-7):
  *   x_n = bf16(2 (x - lo)/(hi - lo) - 1),  Z_l = H_{l-1} W_l^T + b_l,  H_l = bf16(gelu(Z_l)),
  *   y = Z_4 * y_std + y_mean.
  * Parameters per member: FP32, flat in the order W_1 [256][6], b_1 [256], W_2 [256][256],
@@ -278,12 +287,22 @@ int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* 
 /* Gate: y_mean [B][3] = mean over the members of y_members [members][B][3] (NULL to skip);
  * fallback[b] = 1 when x_b leaves the box or the largest per-component population standard
  * deviation over the members exceeds tau; *n_fallback (device, or NULL) is incremented by the
- * number of fallbacks. */
+ * number of fallbacks (zero it first).  With fb_index given, every fallback sample is also
+ * appended, at a slot taken from *n_fallback, to a compacted solver problem in ROWMAJOR FP32
+ * layout: fb_index[slot] = b, fb_params[slot] = (sigma, rho, beta), fb_u0[slot] = u0,
+ * fb_tspan[slot] = (t0, t1) (each array has room for B rows; slot order is arbitrary). */
 int ens_mlp_gate(ens_mlp* m, long long B, const float* x, const float* y_members, float tau,
                  float* y_mean, unsigned char* fallback, unsigned long long* n_fallback,
-                 void* cuda_stream);
+                 long long* fb_index, float* fb_params, float* fb_u0, float* fb_tspan, double t0,
+                 double t1, void* cuda_stream);
+/* y[fb_index[i]] = u[i] (rows of 3) for i < n: the solver's answers for the fallbacks. */
+int ens_mlp_scatter(long long n, const long long* fb_index, const float* u, float* y,
+                    void* cuda_stream);
 /* Synchronise the stream and report a tensor-core wait timeout of an earlier call. */
 int ens_mlp_check(ens_mlp* m, void* cuda_stream);
+/* Test aid: out[i] = gelu(z[i]) (which = 0) or gelu'(z[i]) (which = 1) evaluated exactly as the
+ * network kernels evaluate them (device arrays of n floats). */
+int ens_mlp_activation(int which, long long n, const float* z, float* out, void* cuda_stream);
 
 /* Raw Philox4x32-10 words (Salmon et al. SC'11) of the SDE streams: for trajectory
  * j < n_traj and call c < n_calls, out[(c*4 + w)*n_traj + j] = word w of

@@ -6,7 +6,7 @@ this package only marshals torch tensors into it.
 from ._lib import EnsError, lib  # noqa: F401
 from .solver import EnsembleBatch, EnsembleSolver, make_opts, normals, philox_words  # noqa: F401
 from .autograd import solve_fixed  # noqa: F401
-from .surrogate import SurrogateMLP  # noqa: F401
+from .surrogate import GatedSurrogate, SurrogateMLP  # noqa: F401
 
 __all__ = ["EnsembleBatch", "EnsembleSolver", "EnsError", "make_opts", "normals", "philox_words", "lib",
-           "solve_fixed", "SurrogateMLP"]
+           "solve_fixed", "SurrogateMLP", "GatedSurrogate"]

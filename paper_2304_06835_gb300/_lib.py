@@ -32,7 +32,7 @@ class EnsOpts(ctypes.Structure):
         ("saveat", ctypes.POINTER(ctypes.c_double)), ("n_save", ctypes.c_int),
         ("seed", ctypes.c_ulonglong), ("index_offset", ctypes.c_longlong),
         ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
-        ("refill_min", ctypes.c_int), ("order", ctypes.c_int),
+        ("refill_min", ctypes.c_int), ("order", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
     ]
 
 
@@ -47,7 +47,8 @@ class BatchItem(ctypes.Structure):
 class BatchItemInfo(ctypes.Structure):
     _fields_ = [
         ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
-        ("tuned_ms", ctypes.c_float), ("launch_position", ctypes.c_int), ("graph", ctypes.c_int),
+        ("blocks_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_float),
+        ("launch_position", ctypes.c_int), ("graph", ctypes.c_int),
     ]
 
 
@@ -81,7 +82,7 @@ SIGNATURES = {
     "ens_solve_noalloc": (_INT, [_INT, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP,
                                  _VP]),
     "ens_autotune": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP, _VP,
-                            ctypes.POINTER(_INT), ctypes.POINTER(_INT),
+                            ctypes.POINTER(_INT), ctypes.POINTER(_INT), ctypes.POINTER(_INT),
                             ctypes.POINTER(ctypes.c_float)]),
     "ens_batch_create": (_INT, [ctypes.POINTER(_VP), ctypes.POINTER(BatchItem), _INT, _INT, _VP]),
     "ens_batch_run": (_INT, [_VP, _VP]),
@@ -102,8 +103,11 @@ SIGNATURES = {
     "ens_mlp_grad": (_INT, [_VP, _INT, _LL, _VP, _VP, _VP, _VP, _VP, _VP]),
     "ens_mlp_adam": (_INT, [_VP, _INT, ctypes.c_float, _INT, _VP]),
     "ens_mlp_forward": (_INT, [_VP, _INT, _LL, _VP, _VP, _VP]),
-    "ens_mlp_gate": (_INT, [_VP, _LL, _VP, _VP, ctypes.c_float, _VP, _VP, _VP, _VP]),
+    "ens_mlp_gate": (_INT, [_VP, _LL, _VP, _VP, ctypes.c_float, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                            ctypes.c_double, ctypes.c_double, _VP]),
+    "ens_mlp_scatter": (_INT, [_LL, _VP, _VP, _VP, _VP]),
     "ens_mlp_check": (_INT, [_VP, _VP]),
+    "ens_mlp_activation": (_INT, [_INT, _LL, _VP, _VP, _VP]),
     "ens_probe_fma": (_INT, [_INT, _LL, _INT, _INT, ctypes.POINTER(ctypes.c_double), _VP]),
     "ens_last_error": (ctypes.c_char_p, []),
 }

@@ -283,6 +283,8 @@ int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
     return fail(ENS_EINVAL, "refill_min must be in [0, 32]");
   if (o->order < ENS_ORDER_AUTO || o->order > ENS_ORDER_COST)
     return fail(ENS_EINVAL, "unknown order");
+  if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64)
+    return fail(ENS_EINVAL, "blocks_per_sm must be in [0, 64]");
   if (N > 0 && (!params || !u0 || !tspan || !out)) return fail(ENS_EINVAL, "null array");
   return ENS_OK;
 }
@@ -517,10 +519,11 @@ int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, co
 
 int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
                  const void* tspan, const ens_opts* o, void* out, signed char* status,
-                 int* stats, void* stream, int* block, int* tpt, float* best_ms) {
+                 int* stats, void* stream, int* block, int* tpt, int* blocks_per_sm,
+                 float* best_ms) {
   int rc = validate(h, N, params, u0, tspan, o, out);
   if (rc) return rc;
-  if (!block || !tpt || !best_ms) return fail(ENS_EINVAL, "null result pointer");
+  if (!block || !tpt || !blocks_per_sm || !best_ms) return fail(ENS_EINVAL, "null result pointer");
   if (N == 0) return fail(ENS_EINVAL, "nothing to tune (N = 0)");
   std::lock_guard<std::mutex> lock(h->mu);
   if (N <= 0x7fffffffLL && N > h->order_cap) {
@@ -542,6 +545,7 @@ int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
   if (rc) return rc;
   *block = best.block;
   *tpt = best.tpt;
+  *blocks_per_sm = best.bps;
   return ENS_OK;
 }
 

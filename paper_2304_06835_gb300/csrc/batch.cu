@@ -43,6 +43,7 @@ LaunchCfg default_launch(const ens_opts* o, int sms) {
   c.block = o->block ? o->block : 128;
   c.tpt = o->tpt ? o->tpt : 1;
   c.num_sms = sms;
+  c.bps = o->blocks_per_sm;
   return c;
 }
 
@@ -50,7 +51,7 @@ LaunchCfg default_launch(const ens_opts* o, int sms) {
 
 LaunchCfg resolve_launch(int rhs_id, long long N, const ens_opts* o, int num_sms) {
   LaunchCfg c = default_launch(o, num_sms);
-  if (o->block == 0 && o->tpt == 0) {
+  if (o->block == 0 && o->tpt == 0 && o->blocks_per_sm == 0) {
     std::lock_guard<std::mutex> lock(g_tuned_mu);
     auto it = g_tuned.find(tune_key(rhs_id, N, o, num_sms));
     if (it != g_tuned.end() && (o->schedule == ENS_SCHED_AUTO ||
@@ -79,10 +80,14 @@ int tune_problem(int rhs_id, const ens_opts* o, const SolveArgs& a, const SolveS
     } else {
       for (int t : {1, 2}) {
         if (o->tpt && t != o->tpt) continue;
-        LaunchCfg c = base;
-        c.block = b;
-        c.tpt = t;
-        cand.push_back(c);
+        for (int f : {0, -3, -2}) {  // all resident blocks that fit, 3/4, 1/2 of them
+          if (o->blocks_per_sm && f != 0) continue;
+          LaunchCfg c = base;
+          c.block = b;
+          c.tpt = t;
+          if (!o->blocks_per_sm) c.bps = f;
+          cand.push_back(c);
+        }
       }
     }
   }
@@ -330,6 +335,7 @@ int ens_batch_info(const ens_batch* b, int item, ens_batch_item_info* info) {
   info->schedule = it.cfg.schedule;
   info->block = it.cfg.block;
   info->tpt = it.cfg.tpt;
+  info->blocks_per_sm = it.cfg.bps;
   info->tuned_ms = it.tuned_ms;
   int pos = -1;
   for (size_t k = 0; k < b->order.size(); ++k)

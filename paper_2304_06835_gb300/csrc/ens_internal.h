@@ -63,10 +63,11 @@ struct CostScratch {
 };
 
 struct LaunchCfg {
-  int schedule;  // ENS_SCHED_DIRECT or ENS_SCHED_PERSISTENT (resolved)
-  int block;
-  int tpt;
-  int num_sms;
+  int schedule = ENS_SCHED_DIRECT;  // ENS_SCHED_DIRECT or ENS_SCHED_PERSISTENT (resolved)
+  int block = 128;
+  int tpt = 1;
+  int num_sms = 1;
+  int bps = 0;   // persistent: resident blocks per SM; 0 = as many as fit; < 0: -bps/4 of that
 };
 
 // Launch one solve; returns the CUDA error of the launch.  Implemented per (precision, model)

@@ -71,14 +71,43 @@ struct GemmArgs {
   int* err;                // set to 1 when a wait for the tensor cores times out
 };
 
-constexpr int BM = 128, BK = 64, NTHREADS = 128;
+constexpr int BM = 128, BK = 64, NTHREADS = 256;
 
-__device__ __forceinline__ float gelu_f(float z) {
-  return 0.5f * z * (1.f + erff(z * 0.70710678118654752440f));
+// erf for the GELU by Abramowitz & Stegun 7.1.26 (Hastings' rational approximation):
+//   erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2},  t = 1 / (1 + p x),  x >= 0,
+// |error| <= 1.5e-7, four orders below the bf16 resolution (2^-9) of the stored activations.
+// Branch-free (CUDA's erff branches on |x| and diverges inside warps); e^{-x^2} is returned
+// too, since gelu' needs phi(z) = e^{-z^2/2} / sqrt(2 pi) with the same exponential.
+__device__ __forceinline__ float erf_as(float x, float* ex) {
+  const float ax = fabsf(x);
+  const float t = __fdividef(1.f, fmaf(0.3275911f, ax, 1.f));
+  float q = fmaf(1.061405429f, t, -1.453152027f);
+  q = fmaf(q, t, 1.421413741f);
+  q = fmaf(q, t, -0.284496736f);
+  q = fmaf(q, t, 0.254829592f);
+  q *= t;
+  const float e = ex2_approx(-(ax * ax) * 1.4426950408889634f);  // e^{-x^2}
+  *ex = e;
+  return copysignf(fmaf(-q, e, 1.f), x);
 }
+// gelu(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2   (Hendrycks & Gimpel, exact erf form)
+__device__ __forceinline__ float gelu_f(float z) {
+  float e;
+  const float er = erf_as(z * 0.70710678118654752440f, &e);
+  return 0.5f * z * (1.f + er);
+}
+// gelu'(z) = Phi(z) + z phi(z)
 __device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.f + erff(z * 0.70710678118654752440f)) +
-         z * 0.39894228040143267794f * expf(-0.5f * z * z);
+  float e;
+  const float er = erf_as(z * 0.70710678118654752440f, &e);
+  return fmaf(z * 0.39894228040143267794f, e, 0.5f * (1.f + er));
+}
+
+// (test aid) out[i] = gelu(z[i]) (which = 0) or gelu'(z[i]) (which = 1) as the kernels compute
+__global__ void k_activation(int which, long long n, const float* __restrict__ z,
+                             float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = which ? gelu_grad_f(z[i]) : gelu_f(z[i]);
 }
 
 template <int BN>
@@ -94,46 +123,49 @@ struct Tile {
   static constexpr uint32_t A_MN_LBO = (BM / 8) * 128, B_MN_LBO = (BN / 8) * 128, MN_SBO = 128;
 };
 
-template <int BN>
-__device__ __forceinline__ void load_stage(const GemmArgs& g, unsigned char* sA, unsigned char* sB,
-                                           int m0, int n0, int k0, int kend) {
-  typedef Tile<BN> TL;
-  const int tid = threadIdx.x;
-  const uint32_t a = umma::smem_addr(sA), b = umma::smem_addr(sB);
-  if (!g.a_mn) {
-    for (int c = tid; c < BM * (BK / 8); c += NTHREADS) {
-      const int m = c >> 3, kc = c & 7, gm = m0 + m, gk = k0 + kc * 8;
-      const bool ok = gm < g.M && gk < kend;
-      const bf16* src = ok ? g.A + (long long)gm * g.lda + gk : g.A;
-      umma::cp_async16(a + (m >> 3) * TL::KM_SBO + kc * 128 + (m & 7) * 16, src, ok ? 16 : 0);
-    }
-  } else {
-    for (int c = tid; c < BK * (BM / 8); c += NTHREADS) {
-      const int k = c / (BM / 8), mc = c % (BM / 8), gk = k0 + k, gm = m0 + mc * 8;
-      const bool ok = gk < kend && gm < g.M;
-      const bf16* src = ok ? g.A + (long long)gk * g.lda + gm : g.A;
-      umma::cp_async16(a + (k >> 3) * TL::A_MN_LBO + mc * 128 + (k & 7) * 16, src, ok ? 16 : 0);
-    }
+// One 64-wide K stage of both operands, 16-byte cp.async pieces.  Thread order inside a
+// warp: the 8 rows of a core matrix fastest, then 4 neighbouring core matrices, so a warp
+// fills 512 contiguous bytes of shared memory (no bank conflicts) while reading 64
+// contiguous bytes (two full sectors) from each of 8 global rows.
+template <int ROWS>
+__device__ __forceinline__ void load_kmajor(uint32_t dst, const bf16* src, long long ld, int r0,
+                                            int rlim, int k0, int kend, uint32_t sbo) {
+  // K-major tile [ROWS][BK]: piece (row, kc) -> (row/8)*sbo + kc*128 + (row%8)*16
+  for (int c = threadIdx.x; c < ROWS * (BK / 8); c += NTHREADS) {
+    const int lo = c & 7, kc = (c >> 3) & 7, hi = c >> 6;
+    const int row = hi * 8 + lo, gr = r0 + row, gk = k0 + kc * 8;
+    const bool ok = gr < rlim && gk < kend;
+    umma::cp_async16(dst + hi * sbo + kc * 128 + lo * 16, ok ? src + (long long)gr * ld + gk : src,
+                     ok ? 16 : 0);
   }
-  if (!g.b_mn) {
-    for (int c = tid; c < BN * (BK / 8); c += NTHREADS) {
-      const int n = c >> 3, kc = c & 7, gn = n0 + n, gk = k0 + kc * 8;
-      const bool ok = gn < g.N && gk < kend;
-      const bf16* src = ok ? g.B + (long long)gn * g.ldb + gk : g.B;
-      umma::cp_async16(b + (n >> 3) * TL::KM_SBO + kc * 128 + (n & 7) * 16, src, ok ? 16 : 0);
-    }
-  } else {
-    for (int c = tid; c < BK * (BN / 8); c += NTHREADS) {
-      const int k = c / (BN / 8), nc = c % (BN / 8), gk = k0 + k, gn = n0 + nc * 8;
-      const bool ok = gk < kend && gn < g.N;
-      const bf16* src = ok ? g.B + (long long)gk * g.ldb + gn : g.B;
-      umma::cp_async16(b + (k >> 3) * TL::B_MN_LBO + nc * 128 + (k & 7) * 16, src, ok ? 16 : 0);
-    }
+}
+template <int ROWS>
+__device__ __forceinline__ void load_mnmajor(uint32_t dst, const bf16* src, long long ld, int r0,
+                                             int rlim, int k0, int kend, uint32_t lbo) {
+  // MN-major tile (ROWS along M/N, BK along K): piece (k, rc) -> (k/8)*lbo + rc*128 + (k%8)*16
+  constexpr int RC = ROWS / 8;  // core matrices along M/N
+  for (int c = threadIdx.x; c < BK * RC; c += NTHREADS) {
+    const int lo = c & 7, rest = c >> 3, rc = rest % RC, hi = rest / RC;
+    const int k = hi * 8 + lo, gk = k0 + k, gr = r0 + rc * 8;
+    const bool ok = gk < kend && gr < rlim;
+    umma::cp_async16(dst + hi * lbo + rc * 128 + lo * 16, ok ? src + (long long)gk * ld + gr : src,
+                     ok ? 16 : 0);
   }
 }
 
 template <int BN>
-__global__ void __launch_bounds__(NTHREADS) k_gemm(const GemmArgs g) {
+__device__ __forceinline__ void load_stage(const GemmArgs& g, unsigned char* sA, unsigned char* sB,
+                                           int m0, int n0, int k0, int kend) {
+  typedef Tile<BN> TL;
+  const uint32_t a = umma::smem_addr(sA), b = umma::smem_addr(sB);
+  if (!g.a_mn) load_kmajor<BM>(a, g.A, g.lda, m0, g.M, k0, kend, TL::KM_SBO);
+  else load_mnmajor<BM>(a, g.A, g.lda, m0, g.M, k0, kend, TL::A_MN_LBO);
+  if (!g.b_mn) load_kmajor<BN>(b, g.B, g.ldb, n0, g.N, k0, kend, TL::KM_SBO);
+  else load_mnmajor<BN>(b, g.B, g.ldb, n0, g.N, k0, kend, TL::B_MN_LBO);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS, 1) k_gemm(const GemmArgs g) {
   typedef Tile<BN> TL;
   extern __shared__ unsigned char smraw[];
   __shared__ uint64_t bar[2];
@@ -162,10 +194,17 @@ __global__ void __launch_bounds__(NTHREADS) k_gemm(const GemmArgs g) {
     load_stage<BN>(g, sm, sm + TL::A_BYTES, m0, n0, kbeg, kend);
     umma::cp_async_commit();
   }
+  // Waits for the tensor cores are done by one thread; __syncthreads_and releases the block
+  // and shares the outcome (polling by every thread would take issue slots from the other
+  // resident block's epilogue).
   for (int kt = 0; kt < nk && ok; ++kt) {
     const int s = kt & 1;
     if (kt + 1 < nk) {
-      if (kt >= 1) ok = umma::mbar_wait(&bar[s ^ 1], ((kt - 1) >> 1) & 1);
+      if (kt >= 1) {
+        bool w = true;
+        if (tid == 0) w = umma::mbar_wait(&bar[s ^ 1], ((kt - 1) >> 1) & 1);
+        ok = __syncthreads_and(w);
+      }
       if (!ok) break;
       unsigned char* st = sm + (s ^ 1) * TL::STAGE;
       load_stage<BN>(g, st, st + TL::A_BYTES, m0, n0, kbeg + (kt + 1) * BK, kend);
@@ -192,7 +231,11 @@ __global__ void __launch_bounds__(NTHREADS) k_gemm(const GemmArgs g) {
       umma::mma_commit(&bar[s]);
     }
   }
-  if (nk > 0 && ok) ok = umma::mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+  if (nk > 0 && ok) {
+    bool w = true;
+    if (tid == 0) w = umma::mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+    ok = __syncthreads_and(w);
+  }
   if (!ok) {
     if (tid == 0) atomicExch(g.err, 1);
     umma::cp_async_wait<0>();
@@ -201,61 +244,138 @@ __global__ void __launch_bounds__(NTHREADS) k_gemm(const GemmArgs g) {
   }
   umma::fence_after();
 
-  // epilogue: warp w holds rows m0 + 32 w + lane, 16 columns per tcgen05.ld
-  const int row = m0 + warp * 32 + lane;
-  const bool live = ok && row < g.M;
-  for (int c0 = 0; c0 < BN; c0 += 16) {
-    uint32_t r[16];
-    if (nk > 0) {
-      umma::tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + c0, r);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) r[j] = 0u;
+  // Epilogue, in passes of QW columns staged through the (now idle) operand shared memory:
+  // warps w and w + 4 read TMEM lane quarter w & 3 (rows 32 (w & 3) + lane of the tile),
+  // alternating 16-column chunks; the staged pass is then written to global memory by all
+  // threads in row-contiguous (coalesced) pieces.
+  constexpr int QW = BN < 64 ? BN : 64;
+  constexpr int ZS = QW + 4, HS = QW + 8;  // staging row strides (floats, bf16)
+  float* zst = reinterpret_cast<float*>(sm);
+  bf16* hst = reinterpret_cast<bf16*>(sm + BM * ZS * 4);
+  const int lq = warp & 3, half = warp >> 2;
+  const int r = lq * 32 + lane;
+  const bool fp32_out = g.out_f32 != nullptr && g.epi != EPI_GELU_BWD;
+  const bool bf16_out = g.epi == EPI_GELU_FWD || g.epi == EPI_GELU_BWD;
+  float* obase = g.out_f32 ? g.out_f32 + (g.epi == EPI_PARTIAL
+                                              ? (long long)blockIdx.z * g.split_stride : 0LL)
+                           : nullptr;
+  for (int q = 0; q < BN / QW; ++q) {
+    const int cb = q * QW;  // first column of the pass within the tile
+    if (g.epi == EPI_GELU_BWD) {  // stage the pre-activations Z of this pass (coalesced)
+      for (int i = tid; i < BM * QW; i += NTHREADS) {
+        const int rr = i / QW, cc = i % QW, gr = m0 + rr, gc = n0 + cb + cc;
+        zst[rr * ZS + cc] =
+            (gr < g.M && gc < g.N) ? __ldg(g.aux + (long long)gr * g.ldaux + gc) : 0.f;
+      }
+      __syncthreads();
     }
-    if (!live) continue;
-    const int nb = n0 + c0;
-    float v[16];
+    for (int c16 = (QW >= 32 ? half : 0); c16 < QW / 16; c16 += (QW >= 32 ? 2 : QW / 16)) {
+      if (QW < 32 && half) break;  // a 16-wide tile needs one warp per lane quarter
+      uint32_t rv[16];
+      if (nk > 0) {
+        umma::tmem_ld16(tacc + ((uint32_t)(lq * 32) << 16) + cb + c16 * 16, rv);
+      } else {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-    if (g.epi == EPI_PARTIAL) {
-      float* o = g.out_f32 + (long long)blockIdx.z * g.split_stride + (long long)row * g.ldo + nb;
+        for (int j = 0; j < 16; ++j) rv[j] = 0u;
+      }
+      const int c0 = c16 * 16, nb = n0 + cb + c0;
+      const bool full = nb + 16 <= g.N;  // no column of this chunk is past N
+      float v[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (nb + j < g.N) o[j] = v[j];
-      continue;
-    }
-    if (g.bias) {
+      for (int j = 0; j < 16; ++j) v[j] = ok ? __uint_as_float(rv[j]) : 0.f;
+      if (g.bias && g.epi != EPI_PARTIAL) {
+        if (full) {  // 16 biases as four 16-byte loads (the bias arrays are 16-byte aligned)
+          const float4* b4 = reinterpret_cast<const float4*>(g.bias + nb);
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (nb + j < g.N) v[j] += __ldg(g.bias + nb + j);
-    }
-    if (g.epi == EPI_AFFINE) {
-      float* o = g.out_f32 + (long long)row * g.ldo + nb;
+          for (int j = 0; j < 4; ++j) {
+            const float4 b = __ldg(b4 + j);
+            v[4 * j] += b.x;
+            v[4 * j + 1] += b.y;
+            v[4 * j + 2] += b.z;
+            v[4 * j + 3] += b.w;
+          }
+        } else {
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (nb + j < g.N) {
-          const float sc = g.scale ? __ldg(g.scale + nb + j) : 1.f;
-          const float sh = g.shift ? __ldg(g.shift + nb + j) : 0.f;
-          o[j] = fmaf(v[j], sc, sh);
+          for (int j = 0; j < 16; ++j)
+            if (nb + j < g.N) v[j] += __ldg(g.bias + nb + j);
         }
-    } else if (g.epi == EPI_GELU_FWD) {
-      if (g.out_f32) {
-        float* o = g.out_f32 + (long long)row * g.ldo + nb;
+      }
+      if (g.epi == EPI_AFFINE) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (nb + j < g.N) o[j] = v[j];
+          if (nb + j < g.N) {
+            const float sc = g.scale ? __ldg(g.scale + nb + j) : 1.f;
+            const float sh = g.shift ? __ldg(g.shift + nb + j) : 0.f;
+            v[j] = fmaf(v[j], sc, sh);
+          }
       }
-      bf16* o = g.out_bf16 + (long long)row * g.ldob + nb;
+      if (fp32_out) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (nb + j < g.N) o[j] = __float2bfloat16_rn(gelu_f(v[j]));
-    } else {  // EPI_GELU_BWD
-      const float* z = g.aux + (long long)row * g.ldaux + nb;
-      bf16* o = g.out_bf16 + (long long)row * g.ldob + nb;
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(zst + r * ZS + c0 + j) =
+              make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      }
+      if (bf16_out) {
+        uint32_t pk[8];
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (nb + j < g.N) o[j] = __float2bfloat16_rn(v[j] * gelu_grad_f(__ldg(z + j)));
+        for (int j = 0; j < 16; j += 2) {
+          float a, b;
+          if (g.epi == EPI_GELU_FWD) {
+            a = gelu_f(v[j]);
+            b = gelu_f(v[j + 1]);
+          } else {
+            a = v[j] * gelu_grad_f(zst[r * ZS + c0 + j]);
+            b = v[j + 1] * gelu_grad_f(zst[r * ZS + c0 + j + 1]);
+          }
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+          pk[j / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+        }
+        *reinterpret_cast<uint4*>(hst + r * HS + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(hst + r * HS + c0 + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
     }
+    __syncthreads();
+    // write the pass: rows m0 .. m0 + 127, columns n0 + cb .. n0 + cb + QW - 1 (bounded)
+    const int ncol = min(QW, g.N - (n0 + cb));
+    if (ok && ncol > 0) {
+      if (fp32_out) {
+        const bool vec = (g.ldo % 4 == 0) && (((uintptr_t)obase & 15) == 0) && (ncol % 4 == 0) &&
+                         ((n0 + cb) % 4 == 0);
+        if (vec) {
+          const int vw = ncol / 4;
+          for (int i = tid; i < BM * vw; i += NTHREADS) {
+            const int rr = i / vw, cc = (i % vw) * 4, gr = m0 + rr;
+            if (gr < g.M)
+              *reinterpret_cast<float4*>(obase + (long long)gr * g.ldo + n0 + cb + cc) =
+                  *reinterpret_cast<const float4*>(zst + rr * ZS + cc);
+          }
+        } else {
+          for (int i = tid; i < BM * ncol; i += NTHREADS) {
+            const int rr = i / ncol, cc = i % ncol, gr = m0 + rr;
+            if (gr < g.M) obase[(long long)gr * g.ldo + n0 + cb + cc] = zst[rr * ZS + cc];
+          }
+        }
+      }
+      if (bf16_out) {
+        const bool vec = (g.ldob % 8 == 0) && (((uintptr_t)g.out_bf16 & 15) == 0) &&
+                         (ncol % 8 == 0) && ((n0 + cb) % 8 == 0);
+        if (vec) {
+          const int vw = ncol / 8;
+          for (int i = tid; i < BM * vw; i += NTHREADS) {
+            const int rr = i / vw, cc = (i % vw) * 8, gr = m0 + rr;
+            if (gr < g.M)
+              *reinterpret_cast<uint4*>(g.out_bf16 + (long long)gr * g.ldob + n0 + cb + cc) =
+                  *reinterpret_cast<const uint4*>(hst + rr * HS + cc);
+          }
+        } else {
+          for (int i = tid; i < BM * ncol; i += NTHREADS) {
+            const int rr = i / ncol, cc = i % ncol, gr = m0 + rr;
+            if (gr < g.M) g.out_bf16[(long long)gr * g.ldob + n0 + cb + cc] = hst[rr * HS + cc];
+          }
+        }
+      }
+    }
+    __syncthreads();
   }
   umma::fence_before();
   __syncthreads();
@@ -394,10 +514,19 @@ __global__ void k_init(long long n, int member, unsigned long long seed, float* 
 }
 
 // mean and population standard deviation over the members; fallback when the input leaves
-// the training box or max_j std_j > tau
+// the training box or max_j std_j > tau.  A fallback sample is appended (slot from an atomic
+// counter) to the compacted solver problem: index, params (sigma, rho, beta), u0, tspan.
+struct Compact {
+  long long* index;   // [B] or null (no compaction)
+  float* params;      // [B][3]
+  float* u0;          // [B][3]
+  float* tspan;       // [B][2]
+  float t0, t1;
+};
+
 __global__ void k_gate(long long B, int E, const float* __restrict__ x,
                        const float* __restrict__ ym, Box box, float tau, float* __restrict__ mean,
-                       unsigned char* __restrict__ fb, unsigned long long* n_fb) {
+                       unsigned char* __restrict__ fb, unsigned long long* n_fb, Compact cp) {
   const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool f = false;
   if (b < B) {
@@ -423,8 +552,31 @@ __global__ void k_gate(long long B, int E, const float* __restrict__ x,
     f = out || !(smax <= tau);
     fb[b] = f ? 1 : 0;
   }
-  const unsigned cnt = __popc(__ballot_sync(0xffffffffu, f));
-  if ((threadIdx.x & 31) == 0 && cnt && n_fb) atomicAdd(n_fb, (unsigned long long)cnt);
+  // warp-aggregated slot reservation for the compacted problem
+  const unsigned ballot = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0 && ballot && n_fb) base = atomicAdd(n_fb, (unsigned long long)__popc(ballot));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (f && cp.index && n_fb) {
+    const unsigned long long pos = base + __popc(ballot & ((1u << lane) - 1u));
+    cp.index[pos] = b;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      cp.params[pos * 3 + c] = x[b * 6 + c];
+      cp.u0[pos * 3 + c] = x[b * 6 + 3 + c];
+    }
+    cp.tspan[pos * 2] = cp.t0;
+    cp.tspan[pos * 2 + 1] = cp.t1;
+  }
+}
+
+// y[index[i]] = u[i] for the n solved fallback samples (row-major [n][3])
+__global__ void k_scatter(long long n, const long long* __restrict__ index,
+                          const float* __restrict__ u, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * 3) return;
+  y[index[i / 3] * 3 + i % 3] = u[i];
 }
 
 }  // namespace mlp
@@ -820,13 +972,37 @@ int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* 
 
 int ens_mlp_gate(ens_mlp* m, long long B, const float* x, const float* y_members, float tau,
                  float* y_mean, unsigned char* fallback, unsigned long long* n_fallback,
-                 void* stream) {
+                 long long* fb_index, float* fb_params, float* fb_u0, float* fb_tspan, double t0,
+                 double t1, void* stream) {
   if (!m) return mfail(ENS_EINVAL, "null network");
   if (B < 0) return mfail(ENS_EINVAL, "B < 0");
   if (B == 0) return ENS_OK;
   if (!x || !y_members || !fallback) return mfail(ENS_EINVAL, "null array");
+  if (fb_index && (!fb_params || !fb_u0 || !fb_tspan || !n_fallback))
+    return mfail(ENS_EINVAL, "compaction needs fb_params, fb_u0, fb_tspan and n_fallback");
+  Compact cp{fb_index, fb_params, fb_u0, fb_tspan, (float)t0, (float)t1};
   k_gate<<<blocks_for(B), 256, 0, (cudaStream_t)stream>>>(B, m->E, x, y_members, m->box, tau,
-                                                          y_mean, fallback, n_fallback);
+                                                          y_mean, fallback, n_fallback, cp);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
+}
+
+int ens_mlp_scatter(long long n, const long long* fb_index, const float* u, float* y,
+                    void* stream) {
+  if (n < 0) return mfail(ENS_EINVAL, "n < 0");
+  if (n == 0) return ENS_OK;
+  if (!fb_index || !u || !y) return mfail(ENS_EINVAL, "null array");
+  k_scatter<<<blocks_for(n * 3), 256, 0, (cudaStream_t)stream>>>(n, fb_index, u, y);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
+}
+
+int ens_mlp_activation(int which, long long n, const float* z, float* out, void* stream) {
+  if (which != 0 && which != 1) return mfail(ENS_EINVAL, "which must be 0 (gelu) or 1 (gelu')");
+  if (n < 0) return mfail(ENS_EINVAL, "n < 0");
+  if (n == 0) return ENS_OK;
+  if (!z || !out) return mfail(ENS_EINVAL, "null array");
+  k_activation<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(which, n, z, out);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
 }

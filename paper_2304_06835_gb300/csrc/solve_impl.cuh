@@ -14,6 +14,8 @@ cudaError_t persistent_grid(const LaunchCfg& cfg, int* grid) {
   cudaError_t e =
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent<I, TPT>, cfg.block, 0);
   if (e != cudaSuccess) return e;
+  if (cfg.bps > 0) bps = std::min(bps, cfg.bps);
+  else if (cfg.bps < 0) bps = std::max(1, (bps * -cfg.bps + 3) / 4);  // a quarter-step fraction
   *grid = std::max(1, bps) * cfg.num_sms;
   return cudaSuccess;
 }

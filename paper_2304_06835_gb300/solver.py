@@ -22,7 +22,7 @@ _NP_DT = {np.dtype(np.float32): _lib.F32, np.dtype(np.float64): _lib.F64}
 
 def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-6, reltol=1e-6,
               dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
-              schedule="auto", block=0, tpt=0, refill_min=0, order="auto"):
+              schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0):
     o = _lib.EnsOpts()
     _lib.lib().ens_opts_default(ctypes.byref(o))
     o.alg = _lib.ALG[alg] if isinstance(alg, str) else int(alg)
@@ -45,6 +45,7 @@ def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-
     o.tpt = int(tpt)
     o.refill_min = int(refill_min)
     o.order = _lib.ORDER[order] if isinstance(order, str) else int(order)
+    o.blocks_per_sm = int(blocks_per_sm)
     return o, keep
 
 
@@ -86,8 +87,8 @@ class EnsembleSolver:
 
     def solve(self, params, u0, tspan, alg="tsit5", *, layout="rowmajor", dt=0.0, abstol=1e-6,
               reltol=1e-6, dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
-              schedule="auto", block=0, tpt=0, refill_min=0, order="auto", want_status=True,
-              want_stats=False, out=None, status=None, stats=None, stream=None):
+              schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0,
+              want_status=True, want_stats=False, out=None, status=None, stats=None, stream=None):
         if not (params.is_cuda and u0.is_cuda and tspan.is_cuda):
             raise ValueError("params, u0 and tspan must be CUDA tensors")
         if params.dtype not in _TORCH_DT or u0.dtype != params.dtype or tspan.dtype != params.dtype:
@@ -108,7 +109,8 @@ class EnsembleSolver:
         if want_stats and stats is None:
             stats = torch.empty((3, N), dtype=torch.int32, device=dev)
         o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, dt, abstol, reltol, dt0, maxiters,
-                            saveat, seed, index_offset, schedule, block, tpt, refill_min, order)
+                            saveat, seed, index_offset, schedule, block, tpt, refill_min, order,
+                            blocks_per_sm)
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
         _lib.check(_lib.lib().ens_solve(self._h, N, _ptr(params), _ptr(u0), _ptr(tspan),
                                         ctypes.byref(o), _ptr(out), _ptr(status), _ptr(stats),
@@ -119,7 +121,8 @@ class EnsembleSolver:
     def autotune(self, params, u0, tspan, alg="tsit5", *, layout="rowmajor", out=None,
                  status=None, stats=None, stream=None, **kw):
         """Time the candidate launch shapes on these inputs (the solve really runs) and cache
-        the fastest for later solves with block = tpt = 0.  Returns (block, tpt, ms)."""
+        the fastest for later solves with block = tpt = blocks_per_sm = 0.  Returns
+        (block, tpt, blocks_per_sm, ms)."""
         N = params.shape[0] if layout == "rowmajor" else params.shape[-1]
         saveat = kw.get("saveat")
         saved = saveat is not None and len(saveat) > 0
@@ -130,13 +133,13 @@ class EnsembleSolver:
             out = torch.empty(so, dtype=params.dtype, device=dev)
         o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, **kw)
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
-        b, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        b, t, f, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
         _lib.check(_lib.lib().ens_autotune(self._h, N, _ptr(params), _ptr(u0), _ptr(tspan),
                                            ctypes.byref(o), _ptr(out), _ptr(status), _ptr(stats),
                                            ctypes.c_void_p(s), ctypes.byref(b), ctypes.byref(t),
-                                           ctypes.byref(ms)))
+                                           ctypes.byref(f), ctypes.byref(ms)))
         del keep
-        return b.value, t.value, ms.value
+        return b.value, t.value, f.value, ms.value
 
     # --------------------------------------------------------------- discrete adjoint
     def _adj_common(self, params, u0, tspan, layout):
@@ -332,6 +335,7 @@ class EnsembleBatch:
             inf = _lib.BatchItemInfo()
             _lib.check(_lib.lib().ens_batch_info(self._h, k, ctypes.byref(inf)))
             res.append({"schedule": inf.schedule, "block": inf.block, "tpt": inf.tpt,
+                        "blocks_per_sm": inf.blocks_per_sm,
                         "tuned_ms": inf.tuned_ms, "launch_position": inf.launch_position,
                         "graph": bool(inf.graph)})
         return res

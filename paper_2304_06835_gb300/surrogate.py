@@ -117,8 +117,11 @@ class SurrogateMLP:
                                               _stream(self.device)))
         return out
 
-    def gate(self, x, y_members, tau, mean=None, fallback=None, count=None):
-        """(mean [B, 3], fallback uint8 [B], n_fallback device counter)."""
+    def gate(self, x, y_members, tau, mean=None, fallback=None, count=None, compact=None,
+             t0=0.0, t1=1.0):
+        """(mean [B, 3], fallback uint8 [B], n_fallback device counter).  compact: optional
+        dict of device buffers index int64 [B], params / u0 float32 [B, 3], tspan [B, 2] that
+        receive the fallback samples as a row-major solver problem on [t0, t1]."""
         x, _ = self._xy(x)
         B = x.shape[0]
         if mean is None:
@@ -127,10 +130,17 @@ class SurrogateMLP:
             fallback = torch.empty(B, dtype=torch.uint8, device=self.device)
         if count is None:
             count = torch.zeros(1, dtype=torch.int64, device=self.device)
-        _lib.check(_lib.lib().ens_mlp_gate(self._h, B, _ptr(x), _ptr(y_members.contiguous()),
-                                           float(tau), _ptr(mean), _ptr(fallback), _ptr(count),
-                                           _stream(self.device)))
+        c = compact or {}
+        _lib.check(_lib.lib().ens_mlp_gate(
+            self._h, B, _ptr(x), _ptr(y_members.contiguous()), float(tau), _ptr(mean),
+            _ptr(fallback), _ptr(count), _ptr(c.get("index")), _ptr(c.get("params")),
+            _ptr(c.get("u0")), _ptr(c.get("tspan")), float(t0), float(t1), _stream(self.device)))
         return mean, fallback, count
+
+    def scatter(self, n, index, u, y):
+        """y[index[i]] = u[i] for i < n."""
+        _lib.check(_lib.lib().ens_mlp_scatter(int(n), _ptr(index), _ptr(u.contiguous()), _ptr(y),
+                                              _stream(self.device)))
 
     def check(self):
         _lib.check(_lib.lib().ens_mlp_check(self._h, _stream(self.device)))
@@ -164,3 +174,76 @@ class SurrogateMLP:
                 print("epoch %d loss %.3e" % (ep + 1, hist[-1]))
         self.check()
         return hist
+
+
+def lorenz_u1(solver, x, *, t1=1.0, tol=1e-10, dtype=torch.float64):
+    """u(t1) of the Lorenz problems x [N, 6] = (sigma, rho, beta, u0) by the adaptive Tsit5
+    solver (structure-of-arrays inputs), as float32 [N, 3]."""
+    xd = x.to(dtype)
+    P = xd[:, :3].t().contiguous()
+    U = xd[:, 3:].t().contiguous()
+    N = x.shape[0]
+    T = torch.zeros((2, N), dtype=dtype, device=x.device)
+    T[1] = t1
+    out, st, _ = solver.solve(P, U, T, alg="tsit5", layout="soa", abstol=tol, reltol=tol)
+    return out.t().float().contiguous(), st
+
+
+def member_spread(y_members):
+    """Largest per-component population standard deviation over the members, [B]."""
+    return y_members.double().std(dim=0, unbiased=False).max(dim=1).values
+
+
+def calibrate_tau(net, x_val, y_val, max_err):
+    """Largest gate threshold tau for which every in-box validation sample with member spread
+    <= tau has a mean-prediction error (max over components) <= max_err."""
+    ym = net.forward(x_val)
+    spread = member_spread(ym).cpu().numpy()
+    err = (ym.double().mean(dim=0) - y_val.double()).abs().max(dim=1).values.cpu().numpy()
+    order = np.argsort(spread)
+    bad = np.flatnonzero(err[order] > max_err)
+    if bad.size == 0:
+        return float(spread.max()) * 1.0001
+    k = bad[0]
+    return float(spread[order[k - 1]]) if k > 0 else 0.0
+
+
+class GatedSurrogate:
+    """Surrogate prediction with fallback: the mean of the members where they agree (spread
+    <= tau) and the input lies in the training box, the solver (FP32 adaptive Tsit5 at
+    fallback_tol) everywhere else."""
+
+    def __init__(self, net, solver, tau, *, t1=1.0, fallback_tol=1e-6):
+        self.net, self.solver, self.tau, self.t1 = net, solver, float(tau), t1
+        self.fallback_tol = fallback_tol
+        self._cap = 0
+
+    def _buffers(self, B):
+        if B > self._cap:
+            dev = self.net.device
+            self._ym = torch.empty((self.net.members, B, 3), dtype=torch.float32, device=dev)
+            self._mean = torch.empty((B, 3), dtype=torch.float32, device=dev)
+            self._fb = torch.empty(B, dtype=torch.uint8, device=dev)
+            self._cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+            self._cp = {"index": torch.empty(B, dtype=torch.int64, device=dev),
+                        "params": torch.empty((B, 3), dtype=torch.float32, device=dev),
+                        "u0": torch.empty((B, 3), dtype=torch.float32, device=dev),
+                        "tspan": torch.empty((B, 2), dtype=torch.float32, device=dev)}
+            self._cap = B
+
+    def predict(self, x):
+        """(y [B, 3] float32, fallback uint8 [B], number of fallbacks).  The outputs are views
+        of buffers reused by the next call."""
+        B = x.shape[0]
+        self._buffers(B)
+        ym = self.net.forward(x, out=self._ym[:, :B] if B == self._cap else None)
+        self._cnt.zero_()
+        mean, fb, cnt = self.net.gate(x, ym, self.tau, mean=self._mean[:B], fallback=self._fb[:B],
+                                      count=self._cnt, compact=self._cp, t0=0.0, t1=self.t1)
+        n = int(cnt.item())
+        if n:
+            c = self._cp
+            u, _, _ = self.solver.solve(c["params"][:n], c["u0"][:n], c["tspan"][:n], alg="tsit5",
+                                        abstol=self.fallback_tol, reltol=self.fallback_tol)
+            self.net.scatter(n, c["index"], u, mean)
+        return mean, fb, n

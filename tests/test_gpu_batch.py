@@ -125,12 +125,13 @@ def test_autotune_picks_a_valid_shape_and_changes_no_result():
     ref, _, _ = s.solve(Pd, Ud, Td, alg="tsit5", layout="soa", abstol=1e-6, reltol=1e-6,
                         block=128, tpt=1)
     ref = host(ref)
-    block, tpt, ms = s.autotune(Pd, Ud, Td, alg="tsit5", layout="soa", abstol=1e-6, reltol=1e-6)
-    assert block in (64, 128, 256, 512) and tpt in (1, 2) and ms > 0
+    block, tpt, bps, ms = s.autotune(Pd, Ud, Td, alg="tsit5", layout="soa", abstol=1e-6,
+                                     reltol=1e-6)
+    assert block in (64, 128, 256, 512) and tpt in (1, 2) and bps in (0, -3, -2) and ms > 0
     out, _, _ = s.solve(Pd, Ud, Td, alg="tsit5", layout="soa", abstol=1e-6, reltol=1e-6)
     np.testing.assert_array_equal(host(out), ref)
-    b2, t2, _ = s.autotune(Pd, Ud, Td, alg="tsit5", layout="soa", abstol=1e-6, reltol=1e-6,
-                           block=256)  # a pinned block restricts the search
+    b2, t2, _, _ = s.autotune(Pd, Ud, Td, alg="tsit5", layout="soa", abstol=1e-6, reltol=1e-6,
+                              block=256)  # a pinned block restricts the search
     assert b2 == 256
 
 

@@ -42,6 +42,25 @@ def net():
     m.close()
 
 
+def test_activation_within_published_error_bound():
+    """The kernels' GELU and GELU' (erf by Abramowitz & Stegun 7.1.26, |error| <= 1.5e-7)
+    against the exact erf forms in FP64."""
+    import ctypes
+    from paper_2304_06835_gb300 import _lib
+    z = np.linspace(-12, 12, 200001).astype(np.float32)
+    zd = cuda32(z)
+    out = torch.empty_like(zd)
+    for which, ref in ((0, mlp.gelu), (1, mlp.gelu_grad)):
+        _lib.check(_lib.lib().ens_mlp_activation(which, z.size, ctypes.c_void_p(zd.data_ptr()),
+                                                 ctypes.c_void_p(out.data_ptr()), None))
+        r = ref(z.astype(np.float64))
+        got = out.cpu().double().numpy()
+        # 1.5e-7 from the approximation plus the approximate reciprocal and exponential
+        # (2^-22 relative each), scaled by |z|/2 for gelu, plus float32 rounding
+        bound = 5e-7 * (0.5 * np.abs(z) + 1) + 4e-7 * np.abs(r) + 1e-7
+        assert np.all(np.abs(got - r) <= bound), np.max(np.abs(got - r) - bound)
+
+
 @pytest.mark.parametrize("B", [1, 127, 1000, 4096])
 def test_forward_matches_oracle(net, B):
     p = params(1)
