@@ -1,0 +1,309 @@
+// ens_pair.cuh -- two trajectories per thread in lockstep on the paired FP32 instructions.
+//
+// sm_100-class GPUs issue FFMA2 / FADD2 / FMUL2: one instruction applies the same FP32 operation
+// to the two halves of a register pair, rounding each exactly like the scalar instruction.  The
+// adaptive Tsit5 solve is issue-bound (the FMA pipe is ~60 % busy when every issue slot is
+// used), so a thread that advances two trajectories side by side -- lane 0 and lane 1 of
+// float2 registers -- does the stage combinations, the right-hand sides, the error estimate
+// and the norm with half the instructions.  Every lane performs exactly the operations of the
+// scalar integrator, in the same order, so each trajectory's result is bit-identical to the
+// one-trajectory-per-thread kernel.  Controller decisions, selects and the MUFU exponentials
+// stay per lane.  Used for FP32 adaptive Tsit5 on autonomous models without save times (the
+// persistent schedule with two trajectories per thread); initialisation and output reuse the
+// scalar integrator.
+#pragma once
+
+#include "ens_kernels.cuh"
+
+namespace ens {
+
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float lane(float2 v, int k) { return k ? v.y : v.x; }
+__device__ __forceinline__ void set_lane(float2& v, int k, float x) {
+  v.x = k ? v.x : x;
+  v.y = k ? x : v.y;
+}
+
+// Right-hand side on a pair of states.  Generic: the scalar f on each lane; Lorenz: the same
+// association as Lorenz<float>::f with paired instructions.
+template <class RHS>
+struct Rhs2 {
+  static constexpr int D = RHS::D, P = RHS::P;
+  static __device__ __forceinline__ void f(const float2* u, const float2* p, float2* du) {
+    float ux[D], uy[D], px[P], py[P], dx[D], dy[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      ux[j] = u[j].x;
+      uy[j] = u[j].y;
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      px[j] = p[j].x;
+      py[j] = p[j].y;
+    }
+    RHS::f(ux, px, 0.f, dx);
+    RHS::f(uy, py, 0.f, dy);
+#pragma unroll
+    for (int j = 0; j < D; ++j) du[j] = make_float2(dx[j], dy[j]);
+  }
+};
+template <>
+struct Rhs2<Lorenz<float>> {
+  static __device__ __forceinline__ void f(const float2* u, const float2* p, float2* du) {
+    du[0] = mul2(p[0], sub2(u[1], u[0]));               // sigma (y2 - y1)
+    du[1] = fma2(u[0], sub2(p[1], u[2]), neg2(u[1]));   // y1 (rho - y3) - y2
+    du[2] = fma2(u[0], u[1], neg2(mul2(p[2], u[2])));   // y1 y2 - beta y3
+  }
+};
+
+// One Tsit5 step on a pair (tsit5_step with WANT_ERR, same association).
+template <class RHS>
+__device__ __forceinline__ void tsit5_step2(const float2* u, const float2* p, float2 h,
+                                            const float2* k1, float2* unew, float2* es,
+                                            float2* k7) {
+  constexpr int D = RHS::D;
+  typedef Rhs2<RHS> F;
+  float2 U[D], k2[D], k3[D], k4[D], k5[D], k6[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) U[j] = fma2(h, mul2(bc2(float(Ts5::a21)), k1[j]), u[j]);
+  F::f(U, p, k2);
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    U[j] = fma2(h, fma2(bc2(float(Ts5::a32)), k2[j], mul2(bc2(float(Ts5::a31)), k1[j])), u[j]);
+  F::f(U, p, k3);
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    U[j] = fma2(h,
+                fma2(bc2(float(Ts5::a43)), k3[j],
+                     fma2(bc2(float(Ts5::a42)), k2[j], mul2(bc2(float(Ts5::a41)), k1[j]))),
+                u[j]);
+  F::f(U, p, k4);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    float2 s = mul2(bc2(float(Ts5::a51)), k1[j]);
+    s = fma2(bc2(float(Ts5::a52)), k2[j], s);
+    s = fma2(bc2(float(Ts5::a53)), k3[j], s);
+    s = fma2(bc2(float(Ts5::a54)), k4[j], s);
+    U[j] = fma2(h, s, u[j]);
+  }
+  F::f(U, p, k5);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    float2 s = mul2(bc2(float(Ts5::a61)), k1[j]);
+    s = fma2(bc2(float(Ts5::a62)), k2[j], s);
+    s = fma2(bc2(float(Ts5::a63)), k3[j], s);
+    s = fma2(bc2(float(Ts5::a64)), k4[j], s);
+    s = fma2(bc2(float(Ts5::a65)), k5[j], s);
+    U[j] = fma2(h, s, u[j]);
+  }
+  F::f(U, p, k6);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    float2 s = mul2(bc2(float(Ts5::a71)), k1[j]);
+    s = fma2(bc2(float(Ts5::a72)), k2[j], s);
+    s = fma2(bc2(float(Ts5::a73)), k3[j], s);
+    s = fma2(bc2(float(Ts5::a74)), k4[j], s);
+    s = fma2(bc2(float(Ts5::a75)), k5[j], s);
+    s = fma2(bc2(float(Ts5::a76)), k6[j], s);
+    unew[j] = fma2(h, s, u[j]);
+  }
+  F::f(unew, p, k7);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    float2 s = mul2(bc2(float(Ts5::bt1)), k1[j]);
+    s = fma2(bc2(float(Ts5::bt2)), k2[j], s);
+    s = fma2(bc2(float(Ts5::bt3)), k3[j], s);
+    s = fma2(bc2(float(Ts5::bt4)), k4[j], s);
+    s = fma2(bc2(float(Ts5::bt5)), k5[j], s);
+    s = fma2(bc2(float(Ts5::bt6)), k6[j], s);
+    s = fma2(bc2(float(Ts5::bt7)), k7[j], s);
+    es[j] = s;
+  }
+}
+
+// Two adaptive Tsit5 trajectories (FP32, no save times) advanced in lockstep.
+template <class RHS>
+struct AdaptivePair {
+  static_assert(RHS::autonomous, "the paired integrator passes no time to f");
+  static constexpr int D = RHS::D, P = RHS::P;
+  typedef Adaptive<RHS, float, METH_TSIT5> Scalar;
+
+  float2 u[D], fk[D], p[P];
+  float2 hi, lo;   // compensated time (Neumaier pair), per lane
+  float2 stop, thr, h;
+  float2 lq;
+  int attempts[2], rejected[2], fev0[2], st[2];
+  long long idx[2];
+
+  __device__ __forceinline__ void init(int k, long long i, const SolveArgs& a) {
+    Scalar s;
+    s.init(i, a);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      set_lane(u[j], k, s.u[j]);
+      set_lane(fk[j], k, s.fk[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) set_lane(p[j], k, s.p[j]);
+    set_lane(hi, k, s.t.hi);
+    set_lane(lo, k, s.t.lo);
+    set_lane(stop, k, s.stop);
+    set_lane(thr, k, s.stop_thr);
+    set_lane(h, k, s.h);
+    set_lane(lq, k, s.lq);
+    attempts[k] = s.attempts;
+    rejected[k] = s.rejected;
+    fev0[k] = s.fev0;
+    st[k] = s.st;
+    idx[k] = s.idx;
+  }
+
+  __device__ __forceinline__ void finish(int k, const SolveArgs& a) {
+    Scalar s;
+#pragma unroll
+    for (int j = 0; j < D; ++j) s.u[j] = lane(u[j], k);
+    s.idx = idx[k];
+    s.si = 0;
+    s.st = st[k];
+    s.attempts = attempts[k];
+    s.rejected = rejected[k];
+    s.fev0 = fev0[k];
+    s.finish(a);
+  }
+
+  // One attempt for each live lane; returns the mask of lanes that finished (arrived at tf
+  // or failed).  Finished and idle lanes keep their state.
+  __device__ __forceinline__ unsigned advance(const SolveArgs& a, bool live0, bool live1) {
+    bool live[2] = {live0, live1};
+    unsigned done = 0u;
+    const float2 rem = sub2(sub2(stop, hi), lo);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (live[k] && lane(rem, k) <= lane(thr, k)) {  // arrived at tf: t = tf
+        set_lane(hi, k, lane(stop, k));
+        set_lane(lo, k, 0.f);
+        done |= 1u << k;
+        live[k] = false;
+      }
+    }
+    if (!live[0] && !live[1]) return done;
+    bool last[2];
+    float2 hs;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      last[k] = lane(h, k) >= lane(rem, k);
+      set_lane(hs, k, last[k] ? lane(rem, k) : lane(h, k));
+    }
+    const float2 tnow = add2(hi, lo);
+    float2 unew[D], es[D], fnew[D];
+    tsit5_step2<RHS>(u, p, hs, fk, unew, es, fnew);
+    const float atol = a.abstol_f, rtol = a.reltol_f;
+    float2 r2 = bc2(0.f);
+    float2 he[D], sc[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      he[j] = mul2(hs, es[j]);
+      sc[j] = fma2(bc2(rtol),
+                   make_float2(fmaxf(fabsf(u[j].x), fabsf(unew[j].x)),
+                               fmaxf(fabsf(u[j].y), fabsf(unew[j].y))),
+                   bc2(atol));
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const float2 r = make_float2(__fdividef(he[j].x, sc[j].x), __fdividef(he[j].y, sc[j].y));
+      r2 = fma2(r, r, r2);
+    }
+    const float2 q2 = mul2(r2, bc2(1.f / float(D)));
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!live[k]) continue;
+      bool fin = true;
+#pragma unroll
+      for (int j = 0; j < D; ++j) fin = fin && isfinite(lane(unew[j], k));
+      const float qk = lane(q2, k);
+      const float hk = lane(hs, k);
+      const bool capped = attempts[k] >= a.maxiters_i;
+      const bool tiny = hk < float(M<float>::dtmin_factor) * fmaxf(1.f, fabsf(lane(tnow, k)));
+      if (capped || tiny || !fin || isnan(qk)) {
+        st[k] = capped ? ENS_TRAJ_MAXITERS : (tiny ? ENS_TRAJ_DT_MIN : ENS_TRAJ_NONFINITE);
+        attempts[k] += (capped || tiny) ? 0 : 1;
+        done |= 1u << k;
+        continue;
+      }
+      ++attempts[k];
+      const bool acc = qk <= 1.f;
+      const float L = lg2_approx(fmaxf(qk, 1e-20f));
+      const float e = acc ? __fmaf_rn(-0.35f / 5.f, L, (0.4f / 5.f) * lane(lq, k))
+                          : (-0.5f / 5.f) * L;
+      const float fac = fminf(acc ? 10.f : 1.f, fmaxf(0.2f, float(kEta) * ex2_approx(e)));
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        set_lane(u[j], k, acc ? lane(unew[j], k) : lane(u[j], k));
+        set_lane(fk[j], k, acc ? lane(fnew[j], k) : lane(fk[j], k));
+      }
+      Clock<float> t;
+      t.hi = lane(hi, k);
+      t.lo = lane(lo, k);
+      t.add(acc ? hk : 0.f);
+      t.snap(acc && last[k], lane(stop, k));
+      set_lane(hi, k, t.hi);
+      set_lane(lo, k, t.lo);
+      set_lane(lq, k, acc ? fmaxf(0.5f * L, kLog2QoldInit) : lane(lq, k));
+      rejected[k] += acc ? 0 : 1;
+      set_lane(h, k, hk * fac);
+    }
+    return done;
+  }
+};
+
+// Persistent schedule with one AdaptivePair per thread: the refill logic of k_persistent with
+// two slots, the slots being the two lanes.
+template <class RHS>
+__global__ void k_persistent_pair(const SolveArgs a) {
+  AdaptivePair<RHS> s;
+  bool act[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const long long i = queue_next(a.queue);
+    act[q] = i < a.N;
+    if (act[q]) s.init(q, a.order ? (long long)__ldg(a.order + i) : i, a);
+  }
+  bool drained = __any_sync(0xffffffffu, !act[1]);  // warp-uniform
+  for (;;) {
+    if (act[0] || act[1]) {
+      const unsigned done = s.advance(a, act[0], act[1]);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (done & (1u << q)) {
+          s.finish(q, a);
+          act[q] = false;
+        }
+    }
+    const unsigned busy = __ballot_sync(0xffffffffu, act[0] || act[1]);
+    if (drained) {
+      if (busy == 0u) break;
+      continue;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const unsigned idle = __ballot_sync(0xffffffffu, !act[q]);
+      if (__popc(idle) >= a.refill_min) {
+        bool got = true;
+        if (!act[q]) {
+          const long long i = queue_next(a.queue);
+          act[q] = i < a.N;
+          got = act[q];
+          if (act[q]) s.init(q, a.order ? (long long)__ldg(a.order + i) : i, a);
+        }
+        drained = drained || __any_sync(0xffffffffu, !got);
+      }
+    }
+  }
+}
+
+}  // namespace ens

@@ -5,8 +5,20 @@
 #include <algorithm>
 
 #include "ens_kernels.cuh"
+#include "ens_pair.cuh"
 
 namespace ens {
+
+// Integrators with a paired (two trajectories per thread on FFMA2/FADD2/FMUL2) form.
+template <class I>
+struct PairOf {
+  static constexpr bool ok = false;
+};
+template <class RHS>
+struct PairOf<Adaptive<RHS, float, METH_TSIT5>> {
+  static constexpr bool ok = RHS::autonomous;
+  typedef RHS rhs;
+};
 
 template <class I, int TPT>
 cudaError_t persistent_grid(const LaunchCfg& cfg, int* grid) {
@@ -20,8 +32,27 @@ cudaError_t persistent_grid(const LaunchCfg& cfg, int* grid) {
   return cudaSuccess;
 }
 
+template <class RHS>
+cudaError_t launch_persistent_pair(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
+  int bps = 0;
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent_pair<RHS>, cfg.block, 0);
+  if (e != cudaSuccess) return e;
+  if (cfg.bps > 0) bps = std::min(bps, cfg.bps);
+  else if (cfg.bps < 0) bps = std::max(1, (bps * -cfg.bps + 3) / 4);
+  int grid = std::max(1, bps) * cfg.num_sms;
+  const long long need = (a.N + 2LL * cfg.block - 1) / (2LL * cfg.block);
+  grid = (int)std::min<long long>(grid, std::max<long long>(1, need));
+  k_persistent_pair<RHS><<<grid, cfg.block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class I, int TPT>
 cudaError_t launch_persistent(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
+  if constexpr (TPT == 2 && PairOf<I>::ok) {
+    // two trajectories per thread in lockstep on the paired FP32 instructions (no save times)
+    if (a.n_save == 0) return launch_persistent_pair<typename PairOf<I>::rhs>(a, cfg, s);
+  }
   int grid = 0;
   cudaError_t e = persistent_grid<I, TPT>(cfg, &grid);
   if (e != cudaSuccess) return e;

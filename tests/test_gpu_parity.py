@@ -334,3 +334,43 @@ def test_solve_host_matches_device(S):
                                          want_stats=True)
     np.testing.assert_array_equal(host(a), b)
     np.testing.assert_array_equal(sa.cpu().numpy(), sb)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 33, 1000, 20001])
+def test_paired_lockstep_kernel_bit_identical(S, N):
+    """Two trajectories per thread on the paired FP32 instructions (persistent schedule, TPT 2,
+    FP32 adaptive Tsit5 without save times) give every trajectory exactly the result, status
+    and counters of the one-trajectory-per-thread kernel: uneven spans, zero-length spans,
+    a non-finite parameter and a tiny attempt cap included."""
+    P, U, T = workloads.lorenz_random(N, seed=300 + N, t1=1.0)
+    T[:, 1] = np.random.default_rng(N).uniform(0.0, 4.0, N)
+    T[::17, 1] = 0.0
+    if N > 5:
+        P[5, 0] = np.nan
+    d = lambda a: dev(a, torch.float32)
+    for kw in (dict(), dict(maxiters=40)):
+        outs = []
+        for tpt, extra in ((1, {}), (2, {}), (2, dict(refill_min=1)), (2, dict(order="index"))):
+            o, st, stats = S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5", abstol=1e-6,
+                                             reltol=1e-6, schedule="persistent", tpt=tpt,
+                                             want_stats=True, **kw, **extra)
+            outs.append((host(o), st.cpu().numpy(), stats.cpu().numpy()))
+        for cur in outs[1:]:
+            for x, y in zip(cur, outs[0]):
+                np.testing.assert_array_equal(x, y)
+    if N > 5:
+        assert outs[0][1][5] == 3  # NONFINITE
+
+
+def test_paired_lockstep_generic_rhs(S):
+    """The paired kernel with the per-lane fallback right-hand side (GBM drift, D = 1)."""
+    P, U, T = workloads.gbm_random(3001, seed=77)
+    T[:, 1] = np.random.default_rng(5).uniform(0.1, 3.0, len(T))
+    d = lambda a: dev(a, torch.float32)
+    res = []
+    for tpt in (1, 2):
+        o, st, stats = S["gbm"].solve(d(P), d(U), d(T), alg="tsit5", abstol=1e-7, reltol=1e-7,
+                                      schedule="persistent", tpt=tpt, want_stats=True)
+        res.append((host(o), stats.cpu().numpy()))
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_array_equal(res[0][1], res[1][1])
