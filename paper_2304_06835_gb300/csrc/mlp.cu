@@ -103,6 +103,40 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   return fmaf(z * 0.39894228040143267794f, e, 0.5f * (1.f + er));
 }
 
+// The same two functions on a pair of values with the paired FP32 instructions (FFMA2 / FMUL2 /
+// FADD2 round each half exactly like the scalar instruction, so each lane equals gelu_f /
+// gelu_grad_f of that value); the approximate reciprocal and exponential stay per lane.
+__device__ __forceinline__ float2 erf_as2(float2 x, float2* ex) {
+  const float2 ax = make_float2(fabsf(x.x), fabsf(x.y));
+  const float2 den = __ffma2_rn(make_float2(0.3275911f, 0.3275911f), ax, make_float2(1.f, 1.f));
+  const float2 t = make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y));
+  float2 q = __ffma2_rn(make_float2(1.061405429f, 1.061405429f), t,
+                        make_float2(-1.453152027f, -1.453152027f));
+  q = __ffma2_rn(q, t, make_float2(1.421413741f, 1.421413741f));
+  q = __ffma2_rn(q, t, make_float2(-0.284496736f, -0.284496736f));
+  q = __ffma2_rn(q, t, make_float2(0.254829592f, 0.254829592f));
+  q = __fmul2_rn(q, t);
+  const float2 a2 = __fmul2_rn(__fmul2_rn(ax, ax), make_float2(-1.4426950408889634f,
+                                                                -1.4426950408889634f));
+  const float2 e = make_float2(ex2_approx(a2.x), ex2_approx(a2.y));
+  *ex = e;
+  const float2 y = __ffma2_rn(make_float2(-q.x, -q.y), e, make_float2(1.f, 1.f));
+  return make_float2(copysignf(y.x, x.x), copysignf(y.y, x.y));
+}
+__device__ __forceinline__ float2 gelu_f2(float2 z) {
+  float2 e;
+  const float2 er = erf_as2(__fmul2_rn(z, make_float2(0.70710678118654752440f,
+                                                      0.70710678118654752440f)), &e);
+  return __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), z), __fadd2_rn(make_float2(1.f, 1.f), er));
+}
+__device__ __forceinline__ float2 gelu_grad_f2(float2 z) {
+  float2 e;
+  const float2 er = erf_as2(__fmul2_rn(z, make_float2(0.70710678118654752440f,
+                                                      0.70710678118654752440f)), &e);
+  return __ffma2_rn(__fmul2_rn(z, make_float2(0.39894228040143267794f, 0.39894228040143267794f)),
+                    e, __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(make_float2(1.f, 1.f), er)));
+}
+
 // (test aid) out[i] = gelu(z[i]) (which = 0) or gelu'(z[i]) (which = 1) as the kernels compute
 __global__ void k_activation(int which, long long n, const float* __restrict__ z,
                              float* __restrict__ out) {
@@ -130,26 +164,43 @@ struct Tile {
 template <int ROWS>
 __device__ __forceinline__ void load_kmajor(uint32_t dst, const bf16* src, long long ld, int r0,
                                             int rlim, int k0, int kend, uint32_t sbo) {
-  // K-major tile [ROWS][BK]: piece (row, kc) -> (row/8)*sbo + kc*128 + (row%8)*16
-  for (int c = threadIdx.x; c < ROWS * (BK / 8); c += NTHREADS) {
-    const int lo = c & 7, kc = (c >> 3) & 7, hi = c >> 6;
-    const int row = hi * 8 + lo, gr = r0 + row, gk = k0 + kc * 8;
-    const bool ok = gr < rlim && gk < kend;
-    umma::cp_async16(dst + hi * sbo + kc * 128 + lo * 16, ok ? src + (long long)gr * ld + gk : src,
-                     ok ? 16 : 0);
+  // K-major tile [ROWS][BK]: piece (row, kc) -> (row/8)*sbo + kc*128 + (row%8)*16.  Thread t
+  // owns kc = (t/8)%8 and rows (t/64)*8 + t%8 + 32 i, i < ROWS/32 (constant trip count).
+  constexpr int PIECES = ROWS * (BK / 8);
+  constexpr int IT = (PIECES + NTHREADS - 1) / NTHREADS;
+  const int t = threadIdx.x, lo = t & 7, kc = (t >> 3) & 7, row0 = (t >> 6) * 8 + lo;
+  if (PIECES < NTHREADS && t >= PIECES) return;  // small tile: the first PIECES threads
+  const int gk = k0 + kc * 8;
+  const bool kok = gk < kend;
+  const bf16* p = src + (long long)(r0 + row0) * ld + gk;
+  const long long step = 32 * ld;
+  uint32_t d = dst + (t >> 6) * sbo + kc * 128 + lo * 16;
+#pragma unroll
+  for (int i = 0; i < IT; ++i) {
+    const bool ok = kok && (r0 + row0 + 32 * i) < rlim;
+    umma::cp_async16(d, ok ? p : src, ok ? 16 : 0);
+    p += step;
+    d += 4 * sbo;
   }
 }
 template <int ROWS>
 __device__ __forceinline__ void load_mnmajor(uint32_t dst, const bf16* src, long long ld, int r0,
                                              int rlim, int k0, int kend, uint32_t lbo) {
-  // MN-major tile (ROWS along M/N, BK along K): piece (k, rc) -> (k/8)*lbo + rc*128 + (k%8)*16
-  constexpr int RC = ROWS / 8;  // core matrices along M/N
-  for (int c = threadIdx.x; c < BK * RC; c += NTHREADS) {
-    const int lo = c & 7, rest = c >> 3, rc = rest % RC, hi = rest / RC;
-    const int k = hi * 8 + lo, gk = k0 + k, gr = r0 + rc * 8;
+  // MN-major tile (ROWS along M/N, BK along K): piece (k, rc) -> (k/8)*lbo + rc*128 +
+  // (k%8)*16.  Thread t owns k%8 = t%8; pieces walk rc fastest, then the k groups.
+  constexpr int RC = ROWS / 8;
+  constexpr int PIECES = BK * RC;
+  constexpr int IT = (PIECES + NTHREADS - 1) / NTHREADS;
+  const int t = threadIdx.x, lo = t & 7;
+  if (PIECES < NTHREADS && t >= PIECES) return;  // small tile: the first PIECES threads
+#pragma unroll
+  for (int i = 0; i < IT; ++i) {
+    const int rest = (t >> 3) + i * (NTHREADS / 8);
+    const int rc = rest % RC, hi = rest / RC;
+    const int gk = k0 + hi * 8 + lo, gr = r0 + rc * 8;
     const bool ok = gk < kend && gr < rlim;
-    umma::cp_async16(dst + hi * lbo + rc * 128 + lo * 16, ok ? src + (long long)gk * ld + gr : src,
-                     ok ? 16 : 0);
+    umma::cp_async16(dst + hi * lbo + rc * 128 + lo * 16,
+                     ok ? src + (long long)gk * ld + gr : src, ok ? 16 : 0);
   }
 }
 
@@ -165,7 +216,7 @@ __device__ __forceinline__ void load_stage(const GemmArgs& g, unsigned char* sA,
 }
 
 template <int BN>
-__global__ void __launch_bounds__(NTHREADS, 1) k_gemm(const GemmArgs g) {
+__global__ void __launch_bounds__(NTHREADS, 2) k_gemm(const GemmArgs g) {
   typedef Tile<BN> TL;
   extern __shared__ unsigned char smraw[];
   __shared__ uint64_t bar[2];
@@ -289,10 +340,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm(const GemmArgs g) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const float4 b = __ldg(b4 + j);
-            v[4 * j] += b.x;
-            v[4 * j + 1] += b.y;
-            v[4 * j + 2] += b.z;
-            v[4 * j + 3] += b.w;
+            const float2 s0 = __fadd2_rn(make_float2(v[4 * j], v[4 * j + 1]), make_float2(b.x, b.y));
+            const float2 s1 =
+                __fadd2_rn(make_float2(v[4 * j + 2], v[4 * j + 3]), make_float2(b.z, b.w));
+            v[4 * j] = s0.x;
+            v[4 * j + 1] = s0.y;
+            v[4 * j + 2] = s1.x;
+            v[4 * j + 3] = s1.y;
           }
         } else {
 #pragma unroll
@@ -319,15 +373,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm(const GemmArgs g) {
         uint32_t pk[8];
 #pragma unroll
         for (int j = 0; j < 16; j += 2) {
-          float a, b;
+          float2 ab;
           if (g.epi == EPI_GELU_FWD) {
-            a = gelu_f(v[j]);
-            b = gelu_f(v[j + 1]);
+            ab = gelu_f2(make_float2(v[j], v[j + 1]));
           } else {
-            a = v[j] * gelu_grad_f(zst[r * ZS + c0 + j]);
-            b = v[j + 1] * gelu_grad_f(zst[r * ZS + c0 + j + 1]);
+            const float2 z2 = *reinterpret_cast<const float2*>(zst + r * ZS + c0 + j);
+            ab = __fmul2_rn(make_float2(v[j], v[j + 1]), gelu_grad_f2(z2));
           }
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(ab.x, ab.y);
           pk[j / 2] = *reinterpret_cast<const uint32_t*>(&h2);
         }
         *reinterpret_cast<uint4*>(hst + r * HS + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -341,7 +394,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm(const GemmArgs g) {
       if (fp32_out) {
         const bool vec = (g.ldo % 4 == 0) && (((uintptr_t)obase & 15) == 0) && (ncol % 4 == 0) &&
                          ((n0 + cb) % 4 == 0);
-        if (vec) {
+        if (vec && ncol == QW) {  // full pass: constant width
+          constexpr int VW = QW / 4;
+#pragma unroll
+          for (int i = tid; i < BM * VW; i += NTHREADS) {
+            const int rr = i / VW, cc = (i % VW) * 4, gr = m0 + rr;
+            if (gr < g.M)
+              *reinterpret_cast<float4*>(obase + (long long)gr * g.ldo + n0 + cb + cc) =
+                  *reinterpret_cast<const float4*>(zst + rr * ZS + cc);
+          }
+        } else if (vec) {
           const int vw = ncol / 4;
           for (int i = tid; i < BM * vw; i += NTHREADS) {
             const int rr = i / vw, cc = (i % vw) * 4, gr = m0 + rr;
@@ -359,7 +421,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gemm(const GemmArgs g) {
       if (bf16_out) {
         const bool vec = (g.ldob % 8 == 0) && (((uintptr_t)g.out_bf16 & 15) == 0) &&
                          (ncol % 8 == 0) && ((n0 + cb) % 8 == 0);
-        if (vec) {
+        if (vec && ncol == QW) {  // full pass: constant width
+          constexpr int VW = QW / 8;
+#pragma unroll
+          for (int i = tid; i < BM * VW; i += NTHREADS) {
+            const int rr = i / VW, cc = (i % VW) * 8, gr = m0 + rr;
+            if (gr < g.M)
+              *reinterpret_cast<uint4*>(g.out_bf16 + (long long)gr * g.ldob + n0 + cb + cc) =
+                  *reinterpret_cast<const uint4*>(hst + rr * HS + cc);
+          }
+        } else if (vec) {
           const int vw = ncol / 8;
           for (int i = tid; i < BM * vw; i += NTHREADS) {
             const int rr = i / vw, cc = (i % vw) * 8, gr = m0 + rr;
