@@ -281,8 +281,13 @@ int ens_mlp_grad(ens_mlp* m, int member, long long B, const float* x, const floa
 /* One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8, step count t >= 1) of one
  * member with the gradient of the last ens_mlp_grad call. */
 int ens_mlp_adam(ens_mlp* m, int member, float lr, int t, void* cuda_stream);
-/* Inference: y [E'][B][3] for member (E' = 1) or all members (member = -1, E' = members). */
-int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* y,
+/* Inference: y [E'][B][3] for member (E' = 1) or all members (member = -1, E' = members).
+ * By default one fused persistent kernel computes all layers of all requested members with
+ * the activations kept on chip (warp-specialised: TMA weight streaming, tcgen05 MMAs of two
+ * 128-sample tiles in flight, epilogue warps); flags = ENS_MLP_LAYERWISE runs the same
+ * arithmetic layer by layer through global memory (identical results). */
+#define ENS_MLP_LAYERWISE 1
+int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* y, int flags,
                     void* cuda_stream);
 /* Gate: y_mean [B][3] = mean over the members of y_members [members][B][3] (NULL to skip);
  * fallback[b] = 1 when x_b leaves the box or the largest per-component population standard

@@ -650,6 +650,287 @@ __global__ void k_scatter(long long n, const long long* __restrict__ index,
   y[index[i / 3] * 3 + i % 3] = u[i];
 }
 
+
+// ------------------------------------------------------------------------------ fused forward
+// Inference of all members in one persistent kernel with the activations kept on chip.  A CTA
+// owns two 128-sample tiles at a time (slots 0 and 1), each with its own FP32 accumulator in
+// TMEM (256 columns) and its own activation buffer H in shared memory (128 x 256 bf16 in the
+// K-major core-matrix layout the next layer's MMA reads).  Warp roles:
+//   warp 0      producer: TMA bulk copies of the input tiles and of the weight chunks (packed
+//               beforehand in the exact shared-memory layout) into S stage buffers;
+//   warp 1      MMA issuer: per (member, layer, slot) the K-chunks of tcgen05.mma, committing
+//               each stage back to the producer and the finished accumulator to the epilogue;
+//   warps 2-17  four epilogue groups of four warps, two per slot (alternate 16-column
+//               chunks; a group's warps cover the four TMEM lane quarters): TMEM -> bias,
+//               GELU -> bf16 H (or, after the last layer, y = (z + b4) * y_std + y_mean).
+// Jobs run in the order member, layer, slot, so the MMAs of one slot overlap the epilogue of
+// the other.  The arithmetic per output equals the layer-by-layer k_gemm path (same K order,
+// same epilogue operations), so the results are identical.
+namespace fused {
+constexpr int S = 2;                                  // weight stages
+constexpr int NT = 576;                               // 18 warps: producer, MMA, 16 epilogue
+constexpr uint32_t H_BYTES = 65536, X_BYTES = 4096, W_BYTES = 32768;
+constexpr uint32_t OFF_X = 2 * H_BYTES, OFF_W = OFF_X + 2 * X_BYTES;
+constexpr uint32_t SMEM = OFF_W + S * W_BYTES + 1024;  // dynamic shared memory (+ alignment)
+constexpr long long NWP = 139264;                     // packed bf16 weights per member
+// layer l streams nchunks(l) chunks: W1 whole (8 KB), W2 / W3 in K-chunks of 64 (32 KB),
+// W4 whole (8 KB)
+__host__ __device__ constexpr int nchunks(int l) { return (l == 1 || l == 2) ? 4 : 1; }
+__host__ __device__ constexpr uint32_t chunk_bytes(int l) {
+  return (l == 1 || l == 2) ? 32768u : 8192u;
+}
+__host__ __device__ constexpr long long woff(int l) {  // bf16 elements
+  return l == 0 ? 0 : l == 1 ? 4096 : l == 2 ? 69632 : 135168;
+}
+}  // namespace fused
+
+// element offset of (n, k) in a K-major core-matrix tile whose 8-row groups are `sbo_el`
+// elements apart
+__device__ __forceinline__ long long cm_off(int n, int k, int sbo_el) {
+  return (long long)(n >> 3) * sbo_el + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
+}
+
+// Pack one member's weights for the fused kernel: W1 [256][16] (SBO 256 B), W2 and W3 as four
+// K-chunks of [256][64] (SBO 1024 B), W4 [16][256] (SBO 4096 B), zero padding.
+__global__ void k_pack(const float* __restrict__ p, bf16* __restrict__ wp) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= fused::NWP) return;
+  float v = 0.f;
+  long long dst;
+  if (i < 4096) {  // W1: n < 256, k < 16
+    const int n = (int)(i / 16), k = (int)(i % 16);
+    v = k < 6 ? p[OFF_W1 + n * 6 + k] : 0.f;
+    dst = cm_off(n, k, 128);
+  } else if (i < 4096 + 2 * 65536) {  // W2 / W3: n < 256, k < 256
+    const long long j = (i - 4096) % 65536;
+    const int which = (int)((i - 4096) / 65536);
+    const int n = (int)(j / 256), k = (int)(j % 256);
+    v = p[(which ? OFF_W3 : OFF_W2) + (long long)n * 256 + k];
+    dst = fused::woff(1 + which) + (k / 64) * 16384 + cm_off(n, k % 64, 512);
+  } else {  // W4: n < 16 (3 real), k < 256
+    const long long j = i - 135168;
+    const int n = (int)(j / 256), k = (int)(j % 256);
+    v = n < 3 ? p[OFF_W4 + n * 256 + k] : 0.f;
+    dst = fused::woff(3) + cm_off(n, k, 2048);
+  }
+  wp[dst] = __float2bfloat16_rn(v);
+}
+
+// Normalised inputs in tiles of 128 rows, each tile in the K-major core-matrix layout
+// (SBO 256 B); rows past B are zero.
+__global__ void k_input_tiled(long long B, long long rows, const float* __restrict__ x, Box box,
+                              bf16* __restrict__ xt) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * PAD_IN) return;
+  const long long b = i / PAD_IN;
+  const int c = (int)(i % PAD_IN);
+  float v = 0.f;
+  if (b < B && c < 6) v = (x[b * 6 + c] - box.lo[c]) * box.inv[c] - 1.f;
+  xt[(b / 128) * 2048 + cm_off((int)(b % 128), c, 128)] = __float2bfloat16_rn(v);
+}
+
+struct FusedArgs {
+  long long B;          // rows of this call (tiles cover ceil(B / 128) * 128 rows)
+  long long ystride;    // rows of each member's block of y
+  int ntiles, E;
+  const bf16* xt;       // [ntiles][2048] tiled normalised inputs
+  const bf16* wp;       // [E][NWP] packed weights
+  const float* bias;    // [E][NBB] padded biases
+  const float* ystat;   // y_mean[3], y_std[3]
+  float* y;             // [E][B][3]
+  int* err;
+};
+
+__global__ void __launch_bounds__(fused::NT, 1) k_mlp_fused(const FusedArgs f) {
+  using namespace fused;
+  extern __shared__ unsigned char smraw[];
+  __shared__ uint64_t wfull[S], wempty[S], xfull[2], xempty[2], dfull[2], hready[2];
+  __shared__ uint32_t tslot;
+  __shared__ volatile int abort_flag;
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = umma::smem_addr(sm);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int npairs = (f.ntiles + 1) / 2;
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      umma::mbar_init(&wfull[i], 1);
+      umma::mbar_init(&wempty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      umma::mbar_init(&xfull[i], 1);
+      umma::mbar_init(&xempty[i], 1);
+      umma::mbar_init(&dfull[i], 1);
+      umma::mbar_init(&hready[i], 256);
+    }
+    abort_flag = 0;
+    umma::mbar_init_fence();
+  }
+  if (warp == 0) umma::tmem_alloc<512>(&tslot);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tbase = tslot;
+  auto fail = [&]() {
+    abort_flag = 1;
+    atomicExch(f.err, 1);
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------------- producer
+    int use = 0, xuse[2] = {0, 0};
+    for (int pr = blockIdx.x; pr < npairs && !abort_flag; pr += gridDim.x) {
+      const int ns = (2 * pr + 1 < f.ntiles) ? 2 : 1;
+      for (int sl = 0; sl < ns && !abort_flag; ++sl) {
+        if (!umma::mbar_wait(&xempty[sl], (xuse[sl] & 1) ^ 1)) { fail(); break; }
+        umma::mbar_arrive_expect_tx(&xfull[sl], X_BYTES);
+        umma::bulk_g2s(sbase + OFF_X + sl * X_BYTES, f.xt + (long long)(2 * pr + sl) * 2048,
+                       X_BYTES, &xfull[sl]);
+        ++xuse[sl];
+      }
+      for (int m = 0; m < f.E && !abort_flag; ++m)
+        for (int l = 0; l < 4 && !abort_flag; ++l)
+          for (int sl = 0; sl < ns && !abort_flag; ++sl)
+            for (int c = 0; c < nchunks(l); ++c) {
+              const int st = use % S, n = use / S;
+              if (!umma::mbar_wait(&wempty[st], (n & 1) ^ 1)) { fail(); break; }
+              umma::mbar_arrive_expect_tx(&wfull[st], chunk_bytes(l));
+              umma::bulk_g2s(sbase + OFF_W + st * W_BYTES,
+                             f.wp + (long long)m * NWP + woff(l) + c * (chunk_bytes(l) / 2),
+                             chunk_bytes(l), &wfull[st]);
+              ++use;
+            }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    int use = 0, J[2] = {0, 0}, xuse[2] = {0, 0};
+    for (int pr = blockIdx.x; pr < npairs && !abort_flag; pr += gridDim.x) {
+      const int ns = (2 * pr + 1 < f.ntiles) ? 2 : 1;
+      for (int m = 0; m < f.E && !abort_flag; ++m)
+        for (int l = 0; l < 4 && !abort_flag; ++l)
+          for (int sl = 0; sl < ns && !abort_flag; ++sl) {
+            if (J[sl] > 0 && !umma::mbar_wait(&hready[sl], (J[sl] - 1) & 1)) { fail(); break; }
+            if (l == 0 && m == 0 && !umma::mbar_wait(&xfull[sl], xuse[sl] & 1)) { fail(); break; }
+            umma::fence_after();
+            const uint32_t tacc = tbase + sl * 256;
+            const uint32_t hA = sbase + sl * H_BYTES;
+            const uint32_t idesc = umma::idesc_bf16(128, l == 3 ? 16 : 256, 0, 0);
+            for (int c = 0; c < nchunks(l) && !abort_flag; ++c) {
+              const int st = use % S, n = use / S;
+              if (!umma::mbar_wait(&wfull[st], n & 1)) { fail(); break; }
+              umma::fence_after();
+              const uint32_t wB = sbase + OFF_W + st * W_BYTES;
+              if (l == 0) {
+                umma::mma_bf16(tacc, umma::desc(sbase + OFF_X + sl * X_BYTES, 128, 256),
+                               umma::desc(wB, 128, 256), idesc, 0u);
+              } else if (l < 3) {
+                for (int j = 0; j < 4; ++j)
+                  umma::mma_bf16(tacc, umma::desc(hA + (c * 4 + j) * 256, 128, 4096),
+                                 umma::desc(wB + j * 256, 128, 1024), idesc,
+                                 (c > 0 || j > 0) ? 1u : 0u);
+              } else {
+                for (int j = 0; j < 16; ++j)
+                  umma::mma_bf16(tacc, umma::desc(hA + j * 256, 128, 4096),
+                                 umma::desc(wB + j * 256, 128, 4096), idesc, j > 0 ? 1u : 0u);
+              }
+              umma::mma_commit(&wempty[st]);
+              ++use;
+            }
+            umma::mma_commit(&dfull[sl]);
+            if (l == 0 && m == f.E - 1) {
+              umma::mma_commit(&xempty[sl]);
+              ++xuse[sl];
+            }
+            ++J[sl];
+          }
+    }
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------------- epilogue groups
+    const int grp = (warp - 2) >> 2, sl = grp >> 1, half = grp & 1, lq = warp & 3;
+    const int r = lq * 32 + lane;
+    int J = 0;
+    for (int pr = blockIdx.x; pr < npairs && !abort_flag; pr += gridDim.x) {
+      if (sl == 1 && 2 * pr + 1 >= f.ntiles) continue;
+      const long long grow = (long long)(2 * pr + sl) * 128 + r;
+      for (int m = 0; m < f.E && !abort_flag; ++m)
+        for (int l = 0; l < 4 && !abort_flag; ++l) {
+          // every lane waits; the outcome is made warp-uniform so that a time-out never
+          // leaves part of a warp inside the warp-collective tcgen05.ld below
+          const bool got = __all_sync(0xffffffffu, umma::mbar_wait(&dfull[sl], J & 1));
+          if (!got) { fail(); break; }
+          umma::fence_after();
+          const uint32_t trow = tbase + sl * 256 + ((uint32_t)(lq * 32) << 16);
+          const float* bias = f.bias + (long long)m * NBB + (l == 0 ? BB1 : l == 1 ? BB2 : l == 2 ? BB3 : BB4);
+          if (l < 3) {
+            unsigned char* hrow = sm + sl * H_BYTES + (r >> 3) * 4096 + (r & 7) * 16;
+            // software pipeline over this warp's 8 chunks: the TMEM load and the biases of
+            // chunk i + 1 are in flight while chunk i is evaluated
+            uint32_t ra[16], rb[16];
+            float4 ba[4], bb[4];
+            umma::tmem_ld16_issue(trow + half * 16, ra);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ba[j] = __ldg(reinterpret_cast<const float4*>(bias + half * 16) + j);
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+              const int c16 = half + 2 * it;
+              uint32_t (&cur)[16] = (it & 1) ? rb : ra;
+              uint32_t (&nxt)[16] = (it & 1) ? ra : rb;
+              float4 (&bc)[4] = (it & 1) ? bb : ba;
+              float4 (&bn)[4] = (it & 1) ? ba : bb;
+              umma::tmem_ld_wait(cur);
+              if (it < 7) {
+                umma::tmem_ld16_issue(trow + (c16 + 2) * 16, nxt);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  bn[j] = __ldg(reinterpret_cast<const float4*>(bias + (c16 + 2) * 16) + j);
+              }
+              uint32_t pk[8];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const float4 b = bc[j];
+                const float2 s0 = __fadd2_rn(make_float2(__uint_as_float(cur[4 * j]),
+                                                         __uint_as_float(cur[4 * j + 1])),
+                                             make_float2(b.x, b.y));
+                const float2 s1 = __fadd2_rn(make_float2(__uint_as_float(cur[4 * j + 2]),
+                                                         __uint_as_float(cur[4 * j + 3])),
+                                             make_float2(b.z, b.w));
+                const float2 g0 = gelu_f2(s0), g1 = gelu_f2(s1);
+                const __nv_bfloat162 h0 = __floats2bfloat162_rn(g0.x, g0.y);
+                const __nv_bfloat162 h1 = __floats2bfloat162_rn(g1.x, g1.y);
+                pk[2 * j] = *reinterpret_cast<const uint32_t*>(&h0);
+                pk[2 * j + 1] = *reinterpret_cast<const uint32_t*>(&h1);
+              }
+              *reinterpret_cast<uint4*>(hrow + (c16 * 2) * 128) =
+                  make_uint4(pk[0], pk[1], pk[2], pk[3]);
+              *reinterpret_cast<uint4*>(hrow + (c16 * 2 + 1) * 128) =
+                  make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+            umma::fence_proxy_async();  // H is read next by the tensor cores (async proxy)
+          } else if (half == 0) {
+            uint32_t rv[16];
+            umma::tmem_ld16(trow, rv);
+            if (grow < f.B) {
+              float* yo = f.y + ((long long)m * f.ystride + grow) * 3;
+#pragma unroll
+              for (int j = 0; j < 3; ++j)
+                yo[j] = fmaf(__uint_as_float(rv[j]) + __ldg(bias + j), __ldg(f.ystat + 3 + j),
+                             __ldg(f.ystat + j));
+            }
+          }
+          umma::fence_before();
+          umma::mbar_arrive(&hready[sl]);
+          ++J;
+        }
+    }
+  }
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();  // the producer lane joins the rest of its warp before the collective free
+    umma::fence_after();
+    umma::tmem_dealloc<512>(tbase);
+  }
+}
+
 }  // namespace mlp
 }  // namespace ens
 
@@ -677,6 +958,9 @@ struct ens_mlp {
   bf16* dz4;      // [bmax][16]
   bf16* dz[2];    // [bmax][256]
   float* part;    // [splits_max][256][256]
+  bf16* wp;       // [E][fused::NWP] weights packed for the fused forward
+  bf16* xt;       // [bmax / 128][2048] tiled normalised inputs of the fused forward
+  int num_sms;
   double* loss;
   int* err;
   void* block;    // single allocation holding everything above
@@ -859,6 +1143,8 @@ int ens_mlp_create(ens_mlp** out, int members, long long batch_max, const double
   const long long part_elems = std::max<long long>((long long)m->splits_max * HID * HID,
                                                    (Bm / 256 + 1) * HID);
   long long o_part = off; off += up(4 * part_elems);
+  long long o_wp = off; off += up(2 * E * fused::NWP);
+  long long o_xt = off; off += up(2 * Bm * PAD_IN);
   long long o_loss = off; off += up(8);
   long long o_err = off; off += up(4);
   if (cudaMalloc(&m->block, off) != cudaSuccess) {
@@ -883,9 +1169,17 @@ int ens_mlp_create(ens_mlp** out, int members, long long batch_max, const double
   m->dz4 = (bf16*)(b + o_dz4);
   for (int l = 0; l < 2; ++l) m->dz[l] = (bf16*)(b + o_dz[l]);
   m->part = (float*)(b + o_part);
+  m->wp = (bf16*)(b + o_wp);
+  m->xt = (bf16*)(b + o_xt);
   m->loss = (double*)(b + o_loss);
   m->err = (int*)(b + o_err);
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    m->num_sms = 1;
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   const float ys[6] = {0.f, 0.f, 0.f, 1.f, 1.f, 1.f};
   cudaError_t e = cudaMemcpyAsync(m->ystat, ys, sizeof(ys), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->one3, ys, sizeof(ys), cudaMemcpyHostToDevice, s);
@@ -895,6 +1189,7 @@ int ens_mlp_create(ens_mlp** out, int members, long long batch_max, const double
   for (int k = 0; k < members && e == cudaSuccess; ++k) {
     k_init<<<blocks_for(NP), 256, 0, s>>>(NP, k, seed, m->p + k * NP);
     k_refresh<<<blocks_for(NWB), 256, 0, s>>>(m->p + k * NP, m->wb + k * NWB, m->bb + k * NBB);
+    k_pack<<<blocks_for(fused::NWP), 256, 0, s>>>(m->p + k * NP, m->wp + k * fused::NWP);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host arrays above are stack memory
@@ -941,6 +1236,7 @@ int ens_mlp_params(ens_mlp* m, int member, float* get, const float* set, void* s
     e = cudaMemcpyAsync(p, set, 4 * NP, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) {
       k_refresh<<<blocks_for(NWB), 256, 0, s>>>(p, m->wb + member * NWB, m->bb + member * NBB);
+      k_pack<<<blocks_for(fused::NWP), 256, 0, s>>>(p, m->wp + member * fused::NWP);
       e = cudaGetLastError();
     }
   }
@@ -1018,19 +1314,46 @@ int ens_mlp_adam(ens_mlp* m, int member, float lr, int t, void* stream) {
   k_adam<<<blocks_for(NP), 256, 0, s>>>(NP, m->p + o, m->g, m->am + o, m->av + o, lr, b1, b2,
                                         1e-8f, c1, c2);
   k_refresh<<<blocks_for(NWB), 256, 0, s>>>(m->p + o, m->wb + member * NWB, m->bb + member * NBB);
+  k_pack<<<blocks_for(fused::NWP), 256, 0, s>>>(m->p + o, m->wp + member * fused::NWP);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
 }
 
-int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* y, void* stream) {
+int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* y, int flags,
+                    void* stream) {
   if (!m) return mfail(ENS_EINVAL, "null network");
   if (member < -1 || member >= m->E) return mfail(ENS_EINVAL, "member out of range");
   if (B < 0) return mfail(ENS_EINVAL, "B < 0");
+  if (flags & ~ENS_MLP_LAYERWISE) return mfail(ENS_EINVAL, "unknown flags");
   if (B == 0) return ENS_OK;
   if (!x || !y) return mfail(ENS_EINVAL, "null array");
   cudaStream_t s = (cudaStream_t)stream;
   const int e0 = member < 0 ? 0 : member, e1 = member < 0 ? m->E : member + 1;
   cudaError_t e = cudaSuccess;
+  if (!(flags & ENS_MLP_LAYERWISE)) {
+    e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             fused::SMEM);
+    for (long long b0 = 0; b0 < B && e == cudaSuccess; b0 += m->bmax) {
+      const long long nb = std::min(m->bmax, B - b0);
+      const long long rows = (nb + 127) / 128 * 128;
+      k_input_tiled<<<blocks_for(rows * PAD_IN), 256, 0, s>>>(nb, rows, x + b0 * 6, m->box, m->xt);
+      FusedArgs f;
+      f.B = nb;
+      f.ystride = B;
+      f.ntiles = (int)(rows / 128);
+      f.E = e1 - e0;
+      f.xt = m->xt;
+      f.wp = m->wp + (long long)e0 * fused::NWP;
+      f.bias = m->bb + (long long)e0 * NBB;
+      f.ystat = m->ystat;
+      f.y = y + b0 * 3;
+      f.err = m->err;
+      const int grid = std::max(1, std::min((f.ntiles + 1) / 2, m->num_sms));
+      k_mlp_fused<<<grid, fused::NT, fused::SMEM, s>>>(f);
+      e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
+  }
   for (long long b0 = 0; b0 < B && e == cudaSuccess; b0 += m->bmax) {
     const long long nb = std::min(m->bmax, B - b0);
     k_input<<<blocks_for(nb * PAD_IN), 256, 0, s>>>(nb, x + b0 * 6, nullptr, m->box, m->xn);

@@ -107,14 +107,15 @@ class SurrogateMLP:
         _lib.check(_lib.lib().ens_mlp_adam(self._h, member, float(lr), self.steps[member],
                                            _stream(self.device)))
 
-    def forward(self, x, member=-1, out=None):
-        """y [E', B, 3] for one member (E' = 1) or all (member = -1)."""
+    def forward(self, x, member=-1, out=None, layerwise=False):
+        """y [E', B, 3] for one member (E' = 1) or all (member = -1): by default the fused
+        on-chip kernel, layerwise=True the layer-by-layer path (identical results)."""
         x, _ = self._xy(x)
         E = self.members if member < 0 else 1
         if out is None:
             out = torch.empty((E, x.shape[0], 3), dtype=torch.float32, device=self.device)
         _lib.check(_lib.lib().ens_mlp_forward(self._h, member, x.shape[0], _ptr(x), _ptr(out),
-                                              _stream(self.device)))
+                                              1 if layerwise else 0, _stream(self.device)))
         return out
 
     def gate(self, x, y_members, tau, mean=None, fallback=None, count=None, compact=None,

@@ -92,6 +92,22 @@ def test_forward_all_members_and_chunking(net):
     np.testing.assert_array_equal(y0, y[0, :4096])
 
 
+@pytest.mark.parametrize("B", [1, 127, 128, 129, 1000, 4096, 10000])
+def test_fused_forward_equals_layerwise(net, B):
+    """The fused on-chip forward (all layers and members in one kernel) gives exactly the
+    layer-by-layer result: same K order, same epilogue operations."""
+    net.set_params(0, params(11))
+    net.set_params(1, params(12))
+    net.set_scaling(np.array([0.5, -1.0, 2.0]), np.array([2.0, 3.0, 4.0]))
+    x = cuda32(workloads.surrogate_inputs(B, seed=40 + B))
+    a = net.forward(x).cpu().numpy()
+    b = net.forward(x, layerwise=True).cpu().numpy()
+    net.check()
+    np.testing.assert_array_equal(a, b)
+    c = net.forward(x, member=1).cpu().numpy()[0]
+    np.testing.assert_array_equal(c, b[1])
+
+
 @pytest.mark.parametrize("B", [200, 4096])
 def test_gradient_matches_oracle(net, B):
     p = params(4)
