@@ -70,6 +70,17 @@ WORKLOADS = {
 }
 MLP_FLOPS_PER_SAMPLE = 2 * (6 * 256 + 2 * 256 * 256 + 256 * 3)  # 266,752 per member
 
+# DRAM bytes (read + write) per unit of the dominant kernel, from one ncu capture of that
+# kernel on a smaller case (profiles/), scaled to a full launch by the units processed (the
+# traffic is the per-unit inputs and outputs, so it grows in proportion).  Used only while the
+# timed launch runs that same kernel.
+PROFILED_TRAFFIC = {
+    # k_persistent_pair, N = 393,216: 14.464 MB read + 0.268 MB written
+    "lorenz_adaptive_f32": dict(kernel="k_persistent_pair", per_unit=(14.464e6 + 0.268e6) / 393216),
+    # k_mlp_fused, 1,048,576 samples x 4 members: 34.80 MB read + 3.50 MB written
+    "mlp_forward": dict(kernel="k_mlp_fused", per_unit=(34.7968e6 + 3.4967e6) / 1048576),
+}
+
 # the uneven batch: 500k Lorenz (adaptive Tsit5, tf ~ U[1,100]), 200k Robertson
 # (Rosenbrock23, abstol 1e-8, reltol 1e-4, dt0 1e-4), 300k GBM (Euler-Maruyama, dt 1e-3)
 BATCH_PARTS = (("lorenz", "tsit5", 500_000, dict(abstol=1e-5, reltol=1e-5)),
@@ -806,8 +817,17 @@ def main():
         roofline = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None,
                     "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
-                    "kernel": "4-member forward (k_gemm<256> dominant), 266,752 flop per "
-                              "sample per member"}
+                    "kernel": "k_mlp_fused (4-member fused forward), 266,752 flop per "
+                              "sample per member",
+                    "binding_unit": "GELU epilogue: 2 MUFU + ~15 FMA-pipe lane ops per "
+                                    "activation (exact-erf form), floor ~1.2 ms per 1M samples "
+                                    "x 4 members on either pipe"}
+    prof = PROFILED_TRAFFIC.get(args.workload)
+    tuned = getattr(runner, "tuned", None)
+    if prof and (w["kind"] != "solve" or (tuned and tuned.get("tpt") == 2) or args.tpt == 2):
+        roofline["traffic"] = prof["per_unit"] * N
+        roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of %s on a "
+                                      "smaller case, scaled by units processed" % prof["kernel"])
     e2e = None if args.no_e2e else runner.e2e(stream)
     cfg = {"workload": args.workload, "model": w["rhs"], "alg": w["alg"], "N": N,
            "tspan": [0.0, w["t1"]], **{k: w[k] for k in ("tol", "dt", "dt0", "every") if k in w},

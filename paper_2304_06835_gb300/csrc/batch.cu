@@ -108,6 +108,12 @@ int tune_problem(int rhs_id, const ens_opts* o, const SolveArgs& a, const SolveS
       cudaEventRecord(e0, s);
       cudaError_t e = enqueue_solve(rhs_id, o, a, c, sc, s, &sup);
       cudaEventRecord(e1, s);
+      if (e == cudaErrorLaunchOutOfResources || e == cudaErrorInvalidConfiguration) {
+        // this block size does not fit the kernel's registers / shared memory: not a candidate
+        cudaEventSynchronize(e1);
+        tmin = 1e30f;
+        break;
+      }
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (!sup) rc = set_last_error(ENS_ENOTSUP, "algorithm not available for this model");
       else if (e != cudaSuccess) rc = set_last_error(ENS_ECUDA, cudaGetErrorString(e));
@@ -124,6 +130,7 @@ int tune_problem(int rhs_id, const ens_opts* o, const SolveArgs& a, const SolveS
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != ENS_OK) return rc;
+  if (bms >= 1e30f) return set_last_error(ENS_ECUDA, "no launch shape fits this kernel");
   {
     std::lock_guard<std::mutex> lock(g_tuned_mu);
     g_tuned[tune_key(rhs_id, a.N, o, sms)] = bc;

@@ -26,6 +26,7 @@ cudaError_t persistent_grid(const LaunchCfg& cfg, int* grid) {
   cudaError_t e =
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent<I, TPT>, cfg.block, 0);
   if (e != cudaSuccess) return e;
+  if (bps == 0) return cudaErrorLaunchOutOfResources;  // the block does not fit an SM
   if (cfg.bps > 0) bps = std::min(bps, cfg.bps);
   else if (cfg.bps < 0) bps = std::max(1, (bps * -cfg.bps + 3) / 4);  // a quarter-step fraction
   *grid = std::max(1, bps) * cfg.num_sms;
@@ -38,6 +39,7 @@ cudaError_t launch_persistent_pair(const SolveArgs& a, const LaunchCfg& cfg, cud
   cudaError_t e =
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent_pair<RHS>, cfg.block, 0);
   if (e != cudaSuccess) return e;
+  if (bps == 0) return cudaErrorLaunchOutOfResources;  // the block does not fit an SM
   if (cfg.bps > 0) bps = std::min(bps, cfg.bps);
   else if (cfg.bps < 0) bps = std::max(1, (bps * -cfg.bps + 3) / 4);
   int grid = std::max(1, bps) * cfg.num_sms;

@@ -186,3 +186,18 @@ def test_mixed_batch_full_size_sampled():
     o = host(outs[2][0]).T[idx][:, 0]
     assert np.max(np.abs(o - ref) / np.maximum(np.abs(ref), 1)) <= 1e-5
     b.close()
+
+
+def test_autotune_skips_shapes_that_do_not_fit():
+    """Rosenbrock23 in FP64 uses too many registers for 512-thread blocks: the tuner must
+    skip that shape, not fail."""
+    from paper_2304_06835_gb300 import EnsembleSolver
+    P, U, T = workloads.robertson_random(3000, seed=71)
+    s = EnsembleSolver("robertson")
+    d = lambda a: torch.tensor(np.ascontiguousarray(a.T), dtype=torch.float64, device="cuda")
+    block, tpt, bps, ms = s.autotune(d(P), d(U), d(T), alg="ros23", layout="soa", abstol=1e-6,
+                                     reltol=1e-6, dt0=1e-4)
+    assert block in (64, 128, 256, 512) and ms > 0
+    out, st, _ = s.solve(d(P), d(U), d(T), alg="ros23", layout="soa", abstol=1e-6, reltol=1e-6,
+                         dt0=1e-4)
+    assert int(st.abs().sum()) == 0
