@@ -123,6 +123,18 @@ def solve_kwargs(w):
     return kw
 
 
+def max_over_ranks(seconds, world, device=None):
+    """The job's time: the largest of the ranks' timed totals (one MAX all-reduce; no
+    collective on the data path)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -793,10 +805,7 @@ def main():
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
     tot_s = sum(ms) / 1e3
-    if world > 1:
-        t = torch.tensor([tot_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_s = float(t.item())
+    tot_s = max_over_ranks(tot_s, world, dev)
     value = N * world * args.steps / tot_s
 
     ops, extra = runner.work()
