@@ -9,7 +9,9 @@ network.  This module only marshals NumPy arrays into the C functions.
 
 Identifiers (the same numbers as the public C-ABI, by documentation):
   rhs:  1 Lorenz (D=3, P=3: sigma, rho, beta), 2 Robertson (D=3, P=3: k1, k2, k3),
-        3 geometric Brownian motion (D=1, P=2: mu, sigma)
+        3 geometric Brownian motion (D=1, P=2: mu, sigma; 1 Wiener process),
+        4 sigma-factor CRN (D=4: [sigma], A1, A2, A3; P=6: S, D, tau, nu0, n, eta;
+          8 Wiener processes; Euler-Maruyama only)
   alg:  1 Tsit5 fixed, 2 Tsit5 adaptive, 3 RK4, 4 Rosenbrock23, 5 Euler-Maruyama
 """
 from __future__ import annotations
@@ -27,9 +29,10 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-RHS = {"lorenz": 1, "robertson": 2, "gbm": 3}
+RHS = {"lorenz": 1, "robertson": 2, "gbm": 3, "crn": 4}
 ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5}
-DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2)}
+DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2), 4: (4, 6)}
+NOISE = {1: 0, 2: 0, 3: 1, 4: 8}  # Wiener processes per model
 STATUS = {"ok": 0, "maxiters": 1, "dt_min": 2, "nonfinite": 3}
 
 
@@ -64,6 +67,11 @@ def lib():
             L.oracle_tsit5_tableau.argtypes = [dp, dp, dp, dp]
             L.oracle_rhs.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
             L.oracle_jac.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp, dp]
+            L.oracle_diffusion.restype = ctypes.c_int
+            L.oracle_diffusion.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
+            L.oracle_em_step.restype = ctypes.c_int
+            L.oracle_em_step.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
+                                         dp, dp]
             L.oracle_lu_solve.argtypes = [ctypes.c_int, dp, dp, dp]
             u32p = ctypes.POINTER(ctypes.c_uint32)
             L.oracle_philox4x32_10.restype = None
@@ -159,6 +167,30 @@ def rhs_eval(rhs, u, p, t=0.0):
     du = np.empty(D)
     lib().oracle_rhs(rhs_id, _dp(_f64(u)), _dp(_f64(p)), float(t), _dp(du))
     return du
+
+
+def diffusion(rhs, u, p, t=0.0):
+    """Diffusion matrix G [D, Mw] of an SDE model (column m multiplies dW_{m+1})."""
+    rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    D, _ = DIMS[rhs_id]
+    G = np.empty((D, NOISE[rhs_id]))
+    if lib().oracle_diffusion(rhs_id, _dp(_f64(u)), _dp(_f64(p)), float(t), _dp(G)) != 0:
+        raise ValueError("not an SDE model")
+    return G
+
+
+def em_step(rhs, u, p, t, h, z):
+    """One Euler-Maruyama step with the given normals z [Mw]."""
+    rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    D, _ = DIMS[rhs_id]
+    z = _f64(z).reshape(-1)
+    if z.size != NOISE[rhs_id]:
+        raise ValueError("need one normal per Wiener process")
+    unew = np.empty(D)
+    if lib().oracle_em_step(rhs_id, _dp(_f64(u)), _dp(_f64(p)), float(t), float(h), _dp(z),
+                            _dp(unew)) != 0:
+        raise ValueError("not an SDE model")
+    return unew
 
 
 def jacobians(rhs, u, p, t=0.0):

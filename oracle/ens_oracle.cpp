@@ -44,24 +44,27 @@ namespace {
 
 // ----------------------------------------------------------------------------------------------
 // identifiers (values match the public C-ABI enumeration by documentation, not by a shared header)
-enum { RHS_LORENZ = 1, RHS_ROBERTSON = 2, RHS_GBM = 3 };
+enum { RHS_LORENZ = 1, RHS_ROBERTSON = 2, RHS_GBM = 3, RHS_CRN = 4 };
 enum { ALG_TSIT5_FIXED = 1, ALG_TSIT5_ADAPTIVE = 2, ALG_RK4 = 3, ALG_ROS23 = 4, ALG_EM = 5 };
 enum { ST_OK = 0, ST_MAXITERS = 1, ST_DT_MIN = 2, ST_NONFINITE = 3 };
 enum { LAYOUT_ROWMAJOR = 0, LAYOUT_SOA = 1 };
 
 // ----------------------------------------------------------------------------------------------
-// Models (Appendix: Lorenz, Robertson, linear SDE).  f(u,p,t) and the Jacobians df/du, df/dp.
+// Models (Appendix: Lorenz, Robertson, linear SDE, sigma-factor CRN).  f(u,p,t), the
+// diffusion matrix of the SDE models and the Jacobians df/du, df/dp of the ODE models.
+// Mw = number of Wiener processes (0 for an ODE).
 struct Model {
-  int D, P;
+  int D, P, Mw;
 };
 
 Model model_of(int rhs) {
   switch (rhs) {
-    case RHS_LORENZ: return {3, 3};
-    case RHS_ROBERTSON: return {3, 3};
-    case RHS_GBM: return {1, 2};
+    case RHS_LORENZ: return {3, 3, 0};
+    case RHS_ROBERTSON: return {3, 3, 0};
+    case RHS_GBM: return {1, 2, 1};
+    case RHS_CRN: return {4, 6, 8};
   }
-  return {0, 0};
+  return {0, 0, 0};
 }
 
 // Lorenz: p = (sigma, rho, beta); the paper writes beta as gamma.
@@ -93,11 +96,67 @@ void g_gbm(const T* u, const T* p, T /*t*/, T* gu) {
   gu[0] = p[1] * u[0];
 }
 
+// Sigma-factor stress-response CRN (Appendix, SDE models), the Chemical Langevin form with
+// 4 species u = ([sigma], [A1], [A2], [A3]) and p = (S, D, tau, nu0, n, eta).
+// Drift:   d[sigma] = nu0 + H - [sigma],  H = (S[sigma])^n / ((S[sigma])^n + (D[A3])^n + 1),
+//          d[A1] = [sigma]/tau - [A1]/tau,  d[A2] = [A1]/tau - [A2]/tau,
+//          d[A3] = [A2]/tau - [A3]/tau.
+// Noise (8 Wiener processes, column m of G multiplies dW_{m+1}):
+//          [sigma]: +eta sqrt(nu0 + H) dW1 - eta sqrt([sigma]) dW2,
+//          [A1]:    +eta sqrt([sigma]/tau) dW3 - eta sqrt([A1]/tau) dW4,
+//          [A2]:    +eta sqrt([A1]/tau) dW5 - eta sqrt([A2]/tau) dW6,
+//          [A3]:    +eta sqrt([A2]/tau) dW7 - eta sqrt([A3]/tau) dW8.
+// The Langevin form is defined for non-negative amounts; a path of it can step below zero, so
+// every square-root argument and both Hill bases are taken as max(., 0).
+template <class T>
+T crn_hill(const T* u, const T* p) {
+  const T a = std::pow(std::max(p[0] * u[0], T(0)), p[4]);
+  const T b = std::pow(std::max(p[1] * u[3], T(0)), p[4]);
+  return a / (a + b + T(1));
+}
+
+template <class T>
+void f_crn(const T* u, const T* p, T /*t*/, T* du) {
+  const T tau = p[2], nu0 = p[3];
+  du[0] = nu0 + crn_hill(u, p) - u[0];
+  du[1] = u[0] / tau - u[1] / tau;
+  du[2] = u[1] / tau - u[2] / tau;
+  du[3] = u[2] / tau - u[3] / tau;
+}
+
+template <class T>
+T sqrt0(T x) {
+  return std::sqrt(std::max(x, T(0)));
+}
+
+// G[j*8 + m] = coefficient of dW_{m+1} in the equation of species j
+template <class T>
+void g_crn(const T* u, const T* p, T /*t*/, T* G) {
+  const T tau = p[2], nu0 = p[3], eta = p[5];
+  for (int i = 0; i < 32; ++i) G[i] = T(0);
+  G[0 * 8 + 0] = eta * sqrt0(nu0 + crn_hill(u, p));
+  G[0 * 8 + 1] = -eta * sqrt0(u[0]);
+  G[1 * 8 + 2] = eta * sqrt0(u[0] / tau);
+  G[1 * 8 + 3] = -eta * sqrt0(u[1] / tau);
+  G[2 * 8 + 4] = eta * sqrt0(u[1] / tau);
+  G[2 * 8 + 5] = -eta * sqrt0(u[2] / tau);
+  G[3 * 8 + 6] = eta * sqrt0(u[2] / tau);
+  G[3 * 8 + 7] = -eta * sqrt0(u[3] / tau);
+}
+
+// diffusion matrix G [D][Mw] of an SDE model
+template <class T>
+void diffusion(int id, const T* u, const T* p, T t, T* G) {
+  if (id == RHS_GBM) g_gbm(u, p, t, G);
+  else g_crn(u, p, t, G);
+}
+
 template <class T>
 void rhs(int id, const T* u, const T* p, T t, T* du) {
   if (id == RHS_LORENZ) f_lorenz(u, p, t, du);
   else if (id == RHS_ROBERTSON) f_robertson(u, p, t, du);
-  else f_gbm(u, p, t, du);
+  else if (id == RHS_GBM) f_gbm(u, p, t, du);
+  else f_crn(u, p, t, du);
 }
 
 // J[i*D+j] = d f_i / d u_j
@@ -370,7 +429,7 @@ double normal_draw(uint64_t seed, uint64_t traj, uint64_t k, bool fp64) {
 
 // ----------------------------------------------------------------------------------------------
 struct Opts {
-  int rhs, alg, D, P;
+  int rhs, alg, D, P, Mw;
   double dt, abstol, reltol, dt0;
   long long maxiters;
   const double* saveat;
@@ -468,14 +527,22 @@ void solve_fixed(Traj<T>& tr, uint64_t traj_index) {
     } else if (o.alg == ALG_RK4) {
       rk4_step<T>(o.rhs, D, tr.u, tr.p, tk, h, unew);
       tr.fevals += 4;
-    } else {  // Euler-Maruyama: X_{k+1} = X_k + a(X_k) h + b(X_k) sqrt(h) Z_k
-      T a[8], b[8];
-      f_gbm<T>(tr.u, tr.p, tk, a);
-      g_gbm<T>(tr.u, tr.p, tk, b);
+    } else {  // Euler-Maruyama (Sec. 3.3): X_{k+1} = X_k + a(X_k) h + sum_m b_m(X_k) dW_m,
+      // dW_m = sqrt(h) Z_{k,m}; Z_{k,m} is normal number k*Mw + m of the trajectory's stream
+      const int Mw = o.Mw;
+      T a[8], G[64], z[8];
+      rhs<T>(o.rhs, tr.u, tr.p, tk, a);
+      diffusion<T>(o.rhs, tr.u, tr.p, tk, G);
       tr.fevals += 1;
-      T z = T(normal_draw(o.seed, traj_index, uint64_t(k), o.stream_fp64));
+      for (int m = 0; m < Mw; ++m)
+        z[m] = T(normal_draw(o.seed, traj_index, uint64_t(k) * uint64_t(Mw) + uint64_t(m),
+                             o.stream_fp64));
       T sq = std::sqrt(h);
-      for (int j = 0; j < D; ++j) unew[j] = tr.u[j] + a[j] * h + b[j] * sq * z;
+      for (int j = 0; j < D; ++j) {
+        T x = tr.u[j] + a[j] * h;
+        for (int m = 0; m < Mw; ++m) x = x + G[j * Mw + m] * sq * z[m];
+        unew[j] = x;
+      }
     }
     for (int j = 0; j < D; ++j) tr.u[j] = unew[j];
     tr.accepted += 1;
@@ -657,9 +724,10 @@ int oracle_solve(int rhs_id, int alg, int precision, int layout, long long N,
                  int nthreads) {
   Model m = model_of(rhs_id);
   if (m.D == 0 || N < 0 || alg < 1 || alg > 5) return -1;
-  if (alg == ALG_EM && rhs_id != RHS_GBM) return -1;
+  if (alg == ALG_EM && m.Mw == 0) return -1;  // Euler-Maruyama needs an SDE model
+  if (rhs_id == RHS_CRN && alg != ALG_EM) return -1;
   if (precision < 0 || precision > 2) return -1;
-  Opts o{rhs_id, alg, m.D, m.P, dt, abstol, reltol, dt0, maxiters, saveat, n_save, seed,
+  Opts o{rhs_id, alg, m.D, m.P, m.Mw, dt, abstol, reltol, dt0, maxiters, saveat, n_save, seed,
          index_offset, precision == 0};
   parallel_for(N, nthreads, [&](long long a, long long b) {
     if (precision != 1)
@@ -676,6 +744,7 @@ int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t,
                 double z, double* unew, double* err) {
   Model m = model_of(rhs_id);
   if (m.D == 0) return -1;
+  if (alg == ALG_ROS23 && rhs_id == RHS_CRN) return -1;  // no Jacobian for the CRN
   double e[8] = {0}, fx[8], k1[8];
   if (alg == ALG_TSIT5_FIXED || alg == ALG_TSIT5_ADAPTIVE) {
     rhs<double>(rhs_id, u, p, t, k1);
@@ -714,8 +783,32 @@ int oracle_rhs(int rhs_id, const double* u, const double* p, double t, double* d
   return 0;
 }
 
+// Diffusion matrix G[D][Mw] of an SDE model (GBM, CRN).
+int oracle_diffusion(int rhs_id, const double* u, const double* p, double t, double* G) {
+  if (model_of(rhs_id).Mw == 0) return -1;
+  diffusion<double>(rhs_id, u, p, t, G);
+  return 0;
+}
+
+// One Euler-Maruyama step with the given normals z[Mw] (any SDE model).
+int oracle_em_step(int rhs_id, const double* u, const double* p, double t, double h,
+                   const double* z, double* unew) {
+  const Model m = model_of(rhs_id);
+  if (m.Mw == 0) return -1;
+  double a[8], G[64];
+  rhs<double>(rhs_id, u, p, t, a);
+  diffusion<double>(rhs_id, u, p, t, G);
+  const double sq = std::sqrt(h);
+  for (int j = 0; j < m.D; ++j) {
+    double x = u[j] + a[j] * h;
+    for (int k = 0; k < m.Mw; ++k) x = x + G[j * m.Mw + k] * sq * z[k];
+    unew[j] = x;
+  }
+  return 0;
+}
+
 int oracle_jac(int rhs_id, const double* u, const double* p, double t, double* Ju, double* Jp) {
-  if (model_of(rhs_id).D == 0) return -1;
+  if (model_of(rhs_id).D == 0 || rhs_id == RHS_CRN) return -1;
   if (Ju) jac_u<double>(rhs_id, u, p, t, Ju);
   if (Jp) jac_p<double>(rhs_id, u, p, t, Jp);
   return 0;
@@ -778,7 +871,7 @@ int oracle_fixed_grad(int rhs_id, int alg_id, long long N, const double* params,
     return -1;
   }
   Model m = model_of(rhs_id);
-  if (m.D == 0) return -1;
+  if (m.D == 0 || rhs_id == RHS_CRN) return -1;  // tangents need df/du, df/dp
   const int D = m.D, P = m.P, M = m.P + m.D;
   parallel_for(N, nthreads, [&](long long a, long long bnd) {
     for (long long i = a; i < bnd; ++i) {

@@ -17,6 +17,12 @@ Workloads (the paper's models with the shapes and value ranges of its benchmarks
   * ``adjoint_targets``   -- targets u_target ~ N(0, 5^2) per component.
   * ``surrogate_inputs``  -- (sigma, rho, beta, u0) with u0~U[-5,5]^3, optionally with a share of
                              samples from a 1.25x enlarged box.
+  * ``crn_grid``          -- sigma-factor CRN SDE, p = (S, D, tau, nu0, n, eta): k values of each
+                             parameter drawn uniformly in its range (S, D, tau in [0.1, 100],
+                             nu0 in [0.01, 0.2], n in [2, 4], eta in [0.001, 0.1]), all k^6
+                             combinations (the Cartesian product), u0 = (nu0, nu0, nu0, nu0),
+                             tspan [0, 1000] (Appendix, CRN model and its parameter table).
+  * ``crn_random``        -- the same ranges, each trajectory's parameters drawn independently.
 """
 from __future__ import annotations
 
@@ -25,6 +31,8 @@ import numpy as np
 LORENZ_BOX = np.array([[8.0, 12.0], [0.0, 28.0], [2.0, 3.0]])  # sigma, rho, beta
 U0_BOX = np.array([[-5.0, 5.0]] * 3)
 ROBERTSON_K0 = np.array([0.04, 3e7, 1e4])
+CRN_BOX = np.array([[0.1, 100.0], [0.1, 100.0], [0.1, 100.0], [0.01, 0.2], [2.0, 4.0],
+                    [0.001, 0.1]])  # S, D, tau, nu0, n, eta
 
 
 def lorenz_sweep(N: int = 1024, t1: float = 1.0):
@@ -100,3 +108,25 @@ def surrogate_inputs(N: int, seed: int, outside_share: float = 0.0, enlarge: flo
 
 def surrogate_box():
     return np.concatenate([LORENZ_BOX, U0_BOX], axis=0)
+
+
+def _crn_problem(p: np.ndarray, t1: float):
+    N = p.shape[0]
+    u0 = np.repeat(p[:, 3:4], 4, axis=1)
+    tspan = np.zeros((N, 2))
+    tspan[:, 1] = t1
+    return p, u0, tspan
+
+
+def crn_grid(k: int = 10, seed: int = 8, t1: float = 1000.0):
+    """Cartesian product of k uniform draws per parameter: k**6 trajectories."""
+    rng = np.random.default_rng(seed)
+    axes = [np.sort(rng.uniform(lo, hi, k)) for lo, hi in CRN_BOX]
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, 6)
+    return _crn_problem(np.ascontiguousarray(grid), t1)
+
+
+def crn_random(N: int, seed: int = 9, t1: float = 1000.0):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(CRN_BOX[:, 0], CRN_BOX[:, 1], size=(N, 6))
+    return _crn_problem(p, t1)
