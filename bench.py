@@ -45,8 +45,21 @@ SM_MAX_MHZ = 2070.0
 #   fixed Tsit5 step: stage combinations 81 + six f evaluations 36 -> 117;
 #   adjoint step (Tsit5, Lorenz): forward with checkpoints 117, replay 117, transposed step
 #     189 (six VJP pairs 6 x 18, stage-adjoint sums 45 + 15, seeds 21) -> 423.
+# Euler-Maruyama steps count ALU lane instructions (INT32 and FP32 share the 128 lanes/SM/clk):
+#   GBM step: 3 FP + a quarter of one Philox call (10 rounds x (2 wide IMAD + 4 LOP) = 60 INT)
+#     and of its Box-Muller (~30 FP for 4 normals) -> 25;
+#   CRN step (8 normals): two Philox calls 120 INT, Box-Muller 60 FP, Hill term 11 (two
+#     products, two powers as lg2-mul-ex2, sum, +1, divide), drift 8, noise 17 (5 square
+#     roots, 4 x (mul, fma, mul)), update 8 -> 224; in FP64 the FP64 pipe carries only the
+#     floating-point part -> 104 (the Philox integer work runs on the integer lanes).
 OPS_PER_ATTEMPT = {"tsit5": 160, "tsit5_fixed": 117, "rk4": 48, "ros23": 140, "em": 25,
-                   "adjoint": 423}
+                   "adjoint": 423, "crn_em": 224, "crn_em_f64": 104}
+
+
+def ops_key(w):
+    if w["rhs"] == "crn":
+        return "crn_em_f64" if w["dtype"] == "f64" else "crn_em"
+    return w["alg"]
 
 WORKLOADS = {
     # name: model, algorithm, precision, N, tspan end, tolerance / step, default timed steps
@@ -58,6 +71,10 @@ WORKLOADS = {
                              N=1 << 20, t1=1.0, dt=1e-3, steps=300),
     "robertson_ros23_f64": dict(kind="solve", rhs="robertson", alg="ros23", dtype="f64",
                                 N=1 << 18, t1=1e5, tol=1e-6, dt0=1e-4, steps=20),
+    "crn_em_f32": dict(kind="solve", rhs="crn", alg="em", dtype="f32", N=10 ** 6, t1=1000.0,
+                       dt=0.1, seed=2024, steps=5),
+    "crn_em_f64": dict(kind="solve", rhs="crn", alg="em", dtype="f64", N=10 ** 6, t1=1000.0,
+                       dt=0.1, seed=2024, steps=2),
     "lorenz_adjoint_f64": dict(kind="adjoint", rhs="lorenz", alg="tsit5_fixed", dtype="f64",
                                N=65536, t1=1.0, dt=1e-3, every=64, steps=30),
     "uneven_batch_f32": dict(kind="batch", rhs="mixed", alg="tsit5+ros23+em", dtype="f32",
@@ -107,6 +124,12 @@ def inputs_for(w, rank=0):
             P, U, T = workloads.lorenz_random(N, seed=2 + 1000 * rank, t1=w["t1"])
     elif w["rhs"] == "robertson":
         P, U, T = workloads.robertson_random(N, seed=3 + 1000 * rank, t1=w["t1"])
+    elif w["rhs"] == "crn":  # the Cartesian product of k draws per parameter, k^6 = N
+        k = int(round(N ** (1.0 / 6.0)))
+        if k ** 6 == N:
+            P, U, T = workloads.crn_grid(k, seed=8 + 1000 * rank, t1=w["t1"])
+        else:
+            P, U, T = workloads.crn_random(N, seed=8 + 1000 * rank, t1=w["t1"])
     else:
         P, U, T = workloads.gbm_random(N, seed=4 + 1000 * rank, t1=w["t1"])
     return P, U, T
@@ -120,6 +143,8 @@ def solve_kwargs(w):
         kw["dt"] = w["dt"]
     if "dt0" in w:
         kw["dt0"] = w["dt0"]
+    if "seed" in w:
+        kw["seed"] = w["seed"]
     return kw
 
 
@@ -324,8 +349,8 @@ class SolveRunner:
         st = self.stats.cpu().numpy().astype(np.int64)
         attempts = int(st[0].sum() + st[1].sum())
         ok = int((self.status.cpu().numpy() == 0).sum())
-        return attempts * OPS_PER_ATTEMPT[self.w["alg"]], {
-            "attempts_per_launch": attempts, "ops_per_attempt": OPS_PER_ATTEMPT[self.w["alg"]],
+        return attempts * OPS_PER_ATTEMPT[ops_key(self.w)], {
+            "attempts_per_launch": attempts, "ops_per_attempt": OPS_PER_ATTEMPT[ops_key(self.w)],
             "trajectories_ok": ok, "autotuned_shape": self.tuned}
 
     def e2e(self, stream):
@@ -816,8 +841,11 @@ def main():
     sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
     peak_clk = SMS * lanes * sm_mhz * 1e6 / 1e12
     pipe = "FP32" if w["dtype"] == "f32" else "FP64"
+    unit = "T %s-FMA-pipe instr/s" % pipe
+    if w.get("rhs") == "crn" and w["dtype"] == "f32":
+        unit = "T ALU lane-instr/s (INT32 + FP32)"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_max,
-                "unit": "T %s-FMA-pipe instr/s" % pipe, "frac": achieved / peak_max,
+                "unit": unit, "frac": achieved / peak_max,
                 "frac_at_sampled_clock": achieved / peak_clk, "traffic": None,
                 "peak_basis": "152 SMs x %d %s lanes x 2070 MHz (derived)" % (lanes, pipe)}
     if w["kind"] in ("surrogate", "mlp"):
@@ -839,7 +867,7 @@ def main():
                                       "smaller case, scaled by units processed" % prof["kernel"])
     e2e = None if args.no_e2e else runner.e2e(stream)
     cfg = {"workload": args.workload, "model": w["rhs"], "alg": w["alg"], "N": N,
-           "tspan": [0.0, w["t1"]], **{k: w[k] for k in ("tol", "dt", "dt0", "every") if k in w},
+           "tspan": [0.0, w["t1"]], **{k: w[k] for k in ("tol", "dt", "dt0", "every", "seed") if k in w},
            "layout": "soa", "l2": "flushed between steps (256 MB write outside events)",
            "parallelism": "dp%d" % world}
     if w["kind"] == "solve":

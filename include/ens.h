@@ -41,8 +41,17 @@ enum { ENS_OK = 0, ENS_EINVAL = 1, ENS_ENOTSUP = 2, ENS_ECUDA = 3, ENS_ENOMEM = 
  *   ROBERTSON D=3 P=3  p=(k1, k2, k3)         f = (-k1 y1 + k3 y2 y3, k1 y1 - k3 y2 y3 - k2 y2^2,
  *                                                   k2 y2^2)   (Appendix, Robertson equation)
  *   GBM       D=1 P=2  p=(mu, sigma)          a = mu X, b = sigma X   (Appendix, linear SDE);
- *             ODE algorithms integrate the drift only (u' = mu u). */
-enum { ENS_RHS_LORENZ = 1, ENS_RHS_ROBERTSON = 2, ENS_RHS_GBM = 3 };
+ *             ODE algorithms integrate the drift only (u' = mu u).
+ *   CRN       D=4 P=6  u=([sigma], A1, A2, A3), p=(S, D, tau, nu0, n, eta); 8 Wiener processes
+ *             (Appendix, sigma-factor CRN; Chemical Langevin form):
+ *               a = (nu0 + H - [sigma], ([sigma] - A1)/tau, (A1 - A2)/tau, (A2 - A3)/tau),
+ *               H = (S[sigma])^n / ((S[sigma])^n + (D A3)^n + 1);
+ *               noise of [sigma]: eta(sqrt(nu0 + H) dW1 - sqrt([sigma]) dW2), of A_i:
+ *               eta(sqrt(A_{i-1}/tau) dW_{2i+1} - sqrt(A_i/tau) dW_{2i+2}) with A_0 = [sigma].
+ *             Square-root arguments and the two Hill bases are taken as max(., 0) (the form
+ *             is undefined for negative amounts, which a discrete path can reach).
+ *             Euler-Maruyama only. */
+enum { ENS_RHS_LORENZ = 1, ENS_RHS_ROBERTSON = 2, ENS_RHS_GBM = 3, ENS_RHS_CRN = 4 };
 
 /* algorithms:
  *   TSIT5_FIXED    Tsitouras 5(4) pair, fixed step dt (GPUTsit5, Sec. 5.2.1; RK step Sec. 3.1)
@@ -51,7 +60,10 @@ enum { ENS_RHS_LORENZ = 1, ENS_RHS_ROBERTSON = 2, ENS_RHS_GBM = 3 };
  *   RK4            classic 4-stage Runge-Kutta, fixed step (explicit RK family, Sec. 3.1)
  *   ROS23          Rosenbrock23, the Shampine-Reichelt 2(3) Rosenbrock-W pair with a 3x3 LU of
  *                  W = I - h d J held in registers (GPURosenbrock23, Sec. 5.2.1; Sec. 3.2.1)
- *   EM             Euler-Maruyama, fixed step, diagonal noise (GPUEM, Sec. 5.2.2; Sec. 3.3) */
+ *   EM             Euler-Maruyama, fixed step, X += a h + sum_m b_m sqrt(h) Z_{k,m} over the
+ *                  model's M Wiener processes (diagonal noise for GBM, M = 1; non-diagonal
+ *                  for the CRN, M = 8) (GPUEM, Sec. 5.2.2; Sec. 3.3).  Z_{k,m} is normal
+ *                  number k*M + m of the trajectory's Philox stream (see ens_normals). */
 enum { ENS_TSIT5_FIXED = 1, ENS_TSIT5_ADAPTIVE = 2, ENS_RK4 = 3, ENS_ROS23 = 4, ENS_EM = 5 };
 
 /* element type of every floating-point array of a call */
@@ -129,7 +141,8 @@ int ens_destroy(ens_handle* h);
  *   status            : device int8 [N] (ENS_TRAJ_*) or NULL
  *   stats             : device int32 [3][N] = accepted steps, rejected steps, f evaluations,
  *                       or NULL
- * Validation (ENS_EINVAL): null arrays, N < 0, unsupported (rhs, alg) pair (EM needs GBM),
+ * Validation (ENS_EINVAL): null arrays, N < 0, unsupported (rhs, alg) pair (EM needs an
+ * SDE model: GBM or CRN; the CRN takes EM only),
  * dt <= 0 for fixed-step, tolerances out of range, n_save > ENS_MAX_SAVE or unsorted. */
 int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, const void* tspan,
               const ens_opts* opts, void* out, signed char* status, int* stats,
@@ -316,8 +329,8 @@ int ens_mlp_activation(int which, long long n, const float* z, float* out, void*
 int ens_philox4x32_10(unsigned long long seed, long long index_offset, long long n_traj,
                       long long n_calls, unsigned int* out, void* cuda_stream);
 
-/* The standard normals Z_k (k < n_per) that drive Euler-Maruyama step k of trajectory j:
- * out[k*n_traj + j] in `dtype` (F32: 4 normals per Philox call, F64: 2).  Box-Muller of the
+/* The standard normals Z_k (k < n_per) of trajectory j's stream (Euler-Maruyama step s of a
+ * model with M Wiener processes uses Z_{s*M} .. Z_{s*M+M-1}): out[k*n_traj + j] in `dtype` (F32: 4 normals per Philox call, F64: 2).  Box-Muller of the
  * uniforms ((x>>9)+0.5)*2^-23 (F32) or ((x0:x1 >> 12)+0.5)*2^-52 (F64),
  * exact and inside (0,1). */
 int ens_normals(unsigned long long seed, long long index_offset, long long n_traj,

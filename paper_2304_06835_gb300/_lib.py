@@ -13,8 +13,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libens.so")
 
 ENS_OK, ENS_EINVAL, ENS_ENOTSUP, ENS_ECUDA, ENS_ENOMEM = 0, 1, 2, 3, 4
-RHS = {"lorenz": 1, "robertson": 2, "gbm": 3}
-DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2)}
+RHS = {"lorenz": 1, "robertson": 2, "gbm": 3, "crn": 4}
+DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2), 4: (4, 6)}
+NOISE = {1: 0, 2: 0, 3: 1, 4: 8}  # Wiener processes per model
 ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5}
 F32, F64 = 0, 1
 LAYOUT = {"rowmajor": 0, "soa": 1}

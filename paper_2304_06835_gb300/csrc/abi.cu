@@ -23,15 +23,19 @@ cudaError_t dispatch_f64_robertson(int, const SolveArgs*, const LaunchCfg&, cuda
                                    cudaFuncAttributes*, int*, CostScratch*);
 cudaError_t dispatch_f64_gbm(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
                              cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f32_crn(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                             cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f64_crn(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                             cudaFuncAttributes*, int*, CostScratch*);
 
 typedef cudaError_t (*DispatchFn)(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
                                   cudaFuncAttributes*, int*, CostScratch*);
 
 static DispatchFn table(int rhs_id, int dtype) {
-  static const DispatchFn t[2][3] = {
-      {dispatch_f32_lorenz, dispatch_f32_robertson, dispatch_f32_gbm},
-      {dispatch_f64_lorenz, dispatch_f64_robertson, dispatch_f64_gbm}};
-  if (rhs_id < 1 || rhs_id > 3 || (dtype != ENS_F32 && dtype != ENS_F64)) return nullptr;
+  static const DispatchFn t[2][4] = {
+      {dispatch_f32_lorenz, dispatch_f32_robertson, dispatch_f32_gbm, dispatch_f32_crn},
+      {dispatch_f64_lorenz, dispatch_f64_robertson, dispatch_f64_gbm, dispatch_f64_crn}};
+  if (rhs_id < 1 || rhs_id > 4 || (dtype != ENS_F32 && dtype != ENS_F64)) return nullptr;
   return t[dtype][rhs_id - 1];
 }
 
@@ -237,6 +241,7 @@ bool model_dims(int rhs_id, int* D, int* P) {
     case ENS_RHS_LORENZ: *D = 3; *P = 3; return true;
     case ENS_RHS_ROBERTSON: *D = 3; *P = 3; return true;
     case ENS_RHS_GBM: *D = 1; *P = 2; return true;
+    case ENS_RHS_CRN: *D = 4; *P = 6; return true;
   }
   return false;
 }
@@ -251,8 +256,10 @@ int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
   if (o->dtype != ENS_F32 && o->dtype != ENS_F64) return fail(ENS_EINVAL, "unknown dtype");
   if (o->layout != ENS_LAYOUT_ROWMAJOR && o->layout != ENS_LAYOUT_SOA)
     return fail(ENS_EINVAL, "unknown layout");
-  if (o->alg == ENS_EM && rhs_id != ENS_RHS_GBM)
-    return fail(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM)");
+  if (o->alg == ENS_EM && rhs_id != ENS_RHS_GBM && rhs_id != ENS_RHS_CRN)
+    return fail(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM, CRN)");
+  if (rhs_id == ENS_RHS_CRN && o->alg != ENS_EM)
+    return fail(ENS_EINVAL, "the CRN model takes Euler-Maruyama only");
   if (is_fixed(o->alg) && !(o->dt > 0) ) return fail(ENS_EINVAL, "fixed-step methods need dt > 0");
   if (is_fixed(o->alg) && !std::isfinite(o->dt)) return fail(ENS_EINVAL, "dt not finite");
   if (!is_fixed(o->alg)) {

@@ -67,13 +67,16 @@ struct M<double> {
 };
 
 // ------------------------------------------------------------------------------------------
-// Models.  f = du/dt (drift for SDEs), g = diagonal diffusion, jac = df/du (row-major D x D),
-// vjp_u = (df/du)^T w, vjp_p = (df/dp)^T w.
+// Models.  f = du/dt (drift for SDEs), jac = df/du (row-major D x D), vjp_u = (df/du)^T w,
+// vjp_p = (df/dp)^T w.  SDE models (has_noise) have NW Wiener processes and
+// sde(u, p, t, sq, z, a, b): the drift a(u) and the noise increment b_j = sum_m G_jm(u) sq z_m
+// of one Euler-Maruyama step with sqrt(h) = sq and normals z[NW].  sde_only models have no
+// Jacobian and take Euler-Maruyama only.
 
 template <class T>
 struct Lorenz {
-  static constexpr int D = 3, P = 3;
-  static constexpr bool autonomous = true, has_noise = false;
+  static constexpr int D = 3, P = 3, NW = 0;
+  static constexpr bool autonomous = true, has_noise = false, sde_only = false;
   static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) {
     du[0] = p[0] * (u[1] - u[0]);                  // sigma (y2 - y1)
     du[1] = M<T>::fma(u[0], p[1] - u[2], -u[1]);   // y1 (rho - y3) - y2
@@ -98,8 +101,8 @@ struct Lorenz {
 
 template <class T>
 struct Robertson {
-  static constexpr int D = 3, P = 3;
-  static constexpr bool autonomous = true, has_noise = false;
+  static constexpr int D = 3, P = 3, NW = 0;
+  static constexpr bool autonomous = true, has_noise = false, sde_only = false;
   static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) {
     const T r1 = p[0] * u[0];           // k1 y1
     const T r2 = p[1] * u[1] * u[1];    // k2 y2^2
@@ -129,10 +132,15 @@ struct Robertson {
 
 template <class T>
 struct GBM {
-  static constexpr int D = 1, P = 2;
-  static constexpr bool autonomous = true, has_noise = true;
+  static constexpr int D = 1, P = 2, NW = 1;
+  static constexpr bool autonomous = true, has_noise = true, sde_only = false;
   static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) { du[0] = p[0] * u[0]; }
-  static __device__ __forceinline__ void g(const T* u, const T* p, T, T* gu) { gu[0] = p[1] * u[0]; }
+  // a = mu X, b = (sigma X) sqrt(h) Z
+  static __device__ __forceinline__ void sde(const T* u, const T* p, T, T sq, const T* z, T* a,
+                                             T* b) {
+    a[0] = p[0] * u[0];
+    b[0] = ((p[1] * u[0]) * sq) * z[0];
+  }
   static __device__ __forceinline__ void jac(const T*, const T* p, T, T* J) { J[0] = p[0]; }
   static __device__ __forceinline__ void vjp_u(const T*, const T* p, T, const T* w, T* o) {
     o[0] = p[0] * w[0];
@@ -140,6 +148,50 @@ struct GBM {
   static __device__ __forceinline__ void vjp_p(const T* u, const T*, T, const T* w, T* o) {
     o[0] = u[0] * w[0];
     o[1] = T(0);
+  }
+};
+
+// Sigma-factor stress-response CRN (Appendix, SDE models) in the Chemical Langevin form:
+// u = ([sigma], A1, A2, A3), p = (S, D, tau, nu0, n, eta), 8 Wiener processes.
+//   a = (nu0 + H - [sigma], ([sigma] - A1)/tau, (A1 - A2)/tau, (A2 - A3)/tau),
+//   H = (S[sigma])^n / ((S[sigma])^n + (D A3)^n + 1);
+//   b_sigma = eta sq (sqrt(nu0 + H) z1 - sqrt([sigma]) z2),
+//   b_Ai    = eta sq (sqrt(A_{i-1}/tau) z_{2i+1} - sqrt(A_i/tau) z_{2i+2}),  A_0 = [sigma].
+// Square-root arguments and Hill bases are clamped at 0 (the form is undefined for negative
+// amounts, which a discrete path can reach).  sqrt(x/tau) is formed as sqrt(x) sqrt(1/tau),
+// so each amount's square root serves both terms it appears in.
+template <class T>
+struct CRN {
+  static constexpr int D = 4, P = 6, NW = 8;
+  static constexpr bool autonomous = true, has_noise = true, sde_only = true;
+  static __device__ __forceinline__ T hill(const T* u, const T* p) {
+    const T x = M<T>::pow(M<T>::max(p[0] * u[0], T(0)), p[4]);
+    const T y = M<T>::pow(M<T>::max(p[1] * u[3], T(0)), p[4]);
+    return x / ((x + y) + T(1));
+  }
+  static __device__ __forceinline__ void drift(const T* u, const T* p, T H, T* a) {
+    const T rt = M<T>::rcp(p[2]);
+    a[0] = (p[3] + H) - u[0];
+    a[1] = (u[0] - u[1]) * rt;
+    a[2] = (u[1] - u[2]) * rt;
+    a[3] = (u[2] - u[3]) * rt;
+  }
+  static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) {
+    drift(u, p, hill(u, p), du);
+  }
+  static __device__ __forceinline__ T sqrt0(T x) { return M<T>::sqrt(M<T>::max(x, T(0))); }
+  static __device__ __forceinline__ void sde(const T* u, const T* p, T, T sq, const T* z, T* a,
+                                             T* b) {
+    const T H = hill(u, p);
+    drift(u, p, H, a);
+    const T e = p[5] * sq;
+    const T er = e * M<T>::sqrt(M<T>::rcp(p[2]));  // eta sq / sqrt(tau)
+    const T r0 = sqrt0(p[3] + H), r1 = sqrt0(u[0]), r2 = sqrt0(u[1]), r3 = sqrt0(u[2]),
+            r4 = sqrt0(u[3]);
+    b[0] = e * M<T>::fma(r0, z[0], -(r1 * z[1]));
+    b[1] = er * M<T>::fma(r1, z[2], -(r2 * z[3]));
+    b[2] = er * M<T>::fma(r2, z[4], -(r3 * z[5]));
+    b[3] = er * M<T>::fma(r3, z[6], -(r4 * z[7]));
   }
 };
 

@@ -311,7 +311,12 @@ enum { METH_FIX_TSIT5 = 0, METH_FIX_RK4 = 1, METH_FIX_EM = 2 };
 template <class RHS, class T, int METH>
 struct Fixed {
   static constexpr int D = RHS::D, P = RHS::P;
-  static constexpr int kSub = (METH == METH_FIX_EM) ? Normals<T>::per_call : 1;
+  // Euler-Maruyama step k uses normals k*NW .. k*NW + NW - 1 of the trajectory's stream: one
+  // Philox call serves kSub steps (NW <= per_call) or one step takes kCalls calls.
+  static constexpr int kNW = RHS::NW > 0 ? RHS::NW : 1, kPC = Normals<T>::per_call;
+  static_assert(kPC % kNW == 0 || kNW % kPC == 0, "normals per step vs per Philox call");
+  static constexpr int kSub = (METH == METH_FIX_EM && kNW <= kPC) ? kPC / kNW : 1;
+  static constexpr int kCalls = (METH == METH_FIX_EM && kNW > kPC) ? kNW / kPC : 1;
 
   T u[D], fk[D], p[P];
   T h_reg, h_last, t0f;
@@ -363,7 +368,7 @@ struct Fixed {
     }
   }
 
-  __device__ __forceinline__ void one_step(const SolveArgs& a, const T* z, int sub) {
+  __device__ __forceinline__ void one_step(const SolveArgs& a, const T* z) {
     const T h = (k == n - 1) ? h_last : h_reg;
     const T tk = T(METH == METH_FIX_EM || !RHS::autonomous ? t0f + T(k) * h_reg : T(0));
     T unew[D];
@@ -375,7 +380,7 @@ struct Fixed {
     } else if (METH == METH_FIX_RK4) {
       rk4_step<RHS, T>(u, p, tk, h, unew);
     } else {
-      em_step(u, p, tk, h, z[sub], unew);
+      em_step(u, p, tk, h, z, unew);
     }
 #pragma unroll
     for (int j = 0; j < D; ++j) u[j] = unew[j];
@@ -385,31 +390,36 @@ struct Fixed {
 
   template <class R = RHS>
   __device__ __forceinline__ typename std::enable_if<R::has_noise>::type em_step(
-      const T* uu, const T* pp, T tk, T h, T z, T* unew) {
-    T dr[D], df[D];
-    RHS::f(uu, pp, tk, dr);
-    RHS::g(uu, pp, tk, df);
-    const T sq = M<T>::sqrt(h);
-    // increment first (a h + b sqrt(h) Z), then one rounding at the scale of X
+      const T* uu, const T* pp, T tk, T h, const T* z, T* unew) {
+    T dr[D], nz[D];
+    RHS::sde(uu, pp, tk, M<T>::sqrt(h), z, dr, nz);
+    // increment first (a h + sum_m b_m sqrt(h) Z_m), then one rounding at the scale of X
 #pragma unroll
-    for (int j = 0; j < D; ++j) unew[j] = uu[j] + M<T>::fma(dr[j], h, (df[j] * sq) * z);
+    for (int j = 0; j < D; ++j) unew[j] = uu[j] + M<T>::fma(dr[j], h, nz[j]);
   }
   template <class R = RHS>
   __device__ __forceinline__ typename std::enable_if<!R::has_noise>::type em_step(
-      const T*, const T*, T, T, T, T*) {}
+      const T*, const T*, T, T, const T*, T*) {}
 
   __device__ __forceinline__ bool advance(const SolveArgs& a) {
     if (k >= nrun) return true;
     if (METH == METH_FIX_EM) {
-      T z[Normals<T>::per_call];
-      const uint4 x = Philox::call(a.seed, (unsigned long long)(a.index_offset + idx),
-                                   (unsigned long long)(k / kSub));
-      Normals<T>::draw(x, z);
+      const unsigned long long stream = (unsigned long long)(a.index_offset + idx);
+      T z[kPC * kCalls];
+      if (kCalls == 1) {
+        Normals<T>::draw(Philox::call(a.seed, stream, (unsigned long long)(k / kSub)), z);
 #pragma unroll
-      for (int sub = 0; sub < kSub; ++sub)
-        if (k < nrun) one_step(a, z, sub);
+        for (int sub = 0; sub < kSub; ++sub)
+          if (k < nrun) one_step(a, z + sub * kNW);
+      } else {
+#pragma unroll
+        for (int c = 0; c < kCalls; ++c)
+          Normals<T>::draw(Philox::call(a.seed, stream, (unsigned long long)(k * kCalls + c)),
+                           z + c * kPC);
+        one_step(a, z);
+      }
     } else {
-      one_step(a, nullptr, 0);
+      one_step(a, nullptr);
     }
     return k >= nrun;
   }

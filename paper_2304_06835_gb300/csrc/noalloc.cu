@@ -56,6 +56,7 @@ bool dims_of(int rhs_id, int* D, int* P) {
     case ENS_RHS_LORENZ: *D = 3; *P = 3; return true;
     case ENS_RHS_ROBERTSON: *D = 3; *P = 3; return true;
     case ENS_RHS_GBM: *D = 1; *P = 2; return true;
+    case ENS_RHS_CRN: *D = 4; *P = 6; return true;
   }
   return false;
 }
@@ -75,8 +76,10 @@ int check_args(int rhs_id, long long N, const void* params, const void* u0, cons
   if (o->dtype != ENS_F32 && o->dtype != ENS_F64) return set_last_error(ENS_EINVAL, "unknown dtype");
   if (o->layout != ENS_LAYOUT_ROWMAJOR && o->layout != ENS_LAYOUT_SOA)
     return set_last_error(ENS_EINVAL, "unknown layout");
-  if (o->alg == ENS_EM && rhs_id != ENS_RHS_GBM)
-    return set_last_error(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM)");
+  if (o->alg == ENS_EM && rhs_id != ENS_RHS_GBM && rhs_id != ENS_RHS_CRN)
+    return set_last_error(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM, CRN)");
+  if (rhs_id == ENS_RHS_CRN && o->alg != ENS_EM)
+    return set_last_error(ENS_EINVAL, "the CRN model takes Euler-Maruyama only");
   if (fixed_alg(o->alg) && !(o->dt > 0 && std::isfinite(o->dt)))
     return set_last_error(ENS_EINVAL, "fixed-step methods need a finite dt > 0");
   if (!fixed_alg(o->alg) && (!(o->abstol >= 1e-30) || !std::isfinite(o->abstol) ||

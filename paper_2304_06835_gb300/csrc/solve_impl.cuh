@@ -113,16 +113,22 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
                            bool* supported, cudaFuncAttributes* attr, int* bps,
                            CostScratch* cs) {
   *supported = true;
-  switch (alg) {
-    case ENS_TSIT5_FIXED: return run_integ<Fixed<RHS, T, METH_FIX_TSIT5>>(a, cfg, s, attr, bps, cs);
-    case ENS_TSIT5_ADAPTIVE: return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps, cs);
-    case ENS_RK4: return run_integ<Fixed<RHS, T, METH_FIX_RK4>>(a, cfg, s, attr, bps, cs);
-    case ENS_ROS23: return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps, cs);
-    case ENS_EM:
-      if constexpr (RHS::has_noise) {
-        return run_integ<Fixed<RHS, T, METH_FIX_EM>>(a, cfg, s, attr, bps, cs);
-      }
-      break;
+  if constexpr (RHS::sde_only) {
+    if (alg == ENS_EM) return run_integ<Fixed<RHS, T, METH_FIX_EM>>(a, cfg, s, attr, bps, cs);
+  } else {
+    switch (alg) {
+      case ENS_TSIT5_FIXED:
+        return run_integ<Fixed<RHS, T, METH_FIX_TSIT5>>(a, cfg, s, attr, bps, cs);
+      case ENS_TSIT5_ADAPTIVE:
+        return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps, cs);
+      case ENS_RK4: return run_integ<Fixed<RHS, T, METH_FIX_RK4>>(a, cfg, s, attr, bps, cs);
+      case ENS_ROS23: return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps, cs);
+      case ENS_EM:
+        if constexpr (RHS::has_noise) {
+          return run_integ<Fixed<RHS, T, METH_FIX_EM>>(a, cfg, s, attr, bps, cs);
+        }
+        break;
+    }
   }
   *supported = false;
   return cudaSuccess;

@@ -54,7 +54,8 @@ def _ptr(t):
 
 
 class EnsembleSolver:
-    """One solver handle for one right-hand side ("lorenz", "robertson" or "gbm")."""
+    """One solver handle for one right-hand side ("lorenz", "robertson", "gbm" or "crn"; the
+    CRN takes alg="em" only)."""
 
     def __init__(self, rhs: str):
         self.rhs = rhs
@@ -264,7 +265,7 @@ def normals(seed, n_traj, n_per, dtype=torch.float32, index_offset=0, device="cu
 class EnsembleBatch:
     """Several sub-problems solved by one call (one CUDA graph launch with graph=True).
 
-    items: list of dicts with keys rhs ("lorenz" / "robertson" / "gbm"), params, u0, tspan
+    items: list of dicts with keys rhs ("lorenz" / "robertson" / "gbm" / "crn"), params, u0, tspan
     (CUDA tensors, one dtype per item), alg, layout (default "soa") and any ens_solve option
     (dt, abstol, reltol, dt0, maxiters, saveat, seed, index_offset, ...).  Outputs are
     allocated here: ``batch.outputs[i] = (out, status, stats)``.
