@@ -71,6 +71,8 @@ WORKLOADS = {
                              N=1 << 20, t1=1.0, dt=1e-3, steps=300),
     "robertson_ros23_f64": dict(kind="solve", rhs="robertson", alg="ros23", dtype="f64",
                                 N=1 << 18, t1=1e5, tol=1e-6, dt0=1e-4, steps=20),
+    "lorenz_dense_f32": dict(kind="solve", rhs="lorenz", alg="tsit5", dtype="f32", N=1 << 20,
+                             t1=10.0, tol=1e-5, saves=256, dense=True, steps=200),
     "crn_em_f32": dict(kind="solve", rhs="crn", alg="em", dtype="f32", N=10 ** 6, t1=1000.0,
                        dt=0.1, seed=2024, steps=5),
     "crn_em_f64": dict(kind="solve", rhs="crn", alg="em", dtype="f64", N=10 ** 6, t1=1000.0,
@@ -145,6 +147,9 @@ def solve_kwargs(w):
         kw["dt0"] = w["dt0"]
     if "seed" in w:
         kw["seed"] = w["seed"]
+    if w.get("saves"):  # equally spaced save times over [0, t1]
+        kw["saveat"] = list(np.linspace(0.0, w["t1"], w["saves"]))
+        kw["dense"] = bool(w.get("dense"))
     return kw
 
 
@@ -317,7 +322,8 @@ class SolveRunner:
         t = lambda a: torch.tensor(a.T.copy(), dtype=self.dt_t, device=dev)
         self.Pd, self.Ud, self.Td = t(self.P), t(self.U), t(self.T)
         D = self.U.shape[1]
-        self.out = torch.empty((D, N), dtype=self.dt_t, device=dev)
+        S = w.get("saves", 0)
+        self.out = torch.empty((S, D, N) if S else (D, N), dtype=self.dt_t, device=dev)
         self.status = torch.empty(N, dtype=torch.int8, device=dev)
         self.stats = torch.empty((3, N), dtype=torch.int32, device=dev)
         self.solver = ens.EnsembleSolver(w["rhs"])
@@ -368,7 +374,8 @@ class SolveRunner:
         pin = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=npdt)).pin_memory()
         Pp, Up, Tp = pin(self.P.T), pin(self.U.T), pin(self.T.T)
         D = self.U.shape[1]
-        outp = torch.empty((D, N), dtype=Pp.dtype).pin_memory()
+        S = max(1, w.get("saves", 0))
+        outp = torch.empty((S, D, N), dtype=Pp.dtype).pin_memory()
         stp = torch.empty(N, dtype=torch.int8).pin_memory()
         o, keep = ens.make_opts(w["alg"], _lib.F32 if w["dtype"] == "f32" else _lib.F64, "soa",
                                 schedule=a.schedule, block=a.block, tpt=a.tpt,
@@ -391,7 +398,7 @@ class SolveRunner:
         del keep
         return {"value": N / el, "unit": "trajectories/s",
                 "h2d_bytes_per_step": int(N * es * (self.P.shape[1] + D + 2)),
-                "d2h_bytes_per_step": int(N * es * D + N)}
+                "d2h_bytes_per_step": int(N * es * D * S + N)}
 
 
 class AdjointRunner:
@@ -867,7 +874,8 @@ def main():
                                       "smaller case, scaled by units processed" % prof["kernel"])
     e2e = None if args.no_e2e else runner.e2e(stream)
     cfg = {"workload": args.workload, "model": w["rhs"], "alg": w["alg"], "N": N,
-           "tspan": [0.0, w["t1"]], **{k: w[k] for k in ("tol", "dt", "dt0", "every", "seed") if k in w},
+           "tspan": [0.0, w["t1"]],
+           **{k: w[k] for k in ("tol", "dt", "dt0", "every", "seed", "saves", "dense") if k in w},
            "layout": "soa", "l2": "flushed between steps (256 MB write outside events)",
            "parallelism": "dp%d" % world}
     if w["kind"] == "solve":

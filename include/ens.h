@@ -119,6 +119,13 @@ typedef struct {
   int blocks_per_sm;      /* persistent schedule: resident blocks per SM (0 = as many as fit).
                              Fewer resident lanes each take more trajectories from the queue,
                              which shortens the drain at the end of the queue. */
+  int dense;              /* TSIT5_ADAPTIVE with save times: 0 = the steps are cut to land on
+                             each save time; 1 = the steps run to tf uncut and each save time
+                             s in a step [t_n, t_n + h] takes the dense output
+                             u_n + h sum_i b_i(theta) k_i, theta = (s - t_n)/h: a C1
+                             continuous extension of order 4 of the Tsit5 pair (Sec. 5.1.1
+                             solution storage), so the steps and the final state are those
+                             of the solve without save times.  Other algorithms ignore it. */
 } ens_opts;
 
 /* Fill *o with defaults: TSIT5_ADAPTIVE, F32, SOA, abstol=reltol=1e-6, maxiters=1e6, auto. */

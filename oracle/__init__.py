@@ -59,7 +59,10 @@ def lib():
                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                 dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                 ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_longlong,
-                dp, ctypes.POINTER(ctypes.c_byte), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+                dp, ctypes.POINTER(ctypes.c_byte), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
+                ctypes.c_int]
+            L.oracle_tsit5_dense.restype = None
+            L.oracle_tsit5_dense.argtypes = [dp]
             L.oracle_step.restype = ctypes.c_int
             L.oracle_step.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, dp, dp]
@@ -103,12 +106,13 @@ def default_threads() -> int:
 
 def solve(rhs, alg, params, u0, tspan, *, dt=0.0, abstol=1e-6, reltol=1e-3, dt0=0.0,
           maxiters=1_000_000, saveat=None, seed=0, index_offset=0, precision="f64",
-          nthreads=None):
+          nthreads=None, dense=False):
     """Solve an ensemble.  params [N,P], u0 [N,D], tspan [N,2] (row-major, float64).
 
     precision "f32" runs the same algorithms in float arithmetic on the given (already
     float-representable) inputs; "f64_f32stream" is FP64 arithmetic driven by the FP32 normal
-    stream (4 normals per Philox call).  Returns (out [N,S,D] or [N,D], status [N], stats [N,3]).
+    stream (4 normals per Philox call).  dense=True (adaptive Tsit5 with saveat): the steps
+    run to tf without being cut at save times, which take the dense output (oracle/dense.py).  Returns (out [N,S,D] or [N,D], status [N], stats [N,3]).
     """
     rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
     alg_id = ALG[alg] if isinstance(alg, str) else int(alg)
@@ -129,7 +133,7 @@ def solve(rhs, alg, params, u0, tspan, *, dt=0.0, abstol=1e-6, reltol=1e-3, dt0=
         _dp(sv) if sv is not None and sv.size else None, 0 if sv is None else int(sv.size),
         int(seed), int(index_offset), _dp(out),
         status.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)),
-        stats.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), nt)
+        stats.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), nt, 1 if dense else 0)
     if rc != 0:
         raise ValueError("oracle_solve rejected its arguments")
     if sv is None or sv.size == 0:
@@ -150,6 +154,13 @@ def step(rhs, alg, u, p, t, h, z=0.0):
                          _dp(err)) != 0:
         raise ValueError("bad step arguments")
     return unew, err
+
+
+def tsit5_dense():
+    """The typed dense-output coefficients r [7, 4] of the C++ oracle."""
+    r = np.empty(28)
+    lib().oracle_tsit5_dense(_dp(r))
+    return r.reshape(7, 4)
 
 
 def tsit5_tableau():

@@ -278,7 +278,7 @@ T rms_scaled(const T* x, const T* sc, int D) {
 // k7 = f(unew, t+h).  Stage formula: U_i = u + h sum_j a_ij k_j, k_i = f(U_i, t + c_i h).
 template <class T>
 void tsit5_step(int id, int D, const T* u, const T* p, T t, T h, const T* k1, T* unew, T* err,
-                T* k7) {
+                T* k7, T (*kout)[8] = nullptr) {
   T k[7][8];
   T U[8];
   for (int j = 0; j < D; ++j) k[0][j] = k1[j];
@@ -302,6 +302,37 @@ void tsit5_step(int id, int D, const T* u, const T* p, T t, T h, const T* k1, T*
     for (int m = 0; m < 7; ++m) s += T(TS_BHAT[m] - TS_B[m]) * k[m][j];
     err[j] = h * s;
     k7[j] = k[6][j];
+  }
+  if (kout)
+    for (int i = 0; i < 7; ++i)
+      for (int j = 0; j < D; ++j) kout[i][j] = k[i][j];
+}
+
+// Dense output of a Tsit5 step: u(t_n + theta h) = u_n + h sum_i b_i(theta) k_i with
+// b_i(theta) = sum_q TS_DENSE[i][q] theta^(q+1).  TS_DENSE is the continuous extension of
+// order 4 defined by the order conditions of the trees of order <= 4 at every theta,
+// b_i(1) = b_i and C1 continuity, with the one free parameter minimising the integrated
+// 5th-order defect (values from oracle/dense.py, which derives them in 40 digits).
+const double TS_DENSE[7][4] = {
+    {1.0, -2.7697190760997743, 2.925281219471809, -1.0591013765539699},
+    {0.0, 0.12894208371183252, -0.2178841674236653, 0.09894208371183272},
+    {0.0, 3.956917849412212, -5.994277097166426, 2.5172488981687136},
+    {0.0, -12.899911070336683, 31.315856437088335, -17.03693679264791},
+    {0.0, 39.47651640903875, -92.11331087982184, 49.346724955347},
+    {0.0, -29.443928026595056, 68.1866981495892, -36.418059598894374},
+    {0.0, 1.5511818308687129, -4.102363661737424, 2.551181830868712}};
+
+template <class T>
+void tsit5_dense(int D, const T* u, T h, const T (*k)[8], T theta, T* out) {
+  T bw[7];
+  for (int i = 0; i < 7; ++i)
+    bw[i] = theta * (T(TS_DENSE[i][0]) +
+                     theta * (T(TS_DENSE[i][1]) +
+                              theta * (T(TS_DENSE[i][2]) + theta * T(TS_DENSE[i][3]))));
+  for (int j = 0; j < D; ++j) {
+    T s = 0;
+    for (int i = 0; i < 7; ++i) s += bw[i] * k[i][j];
+    out[j] = u[j] + h * s;
   }
 }
 
@@ -437,6 +468,7 @@ struct Opts {
   unsigned long long seed;
   long long index_offset;
   bool stream_fp64;  // normals from the FP64 stream (2 per Philox call) or the FP32 one (4)
+  bool dense;        // adaptive Tsit5: save times by the dense output, steps not cut at them
 };
 
 // Hairer-Norsett-Wanner I, II.4: starting step size for an order-p method.
@@ -581,9 +613,15 @@ void solve_adaptive(Traj<T>& tr) {
   else h = initial_step<T>(o, tr.u, tr.p, tr.t0, fcur, is_r23 ? 2 : 5, &tr.fevals);
   T qold = T(QOLD_INIT);
   long long attempts = 0;
+  const bool dense = o.dense && !is_r23 && save_mode;
+  if (dense)  // save times equal to t0 take u0; the steps then run to tf uncut
+    while (si < S && T(o.saveat[si]) == tr.t0 && tr.t0 <= tr.tf) {
+      for (int j = 0; j < D; ++j) tr.out[si * D + j] = tr.u[j];
+      ++si;
+    }
 
   for (;;) {
-    const bool stop_is_save = (si < S && T(o.saveat[si]) < tr.tf);
+    const bool stop_is_save = !dense && (si < S && T(o.saveat[si]) < tr.tf);
     const T stop = stop_is_save ? T(o.saveat[si]) : tr.tf;
     const T rem = clk.remaining(stop);
     if (rem <= T(STOP_EPS) * std::max(T(1), std::fabs(stop))) {
@@ -593,8 +631,9 @@ void solve_adaptive(Traj<T>& tr) {
         ++si;
         continue;
       }
-      // reached tf: record every remaining save time equal to tf
-      while (si < S && T(o.saveat[si]) == tr.tf) {
+      // reached tf: record every remaining save time equal to tf (dense: any save left
+      // within the last STOP_EPS of the span)
+      while (si < S && (T(o.saveat[si]) == tr.tf || (dense && T(o.saveat[si]) <= tr.tf))) {
         for (int j = 0; j < D; ++j) tr.out[si * D + j] = tr.u[j];
         ++si;
       }
@@ -608,12 +647,12 @@ void solve_adaptive(Traj<T>& tr) {
       tr.status = ST_DT_MIN;
       break;
     }
-    T unew[8], err[8], fnew[8];
+    T unew[8], err[8], fnew[8], kst[7][8];
     if (is_r23) {
       ros23_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew);
       tr.fevals += 2;
     } else {
-      tsit5_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew);
+      tsit5_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew, dense ? kst : nullptr);
       tr.fevals += 6;
     }
     ++attempts;
@@ -629,6 +668,19 @@ void solve_adaptive(Traj<T>& tr) {
       T fac = T(ETA) * std::pow(qg, -beta1) * std::pow(qold, beta2);
       fac = std::min(T(FAC_MAX), std::max(T(FAC_MIN), fac));
       qold = std::max(q, T(QOLD_INIT));
+      if (dense) {  // save times in (t_n, t_n + hs]: theta = (s - t_n) / hs on the clock
+        while (si < S) {
+          const T sv = T(o.saveat[si]);
+          if (sv > tr.tf) break;
+          const T rs = clk.remaining(sv);
+          if (!(last && sv == stop) && rs > hs) break;
+          if (last && sv == stop)
+            for (int j = 0; j < D; ++j) tr.out[si * D + j] = unew[j];
+          else
+            tsit5_dense<T>(D, tr.u, hs, kst, rs / hs, tr.out + si * D);
+          ++si;
+        }
+      }
       for (int j = 0; j < D; ++j) { tr.u[j] = unew[j]; fcur[j] = fnew[j]; }
       if (last) clk.set(stop);
       else clk.add(hs);
@@ -721,14 +773,14 @@ int oracle_solve(int rhs_id, int alg, int precision, int layout, long long N,
                  double abstol, double reltol, double dt0, long long maxiters,
                  const double* saveat, int n_save, unsigned long long seed,
                  long long index_offset, double* out, signed char* status, long long* stats,
-                 int nthreads) {
+                 int nthreads, int dense) {
   Model m = model_of(rhs_id);
   if (m.D == 0 || N < 0 || alg < 1 || alg > 5) return -1;
   if (alg == ALG_EM && m.Mw == 0) return -1;  // Euler-Maruyama needs an SDE model
   if (rhs_id == RHS_CRN && alg != ALG_EM) return -1;
   if (precision < 0 || precision > 2) return -1;
   Opts o{rhs_id, alg, m.D, m.P, m.Mw, dt, abstol, reltol, dt0, maxiters, saveat, n_save, seed,
-         index_offset, precision == 0};
+         index_offset, precision == 0, dense != 0};
   parallel_for(N, nthreads, [&](long long a, long long b) {
     if (precision != 1)
       solve_range<double>(o, layout, N, a, b, params, u0, tspan, out, status, stats);
@@ -766,6 +818,11 @@ int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t,
   if (err)
     for (int j = 0; j < m.D; ++j) err[j] = e[j];
   return 0;
+}
+
+void oracle_tsit5_dense(double* r) {
+  for (int i = 0; i < 7; ++i)
+    for (int q = 0; q < 4; ++q) r[i * 4 + q] = TS_DENSE[i][q];
 }
 
 void oracle_tsit5_tableau(double* c, double* A, double* b, double* bhat) {

@@ -34,6 +34,7 @@ class EnsOpts(ctypes.Structure):
         ("seed", ctypes.c_ulonglong), ("index_offset", ctypes.c_longlong),
         ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
         ("refill_min", ctypes.c_int), ("order", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+        ("dense", ctypes.c_int),
     ]
 
 

@@ -325,6 +325,7 @@ void fill_args(SolveArgs* a, long long N, const void* params, const void* u0, co
   a->reltol_f = (float)o->reltol;
   a->dt0_f = (float)o->dt0;
   a->refill_min = o->refill_min > 0 ? (o->refill_min > 32 ? 32 : o->refill_min) : 4;
+  a->dense = o->dense != 0 && o->n_save > 0;
   a->seed = o->seed;
   a->index_offset = o->index_offset;
   a->queue = queue;

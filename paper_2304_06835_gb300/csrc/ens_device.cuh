@@ -45,6 +45,12 @@ struct M<float> {
   static __device__ __forceinline__ float fast_pow(float a, float b) {
     return ex2_approx(b * lg2_approx(a));
   }
+  // MUFU square root (sqrt.approx, about 1 ulp; subnormal inputs flush to 0)
+  static __device__ __forceinline__ float fast_sqrt(float a) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+    return y;
+  }
   static __device__ __forceinline__ bool finite(float a) { return isfinite(a); }
   static constexpr double dtmin_factor = 1e-9;
 };
@@ -62,6 +68,7 @@ struct M<double> {
   static __device__ __forceinline__ double pow(double a, double b) { return ::pow(a, b); }
   static __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double fast_pow(double a, double b) { return ::pow(a, b); }
+  static __device__ __forceinline__ double fast_sqrt(double a) { return ::sqrt(a); }
   static __device__ __forceinline__ bool finite(double a) { return isfinite(a); }
   static constexpr double dtmin_factor = 1e-14;
 };
@@ -160,14 +167,18 @@ struct GBM {
 // Square-root arguments and Hill bases are clamped at 0 (the form is undefined for negative
 // amounts, which a discrete path can reach).  sqrt(x/tau) is formed as sqrt(x) sqrt(1/tau),
 // so each amount's square root serves both terms it appears in.
+// In float the powers are ex2(n lg2 x), the division and the square roots the MUFU forms:
+// relative error <= ~5e-6 in (S[sigma])^n for the table's ranges (n lg2 x <= ~30, lg2 and
+// ex2 good to 2^-22), ~1 ulp elsewhere -- far below the step's own O(h) error and inside the
+// FP32 parity bounds.  Double keeps the correctly rounded library functions.
 template <class T>
 struct CRN {
   static constexpr int D = 4, P = 6, NW = 8;
   static constexpr bool autonomous = true, has_noise = true, sde_only = true;
   static __device__ __forceinline__ T hill(const T* u, const T* p) {
-    const T x = M<T>::pow(M<T>::max(p[0] * u[0], T(0)), p[4]);
-    const T y = M<T>::pow(M<T>::max(p[1] * u[3], T(0)), p[4]);
-    return x / ((x + y) + T(1));
+    const T x = M<T>::fast_pow(M<T>::max(p[0] * u[0], T(0)), p[4]);
+    const T y = M<T>::fast_pow(M<T>::max(p[1] * u[3], T(0)), p[4]);
+    return M<T>::fast_div(x, (x + y) + T(1));
   }
   static __device__ __forceinline__ void drift(const T* u, const T* p, T H, T* a) {
     const T rt = M<T>::rcp(p[2]);
@@ -179,7 +190,7 @@ struct CRN {
   static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) {
     drift(u, p, hill(u, p), du);
   }
-  static __device__ __forceinline__ T sqrt0(T x) { return M<T>::sqrt(M<T>::max(x, T(0))); }
+  static __device__ __forceinline__ T sqrt0(T x) { return M<T>::fast_sqrt(M<T>::max(x, T(0))); }
   static __device__ __forceinline__ void sde(const T* u, const T* p, T, T sq, const T* z, T* a,
                                              T* b) {
     const T H = hill(u, p);
@@ -222,7 +233,7 @@ struct Ts5 {
 // (the error estimate is h * es).
 template <class RHS, class T, bool WANT_ERR>
 __device__ __forceinline__ void tsit5_step(const T* u, const T* p, T t, T h, const T* k1,
-                                           T* unew, T* es, T* k7) {
+                                           T* unew, T* es, T* k7, T* kmid = nullptr) {
   constexpr int D = RHS::D;
   typedef M<T> m;
   T U[D], k2[D], k3[D], k4[D], k5[D], k6[D];
@@ -268,6 +279,16 @@ __device__ __forceinline__ void tsit5_step(const T* u, const T* p, T t, T h, con
     unew[j] = m::fma(h, s, u[j]);
   }
   RHS::f(unew, p, t + h, k7);
+  if (kmid) {  // stages 2..6 for the dense output
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      kmid[j] = k2[j];
+      kmid[D + j] = k3[j];
+      kmid[2 * D + j] = k4[j];
+      kmid[3 * D + j] = k5[j];
+      kmid[4 * D + j] = k6[j];
+    }
+  }
   if (WANT_ERR) {
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -280,6 +301,46 @@ __device__ __forceinline__ void tsit5_step(const T* u, const T* p, T t, T h, con
       s = m::fma(T(Ts5::bt7), k7[j], s);
       es[j] = s;
     }
+  }
+}
+
+// Dense output of a Tsit5 step (Sec. 5.1.1 solution storage; the pair's interpolant is not
+// printed in the paper): u(t_n + theta h) = u_n + h sum_i b_i(theta) k_i with
+// b_i(theta) = theta (r_i1 + theta (r_i2 + theta (r_i3 + theta r_i4))).  The r are the C1
+// continuous extension of order 4: for every theta the elementary-weight conditions of the
+// 8 rooted trees of order <= 4 hold, b_i(1) = b_i, b_i'(0) = [i = 1], b_i'(1) = [i = 7]; of
+// the one-parameter family these leave, the member with the smallest integrated squared
+// 5th-order defect (derived in 40-digit arithmetic from the pair's coefficients).
+__host__ __device__ constexpr double ts5_dense(int i, int q) {
+  constexpr double r[7][4] = {
+      {1.0, -2.7697190760997743, 2.925281219471809, -1.0591013765539699},
+      {0.0, 0.12894208371183252, -0.2178841674236653, 0.09894208371183272},
+      {0.0, 3.956917849412212, -5.994277097166426, 2.5172488981687136},
+      {0.0, -12.899911070336683, 31.315856437088335, -17.03693679264791},
+      {0.0, 39.47651640903875, -92.11331087982184, 49.346724955347},
+      {0.0, -29.443928026595056, 68.1866981495892, -36.418059598894374},
+      {0.0, 1.5511818308687129, -4.102363661737424, 2.551181830868712}};
+  return r[i][q];
+}
+
+template <class RHS, class T>
+__device__ __forceinline__ void tsit5_dense(const T* u, T h, const T* k1, const T* kmid,
+                                            const T* k7, T theta, T* out) {
+  constexpr int D = RHS::D;
+  T bw[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i)
+    bw[i] = theta * M<T>::fma(theta, M<T>::fma(theta, M<T>::fma(theta, T(ts5_dense(i, 3)),
+                                                                 T(ts5_dense(i, 2))),
+                                               T(ts5_dense(i, 1))),
+                              T(ts5_dense(i, 0)));
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    T s = bw[0] * k1[j];
+#pragma unroll
+    for (int i = 1; i < 6; ++i) s = M<T>::fma(bw[i], kmid[(i - 1) * D + j], s);
+    s = M<T>::fma(bw[6], k7[j], s);
+    out[j] = M<T>::fma(h, s, u[j]);
   }
 }
 
@@ -459,16 +520,19 @@ template <>
 struct Normals<float> {
   static constexpr int per_call = 4;
   static __device__ __forceinline__ float uni(uint32_t x) {
-    // ((x >> 9) + 0.5) * 2^-23: exact in float, inside (0, 1)
-    return __fmaf_rn(__uint2float_rn(x >> 9), 1.1920928955078125e-07f, 5.9604644775390625e-08f);
+    // ((x >> 9) + 0.5) * 2^-23, exact and inside (0, 1), without an integer conversion: the
+    // bits 1.m (m = x >> 9) are 1 + m 2^-23, and subtracting 1 - 2^-24 is exact (Sterbenz)
+    return __int_as_float(0x3F800000u | (x >> 9)) - 0.99999994039535522f;
   }
   static __device__ __forceinline__ void draw(uint4 x, float* z) {
     float s, c;
-    float r = sqrtf(-2.0f * logf(uni(x.x)));
+    // log and sincospi stay the accurate library functions (the MUFU log loses relative
+    // accuracy as u -> 1); the radius square root is the MUFU one (~1 ulp)
+    float r = M<float>::fast_sqrt(-2.0f * logf(uni(x.x)));
     sincospif(2.0f * uni(x.y), &s, &c);
     z[0] = r * c;
     z[1] = r * s;
-    r = sqrtf(-2.0f * logf(uni(x.z)));
+    r = M<float>::fast_sqrt(-2.0f * logf(uni(x.z)));
     sincospif(2.0f * uni(x.w), &s, &c);
     z[2] = r * c;
     z[3] = r * s;

@@ -136,15 +136,18 @@ __device__ __forceinline__ T rms_scaled(const T* x, const T* sc, int D) {
 
 // ------------------------------------------------------------------------------------------
 // Adaptive integrators: Tsit5 with PI control (Sec. 3.1) and Rosenbrock23 (Sec. 3.2.1).
-enum { METH_TSIT5 = 0, METH_ROS23 = 1 };
+// METH_TSIT5_DENSE is Tsit5 whose save times take the dense output of the step that covers
+// them instead of cutting the steps (the steps are those of the solve without save times).
+enum { METH_TSIT5 = 0, METH_ROS23 = 1, METH_TSIT5_DENSE = 2 };
 
 template <class RHS, class T, int METH>
 struct Adaptive {
   static constexpr int D = RHS::D, P = RHS::P;
+  static constexpr bool kDense = METH == METH_TSIT5_DENSE;
   // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k
-  static constexpr float kOrd = (METH == METH_TSIT5) ? 5.f : 3.f;
-  static constexpr int kInitOrder = (METH == METH_TSIT5) ? 5 : 2;
-  static constexpr int kFevPerAttempt = (METH == METH_TSIT5) ? 6 : 2;
+  static constexpr float kOrd = (METH != METH_ROS23) ? 5.f : 3.f;
+  static constexpr int kInitOrder = (METH != METH_ROS23) ? 5 : 2;
+  static constexpr int kFevPerAttempt = (METH != METH_ROS23) ? 6 : 2;
 
   T u[D], fk[D], p[P];
   Clock<T> t;
@@ -157,7 +160,7 @@ struct Adaptive {
   long long idx;
 
   __device__ __forceinline__ void set_stop(const SolveArgs& a) {
-    stop_is_save = si < a.n_save && T(a.saveat[si]) < tf;
+    stop_is_save = !kDense && si < a.n_save && T(a.saveat[si]) < tf;
     stop = stop_is_save ? T(a.saveat[si]) : tf;
     stop_thr = T(kStopEps) * M<T>::max(T(1), M<T>::abs(stop));
   }
@@ -184,7 +187,34 @@ struct Adaptive {
       write_nan_slot<RHS, T>(a, idx, si);
       ++si;
     }
+    if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
+      while (si < a.n_save && T(a.saveat[si]) == t0 && t0 <= tf) {
+        write_slot<RHS, T>(a, idx, si, u);
+        ++si;
+      }
     set_stop(a);
+  }
+
+  // dense output: every save time in (t_n, t_n + hs] of the accepted step from (u, fk),
+  // theta = (s - t_n) / hs on the compensated clock; a save at the end of the last step is
+  // u_{n+1} itself
+  __device__ __forceinline__ void dense_saves(const SolveArgs& a, T hs, bool last,
+                                              const T* kmid, const T* fnew, const T* unew) {
+    while (si < a.n_save) {
+      const T sv = T(a.saveat[si]);
+      if (sv > tf) break;
+      const T rs = t.remaining(sv);
+      const bool at_end = last && sv == stop;
+      if (!at_end && rs > hs) break;
+      if (at_end) {
+        write_slot<RHS, T>(a, idx, si, unew);
+      } else {
+        T w[D];
+        tsit5_dense<RHS, T>(u, hs, fk, kmid, fnew, rs / hs, w);
+        write_slot<RHS, T>(a, idx, si, w);
+      }
+      ++si;
+    }
   }
 
   // Hairer-Norsett-Wanner I, II.4: starting step size (a heuristic: the FP32 solve forms it
@@ -225,8 +255,9 @@ struct Adaptive {
     if (rem <= stop_thr) {  // arrived at the stop
       do {
         t.set(stop);
-        if (!stop_is_save) {
-          while (si < a.n_save && T(a.saveat[si]) == tf) {
+        if (!stop_is_save) {  // tf (dense: every save left within the arrival threshold)
+          while (si < a.n_save &&
+                 (T(a.saveat[si]) == tf || (kDense && T(a.saveat[si]) <= tf))) {
             write_slot<RHS, T>(a, idx, si, u);
             ++si;
           }
@@ -243,8 +274,9 @@ struct Adaptive {
     const T tnow = t.value();
     const bool capped = attempts >= a.maxiters_i;
     const bool tiny = hs < T(M<T>::dtmin_factor) * M<T>::max(T(1), M<T>::abs(tnow));
-    T unew[D], es[D], fnew[D];
-    if (METH == METH_TSIT5) tsit5_step<RHS, T, true>(u, p, tnow, hs, fk, unew, es, fnew);
+    T unew[D], es[D], fnew[D], kmid[kDense ? 5 * D : 1];
+    if (METH != METH_ROS23)
+      tsit5_step<RHS, T, true>(u, p, tnow, hs, fk, unew, es, fnew, kDense ? kmid : nullptr);
     else ros23_step<RHS, T>(u, p, tnow, hs, fk, unew, es, fnew);
     // q^2 = (1/D) sum_j (E_j / (atol + rtol max(|u_j|, |unew_j|)))^2 with E_j = h es_j.
     // The ratios are formed in FP32 for both precisions (E itself is accumulated in T).
@@ -267,6 +299,7 @@ struct Adaptive {
     }
     ++attempts;
     const bool acc = q2 <= 1.f;
+    if (kDense && acc) dense_saves(a, hs, last, kmid, fnew, unew);
     // PI control: accept fac = eta q_n^{-beta1} q_{n-1}^{beta2} in [0.2, 10];
     // reject fac = max(0.2, eta q_n^{-1/k}).  Exponentials in log2 form (q guarded at 1e-10).
     const float L = lg2_approx(fmaxf(q2, 1e-20f));  // log2 q^2

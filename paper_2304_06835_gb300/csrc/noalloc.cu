@@ -145,6 +145,7 @@ extern "C" int ens_solve_noalloc(int rhs_id, long long N, const void* params, co
   a.reltol_f = (float)o->reltol;
   a.dt0_f = (float)o->dt0;
   a.refill_min = o->refill_min > 0 ? o->refill_min : 4;
+  a.dense = o->dense != 0 && o->n_save > 0;
   a.seed = o->seed;
   a.index_offset = o->index_offset;
   a.queue = (unsigned long long*)(base + kQueueOff);

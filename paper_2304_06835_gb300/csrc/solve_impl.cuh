@@ -120,6 +120,8 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
       case ENS_TSIT5_FIXED:
         return run_integ<Fixed<RHS, T, METH_FIX_TSIT5>>(a, cfg, s, attr, bps, cs);
       case ENS_TSIT5_ADAPTIVE:
+        if (a && a->dense)
+          return run_integ<Adaptive<RHS, T, METH_TSIT5_DENSE>>(a, cfg, s, attr, bps, cs);
         return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps, cs);
       case ENS_RK4: return run_integ<Fixed<RHS, T, METH_FIX_RK4>>(a, cfg, s, attr, bps, cs);
       case ENS_ROS23: return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps, cs);

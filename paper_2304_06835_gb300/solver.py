@@ -22,7 +22,8 @@ _NP_DT = {np.dtype(np.float32): _lib.F32, np.dtype(np.float64): _lib.F64}
 
 def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-6, reltol=1e-6,
               dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
-              schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0):
+              schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0,
+              dense=False):
     o = _lib.EnsOpts()
     _lib.lib().ens_opts_default(ctypes.byref(o))
     o.alg = _lib.ALG[alg] if isinstance(alg, str) else int(alg)
@@ -46,6 +47,7 @@ def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-
     o.refill_min = int(refill_min)
     o.order = _lib.ORDER[order] if isinstance(order, str) else int(order)
     o.blocks_per_sm = int(blocks_per_sm)
+    o.dense = 1 if dense else 0
     return o, keep
 
 
@@ -89,7 +91,11 @@ class EnsembleSolver:
     def solve(self, params, u0, tspan, alg="tsit5", *, layout="rowmajor", dt=0.0, abstol=1e-6,
               reltol=1e-6, dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
               schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0,
-              want_status=True, want_stats=False, out=None, status=None, stats=None, stream=None):
+              dense=False, want_status=True, want_stats=False, out=None, status=None, stats=None,
+              stream=None):
+        """Solve the ensemble on the GPU (device tensors in and out).  dense=True (adaptive
+        Tsit5 with saveat): save times take the step's dense output instead of cutting the
+        steps, so the steps and final state are those of the solve without save times."""
         if not (params.is_cuda and u0.is_cuda and tspan.is_cuda):
             raise ValueError("params, u0 and tspan must be CUDA tensors")
         if params.dtype not in _TORCH_DT or u0.dtype != params.dtype or tspan.dtype != params.dtype:
@@ -111,7 +117,7 @@ class EnsembleSolver:
             stats = torch.empty((3, N), dtype=torch.int32, device=dev)
         o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, dt, abstol, reltol, dt0, maxiters,
                             saveat, seed, index_offset, schedule, block, tpt, refill_min, order,
-                            blocks_per_sm)
+                            blocks_per_sm, dense)
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
         _lib.check(_lib.lib().ens_solve(self._h, N, _ptr(params), _ptr(u0), _ptr(tspan),
                                         ctypes.byref(o), _ptr(out), _ptr(status), _ptr(stats),

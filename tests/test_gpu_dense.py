@@ -1,0 +1,112 @@
+"""GPU parity of the dense output (adaptive Tsit5 with dense=True) against the oracle's dense
+saving on the same inputs, through the C ABI.
+
+* FP64, non-chaotic Lorenz (rho < 10, [0, 10]) and the [0, 1] workload: every save within
+  1e-12 of the oracle (normwise, both follow the same steps and the same interpolant);
+  identical step counts.
+* The steps and the final state equal those of the same GPU solve without save times,
+  bit for bit (dense saving does not touch the step sequence).
+* Save times before t0 / after tf are NaN, at t0 / tf the initial / final state.
+* FP32: every save within 10x tolerance of a tol-1e-12 FP64 reference.
+* Rosenbrock23 ignores the flag (bit-identical to the stepped saving).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+SV = np.array([-1.0, 0.0, 0.0137, 0.25, 0.5, 0.75, 0.999, 1.0, 2.0])
+
+
+def dev(a, dt=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dt, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().double().numpy()
+
+
+def normwise(out, ref):
+    d = np.abs(out - ref)
+    return np.nanmax(d.reshape(d.shape[0], -1), axis=1) / np.maximum(
+        np.nanmax(np.abs(ref).reshape(ref.shape[0], -1), axis=1), 1.0)
+
+
+@pytest.fixture(scope="module")
+def lor():
+    from paper_2304_06835_gb300 import EnsembleSolver
+    s = EnsembleSolver("lorenz")
+    yield s
+    s.close()
+
+
+def _nonchaotic(N, t1):
+    P, U, T = workloads.lorenz_random(N, seed=31, t1=t1)
+    P[:, 1] = np.linspace(0.5, 9.5, N)
+    return P, U, T
+
+
+@pytest.mark.parametrize("schedule", ["direct", "persistent"])
+@pytest.mark.parametrize("t1", [1.0, 10.0])
+def test_dense_fp64_matches_oracle(lor, schedule, t1):
+    N = 700 + 13
+    P, U, T = _nonchaotic(N, t1) if t1 > 1 else workloads.lorenz_random(N, seed=32, t1=t1)
+    sv = SV * t1
+    kw = dict(abstol=1e-8, reltol=1e-8)
+    ref, rst, rstats = oracle.solve("lorenz", "tsit5", P, U, T, saveat=sv, dense=True, **kw)
+    out, st, stats = lor.solve(dev(P), dev(U), dev(T), alg="tsit5", saveat=sv, dense=True,
+                               schedule=schedule, want_stats=True, **kw)
+    o = host(out)
+    np.testing.assert_array_equal(np.isnan(o), np.isnan(ref))
+    assert np.all(np.isnan(o[:, 0])) and np.all(np.isnan(o[:, -1]))
+    np.testing.assert_array_equal(o[:, 1], U)
+    g = stats.cpu().numpy().T
+    same = np.all(g[:, :2] == rstats[:, :2], axis=1)
+    assert same.mean() >= 0.99
+    assert normwise(o[same], ref[same]).max() <= 1e-12
+    # the steps and the final state are those of the solve without save times
+    f, _, fstats = lor.solve(dev(P), dev(U), dev(T), alg="tsit5", schedule=schedule,
+                             want_stats=True, **kw)
+    np.testing.assert_array_equal(fstats.cpu().numpy(), stats.cpu().numpy())
+    np.testing.assert_array_equal(host(f), o[:, 7])
+
+
+def test_dense_soa_layout_equals_rowmajor(lor):
+    P, U, T = workloads.lorenz_random(1000, seed=33, t1=1.0)
+    kw = dict(abstol=1e-7, reltol=1e-7, saveat=SV, dense=True)
+    o1, _, _ = lor.solve(dev(P), dev(U), dev(T), alg="tsit5", **kw)
+    t = lambda a: dev(np.ascontiguousarray(a.T))
+    o2, _, _ = lor.solve(t(P), t(U), t(T), alg="tsit5", layout="soa", **kw)
+    np.testing.assert_array_equal(host(o1), np.transpose(host(o2), (2, 0, 1)))
+
+
+def test_dense_fp32_within_tolerance_of_reference(lor):
+    P, U, T = _nonchaotic(2048, 10.0)
+    P, U, T = (np.asarray(a, np.float32).astype(np.float64) for a in (P, U, T))
+    sv = SV * 10.0
+    tol = 1e-5
+    ref, _, _ = oracle.solve("lorenz", "tsit5", P, U, T, abstol=1e-12, reltol=1e-12, saveat=sv)
+    d32 = lambda a: dev(a, torch.float32)
+    out, st, _ = lor.solve(d32(P), d32(U), d32(T), alg="tsit5", abstol=tol, reltol=tol,
+                           saveat=sv, dense=True)
+    o = host(out)
+    assert int(st.abs().sum()) == 0
+    inner = (slice(None), slice(1, 8))
+    assert np.all(np.abs(o[inner] - ref[inner]) <= 10 * (tol + tol * np.abs(ref[inner])))
+
+
+def test_dense_flag_ignored_by_rosenbrock():
+    from paper_2304_06835_gb300 import EnsembleSolver
+    r = EnsembleSolver("robertson")
+    P, U, T = workloads.robertson_random(256, seed=34, t1=100.0)
+    sv = [0.0, 1.0, 10.0, 100.0]
+    kw = dict(abstol=1e-6, reltol=1e-6, dt0=1e-4, saveat=sv)
+    a, _, _ = r.solve(dev(P), dev(U), dev(T), alg="ros23", dense=True, **kw)
+    b, _, _ = r.solve(dev(P), dev(U), dev(T), alg="ros23", **kw)
+    np.testing.assert_array_equal(host(a), host(b))
+    r.close()
