@@ -52,13 +52,24 @@ SM_MAX_MHZ = 2070.0
 #     products, two powers as lg2-mul-ex2, sum, +1, divide), drift 8, noise 17 (5 square
 #     roots, 4 x (mul, fma, mul)), update 8 -> 224; in FP64 the FP64 pipe carries only the
 #     floating-point part -> 104 (the Philox integer work runs on the integer lanes).
+# Rosenbrock23 attempt on a D-state model: W = I - h d J (D^2), LU (D^3 / 3 + pivoting),
+#   three solves (3 D^2), the stage combinations, error and norm (~18 D), the Jacobian and
+#   two f evaluations (model terms): Robertson 140; Orego 140; HIRES (D = 8: 171 + 192 + 64 +
+#   144 + 70) 640; POLLU (D = 20: 2667 + 1200 + 400 + 360 + 300) 4930.
+# Bouncing ball (D = 2, f costs nothing): a Tsit5 attempt = stage combinations 54, error 14,
+#   norm 13, controller 3 -> 84; each accepted step adds the event scan: the dense
+#   polynomial 4 x 7 x 2 FMA + 8 scalings = 64 and 9 checkpoints x 8 = 72 -> 136.
 OPS_PER_ATTEMPT = {"tsit5": 160, "tsit5_fixed": 117, "rk4": 48, "ros23": 140, "em": 25,
-                   "adjoint": 423, "crn_em": 224, "crn_em_f64": 104}
+                   "adjoint": 423, "crn_em": 224, "crn_em_f64": 104, "ball": 84,
+                   "ball_event_scan": 136, "ros23_orego": 140, "ros23_hires": 640,
+                   "ros23_pollu": 4930}
 
 
 def ops_key(w):
     if w["rhs"] == "crn":
         return "crn_em_f64" if w["dtype"] == "f64" else "crn_em"
+    if w["rhs"] in ("orego", "hires", "pollu"):
+        return "ros23_" + w["rhs"]
     return w["alg"]
 
 WORKLOADS = {
@@ -72,7 +83,17 @@ WORKLOADS = {
     "robertson_ros23_f64": dict(kind="solve", rhs="robertson", alg="ros23", dtype="f64",
                                 N=1 << 18, t1=1e5, tol=1e-6, dt0=1e-4, steps=20),
     "lorenz_dense_f32": dict(kind="solve", rhs="lorenz", alg="tsit5", dtype="f32", N=1 << 20,
-                             t1=10.0, tol=1e-5, saves=256, dense=True, steps=200),
+                             t1=10.0, tol=1e-5, saves=256, dense=True, layout="rowmajor",
+                             steps=200),
+    # the paper's stiff test models at its 8,192 trajectories (tolerance not printed: 1e-6)
+    "orego_ros23_f64": dict(kind="solve", rhs="orego", alg="ros23", dtype="f64", N=8192,
+                            t1=30.0, tol=1e-6, steps=5),
+    "hires_ros23_f64": dict(kind="solve", rhs="hires", alg="ros23", dtype="f64", N=8192,
+                            t1=321.8122, tol=1e-6, steps=5),
+    "pollu_ros23_f64": dict(kind="solve", rhs="pollu", alg="ros23", dtype="f64", N=8192,
+                            t1=60.0, tol=1e-6, steps=5),
+    "ball_events_f32": dict(kind="solve", rhs="ball", alg="tsit5", dtype="f32", N=1 << 20,
+                            t1=15.0, tol=1e-6, dtmax=1.0, steps=100),
     "crn_em_f32": dict(kind="solve", rhs="crn", alg="em", dtype="f32", N=10 ** 6, t1=1000.0,
                        dt=0.1, seed=2024, steps=5),
     "crn_em_f64": dict(kind="solve", rhs="crn", alg="em", dtype="f64", N=10 ** 6, t1=1000.0,
@@ -126,6 +147,10 @@ def inputs_for(w, rank=0):
             P, U, T = workloads.lorenz_random(N, seed=2 + 1000 * rank, t1=w["t1"])
     elif w["rhs"] == "robertson":
         P, U, T = workloads.robertson_random(N, seed=3 + 1000 * rank, t1=w["t1"])
+    elif w["rhs"] in ("orego", "hires", "pollu"):
+        P, U, T = workloads.stiff(w["rhs"], N, seed=11 + 1000 * rank, t1=w["t1"])
+    elif w["rhs"] == "ball":
+        P, U, T = workloads.ball(N, seed=10 + 1000 * rank, t1=w["t1"])
     elif w["rhs"] == "crn":  # the Cartesian product of k draws per parameter, k^6 = N
         k = int(round(N ** (1.0 / 6.0)))
         if k ** 6 == N:
@@ -145,6 +170,8 @@ def solve_kwargs(w):
         kw["dt"] = w["dt"]
     if "dt0" in w:
         kw["dt0"] = w["dt0"]
+    if "dtmax" in w:
+        kw["dtmax"] = w["dtmax"]
     if "seed" in w:
         kw["seed"] = w["seed"]
     if w.get("saves"):  # equally spaced save times over [0, t1]
@@ -319,11 +346,18 @@ class SolveRunner:
         self.dt_t = torch.float32 if w["dtype"] == "f32" else torch.float64
         self.P, self.U, self.T = inputs_for(w, rank)
         N = w["N"]
-        t = lambda a: torch.tensor(a.T.copy(), dtype=self.dt_t, device=dev)
+        self.layout = w.get("layout", "soa")
+        if self.layout == "soa":
+            t = lambda a: torch.tensor(a.T.copy(), dtype=self.dt_t, device=dev)
+        else:
+            t = lambda a: torch.tensor(a, dtype=self.dt_t, device=dev)
         self.Pd, self.Ud, self.Td = t(self.P), t(self.U), t(self.T)
         D = self.U.shape[1]
         S = w.get("saves", 0)
-        self.out = torch.empty((S, D, N) if S else (D, N), dtype=self.dt_t, device=dev)
+        if self.layout == "soa":
+            self.out = torch.empty((S, D, N) if S else (D, N), dtype=self.dt_t, device=dev)
+        else:
+            self.out = torch.empty((N, S, D) if S else (N, D), dtype=self.dt_t, device=dev)
         self.status = torch.empty(N, dtype=torch.int8, device=dev)
         self.stats = torch.empty((3, N), dtype=torch.int32, device=dev)
         self.solver = ens.EnsembleSolver(w["rhs"])
@@ -333,7 +367,8 @@ class SolveRunner:
             # the launch-shape autotuner on these inputs (outside the timed region); later
             # solves with default shapes use its choice
             b, t_, f, ms = self.solver.autotune(self.Pd, self.Ud, self.Td, alg=w["alg"],
-                                                layout="soa", out=self.out, status=self.status,
+                                                layout=self.layout, out=self.out,
+                                                status=self.status,
                                                 stats=self.stats, schedule=args.schedule,
                                                 order=args.order, refill_min=args.refill,
                                                 **self.kw)
@@ -346,7 +381,7 @@ class SolveRunner:
 
     def step(self):
         a = self.args
-        self.solver.solve(self.Pd, self.Ud, self.Td, alg=self.w["alg"], layout="soa",
+        self.solver.solve(self.Pd, self.Ud, self.Td, alg=self.w["alg"], layout=self.layout,
                           out=self.out, status=self.status, stats=self.stats,
                           schedule=a.schedule, block=a.block, tpt=a.tpt, refill_min=a.refill,
                           order=a.order, blocks_per_sm=a.bps, want_stats=True, **self.kw)
@@ -355,6 +390,13 @@ class SolveRunner:
         st = self.stats.cpu().numpy().astype(np.int64)
         attempts = int(st[0].sum() + st[1].sum())
         ok = int((self.status.cpu().numpy() == 0).sum())
+        if self.w["rhs"] == "ball":  # every attempt, plus the event scan of each accepted step
+            ops = attempts * OPS_PER_ATTEMPT["ball"] + int(st[0].sum()) * OPS_PER_ATTEMPT[
+                "ball_event_scan"]
+            return ops, {"attempts_per_launch": attempts, "accepted_per_launch": int(st[0].sum()),
+                         "ops_per_attempt": OPS_PER_ATTEMPT["ball"],
+                         "ops_per_accepted_event_scan": OPS_PER_ATTEMPT["ball_event_scan"],
+                         "trajectories_ok": ok, "autotuned_shape": self.tuned}
         return attempts * OPS_PER_ATTEMPT[ops_key(self.w)], {
             "attempts_per_launch": attempts, "ops_per_attempt": OPS_PER_ATTEMPT[ops_key(self.w)],
             "trajectories_ok": ok, "autotuned_shape": self.tuned}
@@ -372,12 +414,15 @@ class SolveRunner:
         N = w["N"]
         npdt = np.float32 if w["dtype"] == "f32" else np.float64
         pin = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=npdt)).pin_memory()
-        Pp, Up, Tp = pin(self.P.T), pin(self.U.T), pin(self.T.T)
+        soa = self.layout == "soa"
+        Pp, Up, Tp = ((pin(self.P.T), pin(self.U.T), pin(self.T.T)) if soa
+                      else (pin(self.P), pin(self.U), pin(self.T)))
         D = self.U.shape[1]
         S = max(1, w.get("saves", 0))
-        outp = torch.empty((S, D, N), dtype=Pp.dtype).pin_memory()
+        outp = torch.empty((S, D, N) if soa else (N, S, D), dtype=Pp.dtype).pin_memory()
         stp = torch.empty(N, dtype=torch.int8).pin_memory()
-        o, keep = ens.make_opts(w["alg"], _lib.F32 if w["dtype"] == "f32" else _lib.F64, "soa",
+        o, keep = ens.make_opts(w["alg"], _lib.F32 if w["dtype"] == "f32" else _lib.F64,
+                                self.layout,
                                 schedule=a.schedule, block=a.block, tpt=a.tpt,
                                 refill_min=a.refill, order=a.order, blocks_per_sm=a.bps,
                                 **self.kw)
@@ -780,6 +825,8 @@ def main():
     ap.add_argument("--n-train", type=int, default=0, help="surrogate: training solves")
     ap.add_argument("--epochs", type=int, default=0, help="surrogate: training epochs")
     ap.add_argument("--n", type=int, default=0, help="override N (small profiling cases)")
+    ap.add_argument("--layout", default="", choices=["", "soa", "rowmajor"],
+                    help="override the workload's array layout")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--probe", action="store_true", help="also measure FP32/FP64 FMA rates")
@@ -787,6 +834,8 @@ def main():
     w = dict(WORKLOADS[args.workload])
     if args.n:
         w["N"] = args.n
+    if args.layout:
+        w["layout"] = args.layout
     if args.n_train:
         w["n_train"] = args.n_train
     if args.epochs:
@@ -875,8 +924,10 @@ def main():
     e2e = None if args.no_e2e else runner.e2e(stream)
     cfg = {"workload": args.workload, "model": w["rhs"], "alg": w["alg"], "N": N,
            "tspan": [0.0, w["t1"]],
-           **{k: w[k] for k in ("tol", "dt", "dt0", "every", "seed", "saves", "dense") if k in w},
-           "layout": "soa", "l2": "flushed between steps (256 MB write outside events)",
+           **{k: w[k] for k in ("tol", "dt", "dt0", "dtmax", "every", "seed", "saves", "dense")
+              if k in w},
+           "layout": w.get("layout", "soa"),
+           "l2": "flushed between steps (256 MB write outside events)",
            "parallelism": "dp%d" % world}
     if w["kind"] == "solve":
         cfg.update({"block": args.block, "tpt": args.tpt, "schedule": args.schedule,

@@ -50,8 +50,28 @@ enum { ENS_OK = 0, ENS_EINVAL = 1, ENS_ENOTSUP = 2, ENS_ECUDA = 3, ENS_ENOMEM = 
  *               eta(sqrt(A_{i-1}/tau) dW_{2i+1} - sqrt(A_i/tau) dW_{2i+2}) with A_0 = [sigma].
  *             Square-root arguments and the two Hill bases are taken as max(., 0) (the form
  *             is undefined for negative amounts, which a discrete path can reach).
- *             Euler-Maruyama only. */
-enum { ENS_RHS_LORENZ = 1, ENS_RHS_ROBERTSON = 2, ENS_RHS_GBM = 3, ENS_RHS_CRN = 4 };
+ *             Euler-Maruyama only.
+ *   BALL      D=2 P=2  u=(x, v), p=(g, e)       f = (v, -g)   (Appendix, bouncing ball;
+ *             Sec. 6.5 events).  Event: x reaching 0 from above sets v <- -e v.  Each
+ *             accepted step's dense output (see ens_opts.dense) is checked at 10 evenly
+ *             spaced points; the first crossing is located by the Illinois method to 4 ulp
+ *             of the step, the state there takes the affect and the integration restarts
+ *             from it.  A crossing and recrossing between two checkpoints is not seen, so a
+ *             step much longer than the shortest flight needs ens_opts.dtmax.
+ *             TSIT5_ADAPTIVE only.
+ *   OREGO     D=3  P=3   p=(k1, k2, k3)  Oregonator: f = (k1 (y2 + y1 (1 - k2 y1 - y2)),
+ *             (y3 - (1 + y1) y2) / k1, k3 (y1 - y3)) (Appendix; the first equation's leading
+ *             sign read as +, the Field-Noyes model: with the printed minus the printed initial
+ *             state runs to -infinity).
+ *   HIRES     D=8  P=12  p = its 12 distinct rate constants in order of appearance
+ *             (1.71, 0.43, 8.32, 0.0007, 8.75, 10.03, 0.035, 1.12, 1.745, 280, 0.69, 1.81);
+ *             a constant printed in several equations is one parameter (Appendix, HIRES).
+ *   POLLU     D=20 P=25  p=(k1..k25): the printed equations, which are exactly the sum over
+ *             25 mass-action reactions ("k7 u9", "2 k18 u16" read as k7 y9, 2 k18 y16)
+ *             (Appendix, POLLU).  HIRES and POLLU take ROS23 only: the 8x8 / 20x20 LU runs
+ *             as loops over thread-local memory, one trajectory per thread. */
+enum { ENS_RHS_LORENZ = 1, ENS_RHS_ROBERTSON = 2, ENS_RHS_GBM = 3, ENS_RHS_CRN = 4,
+       ENS_RHS_BALL = 5, ENS_RHS_OREGO = 6, ENS_RHS_HIRES = 7, ENS_RHS_POLLU = 8 };
 
 /* algorithms:
  *   TSIT5_FIXED    Tsitouras 5(4) pair, fixed step dt (GPUTsit5, Sec. 5.2.1; RK step Sec. 3.1)
@@ -126,6 +146,7 @@ typedef struct {
                              continuous extension of order 4 of the Tsit5 pair (Sec. 5.1.1
                              solution storage), so the steps and the final state are those
                              of the solve without save times.  Other algorithms ignore it. */
+  double dtmax;           /* adaptive methods: largest step; <= 0: none.  Finite. */
 } ens_opts;
 
 /* Fill *o with defaults: TSIT5_ADAPTIVE, F32, SOA, abstol=reltol=1e-6, maxiters=1e6, auto. */

@@ -11,7 +11,11 @@ Identifiers (the same numbers as the public C-ABI, by documentation):
   rhs:  1 Lorenz (D=3, P=3: sigma, rho, beta), 2 Robertson (D=3, P=3: k1, k2, k3),
         3 geometric Brownian motion (D=1, P=2: mu, sigma; 1 Wiener process),
         4 sigma-factor CRN (D=4: [sigma], A1, A2, A3; P=6: S, D, tau, nu0, n, eta;
-          8 Wiener processes; Euler-Maruyama only)
+          8 Wiener processes; Euler-Maruyama only),
+        5 bouncing ball (D=2: x, v; P=2: g, e; the event x = 0 from above sets v <- -e v;
+          adaptive Tsit5 only),
+        6 Oregonator (D=3, P=3: k1, k2, k3), 7 HIRES (D=8, P=12: its distinct rate constants),
+        8 POLLU (D=20, P=25: k1..k25) -- the paper's stiff test models
   alg:  1 Tsit5 fixed, 2 Tsit5 adaptive, 3 RK4, 4 Rosenbrock23, 5 Euler-Maruyama
 """
 from __future__ import annotations
@@ -29,10 +33,12 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-RHS = {"lorenz": 1, "robertson": 2, "gbm": 3, "crn": 4}
+RHS = {"lorenz": 1, "robertson": 2, "gbm": 3, "crn": 4, "ball": 5, "orego": 6, "hires": 7,
+       "pollu": 8}
 ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5}
-DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2), 4: (4, 6)}
-NOISE = {1: 0, 2: 0, 3: 1, 4: 8}  # Wiener processes per model
+DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2), 4: (4, 6), 5: (2, 2), 6: (3, 3), 7: (8, 12),
+        8: (20, 25)}
+NOISE = {1: 0, 2: 0, 3: 1, 4: 8, 5: 0, 6: 0, 7: 0, 8: 0}  # Wiener processes per model
 STATUS = {"ok": 0, "maxiters": 1, "dt_min": 2, "nonfinite": 3}
 
 
@@ -60,7 +66,9 @@ def lib():
                 dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                 ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_longlong,
                 dp, ctypes.POINTER(ctypes.c_byte), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
-                ctypes.c_int]
+                ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
+            L.oracle_pollu_reaction_sum.restype = None
+            L.oracle_pollu_reaction_sum.argtypes = [dp, dp, dp]
             L.oracle_tsit5_dense.restype = None
             L.oracle_tsit5_dense.argtypes = [dp]
             L.oracle_step.restype = ctypes.c_int
@@ -106,13 +114,15 @@ def default_threads() -> int:
 
 def solve(rhs, alg, params, u0, tspan, *, dt=0.0, abstol=1e-6, reltol=1e-3, dt0=0.0,
           maxiters=1_000_000, saveat=None, seed=0, index_offset=0, precision="f64",
-          nthreads=None, dense=False):
+          nthreads=None, dense=False, dtmax=0.0, want_events=False):
     """Solve an ensemble.  params [N,P], u0 [N,D], tspan [N,2] (row-major, float64).
 
     precision "f32" runs the same algorithms in float arithmetic on the given (already
     float-representable) inputs; "f64_f32stream" is FP64 arithmetic driven by the FP32 normal
     stream (4 normals per Philox call).  dense=True (adaptive Tsit5 with saveat): the steps
-    run to tf without being cut at save times, which take the dense output (oracle/dense.py).  Returns (out [N,S,D] or [N,D], status [N], stats [N,3]).
+    run to tf without being cut at save times, which take the dense output (oracle/dense.py).
+    dtmax > 0 caps the adaptive step; want_events=True appends the events handled per
+    trajectory [N] to the result (bouncing ball).  Returns (out [N,S,D] or [N,D], status [N], stats [N,3]).
     """
     rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
     alg_id = ALG[alg] if isinstance(alg, str) else int(alg)
@@ -126,6 +136,7 @@ def solve(rhs, alg, params, u0, tspan, *, dt=0.0, abstol=1e-6, reltol=1e-3, dt0=
     out = np.empty((N, S, D), np.float64)
     status = np.empty(N, np.int8)
     stats = np.empty((N, 3), np.int64)
+    events = np.zeros(N, np.int64)
     nt = default_threads() if nthreads is None else int(nthreads)
     rc = lib().oracle_solve(
         rhs_id, alg_id, {"f64": 0, "f32": 1, "f64_f32stream": 2}[precision], 0, N, _dp(params), _dp(u0), _dp(tspan),
@@ -133,11 +144,14 @@ def solve(rhs, alg, params, u0, tspan, *, dt=0.0, abstol=1e-6, reltol=1e-3, dt0=
         _dp(sv) if sv is not None and sv.size else None, 0 if sv is None else int(sv.size),
         int(seed), int(index_offset), _dp(out),
         status.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)),
-        stats.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), nt, 1 if dense else 0)
+        stats.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), nt, 1 if dense else 0,
+        float(dtmax), events.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
     if rc != 0:
         raise ValueError("oracle_solve rejected its arguments")
     if sv is None or sv.size == 0:
         out = out[:, 0, :]
+    if want_events:
+        return out, status, stats, events
     return out, status, stats
 
 
@@ -202,6 +216,23 @@ def em_step(rhs, u, p, t, h, z):
                             _dp(unew)) != 0:
         raise ValueError("not an SDE model")
     return unew
+
+
+def jac_u(rhs, u, p, t=0.0):
+    """df/du [D, D] (every model with a Jacobian, the stiff test models included)."""
+    rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    D, _ = DIMS[rhs_id]
+    Ju = np.empty((D, D))
+    if lib().oracle_jac(rhs_id, _dp(_f64(u)), _dp(_f64(p)), float(t), _dp(Ju), None) != 0:
+        raise ValueError("model without a Jacobian")
+    return Ju
+
+
+def pollu_reaction_sum(y, k):
+    """POLLU's right-hand side formed as the sum over its 25 mass-action reactions."""
+    dy = np.empty(20)
+    lib().oracle_pollu_reaction_sum(_dp(_f64(y)), _dp(_f64(k)), _dp(dy))
+    return dy
 
 
 def jacobians(rhs, u, p, t=0.0):

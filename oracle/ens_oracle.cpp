@@ -44,10 +44,14 @@ namespace {
 
 // ----------------------------------------------------------------------------------------------
 // identifiers (values match the public C-ABI enumeration by documentation, not by a shared header)
-enum { RHS_LORENZ = 1, RHS_ROBERTSON = 2, RHS_GBM = 3, RHS_CRN = 4 };
+enum {
+  RHS_LORENZ = 1, RHS_ROBERTSON = 2, RHS_GBM = 3, RHS_CRN = 4, RHS_BALL = 5,
+  RHS_OREGO = 6, RHS_HIRES = 7, RHS_POLLU = 8
+};
 enum { ALG_TSIT5_FIXED = 1, ALG_TSIT5_ADAPTIVE = 2, ALG_RK4 = 3, ALG_ROS23 = 4, ALG_EM = 5 };
 enum { ST_OK = 0, ST_MAXITERS = 1, ST_DT_MIN = 2, ST_NONFINITE = 3 };
 enum { LAYOUT_ROWMAJOR = 0, LAYOUT_SOA = 1 };
+constexpr int MAXD = 20, MAXP = 25;  // largest model: POLLU (D = 20, P = 25)
 
 // ----------------------------------------------------------------------------------------------
 // Models (Appendix: Lorenz, Robertson, linear SDE, sigma-factor CRN).  f(u,p,t), the
@@ -63,6 +67,10 @@ Model model_of(int rhs) {
     case RHS_ROBERTSON: return {3, 3, 0};
     case RHS_GBM: return {1, 2, 1};
     case RHS_CRN: return {4, 6, 8};
+    case RHS_BALL: return {2, 2, 0};
+    case RHS_OREGO: return {3, 3, 0};
+    case RHS_HIRES: return {8, 12, 0};
+    case RHS_POLLU: return {20, 25, 0};
   }
   return {0, 0, 0};
 }
@@ -151,15 +159,186 @@ void diffusion(int id, const T* u, const T* p, T t, T* G) {
   else g_crn(u, p, t, G);
 }
 
+// Bouncing ball (Sec. 6.5 event handling; Appendix, bouncing-ball problem): u = (x, v),
+// p = (g, e); dx/dt = v, dv/dt = -g.  Event: the condition x = 0 reached from above
+// triggers the affect v <- -e v (e the coefficient of restitution).
+template <class T>
+void f_ball(const T* u, const T* p, T /*t*/, T* du) {
+  du[0] = u[1];
+  du[1] = -p[0];
+}
+
+bool has_event(int id) { return id == RHS_BALL; }
+
+// Oregonator (Appendix, OREGO): p = (k1, k2, k3).  The first equation's leading sign is read
+// as + (the Field-Noyes model the paper cites): with the printed minus the concentrations
+// run to -infinity from the printed initial state.
+template <class T>
+void f_orego(const T* y, const T* k, T /*t*/, T* dy) {
+  dy[0] = k[0] * (y[1] + y[0] * (1 - k[1] * y[0] - y[1]));
+  dy[1] = (y[2] - (1 + y[0]) * y[1]) / k[0];
+  dy[2] = k[2] * (y[0] - y[2]);
+}
+
+// HIRES (Appendix): the distinct rate constants as p = (c1..c12) =
+// (1.71, 0.43, 8.32, 0.0007, 8.75, 10.03, 0.035, 1.12, 1.745, 280.0, 0.69, 1.81);
+// a constant printed in several equations is the same parameter in each.
+template <class T>
+void f_hires(const T* y, const T* c, T /*t*/, T* dy) {
+  dy[0] = -c[0] * y[0] + c[1] * y[1] + c[2] * y[2] + c[3];
+  dy[1] = c[0] * y[0] - c[4] * y[1];
+  dy[2] = -c[5] * y[2] + c[1] * y[3] + c[6] * y[4];
+  dy[3] = c[2] * y[1] + c[0] * y[2] - c[7] * y[3];
+  dy[4] = -c[8] * y[4] + c[1] * y[5] + c[1] * y[6];
+  dy[5] = -c[9] * y[5] * y[7] + c[10] * y[3] + c[0] * y[4] - c[1] * y[5] + c[10] * y[6];
+  dy[6] = c[9] * y[5] * y[7] - c[11] * y[6];
+  dy[7] = -c[9] * y[5] * y[7] + c[11] * y[6];
+}
+
+// POLLU (Appendix): p = (k1..k25), the printed equations term by term (the printed "k7 u9"
+// and "2 k18 u16" read as k7 y9 and 2 k18 y16).  0-based: y[i] is y_{i+1}, k[j] is k_{j+1}.
+template <class T>
+void f_pollu(const T* y, const T* k, T /*t*/, T* dy) {
+  dy[0] = -k[0] * y[0] - k[9] * y[10] * y[0] - k[13] * y[0] * y[5] - k[22] * y[0] * y[3] -
+          k[23] * y[18] * y[0] + k[1] * y[1] * y[3] + k[2] * y[4] * y[1] + k[8] * y[10] * y[1] +
+          k[10] * y[12] + k[11] * y[9] * y[1] + k[21] * y[18] + k[24] * y[19];
+  dy[1] = -k[1] * y[1] * y[3] - k[2] * y[4] * y[1] - k[8] * y[10] * y[1] -
+          k[11] * y[9] * y[1] + k[0] * y[0] + k[20] * y[18];
+  dy[2] = -k[14] * y[2] + k[0] * y[0] + k[16] * y[3] + k[18] * y[15] + k[21] * y[18];
+  dy[3] = -k[1] * y[1] * y[3] - k[15] * y[3] - k[16] * y[3] - k[22] * y[0] * y[3] +
+          k[14] * y[2];
+  dy[4] = -k[2] * y[4] * y[1] + 2 * k[3] * y[6] + k[5] * y[6] * y[5] + k[6] * y[8] +
+          k[12] * y[13] + k[19] * y[16] * y[5];
+  dy[5] = -k[5] * y[6] * y[5] - k[7] * y[8] * y[5] - k[13] * y[0] * y[5] -
+          k[19] * y[16] * y[5] + k[2] * y[4] * y[1] + 2 * k[17] * y[15];
+  dy[6] = -k[3] * y[6] - k[4] * y[6] - k[5] * y[6] * y[5] + k[12] * y[13];
+  dy[7] = k[3] * y[6] + k[4] * y[6] + k[5] * y[6] * y[5] + k[6] * y[8];
+  dy[8] = -k[6] * y[8] - k[7] * y[8] * y[5];
+  dy[9] = -k[11] * y[9] * y[1] + k[6] * y[8] + k[8] * y[10] * y[1];
+  dy[10] = -k[8] * y[10] * y[1] - k[9] * y[10] * y[0] + k[7] * y[8] * y[5] + k[10] * y[12];
+  dy[11] = k[8] * y[10] * y[1];
+  dy[12] = -k[10] * y[12] + k[9] * y[10] * y[0];
+  dy[13] = -k[12] * y[13] + k[11] * y[9] * y[1];
+  dy[14] = k[13] * y[0] * y[5];
+  dy[15] = -k[17] * y[15] - k[18] * y[15] + k[15] * y[3];
+  dy[16] = -k[19] * y[16] * y[5];
+  dy[17] = k[19] * y[16] * y[5];
+  dy[18] = -k[20] * y[18] - k[21] * y[18] - k[23] * y[18] * y[0] + k[22] * y[0] * y[3] +
+           k[24] * y[19];
+  dy[19] = -k[24] * y[19] + k[23] * y[18] * y[0];
+}
+
+// POLLU as 25 mass-action reactions: rate r_j = k_j times its reactants, and the change of
+// each species per unit of r_j.  The printed equations are exactly sum_j nu_j r_j (tested);
+// the Jacobian is sum_j nu_j (d r_j / d y)^T.
+struct PolluReaction {
+  int a, b;           // reactant indices (b = -1: first order)
+  int n;              // number of species changed
+  int sp[5];
+  double nu[5];
+};
+const PolluReaction POLLU_R[25] = {
+    {0, -1, 3, {0, 1, 2}, {-1, 1, 1}},           // k1:  y1 -> y2 + y3
+    {1, 3, 3, {0, 1, 3}, {1, -1, -1}},           // k2:  y2 + y4 -> y1
+    {4, 1, 4, {0, 1, 4, 5}, {1, -1, -1, 1}},     // k3:  y5 + y2 -> y1 + y6
+    {6, -1, 3, {4, 6, 7}, {2, -1, 1}},           // k4:  y7 -> 2 y5 + y8
+    {6, -1, 2, {6, 7}, {-1, 1}},                 // k5:  y7 -> y8
+    {6, 5, 4, {4, 5, 6, 7}, {1, -1, -1, 1}},     // k6:  y7 + y6 -> y5 + y8
+    {8, -1, 4, {4, 7, 8, 9}, {1, 1, -1, 1}},     // k7:  y9 -> y5 + y8 + y10
+    {8, 5, 3, {5, 8, 10}, {-1, -1, 1}},          // k8:  y9 + y6 -> y11
+    {10, 1, 5, {0, 1, 9, 10, 11}, {1, -1, 1, -1, 1}},  // k9: y11 + y2 -> y1 + y10 + y12
+    {10, 0, 3, {0, 10, 12}, {-1, -1, 1}},        // k10: y11 + y1 -> y13
+    {12, -1, 3, {0, 10, 12}, {1, 1, -1}},        // k11: y13 -> y1 + y11
+    {9, 1, 4, {0, 1, 9, 13}, {1, -1, -1, 1}},    // k12: y10 + y2 -> y1 + y14
+    {13, -1, 3, {4, 6, 13}, {1, 1, -1}},         // k13: y14 -> y5 + y7
+    {0, 5, 3, {0, 5, 14}, {-1, -1, 1}},          // k14: y1 + y6 -> y15
+    {2, -1, 2, {2, 3}, {-1, 1}},                 // k15: y3 -> y4
+    {3, -1, 2, {3, 15}, {-1, 1}},                // k16: y4 -> y16
+    {3, -1, 2, {2, 3}, {1, -1}},                 // k17: y4 -> y3
+    {15, -1, 2, {5, 15}, {2, -1}},               // k18: y16 -> 2 y6
+    {15, -1, 2, {2, 15}, {1, -1}},               // k19: y16 -> y3
+    {16, 5, 4, {4, 5, 16, 17}, {1, -1, -1, 1}},  // k20: y17 + y6 -> y5 + y18
+    {18, -1, 2, {1, 18}, {1, -1}},               // k21: y19 -> y2
+    {18, -1, 3, {0, 2, 18}, {1, 1, -1}},         // k22: y19 -> y1 + y3
+    {0, 3, 3, {0, 3, 18}, {-1, -1, 1}},          // k23: y1 + y4 -> y19
+    {18, 0, 3, {0, 18, 19}, {-1, -1, 1}},        // k24: y19 + y1 -> y20
+    {19, -1, 3, {0, 18, 19}, {1, 1, -1}},        // k25: y20 -> y1 + y19
+};
+
+template <class T>
+void jac_stiff(int id, const T* y, const T* k, T* J) {
+  const int D = id == RHS_OREGO ? 3 : id == RHS_HIRES ? 8 : 20;
+  for (int i = 0; i < D * D; ++i) J[i] = 0;
+  if (id == RHS_OREGO) {
+    J[0] = k[0] * (1 - 2 * k[1] * y[0] - y[1]);
+    J[1] = k[0] * (1 - y[0]);
+    J[3] = -y[1] / k[0];
+    J[4] = -(1 + y[0]) / k[0];
+    J[5] = 1 / k[0];
+    J[6] = k[2];
+    J[8] = -k[2];
+  } else if (id == RHS_HIRES) {
+    const T* c = k;
+    auto at = [&](int i, int j) -> T& { return J[i * 8 + j]; };
+    at(0, 0) = -c[0]; at(0, 1) = c[1]; at(0, 2) = c[2];
+    at(1, 0) = c[0]; at(1, 1) = -c[4];
+    at(2, 2) = -c[5]; at(2, 3) = c[1]; at(2, 4) = c[6];
+    at(3, 1) = c[2]; at(3, 2) = c[0]; at(3, 3) = -c[7];
+    at(4, 4) = -c[8]; at(4, 5) = c[1]; at(4, 6) = c[1];
+    at(5, 3) = c[10]; at(5, 4) = c[0]; at(5, 5) = -c[9] * y[7] - c[1]; at(5, 6) = c[10];
+    at(5, 7) = -c[9] * y[5];
+    at(6, 5) = c[9] * y[7]; at(6, 6) = -c[11]; at(6, 7) = c[9] * y[5];
+    at(7, 5) = -c[9] * y[7]; at(7, 6) = c[11]; at(7, 7) = -c[9] * y[5];
+  } else {  // POLLU: sum over the reactions of nu_j (d r_j / d y)^T
+    for (int j = 0; j < 25; ++j) {
+      const PolluReaction& r = POLLU_R[j];
+      const T dra = r.b < 0 ? k[j] : k[j] * y[r.b];  // d r_j / d y_a
+      const T drb = r.b < 0 ? T(0) : k[j] * y[r.a];  // d r_j / d y_b
+      for (int m = 0; m < r.n; ++m) {
+        J[r.sp[m] * 20 + r.a] += T(r.nu[m]) * dra;
+        if (r.b >= 0) J[r.sp[m] * 20 + r.b] += T(r.nu[m]) * drb;
+      }
+    }
+  }
+}
+
+// POLLU's right-hand side as the reaction sum (for the test that it equals the printed form)
+void pollu_reaction_sum(const double* y, const double* k, double* dy) {
+  for (int i = 0; i < 20; ++i) dy[i] = 0;
+  for (int j = 0; j < 25; ++j) {
+    const PolluReaction& r = POLLU_R[j];
+    const double rate = k[j] * y[r.a] * (r.b < 0 ? 1.0 : y[r.b]);
+    for (int m = 0; m < r.n; ++m) dy[r.sp[m]] += r.nu[m] * rate;
+  }
+}
+
+template <class T>
+T event_condition(int /*id*/, const T* u, const T* /*p*/, T /*t*/) {
+  return u[0];
+}
+
+template <class T>
+void event_affect(int /*id*/, T* u, const T* p, T /*t*/) {
+  u[1] = -p[1] * u[1];
+}
+
 template <class T>
 void rhs(int id, const T* u, const T* p, T t, T* du) {
   if (id == RHS_LORENZ) f_lorenz(u, p, t, du);
   else if (id == RHS_ROBERTSON) f_robertson(u, p, t, du);
   else if (id == RHS_GBM) f_gbm(u, p, t, du);
-  else f_crn(u, p, t, du);
+  else if (id == RHS_CRN) f_crn(u, p, t, du);
+  else if (id == RHS_BALL) f_ball(u, p, t, du);
+  else if (id == RHS_OREGO) f_orego(u, p, t, du);
+  else if (id == RHS_HIRES) f_hires(u, p, t, du);
+  else f_pollu(u, p, t, du);
 }
 
 // J[i*D+j] = d f_i / d u_j
+// df/du of the stiff models OREGO, HIRES, POLLU (defined with them below)
+template <class T>
+void jac_stiff(int id, const T* u, const T* p, T* J);
+
 template <class T>
 void jac_u(int id, const T* u, const T* p, T /*t*/, T* J) {
   if (id == RHS_LORENZ) {
@@ -172,8 +351,10 @@ void jac_u(int id, const T* u, const T* p, T /*t*/, T* J) {
     J[0] = -k1; J[1] = k3 * u[2]; J[2] = k3 * u[1];
     J[3] = k1; J[4] = -k3 * u[2] - 2 * k2 * u[1]; J[5] = -k3 * u[1];
     J[6] = 0; J[7] = 2 * k2 * u[1]; J[8] = 0;
-  } else {
+  } else if (id == RHS_GBM) {
     J[0] = p[0];
+  } else {
+    jac_stiff<T>(id, u, p, J);
   }
 }
 
@@ -278,9 +459,9 @@ T rms_scaled(const T* x, const T* sc, int D) {
 // k7 = f(unew, t+h).  Stage formula: U_i = u + h sum_j a_ij k_j, k_i = f(U_i, t + c_i h).
 template <class T>
 void tsit5_step(int id, int D, const T* u, const T* p, T t, T h, const T* k1, T* unew, T* err,
-                T* k7, T (*kout)[8] = nullptr) {
-  T k[7][8];
-  T U[8];
+                T* k7, T (*kout)[MAXD] = nullptr) {
+  T k[7][MAXD];
+  T U[MAXD];
   for (int j = 0; j < D; ++j) k[0][j] = k1[j];
   for (int i = 1; i < 7; ++i) {
     for (int j = 0; j < D; ++j) {
@@ -323,7 +504,7 @@ const double TS_DENSE[7][4] = {
     {0.0, 1.5511818308687129, -4.102363661737424, 2.551181830868712}};
 
 template <class T>
-void tsit5_dense(int D, const T* u, T h, const T (*k)[8], T theta, T* out) {
+void tsit5_dense(int D, const T* u, T h, const T (*k)[MAXD], T theta, T* out) {
   T bw[7];
   for (int i = 0; i < 7; ++i)
     bw[i] = theta * (T(TS_DENSE[i][0]) +
@@ -336,9 +517,75 @@ void tsit5_dense(int D, const T* u, T h, const T (*k)[8], T theta, T* out) {
   }
 }
 
+// ---- events (Sec. 6.5): a condition g(u, p, t) crossing zero from above inside an accepted
+// Tsit5 step triggers the model's affect.  The step's dense output is written as a
+// polynomial in theta, u(theta) = u_n + sum_{q=1..4} theta^q c_q with c_q = h sum_i r_iq k_i.
+// The condition is checked at theta = j / EVENT_POINTS (j = 0..EVENT_POINTS, with u_n and
+// u_{n+1} themselves at the ends); the first interval with g > 0 at its left end and g <= 0
+// at its right end is narrowed by the Illinois method (regula falsi that halves the value
+// kept at an end which survives two iterations in a row; Dowell & Jarratt 1971) until it is
+// at most 4 eps wide or after 100 iterations.  The event sits at the interval's right end.
+const int EVENT_POINTS = 10;
+
+template <class T>
+void dense_coeffs(int D, T h, const T (*k)[MAXD], T (*c)[MAXD]) {
+  for (int q = 0; q < 4; ++q)
+    for (int j = 0; j < D; ++j) {
+      T s = 0;
+      for (int i = 0; i < 7; ++i) s += T(TS_DENSE[i][q]) * k[i][j];
+      c[q][j] = h * s;
+    }
+}
+
+template <class T>
+void dense_poly(int D, const T* u, const T (*c)[MAXD], T th, T* out) {
+  for (int j = 0; j < D; ++j)
+    out[j] = u[j] + th * (c[0][j] + th * (c[1][j] + th * (c[2][j] + th * c[3][j])));
+}
+
+// theta in (0, 1] of the first crossing from above in the step, or -1 for none
+template <class T>
+T find_event(int id, int D, const T* u, const T* unew, const T* p, T tn, T h,
+             const T (*c)[MAXD]) {
+  T w[MAXD];
+  auto g_at = [&](T th) {
+    dense_poly<T>(D, u, c, th, w);
+    return event_condition<T>(id, w, p, tn + th * h);
+  };
+  T a = 0, ga = event_condition<T>(id, u, p, tn);
+  for (int j = 1; j <= EVENT_POINTS; ++j) {
+    const T b0 = (j == EVENT_POINTS) ? T(1) : T(j) / T(EVENT_POINTS);
+    const T gb0 = (j == EVENT_POINTS) ? event_condition<T>(id, unew, p, tn + h) : g_at(b0);
+    if (ga > 0 && gb0 <= 0) {
+      T b = b0, gb = gb0;
+      int side = 0;
+      for (int it = 0; it < 100 && b - a > T(4) * std::numeric_limits<T>::epsilon(); ++it) {
+        T x = (a * gb - b * ga) / (gb - ga);
+        if (!(x > a && x < b)) x = (a + b) / 2;
+        const T gx = g_at(x);
+        if (gx > 0) {
+          a = x;
+          ga = gx;
+          if (side == 1) gb /= 2;
+          side = 1;
+        } else {
+          b = x;
+          gb = gx;
+          if (side == -1) ga /= 2;
+          side = -1;
+        }
+      }
+      return b;
+    }
+    a = b0;
+    ga = gb0;
+  }
+  return T(-1);
+}
+
 template <class T>
 void rk4_step(int id, int D, const T* u, const T* p, T t, T h, T* unew) {
-  T k1[8], k2[8], k3[8], k4[8], U[8];
+  T k1[MAXD], k2[MAXD], k3[MAXD], k4[MAXD], U[MAXD];
   rhs<T>(id, u, p, t, k1);
   for (int j = 0; j < D; ++j) U[j] = u[j] + (h / 2) * k1[j];
   rhs<T>(id, U, p, t + h / 2, k2);
@@ -368,7 +615,7 @@ void lu_factor(int D, T* W, int* piv) {
 
 template <class T>
 void lu_solve(int D, const T* LU, const int* piv, const T* b, T* x) {
-  T y[8];
+  T y[MAXD];
   for (int j = 0; j < D; ++j) y[j] = b[j];
   for (int c = 0; c < D; ++c) std::swap(y[c], y[piv[c]]);
   for (int r = 0; r < D; ++r)
@@ -388,13 +635,13 @@ void ros23_step(int id, int D, const T* u, const T* p, T t, T h, const T* f0, T*
                 T* f2) {
   const T d = T(1.0 / (2.0 + std::sqrt(2.0)));
   const T e32 = T(6.0 + std::sqrt(2.0));
-  T J[64], W[64];
-  int piv[8];
+  T J[MAXD * MAXD], W[MAXD * MAXD];
+  int piv[MAXD];
   jac_u<T>(id, u, p, t, J);
   for (int r = 0; r < D; ++r)
     for (int c = 0; c < D; ++c) W[r * D + c] = (r == c ? T(1) : T(0)) - h * d * J[r * D + c];
   lu_factor<T>(D, W, piv);
-  T k1[8], k2[8], k3[8], f1[8], U[8], rhs_v[8] = {};
+  T k1[MAXD], k2[MAXD], k3[MAXD], f1[MAXD], U[MAXD], rhs_v[MAXD] = {};
   lu_solve<T>(D, W, piv, f0, k1);  // k1 = W^{-1} (f0 + h d T), T = 0
   for (int j = 0; j < D; ++j) U[j] = u[j] + (h / 2) * k1[j];
   rhs<T>(id, U, p, t + h / 2, f1);
@@ -469,6 +716,7 @@ struct Opts {
   long long index_offset;
   bool stream_fp64;  // normals from the FP64 stream (2 per Philox call) or the FP32 one (4)
   bool dense;        // adaptive Tsit5: save times by the dense output, steps not cut at them
+  double dtmax;      // adaptive methods: largest step (<= 0: none)
 };
 
 // Hairer-Norsett-Wanner I, II.4: starting step size for an order-p method.
@@ -476,7 +724,7 @@ template <class T>
 T initial_step(const Opts& o, const T* u0, const T* p, T t0, const T* f0, int order,
                long long* fevals) {
   const int D = o.D;
-  T sc[8], tmp[8], u1[8], f1[8];
+  T sc[MAXD], tmp[MAXD], u1[MAXD], f1[MAXD];
   for (int j = 0; j < D; ++j) sc[j] = T(o.abstol) + T(o.reltol) * std::fabs(u0[j]);
   T d0 = rms_scaled(u0, sc, D);
   T d1 = rms_scaled(f0, sc, D);
@@ -495,12 +743,12 @@ T initial_step(const Opts& o, const T* u0, const T* p, T t0, const T* f0, int or
 template <class T>
 struct Traj {
   const Opts* o;
-  T u[8], p[8];
+  T u[MAXD], p[MAXP];
   T t0, tf;
   T* out;  // [S or 1][D] row-major scratch owned by the caller
   int S;
   signed char status;
-  long long accepted, rejected, fevals;
+  long long accepted, rejected, fevals, events;
 };
 
 template <class T>
@@ -542,7 +790,7 @@ void solve_fixed(Traj<T>& tr, uint64_t traj_index) {
     }
   };
   if (save_mode) record_saves(0);
-  T k1[8];
+  T k1[MAXD];
   if (o.alg == ALG_TSIT5_FIXED) {
     rhs<T>(o.rhs, tr.u, tr.p, tr.t0, k1);
     tr.fevals += 1;
@@ -550,9 +798,9 @@ void solve_fixed(Traj<T>& tr, uint64_t traj_index) {
   for (long long k = 0; k < nrun; ++k) {
     const T h = (k == n - 1) ? h_last : h_reg;
     const T tk = T(t0) + T(k) * T(dt);
-    T unew[8];
+    T unew[MAXD];
     if (o.alg == ALG_TSIT5_FIXED) {
-      T err[8], k7[8];
+      T err[MAXD], k7[MAXD];
       tsit5_step<T>(o.rhs, D, tr.u, tr.p, tk, h, k1, unew, err, k7);
       for (int j = 0; j < D; ++j) k1[j] = k7[j];
       tr.fevals += 6;
@@ -562,7 +810,7 @@ void solve_fixed(Traj<T>& tr, uint64_t traj_index) {
     } else {  // Euler-Maruyama (Sec. 3.3): X_{k+1} = X_k + a(X_k) h + sum_m b_m(X_k) dW_m,
       // dW_m = sqrt(h) Z_{k,m}; Z_{k,m} is normal number k*Mw + m of the trajectory's stream
       const int Mw = o.Mw;
-      T a[8], G[64], z[8];
+      T a[MAXD], G[MAXD * 8], z[MAXD];
       rhs<T>(o.rhs, tr.u, tr.p, tk, a);
       diffusion<T>(o.rhs, tr.u, tr.p, tk, G);
       tr.fevals += 1;
@@ -605,7 +853,7 @@ void solve_adaptive(Traj<T>& tr) {
   // skip save times before t0
   while (si < S && T(o.saveat[si]) < tr.t0) ++si;
 
-  T fcur[8];  // k1 (Tsit5) or f0 (R23): f at the current state
+  T fcur[MAXD];  // k1 (Tsit5) or f0 (R23): f at the current state
   rhs<T>(o.rhs, tr.u, tr.p, tr.t0, fcur);
   tr.fevals += 1;
   T h;
@@ -614,6 +862,8 @@ void solve_adaptive(Traj<T>& tr) {
   T qold = T(QOLD_INIT);
   long long attempts = 0;
   const bool dense = o.dense && !is_r23 && save_mode;
+  const bool ev = has_event(o.rhs) && !is_r23;
+  long long events = 0;
   if (dense)  // save times equal to t0 take u0; the steps then run to tf uncut
     while (si < S && T(o.saveat[si]) == tr.t0 && tr.t0 <= tr.tf) {
       for (int j = 0; j < D; ++j) tr.out[si * D + j] = tr.u[j];
@@ -640,24 +890,26 @@ void solve_adaptive(Traj<T>& tr) {
       break;
     }
     if (attempts >= o.maxiters) { tr.status = ST_MAXITERS; break; }
-    const bool last = (h >= rem);
-    const T hs = last ? rem : h;
+    const T hcap = (o.dtmax > 0) ? std::min(h, T(o.dtmax)) : h;
+    const bool last = (hcap >= rem);
+    const T hs = last ? rem : hcap;
     const T tnow = clk.value();
     if (hs < T(Prec<T>::dtmin_factor) * std::max(T(1), std::fabs(tnow))) {
       tr.status = ST_DT_MIN;
       break;
     }
-    T unew[8], err[8], fnew[8], kst[7][8];
+    T unew[MAXD], err[MAXD], fnew[MAXD], kst[7][MAXD];
     if (is_r23) {
       ros23_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew);
       tr.fevals += 2;
     } else {
-      tsit5_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew, dense ? kst : nullptr);
+      tsit5_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew,
+                    (dense || ev) ? kst : nullptr);
       tr.fevals += 6;
     }
     ++attempts;
     // q = || E / (atol + rtol max(|u(t)|, |u(t+h)|)) ||  (RMS norm)
-    T sc[8];
+    T sc[MAXD];
     for (int j = 0; j < D; ++j)
       sc[j] = atol + rtol * std::max(std::fabs(tr.u[j]), std::fabs(unew[j]));
     const T q = rms_scaled(err, sc, D);
@@ -668,21 +920,37 @@ void solve_adaptive(Traj<T>& tr) {
       T fac = T(ETA) * std::pow(qg, -beta1) * std::pow(qold, beta2);
       fac = std::min(T(FAC_MAX), std::max(T(FAC_MIN), fac));
       qold = std::max(q, T(QOLD_INIT));
-      if (dense) {  // save times in (t_n, t_n + hs]: theta = (s - t_n) / hs on the clock
+      T th_ev = -1, cq[4][MAXD];
+      if (ev) {
+        dense_coeffs<T>(D, hs, kst, cq);
+        th_ev = find_event<T>(o.rhs, D, tr.u, unew, tr.p, tnow, hs, cq);
+      }
+      const bool cut = th_ev > 0 && th_ev < 1;  // the step ends at the event
+      if (dense) {  // save times in (t_n, t_n + hs] (up to the event): theta = (s - t_n) / hs
         while (si < S) {
           const T sv = T(o.saveat[si]);
           if (sv > tr.tf) break;
           const T rs = clk.remaining(sv);
-          if (!(last && sv == stop) && rs > hs) break;
-          if (last && sv == stop)
+          const bool at_end = !cut && last && sv == stop;
+          if (!at_end && rs > (cut ? th_ev * hs : hs)) break;
+          if (at_end)
             for (int j = 0; j < D; ++j) tr.out[si * D + j] = unew[j];
           else
             tsit5_dense<T>(D, tr.u, hs, kst, rs / hs, tr.out + si * D);
           ++si;
         }
       }
+      if (th_ev > 0) {  // state at the event, then the affect; f is evaluated afresh
+        if (cut) dense_poly<T>(D, tr.u, cq, th_ev, unew);
+        event_affect<T>(o.rhs, unew, tr.p, tnow + th_ev * hs);
+        rhs<T>(o.rhs, unew, tr.p, tnow + th_ev * hs, fnew);
+        tr.fevals += 1;
+        ++events;
+      }
       for (int j = 0; j < D; ++j) { tr.u[j] = unew[j]; fcur[j] = fnew[j]; }
-      if (last) clk.set(stop);
+      tr.events = events;
+      if (cut) clk.add(th_ev * hs);
+      else if (last) clk.set(stop);
       else clk.add(hs);
       tr.accepted += 1;
       h = hs * fac;
@@ -708,7 +976,7 @@ inline long long idx_out(int layout, long long i, int s, int k, long long N, int
 template <class T>
 void solve_range(const Opts& o, int layout, long long N, long long i0, long long i1,
                  const double* params, const double* u0, const double* tspan, double* out,
-                 signed char* status, long long* stats) {
+                 signed char* status, long long* stats, long long* events) {
   const int D = o.D, P = o.P;
   const int S = o.n_save > 0 ? o.n_save : 1;
   std::vector<T> buf(size_t(S) * D);
@@ -722,7 +990,7 @@ void solve_range(const Opts& o, int layout, long long N, long long i0, long long
     tr.out = buf.data();
     tr.S = S;
     tr.status = ST_OK;
-    tr.accepted = tr.rejected = tr.fevals = 0;
+    tr.accepted = tr.rejected = tr.fevals = tr.events = 0;
     if (o.alg == ALG_TSIT5_ADAPTIVE || o.alg == ALG_ROS23) solve_adaptive<T>(tr);
     else solve_fixed<T>(tr, uint64_t(o.index_offset + i));
     for (int s = 0; s < S; ++s)
@@ -733,6 +1001,7 @@ void solve_range(const Opts& o, int layout, long long N, long long i0, long long
       stats[i * 3 + 1] = tr.rejected;
       stats[i * 3 + 2] = tr.fevals;
     }
+    if (events) events[i] = tr.events;
   }
 }
 
@@ -767,25 +1036,28 @@ extern "C" {
 // (params[P][N], u0[D][N], tspan[2][N], out[S][D][N]).  `precision` 0 = FP64, 1 = FP32 mode
 // (inputs rounded to float first by the caller; arithmetic in float, time compensated),
 // 2 = FP64 arithmetic driven by the FP32 normal stream (the reference for FP32 SDE paths).
-// stats[N][3] = accepted, rejected, f-evaluations.  Returns 0, or -1 on bad arguments.
+// stats[N][3] = accepted, rejected, f-evaluations; events[N] (or NULL) = events handled.
+// dense: adaptive Tsit5 saves by the dense output; dtmax > 0 caps adaptive steps.
+// Returns 0, or -1 on bad arguments.
 int oracle_solve(int rhs_id, int alg, int precision, int layout, long long N,
                  const double* params, const double* u0, const double* tspan, double dt,
                  double abstol, double reltol, double dt0, long long maxiters,
                  const double* saveat, int n_save, unsigned long long seed,
                  long long index_offset, double* out, signed char* status, long long* stats,
-                 int nthreads, int dense) {
+                 int nthreads, int dense, double dtmax, long long* events) {
   Model m = model_of(rhs_id);
   if (m.D == 0 || N < 0 || alg < 1 || alg > 5) return -1;
   if (alg == ALG_EM && m.Mw == 0) return -1;  // Euler-Maruyama needs an SDE model
   if (rhs_id == RHS_CRN && alg != ALG_EM) return -1;
+  if (has_event(rhs_id) && alg != ALG_TSIT5_ADAPTIVE) return -1;  // events need the interpolant
   if (precision < 0 || precision > 2) return -1;
   Opts o{rhs_id, alg, m.D, m.P, m.Mw, dt, abstol, reltol, dt0, maxiters, saveat, n_save, seed,
-         index_offset, precision == 0, dense != 0};
+         index_offset, precision == 0, dense != 0, dtmax};
   parallel_for(N, nthreads, [&](long long a, long long b) {
     if (precision != 1)
-      solve_range<double>(o, layout, N, a, b, params, u0, tspan, out, status, stats);
+      solve_range<double>(o, layout, N, a, b, params, u0, tspan, out, status, stats, events);
     else
-      solve_range<float>(o, layout, N, a, b, params, u0, tspan, out, status, stats);
+      solve_range<float>(o, layout, N, a, b, params, u0, tspan, out, status, stats, events);
   });
   return 0;
 }
@@ -796,8 +1068,8 @@ int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t,
                 double z, double* unew, double* err) {
   Model m = model_of(rhs_id);
   if (m.D == 0) return -1;
-  if (alg == ALG_ROS23 && rhs_id == RHS_CRN) return -1;  // no Jacobian for the CRN
-  double e[8] = {0}, fx[8], k1[8];
+  if (alg == ALG_ROS23 && (rhs_id == RHS_CRN || rhs_id == RHS_BALL)) return -1;  // no Jacobian
+  double e[MAXD] = {0}, fx[MAXD], k1[MAXD];
   if (alg == ALG_TSIT5_FIXED || alg == ALG_TSIT5_ADAPTIVE) {
     rhs<double>(rhs_id, u, p, t, k1);
     tsit5_step<double>(rhs_id, m.D, u, p, t, h, k1, unew, e, fx);
@@ -808,7 +1080,7 @@ int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t,
     ros23_step<double>(rhs_id, m.D, u, p, t, h, k1, unew, e, fx);
   } else if (alg == ALG_EM) {
     if (rhs_id != RHS_GBM) return -1;
-    double a[8], b[8];
+    double a[MAXD], b[MAXD];
     f_gbm<double>(u, p, t, a);
     g_gbm<double>(u, p, t, b);
     for (int j = 0; j < m.D; ++j) unew[j] = u[j] + a[j] * h + b[j] * std::sqrt(h) * z;
@@ -818,6 +1090,10 @@ int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t,
   if (err)
     for (int j = 0; j < m.D; ++j) err[j] = e[j];
   return 0;
+}
+
+void oracle_pollu_reaction_sum(const double* y, const double* k, double* dy) {
+  pollu_reaction_sum(y, k, dy);
 }
 
 void oracle_tsit5_dense(double* r) {
@@ -852,7 +1128,7 @@ int oracle_em_step(int rhs_id, const double* u, const double* p, double t, doubl
                    const double* z, double* unew) {
   const Model m = model_of(rhs_id);
   if (m.Mw == 0) return -1;
-  double a[8], G[64];
+  double a[MAXD], G[MAXD * 8];
   rhs<double>(rhs_id, u, p, t, a);
   diffusion<double>(rhs_id, u, p, t, G);
   const double sq = std::sqrt(h);
@@ -865,7 +1141,8 @@ int oracle_em_step(int rhs_id, const double* u, const double* p, double t, doubl
 }
 
 int oracle_jac(int rhs_id, const double* u, const double* p, double t, double* Ju, double* Jp) {
-  if (model_of(rhs_id).D == 0 || rhs_id == RHS_CRN) return -1;
+  if (model_of(rhs_id).D == 0 || rhs_id == RHS_CRN || rhs_id == RHS_BALL) return -1;
+  if (Jp && rhs_id >= RHS_OREGO) return -1;  // no df/dp for the stiff test models
   if (Ju) jac_u<double>(rhs_id, u, p, t, Ju);
   if (Jp) jac_p<double>(rhs_id, u, p, t, Jp);
   return 0;
@@ -873,9 +1150,9 @@ int oracle_jac(int rhs_id, const double* u, const double* p, double t, double* J
 
 // Solve W x = b by the oracle's LU (for the linear-algebra pin).
 int oracle_lu_solve(int D, const double* W, const double* b, double* x) {
-  if (D < 1 || D > 8) return -1;
-  double LU[64];
-  int piv[8];
+  if (D < 1 || D > MAXD) return -1;
+  double LU[MAXD * MAXD];
+  int piv[MAXD];
   std::memcpy(LU, W, sizeof(double) * D * D);
   lu_factor<double>(D, LU, piv);
   lu_solve<double>(D, LU, piv, b, x);
@@ -928,7 +1205,7 @@ int oracle_fixed_grad(int rhs_id, int alg_id, long long N, const double* params,
     return -1;
   }
   Model m = model_of(rhs_id);
-  if (m.D == 0 || rhs_id == RHS_CRN) return -1;  // tangents need df/du, df/dp
+  if (m.D == 0 || rhs_id == RHS_CRN || rhs_id >= RHS_BALL) return -1;  // needs df/du, df/dp
   const int D = m.D, P = m.P, M = m.P + m.D;
   parallel_for(N, nthreads, [&](long long a, long long bnd) {
     for (long long i = a; i < bnd; ++i) {

@@ -13,9 +13,10 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libens.so")
 
 ENS_OK, ENS_EINVAL, ENS_ENOTSUP, ENS_ECUDA, ENS_ENOMEM = 0, 1, 2, 3, 4
-RHS = {"lorenz": 1, "robertson": 2, "gbm": 3, "crn": 4}
-DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2), 4: (4, 6)}
-NOISE = {1: 0, 2: 0, 3: 1, 4: 8}  # Wiener processes per model
+RHS = {"lorenz": 1, "robertson": 2, "gbm": 3, "crn": 4, "ball": 5, "orego": 6, "hires": 7,
+       "pollu": 8}
+DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2), 4: (4, 6), 5: (2, 2), 6: (3, 3), 7: (8, 12), 8: (20, 25)}
+NOISE = {1: 0, 2: 0, 3: 1, 4: 8, 5: 0, 6: 0, 7: 0, 8: 0}  # Wiener processes per model
 ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5}
 F32, F64 = 0, 1
 LAYOUT = {"rowmajor": 0, "soa": 1}
@@ -34,7 +35,7 @@ class EnsOpts(ctypes.Structure):
         ("seed", ctypes.c_ulonglong), ("index_offset", ctypes.c_longlong),
         ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
         ("refill_min", ctypes.c_int), ("order", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-        ("dense", ctypes.c_int),
+        ("dense", ctypes.c_int), ("dtmax", ctypes.c_double),
     ]
 
 

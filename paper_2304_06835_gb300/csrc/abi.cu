@@ -27,15 +27,33 @@ cudaError_t dispatch_f32_crn(int, const SolveArgs*, const LaunchCfg&, cudaStream
                              cudaFuncAttributes*, int*, CostScratch*);
 cudaError_t dispatch_f64_crn(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
                              cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f32_ball(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                              cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f64_ball(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                              cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f32_orego(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                               cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f64_orego(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                               cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f32_hires(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                               cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f64_hires(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                               cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f32_pollu(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                               cudaFuncAttributes*, int*, CostScratch*);
+cudaError_t dispatch_f64_pollu(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
+                               cudaFuncAttributes*, int*, CostScratch*);
 
 typedef cudaError_t (*DispatchFn)(int, const SolveArgs*, const LaunchCfg&, cudaStream_t, bool*,
                                   cudaFuncAttributes*, int*, CostScratch*);
 
 static DispatchFn table(int rhs_id, int dtype) {
-  static const DispatchFn t[2][4] = {
-      {dispatch_f32_lorenz, dispatch_f32_robertson, dispatch_f32_gbm, dispatch_f32_crn},
-      {dispatch_f64_lorenz, dispatch_f64_robertson, dispatch_f64_gbm, dispatch_f64_crn}};
-  if (rhs_id < 1 || rhs_id > 4 || (dtype != ENS_F32 && dtype != ENS_F64)) return nullptr;
+  static const DispatchFn t[2][8] = {
+      {dispatch_f32_lorenz, dispatch_f32_robertson, dispatch_f32_gbm, dispatch_f32_crn,
+       dispatch_f32_ball, dispatch_f32_orego, dispatch_f32_hires, dispatch_f32_pollu},
+      {dispatch_f64_lorenz, dispatch_f64_robertson, dispatch_f64_gbm, dispatch_f64_crn,
+       dispatch_f64_ball, dispatch_f64_orego, dispatch_f64_hires, dispatch_f64_pollu}};
+  if (rhs_id < 1 || rhs_id > 8 || (dtype != ENS_F32 && dtype != ENS_F64)) return nullptr;
   return t[dtype][rhs_id - 1];
 }
 
@@ -242,6 +260,10 @@ bool model_dims(int rhs_id, int* D, int* P) {
     case ENS_RHS_ROBERTSON: *D = 3; *P = 3; return true;
     case ENS_RHS_GBM: *D = 1; *P = 2; return true;
     case ENS_RHS_CRN: *D = 4; *P = 6; return true;
+    case ENS_RHS_BALL: *D = 2; *P = 2; return true;
+    case ENS_RHS_OREGO: *D = 3; *P = 3; return true;
+    case ENS_RHS_HIRES: *D = 8; *P = 12; return true;
+    case ENS_RHS_POLLU: *D = 20; *P = 25; return true;
   }
   return false;
 }
@@ -260,6 +282,13 @@ int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
     return fail(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM, CRN)");
   if (rhs_id == ENS_RHS_CRN && o->alg != ENS_EM)
     return fail(ENS_EINVAL, "the CRN model takes Euler-Maruyama only");
+  if (rhs_id == ENS_RHS_BALL && o->alg != ENS_TSIT5_ADAPTIVE)
+    return fail(ENS_EINVAL, "the bouncing ball's events need adaptive Tsit5");
+  if ((rhs_id == ENS_RHS_HIRES || rhs_id == ENS_RHS_POLLU) && o->alg != ENS_ROS23)
+    return fail(ENS_EINVAL, "HIRES and POLLU take Rosenbrock23 only");
+  if (rhs_id == ENS_RHS_OREGO && o->alg == ENS_EM)
+    return fail(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM, CRN)");
+  if (!std::isfinite(o->dtmax)) return fail(ENS_EINVAL, "dtmax not finite");
   if (is_fixed(o->alg) && !(o->dt > 0) ) return fail(ENS_EINVAL, "fixed-step methods need dt > 0");
   if (is_fixed(o->alg) && !std::isfinite(o->dt)) return fail(ENS_EINVAL, "dt not finite");
   if (!is_fixed(o->alg)) {
@@ -324,6 +353,8 @@ void fill_args(SolveArgs* a, long long N, const void* params, const void* u0, co
   a->abstol_f = (float)o->abstol;
   a->reltol_f = (float)o->reltol;
   a->dt0_f = (float)o->dt0;
+  a->dtmax = o->dtmax > 0 ? o->dtmax : HUGE_VAL;
+  a->dtmax_f = o->dtmax > 0 ? (float)o->dtmax : HUGE_VALF;
   a->refill_min = o->refill_min > 0 ? (o->refill_min > 32 ? 32 : o->refill_min) : 4;
   a->dense = o->dense != 0 && o->n_save > 0;
   a->seed = o->seed;

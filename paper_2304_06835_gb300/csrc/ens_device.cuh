@@ -83,7 +83,8 @@ struct M<double> {
 template <class T>
 struct Lorenz {
   static constexpr int D = 3, P = 3, NW = 0;
-  static constexpr bool autonomous = true, has_noise = false, sde_only = false;
+  static constexpr bool autonomous = true, has_noise = false, sde_only = false, has_event = false;
+  static constexpr bool stiff_only = false;
   static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) {
     du[0] = p[0] * (u[1] - u[0]);                  // sigma (y2 - y1)
     du[1] = M<T>::fma(u[0], p[1] - u[2], -u[1]);   // y1 (rho - y3) - y2
@@ -109,7 +110,8 @@ struct Lorenz {
 template <class T>
 struct Robertson {
   static constexpr int D = 3, P = 3, NW = 0;
-  static constexpr bool autonomous = true, has_noise = false, sde_only = false;
+  static constexpr bool autonomous = true, has_noise = false, sde_only = false, has_event = false;
+  static constexpr bool stiff_only = false;
   static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) {
     const T r1 = p[0] * u[0];           // k1 y1
     const T r2 = p[1] * u[1] * u[1];    // k2 y2^2
@@ -140,7 +142,8 @@ struct Robertson {
 template <class T>
 struct GBM {
   static constexpr int D = 1, P = 2, NW = 1;
-  static constexpr bool autonomous = true, has_noise = true, sde_only = false;
+  static constexpr bool autonomous = true, has_noise = true, sde_only = false, has_event = false;
+  static constexpr bool stiff_only = false;
   static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) { du[0] = p[0] * u[0]; }
   // a = mu X, b = (sigma X) sqrt(h) Z
   static __device__ __forceinline__ void sde(const T* u, const T* p, T, T sq, const T* z, T* a,
@@ -174,7 +177,8 @@ struct GBM {
 template <class T>
 struct CRN {
   static constexpr int D = 4, P = 6, NW = 8;
-  static constexpr bool autonomous = true, has_noise = true, sde_only = true;
+  static constexpr bool autonomous = true, has_noise = true, sde_only = true, has_event = false;
+  static constexpr bool stiff_only = false;
   static __device__ __forceinline__ T hill(const T* u, const T* p) {
     const T x = M<T>::fast_pow(M<T>::max(p[0] * u[0], T(0)), p[4]);
     const T y = M<T>::fast_pow(M<T>::max(p[1] * u[3], T(0)), p[4]);
@@ -203,6 +207,140 @@ struct CRN {
     b[1] = er * M<T>::fma(r1, z[2], -(r2 * z[3]));
     b[2] = er * M<T>::fma(r2, z[4], -(r3 * z[5]));
     b[3] = er * M<T>::fma(r3, z[6], -(r4 * z[7]));
+  }
+};
+
+// Bouncing ball (Sec. 6.5 event handling; Appendix, bouncing-ball problem): u = (x, v),
+// p = (g, e); dx/dt = v, dv/dt = -g.  Event: the condition x = 0 reached from above
+// triggers the affect v <- -e v (e the coefficient of restitution).  Adaptive Tsit5 only:
+// the event is located on the step's dense output.
+template <class T>
+struct Ball {
+  static constexpr int D = 2, P = 2, NW = 0;
+  static constexpr bool autonomous = true, has_noise = false, sde_only = false, has_event = true;
+  static constexpr bool stiff_only = false;
+  static __device__ __forceinline__ void f(const T* u, const T* p, T, T* du) {
+    du[0] = u[1];
+    du[1] = -p[0];
+  }
+  static __device__ __forceinline__ T event_condition(const T* u, const T*, T) { return u[0]; }
+  static __device__ __forceinline__ void event_affect(T* u, const T* p, T) { u[1] = -p[1] * u[1]; }
+};
+
+// The paper's stiff test models (Appendix): Oregonator (D = 3), HIRES (D = 8), POLLU
+// (D = 20).  f and the Jacobian df/du (row-major); Rosenbrock23 and the explicit methods
+// integrate them.
+template <class T>
+struct Orego {  // p = (k1, k2, k3); the first equation's sign read as + (Field-Noyes)
+  static constexpr int D = 3, P = 3, NW = 0;
+  static constexpr bool autonomous = true, has_noise = false, sde_only = false, has_event = false;
+  static constexpr bool stiff_only = false;
+  static __device__ __forceinline__ void f(const T* y, const T* k, T, T* dy) {
+    dy[0] = k[0] * (y[1] + y[0] * (T(1) - k[1] * y[0] - y[1]));
+    dy[1] = (y[2] - (T(1) + y[0]) * y[1]) / k[0];
+    dy[2] = k[2] * (y[0] - y[2]);
+  }
+  static __device__ __forceinline__ void jac(const T* y, const T* k, T, T* J) {
+    J[0] = k[0] * (T(1) - T(2) * k[1] * y[0] - y[1]);
+    J[1] = k[0] * (T(1) - y[0]);
+    J[2] = T(0);
+    J[3] = -y[1] / k[0];
+    J[4] = -(T(1) + y[0]) / k[0];
+    J[5] = T(1) / k[0];
+    J[6] = k[2];
+    J[7] = T(0);
+    J[8] = -k[2];
+  }
+};
+
+template <class T>
+struct Hires {  // p = the 12 distinct rate constants c1..c12 in order of appearance
+  static constexpr int D = 8, P = 12, NW = 0;
+  static constexpr bool autonomous = true, has_noise = false, sde_only = false, has_event = false;
+  static constexpr bool stiff_only = true;  // Rosenbrock23 only, one trajectory per thread
+  static __device__ __forceinline__ void f(const T* y, const T* c, T, T* dy) {
+    const T r = c[9] * y[5] * y[7];
+    dy[0] = -c[0] * y[0] + c[1] * y[1] + c[2] * y[2] + c[3];
+    dy[1] = c[0] * y[0] - c[4] * y[1];
+    dy[2] = -c[5] * y[2] + c[1] * y[3] + c[6] * y[4];
+    dy[3] = c[2] * y[1] + c[0] * y[2] - c[7] * y[3];
+    dy[4] = -c[8] * y[4] + c[1] * y[5] + c[1] * y[6];
+    dy[5] = -r + c[10] * y[3] + c[0] * y[4] - c[1] * y[5] + c[10] * y[6];
+    dy[6] = r - c[11] * y[6];
+    dy[7] = -r + c[11] * y[6];
+  }
+  static __device__ __forceinline__ void jac(const T* y, const T* c, T, T* J) {
+#pragma unroll
+    for (int i = 0; i < 64; ++i) J[i] = T(0);
+    J[0 * 8 + 0] = -c[0]; J[0 * 8 + 1] = c[1]; J[0 * 8 + 2] = c[2];
+    J[1 * 8 + 0] = c[0]; J[1 * 8 + 1] = -c[4];
+    J[2 * 8 + 2] = -c[5]; J[2 * 8 + 3] = c[1]; J[2 * 8 + 4] = c[6];
+    J[3 * 8 + 1] = c[2]; J[3 * 8 + 2] = c[0]; J[3 * 8 + 3] = -c[7];
+    J[4 * 8 + 4] = -c[8]; J[4 * 8 + 5] = c[1]; J[4 * 8 + 6] = c[1];
+    J[5 * 8 + 3] = c[10]; J[5 * 8 + 4] = c[0]; J[5 * 8 + 5] = -c[9] * y[7] - c[1];
+    J[5 * 8 + 6] = c[10]; J[5 * 8 + 7] = -c[9] * y[5];
+    J[6 * 8 + 5] = c[9] * y[7]; J[6 * 8 + 6] = -c[11]; J[6 * 8 + 7] = c[9] * y[5];
+    J[7 * 8 + 5] = -c[9] * y[7]; J[7 * 8 + 6] = c[11]; J[7 * 8 + 7] = -c[9] * y[5];
+  }
+};
+
+// POLLU as its 25 mass-action reactions: rate r_j = k_j y_a (y_b), and the change of each
+// species per unit of r_j (the printed equations are exactly the sum over the reactions).
+struct PolluRx {
+  int a, b, n;  // reactants (b = -1: first order), number of species changed
+  int sp[5];
+  int nu[5];
+};
+__host__ __device__ constexpr PolluRx pollu_rx(int j) {
+  constexpr PolluRx R[25] = {
+      {0, -1, 3, {0, 1, 2}, {-1, 1, 1}},          {1, 3, 3, {0, 1, 3}, {1, -1, -1}},
+      {4, 1, 4, {0, 1, 4, 5}, {1, -1, -1, 1}},    {6, -1, 3, {4, 6, 7}, {2, -1, 1}},
+      {6, -1, 2, {6, 7}, {-1, 1}},                {6, 5, 4, {4, 5, 6, 7}, {1, -1, -1, 1}},
+      {8, -1, 4, {4, 7, 8, 9}, {1, 1, -1, 1}},    {8, 5, 3, {5, 8, 10}, {-1, -1, 1}},
+      {10, 1, 5, {0, 1, 9, 10, 11}, {1, -1, 1, -1, 1}},
+      {10, 0, 3, {0, 10, 12}, {-1, -1, 1}},       {12, -1, 3, {0, 10, 12}, {1, 1, -1}},
+      {9, 1, 4, {0, 1, 9, 13}, {1, -1, -1, 1}},   {13, -1, 3, {4, 6, 13}, {1, 1, -1}},
+      {0, 5, 3, {0, 5, 14}, {-1, -1, 1}},         {2, -1, 2, {2, 3}, {-1, 1}},
+      {3, -1, 2, {3, 15}, {-1, 1}},               {3, -1, 2, {2, 3}, {1, -1}},
+      {15, -1, 2, {5, 15}, {2, -1}},              {15, -1, 2, {2, 15}, {1, -1}},
+      {16, 5, 4, {4, 5, 16, 17}, {1, -1, -1, 1}}, {18, -1, 2, {1, 18}, {1, -1}},
+      {18, -1, 3, {0, 2, 18}, {1, 1, -1}},        {0, 3, 3, {0, 3, 18}, {-1, -1, 1}},
+      {18, 0, 3, {0, 18, 19}, {-1, -1, 1}},       {19, -1, 3, {0, 18, 19}, {1, 1, -1}}};
+  return R[j];
+}
+
+template <class T>
+struct Pollu {  // p = (k1..k25)
+  static constexpr int D = 20, P = 25, NW = 0;
+  static constexpr bool autonomous = true, has_noise = false, sde_only = false, has_event = false;
+  static constexpr bool stiff_only = true;  // Rosenbrock23 only, one trajectory per thread
+  static __device__ __forceinline__ void f(const T* y, const T* k, T, T* dy) {
+#pragma unroll
+    for (int i = 0; i < 20; ++i) dy[i] = T(0);
+#pragma unroll
+    for (int j = 0; j < 25; ++j) {
+      const PolluRx r = pollu_rx(j);
+      const T rate = r.b < 0 ? k[j] * y[r.a] : k[j] * y[r.a] * y[r.b];
+#pragma unroll
+      for (int m = 0; m < 5; ++m)
+        if (m < r.n) dy[r.sp[m]] = M<T>::fma(T(r.nu[m]), rate, dy[r.sp[m]]);
+    }
+  }
+  static __device__ __forceinline__ void jac(const T* y, const T* k, T, T* J) {
+#pragma unroll
+    for (int i = 0; i < 400; ++i) J[i] = T(0);
+#pragma unroll
+    for (int j = 0; j < 25; ++j) {
+      const PolluRx r = pollu_rx(j);
+      const T dra = r.b < 0 ? k[j] : k[j] * y[r.b];
+      const T drb = r.b < 0 ? T(0) : k[j] * y[r.a];
+#pragma unroll
+      for (int m = 0; m < 5; ++m)
+        if (m < r.n) {
+          J[r.sp[m] * 20 + r.a] = M<T>::fma(T(r.nu[m]), dra, J[r.sp[m] * 20 + r.a]);
+          if (r.b >= 0) J[r.sp[m] * 20 + r.b] = M<T>::fma(T(r.nu[m]), drb, J[r.sp[m] * 20 + r.b]);
+        }
+    }
   }
 };
 
@@ -344,6 +482,86 @@ __device__ __forceinline__ void tsit5_dense(const T* u, T h, const T* k1, const 
   }
 }
 
+// Events (Sec. 6.5): a condition g(u, p, t) crossing zero from above inside an accepted step
+// triggers the model's affect.  The step's dense output is written as a polynomial in theta,
+// u(theta) = u_n + sum_{q=1..4} theta^q c_q with c_q = h sum_i r_iq k_i; the condition is
+// checked at theta = j / kEventPoints (u_n and u_{n+1} themselves at the ends); the first
+// interval with g > 0 at its left end and g <= 0 at its right end is narrowed by the Illinois
+// method (regula falsi that halves the value kept at an end surviving two iterations in a
+// row; Dowell & Jarratt 1971) until it is at most 4 eps wide or after 100 iterations.  The
+// event sits at the interval's right end.
+constexpr int kEventPoints = 10;
+
+template <class RHS, class T>
+__device__ __forceinline__ void dense_coeffs(T h, const T* k1, const T* kmid, const T* k7,
+                                             T (*c)[RHS::D]) {
+  constexpr int D = RHS::D;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      T s = T(ts5_dense(0, q)) * k1[j];
+#pragma unroll
+      for (int i = 1; i < 6; ++i) s = M<T>::fma(T(ts5_dense(i, q)), kmid[(i - 1) * D + j], s);
+      s = M<T>::fma(T(ts5_dense(6, q)), k7[j], s);
+      c[q][j] = h * s;
+    }
+}
+
+template <class RHS, class T>
+__device__ __forceinline__ void dense_poly(const T* u, const T (*c)[RHS::D], T th, T* out) {
+#pragma unroll
+  for (int j = 0; j < RHS::D; ++j)
+    out[j] = M<T>::fma(th, M<T>::fma(th, M<T>::fma(th, M<T>::fma(th, c[3][j], c[2][j]), c[1][j]),
+                                     c[0][j]),
+                       u[j]);
+}
+
+// theta in (0, 1] of the first crossing from above in the step, or -1 for none
+template <class RHS, class T>
+__device__ T find_event(const T* u, const T* unew, const T* p, T tn, T h,
+                        const T (*c)[RHS::D]) {
+  T w[RHS::D];
+  T a = T(0), ga = RHS::event_condition(u, p, tn);
+  for (int j = 1; j <= kEventPoints; ++j) {
+    T b0, gb0;
+    if (j == kEventPoints) {
+      b0 = T(1);
+      gb0 = RHS::event_condition(unew, p, tn + h);
+    } else {
+      b0 = T(j) / T(kEventPoints);
+      dense_poly<RHS, T>(u, c, b0, w);
+      gb0 = RHS::event_condition(w, p, tn + b0 * h);
+    }
+    if (ga > T(0) && gb0 <= T(0)) {
+      T b = b0, gb = gb0;
+      int side = 0;
+      const T width = T(4) * (sizeof(T) == 4 ? T(1.1920928955078125e-07) : T(2.220446049250313e-16));
+      for (int it = 0; it < 100 && b - a > width; ++it) {
+        T x = (a * gb - b * ga) / (gb - ga);
+        if (!(x > a && x < b)) x = (a + b) * T(0.5);
+        dense_poly<RHS, T>(u, c, x, w);
+        const T gx = RHS::event_condition(w, p, tn + x * h);
+        if (gx > T(0)) {
+          a = x;
+          ga = gx;
+          if (side == 1) gb *= T(0.5);
+          side = 1;
+        } else {
+          b = x;
+          gb = gx;
+          if (side == -1) ga *= T(0.5);
+          side = -1;
+        }
+      }
+      return b;
+    }
+    a = b0;
+    ga = gb0;
+  }
+  return T(-1);
+}
+
 // Classic RK4 step.
 template <class RHS, class T>
 __device__ __forceinline__ void rk4_step(const T* u, const T* p, T t, T h, T* unew) {
@@ -443,6 +661,80 @@ struct LU {
   }
 };
 
+// The same factorisation and solve for larger D (8 and up) as loops over a local-memory
+// matrix: the fully unrolled, select-based form above would need D^2 registers and D^3 / 2
+// selects (at D = 20 it spills and takes minutes to compile).  Same pivot rule, same operation
+// order, so the same results.
+template <class T, int D>
+struct LUDyn {
+  T a[D][D];
+  int piv[D];  // row exchanged with row c for column c (c itself: none)
+
+  __device__ void factor(const T (&W)[D][D]) {
+#pragma unroll 1
+    for (int r = 0; r < D; ++r)
+#pragma unroll 1
+      for (int j = 0; j < D; ++j) a[r][j] = W[r][j];
+#pragma unroll 1
+    for (int c = 0; c < D; ++c) {
+      T big = M<T>::abs(a[c][c]);
+      int best = c;
+#pragma unroll 1
+      for (int r = c + 1; r < D; ++r) {
+        const T v = M<T>::abs(a[r][c]);
+        if (v > big) {
+          big = v;
+          best = r;
+        }
+      }
+      piv[c] = best;
+      if (best != c) {
+#pragma unroll 1
+        for (int j = 0; j < D; ++j) {
+          const T t = a[c][j];
+          a[c][j] = a[best][j];
+          a[best][j] = t;
+        }
+      }
+      const T inv = M<T>::rcp(a[c][c]);
+      a[c][c] = inv;
+#pragma unroll 1
+      for (int r = c + 1; r < D; ++r) {
+        const T l = a[r][c] * inv;
+        a[r][c] = l;
+#pragma unroll 1
+        for (int j = c + 1; j < D; ++j) a[r][j] = M<T>::fma(-l, a[c][j], a[r][j]);
+      }
+    }
+  }
+
+  __device__ void solve(const T* b, T* x) const {
+    T y[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) y[r] = b[r];
+#pragma unroll 1
+    for (int c = 0; c < D; ++c) {
+      const int q = piv[c];
+      if (q != c) {
+        const T t = y[c];
+        y[c] = y[q];
+        y[q] = t;
+      }
+    }
+#pragma unroll 1
+    for (int r = 0; r < D; ++r)
+#pragma unroll 1
+      for (int j = 0; j < r; ++j) y[r] = M<T>::fma(-a[r][j], y[j], y[r]);
+#pragma unroll 1
+    for (int r = D - 1; r >= 0; --r) {
+      T v = y[r];
+#pragma unroll 1
+      for (int j = r + 1; j < D; ++j) v = M<T>::fma(-a[r][j], x[j], v);
+      x[r] = v * a[r][r];
+    }
+  }
+};
+
 // One Rosenbrock23 (ode23s) step from (u, t) with f0 = f(u, t); W = I - h d J:
 //   k1 = W^-1 f0,  f1 = f(u + h/2 k1),  k2 = W^-1 (f1 - k1) + k1,  u_{n+1} = u + h k2,
 //   f2 = f(u_{n+1}),  k3 = W^-1 (f2 - e32 (k2 - f1) - 2 (k1 - f0)),  err = h/6 (k1 - 2 k2 + k3).
@@ -463,7 +755,7 @@ __device__ __forceinline__ void ros23_step(const T* u, const T* p, T t, T h, con
   for (int r = 0; r < D; ++r)
 #pragma unroll
     for (int c = 0; c < D; ++c) W[r][c] = m::fma(-hd, Jf[r * D + c], (r == c) ? T(1) : T(0));
-  LU<T, D> lu;
+  typename std::conditional<(D < 8), LU<T, D>, LUDyn<T, D>>::type lu;
   lu.factor(W);
   T k1[D], k2[D], k3[D], f1[D], U[D], v[D];
   lu.solve(f0, k1);

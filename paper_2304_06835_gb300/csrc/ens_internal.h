@@ -22,6 +22,8 @@ struct SolveArgs {
   long long maxiters;
   int maxiters_i;   // the same cap as an int (validated <= 2e9)
   float abstol_f, reltol_f, dt0_f;  // FP32 copies (an FP32 solve never converts in its loop)
+  double dtmax;     // adaptive: largest step (+inf when the caller set none)
+  float dtmax_f;
   int refill_min;   // persistent schedule: refill a warp's idle lanes once this many are idle
   int dense;        // adaptive Tsit5 with save times: dense output instead of cut steps
   unsigned long long seed;

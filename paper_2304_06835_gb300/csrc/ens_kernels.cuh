@@ -116,12 +116,14 @@ struct Tol {
   static __device__ __forceinline__ T abstol(const SolveArgs& a) { return T(a.abstol); }
   static __device__ __forceinline__ T reltol(const SolveArgs& a) { return T(a.reltol); }
   static __device__ __forceinline__ T dt0(const SolveArgs& a) { return T(a.dt0); }
+  static __device__ __forceinline__ T dtmax(const SolveArgs& a) { return T(a.dtmax); }
 };
 template <>
 struct Tol<float> {
   static __device__ __forceinline__ float abstol(const SolveArgs& a) { return a.abstol_f; }
   static __device__ __forceinline__ float reltol(const SolveArgs& a) { return a.reltol_f; }
   static __device__ __forceinline__ float dt0(const SolveArgs& a) { return a.dt0_f; }
+  static __device__ __forceinline__ float dtmax(const SolveArgs& a) { return a.dtmax_f; }
 };
 
 template <class T>
@@ -144,6 +146,9 @@ template <class RHS, class T, int METH>
 struct Adaptive {
   static constexpr int D = RHS::D, P = RHS::P;
   static constexpr bool kDense = METH == METH_TSIT5_DENSE;
+  static constexpr bool kEvent = RHS::has_event && METH != METH_ROS23;
+  static constexpr bool kKeepStages = kDense || kEvent;  // stages 2..6 outlive the step
+  static constexpr int kMaxTpt = RHS::stiff_only ? 1 : 4;  // trajectories per thread
   // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k
   static constexpr float kOrd = (METH != METH_ROS23) ? 5.f : 3.f;
   static constexpr int kInitOrder = (METH != METH_ROS23) ? 5 : 2;
@@ -154,7 +159,7 @@ struct Adaptive {
   T tf, h;
   T stop, stop_thr;   // next stop (a save time before tf, or tf) and its arrival threshold
   float lq;           // log2 q_{n-1}
-  int attempts, rejected, si, fev0;
+  int attempts, rejected, si, fev0, nev;  // nev: events handled (one extra f each)
   int st;             // ENS_TRAJ_* (int, not char: no byte packing in the loop)
   int stop_is_save;
   long long idx;
@@ -181,6 +186,7 @@ struct Adaptive {
     lq = kLog2QoldInit;
     attempts = 0;
     rejected = 0;
+    nev = 0;
     st = ENS_TRAJ_OK;
     si = 0;
     while (si < a.n_save && T(a.saveat[si]) < t0) {
@@ -195,17 +201,17 @@ struct Adaptive {
     set_stop(a);
   }
 
-  // dense output: every save time in (t_n, t_n + hs] of the accepted step from (u, fk),
-  // theta = (s - t_n) / hs on the compensated clock; a save at the end of the last step is
-  // u_{n+1} itself
-  __device__ __forceinline__ void dense_saves(const SolveArgs& a, T hs, bool last,
+  // dense output: every save time in (t_n, t_n + lim] of the accepted step from (u, fk)
+  // (lim = hs, or the event's offset when an event ends the step early), theta =
+  // (s - t_n) / hs on the compensated clock; a save at the end of the last step is u_{n+1}
+  __device__ __forceinline__ void dense_saves(const SolveArgs& a, T hs, T lim, bool last,
                                               const T* kmid, const T* fnew, const T* unew) {
     while (si < a.n_save) {
       const T sv = T(a.saveat[si]);
       if (sv > tf) break;
       const T rs = t.remaining(sv);
       const bool at_end = last && sv == stop;
-      if (!at_end && rs > hs) break;
+      if (!at_end && rs > lim) break;
       if (at_end) {
         write_slot<RHS, T>(a, idx, si, unew);
       } else {
@@ -269,15 +275,20 @@ struct Adaptive {
         rem = t.remaining(stop);
       } while (rem <= stop_thr);
     }
-    const bool last = h >= rem;
-    const T hs = last ? rem : h;
+    // the cap (+inf when not set) keeps a NaN step NaN, so a failing trajectory fails alike
+    // with and without it
+    const T dtmax = Tol<T>::dtmax(a);
+    const T hcap = (h > dtmax) ? dtmax : h;
+    const bool last = hcap >= rem;
+    const T hs = last ? rem : hcap;
     const T tnow = t.value();
     const bool capped = attempts >= a.maxiters_i;
     const bool tiny = hs < T(M<T>::dtmin_factor) * M<T>::max(T(1), M<T>::abs(tnow));
-    T unew[D], es[D], fnew[D], kmid[kDense ? 5 * D : 1];
-    if (METH != METH_ROS23)
-      tsit5_step<RHS, T, true>(u, p, tnow, hs, fk, unew, es, fnew, kDense ? kmid : nullptr);
-    else ros23_step<RHS, T>(u, p, tnow, hs, fk, unew, es, fnew);
+    T unew[D], es[D], fnew[D], kmid[kKeepStages ? 5 * D : 1];
+    if constexpr (METH != METH_ROS23)
+      tsit5_step<RHS, T, true>(u, p, tnow, hs, fk, unew, es, fnew, kKeepStages ? kmid : nullptr);
+    else
+      ros23_step<RHS, T>(u, p, tnow, hs, fk, unew, es, fnew);
     // q^2 = (1/D) sum_j (E_j / (atol + rtol max(|u_j|, |unew_j|)))^2 with E_j = h es_j.
     // The ratios are formed in FP32 for both precisions (E itself is accumulated in T).
     const T atol = Tol<T>::abstol(a), rtol = Tol<T>::reltol(a);
@@ -299,7 +310,24 @@ struct Adaptive {
     }
     ++attempts;
     const bool acc = q2 <= 1.f;
-    if (kDense && acc) dense_saves(a, hs, last, kmid, fnew, unew);
+    T th_ev = T(-1);
+    if constexpr (kEvent) {
+      if (acc) {
+        T cq[4][D];
+        dense_coeffs<RHS, T>(hs, fk, kmid, fnew, cq);
+        th_ev = find_event<RHS, T>(u, unew, p, tnow, hs, cq);
+        if (th_ev > T(0)) {  // the event: saves up to it from this step, state, affect, f
+          const bool cut = th_ev < T(1);
+          if (kDense) dense_saves(a, hs, cut ? th_ev * hs : hs, last && !cut, kmid, fnew, unew);
+          if (cut) dense_poly<RHS, T>(u, cq, th_ev, unew);
+          RHS::event_affect(unew, p, tnow + th_ev * hs);
+          RHS::f(unew, p, tnow + th_ev * hs, fnew);
+          ++nev;
+        }
+      }
+    }
+    if (kDense && acc && !(th_ev > T(0))) dense_saves(a, hs, hs, last, kmid, fnew, unew);
+    const bool cut = th_ev > T(0) && th_ev < T(1);  // an event ended the step early
     // PI control: accept fac = eta q_n^{-beta1} q_{n-1}^{beta2} in [0.2, 10];
     // reject fac = max(0.2, eta q_n^{-1/k}).  Exponentials in log2 form (q guarded at 1e-10).
     const float L = lg2_approx(fmaxf(q2, 1e-20f));  // log2 q^2
@@ -310,8 +338,8 @@ struct Adaptive {
       u[j] = acc ? unew[j] : u[j];
       fk[j] = acc ? fnew[j] : fk[j];
     }
-    t.add(acc ? hs : T(0));
-    t.snap(acc && last, stop);
+    t.add(acc ? (cut ? th_ev * hs : hs) : T(0));
+    t.snap(acc && last && !cut, stop);
     lq = acc ? fmaxf(0.5f * L, kLog2QoldInit) : lq;
     rejected += acc ? 0 : 1;
     h = hs * T(fac);
@@ -321,7 +349,8 @@ struct Adaptive {
   __device__ __forceinline__ void finish(const SolveArgs& a) {
     if (a.n_save == 0) write_slot<RHS, T>(a, idx, 0, u);
     for (; si < a.n_save; ++si) write_nan_slot<RHS, T>(a, idx, si);
-    write_stats(a, idx, st, attempts - rejected, rejected, fev0 + kFevPerAttempt * attempts);
+    write_stats(a, idx, st, attempts - rejected, rejected,
+                fev0 + kFevPerAttempt * attempts + nev);
   }
 
   // expected work of trajectory i: (tf - t0) / (starting step), the number of steps a solve
@@ -348,6 +377,7 @@ struct Fixed {
   // Philox call serves kSub steps (NW <= per_call) or one step takes kCalls calls.
   static constexpr int kNW = RHS::NW > 0 ? RHS::NW : 1, kPC = Normals<T>::per_call;
   static_assert(kPC % kNW == 0 || kNW % kPC == 0, "normals per step vs per Philox call");
+  static constexpr int kMaxTpt = 4;
   static constexpr int kSub = (METH == METH_FIX_EM && kNW <= kPC) ? kPC / kNW : 1;
   static constexpr int kCalls = (METH == METH_FIX_EM && kNW > kPC) ? kNW / kPC : 1;
 

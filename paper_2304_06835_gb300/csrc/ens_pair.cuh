@@ -173,6 +173,7 @@ struct AdaptivePair {
     s.attempts = attempts[k];
     s.rejected = rejected[k];
     s.fev0 = fev0[k];
+    s.nev = 0;  // the paired kernel serves models without events
     s.finish(a);
   }
 

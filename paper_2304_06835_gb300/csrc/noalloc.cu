@@ -57,6 +57,10 @@ bool dims_of(int rhs_id, int* D, int* P) {
     case ENS_RHS_ROBERTSON: *D = 3; *P = 3; return true;
     case ENS_RHS_GBM: *D = 1; *P = 2; return true;
     case ENS_RHS_CRN: *D = 4; *P = 6; return true;
+    case ENS_RHS_BALL: *D = 2; *P = 2; return true;
+    case ENS_RHS_OREGO: *D = 3; *P = 3; return true;
+    case ENS_RHS_HIRES: *D = 8; *P = 12; return true;
+    case ENS_RHS_POLLU: *D = 20; *P = 25; return true;
   }
   return false;
 }
@@ -80,6 +84,11 @@ int check_args(int rhs_id, long long N, const void* params, const void* u0, cons
     return set_last_error(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM, CRN)");
   if (rhs_id == ENS_RHS_CRN && o->alg != ENS_EM)
     return set_last_error(ENS_EINVAL, "the CRN model takes Euler-Maruyama only");
+  if (rhs_id == ENS_RHS_BALL && o->alg != ENS_TSIT5_ADAPTIVE)
+    return set_last_error(ENS_EINVAL, "the bouncing ball's events need adaptive Tsit5");
+  if ((rhs_id == ENS_RHS_HIRES || rhs_id == ENS_RHS_POLLU) && o->alg != ENS_ROS23)
+    return set_last_error(ENS_EINVAL, "HIRES and POLLU take Rosenbrock23 only");
+  if (!std::isfinite(o->dtmax)) return set_last_error(ENS_EINVAL, "dtmax not finite");
   if (fixed_alg(o->alg) && !(o->dt > 0 && std::isfinite(o->dt)))
     return set_last_error(ENS_EINVAL, "fixed-step methods need a finite dt > 0");
   if (!fixed_alg(o->alg) && (!(o->abstol >= 1e-30) || !std::isfinite(o->abstol) ||
@@ -144,6 +153,8 @@ extern "C" int ens_solve_noalloc(int rhs_id, long long N, const void* params, co
   a.abstol_f = (float)o->abstol;
   a.reltol_f = (float)o->reltol;
   a.dt0_f = (float)o->dt0;
+  a.dtmax = o->dtmax > 0 ? o->dtmax : HUGE_VAL;
+  a.dtmax_f = o->dtmax > 0 ? (float)o->dtmax : HUGE_VALF;
   a.refill_min = o->refill_min > 0 ? o->refill_min : 4;
   a.dense = o->dense != 0 && o->n_save > 0;
   a.seed = o->seed;

@@ -16,7 +16,7 @@ struct PairOf {
 };
 template <class RHS>
 struct PairOf<Adaptive<RHS, float, METH_TSIT5>> {
-  static constexpr bool ok = RHS::autonomous;
+  static constexpr bool ok = RHS::autonomous && !RHS::has_event;
   typedef RHS rhs;
 };
 
@@ -52,8 +52,10 @@ cudaError_t launch_persistent_pair(const SolveArgs& a, const LaunchCfg& cfg, cud
 template <class I, int TPT>
 cudaError_t launch_persistent(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
   if constexpr (TPT == 2 && PairOf<I>::ok) {
-    // two trajectories per thread in lockstep on the paired FP32 instructions (no save times)
-    if (a.n_save == 0) return launch_persistent_pair<typename PairOf<I>::rhs>(a, cfg, s);
+    // two trajectories per thread in lockstep on the paired FP32 instructions (no save
+    // times, no step cap)
+    if (a.n_save == 0 && !(a.dtmax_f < HUGE_VALF))
+      return launch_persistent_pair<typename PairOf<I>::rhs>(a, cfg, s);
   }
   int grid = 0;
   cudaError_t e = persistent_grid<I, TPT>(cfg, &grid);
@@ -73,22 +75,28 @@ cudaError_t launch_integ(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t 
     k_direct<I><<<grid, cfg.block, 0, s>>>(a);
     return cudaGetLastError();
   }
-  switch (cfg.tpt) {
-    case 1: return launch_persistent<I, 1>(a, cfg, s);
-    case 2: return launch_persistent<I, 2>(a, cfg, s);
-    case 4: return launch_persistent<I, 4>(a, cfg, s);
+  if constexpr (I::kMaxTpt == 1) {  // one trajectory per thread whatever was asked
+    return launch_persistent<I, 1>(a, cfg, s);
+  } else {
+    switch (cfg.tpt) {
+      case 1: return launch_persistent<I, 1>(a, cfg, s);
+      case 2: return launch_persistent<I, 2>(a, cfg, s);
+      case 4: return launch_persistent<I, 4>(a, cfg, s);
+    }
+    return cudaErrorInvalidValue;
   }
-  return cudaErrorInvalidValue;
 }
 
 template <class I>
 cudaError_t attrs_integ(const LaunchCfg& cfg, cudaFuncAttributes* attr, int* bps) {
   const void* fn = nullptr;
   if (cfg.schedule == ENS_SCHED_DIRECT) fn = (const void*)k_direct<I>;
-  else if (cfg.tpt == 1) fn = (const void*)k_persistent<I, 1>;
-  else if (cfg.tpt == 2) fn = (const void*)k_persistent<I, 2>;
-  else if (cfg.tpt == 4) fn = (const void*)k_persistent<I, 4>;
-  else return cudaErrorInvalidValue;
+  else if (cfg.tpt == 1 || I::kMaxTpt == 1) fn = (const void*)k_persistent<I, 1>;
+  else if constexpr (I::kMaxTpt > 1) {
+    if (cfg.tpt == 2) fn = (const void*)k_persistent<I, 2>;
+    else if (cfg.tpt == 4) fn = (const void*)k_persistent<I, 4>;
+    else return cudaErrorInvalidValue;
+  }
   cudaError_t e = cudaFuncGetAttributes(attr, fn);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, cfg.block, 0);
@@ -113,7 +121,15 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
                            bool* supported, cudaFuncAttributes* attr, int* bps,
                            CostScratch* cs) {
   *supported = true;
-  if constexpr (RHS::sde_only) {
+  if constexpr (RHS::stiff_only) {  // large stiff models: Rosenbrock23 only
+    if (alg == ENS_ROS23) return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps, cs);
+  } else if constexpr (RHS::has_event) {  // events are located on the adaptive Tsit5 interpolant
+    if (alg == ENS_TSIT5_ADAPTIVE) {
+      if (a && a->dense)
+        return run_integ<Adaptive<RHS, T, METH_TSIT5_DENSE>>(a, cfg, s, attr, bps, cs);
+      return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps, cs);
+    }
+  } else if constexpr (RHS::sde_only) {
     if (alg == ENS_EM) return run_integ<Fixed<RHS, T, METH_FIX_EM>>(a, cfg, s, attr, bps, cs);
   } else {
     switch (alg) {

@@ -23,7 +23,7 @@ _NP_DT = {np.dtype(np.float32): _lib.F32, np.dtype(np.float64): _lib.F64}
 def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-6, reltol=1e-6,
               dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
               schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0,
-              dense=False):
+              dense=False, dtmax=0.0):
     o = _lib.EnsOpts()
     _lib.lib().ens_opts_default(ctypes.byref(o))
     o.alg = _lib.ALG[alg] if isinstance(alg, str) else int(alg)
@@ -48,6 +48,7 @@ def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-
     o.order = _lib.ORDER[order] if isinstance(order, str) else int(order)
     o.blocks_per_sm = int(blocks_per_sm)
     o.dense = 1 if dense else 0
+    o.dtmax = float(dtmax)
     return o, keep
 
 
@@ -56,8 +57,8 @@ def _ptr(t):
 
 
 class EnsembleSolver:
-    """One solver handle for one right-hand side ("lorenz", "robertson", "gbm" or "crn"; the
-    CRN takes alg="em" only)."""
+    """One solver handle for one right-hand side ("lorenz", "robertson", "gbm", "crn" or
+    "ball"; the CRN takes alg="em" only, the bouncing ball alg="tsit5" only)."""
 
     def __init__(self, rhs: str):
         self.rhs = rhs
@@ -91,11 +92,12 @@ class EnsembleSolver:
     def solve(self, params, u0, tspan, alg="tsit5", *, layout="rowmajor", dt=0.0, abstol=1e-6,
               reltol=1e-6, dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
               schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0,
-              dense=False, want_status=True, want_stats=False, out=None, status=None, stats=None,
-              stream=None):
+              dense=False, dtmax=0.0, want_status=True, want_stats=False, out=None, status=None,
+              stats=None, stream=None):
         """Solve the ensemble on the GPU (device tensors in and out).  dense=True (adaptive
         Tsit5 with saveat): save times take the step's dense output instead of cutting the
-        steps, so the steps and final state are those of the solve without save times."""
+        steps, so the steps and final state are those of the solve without save times.
+        dtmax > 0 caps adaptive steps."""
         if not (params.is_cuda and u0.is_cuda and tspan.is_cuda):
             raise ValueError("params, u0 and tspan must be CUDA tensors")
         if params.dtype not in _TORCH_DT or u0.dtype != params.dtype or tspan.dtype != params.dtype:
@@ -117,7 +119,7 @@ class EnsembleSolver:
             stats = torch.empty((3, N), dtype=torch.int32, device=dev)
         o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, dt, abstol, reltol, dt0, maxiters,
                             saveat, seed, index_offset, schedule, block, tpt, refill_min, order,
-                            blocks_per_sm, dense)
+                            blocks_per_sm, dense, dtmax)
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
         _lib.check(_lib.lib().ens_solve(self._h, N, _ptr(params), _ptr(u0), _ptr(tspan),
                                         ctypes.byref(o), _ptr(out), _ptr(status), _ptr(stats),

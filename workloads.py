@@ -23,6 +23,16 @@ Workloads (the paper's models with the shapes and value ranges of its benchmarks
                              combinations (the Cartesian product), u0 = (nu0, nu0, nu0, nu0),
                              tspan [0, 1000] (Appendix, CRN model and its parameter table).
   * ``crn_random``        -- the same ranges, each trajectory's parameters drawn independently.
+  * ``stiff``             -- the paper's stiff test models with their printed initial states and
+                             spans: Orego (k = (77.27, 8.375e-6, 0.161), y0 = (1, 2, 3), [0, 30]),
+                             HIRES (its 12 distinct constants, y0 = (1, 0, ..., 0, 0.0057),
+                             [0, 321.8122]), POLLU (k1..k25 as printed, y0 as printed, [0, 60]);
+                             each trajectory scales every constant by a log-uniform factor in
+                             [0.9, 1.1] (the recipe of the Robertson ensemble).
+  * ``ball``              -- bouncing ball, p = (g, e) with g = 9.8 and the coefficient of
+                             restitution e ~ U[0.7, 0.95] per trajectory, u0 = (50, 0) (a drop
+                             from 50 m at rest), tspan [0, 15] (Appendix, bouncing-ball problem;
+                             e >= 0.65 keeps the bounces' accumulation point after t = 15).
 """
 from __future__ import annotations
 
@@ -130,3 +140,35 @@ def crn_random(N: int, seed: int = 9, t1: float = 1000.0):
     rng = np.random.default_rng(seed)
     p = rng.uniform(CRN_BOX[:, 0], CRN_BOX[:, 1], size=(N, 6))
     return _crn_problem(p, t1)
+
+
+def ball(N: int, seed: int = 10, t1: float = 15.0, x0: float = 50.0):
+    rng = np.random.default_rng(seed)
+    p = np.stack([np.full(N, 9.8), rng.uniform(0.7, 0.95, N)], axis=1)
+    u0 = np.tile([x0, 0.0], (N, 1))
+    tspan = np.zeros((N, 2))
+    tspan[:, 1] = t1
+    return p, u0, tspan
+
+
+OREGO_K = [77.27, 8.375e-6, 0.161]
+HIRES_C = [1.71, 0.43, 8.32, 0.0007, 8.75, 10.03, 0.035, 1.12, 1.745, 280.0, 0.69, 1.81]
+POLLU_K = [0.35, 26.6, 12300.0, 0.00086, 0.00082, 15000.0, 0.00013, 24000.0, 16500.0, 9000.0,
+           0.022, 12000.0, 1.88, 16300.0, 4.8e6, 0.00035, 0.0175, 1.0e8, 4.44e11, 1240.0, 2.1,
+           5.78, 0.0474, 1780.0, 3.12]
+STIFF = {
+    "orego": (OREGO_K, [1.0, 2.0, 3.0], 30.0),
+    "hires": (HIRES_C, [1.0, 0, 0, 0, 0, 0, 0, 0.0057], 321.8122),
+    "pollu": (POLLU_K, [0.0, 0.2, 0.0, 0.04, 0.0, 0.0, 0.1, 0.3, 0.017, 0.0, 0.0, 0.0, 0.0, 0.0,
+                        0.0, 0.0, 0.007, 0.0, 0.0, 0.0], 60.0),
+}
+
+
+def stiff(model: str, N: int, seed: int = 11, t1: float | None = None):
+    k0, y0, tf = STIFF[model]
+    rng = np.random.default_rng(seed)
+    k = np.asarray(k0) * np.exp(rng.uniform(np.log(0.9), np.log(1.1), (N, len(k0))))
+    u0 = np.tile(y0, (N, 1)).astype(np.float64)
+    tspan = np.zeros((N, 2))
+    tspan[:, 1] = tf if t1 is None else t1
+    return k, u0, tspan
