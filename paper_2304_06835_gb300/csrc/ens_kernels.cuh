@@ -92,6 +92,8 @@ __device__ __forceinline__ void write_slot(const SolveArgs& a, long long i, int 
   for (int k = 0; k < RHS::D; ++k) o[out_idx(a.layout, i, s, k, a.N, S, RHS::D)] = v[k];
 }
 
+__host__ __device__ constexpr int gcd_int(int a, int b) { return b == 0 ? a : gcd_int(b, a % b); }
+
 template <class RHS, class T>
 __device__ __forceinline__ void write_nan_slot(const SolveArgs& a, long long i, int s) {
   T v[RHS::D];
@@ -149,6 +151,13 @@ struct Adaptive {
   static constexpr bool kEvent = RHS::has_event && METH != METH_ROS23;
   static constexpr bool kKeepStages = kDense || kEvent;  // stages 2..6 outlive the step
   static constexpr int kMaxTpt = RHS::stiff_only ? 1 : 4;  // trajectories per thread
+  // Dense saving stages kSaveK saves (a whole number of 16-byte words) per lane in registers
+  // and writes them with vector stores when the output is trajectory-major, 16-byte aligned
+  // and n_save is a multiple of kSaveK: the lanes of a warp save at different times, so
+  // scalar stores would reach L2 as 4- or 8-byte pieces of separate sectors.
+  static constexpr int kRowBytes = D * int(sizeof(T));
+  static constexpr int kSaveK = kDense ? 16 / gcd_int(16, kRowBytes) : 1;
+  static constexpr int kSaveWords = kSaveK * kRowBytes / 16;
   // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k
   static constexpr float kOrd = (METH != METH_ROS23) ? 5.f : 3.f;
   static constexpr int kInitOrder = (METH != METH_ROS23) ? 5 : 2;
@@ -163,6 +172,38 @@ struct Adaptive {
   int st;             // ENS_TRAJ_* (int, not char: no byte packing in the loop)
   int stop_is_save;
   long long idx;
+  T sbuf[kDense ? kSaveK * D : 1];  // staged saves (dense saving)
+  bool stage;                       // this solve stages its saves (see kSaveK)
+
+  // write save slot si (then ++si): directly, or through the 16-byte staging
+  __device__ __forceinline__ void put(const SolveArgs& a, const T* v) {
+    if constexpr (kDense) {
+      if (stage) {
+        const int k = si % kSaveK;
+#pragma unroll
+        for (int q = 0; q < kSaveK; ++q)
+#pragma unroll
+          for (int j = 0; j < D; ++j) sbuf[q * D + j] = (q == k) ? v[j] : sbuf[q * D + j];
+        if (k == kSaveK - 1) {  // a full group: slots si - k .. si
+          uint4* o = reinterpret_cast<uint4*>(static_cast<T*>(a.out) +
+                                              (idx * a.n_save + (si - k)) * (long long)D);
+          const uint4* w = reinterpret_cast<const uint4*>(sbuf);
+#pragma unroll
+          for (int q = 0; q < kSaveWords; ++q) o[q] = w[q];
+        }
+        ++si;
+        return;
+      }
+    }
+    write_slot<RHS, T>(a, idx, si, v);
+    ++si;
+  }
+  __device__ __forceinline__ void put_nan(const SolveArgs& a) {
+    T v[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) v[j] = nan_of<T>();
+    put(a, v);
+  }
 
   __device__ __forceinline__ void set_stop(const SolveArgs& a) {
     stop_is_save = !kDense && si < a.n_save && T(a.saveat[si]) < tf;
@@ -189,15 +230,11 @@ struct Adaptive {
     nev = 0;
     st = ENS_TRAJ_OK;
     si = 0;
-    while (si < a.n_save && T(a.saveat[si]) < t0) {
-      write_nan_slot<RHS, T>(a, idx, si);
-      ++si;
-    }
+    stage = kDense && a.layout == ENS_LAYOUT_ROWMAJOR && a.n_save % kSaveK == 0 &&
+            (reinterpret_cast<unsigned long long>(a.out) & 15ull) == 0;
+    while (si < a.n_save && T(a.saveat[si]) < t0) put_nan(a);
     if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
-      while (si < a.n_save && T(a.saveat[si]) == t0 && t0 <= tf) {
-        write_slot<RHS, T>(a, idx, si, u);
-        ++si;
-      }
+      while (si < a.n_save && T(a.saveat[si]) == t0 && t0 <= tf) put(a, u);
     set_stop(a);
   }
 
@@ -213,13 +250,12 @@ struct Adaptive {
       const bool at_end = last && sv == stop;
       if (!at_end && rs > lim) break;
       if (at_end) {
-        write_slot<RHS, T>(a, idx, si, unew);
+        put(a, unew);
       } else {
         T w[D];
         tsit5_dense<RHS, T>(u, hs, fk, kmid, fnew, rs / hs, w);
-        write_slot<RHS, T>(a, idx, si, w);
+        put(a, w);
       }
-      ++si;
     }
   }
 
@@ -263,14 +299,11 @@ struct Adaptive {
         t.set(stop);
         if (!stop_is_save) {  // tf (dense: every save left within the arrival threshold)
           while (si < a.n_save &&
-                 (T(a.saveat[si]) == tf || (kDense && T(a.saveat[si]) <= tf))) {
-            write_slot<RHS, T>(a, idx, si, u);
-            ++si;
-          }
+                 (T(a.saveat[si]) == tf || (kDense && T(a.saveat[si]) <= tf)))
+            put(a, u);
           return true;
         }
-        write_slot<RHS, T>(a, idx, si, u);
-        ++si;
+        put(a, u);
         set_stop(a);
         rem = t.remaining(stop);
       } while (rem <= stop_thr);
@@ -348,7 +381,7 @@ struct Adaptive {
 
   __device__ __forceinline__ void finish(const SolveArgs& a) {
     if (a.n_save == 0) write_slot<RHS, T>(a, idx, 0, u);
-    for (; si < a.n_save; ++si) write_nan_slot<RHS, T>(a, idx, si);
+    while (si < a.n_save) put_nan(a);
     write_stats(a, idx, st, attempts - rejected, rejected,
                 fev0 + kFevPerAttempt * attempts + nev);
   }

