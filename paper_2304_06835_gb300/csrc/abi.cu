@@ -360,7 +360,10 @@ void fill_args(SolveArgs* a, long long N, const void* params, const void* u0, co
   a->seed = o->seed;
   a->index_offset = o->index_offset;
   a->queue = queue;
-  for (int i = 0; i < o->n_save; ++i) a->saveat[i] = o->saveat[i];
+  for (int i = 0; i < o->n_save; ++i) {
+    a->saveat[i] = o->saveat[i];
+    a->saveat_f[i] = (float)o->saveat[i];
+  }
 }
 
 LaunchCfg resolve_cfg(const ens_handle* h, long long N, const ens_opts* o) {

@@ -670,11 +670,8 @@ struct LUDyn {
   T a[D][D];
   int piv[D];  // row exchanged with row c for column c (c itself: none)
 
-  __device__ void factor(const T (&W)[D][D]) {
-#pragma unroll 1
-    for (int r = 0; r < D; ++r)
-#pragma unroll 1
-      for (int j = 0; j < D; ++j) a[r][j] = W[r][j];
+  // factor a (filled by the caller) in place
+  __device__ void factor() {
 #pragma unroll 1
     for (int c = 0; c < D; ++c) {
       T big = M<T>::abs(a[c][c]);
@@ -747,16 +744,35 @@ __device__ __forceinline__ void ros23_step(const T* u, const T* p, T t, T h, con
   typedef M<T> m;
   const T d = T(0.29289321881345247559915563789515);   // 1 / (2 + sqrt 2)
   const T e32 = T(7.4142135623730950488016887242097);  // 6 + sqrt 2
-  T Jf[D * D];
-  RHS::jac(u, p, t, Jf);
-  T W[D][D];
   const T hd = h * d;
-#pragma unroll
-  for (int r = 0; r < D; ++r)
-#pragma unroll
-    for (int c = 0; c < D; ++c) W[r][c] = m::fma(-hd, Jf[r * D + c], (r == c) ? T(1) : T(0));
   typename std::conditional<(D < 8), LU<T, D>, LUDyn<T, D>>::type lu;
-  lu.factor(W);
+  if constexpr (D < 12) {  // J and W in registers, copied into the factorisation
+    T Jf[D * D];
+    RHS::jac(u, p, t, Jf);
+    T W[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) W[r][c] = m::fma(-hd, Jf[r * D + c], (r == c) ? T(1) : T(0));
+    if constexpr (D < 8) {
+      lu.factor(W);
+    } else {
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) lu.a[r][c] = W[r][c];
+      lu.factor();
+    }
+  } else {
+    // J, then W = I - h d J, then its LU, all in the one local-memory matrix (a thread's
+    // footprint stays D^2 values, so the resident threads' matrices fit in L1)
+    RHS::jac(u, p, t, &lu.a[0][0]);
+#pragma unroll 1
+    for (int r = 0; r < D; ++r)
+#pragma unroll 1
+      for (int c = 0; c < D; ++c) lu.a[r][c] = m::fma(-hd, lu.a[r][c], (r == c) ? T(1) : T(0));
+    lu.factor();
+  }
   T k1[D], k2[D], k3[D], f1[D], U[D], v[D];
   lu.solve(f0, k1);
   const T hh = T(0.5) * h;

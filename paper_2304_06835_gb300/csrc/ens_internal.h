@@ -31,6 +31,7 @@ struct SolveArgs {
   unsigned long long* queue;  // persistent-schedule counter (device), zeroed before launch
   const int* order;           // persistent schedule: queue slot -> trajectory index (or null)
   double saveat[ENS_MAX_SAVE];
+  float saveat_f[ENS_MAX_SAVE];  // FP32 copies (no double conversion on FP32 solves' path)
 };
 
 // Arguments of the discrete-adjoint kernels (fixed-step explicit RK, one thread per trajectory).

@@ -119,6 +119,7 @@ struct Tol {
   static __device__ __forceinline__ T reltol(const SolveArgs& a) { return T(a.reltol); }
   static __device__ __forceinline__ T dt0(const SolveArgs& a) { return T(a.dt0); }
   static __device__ __forceinline__ T dtmax(const SolveArgs& a) { return T(a.dtmax); }
+  static __device__ __forceinline__ T save(const SolveArgs& a, int s) { return T(a.saveat[s]); }
 };
 template <>
 struct Tol<float> {
@@ -126,6 +127,7 @@ struct Tol<float> {
   static __device__ __forceinline__ float reltol(const SolveArgs& a) { return a.reltol_f; }
   static __device__ __forceinline__ float dt0(const SolveArgs& a) { return a.dt0_f; }
   static __device__ __forceinline__ float dtmax(const SolveArgs& a) { return a.dtmax_f; }
+  static __device__ __forceinline__ float save(const SolveArgs& a, int s) { return a.saveat_f[s]; }
 };
 
 template <class T>
@@ -206,8 +208,8 @@ struct Adaptive {
   }
 
   __device__ __forceinline__ void set_stop(const SolveArgs& a) {
-    stop_is_save = !kDense && si < a.n_save && T(a.saveat[si]) < tf;
-    stop = stop_is_save ? T(a.saveat[si]) : tf;
+    stop_is_save = !kDense && si < a.n_save && Tol<T>::save(a, si) < tf;
+    stop = stop_is_save ? Tol<T>::save(a, si) : tf;
     stop_thr = T(kStopEps) * M<T>::max(T(1), M<T>::abs(stop));
   }
 
@@ -232,9 +234,9 @@ struct Adaptive {
     si = 0;
     stage = kDense && a.layout == ENS_LAYOUT_ROWMAJOR && a.n_save % kSaveK == 0 &&
             (reinterpret_cast<unsigned long long>(a.out) & 15ull) == 0;
-    while (si < a.n_save && T(a.saveat[si]) < t0) put_nan(a);
+    while (si < a.n_save && Tol<T>::save(a, si) < t0) put_nan(a);
     if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
-      while (si < a.n_save && T(a.saveat[si]) == t0 && t0 <= tf) put(a, u);
+      while (si < a.n_save && Tol<T>::save(a, si) == t0 && t0 <= tf) put(a, u);
     set_stop(a);
   }
 
@@ -244,7 +246,7 @@ struct Adaptive {
   __device__ __forceinline__ void dense_saves(const SolveArgs& a, T hs, T lim, bool last,
                                               const T* kmid, const T* fnew, const T* unew) {
     while (si < a.n_save) {
-      const T sv = T(a.saveat[si]);
+      const T sv = Tol<T>::save(a, si);
       if (sv > tf) break;
       const T rs = t.remaining(sv);
       const bool at_end = last && sv == stop;
@@ -299,7 +301,7 @@ struct Adaptive {
         t.set(stop);
         if (!stop_is_save) {  // tf (dense: every save left within the arrival threshold)
           while (si < a.n_save &&
-                 (T(a.saveat[si]) == tf || (kDense && T(a.saveat[si]) <= tf)))
+                 (Tol<T>::save(a, si) == tf || (kDense && Tol<T>::save(a, si) <= tf)))
             put(a, u);
           return true;
         }

@@ -161,7 +161,10 @@ extern "C" int ens_solve_noalloc(int rhs_id, long long N, const void* params, co
   a.index_offset = o->index_offset;
   a.queue = (unsigned long long*)(base + kQueueOff);
   a.order = nullptr;
-  for (int i = 0; i < o->n_save; ++i) a.saveat[i] = o->saveat[i];
+  for (int i = 0; i < o->n_save; ++i) {
+    a.saveat[i] = o->saveat[i];
+    a.saveat_f[i] = (float)o->saveat[i];
+  }
 
   LaunchCfg cfg;
   cfg.schedule = o->schedule != ENS_SCHED_AUTO
