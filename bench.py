@@ -94,6 +94,8 @@ WORKLOADS = {
                             t1=60.0, tol=1e-6, steps=5),
     "ball_events_f32": dict(kind="solve", rhs="ball", alg="tsit5", dtype="f32", N=1 << 20,
                             t1=15.0, tol=1e-6, dtmax=1.0, steps=100),
+    "lorenz_steps_f32": dict(kind="steps", rhs="lorenz", alg="tsit5", dtype="f32", N=1 << 20,
+                             t1=10.0, tol=1e-5, cap=256, layout="rowmajor", steps=100),
     "crn_em_f32": dict(kind="solve", rhs="crn", alg="em", dtype="f32", N=10 ** 6, t1=1000.0,
                        dt=0.1, seed=2024, steps=5),
     "crn_em_f64": dict(kind="solve", rhs="crn", alg="em", dtype="f64", N=10 ** 6, t1=1000.0,
@@ -258,7 +260,10 @@ def _oracle_run(w, P, U, T, n, nt, G=None):
             m = max(1, int(round(n * nk / w["N"])))
             oracle.solve(name, alg, Pk[:m], Uk[:m], Tk[:m], nthreads=nt, **kw)
         return
-    if w["kind"] == "adjoint":
+    if w["kind"] == "steps":  # the record of every accepted step
+        oracle.solve_steps(w["rhs"], w["alg"], P[:n], U[:n], T[:n], w["cap"], abstol=w["tol"],
+                           reltol=w["tol"], nthreads=nt)
+    elif w["kind"] == "adjoint":
         oracle.fixed_grad(w["rhs"], w["alg"], P[:n], U[:n], T[:n], w["dt"], G[:n], nthreads=nt)
     else:
         oracle.solve(w["rhs"], w["alg"], P[:n], U[:n], T[:n], nthreads=nt, **solve_kwargs(w))
@@ -444,6 +449,83 @@ class SolveRunner:
         return {"value": N / el, "unit": "trajectories/s",
                 "h2d_bytes_per_step": int(N * es * (self.P.shape[1] + D + 2)),
                 "d2h_bytes_per_step": int(N * es * D * S + N)}
+
+
+class StepsRunner(SolveRunner):
+    """One step = an adaptive solve that stores every accepted step (ens_opts.step_cap) into
+    preallocated record buffers (trajectory-major): the full-solution output path."""
+
+    def __init__(self, args, w, rank, dev):
+        import ctypes
+
+        import torch
+
+        import paper_2304_06835_gb300 as ens
+        from paper_2304_06835_gb300 import _lib
+        w = dict(w, kind="solve")
+        super().__init__(args, w, rank, dev)
+        N, D, cap = w["N"], self.U.shape[1], w["cap"]
+        self.rec_u = torch.empty((N, cap, D), dtype=self.dt_t, device=dev)
+        self.rec_t = torch.empty((N, cap), dtype=self.dt_t, device=dev)
+        self.rec_n = torch.empty(N, dtype=torch.int32, device=dev)
+        self.opts, self.keep = ens.make_opts(
+            w["alg"], _lib.F32 if w["dtype"] == "f32" else _lib.F64, "rowmajor",
+            abstol=w["tol"], reltol=w["tol"], schedule=args.schedule, block=args.block,
+            tpt=args.tpt, blocks_per_sm=args.bps, step_cap=cap, step_t=self.rec_t,
+            step_n=self.rec_n)
+        self.c = ctypes
+        self.lib = _lib
+
+    def step(self):
+        import torch
+        c = self.c
+        s = torch.cuda.current_stream(self.dev).cuda_stream
+        p = lambda t: c.c_void_p(t.data_ptr())
+        self.lib.check(self.lib.lib().ens_solve(self.solver.handle, self.w["N"], p(self.Pd),
+                                                p(self.Ud), p(self.Td), c.byref(self.opts),
+                                                p(self.rec_u), p(self.status), p(self.stats),
+                                                c.c_void_p(s)))
+
+    def work(self):
+        ops, extra = super().work()
+        n = self.rec_n.cpu().numpy().astype(np.int64)
+        es = 4 if self.w["dtype"] == "f32" else 8
+        extra["record_bytes_per_launch"] = int(np.minimum(n, self.w["cap"]).sum()) * es * (
+            self.U.shape[1] + 1)
+        return ops, extra
+
+    def e2e(self, stream):
+        """Trajectories/s with host buffers: pinned inputs copied in, the solve with its step
+        record, and the whole record (states, times, counts) copied back, in the timed
+        region."""
+        import torch
+        w, N = self.w, self.w["N"]
+        npdt = np.float32 if w["dtype"] == "f32" else np.float64
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=npdt)).pin_memory()
+        hP, hU, hT = pin(self.P), pin(self.U), pin(self.T)
+        hu = torch.empty(self.rec_u.shape, dtype=self.rec_u.dtype).pin_memory()
+        ht = torch.empty(self.rec_t.shape, dtype=self.rec_t.dtype).pin_memory()
+        hn = torch.empty(N, dtype=torch.int32).pin_memory()
+
+        def host_step():
+            self.Pd.copy_(hP, non_blocking=True)
+            self.Ud.copy_(hU, non_blocking=True)
+            self.Td.copy_(hT, non_blocking=True)
+            self.step()
+            hu.copy_(self.rec_u, non_blocking=True)
+            ht.copy_(self.rec_t, non_blocking=True)
+            hn.copy_(self.rec_n, non_blocking=True)
+            torch.cuda.synchronize()
+        host_step()
+        steps = max(3, min(self.args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            host_step()
+        el = (time.perf_counter() - t0) / steps
+        es = np.dtype(npdt).itemsize
+        return {"value": N / el, "unit": "trajectories/s",
+                "h2d_bytes_per_step": int(N * es * (self.P.shape[1] + self.U.shape[1] + 2)),
+                "d2h_bytes_per_step": int(hu.numel() * es + ht.numel() * es + 4 * N)}
 
 
 class AdjointRunner:
@@ -859,7 +941,8 @@ def main():
 
     dev = torch.device("cuda", local)
     runner = {"adjoint": AdjointRunner, "batch": BatchRunner, "surrogate": SurrogateRunner,
-              "mlp": MlpForwardRunner, "solve": SolveRunner}[w["kind"]](args, w, rank, dev)
+              "mlp": MlpForwardRunner, "solve": SolveRunner,
+              "steps": StepsRunner}[w["kind"]](args, w, rank, dev)
     N = w["N"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)

@@ -147,6 +147,17 @@ typedef struct {
                              solution storage), so the steps and the final state are those
                              of the solve without save times.  Other algorithms ignore it. */
   double dtmax;           /* adaptive methods: largest step; <= 0: none.  Finite. */
+  int step_cap;           /* adaptive methods, n_save = 0: > 0 stores every accepted step
+                             (the paper's full-solution storage, Sec. 5.1.1).  out is then
+                             [N][step_cap][D] (SOA: [step_cap][D][N]): entry k is the state
+                             after k accepted steps (entry 0: u0; after an event, the state
+                             that took the affect).  Entries past a trajectory's count are
+                             not written.  Storing stops at step_cap; the solve goes on. */
+  void* step_t;           /* device, opts->dtype: [N][step_cap] (SOA [step_cap][N]) times of
+                             the entries, or NULL */
+  int* step_n;            /* device int32 [N]: accepted steps + 1 (may exceed step_cap), or
+                             NULL.  (ens_solve and ens_solve_noalloc; ens_solve_host
+                             rejects a step record.) */
 } ens_opts;
 
 /* Fill *o with defaults: TSIT5_ADAPTIVE, F32, SOA, abstol=reltol=1e-6, maxiters=1e6, auto. */

@@ -67,6 +67,13 @@ def lib():
                 ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_longlong,
                 dp, ctypes.POINTER(ctypes.c_byte), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
                 ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
+            L.oracle_solve_steps.restype = ctypes.c_int
+            L.oracle_solve_steps.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, dp, dp, dp,
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_longlong,
+                ctypes.c_double, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_byte),
+                ctypes.POINTER(ctypes.c_longlong), dp, dp, ctypes.POINTER(ctypes.c_longlong),
+                ctypes.c_int]
             L.oracle_pollu_reaction_sum.restype = None
             L.oracle_pollu_reaction_sum.argtypes = [dp, dp, dp]
             L.oracle_tsit5_dense.restype = None
@@ -153,6 +160,36 @@ def solve(rhs, alg, params, u0, tspan, *, dt=0.0, abstol=1e-6, reltol=1e-3, dt0=
     if want_events:
         return out, status, stats, events
     return out, status, stats
+
+
+def solve_steps(rhs, alg, params, u0, tspan, cap, *, abstol=1e-6, reltol=1e-3, dt0=0.0,
+                maxiters=1_000_000, dtmax=0.0, precision="f64", nthreads=None):
+    """Every accepted step of an adaptive solve: returns (t [N, cap], u [N, cap, D],
+    n [N] = accepted steps + 1 (entry 0 is the initial state; entries past n are NaN; n may
+    exceed cap), out [N, D], status [N], stats [N, 3])."""
+    rhs_id = RHS[rhs] if isinstance(rhs, str) else int(rhs)
+    alg_id = ALG[alg] if isinstance(alg, str) else int(alg)
+    D, P = DIMS[rhs_id]
+    params = _f64(params).reshape(-1, P)
+    N = params.shape[0]
+    u0 = _f64(u0).reshape(N, D)
+    tspan = _f64(tspan).reshape(N, 2)
+    out = np.empty((N, D))
+    status = np.empty(N, np.int8)
+    stats = np.empty((N, 3), np.int64)
+    rt = np.empty((N, cap))
+    ru = np.empty((N, cap, D))
+    rn = np.empty(N, np.int64)
+    nt = default_threads() if nthreads is None else int(nthreads)
+    ll = ctypes.POINTER(ctypes.c_longlong)
+    rc = lib().oracle_solve_steps(
+        rhs_id, alg_id, {"f64": 0, "f32": 1}[precision], N, _dp(params), _dp(u0), _dp(tspan),
+        float(abstol), float(reltol), float(dt0), int(maxiters), float(dtmax), int(cap),
+        _dp(out), status.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)), stats.ctypes.data_as(ll),
+        _dp(rt), _dp(ru), rn.ctypes.data_as(ll), nt)
+    if rc != 0:
+        raise ValueError("oracle_solve_steps rejected its arguments")
+    return rt, ru, rn, out, status, stats
 
 
 def step(rhs, alg, u, p, t, h, z=0.0):

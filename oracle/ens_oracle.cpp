@@ -749,6 +749,16 @@ struct Traj {
   int S;
   signed char status;
   long long accepted, rejected, fevals, events;
+  // every-step record (adaptive methods): entry k = (t, u) after k accepted steps, k < cap
+  T* rec_t = nullptr;
+  T* rec_u = nullptr;
+  int cap = 0;
+  void record(T t) {
+    if (accepted < cap) {
+      rec_t[accepted] = t;
+      for (int j = 0; j < o->D; ++j) rec_u[accepted * o->D + j] = u[j];
+    }
+  }
 };
 
 template <class T>
@@ -864,6 +874,7 @@ void solve_adaptive(Traj<T>& tr) {
   const bool dense = o.dense && !is_r23 && save_mode;
   const bool ev = has_event(o.rhs) && !is_r23;
   long long events = 0;
+  if (tr.rec_t) tr.record(tr.t0);  // entry 0: the initial state
   if (dense)  // save times equal to t0 take u0; the steps then run to tf uncut
     while (si < S && T(o.saveat[si]) == tr.t0 && tr.t0 <= tr.tf) {
       for (int j = 0; j < D; ++j) tr.out[si * D + j] = tr.u[j];
@@ -953,6 +964,7 @@ void solve_adaptive(Traj<T>& tr) {
       else if (last) clk.set(stop);
       else clk.add(hs);
       tr.accepted += 1;
+      if (tr.rec_t) tr.record(clk.value());
       h = hs * fac;
     } else {
       const T qg = std::max(q, T(Q_FLOOR));
@@ -976,10 +988,12 @@ inline long long idx_out(int layout, long long i, int s, int k, long long N, int
 template <class T>
 void solve_range(const Opts& o, int layout, long long N, long long i0, long long i1,
                  const double* params, const double* u0, const double* tspan, double* out,
-                 signed char* status, long long* stats, long long* events) {
+                 signed char* status, long long* stats, long long* events,
+                 int cap = 0, double* rec_t = nullptr, double* rec_u = nullptr,
+                 long long* rec_n = nullptr) {
   const int D = o.D, P = o.P;
   const int S = o.n_save > 0 ? o.n_save : 1;
-  std::vector<T> buf(size_t(S) * D);
+  std::vector<T> buf(size_t(S) * D), rt(static_cast<size_t>(cap)), ru(static_cast<size_t>(cap) * D);
   for (long long i = i0; i < i1; ++i) {
     Traj<T> tr;
     tr.o = &o;
@@ -991,8 +1005,23 @@ void solve_range(const Opts& o, int layout, long long N, long long i0, long long
     tr.S = S;
     tr.status = ST_OK;
     tr.accepted = tr.rejected = tr.fevals = tr.events = 0;
+    if (cap > 0) {
+      tr.cap = cap;
+      tr.rec_t = rt.data();
+      tr.rec_u = ru.data();
+    }
     if (o.alg == ALG_TSIT5_ADAPTIVE || o.alg == ALG_ROS23) solve_adaptive<T>(tr);
     else solve_fixed<T>(tr, uint64_t(o.index_offset + i));
+    if (cap > 0) {  // row-major [N][cap] / [N][cap][D]; unused entries NaN
+      const long long n = std::min<long long>(tr.accepted + 1, cap);
+      for (int k = 0; k < cap; ++k) {
+        rec_t[i * cap + k] = k < n ? double(rt[k]) : std::numeric_limits<double>::quiet_NaN();
+        for (int j = 0; j < D; ++j)
+          rec_u[(i * cap + k) * D + j] =
+              k < n ? double(ru[k * D + j]) : std::numeric_limits<double>::quiet_NaN();
+      }
+      rec_n[i] = tr.accepted + 1;
+    }
     for (int s = 0; s < S; ++s)
       for (int k = 0; k < D; ++k) out[idx_out(layout, i, s, k, N, S, D)] = double(buf[s * D + k]);
     if (status) status[i] = tr.status;
@@ -1058,6 +1087,33 @@ int oracle_solve(int rhs_id, int alg, int precision, int layout, long long N,
       solve_range<double>(o, layout, N, a, b, params, u0, tspan, out, status, stats, events);
     else
       solve_range<float>(o, layout, N, a, b, params, u0, tspan, out, status, stats, events);
+  });
+  return 0;
+}
+
+// Every accepted step of adaptive solves (Tsit5, Rosenbrock23): rec_t[N][cap], rec_u[N][cap][D]
+// (row-major) hold (t, u) after k = 0, 1, ... accepted steps (k = 0: the initial state), the
+// entries past the count NaN; rec_n[N] = accepted steps + 1, which may exceed cap (the
+// record then holds the first cap).  out / status / stats as for oracle_solve (final state).
+int oracle_solve_steps(int rhs_id, int alg, int precision, long long N, const double* params,
+                       const double* u0, const double* tspan, double abstol, double reltol,
+                       double dt0, long long maxiters, double dtmax, int cap, double* out,
+                       signed char* status, long long* stats, double* rec_t, double* rec_u,
+                       long long* rec_n, int nthreads) {
+  Model m = model_of(rhs_id);
+  if (m.D == 0 || N < 0 || cap < 1) return -1;
+  if (alg != ALG_TSIT5_ADAPTIVE && alg != ALG_ROS23) return -1;
+  if (rhs_id == RHS_CRN || (has_event(rhs_id) && alg != ALG_TSIT5_ADAPTIVE)) return -1;
+  if (precision < 0 || precision > 1) return -1;
+  Opts o{rhs_id, alg, m.D, m.P, m.Mw, 0.0, abstol, reltol, dt0, maxiters, nullptr, 0, 0, 0,
+         precision == 0, false, dtmax};
+  parallel_for(N, nthreads, [&](long long a, long long b) {
+    if (precision == 0)
+      solve_range<double>(o, 0, N, a, b, params, u0, tspan, out, status, stats, nullptr, cap,
+                          rec_t, rec_u, rec_n);
+    else
+      solve_range<float>(o, 0, N, a, b, params, u0, tspan, out, status, stats, nullptr, cap,
+                         rec_t, rec_u, rec_n);
   });
   return 0;
 }

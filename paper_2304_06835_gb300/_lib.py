@@ -35,7 +35,8 @@ class EnsOpts(ctypes.Structure):
         ("seed", ctypes.c_ulonglong), ("index_offset", ctypes.c_longlong),
         ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
         ("refill_min", ctypes.c_int), ("order", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-        ("dense", ctypes.c_int), ("dtmax", ctypes.c_double),
+        ("dense", ctypes.c_int), ("dtmax", ctypes.c_double), ("step_cap", ctypes.c_int),
+        ("step_t", ctypes.c_void_p), ("step_n", ctypes.c_void_p),
     ]
 
 

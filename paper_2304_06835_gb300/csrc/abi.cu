@@ -289,6 +289,9 @@ int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
   if (rhs_id == ENS_RHS_OREGO && o->alg == ENS_EM)
     return fail(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM, CRN)");
   if (!std::isfinite(o->dtmax)) return fail(ENS_EINVAL, "dtmax not finite");
+  if (o->step_cap < 0) return fail(ENS_EINVAL, "step_cap < 0");
+  if (o->step_cap > 0 && (o->n_save > 0 || is_fixed(o->alg)))
+    return fail(ENS_EINVAL, "step_cap needs an adaptive method and no save times");
   if (is_fixed(o->alg) && !(o->dt > 0) ) return fail(ENS_EINVAL, "fixed-step methods need dt > 0");
   if (is_fixed(o->alg) && !std::isfinite(o->dt)) return fail(ENS_EINVAL, "dt not finite");
   if (!is_fixed(o->alg)) {
@@ -354,6 +357,9 @@ void fill_args(SolveArgs* a, long long N, const void* params, const void* u0, co
   a->reltol_f = (float)o->reltol;
   a->dt0_f = (float)o->dt0;
   a->dtmax = o->dtmax > 0 ? o->dtmax : HUGE_VAL;
+  a->step_cap = o->step_cap;
+  a->step_t = o->step_t;
+  a->step_n = o->step_n;
   a->dtmax_f = o->dtmax > 0 ? (float)o->dtmax : HUGE_VALF;
   a->refill_min = o->refill_min > 0 ? (o->refill_min > 32 ? 32 : o->refill_min) : 4;
   a->dense = o->dense != 0 && o->n_save > 0;
@@ -596,6 +602,8 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
                    int* stats, void* stream) {
   int rc = validate(h, N, params, u0, tspan, o, out);
   if (rc) return rc;
+  if (o->step_cap > 0)  // its step_t / step_n are device arrays
+    return fail(ENS_EINVAL, "ens_solve_host does not take a step record (step_cap)");
   if (N == 0) return ENS_OK;
   std::lock_guard<std::mutex> lock(h->mu);
   const size_t es = elem_size(o->dtype);

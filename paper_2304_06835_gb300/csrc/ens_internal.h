@@ -22,6 +22,9 @@ struct SolveArgs {
   long long maxiters;
   int maxiters_i;   // the same cap as an int (validated <= 2e9)
   float abstol_f, reltol_f, dt0_f;  // FP32 copies (an FP32 solve never converts in its loop)
+  int step_cap;     // adaptive: store every accepted step (capacity per trajectory), 0: no
+  void* step_t;     // times of the stored steps (or null)
+  int* step_n;      // accepted steps + 1 (or null)
   double dtmax;     // adaptive: largest step (+inf when the caller set none)
   float dtmax_f;
   int refill_min;   // persistent schedule: refill a warp's idle lanes once this many are idle

@@ -237,7 +237,19 @@ struct Adaptive {
     while (si < a.n_save && Tol<T>::save(a, si) < t0) put_nan(a);
     if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
       while (si < a.n_save && Tol<T>::save(a, si) == t0 && t0 <= tf) put(a, u);
+    if (a.step_cap > 0) record(a, 0, t0);
     set_stop(a);
+  }
+
+  // every-step record: entry k = (t, u) after k accepted steps, k < step_cap
+  __device__ __forceinline__ void record(const SolveArgs& a, int k, T tk) {
+    if (k >= a.step_cap) return;
+    T* o = static_cast<T*>(a.out);
+#pragma unroll
+    for (int j = 0; j < D; ++j) o[out_idx(a.layout, idx, k, j, a.N, a.step_cap, D)] = u[j];
+    if (a.step_t)
+      static_cast<T*>(a.step_t)[a.layout == ENS_LAYOUT_SOA ? (long long)k * a.N + idx
+                                                             : idx * a.step_cap + k] = tk;
   }
 
   // dense output: every save time in (t_n, t_n + lim] of the accepted step from (u, fk)
@@ -377,13 +389,15 @@ struct Adaptive {
     t.snap(acc && last && !cut, stop);
     lq = acc ? fmaxf(0.5f * L, kLog2QoldInit) : lq;
     rejected += acc ? 0 : 1;
+    if (a.step_cap > 0 && acc) record(a, attempts - rejected, t.value());
     h = hs * T(fac);
     return false;
   }
 
   __device__ __forceinline__ void finish(const SolveArgs& a) {
-    if (a.n_save == 0) write_slot<RHS, T>(a, idx, 0, u);
+    if (a.n_save == 0 && a.step_cap == 0) write_slot<RHS, T>(a, idx, 0, u);
     while (si < a.n_save) put_nan(a);
+    if (a.step_n) a.step_n[idx] = attempts - rejected + 1;
     write_stats(a, idx, st, attempts - rejected, rejected,
                 fev0 + kFevPerAttempt * attempts + nev);
   }

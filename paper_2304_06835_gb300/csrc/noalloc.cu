@@ -89,6 +89,9 @@ int check_args(int rhs_id, long long N, const void* params, const void* u0, cons
   if ((rhs_id == ENS_RHS_HIRES || rhs_id == ENS_RHS_POLLU) && o->alg != ENS_ROS23)
     return set_last_error(ENS_EINVAL, "HIRES and POLLU take Rosenbrock23 only");
   if (!std::isfinite(o->dtmax)) return set_last_error(ENS_EINVAL, "dtmax not finite");
+  if (o->step_cap < 0) return set_last_error(ENS_EINVAL, "step_cap < 0");
+  if (o->step_cap > 0 && (o->n_save > 0 || fixed_alg(o->alg)))
+    return set_last_error(ENS_EINVAL, "step_cap needs an adaptive method and no save times");
   if (fixed_alg(o->alg) && !(o->dt > 0 && std::isfinite(o->dt)))
     return set_last_error(ENS_EINVAL, "fixed-step methods need a finite dt > 0");
   if (!fixed_alg(o->alg) && (!(o->abstol >= 1e-30) || !std::isfinite(o->abstol) ||
@@ -154,6 +157,9 @@ extern "C" int ens_solve_noalloc(int rhs_id, long long N, const void* params, co
   a.reltol_f = (float)o->reltol;
   a.dt0_f = (float)o->dt0;
   a.dtmax = o->dtmax > 0 ? o->dtmax : HUGE_VAL;
+  a.step_cap = o->step_cap;
+  a.step_t = o->step_t;
+  a.step_n = o->step_n;
   a.dtmax_f = o->dtmax > 0 ? (float)o->dtmax : HUGE_VALF;
   a.refill_min = o->refill_min > 0 ? o->refill_min : 4;
   a.dense = o->dense != 0 && o->n_save > 0;

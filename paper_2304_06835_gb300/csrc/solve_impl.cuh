@@ -53,8 +53,8 @@ template <class I, int TPT>
 cudaError_t launch_persistent(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
   if constexpr (TPT == 2 && PairOf<I>::ok) {
     // two trajectories per thread in lockstep on the paired FP32 instructions (no save
-    // times, no step cap)
-    if (a.n_save == 0 && !(a.dtmax_f < HUGE_VALF))
+    // times, no step record, no step cap)
+    if (a.n_save == 0 && a.step_cap == 0 && !(a.dtmax_f < HUGE_VALF))
       return launch_persistent_pair<typename PairOf<I>::rhs>(a, cfg, s);
   }
   int grid = 0;

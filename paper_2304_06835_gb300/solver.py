@@ -23,7 +23,7 @@ _NP_DT = {np.dtype(np.float32): _lib.F32, np.dtype(np.float64): _lib.F64}
 def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-6, reltol=1e-6,
               dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
               schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0,
-              dense=False, dtmax=0.0):
+              dense=False, dtmax=0.0, step_cap=0, step_t=None, step_n=None):
     o = _lib.EnsOpts()
     _lib.lib().ens_opts_default(ctypes.byref(o))
     o.alg = _lib.ALG[alg] if isinstance(alg, str) else int(alg)
@@ -49,6 +49,9 @@ def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-
     o.blocks_per_sm = int(blocks_per_sm)
     o.dense = 1 if dense else 0
     o.dtmax = float(dtmax)
+    o.step_cap = int(step_cap)
+    o.step_t = None if step_t is None else step_t.data_ptr()
+    o.step_n = None if step_n is None else step_n.data_ptr()
     return o, keep
 
 
@@ -126,6 +129,36 @@ class EnsembleSolver:
                                         ctypes.c_void_p(s)))
         del keep
         return out, status, stats
+
+    def solve_steps(self, params, u0, tspan, cap, alg="tsit5", *, layout="rowmajor",
+                    abstol=1e-6, reltol=1e-6, dt0=0.0, maxiters=1_000_000, dtmax=0.0,
+                    schedule="auto", block=0, tpt=0, want_stats=False, stream=None):
+        """Store every accepted step of an adaptive solve (the full solution): returns
+        (t, u, n, status, stats) with u [N, cap, D] (SoA: [cap, D, N]) holding the state after
+        k accepted steps (k = 0: u0), t [N, cap] (SoA [cap, N]) their times, n [N] = accepted
+        steps + 1 (may exceed cap: the first cap entries are kept).  Entries past n are not
+        written (left as allocated: NaN here)."""
+        if not (params.is_cuda and u0.is_cuda and tspan.is_cuda):
+            raise ValueError("params, u0 and tspan must be CUDA tensors")
+        N = params.shape[0] if layout == "rowmajor" else params.shape[-1]
+        dev = params.device
+        D = self.D
+        shp_u = (N, cap, D) if layout == "rowmajor" else (cap, D, N)
+        shp_t = (N, cap) if layout == "rowmajor" else (cap, N)
+        u = torch.full(shp_u, float("nan"), dtype=params.dtype, device=dev)
+        t = torch.full(shp_t, float("nan"), dtype=params.dtype, device=dev)
+        n = torch.empty(N, dtype=torch.int32, device=dev)
+        status = torch.empty(N, dtype=torch.int8, device=dev)
+        stats = torch.empty((3, N), dtype=torch.int32, device=dev) if want_stats else None
+        o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, 0.0, abstol, reltol, dt0,
+                            maxiters, None, 0, 0, schedule, block, tpt, 0, "auto", 0, False,
+                            dtmax, cap, t, n)
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+        _lib.check(_lib.lib().ens_solve(self._h, N, _ptr(params), _ptr(u0), _ptr(tspan),
+                                        ctypes.byref(o), _ptr(u), _ptr(status), _ptr(stats),
+                                        ctypes.c_void_p(s)))
+        del keep
+        return t, u, n, status, stats
 
     def autotune(self, params, u0, tspan, alg="tsit5", *, layout="rowmajor", out=None,
                  status=None, stats=None, stream=None, **kw):
