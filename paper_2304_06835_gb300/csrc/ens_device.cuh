@@ -686,7 +686,7 @@ struct LUDyn {
       }
       piv[c] = best;
       if (best != c) {
-#pragma unroll 1
+#pragma unroll 4
         for (int j = 0; j < D; ++j) {
           const T t = a[c][j];
           a[c][j] = a[best][j];
@@ -699,7 +699,8 @@ struct LUDyn {
       for (int r = c + 1; r < D; ++r) {
         const T l = a[r][c] * inv;
         a[r][c] = l;
-#pragma unroll 1
+        // independent across j: unrolled so several local-memory loads are in flight
+#pragma unroll 4
         for (int j = c + 1; j < D; ++j) a[r][j] = M<T>::fma(-l, a[c][j], a[r][j]);
       }
     }
@@ -720,12 +721,12 @@ struct LUDyn {
     }
 #pragma unroll 1
     for (int r = 0; r < D; ++r)
-#pragma unroll 1
+#pragma unroll 4
       for (int j = 0; j < r; ++j) y[r] = M<T>::fma(-a[r][j], y[j], y[r]);
 #pragma unroll 1
     for (int r = D - 1; r >= 0; --r) {
       T v = y[r];
-#pragma unroll 1
+#pragma unroll 4
       for (int j = r + 1; j < D; ++j) v = M<T>::fma(-a[r][j], x[j], v);
       x[r] = v * a[r][r];
     }

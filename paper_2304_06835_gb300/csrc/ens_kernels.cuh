@@ -160,6 +160,11 @@ struct Adaptive {
   static constexpr int kRowBytes = D * int(sizeof(T));
   static constexpr int kSaveK = kDense ? 16 / gcd_int(16, kRowBytes) : 1;
   static constexpr int kSaveWords = kSaveK * kRowBytes / 16;
+  // The every-step record runs on this variant too (it has no save times then) and stages
+  // kRecK entries: whole 16-byte words of states and of times.
+  static constexpr int kTimeK = 16 / int(sizeof(T));
+  static constexpr int kRecK =
+      kDense ? kSaveK * kTimeK / gcd_int(kSaveK, kTimeK) : 1;  // lcm of the two groups
   // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k
   static constexpr float kOrd = (METH != METH_ROS23) ? 5.f : 3.f;
   static constexpr int kInitOrder = (METH != METH_ROS23) ? 5 : 2;
@@ -174,8 +179,10 @@ struct Adaptive {
   int st;             // ENS_TRAJ_* (int, not char: no byte packing in the loop)
   int stop_is_save;
   long long idx;
-  T sbuf[kDense ? kSaveK * D : 1];  // staged saves (dense saving)
+  T sbuf[kDense ? kRecK * D : 1];   // staged saves (dense saving) or record entries
+  T tbuf[kDense ? kRecK : 1];       // staged record times
   bool stage;                       // this solve stages its saves (see kSaveK)
+  bool rstage;                      // this solve stages its record (see kRecK)
 
   // write save slot si (then ++si): directly, or through the 16-byte staging
   __device__ __forceinline__ void put(const SolveArgs& a, const T* v) {
@@ -234,6 +241,10 @@ struct Adaptive {
     si = 0;
     stage = kDense && a.layout == ENS_LAYOUT_ROWMAJOR && a.n_save % kSaveK == 0 &&
             (reinterpret_cast<unsigned long long>(a.out) & 15ull) == 0;
+    rstage = kDense && a.step_cap > 0 && a.layout == ENS_LAYOUT_ROWMAJOR &&
+             a.step_cap % kRecK == 0 && a.step_t != nullptr &&
+             ((reinterpret_cast<unsigned long long>(a.out) |
+               reinterpret_cast<unsigned long long>(a.step_t)) & 15ull) == 0;
     while (si < a.n_save && Tol<T>::save(a, si) < t0) put_nan(a);
     if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
       while (si < a.n_save && Tol<T>::save(a, si) == t0 && t0 <= tf) put(a, u);
@@ -244,6 +255,30 @@ struct Adaptive {
   // every-step record: entry k = (t, u) after k accepted steps, k < step_cap
   __device__ __forceinline__ void record(const SolveArgs& a, int k, T tk) {
     if (k >= a.step_cap) return;
+    if constexpr (kDense) {
+      if (rstage) {  // stage; a full group of kRecK entries goes out as 16-byte stores
+        const int q = k % kRecK;
+#pragma unroll
+        for (int g = 0; g < kRecK; ++g) {
+#pragma unroll
+          for (int j = 0; j < D; ++j) sbuf[g * D + j] = (g == q) ? u[j] : sbuf[g * D + j];
+          tbuf[g] = (g == q) ? tk : tbuf[g];
+        }
+        if (q == kRecK - 1) {
+          uint4* ou = reinterpret_cast<uint4*>(static_cast<T*>(a.out) +
+                                               (idx * a.step_cap + (k - q)) * (long long)D);
+          uint4* ot = reinterpret_cast<uint4*>(static_cast<T*>(a.step_t) + idx * a.step_cap +
+                                               (k - q));
+          const uint4* wu = reinterpret_cast<const uint4*>(sbuf);
+          const uint4* wt = reinterpret_cast<const uint4*>(tbuf);
+#pragma unroll
+          for (int w = 0; w < kRecK * kRowBytes / 16; ++w) ou[w] = wu[w];
+#pragma unroll
+          for (int w = 0; w < kRecK * int(sizeof(T)) / 16; ++w) ot[w] = wt[w];
+        }
+        return;
+      }
+    }
     T* o = static_cast<T*>(a.out);
 #pragma unroll
     for (int j = 0; j < D; ++j) o[out_idx(a.layout, idx, k, j, a.N, a.step_cap, D)] = u[j];
@@ -397,6 +432,22 @@ struct Adaptive {
   __device__ __forceinline__ void finish(const SolveArgs& a) {
     if (a.n_save == 0 && a.step_cap == 0) write_slot<RHS, T>(a, idx, 0, u);
     while (si < a.n_save) put_nan(a);
+    if constexpr (kDense) {
+      if (rstage) {  // the staged entries of an unfinished last group, with scalar stores
+        const int n = attempts - rejected + 1 < a.step_cap ? attempts - rejected + 1
+                                                           : a.step_cap;
+        const int k0 = n - n % kRecK;
+        T* o = static_cast<T*>(a.out);
+        T* ot = static_cast<T*>(a.step_t);
+#pragma unroll
+        for (int g = 0; g < kRecK; ++g)
+          if (k0 + g < n) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) o[(idx * a.step_cap + k0 + g) * D + j] = sbuf[g * D + j];
+            ot[idx * a.step_cap + k0 + g] = tbuf[g];
+          }
+      }
+    }
     if (a.step_n) a.step_n[idx] = attempts - rejected + 1;
     write_stats(a, idx, st, attempts - rejected, rejected,
                 fev0 + kFevPerAttempt * attempts + nev);
