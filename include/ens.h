@@ -175,8 +175,10 @@ int ens_destroy(ens_handle* h);
  *   out               : device array [N][S][D] (layout) written with the state at each save
  *                       time (S = n_save) or the final state (S = 1).  Save times outside
  *                       [t0, tf] of a trajectory, or after a failure, are written as NaN.
- *                       Adaptive methods step exactly onto save times; fixed-step methods
- *                       record after step ceil((s - t0)/dt - 1e-12).
+ *                       Adaptive methods step exactly onto save times (adaptive Tsit5 with
+ *                       opts->dense: the dense output at them, steps not cut); fixed-step
+ *                       methods record after step ceil((s - t0)/dt - 1e-12).  With
+ *                       opts->step_cap > 0: the every-step record instead (see ens_opts).
  *   status            : device int8 [N] (ENS_TRAJ_*) or NULL
  *   stats             : device int32 [3][N] = accepted steps, rejected steps, f evaluations,
  *                       or NULL

@@ -220,6 +220,9 @@ struct Adaptive {
     stop_thr = T(kStopEps) * M<T>::max(T(1), M<T>::abs(stop));
   }
 
+  // kRec = false compiles the every-step record out (for the paired kernel, which the host
+  // never launches with a record: dead code there still cost it a register and ~3 %)
+  template <bool kRec = true>
   __device__ __forceinline__ void init(long long i, const SolveArgs& a) {
     idx = i;
     T t0;
@@ -248,7 +251,7 @@ struct Adaptive {
     while (si < a.n_save && Tol<T>::save(a, si) < t0) put_nan(a);
     if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
       while (si < a.n_save && Tol<T>::save(a, si) == t0 && t0 <= tf) put(a, u);
-    if (a.step_cap > 0) record(a, 0, t0);
+    if (kRec && a.step_cap > 0) record(a, 0, t0);
     set_stop(a);
   }
 
@@ -429,10 +432,11 @@ struct Adaptive {
     return false;
   }
 
+  template <bool kRec = true>
   __device__ __forceinline__ void finish(const SolveArgs& a) {
-    if (a.n_save == 0 && a.step_cap == 0) write_slot<RHS, T>(a, idx, 0, u);
+    if (a.n_save == 0 && (!kRec || a.step_cap == 0)) write_slot<RHS, T>(a, idx, 0, u);
     while (si < a.n_save) put_nan(a);
-    if constexpr (kDense) {
+    if constexpr (kDense && kRec) {
       if (rstage) {  // the staged entries of an unfinished last group, with scalar stores
         const int n = attempts - rejected + 1 < a.step_cap ? attempts - rejected + 1
                                                            : a.step_cap;
@@ -448,7 +452,7 @@ struct Adaptive {
           }
       }
     }
-    if (a.step_n) a.step_n[idx] = attempts - rejected + 1;
+    if (kRec && a.step_n) a.step_n[idx] = attempts - rejected + 1;
     write_stats(a, idx, st, attempts - rejected, rejected,
                 fev0 + kFevPerAttempt * attempts + nev);
   }

@@ -142,7 +142,7 @@ struct AdaptivePair {
 
   __device__ __forceinline__ void init(int k, long long i, const SolveArgs& a) {
     Scalar s;
-    s.init(i, a);
+    s.template init<false>(i, a);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       set_lane(u[j], k, s.u[j]);
@@ -174,7 +174,7 @@ struct AdaptivePair {
     s.rejected = rejected[k];
     s.fev0 = fev0[k];
     s.nev = 0;  // the paired kernel serves models without events
-    s.finish(a);
+    s.template finish<false>(a);
   }
 
   // One attempt for each live lane; returns the mask of lanes that finished (arrived at tf

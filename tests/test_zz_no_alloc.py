@@ -75,6 +75,51 @@ def test_noalloc_matches_ens_solve_twice(case):
     del keep
 
 
+@pytest.mark.parametrize("case", ["crn_em_f32", "ball_events_f64", "lorenz_dense_f32",
+                                  "pollu_ros23_f64"])
+def test_noalloc_new_models_and_options(case):
+    """The newer models (8-noise CRN, the bouncing ball's events, POLLU's loop LU) and the
+    dense saving through the allocation-free path: equal to ens_solve, twice in a row."""
+    from paper_2304_06835_gb300 import EnsembleSolver, _lib, make_opts
+    S = 0
+    if case.startswith("crn"):
+        rhs, alg = "crn", "em"
+        P, U, T = workloads.crn_random(5000, seed=12, t1=50.0)
+        kw = dict(dt=0.1, seed=3)
+    elif case.startswith("ball"):
+        rhs, alg = "ball", "tsit5"
+        P, U, T = workloads.ball(5000, seed=13)
+        kw = dict(abstol=1e-8, reltol=1e-8, dtmax=1.0)
+    elif case.startswith("lorenz"):
+        rhs, alg = "lorenz", "tsit5"
+        P, U, T = workloads.lorenz_random(8000, seed=14, t1=2.0)
+        sv = np.linspace(0.0, 2.0, 17)
+        S = len(sv)
+        kw = dict(abstol=1e-6, reltol=1e-6, saveat=sv, dense=True)
+    else:
+        rhs, alg = "pollu", "ros23"
+        P, U, T = workloads.stiff("pollu", 512, seed=15, t1=5.0)
+        kw = dict(abstol=1e-6, reltol=1e-6)
+    dt = torch.float32 if case.endswith("f32") else torch.float64
+    Pd, Ud, Td = _dev(P.T, dt), _dev(U.T, dt), _dev(T.T, dt)
+    N, D = P.shape[0], U.shape[1]
+    solver = EnsembleSolver(rhs)
+    ref, ref_st, ref_stats = solver.solve(Pd, Ud, Td, alg=alg, layout="soa", want_stats=True,
+                                          **kw)
+    opts, keep = make_opts(alg, _lib.F32 if dt == torch.float32 else _lib.F64, "soa", **kw)
+    for call in range(2):
+        out = torch.full((S, D, N) if S else (D, N), float("nan"), dtype=dt, device="cuda")
+        st = torch.full((N,), -1, dtype=torch.int8, device="cuda")
+        stats = torch.full((3, N), -1, dtype=torch.int32, device="cuda")
+        _noalloc(_lib.RHS[rhs], Pd, Ud, Td, opts, out, st, stats)
+        torch.cuda.synchronize()
+        assert torch.equal(torch.nan_to_num(out), torch.nan_to_num(ref)), call
+        assert torch.equal(st, ref_st), call
+        assert torch.equal(stats, ref_stats), call
+    del keep
+    solver.close()
+
+
 def test_noalloc_first_call_accuracy_against_oracle():
     """The allocation-free path on its own, checked against the CPU oracle (FP64 fixed-step
     Tsit5 on the Lorenz sweep: state-vector error <= 1e-12)."""
