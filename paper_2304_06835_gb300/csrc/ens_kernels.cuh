@@ -220,8 +220,9 @@ struct Adaptive {
     stop_thr = T(kStopEps) * M<T>::max(T(1), M<T>::abs(stop));
   }
 
-  // kRec = false compiles the every-step record out (for the paired kernel, which the host
-  // never launches with a record: dead code there still cost it a register and ~3 %)
+  // kRec = false compiles the every-step record and the save times out (for the paired
+  // kernel, which the host launches with neither: dead code there still cost it a register
+  // and ~3 %)
   template <bool kRec = true>
   __device__ __forceinline__ void init(long long i, const SolveArgs& a) {
     idx = i;
@@ -248,11 +249,17 @@ struct Adaptive {
              a.step_cap % kRecK == 0 && a.step_t != nullptr &&
              ((reinterpret_cast<unsigned long long>(a.out) |
                reinterpret_cast<unsigned long long>(a.step_t)) & 15ull) == 0;
-    while (si < a.n_save && Tol<T>::save(a, si) < t0) put_nan(a);
-    if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
-      while (si < a.n_save && Tol<T>::save(a, si) == t0 && t0 <= tf) put(a, u);
-    if (kRec && a.step_cap > 0) record(a, 0, t0);
-    set_stop(a);
+    if constexpr (kRec) {
+      while (si < a.n_save && Tol<T>::save(a, si) < t0) put_nan(a);
+      if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
+        while (si < a.n_save && Tol<T>::save(a, si) == t0 && t0 <= tf) put(a, u);
+      if (a.step_cap > 0) record(a, 0, t0);
+      set_stop(a);
+    } else {  // no save times: the only stop is tf
+      stop_is_save = 0;
+      stop = tf;
+      stop_thr = T(kStopEps) * M<T>::max(T(1), M<T>::abs(tf));
+    }
   }
 
   // every-step record: entry k = (t, u) after k accepted steps, k < step_cap
@@ -434,8 +441,12 @@ struct Adaptive {
 
   template <bool kRec = true>
   __device__ __forceinline__ void finish(const SolveArgs& a) {
-    if (a.n_save == 0 && (!kRec || a.step_cap == 0)) write_slot<RHS, T>(a, idx, 0, u);
-    while (si < a.n_save) put_nan(a);
+    if (!kRec) {
+      write_slot<RHS, T>(a, idx, 0, u);
+    } else {
+      if (a.n_save == 0 && a.step_cap == 0) write_slot<RHS, T>(a, idx, 0, u);
+      while (si < a.n_save) put_nan(a);
+    }
     if constexpr (kDense && kRec) {
       if (rstage) {  // the staged entries of an unfinished last group, with scalar stores
         const int n = attempts - rejected + 1 < a.step_cap ? attempts - rejected + 1
