@@ -190,7 +190,10 @@ int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, co
               void* cuda_stream);
 
 /* Same as ens_solve with HOST arrays (pageable or pinned): copies inputs to the device,
- * solves, copies out/status/stats back and synchronises the stream before returning
+ * solves, copies out/status/stats back and synchronises the stream before returning.
+ * From 2^20 trajectories the work runs in 2 chunks whose copies, on a stream of the
+ * handle, overlap the other chunk's solve; the results equal one solve over all N (same
+ * launch shape, SDE streams by index)
  * (the paper's high-level path that passes the problem to the GPU and returns the result
  * to the CPU, Sec. 6.1). */
 int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u0,

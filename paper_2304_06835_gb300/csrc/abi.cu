@@ -231,9 +231,11 @@ struct ens_handle {
   unsigned short* bucket;
   unsigned int* hist;
   long long order_cap;
-  // staging for ens_solve_host
+  // staging for ens_solve_host, and its copy stream and chunk events
   void* stage;
   size_t stage_bytes;
+  cudaStream_t copy_stream;
+  cudaEvent_t ev_in[8], ev_done[8];
   // discrete adjoint: one segment of stage inputs, and checkpoints when the caller gives none
   void* adj_seg;
   size_t adj_seg_bytes;
@@ -498,6 +500,7 @@ int ens_create(ens_handle** out, int rhs_id, int D, int P) {
   h->P = P;
   h->stage = nullptr;
   h->stage_bytes = 0;
+  h->copy_stream = nullptr;
   h->order = nullptr;
   h->bucket = nullptr;
   h->hist = nullptr;
@@ -529,17 +532,21 @@ int ens_destroy(ens_handle* h) {
   if (h->stage) cudaFree(h->stage);
   if (h->adj_seg) cudaFree(h->adj_seg);
   if (h->adj_ckpt) cudaFree(h->adj_ckpt);
+  if (h->copy_stream) {
+    for (int c = 0; c < 8; ++c) {
+      if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
+      if (h->ev_done[c]) cudaEventDestroy(h->ev_done[c]);
+    }
+    cudaStreamDestroy(h->copy_stream);
+  }
   delete h;
   return ENS_OK;
 }
 
-int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, const void* tspan,
-              const ens_opts* o, void* out, signed char* status, int* stats, void* stream) {
-  int rc = validate(h, N, params, u0, tspan, o, out);
-  if (rc) return rc;
-  if (N == 0) return ENS_OK;
-  cudaStream_t s = (cudaStream_t)stream;
-  LaunchCfg cfg = resolve_cfg(h, N, o);
+// the solve of N validated trajectories with a resolved launch shape (stream-ordered on s)
+int solve_with_cfg(ens_handle* h, long long N, const void* params, const void* u0,
+                   const void* tspan, const ens_opts* o, void* out, signed char* status,
+                   int* stats, cudaStream_t s, const LaunchCfg& cfg) {
   SolveArgs a;
   fill_args(&a, N, params, u0, tspan, o, out, status, stats, h->queue);
   SolveScratch sc{h->queue, nullptr, nullptr, h->hist};
@@ -563,6 +570,15 @@ int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, co
   if (!sup) return fail(ENS_ENOTSUP, "algorithm not available for this model");
   if (e != cudaSuccess) return cuda_fail(e, "solve launch");
   return ENS_OK;
+}
+
+int ens_solve(ens_handle* h, long long N, const void* params, const void* u0, const void* tspan,
+              const ens_opts* o, void* out, signed char* status, int* stats, void* stream) {
+  int rc = validate(h, N, params, u0, tspan, o, out);
+  if (rc) return rc;
+  if (N == 0) return ENS_OK;
+  return solve_with_cfg(h, N, params, u0, tspan, o, out, status, stats, (cudaStream_t)stream,
+                        resolve_cfg(h, N, o));
 }
 
 int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
@@ -608,8 +624,9 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
   std::lock_guard<std::mutex> lock(h->mu);
   const size_t es = elem_size(o->dtype);
   const int S = o->n_save > 0 ? o->n_save : 1;
-  const size_t b_p = es * N * h->P, b_u = es * N * h->D, b_t = es * N * 2;
-  const size_t b_o = es * N * (size_t)S * h->D, b_s = status ? N : 0;
+  const int P = h->P, D = h->D;
+  const size_t b_p = es * N * P, b_u = es * N * D, b_t = es * N * 2;
+  const size_t b_o = es * N * (size_t)S * D, b_s = status ? N : 0;
   const size_t b_st = stats ? sizeof(int) * 3 * N : 0;
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t total = up(b_p) + up(b_u) + up(b_t) + up(b_o) + up(b_s) + up(b_st);
@@ -621,6 +638,14 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
     if (e != cudaSuccess) return fail(ENS_ENOMEM, "staging allocation failed");
     h->stage_bytes = total;
   }
+  if (!h->copy_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    for (int c = 0; c < 8 && e == cudaSuccess; ++c) {
+      e = cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_done[c], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy stream");
+  }
   char* base = (char*)h->stage;
   char* dp = base;
   char* du = dp + up(b_p);
@@ -628,17 +653,69 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
   char* dout = dt + up(b_t);
   char* dst = dout + up(b_o);
   char* dstats = dst + up(b_s);
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(dp, params, b_p, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(du, u0, b_u, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tspan, b_t, cudaMemcpyHostToDevice, s);
+  cudaStream_t s = (cudaStream_t)stream, cs = h->copy_stream;
+  // Chunks pipeline the copies with the solve: chunk c + 1 arrives (copy stream) while chunk
+  // c is solved (caller's stream), and chunk c returns while c + 1 is solved.  Each chunk's
+  // inputs and outputs are compact blocks of the staging arrays; its solve uses the launch
+  // shape of the whole ensemble and index_offset + its first index, so results (SDE streams
+  // included) are those of one solve over all N.
+  const LaunchCfg cfg = resolve_cfg(h, N, o);
+  // measured (Lorenz, 2^20, end to end): 1 chunk 722.6, 2 chunks 730.5, 4 chunks 602.9 M
+  // trajectories/s -- each chunk's solve drains its own tail, which more chunks repeat
+  const int C = N >= (1LL << 20) ? 2 : 1;
+  const bool soa = o->layout == ENS_LAYOUT_SOA;
+  auto cp = [&](void* dst_, size_t dpitch, const void* src_, size_t spitch, size_t width,
+                size_t height, cudaMemcpyKind kind) {
+    if (height == 1 || (dpitch == width && spitch == width))
+      return cudaMemcpyAsync(dst_, src_, width * height, kind, cs);
+    return cudaMemcpy2DAsync(dst_, dpitch, src_, spitch, width, height, kind, cs);
+  };
+  cudaError_t e = cudaEventRecord(h->ev_done[0], s);  // the copies wait for prior work on s
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->ev_done[0], 0);
+  long long i0 = 0;
+  for (int c = 0; c < C && e == cudaSuccess; ++c) {  // all inputs, chunk by chunk
+    const long long i1 = N * (c + 1) / C, n = i1 - i0;
+    const size_t rowp = soa ? es * n : es * n * P, rowu = soa ? es * n : es * n * D;
+    const size_t rowt = soa ? es * n : es * n * 2;
+    e = cp(dp + es * i0 * P, rowp, (const char*)params + (soa ? es * i0 : es * i0 * P),
+           soa ? es * N : rowp, rowp, soa ? P : 1, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cp(du + es * i0 * D, rowu, (const char*)u0 + (soa ? es * i0 : es * i0 * D),
+             soa ? es * N : rowu, rowu, soa ? D : 1, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cp(dt + es * i0 * 2, rowt, (const char*)tspan + (soa ? es * i0 : es * i0 * 2),
+             soa ? es * N : rowt, rowt, soa ? 2 : 1, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[c], cs);
+    i0 = i1;
+  }
   if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-  rc = ens_solve(h, N, dp, du, dt, o, dout, status ? (signed char*)dst : nullptr,
-                 stats ? (int*)dstats : nullptr, stream);
-  if (rc) return rc;
-  e = cudaMemcpyAsync(out, dout, b_o, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, dst, b_s, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && stats) e = cudaMemcpyAsync(stats, dstats, b_st, cudaMemcpyDeviceToHost, s);
+  i0 = 0;
+  for (int c = 0; c < C; ++c) {  // solves on s; each chunk's outputs go back on cs
+    const long long i1 = N * (c + 1) / C, n = i1 - i0;
+    ens_opts oc = *o;
+    oc.index_offset = o->index_offset + i0;
+    e = cudaStreamWaitEvent(s, h->ev_in[c], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "chunk order");
+    rc = solve_with_cfg(h, n, dp + es * i0 * P, du + es * i0 * D, dt + es * i0 * 2, &oc,
+                        dout + es * i0 * S * D, status ? (signed char*)dst + i0 : nullptr,
+                        stats ? (int*)dstats + 3 * i0 : nullptr, s, cfg);
+    if (rc) return rc;
+    e = cudaEventRecord(h->ev_done[c], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->ev_done[c], 0);
+    const size_t rowo = soa ? es * n : es * n * S * D;
+    if (e == cudaSuccess)
+      e = cp((char*)out + (soa ? es * i0 : es * i0 * S * D), soa ? es * N : rowo,
+             dout + es * i0 * S * D, rowo, rowo, soa ? (size_t)S * D : 1,
+             cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && status)
+      e = cudaMemcpyAsync(status + i0, dst + i0, n, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess && stats)
+      e = cp(stats + i0, sizeof(int) * N, (int*)dstats + 3 * i0, sizeof(int) * n,
+             sizeof(int) * n, 3, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    i0 = i1;
+  }
+  e = cudaStreamSynchronize(cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
   return ENS_OK;
