@@ -475,6 +475,13 @@ class StepsRunner(SolveRunner):
             step_n=self.rec_n)
         self.c = ctypes
         self.lib = _lib
+        if not args.no_autotune and args.block == 0 and args.tpt == 0 and args.bps == 0:
+            # record solves have their own cache entry (they run another kernel)
+            b, t_, f, ms = self.solver.autotune(
+                self.Pd, self.Ud, self.Td, alg=w["alg"], layout="rowmajor", out=self.rec_u,
+                status=self.status, stats=self.stats, abstol=w["tol"], reltol=w["tol"],
+                step_cap=cap, step_t=self.rec_t, step_n=self.rec_n)
+            self.tuned = {"block": b, "tpt": t_, "blocks_per_sm": f, "tuned_ms": round(ms, 4)}
 
     def step(self):
         import torch

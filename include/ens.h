@@ -206,7 +206,8 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
  * trajectories per thread in {1, 2} and resident blocks per SM in {all that fit, 3/4, 1/2 of
  * that}; a nonzero opts->block / opts->tpt / opts->blocks_per_sm pins that value --
  * timing each (one warm-up, best of two), and records the fastest in a process-wide cache
- * keyed by (model, algorithm, dtype, layout, floor(log2 N), saveat or not, SM count).  Later
+ * keyed by (model, algorithm, dtype, layout, floor(log2 N), output kind -- final state, save
+ * times, dense save times or step record --, SM count).  Later
  * ens_solve / ens_batch_create calls with block = tpt = blocks_per_sm = 0 use the cached
  * shape.  Returns it in *block / *tpt / *blocks_per_sm (> 0 a cap, 0 all that fit, < 0 that
  * many quarters of the blocks that fit) and its time in *best_ms.  Synchronises the stream. */

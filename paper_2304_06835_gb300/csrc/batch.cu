@@ -32,7 +32,10 @@ std::mutex g_tuned_mu;
 TuneKey tune_key(int rhs_id, long long N, const ens_opts* o, int sms) {
   int nbits = 0;
   while (nbits < 62 && (1LL << (nbits + 1)) <= N) ++nbits;  // size class floor(log2 N)
-  return TuneKey(rhs_id, o->alg, o->dtype, o->layout, nbits, o->n_save > 0 ? 1 : 0, sms);
+  // output kind: final state, save times (cut steps or dense), every-step record -- they run
+  // different kernels (the paired one only for the final state)
+  const int kind = o->step_cap > 0 ? 3 : o->n_save > 0 ? (o->dense ? 2 : 1) : 0;
+  return TuneKey(rhs_id, o->alg, o->dtype, o->layout, nbits, kind, sms);
 }
 
 LaunchCfg default_launch(const ens_opts* o, int sms) {
