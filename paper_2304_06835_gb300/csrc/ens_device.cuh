@@ -461,30 +461,12 @@ __host__ __device__ constexpr double ts5_dense(int i, int q) {
   return r[i][q];
 }
 
-template <class RHS, class T>
-__device__ __forceinline__ void tsit5_dense(const T* u, T h, const T* k1, const T* kmid,
-                                            const T* k7, T theta, T* out) {
-  constexpr int D = RHS::D;
-  T bw[7];
-#pragma unroll
-  for (int i = 0; i < 7; ++i)
-    bw[i] = theta * M<T>::fma(theta, M<T>::fma(theta, M<T>::fma(theta, T(ts5_dense(i, 3)),
-                                                                 T(ts5_dense(i, 2))),
-                                               T(ts5_dense(i, 1))),
-                              T(ts5_dense(i, 0)));
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    T s = bw[0] * k1[j];
-#pragma unroll
-    for (int i = 1; i < 6; ++i) s = M<T>::fma(bw[i], kmid[(i - 1) * D + j], s);
-    s = M<T>::fma(bw[6], k7[j], s);
-    out[j] = M<T>::fma(h, s, u[j]);
-  }
-}
-
+// The same interpolant as a polynomial in theta, u(theta) = u_n + sum_{q=1..4} theta^q c_q
+// with c_q = h sum_i r_iq k_i (dense_coeffs once per step, dense_poly per point): the form
+// dense saving and event location evaluate.
+//
 // Events (Sec. 6.5): a condition g(u, p, t) crossing zero from above inside an accepted step
-// triggers the model's affect.  The step's dense output is written as a polynomial in theta,
-// u(theta) = u_n + sum_{q=1..4} theta^q c_q with c_q = h sum_i r_iq k_i; the condition is
+// triggers the model's affect.  The condition is
 // checked at theta = j / kEventPoints (u_n and u_{n+1} themselves at the ends); the first
 // interval with g > 0 at its left end and g <= 0 at its right end is narrowed by the Illinois
 // method (regula falsi that halves the value kept at an end surviving two iterations in a

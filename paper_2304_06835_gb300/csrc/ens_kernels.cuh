@@ -130,6 +130,21 @@ struct Tol<float> {
   static __device__ __forceinline__ float save(const SolveArgs& a, int s) { return a.saveat_f[s]; }
 };
 
+// Save times in shared memory, copied at block start by the kernels that run the adaptive
+// integrators: lanes read them at their own save index, and a read of the kernel's parameter
+// array at an index that differs across the warp is serialised over the distinct addresses.
+template <class T>
+__device__ __forceinline__ T* save_times_smem() {
+  __shared__ T s[ENS_MAX_SAVE];
+  return s;
+}
+template <class T>
+__device__ __forceinline__ void load_save_times(const SolveArgs& a) {
+  T* s = save_times_smem<T>();
+  for (int k = threadIdx.x; k < a.n_save; k += blockDim.x) s[k] = Tol<T>::save(a, k);
+  __syncthreads();
+}
+
 template <class T>
 __device__ __forceinline__ T rms_scaled(const T* x, const T* sc, int D) {
   T s = T(0);
@@ -169,6 +184,8 @@ struct Adaptive {
   static constexpr float kOrd = (METH != METH_ROS23) ? 5.f : 3.f;
   static constexpr int kInitOrder = (METH != METH_ROS23) ? 5 : 2;
   static constexpr int kFevPerAttempt = (METH != METH_ROS23) ? 6 : 2;
+  using Real = T;
+  static constexpr bool kSmemSaves = true;  // reads save times from save_times_smem
 
   T u[D], fk[D], p[P];
   Clock<T> t;
@@ -215,8 +232,8 @@ struct Adaptive {
   }
 
   __device__ __forceinline__ void set_stop(const SolveArgs& a) {
-    stop_is_save = !kDense && si < a.n_save && Tol<T>::save(a, si) < tf;
-    stop = stop_is_save ? Tol<T>::save(a, si) : tf;
+    stop_is_save = !kDense && si < a.n_save && save_times_smem<T>()[si] < tf;
+    stop = stop_is_save ? save_times_smem<T>()[si] : tf;
     stop_thr = T(kStopEps) * M<T>::max(T(1), M<T>::abs(stop));
   }
 
@@ -250,9 +267,9 @@ struct Adaptive {
              ((reinterpret_cast<unsigned long long>(a.out) |
                reinterpret_cast<unsigned long long>(a.step_t)) & 15ull) == 0;
     if constexpr (kRec) {
-      while (si < a.n_save && Tol<T>::save(a, si) < t0) put_nan(a);
+      while (si < a.n_save && save_times_smem<T>()[si] < t0) put_nan(a);
       if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
-        while (si < a.n_save && Tol<T>::save(a, si) == t0 && t0 <= tf) put(a, u);
+        while (si < a.n_save && save_times_smem<T>()[si] == t0 && t0 <= tf) put(a, u);
       if (a.step_cap > 0) record(a, 0, t0);
       set_stop(a);
     } else {  // no save times: the only stop is tf
@@ -297,13 +314,20 @@ struct Adaptive {
                                                              : idx * a.step_cap + k] = tk;
   }
 
-  // dense output: every save time in (t_n, t_n + lim] of the accepted step from (u, fk)
-  // (lim = hs, or the event's offset when an event ends the step early), theta =
-  // (s - t_n) / hs on the compensated clock; a save at the end of the last step is u_{n+1}
-  __device__ __forceinline__ void dense_saves(const SolveArgs& a, T hs, T lim, bool last,
-                                              const T* kmid, const T* fnew, const T* unew) {
+  // dense output: every save time in (t_n, t_n + lim] of the accepted step (lim = hs, or the
+  // event's offset when an event ends the step early), theta = (s - t_n) / hs on the
+  // compensated clock; a save at the end of the last step is u_{n+1}.  The interpolant is
+  // evaluated from its coefficients in theta (dense_coeffs, formed once per step and only by
+  // a lane with a save in it): 4 FMA per component and save instead of the 7 weights.
+  __device__ __forceinline__ bool dense_pending(const SolveArgs& a, T lim, bool last) const {
+    if (si >= a.n_save) return false;
+    const T sv = save_times_smem<T>()[si];
+    return sv <= tf && ((last && sv == stop) || t.remaining(sv) <= lim);
+  }
+  __device__ __forceinline__ void dense_saves(const SolveArgs& a, const T (*cq)[D], T hs, T lim,
+                                              bool last, const T* unew) {
     while (si < a.n_save) {
-      const T sv = Tol<T>::save(a, si);
+      const T sv = save_times_smem<T>()[si];
       if (sv > tf) break;
       const T rs = t.remaining(sv);
       const bool at_end = last && sv == stop;
@@ -312,7 +336,7 @@ struct Adaptive {
         put(a, unew);
       } else {
         T w[D];
-        tsit5_dense<RHS, T>(u, hs, fk, kmid, fnew, rs / hs, w);
+        dense_poly<RHS, T>(u, cq, M<T>::fast_div(rs, hs), w);
         put(a, w);
       }
     }
@@ -358,7 +382,7 @@ struct Adaptive {
         t.set(stop);
         if (!stop_is_save) {  // tf (dense: every save left within the arrival threshold)
           while (si < a.n_save &&
-                 (Tol<T>::save(a, si) == tf || (kDense && Tol<T>::save(a, si) <= tf)))
+                 (save_times_smem<T>()[si] == tf || (kDense && save_times_smem<T>()[si] <= tf)))
             put(a, u);
           return true;
         }
@@ -410,7 +434,7 @@ struct Adaptive {
         th_ev = find_event<RHS, T>(u, unew, p, tnow, hs, cq);
         if (th_ev > T(0)) {  // the event: saves up to it from this step, state, affect, f
           const bool cut = th_ev < T(1);
-          if (kDense) dense_saves(a, hs, cut ? th_ev * hs : hs, last && !cut, kmid, fnew, unew);
+          if (kDense) dense_saves(a, cq, hs, cut ? th_ev * hs : hs, last && !cut, unew);
           if (cut) dense_poly<RHS, T>(u, cq, th_ev, unew);
           RHS::event_affect(unew, p, tnow + th_ev * hs);
           RHS::f(unew, p, tnow + th_ev * hs, fnew);
@@ -418,7 +442,13 @@ struct Adaptive {
         }
       }
     }
-    if (kDense && acc && !(th_ev > T(0))) dense_saves(a, hs, hs, last, kmid, fnew, unew);
+    if constexpr (kDense) {
+      if (acc && !(th_ev > T(0)) && dense_pending(a, hs, last)) {
+        T cq[4][D];
+        dense_coeffs<RHS, T>(hs, fk, kmid, fnew, cq);
+        dense_saves(a, cq, hs, hs, last, unew);
+      }
+    }
     const bool cut = th_ev > T(0) && th_ev < T(1);  // an event ended the step early
     // PI control: accept fac = eta q_n^{-beta1} q_{n-1}^{beta2} in [0.2, 10];
     // reject fac = max(0.2, eta q_n^{-1/k}).  Exponentials in log2 form (q guarded at 1e-10).
@@ -487,6 +517,8 @@ enum { METH_FIX_TSIT5 = 0, METH_FIX_RK4 = 1, METH_FIX_EM = 2 };
 
 template <class RHS, class T, int METH>
 struct Fixed {
+  using Real = T;
+  static constexpr bool kSmemSaves = false;
   static constexpr int D = RHS::D, P = RHS::P;
   // Euler-Maruyama step k uses normals k*NW .. k*NW + NW - 1 of the trajectory's stream: one
   // Philox call serves kSub steps (NW <= per_call) or one step takes kCalls calls.
@@ -639,6 +671,8 @@ __device__ __forceinline__ long long queue_next(unsigned long long* q) {
 
 template <class I>
 __global__ void k_direct(const SolveArgs a) {
+  if constexpr (I::kSmemSaves)
+    if (a.n_save > 0) load_save_times<typename I::Real>(a);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
     I s;
@@ -691,6 +725,8 @@ __global__ void k_cost_scatter(long long N, long long chunk, const unsigned shor
 // pass instead of one pass per finishing lane.
 template <class I, int TPT>
 __global__ void k_persistent(const SolveArgs a) {
+  if constexpr (I::kSmemSaves)
+    if (a.n_save > 0) load_save_times<typename I::Real>(a);
   I s[TPT];
   bool act[TPT];
 #pragma unroll
