@@ -608,8 +608,9 @@ class AdjointRunner:
 
 
 class BatchRunner:
-    """One step = one ens_batch_run of the uneven batch (a single CUDA-graph launch that runs
-    the three sub-problems as concurrent persistent kernels, launch shapes autotuned)."""
+    """One step = one ens_batch_run of the uneven batch: a single CUDA-graph launch that runs
+    the three sub-problems' persistent kernels, launch shapes autotuned, concurrently or one
+    after another (the plan times both graphs at creation and keeps the faster)."""
 
     def __init__(self, args, w, rank, dev):
         import torch
@@ -650,6 +651,10 @@ class BatchRunner:
         serial.close()
         res["items_alone_ms"] = [round(i["tuned_ms"], 4) for i in self.plan.info()]
         res["launch_shapes"] = [(i["block"], i["tpt"]) for i in self.plan.info()]
+        inf = self.plan.info()[0]
+        res["graph_form"] = "serial" if inf["serial"] else "concurrent"
+        res["plan_timed_ms"] = {"concurrent": round(inf["graph_ms_concurrent"], 4),
+                                "serial": round(inf["graph_ms_serial"], 4)}
         return res
 
     def work(self):

@@ -227,6 +227,10 @@ int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
  *   ENS_BATCH_AUTOTUNE  run ens_autotune's search on every item during creation (the items'
  *                       outputs are written by the trial solves)
  *   ENS_BATCH_SERIAL    no concurrency: the items run one after another on the caller stream
+ * With GRAPH and AUTOTUNE (and more than one item) the plan also captures the serial order,
+ * times both graphs at creation (one warm-up and three timed launches each, writing the
+ * items' outputs) and keeps the faster: concurrent persistent kernels, each sized for the
+ * whole GPU, can crowd one another.
  * Each item's opts are those of ens_solve; saveat is copied at creation.  The plan keeps the
  * item pointers: ens_batch_run re-solves whatever the input arrays hold at that time. */
 #define ENS_BATCH_MAX_ITEMS 16
@@ -250,6 +254,9 @@ typedef struct {
   float tuned_ms;           /* autotuned solve time of the item alone (0 if not tuned) */
   int launch_position;      /* position in the launch order (-1: empty item) */
   int graph;                /* 1 if the plan runs as a CUDA graph */
+  int serial;               /* 1 if the items run one after another */
+  float graph_ms_concurrent;  /* GRAPH|AUTOTUNE: measured time of the concurrent graph, */
+  float graph_ms_serial;      /* and of the serial one (0: not measured) */
 } ens_batch_item_info;
 
 typedef struct ens_batch ens_batch;

@@ -52,7 +52,8 @@ class BatchItemInfo(ctypes.Structure):
     _fields_ = [
         ("schedule", ctypes.c_int), ("block", ctypes.c_int), ("tpt", ctypes.c_int),
         ("blocks_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_float),
-        ("launch_position", ctypes.c_int), ("graph", ctypes.c_int),
+        ("launch_position", ctypes.c_int), ("graph", ctypes.c_int), ("serial", ctypes.c_int),
+        ("graph_ms_concurrent", ctypes.c_float), ("graph_ms_serial", ctypes.c_float),
     ]
 
 

@@ -161,6 +161,7 @@ struct ens_batch {
   };
   std::vector<Item> items;
   std::vector<int> order;  // launch order (longest measured first when tuned)
+  float graph_ms[2];       // measured graph times: concurrent, serial (0: not measured)
   void* scratch;
   cudaStream_t cap;
   cudaEvent_t fork;
@@ -214,6 +215,48 @@ void batch_free(ens_batch* b) {
 int batch_fail(ens_batch* b, int code, const char* msg) {
   batch_free(b);
   return set_last_error(code, msg);
+}
+
+// capture the plan's launches (concurrent or serial by b->flags) into an instantiated graph
+int capture_graph(ens_batch* b, cudaGraph_t* g, cudaGraphExec_t* x) {
+  *g = nullptr;
+  *x = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return set_last_error(ENS_ECUDA, cudaGetErrorString(e));
+  bool sup = true;
+  cudaError_t e1 = enqueue_batch(b, b->cap, &sup);
+  e = cudaStreamEndCapture(b->cap, g);
+  if (!sup) return set_last_error(ENS_ENOTSUP, "algorithm not available for this model");
+  if (e1 != cudaSuccess) return set_last_error(ENS_ECUDA, cudaGetErrorString(e1));
+  if (e != cudaSuccess) return set_last_error(ENS_ECUDA, cudaGetErrorString(e));
+  e = cudaGraphInstantiate(x, *g, 0);
+  if (e != cudaSuccess) return set_last_error(ENS_ECUDA, cudaGetErrorString(e));
+  return ENS_OK;
+}
+
+// one warm-up launch, then the median of three timed launches (ms); synchronises s
+int time_graph(cudaGraphExec_t x, cudaStream_t s, float* ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return set_last_error(ENS_ECUDA, "event create");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_last_error(ENS_ECUDA, "event create");
+  }
+  float t[3] = {0.f, 0.f, 0.f};
+  cudaError_t e = cudaGraphLaunch(x, s);
+  for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(x, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t[r], e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return set_last_error(ENS_ECUDA, cudaGetErrorString(e));
+  std::sort(t, t + 3);
+  *ms = t[1];
+  return ENS_OK;
 }
 
 }  // namespace
@@ -303,21 +346,32 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
   b->order.erase(std::remove_if(b->order.begin(), b->order.end(),
                                 [&](int i) { return b->items[i].a.N == 0; }),
                  b->order.end());
+  b->graph_ms[0] = b->graph_ms[1] = 0.f;
   if (flags & ENS_BATCH_GRAPH) {
     // wait for the tuning runs (and any caller work on s) before capturing on a private stream
     if (cudaStreamSynchronize(s) != cudaSuccess) return batch_fail(b, ENS_ECUDA, "sync");
-    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e));
-    bool sup = true;
-    cudaError_t e1 = enqueue_batch(b, b->cap, &sup);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(b->cap, &g);
-    b->graph = g;
-    if (!sup) return batch_fail(b, ENS_ENOTSUP, "algorithm not available for this model");
-    if (e1 != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e1));
-    if (e != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-    if (e != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e));
+    int rc = capture_graph(b, &b->graph, &b->exec);
+    if (rc) return batch_fail(b, rc, ens_last_error());
+    if ((flags & ENS_BATCH_AUTOTUNE) && !(flags & ENS_BATCH_SERIAL) && b->order.size() > 1) {
+      // concurrent kernels can share the SMs well or crowd each other (a persistent grid
+      // sized for the whole GPU leaves little room beside it): time the concurrent graph and
+      // the serial one and keep the faster
+      b->flags |= ENS_BATCH_SERIAL;
+      cudaGraph_t g2 = nullptr;
+      cudaGraphExec_t x2 = nullptr;
+      rc = capture_graph(b, &g2, &x2);
+      if (!rc) rc = time_graph(b->exec, s, &b->graph_ms[0]);
+      if (!rc) rc = time_graph(x2, s, &b->graph_ms[1]);
+      if (!rc && b->graph_ms[1] < b->graph_ms[0]) {
+        std::swap(g2, b->graph);
+        std::swap(x2, b->exec);
+      } else {
+        b->flags &= ~ENS_BATCH_SERIAL;
+      }
+      if (x2) cudaGraphExecDestroy(x2);
+      if (g2) cudaGraphDestroy(g2);
+      if (rc) return batch_fail(b, rc, ens_last_error());
+    }
   }
   *out = b;
   return ENS_OK;
@@ -352,6 +406,9 @@ int ens_batch_info(const ens_batch* b, int item, ens_batch_item_info* info) {
     if (b->order[k] == item) pos = (int)k;
   info->launch_position = pos;
   info->graph = b->exec != nullptr;
+  info->serial = (b->flags & ENS_BATCH_SERIAL) != 0;
+  info->graph_ms_concurrent = b->graph_ms[0];
+  info->graph_ms_serial = b->graph_ms[1];
   return ENS_OK;
 }
 

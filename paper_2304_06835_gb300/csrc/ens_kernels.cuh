@@ -158,13 +158,20 @@ __device__ __forceinline__ T rms_scaled(const T* x, const T* sc, int D) {
 // ------------------------------------------------------------------------------------------
 // Adaptive integrators: Tsit5 with PI control (Sec. 3.1) and Rosenbrock23 (Sec. 3.2.1).
 // METH_TSIT5_DENSE is Tsit5 whose save times take the dense output of the step that covers
-// them instead of cutting the steps (the steps are those of the solve without save times).
-enum { METH_TSIT5 = 0, METH_ROS23 = 1, METH_TSIT5_DENSE = 2 };
+// them instead of cutting the steps (the steps are those of the solve without save times);
+// METH_TSIT5_RECORD is Tsit5 that records every accepted step.  Each variant carries only
+// its own output code: the record's staging in the dense kernel cost it 12 registers and
+// ~10 %.
+enum { METH_TSIT5 = 0, METH_ROS23 = 1, METH_TSIT5_DENSE = 2, METH_TSIT5_RECORD = 3 };
 
 template <class RHS, class T, int METH>
 struct Adaptive {
   static constexpr int D = RHS::D, P = RHS::P;
   static constexpr bool kDense = METH == METH_TSIT5_DENSE;
+  static constexpr bool kRecord = METH == METH_TSIT5_RECORD;
+  // the every-step record: staged (kRecord) or with scalar stores (Rosenbrock23); the plain
+  // Tsit5 variant never records (Tsit5 records run on METH_TSIT5_RECORD)
+  static constexpr bool kHasRecord = kRecord || METH == METH_ROS23;
   static constexpr bool kEvent = RHS::has_event && METH != METH_ROS23;
   static constexpr bool kKeepStages = kDense || kEvent;  // stages 2..6 outlive the step
   static constexpr int kMaxTpt = RHS::stiff_only ? 1 : 4;  // trajectories per thread
@@ -173,13 +180,14 @@ struct Adaptive {
   // and n_save is a multiple of kSaveK: the lanes of a warp save at different times, so
   // scalar stores would reach L2 as 4- or 8-byte pieces of separate sectors.
   static constexpr int kRowBytes = D * int(sizeof(T));
-  static constexpr int kSaveK = kDense ? 16 / gcd_int(16, kRowBytes) : 1;
+  static constexpr int kRowK = 16 / gcd_int(16, kRowBytes);  // rows in whole 16-byte words
+  static constexpr int kSaveK = kDense ? kRowK : 1;
   static constexpr int kSaveWords = kSaveK * kRowBytes / 16;
-  // The every-step record runs on this variant too (it has no save times then) and stages
-  // kRecK entries: whole 16-byte words of states and of times.
+  // The every-step record (kRecord) stages kRecK entries: whole 16-byte words of states and
+  // of times.
   static constexpr int kTimeK = 16 / int(sizeof(T));
   static constexpr int kRecK =
-      kDense ? kSaveK * kTimeK / gcd_int(kSaveK, kTimeK) : 1;  // lcm of the two groups
+      kRecord ? kRowK * kTimeK / gcd_int(kRowK, kTimeK) : 1;  // lcm of the two groups
   // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k
   static constexpr float kOrd = (METH != METH_ROS23) ? 5.f : 3.f;
   static constexpr int kInitOrder = (METH != METH_ROS23) ? 5 : 2;
@@ -196,8 +204,8 @@ struct Adaptive {
   int st;             // ENS_TRAJ_* (int, not char: no byte packing in the loop)
   int stop_is_save;
   long long idx;
-  T sbuf[kDense ? kRecK * D : 1];   // staged saves (dense saving) or record entries
-  T tbuf[kDense ? kRecK : 1];       // staged record times
+  T sbuf[kDense ? kSaveK * D : kRecord ? kRecK * D : 1];  // staged saves or record entries
+  T tbuf[kRecord ? kRecK : 1];                            // staged record times
   bool stage;                       // this solve stages its saves (see kSaveK)
   bool rstage;                      // this solve stages its record (see kRecK)
 
@@ -262,7 +270,7 @@ struct Adaptive {
     si = 0;
     stage = kDense && a.layout == ENS_LAYOUT_ROWMAJOR && a.n_save % kSaveK == 0 &&
             (reinterpret_cast<unsigned long long>(a.out) & 15ull) == 0;
-    rstage = kDense && a.step_cap > 0 && a.layout == ENS_LAYOUT_ROWMAJOR &&
+    rstage = kRecord && a.step_cap > 0 && a.layout == ENS_LAYOUT_ROWMAJOR &&
              a.step_cap % kRecK == 0 && a.step_t != nullptr &&
              ((reinterpret_cast<unsigned long long>(a.out) |
                reinterpret_cast<unsigned long long>(a.step_t)) & 15ull) == 0;
@@ -270,7 +278,7 @@ struct Adaptive {
       while (si < a.n_save && save_times_smem<T>()[si] < t0) put_nan(a);
       if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
         while (si < a.n_save && save_times_smem<T>()[si] == t0 && t0 <= tf) put(a, u);
-      if (a.step_cap > 0) record(a, 0, t0);
+      if (kHasRecord && a.step_cap > 0) record(a, 0, t0);
       set_stop(a);
     } else {  // no save times: the only stop is tf
       stop_is_save = 0;
@@ -282,7 +290,7 @@ struct Adaptive {
   // every-step record: entry k = (t, u) after k accepted steps, k < step_cap
   __device__ __forceinline__ void record(const SolveArgs& a, int k, T tk) {
     if (k >= a.step_cap) return;
-    if constexpr (kDense) {
+    if constexpr (kRecord) {
       if (rstage) {  // stage; a full group of kRecK entries goes out as 16-byte stores
         const int q = k % kRecK;
 #pragma unroll
@@ -464,7 +472,8 @@ struct Adaptive {
     t.snap(acc && last && !cut, stop);
     lq = acc ? fmaxf(0.5f * L, kLog2QoldInit) : lq;
     rejected += acc ? 0 : 1;
-    if (a.step_cap > 0 && acc) record(a, attempts - rejected, t.value());
+    if constexpr (kHasRecord)
+      if (a.step_cap > 0 && acc) record(a, attempts - rejected, t.value());
     h = hs * T(fac);
     return false;
   }
@@ -477,7 +486,7 @@ struct Adaptive {
       if (a.n_save == 0 && a.step_cap == 0) write_slot<RHS, T>(a, idx, 0, u);
       while (si < a.n_save) put_nan(a);
     }
-    if constexpr (kDense && kRec) {
+    if constexpr (kRecord && kRec) {
       if (rstage) {  // the staged entries of an unfinished last group, with scalar stores
         const int n = attempts - rejected + 1 < a.step_cap ? attempts - rejected + 1
                                                            : a.step_cap;

@@ -125,7 +125,9 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
     if (alg == ENS_ROS23) return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps, cs);
   } else if constexpr (RHS::has_event) {  // events are located on the adaptive Tsit5 interpolant
     if (alg == ENS_TSIT5_ADAPTIVE) {
-      if (a && (a->dense || a->step_cap > 0))
+      if (a && a->step_cap > 0)
+        return run_integ<Adaptive<RHS, T, METH_TSIT5_RECORD>>(a, cfg, s, attr, bps, cs);
+      if (a && a->dense)
         return run_integ<Adaptive<RHS, T, METH_TSIT5_DENSE>>(a, cfg, s, attr, bps, cs);
       return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps, cs);
     }
@@ -135,8 +137,10 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
     switch (alg) {
       case ENS_TSIT5_FIXED:
         return run_integ<Fixed<RHS, T, METH_FIX_TSIT5>>(a, cfg, s, attr, bps, cs);
-      case ENS_TSIT5_ADAPTIVE:  // dense saving and the every-step record share a variant
-        if (a && (a->dense || a->step_cap > 0))
+      case ENS_TSIT5_ADAPTIVE:  // dense saving and the every-step record: variants of their own
+        if (a && a->step_cap > 0)
+          return run_integ<Adaptive<RHS, T, METH_TSIT5_RECORD>>(a, cfg, s, attr, bps, cs);
+        if (a && a->dense)
           return run_integ<Adaptive<RHS, T, METH_TSIT5_DENSE>>(a, cfg, s, attr, bps, cs);
         return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps, cs);
       case ENS_RK4: return run_integ<Fixed<RHS, T, METH_FIX_RK4>>(a, cfg, s, attr, bps, cs);

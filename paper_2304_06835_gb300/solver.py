@@ -379,7 +379,9 @@ class EnsembleBatch:
             res.append({"schedule": inf.schedule, "block": inf.block, "tpt": inf.tpt,
                         "blocks_per_sm": inf.blocks_per_sm,
                         "tuned_ms": inf.tuned_ms, "launch_position": inf.launch_position,
-                        "graph": bool(inf.graph)})
+                        "graph": bool(inf.graph), "serial": bool(inf.serial),
+                        "graph_ms_concurrent": inf.graph_ms_concurrent,
+                        "graph_ms_serial": inf.graph_ms_serial})
         return res
 
     def close(self):

@@ -82,6 +82,13 @@ def test_batch_equals_separate_solves(mode):
         assert all(i["tuned_ms"] > 0 and i["block"] in (64, 128, 256, 512) for i in info)
         pos = [i["launch_position"] for i in info]
         assert sorted(pos) == [0, 1, 2]
+        # both graph forms were timed; the plan kept the faster
+        c, s_ = info[0]["graph_ms_concurrent"], info[0]["graph_ms_serial"]
+        assert c > 0 and s_ > 0
+        assert all(i["serial"] == (s_ < c) for i in info)
+    else:
+        assert all(i["graph_ms_concurrent"] == 0 and i["graph_ms_serial"] == 0 for i in info)
+        assert all(i["serial"] == mode.get("serial", False) for i in info)
     b.close()
 
 

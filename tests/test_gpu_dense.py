@@ -9,6 +9,7 @@ saving on the same inputs, through the C ABI.
 * Save times before t0 / after tf are NaN, at t0 / tf the initial / final state.
 * FP32: every save within 10x tolerance of a tol-1e-12 FP64 reference.
 * Rosenbrock23 ignores the flag (bit-identical to the stepped saving).
+* Dense saves equal across the direct and persistent schedules, bit for bit.
 """
 import numpy as np
 import pytest
@@ -131,3 +132,31 @@ def test_staged_vector_stores_equal_scalar_stores(lor, dt):
     np.testing.assert_array_equal(np.nan_to_num(a), np.nan_to_num(b))
     np.testing.assert_array_equal(s1.cpu().numpy(), s2.cpu().numpy())
     assert s1.cpu().numpy()[3] != 0
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64])
+def test_dense_saves_equal_across_schedules(lor, dt):
+    """The direct schedule and the persistent one (one and two trajectories per thread, a
+    refilled warp) give the same dense saves bit for bit, in both layouts, with NaN slots,
+    zero-length spans, a save at tf and a failing trajectory; n_save is not a multiple of the
+    staging group, so the rows go out with scalar stores."""
+    P, U, T = workloads.lorenz_random(5000 + 3, seed=36, t1=10.0)
+    T[::11, 1] = 0.0          # zero-length spans
+    T[5::13, 0] = 0.5         # saves before t0 are NaN
+    P[3, 0] = np.nan          # a failing trajectory
+    sv = np.concatenate([[-0.5, 0.0], np.linspace(0.05, 10.0, 200), [12.0]])
+    kw = dict(abstol=1e-6, reltol=1e-6, saveat=sv, dense=True)
+    d = lambda a: dev(a, dt)
+    ref, rst, _ = lor.solve(d(P), d(U), d(T), alg="tsit5", schedule="direct", **kw)
+    r = host(ref)
+    assert int(rst.cpu().numpy()[3]) != 0 and np.isnan(r[3, 3:]).all()
+    for tpt in (1, 2):
+        out, st, _ = lor.solve(d(P), d(U), d(T), alg="tsit5", schedule="persistent", tpt=tpt, **kw)
+        o = host(out)
+        np.testing.assert_array_equal(np.isnan(o), np.isnan(r))
+        np.testing.assert_array_equal(np.nan_to_num(o), np.nan_to_num(r))
+        np.testing.assert_array_equal(st.cpu().numpy(), rst.cpu().numpy())
+    t = lambda a: d(np.ascontiguousarray(a.T))
+    o2, _, _ = lor.solve(t(P), t(U), t(T), alg="tsit5", layout="soa", schedule="persistent", **kw)
+    o2 = np.transpose(host(o2), (2, 0, 1))
+    np.testing.assert_array_equal(np.nan_to_num(o2), np.nan_to_num(r))
