@@ -133,6 +133,9 @@ struct Tol<float> {
 // Save times in shared memory, copied at block start by the kernels that run the adaptive
 // integrators: lanes read them at their own save index, and a read of the kernel's parameter
 // array at an index that differs across the warp is serialised over the distinct addresses.
+// Dynamic shared memory of the kernels: the dense saves' 16-byte staging (Adaptive::put).
+extern __shared__ __align__(16) unsigned char ens_dyn_smem[];
+
 template <class T>
 __device__ __forceinline__ T* save_times_smem() {
   __shared__ T s[ENS_MAX_SAVE];
@@ -174,15 +177,22 @@ struct Adaptive {
   static constexpr bool kHasRecord = kRecord || METH == METH_ROS23;
   static constexpr bool kEvent = RHS::has_event && METH != METH_ROS23;
   static constexpr bool kKeepStages = kDense || kEvent;  // stages 2..6 outlive the step
-  static constexpr int kMaxTpt = RHS::stiff_only ? 1 : 4;  // trajectories per thread
-  // Dense saving stages kSaveK saves (a whole number of 16-byte words) per lane in registers
-  // and writes them with vector stores when the output is trajectory-major, 16-byte aligned
-  // and n_save is a multiple of kSaveK: the lanes of a warp save at different times, so
-  // scalar stores would reach L2 as 4- or 8-byte pieces of separate sectors.
+  // trajectories per thread (dense saving: one, its staging slot is the thread's)
+  static constexpr int kMaxTpt = (RHS::stiff_only || METH == METH_TSIT5_DENSE) ? 1 : 4;
+  // Dense saving stages kSaveK saves (a whole number of 16-byte words) per lane in shared
+  // memory and writes them with vector stores when the output is trajectory-major, 16-byte
+  // aligned and n_save is a multiple of kSaveK: the lanes of a warp save at different times,
+  // so scalar stores would reach L2 as 4- or 8-byte pieces of separate sectors.  (Staged in
+  // registers the group stayed live through the whole solve: 12 registers and ~8 %.)
   static constexpr int kRowBytes = D * int(sizeof(T));
   static constexpr int kRowK = 16 / gcd_int(16, kRowBytes);  // rows in whole 16-byte words
   static constexpr int kSaveK = kDense ? kRowK : 1;
   static constexpr int kSaveWords = kSaveK * kRowBytes / 16;
+  // staged values per thread (the thread's slot: kSaveWords 16-byte words; a runtime stride
+  // between slots kept a dozen addresses live), and the largest block, which keeps the
+  // staging and the save times under the default 48 KB per block
+  static constexpr int kStageElems = kDense ? kSaveK * D : 0;
+  static constexpr int kMaxBlock = kDense ? 512 : 1024;
   // The every-step record (kRecord) stages kRecK entries: whole 16-byte words of states and
   // of times.
   static constexpr int kTimeK = 16 / int(sizeof(T));
@@ -203,9 +213,10 @@ struct Adaptive {
   int attempts, rejected, si, fev0, nev;  // nev: events handled (one extra f each)
   int st;             // ENS_TRAJ_* (int, not char: no byte packing in the loop)
   int stop_is_save;
+  T nsv;  // dense: the next save time (+inf past the last)
   long long idx;
-  T sbuf[kDense ? kSaveK * D : kRecord ? kRecK * D : 1];  // staged saves or record entries
-  T tbuf[kRecord ? kRecK : 1];                            // staged record times
+  T sbuf[kRecord ? kRecK * D : 1];  // staged record entries
+  T tbuf[kRecord ? kRecK : 1];      // staged record times
   bool stage;                       // this solve stages its saves (see kSaveK)
   bool rstage;                      // this solve stages its record (see kRecK)
 
@@ -214,14 +225,13 @@ struct Adaptive {
     if constexpr (kDense) {
       if (stage) {
         const int k = si % kSaveK;
+        T* sl = reinterpret_cast<T*>(ens_dyn_smem) + threadIdx.x * kStageElems;
 #pragma unroll
-        for (int q = 0; q < kSaveK; ++q)
-#pragma unroll
-          for (int j = 0; j < D; ++j) sbuf[q * D + j] = (q == k) ? v[j] : sbuf[q * D + j];
+        for (int j = 0; j < D; ++j) sl[k * D + j] = v[j];
         if (k == kSaveK - 1) {  // a full group: slots si - k .. si
           uint4* o = reinterpret_cast<uint4*>(static_cast<T*>(a.out) +
                                               (idx * a.n_save + (si - k)) * (long long)D);
-          const uint4* w = reinterpret_cast<const uint4*>(sbuf);
+          const uint4* w = reinterpret_cast<const uint4*>(sl);
 #pragma unroll
           for (int q = 0; q < kSaveWords; ++q) o[q] = w[q];
         }
@@ -278,6 +288,7 @@ struct Adaptive {
       while (si < a.n_save && save_times_smem<T>()[si] < t0) put_nan(a);
       if (kDense)  // save times at t0 take u0; the steps then run to tf uncut
         while (si < a.n_save && save_times_smem<T>()[si] == t0 && t0 <= tf) put(a, u);
+      if (kDense) next_save(a);
       if (kHasRecord && a.step_cap > 0) record(a, 0, t0);
       set_stop(a);
     } else {  // no save times: the only stop is tf
@@ -328,9 +339,10 @@ struct Adaptive {
   // evaluated from its coefficients in theta (dense_coeffs, formed once per step and only by
   // a lane with a save in it): 4 FMA per component and save instead of the 7 weights.
   __device__ __forceinline__ bool dense_pending(const SolveArgs& a, T lim, bool last) const {
-    if (si >= a.n_save) return false;
-    const T sv = save_times_smem<T>()[si];
-    return sv <= tf && ((last && sv == stop) || t.remaining(sv) <= lim);
+    return nsv <= tf && ((last && nsv == stop) || t.remaining(nsv) <= lim);
+  }
+  __device__ __forceinline__ void next_save(const SolveArgs& a) {
+    nsv = si < a.n_save ? save_times_smem<T>()[si] : T(INFINITY);
   }
   __device__ __forceinline__ void dense_saves(const SolveArgs& a, const T (*cq)[D], T hs, T lim,
                                               bool last, const T* unew) {
@@ -348,6 +360,7 @@ struct Adaptive {
         put(a, w);
       }
     }
+    next_save(a);
   }
 
   // Hairer-Norsett-Wanner I, II.4: starting step size (a heuristic: the FP32 solve forms it
@@ -528,6 +541,7 @@ template <class RHS, class T, int METH>
 struct Fixed {
   using Real = T;
   static constexpr bool kSmemSaves = false;
+  static constexpr int kStageElems = 0, kMaxBlock = 1024;
   static constexpr int D = RHS::D, P = RHS::P;
   // Euler-Maruyama step k uses normals k*NW .. k*NW + NW - 1 of the trajectory's stream: one
   // Philox call serves kSub steps (NW <= per_call) or one step takes kCalls calls.

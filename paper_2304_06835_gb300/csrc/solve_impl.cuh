@@ -20,11 +20,18 @@ struct PairOf<Adaptive<RHS, float, METH_TSIT5>> {
   typedef RHS rhs;
 };
 
+// dynamic shared memory of a launch (the dense saves' staging)
+template <class I>
+size_t dyn_smem(int block) {
+  return (size_t)block * I::kStageElems * sizeof(typename I::Real);
+}
+
 template <class I, int TPT>
 cudaError_t persistent_grid(const LaunchCfg& cfg, int* grid) {
+  if (cfg.block > I::kMaxBlock) return cudaErrorLaunchOutOfResources;
   int bps = 0;
-  cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent<I, TPT>, cfg.block, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent<I, TPT>,
+                                                                cfg.block, dyn_smem<I>(cfg.block));
   if (e != cudaSuccess) return e;
   if (bps == 0) return cudaErrorLaunchOutOfResources;  // the block does not fit an SM
   if (cfg.bps > 0) bps = std::min(bps, cfg.bps);
@@ -63,7 +70,7 @@ cudaError_t launch_persistent(const SolveArgs& a, const LaunchCfg& cfg, cudaStre
   // never more resident threads than trajectory slots needed
   const long long need = (a.N + (long long)TPT * cfg.block - 1) / ((long long)TPT * cfg.block);
   grid = (int)std::min<long long>(grid, std::max<long long>(1, need));
-  k_persistent<I, TPT><<<grid, cfg.block, 0, s>>>(a);
+  k_persistent<I, TPT><<<grid, cfg.block, dyn_smem<I>(cfg.block), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -72,7 +79,8 @@ cudaError_t launch_integ(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t 
   if (cfg.schedule == ENS_SCHED_DIRECT) {
     const long long blocks = (a.N + cfg.block - 1) / cfg.block;
     const int grid = (int)std::min<long long>(blocks, 1LL << 30);
-    k_direct<I><<<grid, cfg.block, 0, s>>>(a);
+    if (cfg.block > I::kMaxBlock) return cudaErrorLaunchOutOfResources;
+    k_direct<I><<<grid, cfg.block, dyn_smem<I>(cfg.block), s>>>(a);
     return cudaGetLastError();
   }
   if constexpr (I::kMaxTpt == 1) {  // one trajectory per thread whatever was asked
@@ -99,7 +107,12 @@ cudaError_t attrs_integ(const LaunchCfg& cfg, cudaFuncAttributes* attr, int* bps
   }
   cudaError_t e = cudaFuncGetAttributes(attr, fn);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, cfg.block, 0);
+  if (cfg.block > I::kMaxBlock) {  // does not fit
+    *bps = 0;
+    return cudaSuccess;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, cfg.block,
+                                                       dyn_smem<I>(cfg.block));
 }
 
 template <class I>
