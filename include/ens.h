@@ -130,8 +130,11 @@ typedef struct {
   unsigned long long seed;   /* SDE: Philox4x32-10 key */
   long long index_offset;    /* SDE: trajectory i draws from stream index_offset + i */
   int schedule;           /* ENS_SCHED_* */
-  int block;              /* threads per block; 0 = tuned / default */
-  int tpt;                /* trajectories per thread (1, 2 or 4); 0 = tuned / default */
+  int block;              /* threads per block; 0 = tuned / default.  Adaptive Tsit5 with
+                             dense = 1 or a step record stages its output in shared memory
+                             and takes at most 512 (more: ENS_ECUDA, too many resources). */
+  int tpt;                /* trajectories per thread (1, 2 or 4); 0 = tuned / default.  The
+                             Rosenbrock23, dense-output and step-record kernels run one. */
   int refill_min;         /* persistent schedule: a warp refills its idle lanes once at least
                              this many are idle (1..32; 0 = default).  Batching refills trades
                              idle lanes for fewer divergent refill passes. */

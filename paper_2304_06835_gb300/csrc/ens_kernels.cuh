@@ -177,8 +177,10 @@ struct Adaptive {
   static constexpr bool kHasRecord = kRecord || METH == METH_ROS23;
   static constexpr bool kEvent = RHS::has_event && METH != METH_ROS23;
   static constexpr bool kKeepStages = kDense || kEvent;  // stages 2..6 outlive the step
-  // trajectories per thread (dense saving: one, its staging slot is the thread's)
-  static constexpr int kMaxTpt = (RHS::stiff_only || METH == METH_TSIT5_DENSE) ? 1 : 4;
+  // trajectories per thread (dense saving and the record: one, the staging slot is the
+  // thread's)
+  static constexpr int kMaxTpt =
+      (RHS::stiff_only || METH == METH_TSIT5_DENSE || METH == METH_TSIT5_RECORD) ? 1 : 4;
   // Dense saving stages kSaveK saves (a whole number of 16-byte words) per lane in shared
   // memory and writes them with vector stores when the output is trajectory-major, 16-byte
   // aligned and n_save is a multiple of kSaveK: the lanes of a warp save at different times,
@@ -188,16 +190,16 @@ struct Adaptive {
   static constexpr int kRowK = 16 / gcd_int(16, kRowBytes);  // rows in whole 16-byte words
   static constexpr int kSaveK = kDense ? kRowK : 1;
   static constexpr int kSaveWords = kSaveK * kRowBytes / 16;
-  // staged values per thread (the thread's slot: kSaveWords 16-byte words; a runtime stride
-  // between slots kept a dozen addresses live), and the largest block, which keeps the
-  // staging and the save times under the default 48 KB per block
-  static constexpr int kStageElems = kDense ? kSaveK * D : 0;
-  static constexpr int kMaxBlock = kDense ? 512 : 1024;
-  // The every-step record (kRecord) stages kRecK entries: whole 16-byte words of states and
-  // of times.
+  // The every-step record (kRecord) stages kRecK entries in shared memory likewise: whole
+  // 16-byte words of states and of times.
   static constexpr int kTimeK = 16 / int(sizeof(T));
   static constexpr int kRecK =
       kRecord ? kRowK * kTimeK / gcd_int(kRowK, kTimeK) : 1;  // lcm of the two groups
+  // staged values per thread (the thread's slot: whole 16-byte words of saves, or of record
+  // states then times; a runtime stride between slots kept a dozen addresses live), and the
+  // largest block, which keeps the staging and the save times under the default 48 KB
+  static constexpr int kStageElems = kDense ? kSaveK * D : kRecord ? kRecK * (D + 1) : 0;
+  static constexpr int kMaxBlock = (kDense || kRecord) ? 512 : 1024;
   // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k
   static constexpr float kOrd = (METH != METH_ROS23) ? 5.f : 3.f;
   static constexpr int kInitOrder = (METH != METH_ROS23) ? 5 : 2;
@@ -215,8 +217,6 @@ struct Adaptive {
   int stop_is_save;
   T nsv;  // dense: the next save time (+inf past the last)
   long long idx;
-  T sbuf[kRecord ? kRecK * D : 1];  // staged record entries
-  T tbuf[kRecord ? kRecK : 1];      // staged record times
   bool stage;                       // this solve stages its saves (see kSaveK)
   bool rstage;                      // this solve stages its record (see kRecK)
 
@@ -304,12 +304,11 @@ struct Adaptive {
     if constexpr (kRecord) {
       if (rstage) {  // stage; a full group of kRecK entries goes out as 16-byte stores
         const int q = k % kRecK;
+        T* sbuf = reinterpret_cast<T*>(ens_dyn_smem) + threadIdx.x * kStageElems;  // states
+        T* tbuf = sbuf + kRecK * D;                                                 // times
 #pragma unroll
-        for (int g = 0; g < kRecK; ++g) {
-#pragma unroll
-          for (int j = 0; j < D; ++j) sbuf[g * D + j] = (g == q) ? u[j] : sbuf[g * D + j];
-          tbuf[g] = (g == q) ? tk : tbuf[g];
-        }
+        for (int j = 0; j < D; ++j) sbuf[q * D + j] = u[j];
+        tbuf[q] = tk;
         if (q == kRecK - 1) {
           uint4* ou = reinterpret_cast<uint4*>(static_cast<T*>(a.out) +
                                                (idx * a.step_cap + (k - q)) * (long long)D);
@@ -506,6 +505,8 @@ struct Adaptive {
         const int k0 = n - n % kRecK;
         T* o = static_cast<T*>(a.out);
         T* ot = static_cast<T*>(a.step_t);
+        const T* sbuf = reinterpret_cast<const T*>(ens_dyn_smem) + threadIdx.x * kStageElems;
+        const T* tbuf = sbuf + kRecK * D;
 #pragma unroll
         for (int g = 0; g < kRecK; ++g)
           if (k0 + g < n) {

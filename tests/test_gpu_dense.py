@@ -160,3 +160,20 @@ def test_dense_saves_equal_across_schedules(lor, dt):
     o2, _, _ = lor.solve(t(P), t(U), t(T), alg="tsit5", layout="soa", schedule="persistent", **kw)
     o2 = np.transpose(host(o2), (2, 0, 1))
     np.testing.assert_array_equal(np.nan_to_num(o2), np.nan_to_num(r))
+
+
+def test_dense_and_record_take_at_most_512_threads_per_block(lor):
+    """The staged kernels keep their shared memory under the default 48 KB with at most 512
+    threads per block: a larger block is refused before launch (no kernel runs), 512 works."""
+    from paper_2304_06835_gb300 import EnsError
+    P, U, T = workloads.lorenz_random(1000, seed=37, t1=1.0)
+    kw = dict(abstol=1e-6, reltol=1e-6, saveat=SV, dense=True)
+    for sched in ("direct", "persistent"):
+        with pytest.raises(EnsError):
+            lor.solve(dev(P), dev(U), dev(T), alg="tsit5", schedule=sched, block=1024, **kw)
+        a, _, _ = lor.solve(dev(P), dev(U), dev(T), alg="tsit5", schedule=sched, block=512, **kw)
+        b, _, _ = lor.solve(dev(P), dev(U), dev(T), alg="tsit5", schedule=sched, block=128, **kw)
+        np.testing.assert_array_equal(host(a), host(b))
+    cap = 16
+    with pytest.raises(EnsError):
+        lor.solve_steps(dev(P), dev(U), dev(T), cap, abstol=1e-6, reltol=1e-6, block=1024)
