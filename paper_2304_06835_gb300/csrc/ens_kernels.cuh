@@ -200,6 +200,12 @@ struct Adaptive {
   // largest block, which keeps the staging and the save times under the default 48 KB
   static constexpr int kStageElems = kDense ? kSaveK * D : kRecord ? kRecK * (D + 1) : 0;
   static constexpr int kMaxBlock = (kDense || kRecord) ? 512 : 1024;
+  // Slot stride: an odd number of 16-byte words, so the 16-byte reads of 8 consecutive lanes
+  // cover all 32 banks once (an even count, e.g. the record's 64 bytes, put every lane's
+  // 4-byte stores into two banks: 16-way conflicts).
+  static constexpr int kSlotBytes0 = kStageElems * int(sizeof(T));
+  static constexpr int kSlotBytes =
+      (kSlotBytes0 > 0 && (kSlotBytes0 / 16) % 2 == 0) ? kSlotBytes0 + 16 : kSlotBytes0;
   // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k
   static constexpr float kOrd = (METH != METH_ROS23) ? 5.f : 3.f;
   static constexpr int kInitOrder = (METH != METH_ROS23) ? 5 : 2;
@@ -225,7 +231,7 @@ struct Adaptive {
     if constexpr (kDense) {
       if (stage) {
         const int k = si % kSaveK;
-        T* sl = reinterpret_cast<T*>(ens_dyn_smem) + threadIdx.x * kStageElems;
+        T* sl = reinterpret_cast<T*>(ens_dyn_smem + threadIdx.x * kSlotBytes);
 #pragma unroll
         for (int j = 0; j < D; ++j) sl[k * D + j] = v[j];
         if (k == kSaveK - 1) {  // a full group: slots si - k .. si
@@ -304,8 +310,8 @@ struct Adaptive {
     if constexpr (kRecord) {
       if (rstage) {  // stage; a full group of kRecK entries goes out as 16-byte stores
         const int q = k % kRecK;
-        T* sbuf = reinterpret_cast<T*>(ens_dyn_smem) + threadIdx.x * kStageElems;  // states
-        T* tbuf = sbuf + kRecK * D;                                                 // times
+        T* sbuf = reinterpret_cast<T*>(ens_dyn_smem + threadIdx.x * kSlotBytes);  // states
+        T* tbuf = sbuf + kRecK * D;                                                // times
 #pragma unroll
         for (int j = 0; j < D; ++j) sbuf[q * D + j] = u[j];
         tbuf[q] = tk;
@@ -505,7 +511,7 @@ struct Adaptive {
         const int k0 = n - n % kRecK;
         T* o = static_cast<T*>(a.out);
         T* ot = static_cast<T*>(a.step_t);
-        const T* sbuf = reinterpret_cast<const T*>(ens_dyn_smem) + threadIdx.x * kStageElems;
+        const T* sbuf = reinterpret_cast<const T*>(ens_dyn_smem + threadIdx.x * kSlotBytes);
         const T* tbuf = sbuf + kRecK * D;
 #pragma unroll
         for (int g = 0; g < kRecK; ++g)
@@ -542,7 +548,7 @@ template <class RHS, class T, int METH>
 struct Fixed {
   using Real = T;
   static constexpr bool kSmemSaves = false;
-  static constexpr int kStageElems = 0, kMaxBlock = 1024;
+  static constexpr int kStageElems = 0, kSlotBytes = 0, kMaxBlock = 1024;
   static constexpr int D = RHS::D, P = RHS::P;
   // Euler-Maruyama step k uses normals k*NW .. k*NW + NW - 1 of the trajectory's stream: one
   // Philox call serves kSub steps (NW <= per_call) or one step takes kCalls calls.

@@ -23,7 +23,7 @@ struct PairOf<Adaptive<RHS, float, METH_TSIT5>> {
 // dynamic shared memory of a launch (the dense saves' staging)
 template <class I>
 size_t dyn_smem(int block) {
-  return (size_t)block * I::kStageElems * sizeof(typename I::Real);
+  return (size_t)block * I::kSlotBytes;
 }
 
 template <class I, int TPT>
