@@ -298,6 +298,9 @@ def oracle_rate(w, budget_s=12.0):
     return n2 * reps / el, sample, nt
 
 
+REF_BUDGET_S = 120.0
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
@@ -308,15 +311,18 @@ def run_reference(args, w, rank, world):
         P, U, T = inputs_for(w)
     G = workloads.adjoint_targets(w["N"], seed=5) if w["kind"] == "adjoint" else None
     nt = oracle.default_threads()
-    n = min(w["N"], 64 * nt)
-    while True:  # size each step to ~3 s of CPU work
+    # the whole --warmup + --steps run takes about REF_BUDGET_S of CPU work: each step is a
+    # sample of the workload sized to its share (at most 3 s)
+    per_step = min(3.0, REF_BUDGET_S / max(1, args.warmup + args.steps))
+    n = min(w["N"], nt)
+    while True:
         t0 = time.perf_counter()
         _oracle_run(w, P, U, T, n, nt, G)
         dt = time.perf_counter() - t0
-        if dt > 0.3 or n == w["N"]:
+        if dt > 0.1 * per_step or n == w["N"]:
             break
         n = min(w["N"], n * 4)
-    n = max(1, min(w["N"], int(n * 3.0 / max(dt, 1e-3))))
+    n = max(1, min(w["N"], int(n * per_step / max(dt, 1e-6))))
     for _ in range(args.warmup):
         _oracle_run(w, P, U, T, n, nt, G)
     t0 = time.perf_counter()
