@@ -66,6 +66,11 @@ LaunchCfg resolve_launch(int rhs_id, long long N, const ens_opts* o, int num_sms
   return c;
 }
 
+bool one_per_thread(const ens_opts* o) {
+  return o->alg == ENS_ROS23 ||
+         (o->alg == ENS_TSIT5_ADAPTIVE && ((o->dense && o->n_save > 0) || o->step_cap > 0));
+}
+
 // Time every candidate launch shape of one solve (the solve really runs and writes its
 // outputs) and record the fastest in the tuning cache.  Synchronises the stream.
 int tune_problem(int rhs_id, const ens_opts* o, const SolveArgs& a, const SolveScratch& sc,
@@ -83,6 +88,9 @@ int tune_problem(int rhs_id, const ens_opts* o, const SolveArgs& a, const SolveS
     } else {
       for (int t : {1, 2}) {
         if (o->tpt && t != o->tpt) continue;
+        // Rosenbrock23 and the dense-output / step-record Tsit5 kernels run one trajectory
+        // per thread whatever is asked: tpt 2 would repeat tpt 1
+        if (t == 2 && !o->tpt && one_per_thread(o)) continue;
         for (int f : {0, -3, -2}) {  // all resident blocks that fit, 3/4, 1/2 of them
           if (o->blocks_per_sm && f != 0) continue;
           LaunchCfg c = base;

@@ -205,6 +205,7 @@ def test_autotune_skips_shapes_that_do_not_fit():
     block, tpt, bps, ms = s.autotune(d(P), d(U), d(T), alg="ros23", layout="soa", abstol=1e-6,
                                      reltol=1e-6, dt0=1e-4)
     assert block in (64, 128, 256, 512) and ms > 0
+    assert tpt == 1  # Rosenbrock23 runs one trajectory per thread: no tpt-2 candidates
     out, st, _ = s.solve(d(P), d(U), d(T), alg="ros23", layout="soa", abstol=1e-6, reltol=1e-6,
                          dt0=1e-4)
     assert int(st.abs().sum()) == 0
