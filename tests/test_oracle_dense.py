@@ -1,7 +1,8 @@
 """Pins of the oracle's dense output for adaptive Tsit5 (the continuous extension defined in
 oracle/dense.py) to facts fixed outside the C++ code:
 
-* the typed constants equal the 40-digit derivation;
+* the typed constants (the oracle's, and the CUDA header's read as text) equal the 40-digit
+  derivation;
 * against the C++ oracle's own tableau: the order conditions of every rooted tree of order
   <= 4 hold at every theta (checked at several), b_i(1) = b_i, and the derivative is f at
   both ends (C1 across steps);
@@ -36,6 +37,21 @@ def _dweights(theta, r):
 def test_typed_constants_equal_the_derivation():
     np.testing.assert_allclose(oracle.tsit5_dense(), np.array(dense.derive()), rtol=1e-15,
                                atol=1e-16)
+
+
+def test_kernel_constants_equal_the_derivation():
+    """The CUDA path types the same coefficients independently (ts5_dense in its device
+    header); read them from the source text and compare with the derivation."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2304_06835_gb300", "csrc",
+                            "ens_device.cuh")).read()
+    body = src[src.index("constexpr double ts5_dense("):]
+    body = body[body.index("= {") + 3:body.index("};")]
+    rows = re.findall(r"\{([^{}]*)\}", body)
+    k = np.array([[float(x) for x in r.split(",")] for r in rows])
+    assert k.shape == (7, 4)
+    np.testing.assert_allclose(k, np.array(dense.derive()), rtol=1e-15, atol=1e-16)
 
 
 def test_order_conditions_at_every_theta():
