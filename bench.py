@@ -389,6 +389,11 @@ class SolveRunner:
         order = args.order if args.order != "auto" else ("index" if fixed else "cost")
         # kernels of one solve: the integrator, plus key / scan / scatter for the cost order
         self.launches_per_step = 1 + (3 if sched == "persistent" and order == "cost" else 0)
+        # an SDE ensemble's step ends with its moment sums (two reduction kernels), added
+        # across the ranks: the one exchange step of the sharded path
+        self.moments = w["alg"] == "em"
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.launches_per_step += 2 if self.moments else 0
 
     def step(self):
         a = self.args
@@ -396,6 +401,12 @@ class SolveRunner:
                           out=self.out, status=self.status, stats=self.stats,
                           schedule=a.schedule, block=a.block, tpt=a.tpt, refill_min=a.refill,
                           order=a.order, blocks_per_sm=a.bps, want_stats=True, **self.kw)
+        if self.moments:
+            from paper_2304_06835_gb300 import ensemble_sums
+            self.sums = ensemble_sums(self.out, self.status, layout=self.layout)
+            if self.world > 1:
+                import torch.distributed as dist
+                dist.all_reduce(self.sums)
 
     def work(self):
         st = self.stats.cpu().numpy().astype(np.int64)
@@ -408,9 +419,17 @@ class SolveRunner:
                          "ops_per_attempt": OPS_PER_ATTEMPT["ball"],
                          "ops_per_accepted_event_scan": OPS_PER_ATTEMPT["ball_event_scan"],
                          "trajectories_ok": ok, "autotuned_shape": self.tuned}
+        extra = {}
+        if self.moments:  # the job's ensemble mean and variance of each component at tf
+            sm = self.sums.cpu().numpy()
+            D = (len(sm) - 1) // 2
+            n = sm[2 * D]
+            mean = sm[:D] / n
+            extra["moments"] = {"n": int(n), "mean": [float(v) for v in mean],
+                                "var": [float(v) for v in (sm[D:2 * D] - n * mean * mean) / (n - 1)]}
         return attempts * OPS_PER_ATTEMPT[ops_key(self.w)], {
             "attempts_per_launch": attempts, "ops_per_attempt": OPS_PER_ATTEMPT[ops_key(self.w)],
-            "trajectories_ok": ok, "autotuned_shape": self.tuned}
+            "trajectories_ok": ok, "autotuned_shape": self.tuned, **extra}
 
     def e2e(self, stream):
         """Trajectories/s through ens_solve_host: pinned host inputs copied to the device, the

@@ -377,6 +377,26 @@ int ens_mlp_check(ens_mlp* m, void* cuda_stream);
  * network kernels evaluate them (device arrays of n floats). */
 int ens_mlp_activation(int which, long long n, const float* z, float* out, void* cuda_stream);
 
+/* Ensemble sums for moment estimation, the exchange step of a sharded ensemble (each rank
+ * reduces its own trajectories; the ranks then add their sums, e.g. an all-reduce, and form
+ * mean = S1 / n and variance (S2 - n mean^2) / (n - 1)): the expectation and variance of an
+ * SDE's solution estimated by Monte Carlo over the ensemble (Sec. 3.3).
+ *   out    : device array in `dtype`, the layout of ens_solve's output ([N][S][D] row-major,
+ *            [S][D][N] SOA); the sums are over save slot `slot` (0 <= slot < S; S = 1 for a
+ *            final-state solve)
+ *   status : device int8 [N] or NULL; with it only trajectories with status 0 count
+ *   scratch: device double [ENS_MOMENTS_BLOCKS * (2D + 1)], caller-owned: the partial sums
+ *            of the first pass (overwritten)
+ *   sums   : device double [2D + 1]: sums[j] = S1_j = sum of x_j, sums[D + j] = S2_j = sum of
+ *            x_j^2 (j < D), sums[2D] = n, the number of trajectories counted; written, not
+ *            accumulated.
+ * FP64 accumulation; deterministic (fixed reduction orders in two passes: ENS_MOMENTS_BLOCKS
+ * blocks, then one).  Asynchronous on cuda_stream; calls sharing a scratch array must be
+ * ordered on one stream.  ENS_EINVAL for bad sizes, slot, dtype, layout or null pointers. */
+#define ENS_MOMENTS_BLOCKS 608
+int ens_moments(long long N, int D, int dtype, int layout, int S, int slot, const void* out,
+                const signed char* status, double* scratch, double* sums, void* cuda_stream);
+
 /* Raw Philox4x32-10 words (Salmon et al. SC'11) of the SDE streams: for trajectory
  * j < n_traj and call c < n_calls, out[(c*4 + w)*n_traj + j] = word w of
  * Philox(counter = (c lo, c hi, (index_offset+j) lo, hi), key = (seed lo, seed hi)).

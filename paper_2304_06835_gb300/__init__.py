@@ -4,9 +4,11 @@ The compute path is libens.so (hand-written CUDA for sm_103a behind a C ABI, inc
 this package only marshals torch tensors into it.
 """
 from ._lib import EnsError, lib  # noqa: F401
-from .solver import EnsembleBatch, EnsembleSolver, make_opts, normals, philox_words  # noqa: F401
+from .solver import (EnsembleBatch, EnsembleSolver, combine_moments, ensemble_sums,  # noqa: F401
+                     make_opts, normals, philox_words)
 from .autograd import solve_fixed  # noqa: F401
 from .surrogate import GatedSurrogate, SurrogateMLP  # noqa: F401
 
-__all__ = ["EnsembleBatch", "EnsembleSolver", "EnsError", "make_opts", "normals", "philox_words", "lib",
+__all__ = ["EnsembleBatch", "EnsembleSolver", "EnsError", "combine_moments", "ensemble_sums",
+           "make_opts", "normals", "philox_words", "lib",
            "solve_fixed", "SurrogateMLP", "GatedSurrogate"]

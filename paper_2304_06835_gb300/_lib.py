@@ -20,6 +20,7 @@ NOISE = {1: 0, 2: 0, 3: 1, 4: 8, 5: 0, 6: 0, 7: 0, 8: 0}  # Wiener processes per
 ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5}
 F32, F64 = 0, 1
 LAYOUT = {"rowmajor": 0, "soa": 1}
+MOMENTS_BLOCKS = 608  # ENS_MOMENTS_BLOCKS
 SCHED = {"auto": 0, "direct": 1, "persistent": 2}
 ORDER = {"auto": 0, "index": 1, "cost": 2}
 MAX_SAVE = 256
@@ -84,6 +85,7 @@ SIGNATURES = {
                               _VP]),
     "ens_philox4x32_10": (_INT, [_ULL, _LL, _LL, _LL, _VP, _VP]),
     "ens_normals": (_INT, [_ULL, _LL, _LL, _LL, _INT, _VP, _VP]),
+    "ens_moments": (_INT, [_LL, _INT, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP]),
     "ens_solve_noalloc": (_INT, [_INT, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP,
                                  _VP]),
     "ens_autotune": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP, _VP,

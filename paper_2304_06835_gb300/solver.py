@@ -303,6 +303,48 @@ def normals(seed, n_traj, n_per, dtype=torch.float32, index_offset=0, device="cu
     return out
 
 
+def ensemble_sums(out, status=None, *, layout="rowmajor", slot=-1, stream=None):
+    """Per-component sums over an ensemble's trajectories for moment estimation, through
+    ens_moments: a float64 tensor [2D + 1] on out's device = (S1_0..S1_{D-1}, S2_0..S2_{D-1},
+    n), S1 = sum of x, S2 = sum of x^2 at save slot `slot` (negative: from the end) of a solve
+    output (row-major [N, D] / [N, S, D], SoA [D, N] / [S, D, N]), over the trajectories with
+    status 0 (all without a status tensor)."""
+    if not (out.is_cuda and out.is_contiguous()):
+        raise ValueError("out must be a contiguous CUDA tensor")
+    if layout == "rowmajor":
+        N, S, D = (out.shape[0], 1, out.shape[1]) if out.dim() == 2 else tuple(out.shape)
+    else:
+        S, D, N = (1, out.shape[0], out.shape[1]) if out.dim() == 2 else tuple(out.shape)
+    slot = slot + S if slot < 0 else slot
+    if status is not None and (status.dtype != torch.int8 or status.numel() != N):
+        raise ValueError("status must be an int8 tensor of N entries")
+    sums = torch.empty(2 * D + 1, dtype=torch.float64, device=out.device)
+    scratch = torch.empty(_lib.MOMENTS_BLOCKS * (2 * D + 1), dtype=torch.float64,
+                          device=out.device)
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream(out.device).cuda_stream
+    _lib.check(_lib.lib().ens_moments(
+        int(N), int(D), _TORCH_DT[out.dtype], _lib.LAYOUT[layout], int(S), int(slot),
+        _ptr(out), _ptr(status) if status is not None else None, _ptr(scratch), _ptr(sums),
+        ctypes.c_void_p(s)))
+    return sums
+
+
+def combine_moments(sums, group=None):
+    """The exchange step of a sharded ensemble: add every rank's ensemble_sums (an all-reduce
+    over torch.distributed when it is initialised with more than one rank; NCCL wants the
+    tensor on the GPU, gloo on the CPU) and form (n, mean [D], variance [D]) with the
+    unbiased variance (S2 - n mean^2) / (n - 1)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        sums = sums.clone()
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=group)
+    D = (sums.numel() - 1) // 2
+    n = sums[2 * D]
+    mean = sums[:D] / n
+    var = (sums[D:2 * D] - n * mean * mean) / (n - 1)
+    return n, mean, var
+
+
 class EnsembleBatch:
     """Several sub-problems solved by one call (one CUDA graph launch with graph=True).
 

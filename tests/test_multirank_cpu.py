@@ -1,6 +1,7 @@
-"""The multi-rank path of the benchmark on CPU ranks (gloo, world size 2): each rank solves
-its own shard (weak scaling, no collective on the data path) and the job time is the
-maximum over the ranks; the reference arm prints from rank 0 only."""
+"""The multi-rank path on CPU ranks (gloo, world size 2): each rank solves its own shard
+(weak scaling, no collective on the data path) and the job time is the maximum over the
+ranks; the reference arm prints from rank 0 only; the moment sums of sharded ensembles add up
+across the ranks (the one exchange step, an all-reduce after the solve)."""
 import json
 import os
 import subprocess
@@ -54,3 +55,37 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def _moments_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    from paper_2304_06835_gb300 import combine_moments
+    x = np.random.default_rng(11).lognormal(0.3, 0.8, size=(1001, 4))  # the whole ensemble
+    mine = x[rank::world]                                                # this rank's shard
+    sums = torch.tensor(np.concatenate([mine.sum(0), (mine * mine).sum(0), [len(mine)]]),
+                        dtype=torch.float64)
+    n, mean, var = combine_moments(sums)
+    q.put((rank, float(n), mean.numpy(), var.numpy()))
+    dist.destroy_process_group()
+
+
+def test_moments_all_reduce_gloo():
+    """The exchange step of a sharded SDE ensemble: every rank adds the others' sums and
+    obtains the whole ensemble's count, mean and unbiased variance."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 31500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_moments_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    x = np.random.default_rng(11).lognormal(0.3, 0.8, size=(1001, 4))
+    for _, n, mean, var in res:
+        assert n == 1001
+        np.testing.assert_allclose(mean, x.mean(0), rtol=1e-13)
+        np.testing.assert_allclose(var, x.var(0, ddof=1), rtol=1e-11)
