@@ -59,6 +59,18 @@ def test_validation_without_device(L):
     h = ctypes.c_void_p()
     assert L.ens_create(ctypes.byref(h), 99, 3, 3) == _lib.ENS_EINVAL
     assert L.ens_create(ctypes.byref(h), 1, 2, 3) == _lib.ENS_EINVAL
+    # ens_moments(N, D, dtype, layout, S, slot, out, status, scratch, sums, stream)
+    p = ctypes.c_void_p(16)  # never dereferenced: every call below fails validation first
+    for args in ((-1, 3, 0, 0, 1, 0, p, None, p, p),   # N < 0
+                 (4, 0, 0, 0, 1, 0, p, None, p, p),    # D < 1
+                 (4, 3, 0, 0, 2, 2, p, None, p, p),    # slot >= S
+                 (4, 3, 0, 0, 2, -1, p, None, p, p),   # slot < 0
+                 (4, 3, 5, 0, 1, 0, p, None, p, p),    # dtype
+                 (4, 3, 0, 7, 1, 0, p, None, p, p),    # layout
+                 (4, 3, 0, 0, 1, 0, None, None, p, p),  # out
+                 (4, 3, 0, 0, 1, 0, p, None, None, p),  # scratch
+                 (4, 3, 0, 0, 1, 0, p, None, p, None)):  # sums
+        assert L.ens_moments(*args, None) == _lib.ENS_EINVAL, args
 
 
 def test_product_does_not_import_oracle():
