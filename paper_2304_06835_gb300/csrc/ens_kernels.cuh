@@ -133,7 +133,8 @@ struct Tol<float> {
 // Save times in shared memory, copied at block start by the kernels that run the adaptive
 // integrators: lanes read them at their own save index, and a read of the kernel's parameter
 // array at an index that differs across the warp is serialised over the distinct addresses.
-// Dynamic shared memory of the kernels: the dense saves' 16-byte staging (Adaptive::put).
+// Dynamic shared memory of the kernels: the 16-byte staging of dense saves (Adaptive::put)
+// and of the step record (Adaptive::record), one slot per thread.
 extern __shared__ __align__(16) unsigned char ens_dyn_smem[];
 
 template <class T>
