@@ -206,8 +206,10 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
 /* Launch-shape autotuner (the occupancy tuning the paper leaves to KernelAbstractions,
  * Sec. 5.1): runs the solve of ens_solve (same arguments, outputs really written) with every
  * candidate launch shape -- block in {64, 128, 256, 512}, and for the persistent schedule
- * trajectories per thread in {1, 2} and resident blocks per SM in {all that fit, 3/4, 1/2 of
- * that}; a nonzero opts->block / opts->tpt / opts->blocks_per_sm pins that value --
+ * trajectories per thread in {1, 2} (1 only for the kernels that run one: Rosenbrock23, dense
+ * output, step record) and resident blocks per SM in {all that fit, 3/4, 1/2 of that}; a
+ * nonzero opts->block / opts->tpt / opts->blocks_per_sm pins that value; shapes that do not
+ * fit the kernel are skipped --
  * timing each (one warm-up, best of two), and records the fastest in a process-wide cache
  * keyed by (model, algorithm, dtype, layout, floor(log2 N), output kind -- final state, save
  * times, dense save times or step record --, SM count).  Later
