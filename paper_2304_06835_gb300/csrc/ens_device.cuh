@@ -679,6 +679,10 @@ struct LUDyn {
       a[c][c] = inv;
 #pragma unroll 1
       for (int r = c + 1; r < D; ++r) {
+        // a zero below the pivot leaves its row as it is (fma(-0, x, y) = y for finite x):
+        // the stiff models' matrices are mostly zeros, in the same places for every
+        // trajectory, so the skip is the same across the warp
+        if (a[r][c] == T(0)) continue;
         const T l = a[r][c] * inv;
         a[r][c] = l;
         // independent across j: unrolled so several local-memory loads are in flight
