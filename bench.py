@@ -1042,7 +1042,7 @@ def main():
         roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of %s on a "
                                       "smaller case, scaled by units processed" % prof["kernel"])
     e2e = None if args.no_e2e else runner.e2e(stream)
-    cfg = {"workload": args.workload, "model": w["rhs"], "alg": w["alg"], "N": N,
+    cfg = {"workload": args.workload, "rhs": w["rhs"], "alg": w["alg"], "N": N,
            "tspan": [0.0, w["t1"]],
            **{k: w[k] for k in ("tol", "dt", "dt0", "dtmax", "every", "seed", "saves", "dense")
               if k in w},
