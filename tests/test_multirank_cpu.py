@@ -89,3 +89,17 @@ def test_moments_all_reduce_gloo():
         assert n == 1001
         np.testing.assert_allclose(mean, x.mean(0), rtol=1e-13)
         np.testing.assert_allclose(var, x.var(0, ddof=1), rtol=1e-11)
+
+
+def test_combine_moments_single_process():
+    """Without a process group the sums are used as they are: count, mean and the unbiased
+    variance of the ensemble, and the input tensor is not modified."""
+    from paper_2304_06835_gb300 import combine_moments
+    x = np.random.default_rng(12).normal(2.0, 3.0, size=(777, 3))
+    sums = torch.tensor(np.concatenate([x.sum(0), (x * x).sum(0), [len(x)]]))
+    before = sums.clone()
+    n, mean, var = combine_moments(sums)
+    assert float(n) == 777
+    np.testing.assert_allclose(mean.numpy(), x.mean(0), rtol=1e-13)
+    np.testing.assert_allclose(var.numpy(), x.var(0, ddof=1), rtol=1e-10)
+    assert torch.equal(sums, before)
