@@ -42,15 +42,53 @@ NOISE = {1: 0, 2: 0, 3: 1, 4: 8, 5: 0, 6: 0, 7: 0, 8: 0}  # Wiener processes per
 STATUS = {"ok": 0, "maxiters": 1, "dt_min": 2, "nonfinite": 3}
 
 
+def _compile(src: str, target: str) -> None:
+    tmp = target + ".tmp.%d" % os.getpid()
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+           "-o", tmp, src]
+    subprocess.check_call(cmd)
+    os.replace(tmp, target)
+
+
 def build(force: bool = False) -> str:
     """Compile liboracle.so with the host compiler (no FMA contraction, portable flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp.%d" % os.getpid()
-        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
-               "-o", tmp, _SRC]
-        subprocess.check_call(cmd)
-        os.replace(tmp, _LIB)
+        _compile(_SRC, _LIB)
     return _LIB
+
+
+def source() -> str:
+    """The oracle's C++ source text (tests plant mistakes in copies of it)."""
+    with open(_SRC) as f:
+        return f.read()
+
+
+class variant:
+    """Context manager: compile a modified copy of the oracle's source into `workdir` and
+    route every call of this module to it until the block ends.  Used by tests that plant
+    a mistake in the oracle and check that a pin detects it."""
+
+    def __init__(self, text: str, workdir: str):
+        self.text, self.workdir = text, workdir
+
+    def __enter__(self):
+        global _lib
+        src = os.path.join(self.workdir, "ens_oracle_variant.cpp")
+        so = os.path.join(self.workdir, "liboracle_variant.so")
+        with open(src, "w") as f:
+            f.write(self.text)
+        _compile(src, so)
+        lib()  # the regular library first, so that it is restored afterwards
+        with _lock:
+            self._saved = _lib
+            _lib = _bind(ctypes.CDLL(so))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self._saved
+        return False
 
 
 def lib():
@@ -58,53 +96,57 @@ def lib():
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIB)
-            dp = ctypes.POINTER(ctypes.c_double)
-            L.oracle_solve.restype = ctypes.c_int
-            L.oracle_solve.argtypes = [
-                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
-                dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_longlong,
-                dp, ctypes.POINTER(ctypes.c_byte), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
-                ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
-            L.oracle_solve_steps.restype = ctypes.c_int
-            L.oracle_solve_steps.argtypes = [
-                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, dp, dp, dp,
-                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_longlong,
-                ctypes.c_double, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_byte),
-                ctypes.POINTER(ctypes.c_longlong), dp, dp, ctypes.POINTER(ctypes.c_longlong),
-                ctypes.c_int]
-            L.oracle_pollu_reaction_sum.restype = None
-            L.oracle_pollu_reaction_sum.argtypes = [dp, dp, dp]
-            L.oracle_tsit5_dense.restype = None
-            L.oracle_tsit5_dense.argtypes = [dp]
-            L.oracle_step.restype = ctypes.c_int
-            L.oracle_step.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
-                                      ctypes.c_double, ctypes.c_double, dp, dp]
-            L.oracle_tsit5_tableau.restype = None
-            L.oracle_tsit5_tableau.argtypes = [dp, dp, dp, dp]
-            L.oracle_rhs.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
-            L.oracle_jac.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp, dp]
-            L.oracle_diffusion.restype = ctypes.c_int
-            L.oracle_diffusion.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
-            L.oracle_em_step.restype = ctypes.c_int
-            L.oracle_em_step.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
-                                         dp, dp]
-            L.oracle_lu_solve.argtypes = [ctypes.c_int, dp, dp, dp]
-            u32p = ctypes.POINTER(ctypes.c_uint32)
-            L.oracle_philox4x32_10.restype = None
-            L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
-            L.oracle_normals.restype = None
-            L.oracle_normals.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.c_longlong,
-                                         ctypes.c_int, dp]
-            L.oracle_tsit5_fixed_grad.restype = ctypes.c_int
-            L.oracle_tsit5_fixed_grad.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, dp,
-                                                  ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
-            L.oracle_fixed_grad.restype = ctypes.c_int
-            L.oracle_fixed_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, dp, dp,
-                                            dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
-            _lib = L
+            _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
+
+
+def _bind(L):
+    """Declare the C signatures of the oracle's entry points on a loaded library."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_solve.restype = ctypes.c_int
+    L.oracle_solve.argtypes = [
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+        dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+        ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_longlong,
+        dp, ctypes.POINTER(ctypes.c_byte), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
+        ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
+    L.oracle_solve_steps.restype = ctypes.c_int
+    L.oracle_solve_steps.argtypes = [
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, dp, dp, dp,
+        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_longlong,
+        ctypes.c_double, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_byte),
+        ctypes.POINTER(ctypes.c_longlong), dp, dp, ctypes.POINTER(ctypes.c_longlong),
+        ctypes.c_int]
+    L.oracle_pollu_reaction_sum.restype = None
+    L.oracle_pollu_reaction_sum.argtypes = [dp, dp, dp]
+    L.oracle_tsit5_dense.restype = None
+    L.oracle_tsit5_dense.argtypes = [dp]
+    L.oracle_step.restype = ctypes.c_int
+    L.oracle_step.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_double, dp, dp]
+    L.oracle_tsit5_tableau.restype = None
+    L.oracle_tsit5_tableau.argtypes = [dp, dp, dp, dp]
+    L.oracle_rhs.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
+    L.oracle_jac.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp, dp]
+    L.oracle_diffusion.restype = ctypes.c_int
+    L.oracle_diffusion.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
+    L.oracle_em_step.restype = ctypes.c_int
+    L.oracle_em_step.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
+                                 dp, dp]
+    L.oracle_lu_solve.argtypes = [ctypes.c_int, dp, dp, dp]
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    L.oracle_philox4x32_10.restype = None
+    L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.oracle_normals.restype = None
+    L.oracle_normals.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.c_longlong,
+                                 ctypes.c_int, dp]
+    L.oracle_tsit5_fixed_grad.restype = ctypes.c_int
+    L.oracle_tsit5_fixed_grad.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, dp,
+                                          ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
+    L.oracle_fixed_grad.restype = ctypes.c_int
+    L.oracle_fixed_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, dp, dp,
+                                    dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
+    return L
 
 
 def _dp(a):
