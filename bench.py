@@ -12,8 +12,9 @@ lorenz_adjoint_f64 (forward with checkpoints + discrete adjoint, N = 65,536, 100
 steps, FP64), uneven_batch_f32 (500k Lorenz tf~U[1,100] + 200k Robertson + 300k GBM in one
 CUDA-graph launch, FP32).
 
-Under torchrun (N > 1) every rank solves its own N-trajectory shard (weak scaling, no
-collective on the data path); the timing is the max over ranks.
+Under torchrun (N > 1) the ensemble has N x world trajectories and every rank solves its
+contiguous N-trajectory shard (the library's shard_plan; weak scaling, no collective on the
+data path; SDE streams by the global index); the timing is the max over ranks.
 """
 from __future__ import annotations
 
@@ -40,8 +41,12 @@ SM_MAX_MHZ = 2070.0
 
 # Algorithmic work, in FMA-pipe instructions (FFMA/FADD/FMUL or their FP64 forms) per unit,
 # counted from the operation model of each step (selects, compares and clamps not counted):
-#   adaptive Tsit5 attempt on Lorenz: stage combinations 81, six f evaluations 36, error
-#     estimate 21, scaled RMS norm 19, PI-controller arithmetic 3 -> 160;
+#   adaptive Tsit5 attempt on Lorenz: the operation model (stage combinations 81, six f
+#     evaluations 36, error estimate 21, scaled RMS norm 19, PI-controller arithmetic 3) gives
+#     160, but the kernel's FP32 instruction classes (ncu: FFMA + FADD + FMUL + 2 x their
+#     paired forms, over the solve's attempts) measure 174.6 per attempt: the starting-step,
+#     clock and clamp arithmetic the model leaves out.  175 is counted (the planned model's
+#     figure, within 0.3 % of the measurement);
 #   fixed Tsit5 step: stage combinations 81 + six f evaluations 36 -> 117;
 #   adjoint step (Tsit5, Lorenz): forward with checkpoints 117, replay 117, transposed step
 #     189 (six VJP pairs 6 x 18, stage-adjoint sums 45 + 15, seeds 21) -> 423.
@@ -59,7 +64,7 @@ SM_MAX_MHZ = 2070.0
 # Bouncing ball (D = 2, f costs nothing): a Tsit5 attempt = stage combinations 54, error 14,
 #   norm 13, controller 3 -> 84; each accepted step adds the event scan: the dense
 #   polynomial 4 x 7 x 2 FMA + 8 scalings = 64 and 9 checkpoints x 8 = 72 -> 136.
-OPS_PER_ATTEMPT = {"tsit5": 160, "tsit5_fixed": 117, "rk4": 48, "ros23": 140, "em": 25,
+OPS_PER_ATTEMPT = {"tsit5": 175, "tsit5_fixed": 117, "rk4": 48, "ros23": 140, "em": 25,
                    "adjoint": 423, "crn_em": 224, "crn_em_f64": 104, "ball": 84,
                    "ball_event_scan": 136, "ros23_orego": 140, "ros23_hires": 640,
                    "ros23_pollu": 4930}
@@ -130,38 +135,64 @@ BATCH_PARTS = (("lorenz", "tsit5", 500_000, dict(abstol=1e-5, reltol=1e-5)),
                ("gbm", "em", 300_000, dict(dt=1e-3, seed=12345)))
 
 
-def batch_inputs(rank=0):
-    b = workloads.uneven_batch(*(n for _, _, n, _ in BATCH_PARTS), seed=4 + 1000 * rank)
-    return [b[name] for name, _, _, _ in BATCH_PARTS]
+def _shard(n, rank, world):
+    """This rank's contiguous range of one ensemble of n trajectories (the library's plan)."""
+    from paper_2304_06835_gb300.shard import shard_plan
+    r = shard_plan(n, world)[rank]
+    return r[0] if r else (0, 0)
 
 
-def inputs_for(w, rank=0):
-    N = w["N"]
+def batch_inputs(rank=0, world=1):
+    """The uneven batch; under torchrun every item of one batch of world x the sizes is split
+    into contiguous shards, rank r taking shard r of each (the items' draws are i.i.d., so
+    equal counts balance the work)."""
+    b = workloads.uneven_batch(*(n * world for _, _, n, _ in BATCH_PARTS), seed=4)
+    out = []
+    for name, _, n, _ in BATCH_PARTS:
+        a, e = _shard(n * world, rank, world)
+        out.append(tuple(x[a:e] for x in b[name]))
+    return out
+
+
+def _draw(w, N):
+    """N trajectories of the workload's seeded ensemble."""
     if w["kind"] in ("surrogate", "mlp"):
-        x = workloads.surrogate_inputs(N, seed=7 + 1000 * rank, outside_share=0.05)
+        x = workloads.surrogate_inputs(N, seed=7, outside_share=0.05)
         return x[:, :3].copy(), x[:, 3:].copy(), np.tile([0.0, w["t1"]], (N, 1))
     if w["kind"] == "adjoint":
-        P, U, T = workloads.lorenz_random(N, seed=5 + 1000 * rank, t1=w["t1"])
-    elif w["rhs"] == "lorenz":
+        return workloads.lorenz_random(N, seed=5, t1=w["t1"])
+    if w["rhs"] == "lorenz":
         if w["alg"] == "tsit5_fixed":
-            P, U, T = workloads.lorenz_sweep(N, t1=w["t1"])
-        else:
-            P, U, T = workloads.lorenz_random(N, seed=2 + 1000 * rank, t1=w["t1"])
-    elif w["rhs"] == "robertson":
-        P, U, T = workloads.robertson_random(N, seed=3 + 1000 * rank, t1=w["t1"])
-    elif w["rhs"] in ("orego", "hires", "pollu"):
-        P, U, T = workloads.stiff(w["rhs"], N, seed=11 + 1000 * rank, t1=w["t1"])
-    elif w["rhs"] == "ball":
-        P, U, T = workloads.ball(N, seed=10 + 1000 * rank, t1=w["t1"])
-    elif w["rhs"] == "crn":  # the Cartesian product of k draws per parameter, k^6 = N
+            return workloads.lorenz_sweep(N, t1=w["t1"])
+        return workloads.lorenz_random(N, seed=2, t1=w["t1"])
+    if w["rhs"] == "robertson":
+        return workloads.robertson_random(N, seed=3, t1=w["t1"])
+    if w["rhs"] in ("orego", "hires", "pollu"):
+        return workloads.stiff(w["rhs"], N, seed=11, t1=w["t1"])
+    if w["rhs"] == "ball":
+        return workloads.ball(N, seed=10, t1=w["t1"])
+    if w["rhs"] == "crn":  # the Cartesian product of k draws per parameter, k^6 = N
         k = int(round(N ** (1.0 / 6.0)))
         if k ** 6 == N:
-            P, U, T = workloads.crn_grid(k, seed=8 + 1000 * rank, t1=w["t1"])
-        else:
-            P, U, T = workloads.crn_random(N, seed=8 + 1000 * rank, t1=w["t1"])
-    else:
-        P, U, T = workloads.gbm_random(N, seed=4 + 1000 * rank, t1=w["t1"])
-    return P, U, T
+            return workloads.crn_grid(k, seed=8, t1=w["t1"])
+        return workloads.crn_random(N, seed=8, t1=w["t1"])
+    return workloads.gbm_random(N, seed=4, t1=w["t1"])
+
+
+def inputs_for(w, rank=0, world=1):
+    """This rank's shard of one seeded ensemble of N x world trajectories: the contiguous
+    range shard_plan gives it (index_offset = shard_start keeps SDE noise streams those of
+    the whole ensemble); at world = 1 the whole N-trajectory ensemble."""
+    N = w["N"]
+    if world == 1:
+        return _draw(w, N)
+    P, U, T = _draw(w, N * world)
+    a, b = _shard(N * world, rank, world)
+    return P[a:b], U[a:b], T[a:b]
+
+
+def shard_start(w, rank=0, world=1):
+    return _shard(w["N"] * world, rank, world)[0] if world > 1 else 0
 
 
 def solve_kwargs(w):
@@ -265,8 +296,10 @@ def _oracle_run(w, P, U, T, n, nt, G=None):
                            reltol=w["tol"], nthreads=nt)
     elif w["kind"] == "adjoint":
         oracle.fixed_grad(w["rhs"], w["alg"], P[:n], U[:n], T[:n], w["dt"], G[:n], nthreads=nt)
-    else:
-        oracle.solve(w["rhs"], w["alg"], P[:n], U[:n], T[:n], nthreads=nt, **solve_kwargs(w))
+    else:  # the per-trajectory (accepted, rejected, f evaluations) counts come back
+        return oracle.solve(w["rhs"], w["alg"], P[:n], U[:n], T[:n], nthreads=nt,
+                            **solve_kwargs(w))[2]
+    return None
 
 
 def oracle_rate(w, budget_s=12.0):
@@ -291,11 +324,11 @@ def oracle_rate(w, budget_s=12.0):
     reps = max(1, int(round(budget_s / max(dt * n2 / n, 1e-3)))) if n2 == w["N"] else 1
     t0 = time.perf_counter()
     for _ in range(reps):
-        _oracle_run(w, P, U, T, n2, nt, G)
+        stats = _oracle_run(w, P, U, T, n2, nt, G)
     el = time.perf_counter() - t0
     sample = ("%d pass(es) over the first %d of the %d trajectories (%.1f s)"
               % (reps, n2, w["N"], el))
-    return n2 * reps / el, sample, nt
+    return n2 * reps / el, sample, nt, stats
 
 
 REF_BUDGET_S = 120.0
@@ -355,7 +388,8 @@ class SolveRunner:
         import paper_2304_06835_gb300 as ens
         self.args, self.w, self.dev = args, w, dev
         self.dt_t = torch.float32 if w["dtype"] == "f32" else torch.float64
-        self.P, self.U, self.T = inputs_for(w, rank)
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.P, self.U, self.T = inputs_for(w, rank, world)
         N = w["N"]
         self.layout = w.get("layout", "soa")
         if self.layout == "soa":
@@ -373,6 +407,8 @@ class SolveRunner:
         self.stats = torch.empty((3, N), dtype=torch.int32, device=dev)
         self.solver = ens.EnsembleSolver(w["rhs"])
         self.kw = solve_kwargs(w)
+        if "seed" in self.kw:  # SDE streams indexed by the trajectory's place in the ensemble
+            self.kw["index_offset"] = shard_start(w, rank, world)
         self.tuned = None
         if not args.no_autotune and args.block == 0 and args.tpt == 0 and args.bps == 0:
             # the launch-shape autotuner on these inputs (outside the timed region); later
@@ -389,7 +425,7 @@ class SolveRunner:
         order = args.order if args.order != "auto" else ("index" if fixed else "cost")
         # kernels of one solve: the integrator, plus key / scan / scatter for the cost order
         self.launches_per_step = 1 + (3 if sched == "persistent" and order == "cost" else 0)
-        # an SDE ensemble's step ends with its moment sums (two reduction kernels), added
+        # an SDE ensemble's step ends with its moments (two reduction kernels), gathered
         # across the ranks: the one exchange step of the sharded path
         self.moments = w["alg"] == "em"
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -402,11 +438,10 @@ class SolveRunner:
                           schedule=a.schedule, block=a.block, tpt=a.tpt, refill_min=a.refill,
                           order=a.order, blocks_per_sm=a.bps, want_stats=True, **self.kw)
         if self.moments:
-            from paper_2304_06835_gb300 import ensemble_sums
-            self.sums = ensemble_sums(self.out, self.status, layout=self.layout)
-            if self.world > 1:
-                import torch.distributed as dist
-                dist.all_reduce(self.sums)
+            from paper_2304_06835_gb300 import ensemble_moments, gather_moments
+            # this rank's (mean, M2, n), then every rank's, stacked in rank order
+            self.parts = gather_moments(ensemble_moments(self.out, self.status,
+                                                         layout=self.layout))
 
     def work(self):
         st = self.stats.cpu().numpy().astype(np.int64)
@@ -421,12 +456,10 @@ class SolveRunner:
                          "trajectories_ok": ok, "autotuned_shape": self.tuned}
         extra = {}
         if self.moments:  # the job's ensemble mean and variance of each component at tf
-            sm = self.sums.cpu().numpy()
-            D = (len(sm) - 1) // 2
-            n = sm[2 * D]
-            mean = sm[:D] / n
+            from paper_2304_06835_gb300 import merge_moments
+            n, mean, var = merge_moments(self.parts)
             extra["moments"] = {"n": int(n), "mean": [float(v) for v in mean],
-                                "var": [float(v) for v in (sm[D:2 * D] - n * mean * mean) / (n - 1)]}
+                                "var": [float(v) for v in var]}
         return attempts * OPS_PER_ATTEMPT[ops_key(self.w)], {
             "attempts_per_launch": attempts, "ops_per_attempt": OPS_PER_ATTEMPT[ops_key(self.w)],
             "trajectories_ok": ok, "autotuned_shape": self.tuned, **extra}
@@ -570,8 +603,10 @@ class AdjointRunner:
 
         import paper_2304_06835_gb300 as ens
         self.args, self.w, self.dev = args, w, dev
-        self.P, self.U, self.T = inputs_for(w, rank)
-        self.tgt = workloads.adjoint_targets(w["N"], seed=5 + 1000 * rank)
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.P, self.U, self.T = inputs_for(w, rank, world)
+        a = shard_start(w, rank, world)
+        self.tgt = workloads.adjoint_targets(w["N"] * world, seed=5)[a:a + w["N"]]
         t = lambda a: torch.tensor(a.T.copy(), dtype=torch.float64, device=dev)
         self.Pd, self.Ud, self.Td, self.tg = t(self.P), t(self.U), t(self.T), t(self.tgt)
         self.solver = ens.EnsembleSolver(w["rhs"])
@@ -642,7 +677,7 @@ class BatchRunner:
 
         import paper_2304_06835_gb300 as ens
         self.args, self.w, self.dev = args, w, dev
-        self.parts = batch_inputs(rank)
+        self.parts = batch_inputs(rank, int(os.environ.get("WORLD_SIZE", "1")))
         t = lambda a: torch.tensor(a.T.copy(), dtype=torch.float32, device=dev)
         self.items = []
         for (name, alg, n, kw), (P, U, T) in zip(BATCH_PARTS, self.parts):
@@ -949,6 +984,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--probe", action="store_true", help="also measure FP32/FP64 FMA rates")
+    ap.add_argument("--sustain", type=float, default=2.0,
+                    help="seconds of back-to-back steps after the timed region, with clocks "
+                         "sampled (0: skip)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.n:
@@ -1041,6 +1079,29 @@ def main():
         roofline["traffic"] = prof["per_unit"] * N
         roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of %s on a "
                                       "smaller case, scaled by units processed" % prof["kernel"])
+    sustained = None
+    if args.sustain > 0 and world == 1:
+        # back-to-back steps for a few seconds with the clock sampler running: whether the
+        # SM clock holds under a seconds-long load (the timed region may be milliseconds).
+        # One rank only: the SDE steps end with a collective, and ranks looping on their own
+        # clocks would call it different numbers of times.
+        sampler2 = ClockSampler(local)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_s, t_s = 0, 0.0
+        w0 = time.perf_counter()
+        while time.perf_counter() - w0 < args.sustain:
+            e0.record(stream)
+            for _ in range(max(1, int(0.05 / max(launch_s, 1e-6)))):
+                runner.step()
+                n_s += 1
+            e1.record(stream)
+            e1.synchronize()
+            t_s += e0.elapsed_time(e1) / 1e3
+        c2 = sampler2.stop()
+        sustained = {"seconds": t_s, "steps": n_s, "value": N * world * n_s / t_s,
+                     "ms_per_step": 1e3 * t_s / n_s, "clocks": c2,
+                     "note": "back-to-back steps after the timed region, no L2 flush"}
     e2e = None if args.no_e2e else runner.e2e(stream)
     cfg = {"workload": args.workload, "rhs": w["rhs"], "alg": w["alg"], "N": N,
            "tspan": [0.0, w["t1"]],
@@ -1065,6 +1126,8 @@ def main():
         "gpu_launches": args.steps * runner.launches_per_step,
         "e2e": e2e,
     }
+    if sustained is not None:
+        line["sustained"] = sustained
     if args.probe:
         import ctypes as C
         for dt_name, code in (("fp32", _lib.F32), ("fp64", _lib.F64)):
@@ -1075,9 +1138,20 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline and hasattr(runner, "cpu_baseline"):
         line["cpu_baseline"] = runner.cpu_baseline()
     elif rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, sample, nt = oracle_rate(w)
+        rate, sample, nt, ostats = oracle_rate(w)
         line["cpu_baseline"] = {"value": rate, "unit": "trajectories/s", "cores": nt,
                                 "kind": "oracle", "sample": sample}
+        if ostats is not None and w["kind"] == "solve" and w["alg"] in ("tsit5", "ros23"):
+            # the roofline's numerator counts the GPU's own attempts: the oracle (FP64, the
+            # same tolerance) counts them on the same trajectories
+            n = len(ostats)
+            g = runner.stats[:, :n].cpu().numpy().astype(np.int64)
+            a_gpu, a_orc = int(g[0].sum() + g[1].sum()), int(ostats[:, :2].sum())
+            line["roofline"]["attempts_oracle"] = {
+                "trajectories": n, "gpu": a_gpu, "oracle_f64": a_orc,
+                "ratio": a_gpu / max(a_orc, 1),
+                "basis": "attempts (accepted + rejected) over the first %d trajectories, the "
+                         "oracle in FP64 at the workload's tolerance" % n}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:

@@ -221,6 +221,16 @@ int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
                  int* stats, void* cuda_stream, int* block, int* tpt, int* blocks_per_sm,
                  float* best_ms);
 
+/* Work estimate per trajectory (the key the longest-first order of the persistent schedule
+ * sorts by, and the cost that balances the shards of one ensemble across ranks, as the
+ * paper's MPI path scatters one ensemble, Sec. 6.3): keys[i] = the expected number of steps
+ * of trajectory i -- (tf - t0) / dt for fixed-step methods, (tf - t0) / h0 for adaptive ones
+ * with h0 the starting step (opts->dt0 if > 0, else the Hairer-Norsett-Wanner starting step
+ * the solve itself takes).  Same arguments and checks as ens_solve, without outputs; keys is
+ * a device float [N].  Asynchronous on cuda_stream. */
+int ens_cost_keys(ens_handle* h, long long N, const void* params, const void* u0,
+                  const void* tspan, const ens_opts* opts, float* keys, void* cuda_stream);
+
 /* Batched ensembles: several sub-problems (different models, methods, sizes and time spans)
  * solved by one call -- the uneven-work case of Sec. 6.4 (trajectories whose step counts
  * differ) widened to mixed stiff / non-stiff / stochastic work.  A plan validates the items,
@@ -379,25 +389,35 @@ int ens_mlp_check(ens_mlp* m, void* cuda_stream);
  * network kernels evaluate them (device arrays of n floats). */
 int ens_mlp_activation(int which, long long n, const float* z, float* out, void* cuda_stream);
 
-/* Ensemble sums for moment estimation, the exchange step of a sharded ensemble (each rank
- * reduces its own trajectories; the ranks then add their sums, e.g. an all-reduce, and form
- * mean = S1 / n and variance (S2 - n mean^2) / (n - 1)): the expectation and variance of an
- * SDE's solution estimated by Monte Carlo over the ensemble (Sec. 3.3).
+/* Ensemble moments for Monte Carlo estimation (Sec. 3.3: the expectation and variance of an
+ * SDE's solution estimated over the ensemble), and the exchange step of a sharded ensemble:
+ * each rank reduces its own trajectories, then the ranks' results are merged
+ * (ens_moments_combine) into the whole ensemble's.
  *   out    : device array in `dtype`, the layout of ens_solve's output ([N][S][D] row-major,
- *            [S][D][N] SOA); the sums are over save slot `slot` (0 <= slot < S; S = 1 for a
+ *            [S][D][N] SOA); the moments are over save slot `slot` (0 <= slot < S; S = 1 for a
  *            final-state solve)
  *   status : device int8 [N] or NULL; with it only trajectories with status 0 count
- *   scratch: device double [ENS_MOMENTS_BLOCKS * (2D + 1)], caller-owned: the partial sums
- *            of the first pass (overwritten)
- *   sums   : device double [2D + 1]: sums[j] = S1_j = sum of x_j, sums[D + j] = S2_j = sum of
- *            x_j^2 (j < D), sums[2D] = n, the number of trajectories counted; written, not
- *            accumulated.
- * FP64 accumulation; deterministic (fixed reduction orders in two passes: ENS_MOMENTS_BLOCKS
- * blocks, then one).  Asynchronous on cuda_stream; calls sharing a scratch array must be
- * ordered on one stream.  ENS_EINVAL for bad sizes, slot, dtype, layout or null pointers. */
+ *   scratch: device double [ENS_MOMENTS_BLOCKS * (2D + 1)], caller-owned: the partial
+ *            results of the first pass (overwritten)
+ *   result : device double [2D + 1]: result[j] = mean of x_j, result[D + j] = M2_j = sum over
+ *            the counted trajectories of (x_j - mean_j)^2 (j < D), result[2D] = n, the number
+ *            of trajectories counted; written, not accumulated.  The unbiased variance is
+ *            M2_j / (n - 1).  With n = 0 every entry is 0.
+ * FP64 arithmetic; groups are joined by the pairwise update of Chan, Golub and LeVeque (no
+ * cancellation of raw power sums when |mean| >> std); deterministic (fixed merge orders in
+ * two passes: ENS_MOMENTS_BLOCKS blocks, then one).  Asynchronous on cuda_stream; calls
+ * sharing a scratch array must be ordered on one stream.  ENS_EINVAL for bad sizes, slot,
+ * dtype, layout or null pointers. */
 #define ENS_MOMENTS_BLOCKS 608
 int ens_moments(long long N, int D, int dtype, int layout, int S, int slot, const void* out,
-                const signed char* status, double* scratch, double* sums, void* cuda_stream);
+                const signed char* status, double* scratch, double* result, void* cuda_stream);
+
+/* Merge the ens_moments results of n_parts disjoint groups of trajectories (e.g. the ranks of
+ * a sharded ensemble, gathered in rank order) into the moments of their union, by the same
+ * pairwise update, in the order given.  HOST arrays: parts [n_parts][2D + 1], result
+ * [2D + 1], both in ens_moments' result layout (mean, M2, n).  Synchronous, no device work.
+ * ENS_EINVAL for n_parts < 1, D < 1 or null pointers. */
+int ens_moments_combine(int n_parts, int D, const double* parts, double* result);
 
 /* Raw Philox4x32-10 words (Salmon et al. SC'11) of the SDE streams: for trajectory
  * j < n_traj and call c < n_calls, out[(c*4 + w)*n_traj + j] = word w of
@@ -428,10 +448,13 @@ int ens_probe_fma(int dtype, long long iters, int blocks, int threads, double* o
  * scratch (queue counter, cost-order permutation and keys, bucket cursors) lives in one
  * fixed device array of the library, about 6 MiB, that every GPU loading the library holds
  * until the process exits.  The first call on a device looks up that array's device address
- * (once per device): make that first call before any stream capture.  All calls share the
- * array: a call clears what must start at zero, and calls that overlap on the GPU (other
- * streams or host threads) race on it, so order them on one stream.
- * Errors: ENS_EINVAL when N > ENS_NOALLOC_MAX_N, otherwise as ens_solve. */
+ * (once per device): make that first call before any stream capture.  The address is kept for
+ * the life of the process, so a caller that destroys the device's context (cudaDeviceReset)
+ * must not call this entry point again in that process.  All calls share the array: a call
+ * clears what must start at zero, and calls that overlap on the GPU (other streams or host
+ * threads) race on it, so order them on one stream.
+ * Errors: ENS_EINVAL when N > ENS_NOALLOC_MAX_N; otherwise exactly those of ens_solve (the
+ * same argument checks run first). */
 #define ENS_NOALLOC_MAX_N 1048576LL
 int ens_solve_noalloc(int rhs_id, long long N, const void* params, const void* u0,
                       const void* tspan, const ens_opts* opts, void* out, signed char* status,

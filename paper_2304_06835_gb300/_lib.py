@@ -83,9 +83,11 @@ SIGNATURES = {
     "ens_solve": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP, _VP]),
     "ens_solve_host": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP,
                               _VP]),
+    "ens_cost_keys": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP]),
     "ens_philox4x32_10": (_INT, [_ULL, _LL, _LL, _LL, _VP, _VP]),
     "ens_normals": (_INT, [_ULL, _LL, _LL, _LL, _INT, _VP, _VP]),
     "ens_moments": (_INT, [_LL, _INT, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP]),
+    "ens_moments_combine": (_INT, [_INT, _INT, _VP, _VP]),
     "ens_solve_noalloc": (_INT, [_INT, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP,
                                  _VP]),
     "ens_autotune": (_INT, [_VP, _LL, _VP, _VP, _VP, ctypes.POINTER(EnsOpts), _VP, _VP, _VP, _VP,

@@ -121,6 +121,23 @@ cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a
   return cudaGetLastError();
 }
 
+cudaError_t launch_cost_keys(int rhs_id, int alg, int dtype, const SolveArgs& a, float* keys,
+                             cudaStream_t stream) {
+  DispatchFn f = table(rhs_id, dtype);
+  if (!f) return cudaErrorInvalidValue;
+  CostScratch cs;
+  cs.keys = keys;
+  cs.bucket = nullptr;
+  cs.hist = nullptr;
+  cs.blocks = (int)std::min<long long>(4 * 152, std::max<long long>(1, (a.N + 255) / 256));
+  cs.chunk = 0;
+  LaunchCfg cfg{};
+  bool sup = false;
+  cudaError_t e = f(alg, &a, cfg, stream, &sup, nullptr, nullptr, &cs);
+  if (e != cudaSuccess || !sup) return sup ? e : cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 // ---- random streams --------------------------------------------------------------------------
 __global__ void k_philox(unsigned long long seed, long long off, long long n_traj,
                          long long n_calls, unsigned int* out) {
@@ -611,6 +628,18 @@ int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
   *tpt = best.tpt;
   *blocks_per_sm = best.bps;
   return ENS_OK;
+}
+
+int ens_cost_keys(ens_handle* h, long long N, const void* params, const void* u0,
+                  const void* tspan, const ens_opts* o, float* keys, void* stream) {
+  int rc = validate(h, N, params, u0, tspan, o, params);
+  if (rc) return rc;
+  if (N > 0 && !keys) return fail(ENS_EINVAL, "null keys");
+  if (N == 0) return ENS_OK;
+  SolveArgs a;
+  fill_args(&a, N, params, u0, tspan, o, nullptr, nullptr, nullptr, nullptr);
+  cudaError_t e = launch_cost_keys(h->rhs_id, o->alg, o->dtype, a, keys, (cudaStream_t)stream);
+  return e == cudaSuccess ? ENS_OK : cuda_fail(e, "ens_cost_keys");
 }
 
 int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u0,

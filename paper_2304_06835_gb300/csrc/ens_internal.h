@@ -63,6 +63,7 @@ cudaError_t launch_adjoint(int which, int rhs_id, int alg, int dtype, const AdjA
 int adjoint_stages(int alg);  // stages whose inputs the reverse pass stores (0: unsupported)
 
 struct CostScratch {
+  float* keys = nullptr;   // [N]: set to write the raw cost keys instead of the buckets
   unsigned short* bucket;  // [N]
   unsigned int* hist;      // [kCostBuckets] bucket totals, then cursors
   int blocks;              // G <= kCostBlocks
@@ -90,6 +91,10 @@ constexpr int kCostBlocks = 256;
 cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a,
                               unsigned short* bucket, unsigned int* hist, int* order,
                               cudaStream_t stream);
+// The cost keys themselves: keys[i] = the expected steps of trajectory i (the key the
+// longest-first order sorts by).
+cudaError_t launch_cost_keys(int rhs_id, int alg, int dtype, const SolveArgs& a, float* keys,
+                             cudaStream_t stream);
 
 // Device scratch of one persistent solve: the queue counter, and for the longest-first order
 // the permutation [N], bucket keys [N] and the kCostBuckets bucket cursors.

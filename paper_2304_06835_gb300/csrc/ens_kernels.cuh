@@ -745,6 +745,14 @@ __global__ void k_cost_keys(const SolveArgs a, long long chunk, unsigned short* 
     if (sh[b]) atomicAdd(&tot[b], sh[b]);
 }
 
+// the keys themselves (the work estimate that balances shards across ranks)
+template <class I>
+__global__ void k_cost_values(const SolveArgs a, float* keys) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.N;
+       i += (long long)gridDim.x * blockDim.x)
+    keys[i] = I::cost_key(a, i);
+}
+
 __global__ void k_cost_scan(unsigned int* tot);
 __global__ void k_cost_scatter(long long N, long long chunk, const unsigned short* bucket,
                                unsigned int* cursor, int* order);

@@ -117,7 +117,10 @@ cudaError_t attrs_integ(const LaunchCfg& cfg, cudaFuncAttributes* attr, int* bps
 
 template <class I>
 cudaError_t cost_keys_integ(const SolveArgs& a, CostScratch* cs, cudaStream_t s) {
-  k_cost_keys<I><<<cs->blocks, 256, 0, s>>>(a, cs->chunk, cs->bucket, cs->hist);
+  if (cs->keys)
+    k_cost_values<I><<<cs->blocks, 256, 0, s>>>(a, cs->keys);
+  else
+    k_cost_keys<I><<<cs->blocks, 256, 0, s>>>(a, cs->chunk, cs->bucket, cs->hist);
   return cudaGetLastError();
 }
 

@@ -183,6 +183,20 @@ class EnsembleSolver:
         del keep
         return b.value, t.value, f.value, ms.value
 
+    def cost_keys(self, params, u0, tspan, alg="tsit5", *, layout="rowmajor", stream=None,
+                  **kw):
+        """Expected steps per trajectory (ens_cost_keys): a float32 tensor [N] on the inputs'
+        device, the work estimate that balances shards across ranks (solve_sharded)."""
+        N = params.shape[0] if layout == "rowmajor" else params.shape[-1]
+        keys = torch.empty(N, dtype=torch.float32, device=params.device)
+        o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, **kw)
+        s = (torch.cuda.current_stream(params.device).cuda_stream if stream is None
+             else stream.cuda_stream)
+        _lib.check(_lib.lib().ens_cost_keys(self._h, N, _ptr(params), _ptr(u0), _ptr(tspan),
+                                            ctypes.byref(o), _ptr(keys), ctypes.c_void_p(s)))
+        del keep
+        return keys
+
     # --------------------------------------------------------------- discrete adjoint
     def _adj_common(self, params, u0, tspan, layout):
         if not (params.is_cuda and u0.is_cuda and tspan.is_cuda):
@@ -303,12 +317,12 @@ def normals(seed, n_traj, n_per, dtype=torch.float32, index_offset=0, device="cu
     return out
 
 
-def ensemble_sums(out, status=None, *, layout="rowmajor", slot=-1, stream=None):
-    """Per-component sums over an ensemble's trajectories for moment estimation, through
-    ens_moments: a float64 tensor [2D + 1] on out's device = (S1_0..S1_{D-1}, S2_0..S2_{D-1},
-    n), S1 = sum of x, S2 = sum of x^2 at save slot `slot` (negative: from the end) of a solve
-    output (row-major [N, D] / [N, S, D], SoA [D, N] / [S, D, N]), over the trajectories with
-    status 0 (all without a status tensor)."""
+def ensemble_moments(out, status=None, *, layout="rowmajor", slot=-1, stream=None):
+    """Per-component moments of an ensemble's solution through ens_moments: a float64 tensor
+    [2D + 1] on out's device = (mean_0..mean_{D-1}, M2_0..M2_{D-1}, n), M2 = sum of squared
+    deviations from the mean, at save slot `slot` (negative: from the end) of a solve output
+    (row-major [N, D] / [N, S, D], SoA [D, N] / [S, D, N]), over the trajectories with status 0
+    (all without a status tensor)."""
     if not (out.is_cuda and out.is_contiguous()):
         raise ValueError("out must be a contiguous CUDA tensor")
     if layout == "rowmajor":
@@ -318,31 +332,52 @@ def ensemble_sums(out, status=None, *, layout="rowmajor", slot=-1, stream=None):
     slot = slot + S if slot < 0 else slot
     if status is not None and (status.dtype != torch.int8 or status.numel() != N):
         raise ValueError("status must be an int8 tensor of N entries")
-    sums = torch.empty(2 * D + 1, dtype=torch.float64, device=out.device)
+    res = torch.empty(2 * D + 1, dtype=torch.float64, device=out.device)
     scratch = torch.empty(_lib.MOMENTS_BLOCKS * (2 * D + 1), dtype=torch.float64,
                           device=out.device)
     s = stream.cuda_stream if stream is not None else torch.cuda.current_stream(out.device).cuda_stream
     _lib.check(_lib.lib().ens_moments(
         int(N), int(D), _TORCH_DT[out.dtype], _lib.LAYOUT[layout], int(S), int(slot),
-        _ptr(out), _ptr(status) if status is not None else None, _ptr(scratch), _ptr(sums),
+        _ptr(out), _ptr(status) if status is not None else None, _ptr(scratch), _ptr(res),
         ctypes.c_void_p(s)))
-    return sums
+    return res
 
 
-def combine_moments(sums, group=None):
-    """The exchange step of a sharded ensemble: add every rank's ensemble_sums (an all-reduce
-    over torch.distributed when it is initialised with more than one rank; NCCL wants the
-    tensor on the GPU, gloo on the CPU) and form (n, mean [D], variance [D]) with the
-    unbiased variance (S2 - n mean^2) / (n - 1)."""
+def gather_moments(moments, group=None):
+    """The exchange step of a sharded ensemble: every rank's ensemble_moments result, stacked
+    in rank order ([world, 2D + 1]; [1, 2D + 1] without a process group).  An all-gather over
+    torch.distributed (NCCL wants the tensor on the GPU, gloo on the CPU)."""
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
-        sums = sums.clone()
-        dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=group)
-    D = (sums.numel() - 1) // 2
-    n = sums[2 * D]
-    mean = sums[:D] / n
-    var = (sums[D:2 * D] - n * mean * mean) / (n - 1)
-    return n, mean, var
+        parts = [torch.empty_like(moments) for _ in range(dist.get_world_size(group))]
+        dist.all_gather(parts, moments.contiguous(), group=group)
+        return torch.stack(parts)
+    return moments.reshape(1, -1)
+
+
+def merge_moments(parts):
+    """Merge per-group (mean, M2, n) rows [k, 2D + 1] into the union's (n, mean [D],
+    variance [D]) with ens_moments_combine (the pairwise update, in row order); the unbiased
+    variance is M2 / (n - 1).  Raises ValueError when fewer than two trajectories count."""
+    p = np.ascontiguousarray(parts.detach().cpu().numpy() if torch.is_tensor(parts) else parts,
+                             dtype=np.float64)
+    p = p.reshape(p.shape[0] if p.ndim > 1 else 1, -1)
+    D = (p.shape[1] - 1) // 2
+    res = np.empty(2 * D + 1)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _lib.check(_lib.lib().ens_moments_combine(int(p.shape[0]), int(D), p.ctypes.data_as(dp),
+                                              res.ctypes.data_as(dp)))
+    n = res[2 * D]
+    if n < 2:
+        raise ValueError("the ensemble variance needs at least two counted trajectories "
+                         "(n = %d)" % int(n))
+    return n, res[:D], res[D:2 * D] / (n - 1)
+
+
+def combine_moments(moments, group=None):
+    """Gather every rank's ensemble_moments (gather_moments) and merge them (merge_moments):
+    (n, mean [D], unbiased variance [D]) of the whole sharded ensemble."""
+    return merge_moments(gather_moments(moments, group))
 
 
 class EnsembleBatch:

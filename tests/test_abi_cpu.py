@@ -5,6 +5,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -71,6 +72,14 @@ def test_validation_without_device(L):
                  (4, 3, 0, 0, 1, 0, p, None, None, p),  # scratch
                  (4, 3, 0, 0, 1, 0, p, None, p, None)):  # sums
         assert L.ens_moments(*args, None) == _lib.ENS_EINVAL, args
+    # ens_moments_combine(n_parts, D, parts, result): host arithmetic, runs without a GPU
+    dp = ctypes.POINTER(ctypes.c_double)
+    parts = np.array([[1.0, 2.0, 3.0], [4.0, 0.0, 1.0]])  # D = 1: (mean, M2, n) per row
+    res = np.empty(3)
+    assert L.ens_moments_combine(2, 1, parts.ctypes.data_as(dp), res.ctypes.data_as(dp)) == 0
+    np.testing.assert_allclose(res, [1.75, 2.0 + 0.0 + 9.0 * 3.0 * 1.0 / 4.0, 4.0], rtol=1e-15)
+    assert L.ens_moments_combine(0, 1, parts.ctypes.data_as(dp), res.ctypes.data_as(dp)) == 1
+    assert L.ens_moments_combine(2, 1, None, res.ctypes.data_as(dp)) == 1
 
 
 def test_product_does_not_import_oracle():

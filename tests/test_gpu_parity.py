@@ -217,9 +217,15 @@ def test_adaptive_single_step_parity(S, rhs, alg):
 def test_rosenbrock23_robertson_fp64(S):
     """Robertson at tol 1e-6 with 10 log-spaced save times.  Every trajectory must be within
     10x tol of a tol-1e-12 reference and within 10x tol of the oracle at the same tolerance.
-    (At steady state the stiff error estimate is round-off dominated, so FMA-contraction and
-    controller-rounding differences can flip accept/reject decisions: step sequences are not
-    required to be identical; the single-step test above pins each step exactly.)"""
+    At steady state the stiff error estimate is round-off dominated, so FMA-contraction and
+    controller-rounding differences can flip accept/reject decisions: at least 80 % of the
+    trajectories must take the oracle's (accepted, rejected) counts.  On those, the GPU and the
+    oracle agree to a tenth of the error the oracle itself makes against the reference (per
+    trajectory, the largest component error over the save times, in units of the tolerance:
+    4.4 to 6.9 here; the GPU - oracle difference measured 0.27 at most).  Equal counts do not
+    mean equal step sizes: the kernel forms the controller's factor in FP32, and where the
+    error estimate is round-off the step sizes drift apart within the tolerance; the
+    single-step test above pins each step exactly."""
     P, U, T = workloads.robertson_random(512, seed=31)
     tol = dict(abstol=1e-6, reltol=1e-6)
     sv = np.logspace(-4, 5, 10)
@@ -228,13 +234,21 @@ def test_rosenbrock23_robertson_fp64(S):
                                           saveat=sv, want_stats=True, **tol)
     o = host(out)
     assert int(st.abs().sum()) == 0
+    fine, _, _ = oracle.solve("robertson", "ros23", P, U, T, abstol=1e-12, reltol=1e-12,
+                              dt0=1e-8, saveat=sv)
+    unit = lambda x: x / (1e-6 + 1e-6 * np.abs(fine))
+    e_orc = unit(np.abs(ref - fine)).reshape(len(P), -1).max(axis=1)
     gs = stats.cpu().numpy().T
     same = np.all(gs[:, :2] == rst[:, :2], axis=1)
+    d = unit(np.abs(o - ref)).reshape(len(P), -1).max(axis=1)
+    print("Robertson FP64: identical counts %.3f; on those GPU - oracle %.3g tol at most, "
+          "oracle - reference %.3g..%.3g tol" % (same.mean(), d[same].max(), e_orc.min(),
+                                                 e_orc.max()))
     assert same.mean() >= 0.8, same.mean()
+    assert np.all(d[same] <= 0.1 * e_orc[same])
+    assert np.all(gs[same, 2] == rst[same, 2])
     assert np.all(np.abs(o - ref) <= 10 * (1e-6 + 1e-6 * np.abs(ref)))
-    fine, _, _ = oracle.solve("robertson", "ros23", P[:128], U[:128], T[:128], abstol=1e-12,
-                              reltol=1e-12, dt0=1e-8, saveat=sv)
-    assert np.all(np.abs(o[:128] - fine) <= 10 * (1e-6 + 1e-6 * np.abs(fine)))
+    assert np.all(np.abs(o - fine) <= 10 * (1e-6 + 1e-6 * np.abs(fine)))
     assert np.abs(o.sum(axis=2) - 1).max() < 1e-10  # y1 + y2 + y3 = 1
 
 
@@ -254,6 +268,33 @@ def test_rosenbrock23_robertson_fp32(S):
     assert np.abs(o.sum(axis=2) - 1).max() < 1e-4
 
 
+def test_rosenbrock23_robertson_fp32_against_fp32_oracle(S):
+    """FP32 against the oracle's FP32 mode at the same tolerances.  Identical step counts are
+    no criterion here: even the oracle's FP32 and FP64 modes share them on only ~5 % of the
+    trajectories (the FP32 error estimate at steady state is round-off).  The yardstick is
+    the oracle's FP64 mode at the same tolerance: per trajectory (largest component
+    difference over the save times, in units of the tolerance) the GPU's distance from the
+    FP32 oracle stays within 3x the FP64 oracle's distance from it at the median and the
+    maximum (FP64 oracle: median 0.09, max 0.28 of the tolerance)."""
+    P, U, T = workloads.robertson_random(256, seed=33)
+    P = f32(P)
+    sv = np.logspace(-4, 5, 10)
+    tol = dict(abstol=1e-8, reltol=1e-4)
+    o32, rs, _ = oracle.solve("robertson", "ros23", P, U, T, dt0=1e-4, saveat=sv,
+                              precision="f32", **tol)
+    o64, _, _ = oracle.solve("robertson", "ros23", P, U, T, dt0=1e-4, saveat=sv, **tol)
+    out, st, _ = S["robertson"].solve(dev(P, torch.float32), dev(U, torch.float32),
+                                      dev(T, torch.float32), alg="ros23", dt0=1e-4, saveat=sv,
+                                      **tol)
+    o = host(out)
+    assert int(st.abs().sum()) == 0 and np.all(rs == 0)
+    unit = lambda x: (x / (1e-8 + 1e-4 * np.abs(o32))).reshape(len(P), -1).max(axis=1)
+    d, d_ref = unit(np.abs(o - o32)), unit(np.abs(o64 - o32))
+    print("Robertson FP32: GPU - FP32 oracle median %.3g max %.3g tol; FP64 oracle - FP32 "
+          "oracle median %.3g max %.3g tol" % (np.median(d), d.max(), np.median(d_ref),
+                                               d_ref.max()))
+    assert np.median(d) <= 3 * np.median(d_ref)
+    assert d.max() <= 3 * d_ref.max()
 # ----------------------------------------------------------------------------- SDE
 def test_philox_words_bit_exact():
     from paper_2304_06835_gb300 import philox_words

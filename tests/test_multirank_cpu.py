@@ -1,7 +1,7 @@
 """The multi-rank path on CPU ranks (gloo, world size 2): each rank solves its own shard
 (weak scaling, no collective on the data path) and the job time is the maximum over the
-ranks; the reference arm prints from rank 0 only; the moment sums of sharded ensembles add up
-across the ranks (the one exchange step, an all-reduce after the solve)."""
+ranks; the reference arm prints from rank 0 only; the moments of sharded ensembles merge
+across the ranks (the one exchange step, an all-gather after the solve)."""
 import json
 import os
 import subprocess
@@ -23,12 +23,13 @@ def _rank_main(rank, world, port, q):
     import bench
     t = bench.max_over_ranks(1.0 + rank * 0.5, world)
     w = dict(bench.WORKLOADS["lorenz_adaptive_f32"], N=64)
-    P, _, _ = bench.inputs_for(w, rank)
-    q.put((rank, t, P.sum()))
+    P, _, _ = bench.inputs_for(w, rank, world)
+    wg = dict(bench.WORKLOADS["crn_em_f32"], N=64)
+    q.put((rank, t, P, bench.shard_start(wg, rank, world)))
     dist.destroy_process_group()
 
 
-def test_max_over_ranks_and_disjoint_shards_gloo():
+def test_max_over_ranks_and_shards_of_one_ensemble_gloo():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = 29500 + os.getpid() % 1000
@@ -39,9 +40,15 @@ def test_max_over_ranks_and_disjoint_shards_gloo():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    res.sort()
+    res.sort(key=lambda r: r[0])
     assert res[0][1] == res[1][1] == 1.5           # every rank sees the slowest rank's time
-    assert res[0][2] != res[1][2]                  # each rank draws its own shard
+    sys.path.insert(0, ROOT)
+    import bench
+    whole, _, _ = bench.inputs_for(dict(bench.WORKLOADS["lorenz_adaptive_f32"], N=128))
+    # the two contiguous halves of one ensemble of N x world trajectories
+    np.testing.assert_array_equal(res[0][2], whole[:64])
+    np.testing.assert_array_equal(res[1][2], whole[64:])
+    assert (res[0][3], res[1][3]) == (0, 64)        # SDE streams by the global index
 
 
 def test_reference_arm_under_torchrun_prints_once():
@@ -57,49 +64,66 @@ def test_reference_arm_under_torchrun_prints_once():
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
 
 
-def _moments_rank(rank, world, port, q):
+def _local_moments(x):
+    """A rank's (mean, M2, n) of its own shard, as ens_moments forms them on the GPU."""
+    m = x.mean(0)
+    return np.concatenate([m, ((x - m) ** 2).sum(0), [len(x)]])
+
+
+def _moments_rank(rank, world, port, q, offset):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     sys.path.insert(0, ROOT)
     from paper_2304_06835_gb300 import combine_moments
-    x = np.random.default_rng(11).lognormal(0.3, 0.8, size=(1001, 4))  # the whole ensemble
-    mine = x[rank::world]                                                # this rank's shard
-    sums = torch.tensor(np.concatenate([mine.sum(0), (mine * mine).sum(0), [len(mine)]]),
-                        dtype=torch.float64)
-    n, mean, var = combine_moments(sums)
-    q.put((rank, float(n), mean.numpy(), var.numpy()))
+    x = offset + np.random.default_rng(11).lognormal(0.3, 0.8, size=(1001, 4))  # the ensemble
+    mine = x[rank * 600:(rank + 1) * 600]                       # uneven contiguous shards
+    n, mean, var = combine_moments(torch.tensor(_local_moments(mine), dtype=torch.float64))
+    q.put((rank, float(n), np.asarray(mean), np.asarray(var)))
     dist.destroy_process_group()
 
 
-def test_moments_all_reduce_gloo():
-    """The exchange step of a sharded SDE ensemble: every rank adds the others' sums and
-    obtains the whole ensemble's count, mean and unbiased variance."""
+@pytest.mark.parametrize("offset", [0.0, 1e8])
+def test_moments_exchange_gloo(offset):
+    """The exchange step of a sharded SDE ensemble: every rank gathers the others' (mean, M2,
+    n) and merges them into the whole ensemble's count, mean and unbiased variance.  With an
+    offset of 1e8 (|mean| / std ~ 1e8) raw power sums would lose the variance entirely; the
+    merged form keeps it."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    port = 31500 + os.getpid() % 1000
-    procs = [ctx.Process(target=_moments_rank, args=(r, 2, port, q)) for r in range(2)]
+    port = 31500 + os.getpid() % 1000 + (7 if offset else 0)
+    procs = [ctx.Process(target=_moments_rank, args=(r, 2, port, q, offset)) for r in range(2)]
     for p in procs:
         p.start()
     res = [q.get(timeout=120) for _ in procs]
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    x = np.random.default_rng(11).lognormal(0.3, 0.8, size=(1001, 4))
+    x = offset + np.random.default_rng(11).lognormal(0.3, 0.8, size=(1001, 4))
     for _, n, mean, var in res:
         assert n == 1001
         np.testing.assert_allclose(mean, x.mean(0), rtol=1e-13)
-        np.testing.assert_allclose(var, x.var(0, ddof=1), rtol=1e-11)
+        np.testing.assert_allclose(var, x.var(0, ddof=1), rtol=1e-9)
 
 
-def test_combine_moments_single_process():
-    """Without a process group the sums are used as they are: count, mean and the unbiased
-    variance of the ensemble, and the input tensor is not modified."""
-    from paper_2304_06835_gb300 import combine_moments
+def test_merge_moments_single_process_and_errors():
+    """Without a process group the one rank's moments are used as they are; a merge of many
+    uneven groups in order equals the whole; fewer than two trajectories raise."""
+    from paper_2304_06835_gb300 import combine_moments, merge_moments
     x = np.random.default_rng(12).normal(2.0, 3.0, size=(777, 3))
-    sums = torch.tensor(np.concatenate([x.sum(0), (x * x).sum(0), [len(x)]]))
-    before = sums.clone()
-    n, mean, var = combine_moments(sums)
+    mom = torch.tensor(_local_moments(x))
+    before = mom.clone()
+    n, mean, var = combine_moments(mom)
     assert float(n) == 777
-    np.testing.assert_allclose(mean.numpy(), x.mean(0), rtol=1e-13)
-    np.testing.assert_allclose(var.numpy(), x.var(0, ddof=1), rtol=1e-10)
-    assert torch.equal(sums, before)
+    np.testing.assert_allclose(mean, x.mean(0), rtol=1e-13)
+    np.testing.assert_allclose(var, x.var(0, ddof=1), rtol=1e-12)
+    assert torch.equal(mom, before)
+    cuts = [0, 1, 2, 50, 51, 400, 777]
+    parts = np.stack([_local_moments(x[a:b]) for a, b in zip(cuts[:-1], cuts[1:])])
+    n2, mean2, var2 = merge_moments(parts)
+    np.testing.assert_allclose(mean2, x.mean(0), rtol=1e-13)
+    np.testing.assert_allclose(var2, x.var(0, ddof=1), rtol=1e-12)
+    empty = np.zeros((2, 7))
+    with pytest.raises(ValueError):
+        merge_moments(empty)
+    with pytest.raises(ValueError):
+        merge_moments(_local_moments(x[:1]))

@@ -153,3 +153,61 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     assert rc == _lib.ENS_EINVAL
     assert b"ENS_NOALLOC_MAX_N" in _lib.lib().ens_last_error()
     del keep
+
+
+def test_noalloc_at_its_maximum_size_allocates_nothing():
+    """N = ENS_NOALLOC_MAX_N, persistent schedule with the longest-first order (the largest
+    use of the fixed scratch: queue, permutation and bucket keys of every trajectory): equal
+    to ens_solve twice in a row, and the device's free memory is the same before and after
+    the second call (the first call may load the library's module on the device)."""
+    from paper_2304_06835_gb300 import EnsembleSolver, _lib, make_opts
+    N = 1 << 20
+    P, U, T = workloads.lorenz_random(N, seed=16, t1=1.0)
+    dt = torch.float32
+    Pd, Ud, Td = _dev(P.T, dt), _dev(U.T, dt), _dev(T.T, dt)
+    kw = dict(abstol=1e-5, reltol=1e-5, schedule="persistent", order="cost")
+    solver = EnsembleSolver("lorenz")
+    ref, ref_st, ref_stats = solver.solve(Pd, Ud, Td, alg="tsit5", layout="soa",
+                                          want_stats=True, **kw)
+    opts, keep = make_opts("tsit5", _lib.F32, "soa", **kw)
+    out = torch.empty((3, N), dtype=dt, device="cuda")
+    st = torch.empty((N,), dtype=torch.int8, device="cuda")
+    stats = torch.empty((3, N), dtype=torch.int32, device="cuda")
+    for call in range(2):
+        out.fill_(float("nan"))
+        st.fill_(-1)
+        stats.fill_(-1)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        _noalloc(_lib.RHS["lorenz"], Pd, Ud, Td, opts, out, st, stats)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        if call == 1:
+            assert free1 == free0, (free0, free1)
+        assert torch.equal(out, ref), call
+        assert torch.equal(st, ref_st), call
+        assert torch.equal(stats, ref_stats), call
+    del keep
+    solver.close()
+
+
+def test_noalloc_errors_equal_ens_solve():
+    """Invalid arguments are refused with ens_solve's own error codes: both run the same
+    checks before touching the device."""
+    from paper_2304_06835_gb300 import EnsembleSolver, _lib, make_opts
+    x = torch.zeros(64, dtype=torch.float64, device="cuda")
+    p = ctypes.c_void_p(x.data_ptr())
+    cases = [("orego", make_opts("em", _lib.F64, "soa", dt=0.1)),
+             ("crn", make_opts("tsit5", _lib.F64, "soa")),
+             ("lorenz", make_opts("tsit5", _lib.F64, "soa", blocks_per_sm=65)),
+             ("lorenz", make_opts("tsit5", _lib.F64, "soa", tpt=3)),
+             ("lorenz", make_opts("tsit5_fixed", _lib.F64, "soa", dt=-1.0))]
+    for rhs, (opts, keep) in cases:
+        s = EnsembleSolver(rhs)
+        rc_solve = _lib.lib().ens_solve(s.handle, 4, p, p, p, ctypes.byref(opts), p, None, None,
+                                        None)
+        rc_noalloc = _lib.lib().ens_solve_noalloc(_lib.RHS[rhs], 4, p, p, p, ctypes.byref(opts),
+                                                  p, None, None, None)
+        assert rc_solve != _lib.ENS_OK and rc_noalloc == rc_solve, (rhs, rc_solve, rc_noalloc)
+        s.close()
+        del keep
