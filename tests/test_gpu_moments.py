@@ -9,6 +9,8 @@
   mean and second moment of X_n lie within five standard errors of the exact moments of the
   discrete scheme, E X_n = X0 (1 + mu h)^n and E X_n^2 = X0^2 ((1 + mu h)^2 + sigma^2 h)^n.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -74,12 +76,14 @@ def test_large_mean_small_spread():
     rng = np.random.default_rng(5)
     x = 1e6 + 1e-3 * rng.normal(size=(500_001, 2))
     res = ensemble_moments(dev(x)).cpu().numpy()
-    m = x.mean(0)
-    m2 = ((x - m) ** 2).sum(0)
-    np.testing.assert_allclose(res[:2], m, rtol=1e-15)
+    # exactly rounded references (NumPy's column mean of a row-major array adds in sequence
+    # and is ~20 ulp off here)
+    m = np.array([math.fsum(x[:, j]) / len(x) for j in range(2)])
+    m2 = np.array([math.fsum((x[:, j] - m[j]) ** 2) for j in range(2)])
+    np.testing.assert_allclose(res[:2], m, rtol=3e-16)
     np.testing.assert_allclose(res[2:4], m2, rtol=1e-9)
     n, mean, var = merge_moments(res)
-    np.testing.assert_allclose(var, x.var(0, ddof=1), rtol=1e-9)
+    np.testing.assert_allclose(var, m2 / (len(x) - 1), rtol=1e-9)
 
 
 def test_gbm_moments_match_the_discrete_scheme():
