@@ -16,7 +16,8 @@ Identifiers (the same numbers as the public C-ABI, by documentation):
           adaptive Tsit5 only),
         6 Oregonator (D=3, P=3: k1, k2, k3), 7 HIRES (D=8, P=12: its distinct rate constants),
         8 POLLU (D=20, P=25: k1..k25) -- the paper's stiff test models
-  alg:  1 Tsit5 fixed, 2 Tsit5 adaptive, 3 RK4, 4 Rosenbrock23, 5 Euler-Maruyama
+  alg:  1 Tsit5 fixed, 2 Tsit5 adaptive, 3 RK4, 4 Rosenbrock23, 5 Euler-Maruyama,
+        6 Rodas4, 7 Rodas5P (stiffly accurate Rosenbrock 4(3) and 5(4))
 """
 from __future__ import annotations
 
@@ -35,7 +36,7 @@ _lib = None
 
 RHS = {"lorenz": 1, "robertson": 2, "gbm": 3, "crn": 4, "ball": 5, "orego": 6, "hires": 7,
        "pollu": 8}
-ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5}
+ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5, "rodas4": 6, "rodas5p": 7}
 DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2), 4: (4, 6), 5: (2, 2), 6: (3, 3), 7: (8, 12),
         8: (20, 25)}
 NOISE = {1: 0, 2: 0, 3: 1, 4: 8, 5: 0, 6: 0, 7: 0, 8: 0}  # Wiener processes per model
@@ -124,6 +125,8 @@ def _bind(L):
     L.oracle_step.restype = ctypes.c_int
     L.oracle_step.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
                               ctypes.c_double, ctypes.c_double, dp, dp]
+    L.oracle_rosenbrock_tableau.restype = ctypes.c_int
+    L.oracle_rosenbrock_tableau.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
     L.oracle_tsit5_tableau.restype = None
     L.oracle_tsit5_tableau.argtypes = [dp, dp, dp, dp]
     L.oracle_rhs.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
@@ -263,6 +266,21 @@ def tsit5_tableau():
     bh = np.empty(7)
     lib().oracle_tsit5_tableau(_dp(c), _dp(A), _dp(b), _dp(bh))
     return c, A, b, bh
+
+
+def rosenbrock_tableau(alg):
+    """Standard-form coefficients of Rodas4 / Rodas5P as the oracle steps them:
+    (gamma, alpha [s,s], Gamma [s,s] with gamma on the diagonal, b [s], bhat [s])."""
+    alg_id = ALG[alg] if isinstance(alg, str) else int(alg)
+    g = ctypes.c_double()
+    A = np.empty(64)
+    G = np.empty(64)
+    b = np.empty(8)
+    bh = np.empty(8)
+    s = lib().oracle_rosenbrock_tableau(alg_id, ctypes.byref(g), _dp(A), _dp(G), _dp(b), _dp(bh))
+    if s < 0:
+        raise ValueError("not a Rodas method")
+    return g.value, A.reshape(8, 8)[:s, :s], G.reshape(8, 8)[:s, :s], b[:s], bh[:s]
 
 
 def rhs_eval(rhs, u, p, t=0.0):

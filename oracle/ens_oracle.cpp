@@ -48,7 +48,10 @@ enum {
   RHS_LORENZ = 1, RHS_ROBERTSON = 2, RHS_GBM = 3, RHS_CRN = 4, RHS_BALL = 5,
   RHS_OREGO = 6, RHS_HIRES = 7, RHS_POLLU = 8
 };
-enum { ALG_TSIT5_FIXED = 1, ALG_TSIT5_ADAPTIVE = 2, ALG_RK4 = 3, ALG_ROS23 = 4, ALG_EM = 5 };
+enum {
+  ALG_TSIT5_FIXED = 1, ALG_TSIT5_ADAPTIVE = 2, ALG_RK4 = 3, ALG_ROS23 = 4, ALG_EM = 5,
+  ALG_RODAS4 = 6, ALG_RODAS5P = 7
+};
 enum { ST_OK = 0, ST_MAXITERS = 1, ST_DT_MIN = 2, ST_NONFINITE = 3 };
 enum { LAYOUT_ROWMAJOR = 0, LAYOUT_SOA = 1 };
 constexpr int MAXD = 20, MAXP = 25;  // largest model: POLLU (D = 20, P = 25)
@@ -656,6 +659,159 @@ void ros23_step(int id, int D, const T* u, const T* p, T t, T h, const T* f0, T*
 }
 
 // ----------------------------------------------------------------------------------------------
+// Rodas4 and Rodas5P (Sec. 5.2.1: GPURodas4 after Hairer-Wanner, GPURodas5P after Steinebach
+// 2023), stiffly accurate Rosenbrock methods of orders 4(3) and 5(4).  They are stepped here in
+// the standard form of Hairer-Wanner II, IV.7 for an autonomous f:
+//   W = I - h gamma J,   W k_i = h f(y + sum_{j<i} alpha_ij k_j) + h J sum_{j<i} gamma_ij k_j,
+//   y_{n+1} = y + sum_j b_j k_j,   yhat = y + sum_j bhat_j k_j,   E = y_{n+1} - yhat.
+// The publications give the coefficients for the transformed stages u_i = sum_{j<=i} gamma_ij k_j:
+// gamma, a_ij (stage arguments y + sum a_ij u_j) and c_ij (the right-hand sides
+// f(...) + sum (c_ij / h) u_j).  With Gamma = (gamma_ij) (gamma on the diagonal) and
+// C = (c_ij), Gamma^{-1} = diag(1/gamma) - C and alpha = A Gamma.  Both methods are stiffly
+// accurate: the last stage's argument is the embedded solution and y_{n+1} adds u_s, so
+// bhat = row s of alpha and b = row s of (alpha + Gamma).
+struct RosTab {
+  int s = 0;
+  double gamma = 0;
+  double alpha[8][8] = {}, G[8][8] = {}, b[8] = {}, bhat[8] = {};
+};
+
+// transformed coefficients (a, c) -> standard form, as described above
+RosTab ros_convert(int s, double gamma, const double (*a)[8], const double (*c)[8]) {
+  RosTab t;
+  t.s = s;
+  t.gamma = gamma;
+  // Gamma = (diag(1/gamma) - C)^{-1}: lower triangular, by forward substitution per column
+  double Ginv[8][8] = {};
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) Ginv[i][j] = (i == j) ? 1.0 / gamma : (j < i ? -c[i][j] : 0.0);
+  for (int col = 0; col < s; ++col)
+    for (int i = 0; i < s; ++i) {
+      double v = (i == col) ? 1.0 : 0.0;
+      for (int j = 0; j < i; ++j) v -= Ginv[i][j] * t.G[j][col];
+      t.G[i][col] = v / Ginv[i][i];
+    }
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      double v = 0;
+      for (int k = 0; k < s; ++k) v += a[i][k] * t.G[k][j];
+      t.alpha[i][j] = v;
+    }
+  for (int j = 0; j < s; ++j) {
+    t.bhat[j] = t.alpha[s - 1][j];
+    t.b[j] = t.alpha[s - 1][j] + t.G[s - 1][j];
+  }
+  return t;
+}
+
+// Rodas4: Hairer & Wanner, Solving ODEs II (RODAS, 6 stages); stage 6 adds u_5 to stage 5's
+// argument (c_5 = c_6 = 1)
+RosTab make_rodas4() {
+  double a[8][8] = {}, c[8][8] = {};
+  a[1][0] = 1.544;
+  a[2][0] = 0.9466785280815826; a[2][1] = 0.2557011698983284;
+  a[3][0] = 3.314825187068521; a[3][1] = 2.896124015972201; a[3][2] = 0.9986419139977817;
+  a[4][0] = 1.221224509226641; a[4][1] = 6.019134481288629; a[4][2] = 12.53708332932087;
+  a[4][3] = -0.6878860361058950;
+  for (int j = 0; j < 4; ++j) a[5][j] = a[4][j];
+  a[5][4] = 1.0;
+  c[1][0] = -5.6688;
+  c[2][0] = -2.430093356833875; c[2][1] = -0.2063599157091915;
+  c[3][0] = -0.1073529058151375; c[3][1] = -9.594562251023355; c[3][2] = -20.47028614809616;
+  c[4][0] = 7.496443313967647; c[4][1] = -10.24680431464352; c[4][2] = -33.99990352819905;
+  c[4][3] = 11.70890893206160;
+  c[5][0] = 8.083246795921522; c[5][1] = -7.981132988064893; c[5][2] = -31.52159432874371;
+  c[5][3] = 16.31930543123136; c[5][4] = -6.058818238834054;
+  return ros_convert(6, 0.25, a, c);
+}
+
+// Rodas5P: Steinebach (2023), 8 stages; stages 7 and 8 each add the previous stage's u to the
+// argument before them (c_6 = c_7 = c_8 = 1)
+RosTab make_rodas5p() {
+  double a[8][8] = {}, c[8][8] = {};
+  a[1][0] = 3.0;
+  a[2][0] = 2.849394379747939; a[2][1] = 0.45842242204463923;
+  a[3][0] = -6.954028509809101; a[3][1] = 2.489845061869568; a[3][2] = -10.358996098473584;
+  a[4][0] = 2.8029986275628964; a[4][1] = 0.5072464736228206; a[4][2] = -0.3988312541770524;
+  a[4][3] = -0.04721187230404641;
+  a[5][0] = -7.502846399306121; a[5][1] = 2.561846144803919; a[5][2] = -11.627539656261098;
+  a[5][3] = -0.18268767659942256; a[5][4] = 0.030198172008377946;
+  for (int j = 0; j < 5; ++j) a[6][j] = a[5][j];
+  a[6][5] = 1.0;
+  for (int j = 0; j < 6; ++j) a[7][j] = a[6][j];
+  a[7][6] = 1.0;
+  c[1][0] = -14.155112264123755;
+  c[2][0] = -17.97296035885952; c[2][1] = -2.859693295451294;
+  c[3][0] = 147.12150275711716; c[3][1] = -1.41221402718213; c[3][2] = 71.68940251302358;
+  c[4][0] = 165.43517024871676; c[4][1] = -0.4592823456491126; c[4][2] = 42.90938336958603;
+  c[4][3] = -5.961986721573306;
+  c[5][0] = 24.854864614690072; c[5][1] = -3.0009227002832186; c[5][2] = 47.4931110020768;
+  c[5][3] = 5.5814197821558125; c[5][4] = -0.6610691825249471;
+  c[6][0] = 30.91273214028599; c[6][1] = -3.1208243349937974; c[6][2] = 77.79954646070892;
+  c[6][3] = 34.28646028294783; c[6][4] = -19.097331116725623; c[6][5] = -28.087943162872662;
+  c[7][0] = 37.80277123390563; c[7][1] = -3.2571969029072276; c[7][2] = 112.26918849496327;
+  c[7][3] = 66.9347231244047; c[7][4] = -40.06618937091002; c[7][5] = -54.66780262877968;
+  c[7][6] = -9.48861652309627;
+  return ros_convert(8, 0.21193756319429014, a, c);
+}
+
+const RosTab& ros_tab(int alg) {
+  static const RosTab r4 = make_rodas4(), r5 = make_rodas5p();
+  return alg == ALG_RODAS4 ? r4 : r5;
+}
+
+// One Rodas4 / Rodas5P step from u with f0 = f(u) (the first stage's f).  Fills unew = y_{n+1},
+// err = E and f1 = f(unew) (the next step's f0).
+template <class T>
+void rodas_step(int alg, int id, int D, const T* u, const T* p, T t, T h, const T* f0, T* unew,
+                T* err, T* f1) {
+  const RosTab& tb = ros_tab(alg);
+  const int s = tb.s;
+  T J[MAXD * MAXD], W[MAXD * MAXD];
+  int piv[MAXD];
+  jac_u<T>(id, u, p, t, J);
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c)
+      W[r * D + c] = (r == c ? T(1) : T(0)) - h * T(tb.gamma) * J[r * D + c];
+  lu_factor<T>(D, W, piv);
+  T k[8][MAXD];
+  for (int i = 0; i < s; ++i) {
+    T g[MAXD], fi[MAXD], v[MAXD], r[MAXD];
+    for (int j = 0; j < D; ++j) {
+      g[j] = u[j];
+      v[j] = T(0);
+      for (int l = 0; l < i; ++l) {
+        g[j] += T(tb.alpha[i][l]) * k[l][j];
+        v[j] += T(tb.G[i][l]) * k[l][j];
+      }
+    }
+    if (i == 0) {
+      for (int j = 0; j < D; ++j) fi[j] = f0[j];
+    } else {
+      rhs<T>(id, g, p, t, fi);  // autonomous models: the stage time does not enter f
+    }
+    for (int row = 0; row < D; ++row) {
+      T Jv = T(0);
+      for (int c = 0; c < D; ++c) Jv += J[row * D + c] * v[c];
+      r[row] = h * fi[row] + h * Jv;
+    }
+    lu_solve<T>(D, W, piv, r, k[i]);
+  }
+  for (int j = 0; j < D; ++j) {
+    T y1 = u[j], yh = u[j];
+    for (int l = 0; l < s; ++l) {
+      y1 += T(tb.b[l]) * k[l][j];
+      yh += T(tb.bhat[l]) * k[l][j];
+    }
+    unew[j] = y1;
+    err[j] = y1 - yh;
+  }
+  rhs<T>(id, unew, p, t + h, f1);
+}
+
+bool is_rosenbrock(int alg) { return alg == ALG_ROS23 || alg == ALG_RODAS4 || alg == ALG_RODAS5P; }
+
+// ----------------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 Philox S-box with a Weyl key
 // schedule.  Round: (c0,c1,c2,c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)).
 void philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
@@ -849,8 +1005,12 @@ template <class T>
 void solve_adaptive(Traj<T>& tr) {
   const Opts& o = *tr.o;
   const int D = o.D;
-  const bool is_r23 = (o.alg == ALG_ROS23);
-  const int k_ord = is_r23 ? 3 : 5;  // exponent denominators of the controller
+  // Rosenbrock methods (no dense output, no events); the controller's exponent denominator k
+  // is the error estimate's order + 1: Tsit5 5(4) and Rodas5P 5(4): 5, Rodas4 4(3): 4,
+  // Rosenbrock23 2(3): 3; the starting step uses the order of the advancing solution
+  const bool is_ros = is_rosenbrock(o.alg);
+  const int k_ord = o.alg == ALG_ROS23 ? 3 : o.alg == ALG_RODAS4 ? 4 : 5;
+  const int p_ord = o.alg == ALG_ROS23 ? 2 : o.alg == ALG_RODAS4 ? 4 : 5;
   const T beta1 = T(0.7 / k_ord), beta2 = T(0.4 / k_ord), rej_exp = T(1.0 / k_ord);
   const T atol = T(o.abstol), rtol = T(o.reltol);
   const int S = o.n_save;  // number of save times (0: final state only)
@@ -868,11 +1028,11 @@ void solve_adaptive(Traj<T>& tr) {
   tr.fevals += 1;
   T h;
   if (o.dt0 > 0) h = T(o.dt0);
-  else h = initial_step<T>(o, tr.u, tr.p, tr.t0, fcur, is_r23 ? 2 : 5, &tr.fevals);
+  else h = initial_step<T>(o, tr.u, tr.p, tr.t0, fcur, p_ord, &tr.fevals);
   T qold = T(QOLD_INIT);
   long long attempts = 0;
-  const bool dense = o.dense && !is_r23 && save_mode;
-  const bool ev = has_event(o.rhs) && !is_r23;
+  const bool dense = o.dense && !is_ros && save_mode;
+  const bool ev = has_event(o.rhs) && !is_ros;
   long long events = 0;
   if (tr.rec_t) tr.record(tr.t0);  // entry 0: the initial state
   if (dense)  // save times equal to t0 take u0; the steps then run to tf uncut
@@ -910,9 +1070,12 @@ void solve_adaptive(Traj<T>& tr) {
       break;
     }
     T unew[MAXD], err[MAXD], fnew[MAXD], kst[7][MAXD];
-    if (is_r23) {
+    if (o.alg == ALG_ROS23) {
       ros23_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew);
       tr.fevals += 2;
+    } else if (is_ros) {  // Rodas4 / Rodas5P: stages 2..s and f(u_{n+1})
+      rodas_step<T>(o.alg, o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew);
+      tr.fevals += ros_tab(o.alg).s;
     } else {
       tsit5_step<T>(o.rhs, D, tr.u, tr.p, tnow, hs, fcur, unew, err, fnew,
                     (dense || ev) ? kst : nullptr);
@@ -1010,7 +1173,7 @@ void solve_range(const Opts& o, int layout, long long N, long long i0, long long
       tr.rec_t = rt.data();
       tr.rec_u = ru.data();
     }
-    if (o.alg == ALG_TSIT5_ADAPTIVE || o.alg == ALG_ROS23) solve_adaptive<T>(tr);
+    if (o.alg == ALG_TSIT5_ADAPTIVE || is_rosenbrock(o.alg)) solve_adaptive<T>(tr);
     else solve_fixed<T>(tr, uint64_t(o.index_offset + i));
     if (cap > 0) {  // row-major [N][cap] / [N][cap][D]; unused entries NaN
       const long long n = std::min<long long>(tr.accepted + 1, cap);
@@ -1075,9 +1238,10 @@ int oracle_solve(int rhs_id, int alg, int precision, int layout, long long N,
                  long long index_offset, double* out, signed char* status, long long* stats,
                  int nthreads, int dense, double dtmax, long long* events) {
   Model m = model_of(rhs_id);
-  if (m.D == 0 || N < 0 || alg < 1 || alg > 5) return -1;
+  if (m.D == 0 || N < 0 || alg < 1 || alg > 7) return -1;
   if (alg == ALG_EM && m.Mw == 0) return -1;  // Euler-Maruyama needs an SDE model
   if (rhs_id == RHS_CRN && alg != ALG_EM) return -1;
+  if (is_rosenbrock(alg) && rhs_id == RHS_BALL) return -1;  // no Jacobian
   if (has_event(rhs_id) && alg != ALG_TSIT5_ADAPTIVE) return -1;  // events need the interpolant
   if (precision < 0 || precision > 2) return -1;
   Opts o{rhs_id, alg, m.D, m.P, m.Mw, dt, abstol, reltol, dt0, maxiters, saveat, n_save, seed,
@@ -1102,7 +1266,7 @@ int oracle_solve_steps(int rhs_id, int alg, int precision, long long N, const do
                        long long* rec_n, int nthreads) {
   Model m = model_of(rhs_id);
   if (m.D == 0 || N < 0 || cap < 1) return -1;
-  if (alg != ALG_TSIT5_ADAPTIVE && alg != ALG_ROS23) return -1;
+  if (alg != ALG_TSIT5_ADAPTIVE && !is_rosenbrock(alg)) return -1;
   if (rhs_id == RHS_CRN || (has_event(rhs_id) && alg != ALG_TSIT5_ADAPTIVE)) return -1;
   if (precision < 0 || precision > 1) return -1;
   Opts o{rhs_id, alg, m.D, m.P, m.Mw, 0.0, abstol, reltol, dt0, maxiters, nullptr, 0, 0, 0,
@@ -1124,7 +1288,7 @@ int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t,
                 double z, double* unew, double* err) {
   Model m = model_of(rhs_id);
   if (m.D == 0) return -1;
-  if (alg == ALG_ROS23 && (rhs_id == RHS_CRN || rhs_id == RHS_BALL)) return -1;  // no Jacobian
+  if (is_rosenbrock(alg) && (rhs_id == RHS_CRN || rhs_id == RHS_BALL)) return -1;  // no Jacobian
   double e[MAXD] = {0}, fx[MAXD], k1[MAXD];
   if (alg == ALG_TSIT5_FIXED || alg == ALG_TSIT5_ADAPTIVE) {
     rhs<double>(rhs_id, u, p, t, k1);
@@ -1134,6 +1298,9 @@ int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t,
   } else if (alg == ALG_ROS23) {
     rhs<double>(rhs_id, u, p, t, k1);
     ros23_step<double>(rhs_id, m.D, u, p, t, h, k1, unew, e, fx);
+  } else if (alg == ALG_RODAS4 || alg == ALG_RODAS5P) {
+    rhs<double>(rhs_id, u, p, t, k1);
+    rodas_step<double>(alg, rhs_id, m.D, u, p, t, h, k1, unew, e, fx);
   } else if (alg == ALG_EM) {
     if (rhs_id != RHS_GBM) return -1;
     double a[MAXD], b[MAXD];
@@ -1155,6 +1322,25 @@ void oracle_pollu_reaction_sum(const double* y, const double* k, double* dy) {
 void oracle_tsit5_dense(double* r) {
   for (int i = 0; i < 7; ++i)
     for (int q = 0; q < 4; ++q) r[i * 4 + q] = TS_DENSE[i][q];
+}
+
+// The standard-form coefficients the oracle steps Rodas4 (alg 6) / Rodas5P (alg 7) with:
+// returns s and fills gamma, alpha[s][s], Gamma[s][s] (gamma on the diagonal), b[s], bhat[s]
+// (arrays of 8 x 8 / 8 entries, row-major with stride 8); -1 for another alg.
+int oracle_rosenbrock_tableau(int alg, double* gamma, double* alpha, double* G, double* b,
+                              double* bhat) {
+  if (alg != ALG_RODAS4 && alg != ALG_RODAS5P) return -1;
+  const RosTab& t = ros_tab(alg);
+  *gamma = t.gamma;
+  for (int i = 0; i < 8; ++i) {
+    b[i] = t.b[i];
+    bhat[i] = t.bhat[i];
+    for (int j = 0; j < 8; ++j) {
+      alpha[i * 8 + j] = t.alpha[i][j];
+      G[i * 8 + j] = t.G[i][j];
+    }
+  }
+  return t.s;
 }
 
 void oracle_tsit5_tableau(double* c, double* A, double* b, double* bhat) {
