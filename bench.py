@@ -61,20 +61,27 @@ SM_MAX_MHZ = 2070.0
 #   three solves (3 D^2), the stage combinations, error and norm (~18 D), the Jacobian and
 #   two f evaluations (model terms): Robertson 140; Orego 140; HIRES (D = 8: 171 + 192 + 64 +
 #   144 + 70) 640; POLLU (D = 20: 2667 + 1200 + 400 + 360 + 300) 4930.
+# Rosenbrock attempts on Robertson, measured: ncu's FP64 instruction classes (DFMA + DADD +
+#   DMUL, N = 65,536 of the bench distribution, tol 1e-6) over the solve's attempts give 122
+#   (Rosenbrock23), 242 (Rodas4, S = 6) and 337 (Rodas5P, S = 8) per attempt -- below the
+#   operation models (140, 294, 418: J, W, LU, S solves, S f evaluations, stage sums, error
+#   and norm), which counted constant-zero and folded terms; the measured counts are used.
+#   POLLU (D = 20) under Rodas5P, from the model: LU 2667, W 400, 8 solves x 400,
+#   8 f evaluations x 90, stage combinations 20 x 64, error and norm 300 -> 8567.
 # Bouncing ball (D = 2, f costs nothing): a Tsit5 attempt = stage combinations 54, error 14,
 #   norm 13, controller 3 -> 84; each accepted step adds the event scan: the dense
 #   polynomial 4 x 7 x 2 FMA + 8 scalings = 64 and 9 checkpoints x 8 = 72 -> 136.
-OPS_PER_ATTEMPT = {"tsit5": 175, "tsit5_fixed": 117, "rk4": 48, "ros23": 140, "em": 25,
+OPS_PER_ATTEMPT = {"tsit5": 175, "tsit5_fixed": 117, "rk4": 48, "ros23": 122, "em": 25,
                    "adjoint": 423, "crn_em": 224, "crn_em_f64": 104, "ball": 84,
                    "ball_event_scan": 136, "ros23_orego": 140, "ros23_hires": 640,
-                   "ros23_pollu": 4930}
+                   "ros23_pollu": 4930, "rodas4": 242, "rodas5p": 337, "rodas5p_pollu": 8567}
 
 
 def ops_key(w):
     if w["rhs"] == "crn":
         return "crn_em_f64" if w["dtype"] == "f64" else "crn_em"
     if w["rhs"] in ("orego", "hires", "pollu"):
-        return "ros23_" + w["rhs"]
+        return w["alg"] + "_" + w["rhs"]
     return w["alg"]
 
 WORKLOADS = {
@@ -87,6 +94,12 @@ WORKLOADS = {
                              N=1 << 20, t1=1.0, dt=1e-3, steps=300),
     "robertson_ros23_f64": dict(kind="solve", rhs="robertson", alg="ros23", dtype="f64",
                                 N=1 << 18, t1=1e5, tol=1e-6, dt0=1e-4, steps=20),
+    "robertson_rodas4_f64": dict(kind="solve", rhs="robertson", alg="rodas4", dtype="f64",
+                                 N=1 << 18, t1=1e5, tol=1e-6, dt0=1e-4, steps=20),
+    "robertson_rodas5p_f64": dict(kind="solve", rhs="robertson", alg="rodas5p", dtype="f64",
+                                  N=1 << 18, t1=1e5, tol=1e-6, dt0=1e-4, steps=20),
+    "pollu_rodas5p_f64": dict(kind="solve", rhs="pollu", alg="rodas5p", dtype="f64", N=8192,
+                              t1=60.0, tol=1e-6, steps=5),
     "lorenz_dense_f32": dict(kind="solve", rhs="lorenz", alg="tsit5", dtype="f32", N=1 << 20,
                              t1=10.0, tol=1e-5, saves=256, dense=True, layout="rowmajor",
                              steps=200),
@@ -1141,7 +1154,8 @@ def main():
         rate, sample, nt, ostats = oracle_rate(w)
         line["cpu_baseline"] = {"value": rate, "unit": "trajectories/s", "cores": nt,
                                 "kind": "oracle", "sample": sample}
-        if ostats is not None and w["kind"] == "solve" and w["alg"] in ("tsit5", "ros23"):
+        if ostats is not None and w["kind"] == "solve" and w["alg"] in ("tsit5", "ros23", "rodas4",
+                                                                            "rodas5p"):
             # the roofline's numerator counts the GPU's own attempts: the oracle (FP64, the
             # same tolerance) counts them on the same trajectories
             n = len(ostats)

@@ -83,8 +83,18 @@ enum { ENS_RHS_LORENZ = 1, ENS_RHS_ROBERTSON = 2, ENS_RHS_GBM = 3, ENS_RHS_CRN =
  *   EM             Euler-Maruyama, fixed step, X += a h + sum_m b_m sqrt(h) Z_{k,m} over the
  *                  model's M Wiener processes (diagonal noise for GBM, M = 1; non-diagonal
  *                  for the CRN, M = 8) (GPUEM, Sec. 5.2.2; Sec. 3.3).  Z_{k,m} is normal
- *                  number k*M + m of the trajectory's Philox stream (see ens_normals). */
-enum { ENS_TSIT5_FIXED = 1, ENS_TSIT5_ADAPTIVE = 2, ENS_RK4 = 3, ENS_ROS23 = 4, ENS_EM = 5 };
+ *                  number k*M + m of the trajectory's Philox stream (see ens_normals).
+ *   RODAS4         Rodas4, the stiffly accurate 4(3) Rosenbrock method of Hairer and Wanner
+ *                  (GPURodas4, Sec. 5.2.1; Sec. 3.2.1), 6 stages, one LU of W = I - h gamma J
+ *                  per attempt; adaptive with the PI control of TSIT5_ADAPTIVE (k = 4)
+ *   RODAS5P        Rodas5P, Steinebach's stiffly accurate 5(4) Rosenbrock method (GPURodas5P,
+ *                  Sec. 5.2.1), 8 stages; adaptive (k = 5).
+ * The Rosenbrock methods save at save times by stepping onto them (no interpolation) and need
+ * a model with a Jacobian (not the CRN or the bouncing ball). */
+enum {
+  ENS_TSIT5_FIXED = 1, ENS_TSIT5_ADAPTIVE = 2, ENS_RK4 = 3, ENS_ROS23 = 4, ENS_EM = 5,
+  ENS_RODAS4 = 6, ENS_RODAS5P = 7
+};
 
 /* element type of every floating-point array of a call */
 enum { ENS_F32 = 0, ENS_F64 = 1 };
@@ -117,7 +127,7 @@ enum {
 #define ENS_MAX_SAVE 256
 
 typedef struct {
-  int alg;                /* ENS_TSIT5_FIXED ... ENS_EM */
+  int alg;                /* ENS_TSIT5_FIXED ... ENS_RODAS5P */
   int dtype;              /* ENS_F32 / ENS_F64 */
   int layout;             /* ENS_LAYOUT_* */
   double dt;              /* fixed-step size (TSIT5_FIXED, RK4, EM), > 0 */

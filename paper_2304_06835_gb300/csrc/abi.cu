@@ -293,7 +293,8 @@ int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
                   const void* tspan, const ens_opts* o, const void* out) {
   if (!o) return fail(ENS_EINVAL, "null options");
   if (N < 0) return fail(ENS_EINVAL, "N < 0");
-  if (o->alg < ENS_TSIT5_FIXED || o->alg > ENS_EM) return fail(ENS_EINVAL, "unknown algorithm");
+  if (o->alg < ENS_TSIT5_FIXED || o->alg > ENS_RODAS5P)
+    return fail(ENS_EINVAL, "unknown algorithm");
   if (o->dtype != ENS_F32 && o->dtype != ENS_F64) return fail(ENS_EINVAL, "unknown dtype");
   if (o->layout != ENS_LAYOUT_ROWMAJOR && o->layout != ENS_LAYOUT_SOA)
     return fail(ENS_EINVAL, "unknown layout");
@@ -303,8 +304,9 @@ int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
     return fail(ENS_EINVAL, "the CRN model takes Euler-Maruyama only");
   if (rhs_id == ENS_RHS_BALL && o->alg != ENS_TSIT5_ADAPTIVE)
     return fail(ENS_EINVAL, "the bouncing ball's events need adaptive Tsit5");
-  if ((rhs_id == ENS_RHS_HIRES || rhs_id == ENS_RHS_POLLU) && o->alg != ENS_ROS23)
-    return fail(ENS_EINVAL, "HIRES and POLLU take Rosenbrock23 only");
+  if ((rhs_id == ENS_RHS_HIRES || rhs_id == ENS_RHS_POLLU) && o->alg != ENS_ROS23 &&
+      o->alg != ENS_RODAS4 && o->alg != ENS_RODAS5P)
+    return fail(ENS_EINVAL, "HIRES and POLLU take the Rosenbrock methods only");
   if (rhs_id == ENS_RHS_OREGO && o->alg == ENS_EM)
     return fail(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM, CRN)");
   if (!std::isfinite(o->dtmax)) return fail(ENS_EINVAL, "dtmax not finite");

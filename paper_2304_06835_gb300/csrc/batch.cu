@@ -67,7 +67,7 @@ LaunchCfg resolve_launch(int rhs_id, long long N, const ens_opts* o, int num_sms
 }
 
 bool one_per_thread(const ens_opts* o) {
-  return o->alg == ENS_ROS23 ||
+  return o->alg == ENS_ROS23 || o->alg == ENS_RODAS4 || o->alg == ENS_RODAS5P ||
          (o->alg == ENS_TSIT5_ADAPTIVE && ((o->dense && o->n_save > 0) || o->step_cap > 0));
 }
 

@@ -719,6 +719,43 @@ struct LUDyn {
   }
 };
 
+// W = I - hg J for a Rosenbrock step (hg = h times the method's diagonal coefficient), factored
+// into lu: J and W in registers for small D, all in the one local-memory matrix for large D (a
+// thread's footprint stays D^2 values, so the resident threads' matrices fit in L1).
+template <class RHS, class T, class LUT>
+__device__ __forceinline__ void ros_factor(const T* u, const T* p, T t, T hg, LUT& lu) {
+  constexpr int D = RHS::D;
+  typedef M<T> m;
+  if constexpr (D < 12) {
+    T Jf[D * D];
+    RHS::jac(u, p, t, Jf);
+    T W[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) W[r][c] = m::fma(-hg, Jf[r * D + c], (r == c) ? T(1) : T(0));
+    if constexpr (D < 8) {
+      lu.factor(W);
+    } else {
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) lu.a[r][c] = W[r][c];
+      lu.factor();
+    }
+  } else {
+    RHS::jac(u, p, t, &lu.a[0][0]);
+#pragma unroll 1
+    for (int r = 0; r < D; ++r)
+#pragma unroll 1
+      for (int c = 0; c < D; ++c) lu.a[r][c] = m::fma(-hg, lu.a[r][c], (r == c) ? T(1) : T(0));
+    lu.factor();
+  }
+}
+
+template <class T, int D>
+using RosLU = typename std::conditional<(D < 8), LU<T, D>, LUDyn<T, D>>::type;
+
 // One Rosenbrock23 (ode23s) step from (u, t) with f0 = f(u, t); W = I - h d J:
 //   k1 = W^-1 f0,  f1 = f(u + h/2 k1),  k2 = W^-1 (f1 - k1) + k1,  u_{n+1} = u + h k2,
 //   f2 = f(u_{n+1}),  k3 = W^-1 (f2 - e32 (k2 - f1) - 2 (k1 - f0)),  err = h/6 (k1 - 2 k2 + k3).
@@ -732,34 +769,8 @@ __device__ __forceinline__ void ros23_step(const T* u, const T* p, T t, T h, con
   const T d = T(0.29289321881345247559915563789515);   // 1 / (2 + sqrt 2)
   const T e32 = T(7.4142135623730950488016887242097);  // 6 + sqrt 2
   const T hd = h * d;
-  typename std::conditional<(D < 8), LU<T, D>, LUDyn<T, D>>::type lu;
-  if constexpr (D < 12) {  // J and W in registers, copied into the factorisation
-    T Jf[D * D];
-    RHS::jac(u, p, t, Jf);
-    T W[D][D];
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) W[r][c] = m::fma(-hd, Jf[r * D + c], (r == c) ? T(1) : T(0));
-    if constexpr (D < 8) {
-      lu.factor(W);
-    } else {
-#pragma unroll
-      for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int c = 0; c < D; ++c) lu.a[r][c] = W[r][c];
-      lu.factor();
-    }
-  } else {
-    // J, then W = I - h d J, then its LU, all in the one local-memory matrix (a thread's
-    // footprint stays D^2 values, so the resident threads' matrices fit in L1)
-    RHS::jac(u, p, t, &lu.a[0][0]);
-#pragma unroll 1
-    for (int r = 0; r < D; ++r)
-#pragma unroll 1
-      for (int c = 0; c < D; ++c) lu.a[r][c] = m::fma(-hd, lu.a[r][c], (r == c) ? T(1) : T(0));
-    lu.factor();
-  }
+  RosLU<T, D> lu;
+  ros_factor<RHS, T>(u, p, t, hd, lu);
   T k1[D], k2[D], k3[D], f1[D], U[D], v[D];
   lu.solve(f0, k1);
   const T hh = T(0.5) * h;
@@ -781,6 +792,123 @@ __device__ __forceinline__ void ros23_step(const T* u, const T* p, T t, T h, con
   lu.solve(v, k3);
 #pragma unroll
   for (int j = 0; j < D; ++j) es[j] = (m::fma(T(-2), k2[j], k1[j]) + k3[j]) * T(1.0 / 6.0);
+}
+
+// Rodas4 and Rodas5P (Sec. 5.2.1: GPURodas4 after Hairer-Wanner, GPURodas5P after
+// Steinebach 2023): stiffly accurate Rosenbrock methods of orders 4(3) and 5(4), in the
+// transformed form the publications give their coefficients in.  With W = I - h gamma J and
+// stages U_i (i = 0..S-1):
+//   W U_i = h gamma f(y + sum_{j<i} a_ij U_j) + gamma sum_{j<i} c_ij U_j,
+//   y_{n+1} = (the last stage's argument) + U_{S-1},   E = U_{S-1}
+// (the last stage's argument is the embedded solution).  Autonomous models: the stage times
+// and the time-derivative terms do not enter.
+struct Rodas4Tab {
+  static constexpr int S = 6;
+  static constexpr double gamma = 0.25;
+  // stage 5's argument adds U_4 to stage 4's
+  static __host__ __device__ constexpr double a(int i, int j) {
+    constexpr double v[6][5] = {
+        {0, 0, 0, 0, 0},
+        {1.544, 0, 0, 0, 0},
+        {0.9466785280815826, 0.2557011698983284, 0, 0, 0},
+        {3.314825187068521, 2.896124015972201, 0.9986419139977817, 0, 0},
+        {1.221224509226641, 6.019134481288629, 12.53708332932087, -0.6878860361058950, 0},
+        {1.221224509226641, 6.019134481288629, 12.53708332932087, -0.6878860361058950, 1.0}};
+    return v[i][j];
+  }
+  static __host__ __device__ constexpr double c(int i, int j) {
+    constexpr double v[6][5] = {
+        {0, 0, 0, 0, 0},
+        {-5.6688, 0, 0, 0, 0},
+        {-2.430093356833875, -0.2063599157091915, 0, 0, 0},
+        {-0.1073529058151375, -9.594562251023355, -20.47028614809616, 0, 0},
+        {7.496443313967647, -10.24680431464352, -33.99990352819905, 11.70890893206160, 0},
+        {8.083246795921522, -7.981132988064893, -31.52159432874371, 16.31930543123136,
+         -6.058818238834054}};
+    return v[i][j];
+  }
+};
+
+struct Rodas5PTab {
+  static constexpr int S = 8;
+  static constexpr double gamma = 0.21193756319429014;
+  // stages 6 and 7 each add the previous stage's U to the argument before them
+  static __host__ __device__ constexpr double a(int i, int j) {
+    constexpr double v[8][7] = {
+        {0, 0, 0, 0, 0, 0, 0},
+        {3.0, 0, 0, 0, 0, 0, 0},
+        {2.849394379747939, 0.45842242204463923, 0, 0, 0, 0, 0},
+        {-6.954028509809101, 2.489845061869568, -10.358996098473584, 0, 0, 0, 0},
+        {2.8029986275628964, 0.5072464736228206, -0.3988312541770524, -0.04721187230404641, 0, 0,
+         0},
+        {-7.502846399306121, 2.561846144803919, -11.627539656261098, -0.18268767659942256,
+         0.030198172008377946, 0, 0},
+        {-7.502846399306121, 2.561846144803919, -11.627539656261098, -0.18268767659942256,
+         0.030198172008377946, 1.0, 0},
+        {-7.502846399306121, 2.561846144803919, -11.627539656261098, -0.18268767659942256,
+         0.030198172008377946, 1.0, 1.0}};
+    return v[i][j];
+  }
+  static __host__ __device__ constexpr double c(int i, int j) {
+    constexpr double v[8][7] = {
+        {0, 0, 0, 0, 0, 0, 0},
+        {-14.155112264123755, 0, 0, 0, 0, 0, 0},
+        {-17.97296035885952, -2.859693295451294, 0, 0, 0, 0, 0},
+        {147.12150275711716, -1.41221402718213, 71.68940251302358, 0, 0, 0, 0},
+        {165.43517024871676, -0.4592823456491126, 42.90938336958603, -5.961986721573306, 0, 0,
+         0},
+        {24.854864614690072, -3.0009227002832186, 47.4931110020768, 5.5814197821558125,
+         -0.6610691825249471, 0, 0},
+        {30.91273214028599, -3.1208243349937974, 77.79954646070892, 34.28646028294783,
+         -19.097331116725623, -28.087943162872662, 0},
+        {37.80277123390563, -3.2571969029072276, 112.26918849496327, 66.9347231244047,
+         -40.06618937091002, -54.66780262877968, -9.48861652309627}};
+    return v[i][j];
+  }
+};
+
+// One Rodas step from (u, t) with f0 = f(u, t): fills unew = y_{n+1}, err = E (the full error,
+// not divided by h) and f1 = f(unew) (the next step's f0).
+template <class RHS, class T, class TAB>
+__device__ __forceinline__ void rodas_step(const T* u, const T* p, T t, T h, const T* f0,
+                                           T* unew, T* err, T* f1) {
+  static_assert(RHS::autonomous, "the Rodas methods here assume df/dt = 0");
+  constexpr int D = RHS::D, S = TAB::S;
+  typedef M<T> m;
+  const T hg = h * T(TAB::gamma);
+  RosLU<T, D> lu;
+  ros_factor<RHS, T>(u, p, t, hg, lu);
+  T U[S][D], g[D], fi[D], v[D];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    if (i == 0) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) v[j] = hg * f0[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        T x = u[j];
+#pragma unroll
+        for (int l = 0; l < i; ++l) x = m::fma(T(TAB::a(i, l)), U[l][j], x);
+        g[j] = x;
+      }
+      RHS::f(g, p, t, fi);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        T x = hg * fi[j];
+#pragma unroll
+        for (int l = 0; l < i; ++l) x = m::fma(T(TAB::gamma * TAB::c(i, l)), U[l][j], x);
+        v[j] = x;
+      }
+    }
+    lu.solve(v, U[i]);
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    unew[j] = g[j] + U[S - 1][j];
+    err[j] = U[S - 1][j];
+  }
+  RHS::f(unew, p, t + h, f1);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -166,7 +166,10 @@ __device__ __forceinline__ T rms_scaled(const T* x, const T* sc, int D) {
 // METH_TSIT5_RECORD is Tsit5 that records every accepted step.  Each variant carries only
 // its own output code: the record's staging in the dense kernel cost it 12 registers and
 // ~10 %.
-enum { METH_TSIT5 = 0, METH_ROS23 = 1, METH_TSIT5_DENSE = 2, METH_TSIT5_RECORD = 3 };
+enum {
+  METH_TSIT5 = 0, METH_ROS23 = 1, METH_TSIT5_DENSE = 2, METH_TSIT5_RECORD = 3, METH_RODAS4 = 4,
+  METH_RODAS5P = 5
+};
 
 template <class RHS, class T, int METH>
 struct Adaptive {
@@ -175,13 +178,17 @@ struct Adaptive {
   static constexpr bool kRecord = METH == METH_TSIT5_RECORD;
   // the every-step record: staged (kRecord) or with scalar stores (Rosenbrock23); the plain
   // Tsit5 variant never records (Tsit5 records run on METH_TSIT5_RECORD)
-  static constexpr bool kHasRecord = kRecord || METH == METH_ROS23;
-  static constexpr bool kEvent = RHS::has_event && METH != METH_ROS23;
+  // Rosenbrock methods: Rosenbrock23, Rodas4, Rodas5P (no dense output, no events)
+  static constexpr bool kRos = METH == METH_ROS23 || METH == METH_RODAS4 || METH == METH_RODAS5P;
+  static constexpr bool kRodas = METH == METH_RODAS4 || METH == METH_RODAS5P;
+  static constexpr bool kHasRecord = kRecord || kRos;
+  static constexpr bool kEvent = RHS::has_event && !kRos;
   static constexpr bool kKeepStages = kDense || kEvent;  // stages 2..6 outlive the step
   // trajectories per thread (dense saving and the record: one, the staging slot is the
   // thread's)
   static constexpr int kMaxTpt =
-      (RHS::stiff_only || METH == METH_TSIT5_DENSE || METH == METH_TSIT5_RECORD) ? 1 : 4;
+      (RHS::stiff_only || kRodas || METH == METH_TSIT5_DENSE || METH == METH_TSIT5_RECORD) ? 1
+                                                                                          : 4;
   // Dense saving stages kSaveK saves (a whole number of 16-byte words) per lane in shared
   // memory and writes them with vector stores when the output is trajectory-major, 16-byte
   // aligned and n_save is a multiple of kSaveK: the lanes of a warp save at different times,
@@ -207,10 +214,17 @@ struct Adaptive {
   static constexpr int kSlotBytes0 = kStageElems * int(sizeof(T));
   static constexpr int kSlotBytes =
       (kSlotBytes0 > 0 && (kSlotBytes0 / 16) % 2 == 0) ? kSlotBytes0 + 16 : kSlotBytes0;
-  // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k
-  static constexpr float kOrd = (METH != METH_ROS23) ? 5.f : 3.f;
-  static constexpr int kInitOrder = (METH != METH_ROS23) ? 5 : 2;
-  static constexpr int kFevPerAttempt = (METH != METH_ROS23) ? 6 : 2;
+  // controller exponents: beta1 = 0.7/k, beta2 = 0.4/k, reject exponent 1/k, with k the error
+  // estimate's order + 1 (Tsit5 5(4) and Rodas5P 5(4): 5, Rodas4 4(3): 4, Rosenbrock23: 3);
+  // the starting step takes the advancing solution's order
+  static constexpr float kOrd =
+      METH == METH_ROS23 ? 3.f : METH == METH_RODAS4 ? 4.f : 5.f;
+  static constexpr int kInitOrder = METH == METH_ROS23 ? 2 : METH == METH_RODAS4 ? 4 : 5;
+  // f evaluations per attempt: Tsit5 6 (FSAL), Rosenbrock23 2 (FSAL), Rodas: stages 2..S and
+  // f(u_{n+1})
+  static constexpr int kFevPerAttempt = METH == METH_ROS23 ? 2
+                                        : METH == METH_RODAS4 ? Rodas4Tab::S
+                                        : METH == METH_RODAS5P ? Rodas5PTab::S : 6;
   using Real = T;
   static constexpr bool kSmemSaves = true;  // reads save times from save_times_smem
 
@@ -428,11 +442,16 @@ struct Adaptive {
     const bool capped = attempts >= a.maxiters_i;
     const bool tiny = hs < T(M<T>::dtmin_factor) * M<T>::max(T(1), M<T>::abs(tnow));
     T unew[D], es[D], fnew[D], kmid[kKeepStages ? 5 * D : 1];
-    if constexpr (METH != METH_ROS23)
-      tsit5_step<RHS, T, true>(u, p, tnow, hs, fk, unew, es, fnew, kKeepStages ? kmid : nullptr);
-    else
+    if constexpr (METH == METH_ROS23)
       ros23_step<RHS, T>(u, p, tnow, hs, fk, unew, es, fnew);
-    // q^2 = (1/D) sum_j (E_j / (atol + rtol max(|u_j|, |unew_j|)))^2 with E_j = h es_j.
+    else if constexpr (METH == METH_RODAS4)
+      rodas_step<RHS, T, Rodas4Tab>(u, p, tnow, hs, fk, unew, es, fnew);
+    else if constexpr (METH == METH_RODAS5P)
+      rodas_step<RHS, T, Rodas5PTab>(u, p, tnow, hs, fk, unew, es, fnew);
+    else
+      tsit5_step<RHS, T, true>(u, p, tnow, hs, fk, unew, es, fnew, kKeepStages ? kmid : nullptr);
+    // q^2 = (1/D) sum_j (E_j / (atol + rtol max(|u_j|, |unew_j|)))^2 with E_j = h es_j
+    // (the Rodas steps return E_j itself).
     // The ratios are formed in FP32 for both precisions (E itself is accumulated in T).
     const T atol = Tol<T>::abstol(a), rtol = Tol<T>::reltol(a);
     float r2 = 0.f;
@@ -440,7 +459,7 @@ struct Adaptive {
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       const T sc = M<T>::fma(rtol, M<T>::max(M<T>::abs(u[j]), M<T>::abs(unew[j])), atol);
-      const float r = __fdividef(float(hs * es[j]), float(sc));
+      const float r = __fdividef(float(kRodas ? es[j] : hs * es[j]), float(sc));  // Rodas: E itself
       r2 = __fmaf_rn(r, r, r2);
       fin = fin && M<T>::finite(unew[j]);
     }

@@ -139,6 +139,10 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
   *supported = true;
   if constexpr (RHS::stiff_only) {  // large stiff models: Rosenbrock23 only
     if (alg == ENS_ROS23) return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps, cs);
+    if (alg == ENS_RODAS4)
+      return run_integ<Adaptive<RHS, T, METH_RODAS4>>(a, cfg, s, attr, bps, cs);
+    if (alg == ENS_RODAS5P)
+      return run_integ<Adaptive<RHS, T, METH_RODAS5P>>(a, cfg, s, attr, bps, cs);
   } else if constexpr (RHS::has_event) {  // events are located on the adaptive Tsit5 interpolant
     if (alg == ENS_TSIT5_ADAPTIVE) {
       if (a && a->step_cap > 0)
@@ -161,6 +165,10 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
         return run_integ<Adaptive<RHS, T, METH_TSIT5>>(a, cfg, s, attr, bps, cs);
       case ENS_RK4: return run_integ<Fixed<RHS, T, METH_FIX_RK4>>(a, cfg, s, attr, bps, cs);
       case ENS_ROS23: return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps, cs);
+      case ENS_RODAS4:
+        return run_integ<Adaptive<RHS, T, METH_RODAS4>>(a, cfg, s, attr, bps, cs);
+      case ENS_RODAS5P:
+        return run_integ<Adaptive<RHS, T, METH_RODAS5P>>(a, cfg, s, attr, bps, cs);
       case ENS_EM:
         if constexpr (RHS::has_noise) {
           return run_integ<Fixed<RHS, T, METH_FIX_EM>>(a, cfg, s, attr, bps, cs);
