@@ -17,7 +17,8 @@ Identifiers (the same numbers as the public C-ABI, by documentation):
         6 Oregonator (D=3, P=3: k1, k2, k3), 7 HIRES (D=8, P=12: its distinct rate constants),
         8 POLLU (D=20, P=25: k1..k25) -- the paper's stiff test models
   alg:  1 Tsit5 fixed, 2 Tsit5 adaptive, 3 RK4, 4 Rosenbrock23, 5 Euler-Maruyama,
-        6 Rodas4, 7 Rodas5P (stiffly accurate Rosenbrock 4(3) and 5(4))
+        6 Rodas4, 7 Rodas5P (stiffly accurate Rosenbrock 4(3) and 5(4)),
+        8 SIEA (weak order 2 stochastic Runge-Kutta, diagonal noise: GBM)
 """
 from __future__ import annotations
 
@@ -36,7 +37,8 @@ _lib = None
 
 RHS = {"lorenz": 1, "robertson": 2, "gbm": 3, "crn": 4, "ball": 5, "orego": 6, "hires": 7,
        "pollu": 8}
-ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5, "rodas4": 6, "rodas5p": 7}
+ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5, "rodas4": 6, "rodas5p": 7,
+       "siea": 8}
 DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2), 4: (4, 6), 5: (2, 2), 6: (3, 3), 7: (8, 12),
         8: (20, 25)}
 NOISE = {1: 0, 2: 0, 3: 1, 4: 8, 5: 0, 6: 0, 7: 0, 8: 0}  # Wiener processes per model

@@ -50,7 +50,7 @@ enum {
 };
 enum {
   ALG_TSIT5_FIXED = 1, ALG_TSIT5_ADAPTIVE = 2, ALG_RK4 = 3, ALG_ROS23 = 4, ALG_EM = 5,
-  ALG_RODAS4 = 6, ALG_RODAS5P = 7
+  ALG_RODAS4 = 6, ALG_RODAS5P = 7, ALG_SIEA = 8
 };
 enum { ST_OK = 0, ST_MAXITERS = 1, ST_DT_MIN = 2, ST_NONFINITE = 3 };
 enum { LAYOUT_ROWMAJOR = 0, LAYOUT_SOA = 1 };
@@ -922,7 +922,41 @@ void fill_nan(T* v, int n) {
   for (int i = 0; i < n; ++i) v[i] = std::numeric_limits<T>::quiet_NaN();
 }
 
-// ---- fixed-step drivers (Tsit5 fixed, RK4, Euler-Maruyama) ------------------------------------
+// ---- the weak order 2 stochastic Runge-Kutta step (GPUSIEA, Sec. 5.2.2) ------------------------
+// The paper names a weak second-order method of Tocino and Vigo-Aguiar for diagonal noise and
+// writes the explicit stochastic Runge-Kutta family it belongs to (Sec. 3.3: stage values
+// eta_j, weights alpha_j for the drift and beta_j for the noise, and a fit term R), but prints
+// no scheme.  Taken: the weak second-order scheme of improved-Euler type in that family
+// (Kloeden and Platen, the explicit weak order 2.0 scheme), per component j with its own
+// increment dW_j and diffusion b_j depending on component j:
+//   Ybar = X + a(X) h + b(X) dW,     Y+- = X + a(X) h +- b(X) sqrt(h),
+//   X_{n+1} = X + (a(X) + a(Ybar)) h / 2 + (b(Y+) + b(Y-) + 2 b(X)) dW / 4
+//                 + (b(Y+) - b(Y-)) (dW^2 - h) / (4 sqrt(h)),
+// the last term being the fit term R.  With b = 0 it is Heun's (improved Euler) method.
+template <class T>
+void siea_step(int id, int D, int Mw, const T* u, const T* p, T t, T h, const T* z, T* unew) {
+  T a0[MAXD], a1[MAXD], G[MAXD * 8], b0[MAXD], bp[MAXD], bm[MAXD], Y[MAXD], dW[MAXD];
+  const T sq = std::sqrt(h);
+  rhs<T>(id, u, p, t, a0);
+  diffusion<T>(id, u, p, t, G);
+  for (int j = 0; j < D; ++j) {
+    b0[j] = G[j * Mw + j];
+    dW[j] = sq * z[j];
+  }
+  for (int j = 0; j < D; ++j) Y[j] = u[j] + a0[j] * h + b0[j] * dW[j];  // Ybar
+  rhs<T>(id, Y, p, t + h, a1);
+  for (int j = 0; j < D; ++j) Y[j] = u[j] + a0[j] * h + b0[j] * sq;     // Y+
+  diffusion<T>(id, Y, p, t + h, G);
+  for (int j = 0; j < D; ++j) bp[j] = G[j * Mw + j];
+  for (int j = 0; j < D; ++j) Y[j] = u[j] + a0[j] * h - b0[j] * sq;     // Y-
+  diffusion<T>(id, Y, p, t + h, G);
+  for (int j = 0; j < D; ++j) bm[j] = G[j * Mw + j];
+  for (int j = 0; j < D; ++j)
+    unew[j] = u[j] + (a0[j] + a1[j]) * h / T(2) + (bp[j] + bm[j] + T(2) * b0[j]) * dW[j] / T(4) +
+              (bp[j] - bm[j]) * (dW[j] * dW[j] - h) / (T(4) * sq);
+}
+
+// ---- fixed-step drivers (Tsit5 fixed, RK4, Euler-Maruyama, SIEA) -------------------------------
 // n = ceil((tf - t0)/dt - 1e-12); steps 0..n-2 use h = dt, the last uses tf - (t0 + (n-1) dt);
 // step k starts at t_k = t0 + k dt.  A save time s is recorded after step
 // k_s = ceil((s - t0)/dt - 1e-12) (clamped to [0, n]); save times outside [t0, tf] give NaN.
@@ -973,6 +1007,15 @@ void solve_fixed(Traj<T>& tr, uint64_t traj_index) {
     } else if (o.alg == ALG_RK4) {
       rk4_step<T>(o.rhs, D, tr.u, tr.p, tk, h, unew);
       tr.fevals += 4;
+    } else if (o.alg == ALG_SIEA) {
+      // weak order 2 (Sec. 5.2.2, GPUSIEA), diagonal noise: step k uses normal k*Mw + j
+      // for component j, dW_j = sqrt(h) Z_{k,j}
+      T z[MAXD];
+      for (int j = 0; j < D; ++j)
+        z[j] = T(normal_draw(o.seed, traj_index, uint64_t(k) * uint64_t(o.Mw) + uint64_t(j),
+                             o.stream_fp64));
+      siea_step<T>(o.rhs, D, o.Mw, tr.u, tr.p, tk, h, z, unew);
+      tr.fevals += 2;
     } else {  // Euler-Maruyama (Sec. 3.3): X_{k+1} = X_k + a(X_k) h + sum_m b_m(X_k) dW_m,
       // dW_m = sqrt(h) Z_{k,m}; Z_{k,m} is normal number k*Mw + m of the trajectory's stream
       const int Mw = o.Mw;
@@ -1238,10 +1281,12 @@ int oracle_solve(int rhs_id, int alg, int precision, int layout, long long N,
                  long long index_offset, double* out, signed char* status, long long* stats,
                  int nthreads, int dense, double dtmax, long long* events) {
   Model m = model_of(rhs_id);
-  if (m.D == 0 || N < 0 || alg < 1 || alg > 7) return -1;
+  if (m.D == 0 || N < 0 || alg < 1 || alg > 8) return -1;
   if (alg == ALG_EM && m.Mw == 0) return -1;  // Euler-Maruyama needs an SDE model
+  if (alg == ALG_SIEA && (m.Mw == 0 || m.Mw != m.D)) return -1;  // diagonal noise only
   if (rhs_id == RHS_CRN && alg != ALG_EM) return -1;
   if (is_rosenbrock(alg) && rhs_id == RHS_BALL) return -1;  // no Jacobian
+  if (alg == ALG_SIEA && rhs_id != RHS_GBM) return -1;
   if (has_event(rhs_id) && alg != ALG_TSIT5_ADAPTIVE) return -1;  // events need the interpolant
   if (precision < 0 || precision > 2) return -1;
   Opts o{rhs_id, alg, m.D, m.P, m.Mw, dt, abstol, reltol, dt0, maxiters, saveat, n_save, seed,
@@ -1283,7 +1328,8 @@ int oracle_solve_steps(int rhs_id, int alg, int precision, long long N, const do
 }
 
 // One step of a method (for convergence-order and stability pins).  alg: 1 Tsit5, 3 RK4,
-// 4 Rosenbrock23, 5 Euler-Maruyama with the given normal z.  err (Tsit5/R23) may be NULL.
+// 4 Rosenbrock23, 5 Euler-Maruyama and 8 SIEA with the given normal z (GBM), 6 Rodas4,
+// 7 Rodas5P.  err (Tsit5, Rosenbrock methods) may be NULL.
 int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t, double h,
                 double z, double* unew, double* err) {
   Model m = model_of(rhs_id);
@@ -1301,6 +1347,10 @@ int oracle_step(int rhs_id, int alg, const double* u, const double* p, double t,
   } else if (alg == ALG_RODAS4 || alg == ALG_RODAS5P) {
     rhs<double>(rhs_id, u, p, t, k1);
     rodas_step<double>(alg, rhs_id, m.D, u, p, t, h, k1, unew, e, fx);
+  } else if (alg == ALG_SIEA) {
+    if (rhs_id != RHS_GBM) return -1;
+    const double zz[1] = {z};
+    siea_step<double>(rhs_id, m.D, m.Mw, u, p, t, h, zz, unew);
   } else if (alg == ALG_EM) {
     if (rhs_id != RHS_GBM) return -1;
     double a[MAXD], b[MAXD];
