@@ -53,6 +53,9 @@ SM_MAX_MHZ = 2070.0
 # Euler-Maruyama steps count ALU lane instructions (INT32 and FP32 share the 128 lanes/SM/clk):
 #   GBM step: 3 FP + a quarter of one Philox call (10 rounds x (2 wide IMAD + 4 LOP) = 60 INT)
 #     and of its Box-Muller (~30 FP for 4 normals) -> 25;
+#   GBM step of the weak order 2 scheme (SIEA): 22 FP (drift twice, diffusion three times,
+#     dW, the three shifted states, the drift average, noise and fit terms, sqrt(h) and
+#     1/(4 sqrt(h))) + a quarter of one Philox call and its Box-Muller (22.5) -> 45;
 #   CRN step (8 normals): two Philox calls 120 INT, Box-Muller 60 FP, Hill term 11 (two
 #     products, two powers as lg2-mul-ex2, sum, +1, divide), drift 8, noise 17 (5 square
 #     roots, 4 x (mul, fma, mul)), update 8 -> 224; in FP64 the FP64 pipe carries only the
@@ -72,6 +75,7 @@ SM_MAX_MHZ = 2070.0
 #   norm 13, controller 3 -> 84; each accepted step adds the event scan: the dense
 #   polynomial 4 x 7 x 2 FMA + 8 scalings = 64 and 9 checkpoints x 8 = 72 -> 136.
 OPS_PER_ATTEMPT = {"tsit5": 175, "tsit5_fixed": 117, "rk4": 48, "ros23": 122, "em": 25,
+                   "siea": 45,
                    "adjoint": 423, "crn_em": 224, "crn_em_f64": 104, "ball": 84,
                    "ball_event_scan": 136, "ros23_orego": 140, "ros23_hires": 640,
                    "ros23_pollu": 4930, "rodas4": 242, "rodas5p": 337, "rodas5p_pollu": 8567}
@@ -114,6 +118,10 @@ WORKLOADS = {
                             t1=15.0, tol=1e-6, dtmax=1.0, steps=100),
     "lorenz_steps_f32": dict(kind="steps", rhs="lorenz", alg="tsit5", dtype="f32", N=1 << 20,
                              t1=10.0, tol=1e-5, cap=256, layout="rowmajor", steps=100),
+    "gbm_em_f32": dict(kind="solve", rhs="gbm", alg="em", dtype="f32", N=1 << 20, t1=1.0,
+                       dt=1e-3, seed=12345, steps=50),
+    "gbm_siea_f32": dict(kind="solve", rhs="gbm", alg="siea", dtype="f32", N=1 << 20, t1=1.0,
+                         dt=1e-3, seed=12345, steps=50),
     "crn_em_f32": dict(kind="solve", rhs="crn", alg="em", dtype="f32", N=10 ** 6, t1=1000.0,
                        dt=0.1, seed=2024, steps=5),
     "crn_em_f64": dict(kind="solve", rhs="crn", alg="em", dtype="f64", N=10 ** 6, t1=1000.0,
@@ -420,6 +428,7 @@ class SolveRunner:
         self.stats = torch.empty((3, N), dtype=torch.int32, device=dev)
         self.solver = ens.EnsembleSolver(w["rhs"])
         self.kw = solve_kwargs(w)
+        self.kev = None  # (start, stop) events around the integrator kernel of the next step
         if "seed" in self.kw:  # SDE streams indexed by the trajectory's place in the ensemble
             self.kw["index_offset"] = shard_start(w, rank, world)
         self.tuned = None
@@ -440,7 +449,7 @@ class SolveRunner:
         self.launches_per_step = 1 + (3 if sched == "persistent" and order == "cost" else 0)
         # an SDE ensemble's step ends with its moments (two reduction kernels), gathered
         # across the ranks: the one exchange step of the sharded path
-        self.moments = w["alg"] == "em"
+        self.moments = w["alg"] in ("em", "siea")
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.launches_per_step += 2 if self.moments else 0
 
@@ -449,7 +458,8 @@ class SolveRunner:
         self.solver.solve(self.Pd, self.Ud, self.Td, alg=self.w["alg"], layout=self.layout,
                           out=self.out, status=self.status, stats=self.stats,
                           schedule=a.schedule, block=a.block, tpt=a.tpt, refill_min=a.refill,
-                          order=a.order, blocks_per_sm=a.bps, want_stats=True, **self.kw)
+                          order=a.order, blocks_per_sm=a.bps, want_stats=True,
+                          kernel_events=self.kev, **self.kw)
         if self.moments:
             from paper_2304_06835_gb300 import ensemble_moments, gather_moments
             # this rank's (mean, M2, n), then every rank's, stacked in rank order
@@ -1044,13 +1054,21 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # the integrator kernel's own duration (solve workloads): events the library records
+    # around that launch alone, inside each timed step
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)] if hasattr(runner, "kev") else None
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(i & 0xFF)  # L2 flush between timed steps (outside the events)
+        if kev:
+            runner.kev = kev[i]
         ev[i][0].record(stream)
         runner.step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    if kev:
+        runner.kev = None
     if world > 1:
         dist.barrier()
     wall = time.perf_counter() - wall0
@@ -1062,14 +1080,20 @@ def main():
 
     ops, extra = runner.work()
     launch_s = tot_s / args.steps
-    achieved = ops / launch_s / 1e12
+    kernel_s = launch_s
+    if kev:  # the dominant kernel's average duration (max over ranks, like the step time)
+        kernel_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in kev) / 1e3 / args.steps,
+                                  world, dev)
+        extra["kernel_ms"] = 1e3 * kernel_s
+        extra["step_ms"] = 1e3 * launch_s
+    achieved = ops / kernel_s / 1e12
     lanes = FP32_LANES if w["dtype"] == "f32" else FP64_LANES
     peak_max = SMS * lanes * SM_MAX_MHZ * 1e6 / 1e12
     sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
     peak_clk = SMS * lanes * sm_mhz * 1e6 / 1e12
     pipe = "FP32" if w["dtype"] == "f32" else "FP64"
     unit = "T %s-FMA-pipe instr/s" % pipe
-    if w.get("rhs") == "crn" and w["dtype"] == "f32":
+    if w.get("rhs") in ("crn", "gbm") and w["dtype"] == "f32":
         unit = "T ALU lane-instr/s (INT32 + FP32)"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_max,
                 "unit": unit, "frac": achieved / peak_max,

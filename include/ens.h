@@ -89,11 +89,17 @@ enum { ENS_RHS_LORENZ = 1, ENS_RHS_ROBERTSON = 2, ENS_RHS_GBM = 3, ENS_RHS_CRN =
  *                  per attempt; adaptive with the PI control of TSIT5_ADAPTIVE (k = 4)
  *   RODAS5P        Rodas5P, Steinebach's stiffly accurate 5(4) Rosenbrock method (GPURodas5P,
  *                  Sec. 5.2.1), 8 stages; adaptive (k = 5).
+ *   SIEA           weak order 2 stochastic Runge-Kutta step, fixed step, diagonal noise
+ *                  (GPUSIEA, Sec. 5.2.2; the improved-Euler-type member of the SRK family of
+ *                  Sec. 3.3): Ybar = X + a h + b dW, Y+- = X + a h +- b sqrt(h),
+ *                  X += (a(X) + a(Ybar)) h/2 + (b(Y+) + b(Y-) + 2 b(X)) dW/4
+ *                       + (b(Y+) - b(Y-)) (dW^2 - h) / (4 sqrt(h)), dW = sqrt(h) Z_k
+ *                  (the normals of EM's stream); models with diagonal noise only (GBM).
  * The Rosenbrock methods save at save times by stepping onto them (no interpolation) and need
  * a model with a Jacobian (not the CRN or the bouncing ball). */
 enum {
   ENS_TSIT5_FIXED = 1, ENS_TSIT5_ADAPTIVE = 2, ENS_RK4 = 3, ENS_ROS23 = 4, ENS_EM = 5,
-  ENS_RODAS4 = 6, ENS_RODAS5P = 7
+  ENS_RODAS4 = 6, ENS_RODAS5P = 7, ENS_SIEA = 8
 };
 
 /* element type of every floating-point array of a call */
@@ -127,7 +133,7 @@ enum {
 #define ENS_MAX_SAVE 256
 
 typedef struct {
-  int alg;                /* ENS_TSIT5_FIXED ... ENS_RODAS5P */
+  int alg;                /* ENS_TSIT5_FIXED ... ENS_SIEA */
   int dtype;              /* ENS_F32 / ENS_F64 */
   int layout;             /* ENS_LAYOUT_* */
   double dt;              /* fixed-step size (TSIT5_FIXED, RK4, EM), > 0 */
@@ -171,6 +177,12 @@ typedef struct {
   int* step_n;            /* device int32 [N]: accepted steps + 1 (may exceed step_cap), or
                              NULL.  (ens_solve and ens_solve_noalloc; ens_solve_host
                              rejects a step record.) */
+  /* measurement aid: two cudaEvent_t (or NULL), recorded on the solve's stream just before
+     and just after the integrator kernel itself (not the longest-first ordering before it),
+     so that the kernel's own duration can be read with cudaEventElapsedTime.  Both or none;
+     batch plans and ens_solve_host ignore them. */
+  void* kernel_start;
+  void* kernel_stop;
 } ens_opts;
 
 /* Fill *o with defaults: TSIT5_ADAPTIVE, F32, SOA, abstol=reltol=1e-6, maxiters=1e6, auto. */

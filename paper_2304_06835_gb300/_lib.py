@@ -17,7 +17,8 @@ RHS = {"lorenz": 1, "robertson": 2, "gbm": 3, "crn": 4, "ball": 5, "orego": 6, "
        "pollu": 8}
 DIMS = {1: (3, 3), 2: (3, 3), 3: (1, 2), 4: (4, 6), 5: (2, 2), 6: (3, 3), 7: (8, 12), 8: (20, 25)}
 NOISE = {1: 0, 2: 0, 3: 1, 4: 8, 5: 0, 6: 0, 7: 0, 8: 0}  # Wiener processes per model
-ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5, "rodas4": 6, "rodas5p": 7}
+ALG = {"tsit5_fixed": 1, "tsit5": 2, "rk4": 3, "ros23": 4, "em": 5, "rodas4": 6, "rodas5p": 7,
+       "siea": 8}
 F32, F64 = 0, 1
 LAYOUT = {"rowmajor": 0, "soa": 1}
 MOMENTS_BLOCKS = 608  # ENS_MOMENTS_BLOCKS
@@ -38,6 +39,7 @@ class EnsOpts(ctypes.Structure):
         ("refill_min", ctypes.c_int), ("order", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
         ("dense", ctypes.c_int), ("dtmax", ctypes.c_double), ("step_cap", ctypes.c_int),
         ("step_t", ctypes.c_void_p), ("step_n", ctypes.c_void_p),
+        ("kernel_start", ctypes.c_void_p), ("kernel_stop", ctypes.c_void_p),
     ]
 
 

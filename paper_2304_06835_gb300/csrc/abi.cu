@@ -287,14 +287,18 @@ bool model_dims(int rhs_id, int* D, int* P) {
   return false;
 }
 
-bool is_fixed(int alg) { return alg == ENS_TSIT5_FIXED || alg == ENS_RK4 || alg == ENS_EM; }
+bool is_fixed(int alg) {
+  return alg == ENS_TSIT5_FIXED || alg == ENS_RK4 || alg == ENS_EM || alg == ENS_SIEA;
+}
 
 int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
                   const void* tspan, const ens_opts* o, const void* out) {
   if (!o) return fail(ENS_EINVAL, "null options");
   if (N < 0) return fail(ENS_EINVAL, "N < 0");
-  if (o->alg < ENS_TSIT5_FIXED || o->alg > ENS_RODAS5P)
+  if (o->alg < ENS_TSIT5_FIXED || o->alg > ENS_SIEA)
     return fail(ENS_EINVAL, "unknown algorithm");
+  if (o->alg == ENS_SIEA && rhs_id != ENS_RHS_GBM)
+    return fail(ENS_EINVAL, "SIEA needs a model with diagonal noise (GBM)");
   if (o->dtype != ENS_F32 && o->dtype != ENS_F64) return fail(ENS_EINVAL, "unknown dtype");
   if (o->layout != ENS_LAYOUT_ROWMAJOR && o->layout != ENS_LAYOUT_SOA)
     return fail(ENS_EINVAL, "unknown layout");
@@ -311,6 +315,8 @@ int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
     return fail(ENS_EINVAL, "Euler-Maruyama needs a model with noise (GBM, CRN)");
   if (!std::isfinite(o->dtmax)) return fail(ENS_EINVAL, "dtmax not finite");
   if (o->step_cap < 0) return fail(ENS_EINVAL, "step_cap < 0");
+  if ((o->kernel_start == nullptr) != (o->kernel_stop == nullptr))
+    return fail(ENS_EINVAL, "kernel_start and kernel_stop: both or none");
   if (o->step_cap > 0 && (o->n_save > 0 || is_fixed(o->alg)))
     return fail(ENS_EINVAL, "step_cap needs an adaptive method and no save times");
   if (is_fixed(o->alg) && !(o->dt > 0) ) return fail(ENS_EINVAL, "fixed-step methods need dt > 0");
@@ -487,7 +493,15 @@ cudaError_t enqueue_solve(int rhs_id, const ens_opts* o, SolveArgs a, const Laun
     cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
   }
-  return launch_solve(rhs_id, o->alg, o->dtype, a, cfg, s, supported);
+  const bool timed = o->kernel_start && o->kernel_stop;
+  if (timed) {
+    cudaError_t e = cudaEventRecord((cudaEvent_t)o->kernel_start, s);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = launch_solve(rhs_id, o->alg, o->dtype, a, cfg, s, supported);
+  if (timed && e == cudaSuccess && *supported)
+    e = cudaEventRecord((cudaEvent_t)o->kernel_stop, s);
+  return e;
 }
 }  // namespace ens
 
@@ -725,6 +739,7 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
     const long long i1 = N * (c + 1) / C, n = i1 - i0;
     ens_opts oc = *o;
     oc.index_offset = o->index_offset + i0;
+    oc.kernel_start = oc.kernel_stop = nullptr;  // one event pair cannot time several chunks
     e = cudaStreamWaitEvent(s, h->ev_in[c], 0);
     if (e != cudaSuccess) return cuda_fail(e, "chunk order");
     rc = solve_with_cfg(h, n, dp + es * i0 * P, du + es * i0 * D, dt + es * i0 * 2, &oc,

@@ -23,7 +23,9 @@ namespace ens {
 
 namespace {
 
-bool fixed_method(int alg) { return alg == ENS_TSIT5_FIXED || alg == ENS_RK4 || alg == ENS_EM; }
+bool fixed_method(int alg) {
+  return alg == ENS_TSIT5_FIXED || alg == ENS_RK4 || alg == ENS_EM || alg == ENS_SIEA;
+}
 
 typedef std::tuple<int, int, int, int, int, int, int> TuneKey;
 std::map<TuneKey, LaunchCfg> g_tuned;
@@ -317,6 +319,7 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
                     src.stats);
     it.o.saveat = nullptr;  // the save times now live in it.a (copied); the plan keeps no
                             // pointer into the caller's host memory
+    it.o.kernel_start = it.o.kernel_stop = nullptr;  // no timing events inside a plan
     it.cfg = resolve_launch(src.rhs_id, src.N, &src.opts, sms);
     char* base = (char*)b->scratch + off[i];
     it.sc.queue = (unsigned long long*)base;
@@ -338,6 +341,7 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
       if (it.a.N == 0) continue;
       // the trial solves need the save times in the options only for the cache key
       ens_opts o = items[i].opts;
+      o.kernel_start = o.kernel_stop = nullptr;
       int rc = tune_problem(it.rhs_id, &o, it.a, it.sc, sms, s, &it.cfg, &it.tuned_ms);
       if (rc) {
         batch_free(b);

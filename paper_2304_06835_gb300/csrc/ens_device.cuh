@@ -151,6 +151,11 @@ struct GBM {
     a[0] = p[0] * u[0];
     b[0] = ((p[1] * u[0]) * sq) * z[0];
   }
+  // diagonal noise: component j's diffusion b_j (the weak order 2 step evaluates it at shifted
+  // states)
+  static __device__ __forceinline__ void diag_b(const T* u, const T* p, T, T* b) {
+    b[0] = p[1] * u[0];
+  }
   static __device__ __forceinline__ void jac(const T*, const T* p, T, T* J) { J[0] = p[0]; }
   static __device__ __forceinline__ void vjp_u(const T*, const T* p, T, const T* w, T* o) {
     o[0] = p[0] * w[0];

@@ -562,7 +562,13 @@ struct Adaptive {
 // ------------------------------------------------------------------------------------------
 // Fixed-step integrators: Tsit5, RK4 and Euler-Maruyama.
 // n = ceil((tf - t0)/dt - 1e-12) steps; h = dt except the last, h = tf - (t0 + (n-1) dt).
-enum { METH_FIX_TSIT5 = 0, METH_FIX_RK4 = 1, METH_FIX_EM = 2 };
+enum { METH_FIX_TSIT5 = 0, METH_FIX_RK4 = 1, METH_FIX_EM = 2, METH_FIX_SIEA = 3 };
+
+// models whose noise is diagonal (component j driven by W_j through b_j(u)) expose diag_b
+template <class R, class = void>
+struct DiagNoise : std::false_type {};
+template <class R>
+struct DiagNoise<R, std::void_t<decltype(&R::diag_b)>> : std::true_type {};
 
 template <class RHS, class T, int METH>
 struct Fixed {
@@ -575,8 +581,9 @@ struct Fixed {
   static constexpr int kNW = RHS::NW > 0 ? RHS::NW : 1, kPC = Normals<T>::per_call;
   static_assert(kPC % kNW == 0 || kNW % kPC == 0, "normals per step vs per Philox call");
   static constexpr int kMaxTpt = 4;
-  static constexpr int kSub = (METH == METH_FIX_EM && kNW <= kPC) ? kPC / kNW : 1;
-  static constexpr int kCalls = (METH == METH_FIX_EM && kNW > kPC) ? kNW / kPC : 1;
+  static constexpr bool kSde = METH == METH_FIX_EM || METH == METH_FIX_SIEA;
+  static constexpr int kSub = (kSde && kNW <= kPC) ? kPC / kNW : 1;
+  static constexpr int kCalls = (kSde && kNW > kPC) ? kNW / kPC : 1;
 
   T u[D], fk[D], p[P];
   T h_reg, h_last, t0f;
@@ -630,7 +637,7 @@ struct Fixed {
 
   __device__ __forceinline__ void one_step(const SolveArgs& a, const T* z) {
     const T h = (k == n - 1) ? h_last : h_reg;
-    const T tk = T(METH == METH_FIX_EM || !RHS::autonomous ? t0f + T(k) * h_reg : T(0));
+    const T tk = T(kSde || !RHS::autonomous ? t0f + T(k) * h_reg : T(0));
     T unew[D];
     if (METH == METH_FIX_TSIT5) {
       T k7[D];
@@ -639,6 +646,8 @@ struct Fixed {
       for (int j = 0; j < D; ++j) fk[j] = k7[j];
     } else if (METH == METH_FIX_RK4) {
       rk4_step<RHS, T>(u, p, tk, h, unew);
+    } else if (METH == METH_FIX_SIEA) {
+      siea_step(u, p, tk, h, z, unew);
     } else {
       em_step(u, p, tk, h, z, unew);
     }
@@ -661,9 +670,48 @@ struct Fixed {
   __device__ __forceinline__ typename std::enable_if<!R::has_noise>::type em_step(
       const T*, const T*, T, T, const T*, T*) {}
 
+  // Weak order 2 stochastic Runge-Kutta step (GPUSIEA, Sec. 5.2.2; the improved-Euler-type
+  // member of the SRK family of Sec. 3.3), diagonal noise, dW_j = sqrt(h) Z_j:
+  //   Ybar = X + a h + b dW,  Y+- = X + a h +- b sqrt(h),
+  //   X1 = X + (a(X) + a(Ybar)) h/2 + (b(Y+) + b(Y-) + 2 b(X)) dW/4
+  //        + (b(Y+) - b(Y-)) (dW^2 - h) / (4 sqrt(h)).
+  template <class R = RHS>
+  __device__ __forceinline__ typename std::enable_if<DiagNoise<R>::value>::type siea_step(
+      const T* uu, const T* pp, T tk, T h, const T* z, T* unew) {
+    typedef M<T> m;
+    T a0[D], a1[D], b0[D], bp[D], bm[D], Y[D], dW[D], ah[D];
+    const T sq = m::sqrt(h);
+    const T q4 = T(0.25) / sq;
+    RHS::f(uu, pp, tk, a0);
+    RHS::diag_b(uu, pp, tk, b0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      dW[j] = sq * z[j];
+      ah[j] = m::fma(a0[j], h, uu[j]);  // X + a h
+      Y[j] = m::fma(b0[j], dW[j], ah[j]);
+    }
+    RHS::f(Y, pp, tk + h, a1);
+#pragma unroll
+    for (int j = 0; j < D; ++j) Y[j] = m::fma(b0[j], sq, ah[j]);
+    RHS::diag_b(Y, pp, tk + h, bp);
+#pragma unroll
+    for (int j = 0; j < D; ++j) Y[j] = m::fma(-b0[j], sq, ah[j]);
+    RHS::diag_b(Y, pp, tk + h, bm);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const T drift = (a0[j] + a1[j]) * (T(0.5) * h);
+      const T noise = (bp[j] + bm[j] + T(2) * b0[j]) * (T(0.25) * dW[j]);
+      const T fit = (bp[j] - bm[j]) * (m::fma(dW[j], dW[j], -h) * q4);
+      unew[j] = uu[j] + (drift + (noise + fit));
+    }
+  }
+  template <class R = RHS>
+  __device__ __forceinline__ typename std::enable_if<!DiagNoise<R>::value>::type siea_step(
+      const T*, const T*, T, T, const T*, T*) {}
+
   __device__ __forceinline__ bool advance(const SolveArgs& a) {
     if (k >= nrun) return true;
-    if (METH == METH_FIX_EM) {
+    if (kSde) {
       const unsigned long long stream = (unsigned long long)(a.index_offset + idx);
       T z[kPC * kCalls];
       if (kCalls == 1) {
@@ -693,8 +741,11 @@ struct Fixed {
     else if (!fin) st = ENS_TRAJ_NONFINITE;
     if (a.n_save == 0) write_slot<RHS, T>(a, idx, 0, u);
     for (; si < a.n_save; ++si) write_nan_slot<RHS, T>(a, idx, si);
-    const int fev = METH == METH_FIX_TSIT5 ? int(1 + 6 * k) : METH == METH_FIX_RK4 ? int(4 * k)
-                                                                                  : int(k);
+    // f evaluations: Tsit5 1 + 6 per step (FSAL), RK4 4, Euler-Maruyama 1, SIEA 2 (drift at
+    // X and at Ybar)
+    const int fev = METH == METH_FIX_TSIT5 ? int(1 + 6 * k)
+                    : METH == METH_FIX_RK4 ? int(4 * k)
+                    : METH == METH_FIX_SIEA ? int(2 * k) : int(k);
     write_stats(a, idx, st, int(k), 0, fev);
   }
 

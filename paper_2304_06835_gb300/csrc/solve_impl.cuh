@@ -174,6 +174,11 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
           return run_integ<Fixed<RHS, T, METH_FIX_EM>>(a, cfg, s, attr, bps, cs);
         }
         break;
+      case ENS_SIEA:
+        if constexpr (DiagNoise<RHS>::value) {
+          return run_integ<Fixed<RHS, T, METH_FIX_SIEA>>(a, cfg, s, attr, bps, cs);
+        }
+        break;
     }
   }
   *supported = false;

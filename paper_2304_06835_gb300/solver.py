@@ -23,7 +23,8 @@ _NP_DT = {np.dtype(np.float32): _lib.F32, np.dtype(np.float64): _lib.F64}
 def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-6, reltol=1e-6,
               dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
               schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0,
-              dense=False, dtmax=0.0, step_cap=0, step_t=None, step_n=None):
+              dense=False, dtmax=0.0, step_cap=0, step_t=None, step_n=None,
+              kernel_events=None):
     o = _lib.EnsOpts()
     _lib.lib().ens_opts_default(ctypes.byref(o))
     o.alg = _lib.ALG[alg] if isinstance(alg, str) else int(alg)
@@ -52,6 +53,9 @@ def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-
     o.step_cap = int(step_cap)
     o.step_t = None if step_t is None else step_t.data_ptr()
     o.step_n = None if step_n is None else step_n.data_ptr()
+    if kernel_events is not None:  # (start, stop) torch.cuda.Event, recorded around the kernel
+        o.kernel_start = kernel_events[0].cuda_event
+        o.kernel_stop = kernel_events[1].cuda_event
     return o, keep
 
 
@@ -96,7 +100,7 @@ class EnsembleSolver:
               reltol=1e-6, dt0=0.0, maxiters=1_000_000, saveat=None, seed=0, index_offset=0,
               schedule="auto", block=0, tpt=0, refill_min=0, order="auto", blocks_per_sm=0,
               dense=False, dtmax=0.0, want_status=True, want_stats=False, out=None, status=None,
-              stats=None, stream=None):
+              stats=None, stream=None, kernel_events=None):
         """Solve the ensemble on the GPU (device tensors in and out).  dense=True (adaptive
         Tsit5 with saveat): save times take the step's dense output instead of cutting the
         steps, so the steps and final state are those of the solve without save times.
@@ -122,7 +126,7 @@ class EnsembleSolver:
             stats = torch.empty((3, N), dtype=torch.int32, device=dev)
         o, keep = make_opts(alg, _TORCH_DT[params.dtype], layout, dt, abstol, reltol, dt0, maxiters,
                             saveat, seed, index_offset, schedule, block, tpt, refill_min, order,
-                            blocks_per_sm, dense, dtmax)
+                            blocks_per_sm, dense, dtmax, kernel_events=kernel_events)
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
         _lib.check(_lib.lib().ens_solve(self._h, N, _ptr(params), _ptr(u0), _ptr(tspan),
                                         ctypes.byref(o), _ptr(out), _ptr(status), _ptr(stats),
