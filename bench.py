@@ -692,8 +692,9 @@ class AdjointRunner:
 
 class BatchRunner:
     """One step = one ens_batch_run of the uneven batch: a single CUDA-graph launch that runs
-    the three sub-problems' persistent kernels, launch shapes autotuned, concurrently or one
-    after another (the plan times both graphs at creation and keeps the faster)."""
+    the three sub-problems -- as persistent kernels, launch shapes autotuned, concurrently or
+    one after another, or as one fused persistent kernel whose warps take the items' queues
+    in turn (the plan times the three graphs at creation and keeps the fastest)."""
 
     def __init__(self, args, w, rank, dev):
         import torch
@@ -735,22 +736,28 @@ class BatchRunner:
         res["items_alone_ms"] = [round(i["tuned_ms"], 4) for i in self.plan.info()]
         res["launch_shapes"] = [(i["block"], i["tpt"]) for i in self.plan.info()]
         inf = self.plan.info()[0]
-        res["graph_form"] = "serial" if inf["serial"] else "concurrent"
+        res["graph_form"] = "fused" if inf["fused"] else ("serial" if inf["serial"]
+                                                          else "concurrent")
         res["plan_timed_ms"] = {"concurrent": round(inf["graph_ms_concurrent"], 4),
-                                "serial": round(inf["graph_ms_serial"], 4)}
+                                "serial": round(inf["graph_ms_serial"], 4),
+                                "fused": round(inf["graph_ms_fused"], 4)}
         return res
 
     def work(self):
-        ops, att, ok = 0, [], 0
-        for (name, alg, n, kw), (o, st, stats) in zip(BATCH_PARTS, self.plan.outputs):
+        ops, att, ok, eff = 0, [], 0, []
+        for (name, alg, n, kw), (o, st, stats), inf in zip(BATCH_PARTS, self.plan.outputs,
+                                                             self.plan.info()):
             sts = stats.cpu().numpy().astype(np.int64)
             a = int(sts[0].sum() + sts[1].sum())
             att.append(a)
             ops += a * OPS_PER_ATTEMPT[alg]
             ok += int((st.cpu().numpy() == 0).sum())
+            # useful lane-attempts / issued lane slots of the item's persistent loop (a
+            # direct-schedule item issues no counted slots)
+            eff.append(round(a / inf["lane_slots"], 4) if inf["lane_slots"] else None)
         return ops, {"attempts_per_launch": att,
                      "ops_per_attempt": [OPS_PER_ATTEMPT[a] for _, a, _, _ in BATCH_PARTS],
-                     "trajectories_ok": ok, **self.compare(10)}
+                     "lane_efficiency": eff, "trajectories_ok": ok, **self.compare(10)}
 
     def e2e(self, stream):
         """Trajectories/s with host inputs: pinned inputs of all three parts copied in, one

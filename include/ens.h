@@ -264,14 +264,22 @@ int ens_cost_keys(ens_handle* h, long long N, const void* params, const void* u0
  *   ENS_BATCH_AUTOTUNE  run ens_autotune's search on every item during creation (the items'
  *                       outputs are written by the trial solves)
  *   ENS_BATCH_SERIAL    no concurrency: the items run one after another on the caller stream
- * With GRAPH and AUTOTUNE (and more than one item) the plan also captures the serial order,
- * times both graphs at creation (one warm-up and three timed launches each, writing the
- * items' outputs) and keeps the faster: concurrent persistent kernels, each sized for the
- * whole GPU, can crowd one another.
+ *   ENS_BATCH_FUSED     one persistent kernel for all items: every warp works through the
+ *                       items' queues in the plan's order (longest measured first), taking the
+ *                       next item's trajectories once the current item's queue is drained and
+ *                       its lanes are done, so one item's tail overlaps the next item's work.
+ *                       Available for items of three kinds, at most one of each, without save
+ *                       times or step records: Lorenz FP32 TSIT5_ADAPTIVE, Robertson FP32
+ *                       ROS23, GBM FP32 EM (one trajectory per thread, block 128);
+ *                       ENS_ENOTSUP otherwise.
+ * With GRAPH and AUTOTUNE (and more than one item) the plan also captures the serial order
+ * and, when the items allow it, the fused kernel, times every graph at creation (one warm-up
+ * and three timed launches each, writing the items' outputs) and keeps the fastest:
+ * concurrent persistent kernels, each sized for the whole GPU, can crowd one another.
  * Each item's opts are those of ens_solve; saveat is copied at creation.  The plan keeps the
  * item pointers: ens_batch_run re-solves whatever the input arrays hold at that time. */
 #define ENS_BATCH_MAX_ITEMS 16
-enum { ENS_BATCH_GRAPH = 1, ENS_BATCH_AUTOTUNE = 2, ENS_BATCH_SERIAL = 4 };
+enum { ENS_BATCH_GRAPH = 1, ENS_BATCH_AUTOTUNE = 2, ENS_BATCH_SERIAL = 4, ENS_BATCH_FUSED = 8 };
 
 typedef struct {
   int rhs_id;               /* ENS_RHS_* */
@@ -293,7 +301,14 @@ typedef struct {
   int graph;                /* 1 if the plan runs as a CUDA graph */
   int serial;               /* 1 if the items run one after another */
   float graph_ms_concurrent;  /* GRAPH|AUTOTUNE: measured time of the concurrent graph, */
-  float graph_ms_serial;      /* and of the serial one (0: not measured) */
+  float graph_ms_serial;      /* of the serial one, */
+  float graph_ms_fused;       /* and of the fused kernel (0: not measured) */
+  int fused;                /* 1 if the plan runs the fused kernel */
+  unsigned long long lane_slots;  /* lane slots the item's persistent loops issued in the last
+                                     run (iterations x 32 x trajectories per thread; 0 for a
+                                     direct-schedule item): the item's attempts divided by this
+                                     is its lane efficiency.  Reading it synchronises with the
+                                     device. */
 } ens_batch_item_info;
 
 typedef struct ens_batch ens_batch;

@@ -57,10 +57,12 @@ class BatchItemInfo(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_float),
         ("launch_position", ctypes.c_int), ("graph", ctypes.c_int), ("serial", ctypes.c_int),
         ("graph_ms_concurrent", ctypes.c_float), ("graph_ms_serial", ctypes.c_float),
+        ("graph_ms_fused", ctypes.c_float), ("fused", ctypes.c_int),
+        ("lane_slots", ctypes.c_ulonglong),
     ]
 
 
-BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_SERIAL = 1, 2, 4
+BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_SERIAL, BATCH_FUSED = 1, 2, 4, 8
 BATCH_MAX_ITEMS = 16
 
 

@@ -478,19 +478,28 @@ bool uses_cost_order(const ens_opts* o, const LaunchCfg& cfg) {
          (o->order == ENS_ORDER_COST || (o->order == ENS_ORDER_AUTO && !is_fixed(o->alg)));
 }
 
+cudaError_t prepare_solve(int rhs_id, const ens_opts* o, SolveArgs* a, const LaunchCfg& cfg,
+                          const SolveScratch& sc, cudaStream_t s) {
+  a->queue = sc.queue;
+  a->order = nullptr;
+  if (cfg.schedule == ENS_SCHED_PERSISTENT) {
+    if (uses_cost_order(o, cfg) && a->N <= 0x7fffffffLL && sc.order) {
+      cudaError_t e = launch_cost_order(rhs_id, o->alg, o->dtype, *a, sc.bucket, sc.hist,
+                                        sc.order, s);
+      if (e != cudaSuccess) return e;
+      a->order = sc.order;
+    }
+    cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t enqueue_solve(int rhs_id, const ens_opts* o, SolveArgs a, const LaunchCfg& cfg,
                           const SolveScratch& sc, cudaStream_t s, bool* supported) {
   *supported = true;
-  a.queue = sc.queue;
-  a.order = nullptr;
-  if (cfg.schedule == ENS_SCHED_PERSISTENT) {
-    if (uses_cost_order(o, cfg) && a.N <= 0x7fffffffLL && sc.order) {
-      cudaError_t e = launch_cost_order(rhs_id, o->alg, o->dtype, a, sc.bucket, sc.hist,
-                                        sc.order, s);
-      if (e != cudaSuccess) return e;
-      a.order = sc.order;
-    }
-    cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned long long), s);
+  {
+    cudaError_t e = prepare_solve(rhs_id, o, &a, cfg, sc, s);
     if (e != cudaSuccess) return e;
   }
   const bool timed = o->kernel_start && o->kernel_stop;

@@ -168,10 +168,16 @@ struct ens_batch {
     float tuned_ms;
     cudaStream_t st;
     cudaEvent_t done;
+    int slot;      // kind of the fused kernel (mixed_slot), -1: none
+    LaunchCfg fcfg;  // its shape inside the fused kernel (persistent, block 128)
   };
   std::vector<Item> items;
   std::vector<int> order;  // launch order (longest measured first when tuned)
-  float graph_ms[2];       // measured graph times: concurrent, serial (0: not measured)
+  float graph_ms[3];       // measured graph times: concurrent, serial, fused (0: not measured)
+  bool fusable;            // the items fit the fused kernel
+  int fblock;              // the fused kernel's block size
+  int sms;
+  unsigned long long* slots;  // device: per item, the lane slots its persistent loops issued
   void* scratch;
   cudaStream_t cap;
   cudaEvent_t fork;
@@ -187,6 +193,25 @@ int batch_fail(ens_batch* b, int code, const char* msg);
 
 cudaError_t enqueue_batch(ens_batch* b, cudaStream_t s, bool* sup) {
   *sup = true;
+  cudaError_t e0 =
+      cudaMemsetAsync(b->slots, 0, sizeof(unsigned long long) * b->items.size(), s);
+  if (e0 != cudaSuccess) return e0;
+  if (b->flags & ENS_BATCH_FUSED) {
+    // every item's ordering pass and queue reset, then the one kernel over all of them
+    const SolveArgs* by_slot[3] = {nullptr, nullptr, nullptr};
+    int order[3], n = 0;
+    for (int i : b->order) {
+      ens_batch::Item& it = b->items[i];
+      SolveArgs a = it.a;
+      cudaError_t e = prepare_solve(it.rhs_id, &it.o, &a, it.fcfg, it.sc, s);
+      if (e != cudaSuccess) return e;
+      it.a.order = a.order;  // the prepared arguments (queue, order) stay with the item
+      it.a.queue = a.queue;
+      by_slot[it.slot] = &it.a;
+      order[n++] = it.slot;
+    }
+    return launch_mixed(by_slot, order, n, b->fblock, b->sms, s);
+  }
   if (b->flags & ENS_BATCH_SERIAL) {
     for (int i : b->order) {
       ens_batch::Item& it = b->items[i];
@@ -279,8 +304,10 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
   *out = nullptr;
   if (n_items < 1 || n_items > ENS_BATCH_MAX_ITEMS || !items)
     return set_last_error(ENS_EINVAL, "n_items must be in [1, ENS_BATCH_MAX_ITEMS]");
-  if (flags & ~(ENS_BATCH_GRAPH | ENS_BATCH_AUTOTUNE | ENS_BATCH_SERIAL))
+  if (flags & ~(ENS_BATCH_GRAPH | ENS_BATCH_AUTOTUNE | ENS_BATCH_SERIAL | ENS_BATCH_FUSED))
     return set_last_error(ENS_EINVAL, "unknown flags");
+  if ((flags & ENS_BATCH_SERIAL) && (flags & ENS_BATCH_FUSED))
+    return set_last_error(ENS_EINVAL, "ENS_BATCH_SERIAL and ENS_BATCH_FUSED exclude each other");
   for (int i = 0; i < n_items; ++i) {
     const ens_batch_item& it = items[i];
     int rc = validate_problem(it.rhs_id, it.N, it.params, it.u0, it.tspan, &it.opts, it.out);
@@ -292,11 +319,31 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
   b->fork = nullptr;
   b->graph = nullptr;
   b->exec = nullptr;
+  b->slots = nullptr;
   b->flags = flags;
   int sms = 0;
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e != cudaSuccess) return batch_fail(b, ENS_ECUDA, cudaGetErrorString(e));
+  b->sms = sms;
+  b->fblock = 64;  // 110 registers: 9 blocks of 64 (18 warps) per SM against 4 of 128
+  // the fused kernel takes at most one item of each of its kinds, none of them empty
+  {
+    int seen = 0;
+    b->fusable = true;
+    for (int i = 0; i < n_items; ++i) {
+      const int k = mixed_slot(items[i].rhs_id, &items[i].opts);
+      if (k < 0 || (seen & (1 << k)) || items[i].N == 0) b->fusable = false;
+      if (k >= 0) seen |= 1 << k;
+    }
+  }
+  if ((flags & ENS_BATCH_FUSED) && !b->fusable) {
+    delete b;
+    return set_last_error(ENS_ENOTSUP,
+                          "ENS_BATCH_FUSED takes at most one each of Lorenz FP32 adaptive "
+                          "Tsit5, Robertson FP32 Rosenbrock23 and GBM FP32 Euler-Maruyama, "
+                          "without save times or step records");
+  }
   // one scratch block: per item a 256-byte queue slot, the bucket cursors, order and keys
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   std::vector<size_t> off(n_items);
@@ -306,8 +353,11 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
     const long long N = items[i].N;
     total += 256 + up(4 * (size_t)kCostBuckets) + up(4 * (size_t)N) + up(2 * (size_t)N);
   }
+  const size_t slots_off = total;
+  total += up(sizeof(unsigned long long) * n_items);
   if (cudaMalloc(&b->scratch, total) != cudaSuccess)
     return batch_fail(b, ENS_ENOMEM, "batch scratch");
+  b->slots = (unsigned long long*)((char*)b->scratch + slots_off);
   b->items.resize(n_items);
   for (int i = 0; i < n_items; ++i) {
     const ens_batch_item& src = items[i];
@@ -321,6 +371,13 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
                             // pointer into the caller's host memory
     it.o.kernel_start = it.o.kernel_stop = nullptr;  // no timing events inside a plan
     it.cfg = resolve_launch(src.rhs_id, src.N, &src.opts, sms);
+    it.a.slots = b->slots + i;
+    it.slot = mixed_slot(src.rhs_id, &src.opts);
+    it.fcfg = LaunchCfg{};
+    it.fcfg.schedule = ENS_SCHED_PERSISTENT;
+    it.fcfg.block = 128;
+    it.fcfg.tpt = 1;
+    it.fcfg.num_sms = sms;
     char* base = (char*)b->scratch + off[i];
     it.sc.queue = (unsigned long long*)base;
     it.sc.hist = (unsigned int*)(base + 256);
@@ -358,31 +415,52 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
   b->order.erase(std::remove_if(b->order.begin(), b->order.end(),
                                 [&](int i) { return b->items[i].a.N == 0; }),
                  b->order.end());
-  b->graph_ms[0] = b->graph_ms[1] = 0.f;
+  b->graph_ms[0] = b->graph_ms[1] = b->graph_ms[2] = 0.f;
   if (flags & ENS_BATCH_GRAPH) {
     // wait for the tuning runs (and any caller work on s) before capturing on a private stream
     if (cudaStreamSynchronize(s) != cudaSuccess) return batch_fail(b, ENS_ECUDA, "sync");
-    int rc = capture_graph(b, &b->graph, &b->exec);
-    if (rc) return batch_fail(b, rc, ens_last_error());
-    if ((flags & ENS_BATCH_AUTOTUNE) && !(flags & ENS_BATCH_SERIAL) && b->order.size() > 1) {
-      // concurrent kernels can share the SMs well or crowd each other (a persistent grid
-      // sized for the whole GPU leaves little room beside it): time the concurrent graph and
-      // the serial one and keep the faster
-      b->flags |= ENS_BATCH_SERIAL;
-      cudaGraph_t g2 = nullptr;
-      cudaGraphExec_t x2 = nullptr;
-      rc = capture_graph(b, &g2, &x2);
-      if (!rc) rc = time_graph(b->exec, s, &b->graph_ms[0]);
-      if (!rc) rc = time_graph(x2, s, &b->graph_ms[1]);
-      if (!rc && b->graph_ms[1] < b->graph_ms[0]) {
-        std::swap(g2, b->graph);
-        std::swap(x2, b->exec);
-      } else {
-        b->flags &= ~ENS_BATCH_SERIAL;
-      }
-      if (x2) cudaGraphExecDestroy(x2);
-      if (g2) cudaGraphDestroy(g2);
+    const bool compare = (flags & ENS_BATCH_AUTOTUNE) && !(flags & ENS_BATCH_SERIAL) &&
+                         !(flags & ENS_BATCH_FUSED) && b->order.size() > 1;
+    if (!compare) {
+      int rc = capture_graph(b, &b->graph, &b->exec);
       if (rc) return batch_fail(b, rc, ens_last_error());
+    } else {
+      // concurrent kernels can share the SMs well or crowd each other (a persistent grid
+      // sized for the whole GPU leaves little room beside it); the fused kernel shares one
+      // grid: capture each form the items allow, time them, keep the fastest
+      // candidates: concurrent, serial, fused with blocks of 64 and of 128
+      const int forms[4] = {0, ENS_BATCH_SERIAL, ENS_BATCH_FUSED, ENS_BATCH_FUSED};
+      const int fblocks[4] = {0, 0, 64, 128};
+      int best = -1, best_fblock = 64;
+      float best_ms = 0.f;
+      for (int f = 0; f < 4; ++f) {
+        if (forms[f] == ENS_BATCH_FUSED && !b->fusable) continue;
+        b->flags = (flags & ~(ENS_BATCH_SERIAL | ENS_BATCH_FUSED)) | forms[f];
+        if (fblocks[f]) b->fblock = fblocks[f];
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        float ms = 0.f;
+        int rc = capture_graph(b, &g, &x);
+        if (!rc) rc = time_graph(x, s, &ms);
+        if (rc) {
+          if (x) cudaGraphExecDestroy(x);
+          if (g) cudaGraphDestroy(g);
+          return batch_fail(b, rc, ens_last_error());
+        }
+        const int slot = f < 2 ? f : 2;  // graph_ms: concurrent, serial, best fused
+        if (b->graph_ms[slot] == 0.f || ms < b->graph_ms[slot]) b->graph_ms[slot] = ms;
+        if (best < 0 || ms < best_ms) {
+          std::swap(g, b->graph);
+          std::swap(x, b->exec);
+          best = f;
+          best_ms = ms;
+          if (fblocks[f]) best_fblock = fblocks[f];
+        }
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+      }
+      b->flags = (flags & ~(ENS_BATCH_SERIAL | ENS_BATCH_FUSED)) | forms[best];
+      b->fblock = best_fblock;
     }
   }
   *out = b;
@@ -419,8 +497,14 @@ int ens_batch_info(const ens_batch* b, int item, ens_batch_item_info* info) {
   info->launch_position = pos;
   info->graph = b->exec != nullptr;
   info->serial = (b->flags & ENS_BATCH_SERIAL) != 0;
+  info->fused = (b->flags & ENS_BATCH_FUSED) != 0;
   info->graph_ms_concurrent = b->graph_ms[0];
   info->graph_ms_serial = b->graph_ms[1];
+  info->graph_ms_fused = b->graph_ms[2];
+  info->lane_slots = 0;
+  cudaError_t e = cudaMemcpy(&info->lane_slots, b->slots + item, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_last_error(ENS_ECUDA, cudaGetErrorString(e));
   return ENS_OK;
 }
 

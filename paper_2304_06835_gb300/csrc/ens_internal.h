@@ -33,6 +33,8 @@ struct SolveArgs {
   long long index_offset;
   unsigned long long* queue;  // persistent-schedule counter (device), zeroed before launch
   const int* order;           // persistent schedule: queue slot -> trajectory index (or null)
+  unsigned long long* slots;  // persistent schedule: adds the lane slots its warps issue (loop
+                              // iterations x 32 x trajectories per thread), or null
   double saveat[ENS_MAX_SAVE];
   float saveat_f[ENS_MAX_SAVE];  // FP32 copies (no double conversion on FP32 solves' path)
 };
@@ -112,6 +114,10 @@ void fill_solve_args(SolveArgs* a, long long N, const void* params, const void* 
                      const void* tspan, const ens_opts* o, void* out, signed char* status,
                      int* stats);
 bool uses_cost_order(const ens_opts* o, const LaunchCfg& cfg);
+// the steps of a persistent solve before its kernel: longest-first ordering into sc.order (sets
+// a->order) and the queue reset (sets a->queue)
+cudaError_t prepare_solve(int rhs_id, const ens_opts* o, SolveArgs* a, const LaunchCfg& cfg,
+                          const SolveScratch& sc, cudaStream_t s);
 // enqueue one solve on stream s: [cost order], queue reset, integrator kernel
 cudaError_t enqueue_solve(int rhs_id, const ens_opts* o, SolveArgs a, const LaunchCfg& cfg,
                           const SolveScratch& sc, cudaStream_t s, bool* supported);
@@ -127,6 +133,15 @@ int tune_problem(int rhs_id, const ens_opts* o, const SolveArgs& a, const SolveS
 // Register / shared-memory attributes of the kernel a launch would use (for tuning).
 cudaError_t solve_kernel_attrs(int rhs_id, int alg, int dtype, const LaunchCfg& cfg,
                                cudaFuncAttributes* attr, int* blocks_per_sm);
+
+// The mixed-batch kernel (batch_multi.cu): one persistent launch over items of three fixed
+// kinds -- slot 0 Lorenz FP32 adaptive Tsit5, slot 1 Robertson FP32 Rosenbrock23,
+// slot 2 GBM FP32 Euler-Maruyama, each without save times or step records -- its warps taking
+// the items' queues in `order` (n entries, slot numbers), blocks of `block` (32..128) threads,
+// as many as fit per SM.  mixed_slot gives an item's slot or -1.
+int mixed_slot(int rhs_id, const ens_opts* o);
+cudaError_t launch_mixed(const SolveArgs* const* by_slot, const int* order, int n, int block,
+                         int num_sms, cudaStream_t s);
 
 cudaError_t launch_philox(unsigned long long seed, long long index_offset, long long n_traj,
                           long long n_calls, unsigned int* out, cudaStream_t s);

@@ -222,6 +222,7 @@ struct Adaptive {
   static constexpr int kInitOrder = METH == METH_ROS23 ? 2 : METH == METH_RODAS4 ? 4 : 5;
   // f evaluations per attempt: Tsit5 6 (FSAL), Rosenbrock23 2 (FSAL), Rodas: stages 2..S and
   // f(u_{n+1})
+  static constexpr int kStepsPerAdvance = 1;  // attempts one advance() can make
   static constexpr int kFevPerAttempt = METH == METH_ROS23 ? 2
                                         : METH == METH_RODAS4 ? Rodas4Tab::S
                                         : METH == METH_RODAS5P ? Rodas5PTab::S : 6;
@@ -584,6 +585,7 @@ struct Fixed {
   static constexpr bool kSde = METH == METH_FIX_EM || METH == METH_FIX_SIEA;
   static constexpr int kSub = (kSde && kNW <= kPC) ? kPC / kNW : 1;
   static constexpr int kCalls = (kSde && kNW > kPC) ? kNW / kPC : 1;
+  static constexpr int kStepsPerAdvance = kSde ? kSub : 1;  // one Philox call serves kSub steps
 
   T u[D], fk[D], p[P];
   T h_reg, h_last, t0f;
@@ -831,11 +833,17 @@ __global__ void k_cost_scatter(long long N, long long chunk, const unsigned shor
 // so warp-wide votes are safe.  A lane that finishes its trajectory writes it out and idles;
 // once at least a.refill_min lanes of the warp are idle (or all are), the idle lanes fetch
 // the next indices together (one warp-aggregated atomic) and initialise in one divergent
-// pass instead of one pass per finishing lane.
+// pass instead of one pass per finishing lane.  The loop returns when the queue is drained
+// and every lane of the warp is done (no block-wide synchronisation inside, so a kernel can
+// run several solves' loops one after another per warp); with a.slots it adds the lane slots
+// it issued (iterations x 32 x TPT), the denominator of the lane efficiency.
+__device__ __forceinline__ void count_slots(unsigned long long* slots, unsigned long long n) {
+  if (slots && (threadIdx.x & 31) == 0) atomicAdd(slots, n * 32ull);
+}
+
 template <class I, int TPT>
-__global__ void k_persistent(const SolveArgs a) {
-  if constexpr (I::kSmemSaves)
-    if (a.n_save > 0) load_save_times<typename I::Real>(a);
+__device__ __forceinline__ void persistent_loop(const SolveArgs& a) {
+  unsigned iters = 0;  // loop iterations of this warp
   I s[TPT];
   bool act[TPT];
 #pragma unroll
@@ -846,6 +854,7 @@ __global__ void k_persistent(const SolveArgs a) {
   }
   bool drained = __any_sync(0xffffffffu, !act[TPT - 1]);  // warp-uniform
   for (;;) {
+    ++iters;
     unsigned busy = 0u;
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
@@ -874,6 +883,14 @@ __global__ void k_persistent(const SolveArgs a) {
       }
     }
   }
+  count_slots(a.slots, (unsigned long long)iters * TPT * I::kStepsPerAdvance);
+}
+
+template <class I, int TPT>
+__global__ void k_persistent(const SolveArgs a) {
+  if constexpr (I::kSmemSaves)
+    if (a.n_save > 0) load_save_times<typename I::Real>(a);
+  persistent_loop<I, TPT>(a);
 }
 
 }  // namespace ens

@@ -262,10 +262,11 @@ struct AdaptivePair {
   }
 };
 
-// Persistent schedule with one AdaptivePair per thread: the refill logic of k_persistent with
-// two slots, the slots being the two lanes.
+// Persistent schedule with one AdaptivePair per thread: the refill logic of persistent_loop
+// with two slots, the slots being the two lanes.
 template <class RHS>
-__global__ void k_persistent_pair(const SolveArgs a) {
+__device__ __forceinline__ void persistent_pair_loop(const SolveArgs& a) {
+  unsigned iters = 0;  // loop iterations of this warp
   AdaptivePair<RHS> s;
   bool act[2];
 #pragma unroll
@@ -276,6 +277,7 @@ __global__ void k_persistent_pair(const SolveArgs a) {
   }
   bool drained = __any_sync(0xffffffffu, !act[1]);  // warp-uniform
   for (;;) {
+    ++iters;
     if (act[0] || act[1]) {
       const unsigned done = s.advance(a, act[0], act[1]);
 #pragma unroll
@@ -305,6 +307,12 @@ __global__ void k_persistent_pair(const SolveArgs a) {
       }
     }
   }
+  count_slots(a.slots, (unsigned long long)iters * 2);
+}
+
+template <class RHS>
+__global__ void k_persistent_pair(const SolveArgs a) {
+  persistent_pair_loop<RHS>(a);
 }
 
 }  // namespace ens

@@ -54,6 +54,9 @@ def make_opts(alg="tsit5", dtype=_lib.F32, layout="rowmajor", dt=0.0, abstol=1e-
     o.step_t = None if step_t is None else step_t.data_ptr()
     o.step_n = None if step_n is None else step_n.data_ptr()
     if kernel_events is not None:  # (start, stop) torch.cuda.Event, recorded around the kernel
+        for e in kernel_events:
+            if not e.cuda_event:  # torch creates the CUDA event at its first record
+                e.record()
         o.kernel_start = kernel_events[0].cuda_event
         o.kernel_stop = kernel_events[1].cuda_event
     return o, keep
@@ -386,6 +389,10 @@ def combine_moments(moments, group=None):
 
 class EnsembleBatch:
     """Several sub-problems solved by one call (one CUDA graph launch with graph=True).
+    fused=True runs them in one persistent kernel (ENS_BATCH_FUSED: Lorenz FP32 adaptive
+    Tsit5, Robertson FP32 Rosenbrock23, GBM FP32 Euler-Maruyama, at most one of each);
+    autotune=True times the concurrent, serial and (where allowed) fused forms and keeps the
+    fastest.
 
     items: list of dicts with keys rhs ("lorenz" / "robertson" / "gbm" / "crn"), params, u0, tspan
     (CUDA tensors, one dtype per item), alg, layout (default "soa") and any ens_solve option
@@ -393,8 +400,8 @@ class EnsembleBatch:
     allocated here: ``batch.outputs[i] = (out, status, stats)``.
     """
 
-    def __init__(self, items, *, graph=True, autotune=False, serial=False, want_stats=True,
-                 stream=None):
+    def __init__(self, items, *, graph=True, autotune=False, serial=False, fused=False,
+                 want_stats=True, stream=None):
         if not items or len(items) > _lib.BATCH_MAX_ITEMS:
             raise ValueError("1 .. %d items" % _lib.BATCH_MAX_ITEMS)
         arr = (_lib.BatchItem * len(items))()
@@ -437,7 +444,7 @@ class EnsembleBatch:
             self.outputs.append((out, status, stats))
             self._keep.append((params, u0, tspan, keep))
         flags = (_lib.BATCH_GRAPH if graph else 0) | (_lib.BATCH_AUTOTUNE if autotune else 0) | \
-            (_lib.BATCH_SERIAL if serial else 0)
+            (_lib.BATCH_SERIAL if serial else 0) | (_lib.BATCH_FUSED if fused else 0)
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
         h = ctypes.c_void_p()
         _lib.check(_lib.lib().ens_batch_create(ctypes.byref(h), arr, len(items), flags,
@@ -462,7 +469,9 @@ class EnsembleBatch:
                         "tuned_ms": inf.tuned_ms, "launch_position": inf.launch_position,
                         "graph": bool(inf.graph), "serial": bool(inf.serial),
                         "graph_ms_concurrent": inf.graph_ms_concurrent,
-                        "graph_ms_serial": inf.graph_ms_serial})
+                        "graph_ms_serial": inf.graph_ms_serial,
+                        "graph_ms_fused": inf.graph_ms_fused, "fused": bool(inf.fused),
+                        "lane_slots": int(inf.lane_slots)})
         return res
 
     def close(self):

@@ -63,7 +63,8 @@ def solo(it):
 
 @pytest.mark.parametrize("mode", [dict(graph=True, autotune=True), dict(graph=True),
                                   dict(graph=False), dict(graph=False, serial=True),
-                                  dict(graph=True, serial=True)])
+                                  dict(graph=True, serial=True), dict(graph=True, fused=True),
+                                  dict(graph=False, fused=True)])
 def test_batch_equals_separate_solves(mode):
     from paper_2304_06835_gb300 import EnsembleBatch
     items, _ = mixed_items(3000, 600, 2000, seed=7, tf_max=20.0)
@@ -209,3 +210,35 @@ def test_autotune_skips_shapes_that_do_not_fit():
     out, st, _ = s.solve(d(P), d(U), d(T), alg="ros23", layout="soa", abstol=1e-6, reltol=1e-6,
                          dt0=1e-4)
     assert int(st.abs().sum()) == 0
+
+
+def test_fused_batch_lane_slots_and_refusals():
+    """The fused kernel: every item solved as alone (bit for bit), in any item order; its
+    persistent loops count the lane slots they issue, so attempts / slots is each item's lane
+    efficiency (<= 1); autotuning times all three forms; unsupported items are refused."""
+    from paper_2304_06835_gb300 import EnsError, EnsembleBatch
+    items, _ = mixed_items(4000, 800, 3000, seed=9, tf_max=30.0)
+    items = [items[2], items[0], items[1]]  # GBM, Lorenz, Robertson
+    ref = [solo(it) for it in items]
+    b = EnsembleBatch(items, fused=True)
+    outs = b.run()
+    torch.cuda.synchronize()
+    for (o, st, stats), (ro, rst, rstats) in zip(outs, ref):
+        np.testing.assert_array_equal(host(o), ro)
+        np.testing.assert_array_equal(stats.cpu().numpy(), rstats)
+    for inf, (_, _, rstats) in zip(b.info(), ref):
+        attempts = int(rstats[0].sum() + rstats[1].sum())
+        assert inf["fused"] and inf["lane_slots"] >= attempts > 0
+        print("lane efficiency %.3f" % (attempts / inf["lane_slots"]))
+    b.close()
+    t = EnsembleBatch(items, autotune=True)
+    i0 = t.info()[0]
+    assert i0["graph_ms_concurrent"] > 0 and i0["graph_ms_serial"] > 0 and i0["graph_ms_fused"] > 0
+    print("graphs: concurrent %.3f serial %.3f fused %.3f ms; kept fused: %s"
+          % (i0["graph_ms_concurrent"], i0["graph_ms_serial"], i0["graph_ms_fused"], i0["fused"]))
+    t.close()
+    with pytest.raises(EnsError):  # two Lorenz items
+        EnsembleBatch([items[1], items[1]], fused=True)
+    sv = dict(items[1], saveat=[0.5, 1.0])
+    with pytest.raises(EnsError):  # save times
+        EnsembleBatch([sv, items[2]], fused=True)

@@ -121,12 +121,21 @@ def test_gradient_matches_oracle(net, B):
     g = g.cpu().double().numpy()
     net.check()
     assert abs(float(loss.item()) - loss_ref) <= 2e-3 * loss_ref
-    o = 0
+    # per weight / bias block: relative Frobenius error <= 1e-2, and element by element
+    # |a - r| <= 2^-6 |r| + 2^-8 max |r| -- the oracle rounds at the kernels' points (bf16
+    # activations and stage gradients, 2^-9 relative), so elements differ by accumulation
+    # order and by the rare bf16 rounding that lands on the other side of a tie (2^-8);
+    # one wrong element, e.g. a bias with a flipped sign, exceeds it
+    o, worst = 0, 0.0
     for (wo, wi), (bo,) in mlp.param_shapes():
         for n in (wo * wi, bo):
             a, r = g[o:o + n], g_ref[o:o + n]
             assert np.linalg.norm(a - r) <= 1e-2 * np.linalg.norm(r), (o, n)
+            bound = 2.0 ** -6 * np.abs(r) + 2.0 ** -8 * np.abs(r).max()
+            worst = max(worst, float((np.abs(a - r) / bound).max()))
+            assert np.all(np.abs(a - r) <= bound), (o, n, np.abs(a - r).max())
             o += n
+    print("B = %d: worst element error / bound %.3g" % (B, worst))
 
 
 def test_gradient_with_index_gather(net):

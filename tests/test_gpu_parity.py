@@ -415,3 +415,21 @@ def test_paired_lockstep_generic_rhs(S):
         res.append((host(o), stats.cpu().numpy()))
     np.testing.assert_array_equal(res[0][0], res[1][0])
     np.testing.assert_array_equal(res[0][1], res[1][1])
+
+
+def test_kernel_events_time_the_integrator_alone(S):
+    """ens_opts.kernel_start / kernel_stop bracket the integrator kernel: a positive time no
+    longer than the whole solve's (which adds the longest-first ordering kernels)."""
+    P, U, T = workloads.lorenz_random(1 << 16, seed=25, t1=2.0)
+    f = lambda a: dev(a, torch.float32)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    args = (f(P), f(U), f(T))
+    S["lorenz"].solve(*args, alg="tsit5", abstol=1e-6, reltol=1e-6)  # warm up
+    s0.record()
+    S["lorenz"].solve(*args, alg="tsit5", abstol=1e-6, reltol=1e-6, order="cost",
+                      kernel_events=(k0, k1))
+    s1.record()
+    torch.cuda.synchronize()
+    tk, ts = k0.elapsed_time(k1), s0.elapsed_time(s1)
+    assert 0.0 < tk <= ts, (tk, ts)
