@@ -569,6 +569,12 @@ class StepsRunner(SolveRunner):
         c = self.c
         s = torch.cuda.current_stream(self.dev).cuda_stream
         p = lambda t: c.c_void_p(t.data_ptr())
+        if self.kev is not None:  # the integrator kernel's own events, as in SolveRunner
+            for e in self.kev:
+                if not e.cuda_event:
+                    e.record()
+        self.opts.kernel_start = self.kev[0].cuda_event if self.kev is not None else None
+        self.opts.kernel_stop = self.kev[1].cuda_event if self.kev is not None else None
         self.lib.check(self.lib.lib().ens_solve(self.solver.handle, self.w["N"], p(self.Pd),
                                                 p(self.Ud), p(self.Td), c.byref(self.opts),
                                                 p(self.rec_u), p(self.status), p(self.stats),
@@ -1197,6 +1203,21 @@ def main():
                 "ratio": a_gpu / max(a_orc, 1),
                 "basis": "attempts (accepted + rejected) over the first %d trajectories, the "
                          "oracle in FP64 at the workload's tolerance" % n}
+            if w["dtype"] == "f32":
+                # an FP32 solve takes other step sizes where its error estimate is rounding
+                # (the ball's exact quadratic arcs): the oracle's FP32 mode on the same
+                # float-rounded inputs counts those
+                import oracle
+                m = min(n, 1 << 16)
+                P, U, T = (np.asarray(a[:m], np.float32).astype(np.float64)
+                           for a in inputs_for(w))
+                s32 = oracle.solve(w["rhs"], w["alg"], P, U, T, nthreads=nt, precision="f32",
+                                   **solve_kwargs(w))[2]
+                a_g = int(g[0, :m].sum() + g[1, :m].sum())
+                line["roofline"]["attempts_oracle"].update(
+                    trajectories_f32=m, gpu_on_those=a_g,
+                    oracle_f32=int(s32[:, :2].sum()),
+                    ratio_f32=a_g / max(int(s32[:, :2].sum()), 1))
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:

@@ -150,7 +150,10 @@ typedef struct {
                              dense = 1 or a step record stages its output in shared memory
                              and takes at most 512 (more: ENS_ECUDA, too many resources). */
   int tpt;                /* trajectories per thread (1, 2 or 4); 0 = tuned / default.  The
-                             Rosenbrock23, dense-output and step-record kernels run one. */
+                             Rosenbrock kernels, dense output and the step record run one.
+                             FP32 adaptive Tsit5 on the final-state output runs 2 as one
+                             lockstep pair on the paired FP32 instructions.  Every shape gives
+                             each trajectory the result of 1. */
   int refill_min;         /* persistent schedule: a warp refills its idle lanes once at least
                              this many are idle (1..32; 0 = default).  Batching refills trades
                              idle lanes for fewer divergent refill passes. */
