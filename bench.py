@@ -62,23 +62,25 @@ SM_MAX_MHZ = 2070.0
 #     floating-point part -> 104 (the Philox integer work runs on the integer lanes).
 # Rosenbrock23 attempt on a D-state model: W = I - h d J (D^2), LU (D^3 / 3 + pivoting),
 #   three solves (3 D^2), the stage combinations, error and norm (~18 D), the Jacobian and
-#   two f evaluations (model terms): Robertson 140; Orego 140; HIRES (D = 8: 171 + 192 + 64 +
-#   144 + 70) 640; POLLU (D = 20: 2667 + 1200 + 400 + 360 + 300) 4930.
+#   two f evaluations (model terms): Robertson 140; Orego 140.  HIRES and POLLU factor W by
+#   the sparse LU on their fixed Jacobian patterns; their FP64 work is measured (ncu: DFMA +
+#   DADD + DMUL over the bench solve's attempts, all 8,192 trajectories): HIRES 378, POLLU
+#   1,397 (the dense model's 4,930 counted the full 20 x 20 factorisation and solves).
 # Rosenbrock attempts on Robertson, measured: ncu's FP64 instruction classes (DFMA + DADD +
 #   DMUL, N = 65,536 of the bench distribution, tol 1e-6) over the solve's attempts give 122
 #   (Rosenbrock23), 242 (Rodas4, S = 6) and 337 (Rodas5P, S = 8) per attempt -- below the
 #   operation models (140, 294, 418: J, W, LU, S solves, S f evaluations, stage sums, error
 #   and norm), which counted constant-zero and folded terms; the measured counts are used.
-#   POLLU (D = 20) under Rodas5P, from the model: LU 2667, W 400, 8 solves x 400,
-#   8 f evaluations x 90, stage combinations 20 x 64, error and norm 300 -> 8567.
+#   POLLU (D = 20) under Rodas5P, measured the same way: 3,171 (the sparse LU, 8 solves of
+#   109 multiply-adds, 8 f evaluations, the stage sums, error and norm).
 # Bouncing ball (D = 2, f costs nothing): a Tsit5 attempt = stage combinations 54, error 14,
 #   norm 13, controller 3 -> 84; each accepted step adds the event scan: the dense
 #   polynomial 4 x 7 x 2 FMA + 8 scalings = 64 and 9 checkpoints x 8 = 72 -> 136.
 OPS_PER_ATTEMPT = {"tsit5": 175, "tsit5_fixed": 117, "rk4": 48, "ros23": 122, "em": 25,
                    "siea": 45,
                    "adjoint": 423, "crn_em": 224, "crn_em_f64": 104, "ball": 84,
-                   "ball_event_scan": 136, "ros23_orego": 140, "ros23_hires": 640,
-                   "ros23_pollu": 4930, "rodas4": 242, "rodas5p": 337, "rodas5p_pollu": 8567}
+                   "ball_event_scan": 136, "ros23_orego": 140, "ros23_hires": 378,
+                   "ros23_pollu": 1397, "rodas4": 242, "rodas5p": 337, "rodas5p_pollu": 3171}
 
 
 def ops_key(w):
@@ -103,17 +105,17 @@ WORKLOADS = {
     "robertson_rodas5p_f64": dict(kind="solve", rhs="robertson", alg="rodas5p", dtype="f64",
                                   N=1 << 18, t1=1e5, tol=1e-6, dt0=1e-4, steps=20),
     "pollu_rodas5p_f64": dict(kind="solve", rhs="pollu", alg="rodas5p", dtype="f64", N=8192,
-                              t1=60.0, tol=1e-6, steps=5),
+                              t1=60.0, tol=1e-6, steps=20),
     "lorenz_dense_f32": dict(kind="solve", rhs="lorenz", alg="tsit5", dtype="f32", N=1 << 20,
                              t1=10.0, tol=1e-5, saves=256, dense=True, layout="rowmajor",
                              steps=200),
     # the paper's stiff test models at its 8,192 trajectories (tolerance not printed: 1e-6)
     "orego_ros23_f64": dict(kind="solve", rhs="orego", alg="ros23", dtype="f64", N=8192,
-                            t1=30.0, tol=1e-6, steps=5),
+                            t1=30.0, tol=1e-6, steps=20),
     "hires_ros23_f64": dict(kind="solve", rhs="hires", alg="ros23", dtype="f64", N=8192,
-                            t1=321.8122, tol=1e-6, steps=5),
+                            t1=321.8122, tol=1e-6, steps=20),
     "pollu_ros23_f64": dict(kind="solve", rhs="pollu", alg="ros23", dtype="f64", N=8192,
-                            t1=60.0, tol=1e-6, steps=5),
+                            t1=60.0, tol=1e-6, steps=20),
     "ball_events_f32": dict(kind="solve", rhs="ball", alg="tsit5", dtype="f32", N=1 << 20,
                             t1=15.0, tol=1e-6, dtmax=1.0, steps=100),
     "lorenz_steps_f32": dict(kind="steps", rhs="lorenz", alg="tsit5", dtype="f32", N=1 << 20,

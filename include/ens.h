@@ -410,14 +410,16 @@ int ens_mlp_adam(ens_mlp* m, int member, float lr, int t, void* cuda_stream);
 int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* y, int flags,
                     void* cuda_stream);
 /* Gate: y_mean [B][3] = mean over the members of y_members [members][B][3] (NULL to skip);
- * fallback[b] = 1 when x_b leaves the box or the largest per-component population standard
- * deviation over the members exceeds tau; *n_fallback (device, or NULL) is incremented by the
+ * spread [B] = the largest per-component population standard deviation over the members
+ * (NULL to skip; the statistic a gate threshold is calibrated on);
+ * fallback[b] = 1 when x_b leaves the box or spread[b] exceeds tau; *n_fallback (device, or
+ * NULL) is incremented by the
  * number of fallbacks (zero it first).  With fb_index given, every fallback sample is also
  * appended, at a slot taken from *n_fallback, to a compacted solver problem in ROWMAJOR FP32
  * layout: fb_index[slot] = b, fb_params[slot] = (sigma, rho, beta), fb_u0[slot] = u0,
  * fb_tspan[slot] = (t0, t1) (each array has room for B rows; slot order is arbitrary). */
 int ens_mlp_gate(ens_mlp* m, long long B, const float* x, const float* y_members, float tau,
-                 float* y_mean, unsigned char* fallback, unsigned long long* n_fallback,
+                 float* y_mean, float* spread, unsigned char* fallback, unsigned long long* n_fallback,
                  long long* fb_index, float* fb_params, float* fb_u0, float* fb_tspan, double t0,
                  double t1, void* cuda_stream);
 /* y[fb_index[i]] = u[i] (rows of 3) for i < n: the solver's answers for the fallbacks. */

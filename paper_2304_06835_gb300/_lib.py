@@ -116,7 +116,7 @@ SIGNATURES = {
     "ens_mlp_grad": (_INT, [_VP, _INT, _LL, _VP, _VP, _VP, _VP, _VP, _VP]),
     "ens_mlp_adam": (_INT, [_VP, _INT, ctypes.c_float, _INT, _VP]),
     "ens_mlp_forward": (_INT, [_VP, _INT, _LL, _VP, _VP, _INT, _VP]),
-    "ens_mlp_gate": (_INT, [_VP, _LL, _VP, _VP, ctypes.c_float, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+    "ens_mlp_gate": (_INT, [_VP, _LL, _VP, _VP, ctypes.c_float, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                             ctypes.c_double, ctypes.c_double, _VP]),
     "ens_mlp_scatter": (_INT, [_LL, _VP, _VP, _VP, _VP]),
     "ens_mlp_check": (_INT, [_VP, _VP]),

@@ -73,6 +73,25 @@ struct M<double> {
   static constexpr double dtmin_factor = 1e-14;
 };
 
+// Structural nonzeros of a D x D matrix.
+template <int D>
+struct Pattern {
+  bool nz[D][D];
+};
+
+// Calls f(std::integral_constant<int, i>) for i in [B, E), halving the range (shallow
+// template recursion).
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (E - B == 1) {
+    f(std::integral_constant<int, B>());
+  } else if constexpr (E - B > 1) {
+    constexpr int Mid = B + (E - B) / 2;
+    static_for<B, Mid>(f);
+    static_for<Mid, E>(f);
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Models.  f = du/dt (drift for SDEs), jac = df/du (row-major D x D), vjp_u = (df/du)^T w,
 // vjp_p = (df/dp)^T w.  SDE models (has_noise) have NW Wiener processes and
@@ -262,7 +281,7 @@ template <class T>
 struct Hires {  // p = the 12 distinct rate constants c1..c12 in order of appearance
   static constexpr int D = 8, P = 12, NW = 0;
   static constexpr bool autonomous = true, has_noise = false, sde_only = false, has_event = false;
-  static constexpr bool stiff_only = true;  // Rosenbrock23 only, one trajectory per thread
+  static constexpr bool stiff_only = true;  // Rosenbrock methods only, one per thread
   static __device__ __forceinline__ void f(const T* y, const T* c, T, T* dy) {
     const T r = c[9] * y[5] * y[7];
     dy[0] = -c[0] * y[0] + c[1] * y[1] + c[2] * y[2] + c[3];
@@ -274,18 +293,46 @@ struct Hires {  // p = the 12 distinct rate constants c1..c12 in order of appear
     dy[6] = r - c[11] * y[6];
     dy[7] = -r + c[11] * y[6];
   }
-  static __device__ __forceinline__ void jac(const T* y, const T* c, T, T* J) {
+  // The Jacobian's entries as add(row, col, 1, value) with compile-time row and col (each
+  // entry once, so J[r][c] = fma(1, value, 0) = value).
+  template <class ADD>
+  static __device__ __forceinline__ void jac_visit(const T* y, const T* c, T, ADD&& add) {
+    const T one(1);
+    auto e = [&](auto r, auto col, T v) { add(r, col, one, v); };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    using I4 = std::integral_constant<int, 4>;
+    using I5 = std::integral_constant<int, 5>;
+    using I6 = std::integral_constant<int, 6>;
+    using I7 = std::integral_constant<int, 7>;
+    e(I0(), I0(), -c[0]); e(I0(), I1(), c[1]); e(I0(), I2(), c[2]);
+    e(I1(), I0(), c[0]); e(I1(), I1(), -c[4]);
+    e(I2(), I2(), -c[5]); e(I2(), I3(), c[1]); e(I2(), I4(), c[6]);
+    e(I3(), I1(), c[2]); e(I3(), I2(), c[0]); e(I3(), I3(), -c[7]);
+    e(I4(), I4(), -c[8]); e(I4(), I5(), c[1]); e(I4(), I6(), c[1]);
+    e(I5(), I3(), c[10]); e(I5(), I4(), c[0]); e(I5(), I5(), -c[9] * y[7] - c[1]);
+    e(I5(), I6(), c[10]); e(I5(), I7(), -c[9] * y[5]);
+    e(I6(), I5(), c[9] * y[7]); e(I6(), I6(), -c[11]); e(I6(), I7(), c[9] * y[5]);
+    e(I7(), I5(), -c[9] * y[7]); e(I7(), I6(), c[11]); e(I7(), I7(), -c[9] * y[5]);
+  }
+  static __host__ __device__ constexpr Pattern<8> jac_pattern() {
+    Pattern<8> s{};
+    constexpr int nz[25][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 0}, {1, 1}, {2, 2}, {2, 3},
+                               {2, 4}, {3, 1}, {3, 2}, {3, 3}, {4, 4}, {4, 5}, {4, 6},
+                               {5, 3}, {5, 4}, {5, 5}, {5, 6}, {5, 7}, {6, 5}, {6, 6},
+                               {6, 7}, {7, 5}, {7, 6}, {7, 7}};
+    for (int i = 0; i < 25; ++i) s.nz[nz[i][0]][nz[i][1]] = true;
+    return s;
+  }
+  static __device__ __forceinline__ void jac(const T* y, const T* c, T t, T* J) {
 #pragma unroll
     for (int i = 0; i < 64; ++i) J[i] = T(0);
-    J[0 * 8 + 0] = -c[0]; J[0 * 8 + 1] = c[1]; J[0 * 8 + 2] = c[2];
-    J[1 * 8 + 0] = c[0]; J[1 * 8 + 1] = -c[4];
-    J[2 * 8 + 2] = -c[5]; J[2 * 8 + 3] = c[1]; J[2 * 8 + 4] = c[6];
-    J[3 * 8 + 1] = c[2]; J[3 * 8 + 2] = c[0]; J[3 * 8 + 3] = -c[7];
-    J[4 * 8 + 4] = -c[8]; J[4 * 8 + 5] = c[1]; J[4 * 8 + 6] = c[1];
-    J[5 * 8 + 3] = c[10]; J[5 * 8 + 4] = c[0]; J[5 * 8 + 5] = -c[9] * y[7] - c[1];
-    J[5 * 8 + 6] = c[10]; J[5 * 8 + 7] = -c[9] * y[5];
-    J[6 * 8 + 5] = c[9] * y[7]; J[6 * 8 + 6] = -c[11]; J[6 * 8 + 7] = c[9] * y[5];
-    J[7 * 8 + 5] = -c[9] * y[7]; J[7 * 8 + 6] = c[11]; J[7 * 8 + 7] = -c[9] * y[5];
+    jac_visit(y, c, t, [&](auto r, auto col, T nu, T v) {
+      J[decltype(r)::value * 8 + decltype(col)::value] =
+          M<T>::fma(nu, v, J[decltype(r)::value * 8 + decltype(col)::value]);
+    });
   }
 };
 
@@ -318,7 +365,7 @@ template <class T>
 struct Pollu {  // p = (k1..k25)
   static constexpr int D = 20, P = 25, NW = 0;
   static constexpr bool autonomous = true, has_noise = false, sde_only = false, has_event = false;
-  static constexpr bool stiff_only = true;  // Rosenbrock23 only, one trajectory per thread
+  static constexpr bool stiff_only = true;  // Rosenbrock methods only, one per thread
   static __device__ __forceinline__ void f(const T* y, const T* k, T, T* dy) {
 #pragma unroll
     for (int i = 0; i < 20; ++i) dy[i] = T(0);
@@ -331,21 +378,47 @@ struct Pollu {  // p = (k1..k25)
         if (m < r.n) dy[r.sp[m]] = M<T>::fma(T(r.nu[m]), rate, dy[r.sp[m]]);
     }
   }
-  static __device__ __forceinline__ void jac(const T* y, const T* k, T, T* J) {
-#pragma unroll
-    for (int i = 0; i < 400; ++i) J[i] = T(0);
-#pragma unroll
+  // The Jacobian as a sum over the reactions: reaction j adds nu_m d(r_j)/d(y_a) (and
+  // d(r_j)/d(y_b)) to row sp_m, as add(row, col, nu, derivative) with compile-time row and
+  // col, in reaction order.
+  template <class ADD>
+  static __device__ __forceinline__ void jac_visit(const T* y, const T* k, T, ADD&& add) {
+    static_for<0, 25>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr PolluRx r = pollu_rx(j);
+      const T dra = r.b < 0 ? k[j] : k[j] * y[r.b < 0 ? 0 : r.b];
+      const T drb = r.b < 0 ? T(0) : k[j] * y[r.a];
+      static_for<0, r.n>([&](auto Q) {
+        constexpr PolluRx x = pollu_rx(j);  // (a lambda cannot read the enclosing one's r at
+                                            // compile time)
+        constexpr int q = decltype(Q)::value;
+        constexpr int row = x.sp[q];
+        add(std::integral_constant<int, row>(), std::integral_constant<int, x.a>(), T(x.nu[q]),
+            dra);
+        if constexpr (x.b >= 0)
+          add(std::integral_constant<int, row>(), std::integral_constant<int, (x.b < 0 ? 0 : x.b)>(),
+              T(x.nu[q]), drb);
+      });
+    });
+  }
+  static __host__ __device__ constexpr Pattern<20> jac_pattern() {
+    Pattern<20> s{};
     for (int j = 0; j < 25; ++j) {
       const PolluRx r = pollu_rx(j);
-      const T dra = r.b < 0 ? k[j] : k[j] * y[r.b];
-      const T drb = r.b < 0 ? T(0) : k[j] * y[r.a];
-#pragma unroll
-      for (int m = 0; m < 5; ++m)
-        if (m < r.n) {
-          J[r.sp[m] * 20 + r.a] = M<T>::fma(T(r.nu[m]), dra, J[r.sp[m] * 20 + r.a]);
-          if (r.b >= 0) J[r.sp[m] * 20 + r.b] = M<T>::fma(T(r.nu[m]), drb, J[r.sp[m] * 20 + r.b]);
-        }
+      for (int m = 0; m < r.n; ++m) {
+        s.nz[r.sp[m]][r.a] = true;
+        if (r.b >= 0) s.nz[r.sp[m]][r.b] = true;
+      }
     }
+    return s;
+  }
+  static __device__ __forceinline__ void jac(const T* y, const T* k, T t, T* J) {
+#pragma unroll
+    for (int i = 0; i < 400; ++i) J[i] = T(0);
+    jac_visit(y, k, t, [&](auto r, auto c, T nu, T v) {
+      J[decltype(r)::value * 20 + decltype(c)::value] =
+          M<T>::fma(nu, v, J[decltype(r)::value * 20 + decltype(c)::value]);
+    });
   }
 };
 
@@ -724,6 +797,227 @@ struct LUDyn {
   }
 };
 
+// ------------------------------------------------------------------------------------------
+// Sparse LU of W = I - hg J on a model's fixed Jacobian pattern (the large stiff models,
+// Appendix: HIRES, POLLU).  Everything about the structure is decided at compile time:
+//  * the elimination order: greedy minimum degree on the symmetrised pattern (the variable
+//    with the fewest remaining neighbours first, ties to the lower index; its neighbours then
+//    form a clique);
+//  * the filled pattern of the symmetrically permuted matrix P W P^T (symbolic elimination)
+//    and a compressed slot for each of its entries;
+//  * the factorisation and the two triangular solves as flat operation lists, expanded into
+//    straight-line code with constant slots (no index arithmetic, no zero tests).
+// The numeric factorisation exchanges no rows and checks, column by column, that partial
+// pivoting would not exchange any either (|a_kk| >= |a_rk| for every r below k; a NaN fails):
+// when every check passes the factors are those of partial pivoting on P W P^T.  When one
+// fails the step factors W again, densely and with row exchanges (LUDyn).  On POLLU in
+// natural order partial pivoting exchanges rows in most factorisations and the factors fill
+// 262 of 400 entries; in the minimum-degree order the factors hold 109 entries, the
+// elimination takes 162 multiply-adds, and the checks held on every factorisation of the
+// oracle's solves (Rosenbrock23, Rodas4, Rodas5P at tolerance 1e-6, also at 3x the step).
+
+enum SpKind : short { SP_CHECK, SP_RCP, SP_MUL, SP_FMA, SP_DIAG };
+
+struct SpOp {
+  short kind, d, s1, s2;
+};
+
+template <int D>
+struct SpPlan {
+  static constexpr int MAXOP = 1024;
+  int order[D];      // order[k]: the variable eliminated k-th
+  int pos[D];        // pos[v]: the position of variable v
+  int slot[D][D];    // compressed slot of entry (position r, position c); -1 outside the fill
+  int nnz;
+  bool w_entry[D * D];  // slot holds a structural entry of W (of J, or the diagonal)
+  bool is_diag[D * D];
+  SpOp fac[MAXOP];   // factorisation: checks, reciprocal pivots, multipliers, updates
+  int nfac;
+  SpOp fwd[D * D];   // forward substitution with unit L (positions)
+  int nfwd;
+  SpOp bwd[D * D];   // back substitution with U (diagonal stored inverted)
+  int nbwd;
+};
+
+template <int D>
+__host__ __device__ constexpr SpPlan<D> make_sp_plan(const Pattern<D> J) {
+  SpPlan<D> P{};
+  // minimum degree on the symmetrised pattern
+  bool G[D][D] = {};
+  bool alive[D] = {};
+  for (int r = 0; r < D; ++r) {
+    alive[r] = true;
+    for (int c = 0; c < D; ++c) G[r][c] = J.nz[r][c] || J.nz[c][r] || r == c;
+  }
+  for (int k = 0; k < D; ++k) {
+    int best = -1, bdeg = D + 1;
+    for (int v = 0; v < D; ++v) {
+      if (!alive[v]) continue;
+      int deg = 0;
+      for (int u = 0; u < D; ++u) deg += (alive[u] && G[v][u]) ? 1 : 0;
+      if (deg < bdeg) {
+        bdeg = deg;
+        best = v;
+      }
+    }
+    P.order[k] = best;
+    P.pos[best] = k;
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b < D; ++b)
+        if (alive[a] && alive[b] && a != best && b != best && G[best][a] && G[best][b])
+          G[a][b] = true;
+    alive[best] = false;
+  }
+  // filled pattern of P W P^T
+  bool F[D][D] = {};
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) F[r][c] = J.nz[P.order[r]][P.order[c]] || r == c;
+  bool W[D][D] = {};
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) W[r][c] = F[r][c];
+  for (int k = 0; k < D; ++k)
+    for (int r = k + 1; r < D; ++r)
+      if (F[r][k])
+        for (int j = k + 1; j < D; ++j)
+          if (F[k][j]) F[r][j] = true;
+  int e = 0;
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) {
+      P.slot[r][c] = F[r][c] ? e : -1;
+      if (F[r][c]) {
+        P.w_entry[e] = W[r][c];
+        P.is_diag[e] = r == c;
+        ++e;
+      }
+    }
+  P.nnz = e;
+  // factorisation, right-looking in position order
+  int n = 0;
+  for (int k = 0; k < D; ++k) {
+    const short kk = (short)P.slot[k][k];
+    for (int r = k + 1; r < D; ++r)
+      if (F[r][k]) P.fac[n++] = SpOp{SP_CHECK, kk, (short)P.slot[r][k], 0};
+    P.fac[n++] = SpOp{SP_RCP, kk, 0, 0};
+    for (int r = k + 1; r < D; ++r) {
+      if (!F[r][k]) continue;
+      const short rk = (short)P.slot[r][k];
+      P.fac[n++] = SpOp{SP_MUL, rk, kk, 0};
+      for (int j = k + 1; j < D; ++j)
+        if (F[k][j]) P.fac[n++] = SpOp{SP_FMA, (short)P.slot[r][j], rk, (short)P.slot[k][j]};
+    }
+  }
+  P.nfac = n;
+  // solves, column-oriented (each finished unknown updates the rows that use it)
+  n = 0;
+  for (int k = 0; k < D; ++k)
+    for (int r = k + 1; r < D; ++r)
+      if (F[r][k]) P.fwd[n++] = SpOp{SP_FMA, (short)r, (short)P.slot[r][k], (short)k};
+  P.nfwd = n;
+  n = 0;
+  for (int k = D - 1; k >= 0; --k) {
+    P.bwd[n++] = SpOp{SP_DIAG, (short)k, (short)P.slot[k][k], 0};
+    for (int r = 0; r < k; ++r)
+      if (F[r][k]) P.bwd[n++] = SpOp{SP_FMA, (short)r, (short)P.slot[r][k], (short)k};
+  }
+  P.nbwd = n;
+  return P;
+}
+
+template <class RHS>
+struct SpPlanOf {
+  static constexpr SpPlan<RHS::D> plan = make_sp_plan<RHS::D>(RHS::jac_pattern());
+  static_assert(plan.nfac <= SpPlan<RHS::D>::MAXOP, "factorisation list too long");
+};
+
+template <class RHS>
+struct HasSparseJac {
+ private:
+  template <class R>
+  static constexpr bool test(decltype(R::jac_pattern())*) { return true; }
+  template <class R>
+  static constexpr bool test(...) { return false; }
+
+ public:
+  static constexpr bool value = test<RHS>(nullptr);
+};
+
+template <class RHS, class T>
+struct SparseRosLU {
+  static constexpr int D = RHS::D;
+  typedef SpPlanOf<RHS> PL;
+  T a[PL::plan.nnz];
+  bool dense;       // a pivot check failed: lud holds the row-exchanging factorisation
+  LUDyn<T, D> lud;
+
+  // W = I - hg J at (u, p, t), factored
+  __device__ __forceinline__ void factor(const T* u, const T* p, T t, T hg) {
+    typedef M<T> m;
+    static_for<0, PL::plan.nnz>([&](auto E) { a[decltype(E)::value] = T(0); });
+    RHS::jac_visit(u, p, t, [&](auto R, auto C, T nu, T v) {
+      constexpr int e = PL::plan.slot[PL::plan.pos[decltype(R)::value]][PL::plan.pos[decltype(C)::value]];
+      static_assert(e >= 0, "a Jacobian entry outside the declared pattern");
+      a[e] = m::fma(nu, v, a[e]);
+    });
+    static_for<0, PL::plan.nnz>([&](auto E) {
+      constexpr int e = decltype(E)::value;
+      constexpr bool diag = PL::plan.is_diag[e];
+      if constexpr (PL::plan.w_entry[e]) a[e] = m::fma(-hg, a[e], diag ? T(1) : T(0));
+    });
+    bool bad = false;
+    static_for<0, PL::plan.nfac>([&](auto I) {
+      constexpr SpOp o = PL::plan.fac[decltype(I)::value];
+      if constexpr (o.kind == SP_CHECK) {
+        bad = bad || !(m::abs(a[o.s1]) <= m::abs(a[o.d]));
+      } else if constexpr (o.kind == SP_RCP) {
+        a[o.d] = m::rcp(a[o.d]);
+      } else if constexpr (o.kind == SP_MUL) {
+        a[o.d] = a[o.d] * a[o.s1];
+      } else {
+        a[o.d] = m::fma(-a[o.s1], a[o.s2], a[o.d]);
+      }
+    });
+    dense = bad;
+    if (bad) {  // partial pivoting would exchange rows here: the dense factorisation
+      RHS::jac(u, p, t, &lud.a[0][0]);
+#pragma unroll 1
+      for (int r = 0; r < D; ++r)
+#pragma unroll 1
+        for (int c = 0; c < D; ++c) lud.a[r][c] = m::fma(-hg, lud.a[r][c], (r == c) ? T(1) : T(0));
+      lud.factor();
+    }
+  }
+
+  // x = W^{-1} b
+  __device__ __forceinline__ void solve(const T* b, T* x) const {
+    typedef M<T> m;
+    if (dense) {
+      lud.solve(b, x);
+      return;
+    }
+    T y[D];
+    static_for<0, D>([&](auto K) {
+      constexpr int k = decltype(K)::value, v = PL::plan.order[k];
+      y[k] = b[v];
+    });
+    static_for<0, PL::plan.nfwd>([&](auto I) {
+      constexpr SpOp o = PL::plan.fwd[decltype(I)::value];
+      y[o.d] = m::fma(-a[o.s1], y[o.s2], y[o.d]);
+    });
+    static_for<0, PL::plan.nbwd>([&](auto I) {
+      constexpr SpOp o = PL::plan.bwd[decltype(I)::value];
+      if constexpr (o.kind == SP_DIAG) {
+        y[o.d] = y[o.d] * a[o.s1];
+      } else {
+        y[o.d] = m::fma(-a[o.s1], y[o.s2], y[o.d]);
+      }
+    });
+    static_for<0, D>([&](auto K) {
+      constexpr int k = decltype(K)::value, v = PL::plan.order[k];
+      x[v] = y[k];
+    });
+  }
+};
+
 // W = I - hg J for a Rosenbrock step (hg = h times the method's diagonal coefficient), factored
 // into lu: J and W in registers for small D, all in the one local-memory matrix for large D (a
 // thread's footprint stays D^2 values, so the resident threads' matrices fit in L1).
@@ -731,7 +1025,9 @@ template <class RHS, class T, class LUT>
 __device__ __forceinline__ void ros_factor(const T* u, const T* p, T t, T hg, LUT& lu) {
   constexpr int D = RHS::D;
   typedef M<T> m;
-  if constexpr (D < 12) {
+  if constexpr (HasSparseJac<RHS>::value) {
+    lu.factor(u, p, t, hg);
+  } else if constexpr (D < 12) {
     T Jf[D * D];
     RHS::jac(u, p, t, Jf);
     T W[D][D];
@@ -761,6 +1057,12 @@ __device__ __forceinline__ void ros_factor(const T* u, const T* p, T t, T hg, LU
 template <class T, int D>
 using RosLU = typename std::conditional<(D < 8), LU<T, D>, LUDyn<T, D>>::type;
 
+// the factorisation a Rosenbrock step of model RHS uses: the sparse one where the model
+// declares its Jacobian pattern, else the dense one for its size
+template <class RHS, class T>
+using RosLUOf = typename std::conditional<HasSparseJac<RHS>::value, SparseRosLU<RHS, T>,
+                                          RosLU<T, RHS::D>>::type;
+
 // One Rosenbrock23 (ode23s) step from (u, t) with f0 = f(u, t); W = I - h d J:
 //   k1 = W^-1 f0,  f1 = f(u + h/2 k1),  k2 = W^-1 (f1 - k1) + k1,  u_{n+1} = u + h k2,
 //   f2 = f(u_{n+1}),  k3 = W^-1 (f2 - e32 (k2 - f1) - 2 (k1 - f0)),  err = h/6 (k1 - 2 k2 + k3).
@@ -774,7 +1076,7 @@ __device__ __forceinline__ void ros23_step(const T* u, const T* p, T t, T h, con
   const T d = T(0.29289321881345247559915563789515);   // 1 / (2 + sqrt 2)
   const T e32 = T(7.4142135623730950488016887242097);  // 6 + sqrt 2
   const T hd = h * d;
-  RosLU<T, D> lu;
+  RosLUOf<RHS, T> lu;
   ros_factor<RHS, T>(u, p, t, hd, lu);
   T k1[D], k2[D], k3[D], f1[D], U[D], v[D];
   lu.solve(f0, k1);
@@ -881,7 +1183,7 @@ __device__ __forceinline__ void rodas_step(const T* u, const T* p, T t, T h, con
   constexpr int D = RHS::D, S = TAB::S;
   typedef M<T> m;
   const T hg = h * T(TAB::gamma);
-  RosLU<T, D> lu;
+  RosLUOf<RHS, T> lu;
   ros_factor<RHS, T>(u, p, t, hg, lu);
   T U[S][D], g[D], fi[D], v[D];
 #pragma unroll

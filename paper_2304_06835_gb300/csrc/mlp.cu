@@ -597,7 +597,7 @@ struct Compact {
 
 __global__ void k_gate(long long B, int E, const float* __restrict__ x,
                        const float* __restrict__ ym, Box box, float tau, float* __restrict__ mean,
-                       unsigned char* __restrict__ fb, unsigned long long* n_fb, Compact cp) {
+                       float* __restrict__ spread, unsigned char* __restrict__ fb, unsigned long long* n_fb, Compact cp) {
   const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool f = false;
   if (b < B) {
@@ -620,6 +620,7 @@ __global__ void k_gate(long long B, int E, const float* __restrict__ x,
       smax = fmaxf(smax, sqrtf(q / (float)E));
       if (mean) mean[b * 3 + j] = mu;
     }
+    if (spread) spread[b] = smax;
     f = out || !(smax <= tau);
     fb[b] = f ? 1 : 0;
   }
@@ -1365,7 +1366,7 @@ int ens_mlp_forward(ens_mlp* m, int member, long long B, const float* x, float* 
 }
 
 int ens_mlp_gate(ens_mlp* m, long long B, const float* x, const float* y_members, float tau,
-                 float* y_mean, unsigned char* fallback, unsigned long long* n_fallback,
+                 float* y_mean, float* spread, unsigned char* fallback, unsigned long long* n_fallback,
                  long long* fb_index, float* fb_params, float* fb_u0, float* fb_tspan, double t0,
                  double t1, void* stream) {
   if (!m) return mfail(ENS_EINVAL, "null network");
@@ -1376,7 +1377,7 @@ int ens_mlp_gate(ens_mlp* m, long long B, const float* x, const float* y_members
     return mfail(ENS_EINVAL, "compaction needs fb_params, fb_u0, fb_tspan and n_fallback");
   Compact cp{fb_index, fb_params, fb_u0, fb_tspan, (float)t0, (float)t1};
   k_gate<<<blocks_for(B), 256, 0, (cudaStream_t)stream>>>(B, m->E, x, y_members, m->box, tau,
-                                                          y_mean, fallback, n_fallback, cp);
+                                                          y_mean, spread, fallback, n_fallback, cp);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? ENS_OK : mfail(ENS_ECUDA, cudaGetErrorString(e));
 }

@@ -137,7 +137,7 @@ cudaError_t dispatch_model(int alg, const SolveArgs* a, const LaunchCfg& cfg, cu
                            bool* supported, cudaFuncAttributes* attr, int* bps,
                            CostScratch* cs) {
   *supported = true;
-  if constexpr (RHS::stiff_only) {  // large stiff models: Rosenbrock23 only
+  if constexpr (RHS::stiff_only) {  // large stiff models: the Rosenbrock methods only
     if (alg == ENS_ROS23) return run_integ<Adaptive<RHS, T, METH_ROS23>>(a, cfg, s, attr, bps, cs);
     if (alg == ENS_RODAS4)
       return run_integ<Adaptive<RHS, T, METH_RODAS4>>(a, cfg, s, attr, bps, cs);

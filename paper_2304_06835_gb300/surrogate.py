@@ -119,10 +119,12 @@ class SurrogateMLP:
         return out
 
     def gate(self, x, y_members, tau, mean=None, fallback=None, count=None, compact=None,
-             t0=0.0, t1=1.0):
+             t0=0.0, t1=1.0, spread=None):
         """(mean [B, 3], fallback uint8 [B], n_fallback device counter).  compact: optional
         dict of device buffers index int64 [B], params / u0 float32 [B, 3], tspan [B, 2] that
-        receive the fallback samples as a row-major solver problem on [t0, t1]."""
+        receive the fallback samples as a row-major solver problem on [t0, t1].  spread:
+        optional float32 [B] that receives the members' disagreement the gate compares with
+        tau (the largest per-component population standard deviation)."""
         x, _ = self._xy(x)
         B = x.shape[0]
         if mean is None:
@@ -134,7 +136,7 @@ class SurrogateMLP:
         c = compact or {}
         _lib.check(_lib.lib().ens_mlp_gate(
             self._h, B, _ptr(x), _ptr(y_members.contiguous()), float(tau), _ptr(mean),
-            _ptr(fallback), _ptr(count), _ptr(c.get("index")), _ptr(c.get("params")),
+            _ptr(spread), _ptr(fallback), _ptr(count), _ptr(c.get("index")), _ptr(c.get("params")),
             _ptr(c.get("u0")), _ptr(c.get("tspan")), float(t0), float(t1), _stream(self.device)))
         return mean, fallback, count
 
@@ -190,17 +192,18 @@ def lorenz_u1(solver, x, *, t1=1.0, tol=1e-10, dtype=torch.float64):
     return out.t().float().contiguous(), st
 
 
-def member_spread(y_members):
-    """Largest per-component population standard deviation over the members, [B]."""
-    return y_members.double().std(dim=0, unbiased=False).max(dim=1).values
-
-
 def calibrate_tau(net, x_val, y_val, max_err):
-    """Largest gate threshold tau for which every in-box validation sample with member spread
-    <= tau has a mean-prediction error (max over components) <= max_err."""
+    """Largest gate threshold tau for which every validation sample with member spread <= tau
+    has a mean-prediction error (max over components) <= max_err.  The spread and the mean
+    are the gate kernel's own (ens_mlp_gate), so the threshold is calibrated on the statistic
+    the gate compares with it."""
     ym = net.forward(x_val)
-    spread = member_spread(ym).cpu().numpy()
-    err = (ym.double().mean(dim=0) - y_val.double()).abs().max(dim=1).values.cpu().numpy()
+    B = ym.shape[1]
+    spread_d = torch.empty(B, dtype=torch.float32, device=ym.device)
+    mean_d, _, _ = net.gate(x_val, ym, float("inf"), spread=spread_d)
+    spread = spread_d.cpu().numpy().astype(np.float64)
+    err = np.abs(mean_d.cpu().numpy().astype(np.float64)
+                 - y_val.cpu().numpy().astype(np.float64)).max(axis=1)
     order = np.argsort(spread)
     bad = np.flatnonzero(err[order] > max_err)
     if bad.size == 0:

@@ -179,9 +179,13 @@ def test_gate_matches_oracle(net):
     ym = rng.normal(0, 1, (2, B, 3)).astype(np.float32)
     ym[:, ::3] *= 1e-3  # a third of the samples agree closely
     tau = 0.05
-    mean, fb, cnt = net.gate(cuda32(x), cuda32(ym), tau)
+    spread = torch.empty(B, dtype=torch.float32, device="cuda")
+    mean, fb, cnt = net.gate(cuda32(x), cuda32(ym), tau, spread=spread)
     mean_ref, fb_ref = mlp.gate(ym.astype(np.float64), x.astype(np.float64), BOX, tau)
-    std = np.sqrt(((ym - ym.mean(0)) ** 2).mean(0)).max(axis=1)
+    y64 = ym.astype(np.float64)
+    std = np.sqrt(((y64 - y64.mean(0)) ** 2).mean(0)).max(axis=1)
+    # the kernel's statistic is the population standard deviation in FP32 (two members here)
+    np.testing.assert_allclose(spread.cpu().numpy(), std, rtol=1e-5, atol=1e-7)
     far = np.abs(std - tau) > 1e-5
     np.testing.assert_array_equal(fb.cpu().numpy()[far].astype(bool), fb_ref[far])
     assert int(cnt.item()) == int(fb.cpu().numpy().sum())
