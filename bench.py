@@ -62,10 +62,11 @@ SM_MAX_MHZ = 2070.0
 #     floating-point part -> 104 (the Philox integer work runs on the integer lanes).
 # Rosenbrock23 attempt on a D-state model: W = I - h d J (D^2), LU (D^3 / 3 + pivoting),
 #   three solves (3 D^2), the stage combinations, error and norm (~18 D), the Jacobian and
-#   two f evaluations (model terms): Robertson 140; Orego 140.  HIRES and POLLU factor W by
-#   the sparse LU on their fixed Jacobian patterns; their FP64 work is measured (ncu: DFMA +
-#   DADD + DMUL over the bench solve's attempts, all 8,192 trajectories): HIRES 378, POLLU
-#   1,397 (the dense model's 4,930 counted the full 20 x 20 factorisation and solves).
+#   two f evaluations (model terms): Robertson 140.  The stiff test models' FP64 work is
+#   measured (ncu: DFMA + DADD + DMUL over the bench solve's attempts, all 8,192
+#   trajectories): Orego 165 (the model's 140 leaves out the divisions' Newton steps);
+#   HIRES 378 and POLLU 1,397 with the sparse LU on their fixed Jacobian patterns (the dense
+#   model's 4,930 for POLLU counted the full 20 x 20 factorisation and solves).
 # Rosenbrock attempts on Robertson, measured: ncu's FP64 instruction classes (DFMA + DADD +
 #   DMUL, N = 65,536 of the bench distribution, tol 1e-6) over the solve's attempts give 122
 #   (Rosenbrock23), 242 (Rodas4, S = 6) and 337 (Rodas5P, S = 8) per attempt -- below the
@@ -79,7 +80,7 @@ SM_MAX_MHZ = 2070.0
 OPS_PER_ATTEMPT = {"tsit5": 175, "tsit5_fixed": 117, "rk4": 48, "ros23": 122, "em": 25,
                    "siea": 45,
                    "adjoint": 423, "crn_em": 224, "crn_em_f64": 104, "ball": 84,
-                   "ball_event_scan": 136, "ros23_orego": 140, "ros23_hires": 378,
+                   "ball_event_scan": 136, "ros23_orego": 165, "ros23_hires": 378,
                    "ros23_pollu": 1397, "rodas4": 242, "rodas5p": 337, "rodas5p_pollu": 3171}
 
 

@@ -12,8 +12,12 @@ D = 8, POLLU D = 20), FP64, through the C ABI, against the oracle:
   of a stiff W) move every step size a little and the stiff dynamics amplify that; measured
   0.072 of the tolerance on HIRES, far below the solutions' own error against the
   reference (1.5e-5 there, equal on both sides);
-* the models without events or noise reject Euler-Maruyama; HIRES and POLLU take only
-  Rosenbrock23.
+* HIRES and POLLU factor W by the compile-time sparse LU (minimum-degree order) with a
+  partial-pivoting check per column and a dense fallback: POLLU with every rate constant
+  scaled by 10^U[-1, 1] makes the checks fail on some factorisations (counted here on the
+  oracle's states), so warps mix sparse and fallback steps; the results meet the same
+  bounds against the oracle;
+* the stiff models reject the non-Rosenbrock methods.
 """
 import numpy as np
 import pytest
@@ -50,6 +54,50 @@ def test_ros23_stiff_models_fp64(model, N):
     assert eq.mean() >= 0.8
     d = np.abs(o[eq] - same[eq]) / (tol + tol * np.abs(same[eq]))
     print("%s: GPU - oracle, in units of the tolerance: max %.3g" % (model, d.max()))
+    assert d.max() <= 0.1
+    s.close()
+
+
+def test_pollu_sparse_lu_fallback_fp64():
+    from paper_2304_06835_gb300 import EnsembleSolver
+    from test_sparse_plan_cpu import jac_pattern, min_degree
+    N, tol = 256, 1e-6
+    P, U, T = workloads.stiff("pollu", N, seed=23)
+    P = P * 10.0 ** np.random.default_rng(7).uniform(-1.0, 1.0, P.shape)
+    order = min_degree(jac_pattern("pollu", 20))
+    # the oracle's own states and steps: how many factorisations would fail a check
+    t, u, n, _, _, _ = oracle.solve_steps("pollu", "ros23", P[:48], U[:48], T[:48], 4096,
+                                          abstol=tol, reltol=tol)
+    fails, hit = 0, set()
+    gamma = 1.0 / (2.0 + np.sqrt(2.0))
+    for i in range(48):
+        for k in range(min(n[i], 4096) - 1):
+            A = np.eye(20) - (t[i, k + 1] - t[i, k]) * gamma * oracle.jac_u("pollu", u[i, k], P[i])
+            A = A[np.ix_(order, order)]
+            for c in range(19):
+                if np.abs(A[c + 1:, c]).max() > abs(A[c, c]):
+                    fails += 1
+                    hit.add(i)
+                    break
+                l = A[c + 1:, c] / A[c, c]
+                A[c + 1:, c + 1:] -= np.outer(l, A[c, c + 1:])
+                A[c + 1:, c] = l
+    print("pivot checks failing on %d factorisations of %d of 48 trajectories" % (fails, len(hit)))
+    assert len(hit) >= 3
+    s = EnsembleSolver("pollu")
+    ref, _, _ = oracle.solve("pollu", "ros23", P, U, T, abstol=1e-10, reltol=1e-10)
+    same, sst, sstats = oracle.solve("pollu", "ros23", P, U, T, abstol=tol, reltol=tol)
+    out, st, stats = s.solve(dev(P), dev(U), dev(T), alg="ros23", abstol=tol, reltol=tol,
+                             want_stats=True)
+    o = out.cpu().numpy()
+    assert int(st.abs().sum()) == 0 and np.all(sst == 0)
+    e_gpu, e_orc = np.abs(o - ref), np.abs(same - ref)
+    assert np.all(e_gpu <= 3 * e_orc + 10 * (tol + tol * np.abs(ref)))
+    g = stats.cpu().numpy().T
+    eq = np.all(g[:, :2] == sstats[:, :2], axis=1)
+    d = np.abs(o[eq] - same[eq]) / (tol + tol * np.abs(same[eq]))
+    print("identical step counts %.3f, GPU - oracle on those max %.3g tol" % (eq.mean(), d.max()))
+    assert eq.mean() >= 0.8
     assert d.max() <= 0.1
     s.close()
 
