@@ -74,6 +74,11 @@ SM_MAX_MHZ = 2070.0
 #   and norm), which counted constant-zero and folded terms; the measured counts are used.
 #   POLLU (D = 20) under Rodas5P, measured the same way: 3,171 (the sparse LU, 8 solves of
 #   109 multiply-adds, 8 f evaluations, the stage sums, error and norm).
+# Dense output (Tsit5 interpolant at save times the steps are not cut at): per accepted step
+#   that saves, the interpolant's coefficients 4 x 7 x D = 84 multiply-adds, per save Horner
+#   4 x D plus theta, ~14 -> ~64 per save at 256 saves over ~150 steps; measured 70.4 FMA-pipe
+#   lane operations per save (ncu FP32 classes of the dense kernel minus the plain one on
+#   131,072 trajectories of the same workload), 70 is counted on top of the attempts.
 # Bouncing ball (D = 2, f costs nothing): a Tsit5 attempt = stage combinations 54, error 14,
 #   norm 13, controller 3 -> 84; each accepted step adds the event scan: the dense
 #   polynomial 4 x 7 x 2 FMA + 8 scalings = 64 and 9 checkpoints x 8 = 72 -> 136.
@@ -82,6 +87,7 @@ OPS_PER_ATTEMPT = {"tsit5": 175, "tsit5_fixed": 117, "rk4": 48, "ros23": 122, "e
                    "adjoint": 423, "crn_em": 224, "crn_em_f64": 104, "ball": 84,
                    "ball_event_scan": 136, "ros23_orego": 165, "ros23_hires": 378,
                    "ros23_pollu": 1397, "rodas4": 242, "rodas5p": 337, "rodas5p_pollu": 3171}
+OPS_PER_DENSE_SAVE = 70
 
 
 def ops_key(w):
@@ -481,12 +487,16 @@ class SolveRunner:
                          "ops_per_accepted_event_scan": OPS_PER_ATTEMPT["ball_event_scan"],
                          "trajectories_ok": ok, "autotuned_shape": self.tuned}
         extra = {}
+        save_ops = 0
+        if self.w.get("dense") and self.w.get("saves"):  # the interpolant at every save time
+            save_ops = ok * self.w["saves"] * OPS_PER_DENSE_SAVE
+            extra.update(saves_per_launch=ok * self.w["saves"], ops_per_save=OPS_PER_DENSE_SAVE)
         if self.moments:  # the job's ensemble mean and variance of each component at tf
             from paper_2304_06835_gb300 import merge_moments
             n, mean, var = merge_moments(self.parts)
             extra["moments"] = {"n": int(n), "mean": [float(v) for v in mean],
                                 "var": [float(v) for v in var]}
-        return attempts * OPS_PER_ATTEMPT[ops_key(self.w)], {
+        return attempts * OPS_PER_ATTEMPT[ops_key(self.w)] + save_ops, {
             "attempts_per_launch": attempts, "ops_per_attempt": OPS_PER_ATTEMPT[ops_key(self.w)],
             "trajectories_ok": ok, "autotuned_shape": self.tuned, **extra}
 
