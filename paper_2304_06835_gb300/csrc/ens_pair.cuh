@@ -61,8 +61,8 @@ struct Rhs2<Lorenz<float>> {
   }
 };
 
-// One Tsit5 step on a pair (tsit5_step with WANT_ERR, same association).
-template <class RHS>
+// One Tsit5 step on a pair (tsit5_step, same association); es only with WANT_ERR.
+template <class RHS, bool WANT_ERR = true>
 __device__ __forceinline__ void tsit5_step2(const float2* u, const float2* p, float2 h,
                                             const float2* k1, float2* unew, float2* es,
                                             float2* k7) {
@@ -113,6 +113,7 @@ __device__ __forceinline__ void tsit5_step2(const float2* u, const float2* p, fl
     unew[j] = fma2(h, s, u[j]);
   }
   F::f(unew, p, k7);
+  if constexpr (!WANT_ERR) return;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     float2 s = mul2(bc2(float(Ts5::bt1)), k1[j]);
@@ -313,6 +314,72 @@ __device__ __forceinline__ void persistent_pair_loop(const SolveArgs& a) {
 template <class RHS>
 __global__ void k_persistent_pair(const SolveArgs a) {
   persistent_pair_loop<RHS>(a);
+}
+
+// Fixed-step Tsit5 on two trajectories per thread (FP32, final state only, the direct
+// schedule): the two lanes take the scalar integrator's steps side by side, the last step of
+// each lane shortened to land on its tf as in Fixed::one_step; once one lane's steps are
+// done it keeps its state (selects) while the other finishes.  Initialisation and output are
+// the scalar integrator's, so results, status and counters equal the one-per-thread kernel's
+// bit for bit.  With equal step counts (one tspan for the whole ensemble) no lane idles.
+template <class RHS>
+__global__ void k_direct_pair(const SolveArgs a) {
+  static_assert(RHS::autonomous, "the paired integrator passes no time to f");
+  typedef Fixed<RHS, float, METH_FIX_TSIT5> Scalar;
+  constexpr int D = RHS::D, P = RHS::P;
+  const long long stride = 2LL * gridDim.x * blockDim.x;
+  for (long long i0 = 2LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x); i0 < a.N;
+       i0 += stride) {
+    const bool two = i0 + 1 < a.N;
+    Scalar s0, s1;
+    s0.init(i0, a);
+    s1.init(two ? i0 + 1 : i0, a);  // a lone last trajectory: lane 1 repeats it, unwritten
+    float2 u[D], fk[D], p[P];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      u[j] = make_float2(s0.u[j], s1.u[j]);
+      fk[j] = make_float2(s0.fk[j], s1.fk[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) p[j] = make_float2(s0.p[j], s1.p[j]);
+    const long long m0 = s0.nrun, m1 = two ? s1.nrun : 0;
+    const long long last0 = s0.n - 1, last1 = s1.n - 1;
+    const float hr = s0.h_reg, hl0 = s0.h_last, hl1 = s1.h_last;
+    const long long mlo = m0 < m1 ? m0 : m1, mhi = m0 < m1 ? m1 : m0;
+    long long k = 0;
+    for (; k < mlo; ++k) {  // both lanes step
+      const float2 h = make_float2(k == last0 ? hl0 : hr, k == last1 ? hl1 : hr);
+      float2 unew[D], k7[D];
+      tsit5_step2<RHS, false>(u, p, h, fk, unew, nullptr, k7);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        u[j] = unew[j];
+        fk[j] = k7[j];
+      }
+    }
+    for (; k < mhi; ++k) {  // one lane steps, the other keeps its final state
+      const bool l0 = k < m0, l1 = k < m1;
+      const float2 h = make_float2(k == last0 ? hl0 : hr, k == last1 ? hl1 : hr);
+      float2 unew[D], k7[D];
+      tsit5_step2<RHS, false>(u, p, h, fk, unew, nullptr, k7);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        u[j] = make_float2(l0 ? unew[j].x : u[j].x, l1 ? unew[j].y : u[j].y);
+        fk[j] = make_float2(l0 ? k7[j].x : fk[j].x, l1 ? k7[j].y : fk[j].y);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      s0.u[j] = u[j].x;
+      s1.u[j] = u[j].y;
+    }
+    s0.k = m0;
+    s0.finish(a);
+    if (two) {
+      s1.k = m1;
+      s1.finish(a);
+    }
+  }
 }
 
 }  // namespace ens

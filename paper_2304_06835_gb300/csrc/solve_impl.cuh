@@ -20,6 +20,17 @@ struct PairOf<Adaptive<RHS, float, METH_TSIT5>> {
   typedef RHS rhs;
 };
 
+// Fixed-step integrators with a paired direct kernel (k_direct_pair).
+template <class I>
+struct DirectPairOf {
+  static constexpr bool ok = false;
+};
+template <class RHS>
+struct DirectPairOf<Fixed<RHS, float, METH_FIX_TSIT5>> {
+  static constexpr bool ok = RHS::autonomous && !RHS::has_event;
+  typedef RHS rhs;
+};
+
 // dynamic shared memory of a launch (the dense saves' staging)
 template <class I>
 size_t dyn_smem(int block) {
@@ -77,6 +88,16 @@ cudaError_t launch_persistent(const SolveArgs& a, const LaunchCfg& cfg, cudaStre
 template <class I>
 cudaError_t launch_integ(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t s) {
   if (cfg.schedule == ENS_SCHED_DIRECT) {
+    if constexpr (DirectPairOf<I>::ok) {
+      // two trajectories per thread in lockstep on the paired FP32 instructions (final
+      // state only)
+      if (cfg.tpt == 2 && a.n_save == 0) {
+        const long long pairs = (a.N + 2LL * cfg.block - 1) / (2LL * cfg.block);
+        const int grid = (int)std::min<long long>(std::max<long long>(pairs, 1), 1LL << 30);
+        k_direct_pair<typename DirectPairOf<I>::rhs><<<grid, cfg.block, 0, s>>>(a);
+        return cudaGetLastError();
+      }
+    }
     const long long blocks = (a.N + cfg.block - 1) / cfg.block;
     const int grid = (int)std::min<long long>(blocks, 1LL << 30);
     if (cfg.block > I::kMaxBlock) return cudaErrorLaunchOutOfResources;
@@ -98,8 +119,11 @@ cudaError_t launch_integ(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t 
 template <class I>
 cudaError_t attrs_integ(const LaunchCfg& cfg, cudaFuncAttributes* attr, int* bps) {
   const void* fn = nullptr;
-  if (cfg.schedule == ENS_SCHED_DIRECT) fn = (const void*)k_direct<I>;
-  else if (cfg.tpt == 1 || I::kMaxTpt == 1) fn = (const void*)k_persistent<I, 1>;
+  if (cfg.schedule == ENS_SCHED_DIRECT) {
+    fn = (const void*)k_direct<I>;
+    if constexpr (DirectPairOf<I>::ok)
+      if (cfg.tpt == 2) fn = (const void*)k_direct_pair<typename DirectPairOf<I>::rhs>;
+  } else if (cfg.tpt == 1 || I::kMaxTpt == 1) fn = (const void*)k_persistent<I, 1>;
   else if constexpr (I::kMaxTpt > 1) {
     if (cfg.tpt == 2) fn = (const void*)k_persistent<I, 2>;
     else if (cfg.tpt == 4) fn = (const void*)k_persistent<I, 4>;

@@ -417,6 +417,63 @@ def test_paired_lockstep_generic_rhs(S):
     np.testing.assert_array_equal(res[0][1], res[1][1])
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 33, 1001, 20001])
+def test_paired_fixed_step_kernel_bit_identical(S, N):
+    """Fixed-step Tsit5 with two trajectories per thread (direct schedule, TPT 2, FP32, final
+    state only: the paired instructions) gives every trajectory exactly the result, status
+    and counters of the one-per-thread kernel: spans with different step counts (a lane
+    idles while its partner finishes), zero-length spans, a last step shorter than dt, an
+    odd N (a thread with one trajectory), a non-finite parameter and a step cap."""
+    P, U, T = workloads.lorenz_random(N, seed=400 + N, t1=1.0)
+    T[:, 1] = np.random.default_rng(N).uniform(0.0, 0.5, N)
+    T[::13, 1] = 0.0
+    T[1::7, 1] = 0.25  # a whole number of steps
+    if N > 5:
+        P[4, 1] = np.nan
+    d = lambda a: dev(a, torch.float32)
+    first = None
+    for kw in (dict(), dict(maxiters=100)):
+        outs = []
+        for tpt, block in ((1, 128), (2, 128), (2, 64), (2, 256)):
+            o, st, stats = S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5_fixed", dt=2e-3,
+                                             schedule="direct", tpt=tpt, block=block,
+                                             want_stats=True, **kw)
+            outs.append((host(o), st.cpu().numpy(), stats.cpu().numpy()))
+        for cur in outs[1:]:
+            for x, y in zip(cur, outs[0]):
+                np.testing.assert_array_equal(x, y)
+        if kw and N > 100:  # spans past 100 steps of 2e-3 stop at the cap: MAXITERS
+            assert np.all(outs[0][1][T[:, 1] > 0.21] == 1)
+        first = first or outs
+    if N > 5:
+        assert first[0][1][4] == 3  # NONFINITE (without the cap)
+
+
+def test_paired_fixed_step_generic_rhs_and_oracle(S):
+    """The paired fixed-step kernel with the per-lane right-hand side (GBM drift, D = 1) and
+    on Lorenz against the oracle's FP32 mode (the fixed-step bar, 1e-5 relative)."""
+    P, U, T = workloads.gbm_random(3001, seed=78)
+    T[:, 1] = np.random.default_rng(6).uniform(0.1, 1.0, len(T))
+    d = lambda a: dev(a, torch.float32)
+    res = []
+    for tpt in (1, 2):
+        o, st, stats = S["gbm"].solve(d(P), d(U), d(T), alg="tsit5_fixed", dt=1e-2,
+                                      schedule="direct", tpt=tpt, want_stats=True)
+        res.append((host(o), stats.cpu().numpy()))
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+    P, U, T = workloads.lorenz_random(2049, seed=79, t1=1.0)
+    r = lambda a: a.astype(np.float32).astype(np.float64)
+    ref, _, _ = oracle.solve("lorenz", "tsit5_fixed", r(P), r(U), r(T), dt=1e-3,
+                             precision="f32")
+    o, st, _ = S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5_fixed", dt=1e-3,
+                                 schedule="direct", tpt=2)
+    g = host(o)
+    assert np.all(st.cpu().numpy() == 0)
+    e = np.abs(g - ref).max(axis=1) / np.maximum(np.abs(ref).max(axis=1), 1.0)
+    assert e.max() <= 1e-5, e.max()
+
+
 def test_kernel_events_time_the_integrator_alone(S):
     """ens_opts.kernel_start / kernel_stop bracket the integrator kernel: a positive time no
     longer than the whole solve's (which adds the longest-first ordering kernels)."""
