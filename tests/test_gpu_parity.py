@@ -423,7 +423,8 @@ def test_paired_fixed_step_kernel_bit_identical(S, N):
     state only: the paired instructions) gives every trajectory exactly the result, status
     and counters of the one-per-thread kernel: spans with different step counts (a lane
     idles while its partner finishes), zero-length spans, a last step shorter than dt, an
-    odd N (a thread with one trajectory), a non-finite parameter and a step cap."""
+    odd N (a thread with one trajectory), a non-finite parameter, a step cap, and the
+    structure-of-arrays layout."""
     P, U, T = workloads.lorenz_random(N, seed=400 + N, t1=1.0)
     T[:, 1] = np.random.default_rng(N).uniform(0.0, 0.5, N)
     T[::13, 1] = 0.0
@@ -434,10 +435,18 @@ def test_paired_fixed_step_kernel_bit_identical(S, N):
     first = None
     for kw in (dict(), dict(maxiters=100)):
         outs = []
-        for tpt, block in ((1, 128), (2, 128), (2, 64), (2, 256)):
-            o, st, stats = S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5_fixed", dt=2e-3,
-                                             schedule="direct", tpt=tpt, block=block,
-                                             want_stats=True, **kw)
+        for tpt, block, soa in ((1, 128, False), (2, 128, False), (2, 64, False),
+                                (2, 256, False), (2, 128, True)):
+            if soa:  # structure-of-arrays inputs and output
+                o, st, stats = S["lorenz"].solve(d(P.T.copy()), d(U.T.copy()), d(T.T.copy()),
+                                                 alg="tsit5_fixed", dt=2e-3, layout="soa",
+                                                 schedule="direct", tpt=tpt, block=block,
+                                                 want_stats=True, **kw)
+                o = o.t()
+            else:
+                o, st, stats = S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5_fixed", dt=2e-3,
+                                                 schedule="direct", tpt=tpt, block=block,
+                                                 want_stats=True, **kw)
             outs.append((host(o), st.cpu().numpy(), stats.cpu().numpy()))
         for cur in outs[1:]:
             for x, y in zip(cur, outs[0]):
