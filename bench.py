@@ -48,6 +48,8 @@ SM_MAX_MHZ = 2070.0
 #     clock and clamp arithmetic the model leaves out.  175 is counted (the planned model's
 #     figure, within 0.3 % of the measurement);
 #   fixed Tsit5 step: stage combinations 81 + six f evaluations 36 -> 117;
+#   RK4 step (Lorenz): four f evaluations 24 + stage arguments 3 x D + the weighted sum
+#     (2 adds, one FMA by 2, the final FMA per component) 4 x D + h / 2, h / 6 -> 48;
 #   adjoint step (Tsit5, Lorenz): forward with checkpoints 117, replay 117, transposed step
 #     189 (six VJP pairs 6 x 18, stage-adjoint sums 45 + 15, seeds 21) -> 423.
 # Euler-Maruyama steps count ALU lane instructions (INT32 and FP32 share the 128 lanes/SM/clk):
@@ -105,6 +107,8 @@ WORKLOADS = {
                                 t1=10.0, tol=1e-8, steps=5),
     "lorenz_fixed_f32": dict(kind="solve", rhs="lorenz", alg="tsit5_fixed", dtype="f32",
                              N=1 << 20, t1=1.0, dt=1e-3, steps=300),
+    "lorenz_rk4_f32": dict(kind="solve", rhs="lorenz", alg="rk4", dtype="f32", N=1 << 20,
+                           t1=1.0, dt=1e-3, steps=300),
     "robertson_ros23_f64": dict(kind="solve", rhs="robertson", alg="ros23", dtype="f64",
                                 N=1 << 18, t1=1e5, tol=1e-6, dt0=1e-4, steps=20),
     "robertson_rodas4_f64": dict(kind="solve", rhs="robertson", alg="rodas4", dtype="f64",

@@ -54,10 +54,11 @@ LaunchCfg default_launch(const ens_opts* o, int sms) {
 
 }  // namespace
 
-// fixed-step Tsit5 problems the paired direct kernel serves (FP32, final state only,
+// fixed-step Tsit5 / RK4 problems the paired direct kernel serves (FP32, final state only,
 // autonomous models without events)
 bool fixed_pairs(int rhs_id, const ens_opts* o) {
-  return o->alg == ENS_TSIT5_FIXED && o->dtype == ENS_F32 && o->n_save == 0 &&
+  return (o->alg == ENS_TSIT5_FIXED || o->alg == ENS_RK4) && o->dtype == ENS_F32 &&
+         o->n_save == 0 &&
          (rhs_id == ENS_RHS_LORENZ || rhs_id == ENS_RHS_ROBERTSON || rhs_id == ENS_RHS_GBM ||
           rhs_id == ENS_RHS_OREGO);
 }

@@ -127,6 +127,31 @@ __device__ __forceinline__ void tsit5_step2(const float2* u, const float2* p, fl
   }
 }
 
+// One classical RK4 step on a pair (rk4_step, same association; the factor 2 is exact, so
+// its product rounds alike contracted or not).
+template <class RHS>
+__device__ __forceinline__ void rk4_step2(const float2* u, const float2* p, float2 h,
+                                          float2* unew) {
+  constexpr int D = RHS::D;
+  typedef Rhs2<RHS> F;
+  float2 k1[D], k2[D], k3[D], k4[D], U[D];
+  const float2 hh = mul2(bc2(0.5f), h);
+  F::f(u, p, k1);
+#pragma unroll
+  for (int j = 0; j < D; ++j) U[j] = fma2(hh, k1[j], u[j]);
+  F::f(U, p, k2);
+#pragma unroll
+  for (int j = 0; j < D; ++j) U[j] = fma2(hh, k2[j], u[j]);
+  F::f(U, p, k3);
+#pragma unroll
+  for (int j = 0; j < D; ++j) U[j] = fma2(h, k3[j], u[j]);
+  F::f(U, p, k4);
+  const float2 h6 = mul2(h, bc2(float(1.0 / 6.0)));
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    unew[j] = fma2(h6, fma2(bc2(2.f), add2(k2[j], k3[j]), add2(k1[j], k4[j])), u[j]);
+}
+
 // Two adaptive Tsit5 trajectories (FP32, no save times) advanced in lockstep.
 template <class RHS>
 struct AdaptivePair {
@@ -316,16 +341,17 @@ __global__ void k_persistent_pair(const SolveArgs a) {
   persistent_pair_loop<RHS>(a);
 }
 
-// Fixed-step Tsit5 on two trajectories per thread (FP32, final state only, the direct
+// Fixed-step Tsit5 or RK4 on two trajectories per thread (FP32, final state only, the direct
 // schedule): the two lanes take the scalar integrator's steps side by side, the last step of
 // each lane shortened to land on its tf as in Fixed::one_step; once one lane's steps are
 // done it keeps its state (selects) while the other finishes.  Initialisation and output are
 // the scalar integrator's, so results, status and counters equal the one-per-thread kernel's
 // bit for bit.  With equal step counts (one tspan for the whole ensemble) no lane idles.
-template <class RHS>
+template <class RHS, int METH>
 __global__ void k_direct_pair(const SolveArgs a) {
   static_assert(RHS::autonomous, "the paired integrator passes no time to f");
-  typedef Fixed<RHS, float, METH_FIX_TSIT5> Scalar;
+  static_assert(METH == METH_FIX_TSIT5 || METH == METH_FIX_RK4, "Tsit5 or RK4");
+  typedef Fixed<RHS, float, METH> Scalar;
   constexpr int D = RHS::D, P = RHS::P;
   const long long stride = 2LL * gridDim.x * blockDim.x;
   for (long long i0 = 2LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x); i0 < a.N;
@@ -350,22 +376,29 @@ __global__ void k_direct_pair(const SolveArgs a) {
     for (; k < mlo; ++k) {  // both lanes step
       const float2 h = make_float2(k == last0 ? hl0 : hr, k == last1 ? hl1 : hr);
       float2 unew[D], k7[D];
-      tsit5_step2<RHS, false>(u, p, h, fk, unew, nullptr, k7);
+      if constexpr (METH == METH_FIX_TSIT5)
+        tsit5_step2<RHS, false>(u, p, h, fk, unew, nullptr, k7);
+      else
+        rk4_step2<RHS>(u, p, h, unew);
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         u[j] = unew[j];
-        fk[j] = k7[j];
+        if constexpr (METH == METH_FIX_TSIT5) fk[j] = k7[j];
       }
     }
     for (; k < mhi; ++k) {  // one lane steps, the other keeps its final state
       const bool l0 = k < m0, l1 = k < m1;
       const float2 h = make_float2(k == last0 ? hl0 : hr, k == last1 ? hl1 : hr);
       float2 unew[D], k7[D];
-      tsit5_step2<RHS, false>(u, p, h, fk, unew, nullptr, k7);
+      if constexpr (METH == METH_FIX_TSIT5)
+        tsit5_step2<RHS, false>(u, p, h, fk, unew, nullptr, k7);
+      else
+        rk4_step2<RHS>(u, p, h, unew);
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         u[j] = make_float2(l0 ? unew[j].x : u[j].x, l1 ? unew[j].y : u[j].y);
-        fk[j] = make_float2(l0 ? k7[j].x : fk[j].x, l1 ? k7[j].y : fk[j].y);
+        if constexpr (METH == METH_FIX_TSIT5)
+          fk[j] = make_float2(l0 ? k7[j].x : fk[j].x, l1 ? k7[j].y : fk[j].y);
       }
     }
 #pragma unroll

@@ -25,10 +25,12 @@ template <class I>
 struct DirectPairOf {
   static constexpr bool ok = false;
 };
-template <class RHS>
-struct DirectPairOf<Fixed<RHS, float, METH_FIX_TSIT5>> {
-  static constexpr bool ok = RHS::autonomous && !RHS::has_event;
+template <class RHS, int METH>
+struct DirectPairOf<Fixed<RHS, float, METH>> {
+  static constexpr bool ok =
+      (METH == METH_FIX_TSIT5 || METH == METH_FIX_RK4) && RHS::autonomous && !RHS::has_event;
   typedef RHS rhs;
+  static constexpr int meth = METH;
 };
 
 // dynamic shared memory of a launch (the dense saves' staging)
@@ -94,7 +96,8 @@ cudaError_t launch_integ(const SolveArgs& a, const LaunchCfg& cfg, cudaStream_t 
       if (cfg.tpt == 2 && a.n_save == 0) {
         const long long pairs = (a.N + 2LL * cfg.block - 1) / (2LL * cfg.block);
         const int grid = (int)std::min<long long>(std::max<long long>(pairs, 1), 1LL << 30);
-        k_direct_pair<typename DirectPairOf<I>::rhs><<<grid, cfg.block, 0, s>>>(a);
+        typedef DirectPairOf<I> DP;
+        k_direct_pair<typename DP::rhs, DP::meth><<<grid, cfg.block, 0, s>>>(a);
         return cudaGetLastError();
       }
     }
@@ -122,7 +125,8 @@ cudaError_t attrs_integ(const LaunchCfg& cfg, cudaFuncAttributes* attr, int* bps
   if (cfg.schedule == ENS_SCHED_DIRECT) {
     fn = (const void*)k_direct<I>;
     if constexpr (DirectPairOf<I>::ok)
-      if (cfg.tpt == 2) fn = (const void*)k_direct_pair<typename DirectPairOf<I>::rhs>;
+      if (cfg.tpt == 2)
+        fn = (const void*)k_direct_pair<typename DirectPairOf<I>::rhs, DirectPairOf<I>::meth>;
   } else if (cfg.tpt == 1 || I::kMaxTpt == 1) fn = (const void*)k_persistent<I, 1>;
   else if constexpr (I::kMaxTpt > 1) {
     if (cfg.tpt == 2) fn = (const void*)k_persistent<I, 2>;

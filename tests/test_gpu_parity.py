@@ -417,9 +417,10 @@ def test_paired_lockstep_generic_rhs(S):
     np.testing.assert_array_equal(res[0][1], res[1][1])
 
 
+@pytest.mark.parametrize("alg", ["tsit5_fixed", "rk4"])
 @pytest.mark.parametrize("N", [1, 2, 3, 33, 1001, 20001])
-def test_paired_fixed_step_kernel_bit_identical(S, N):
-    """Fixed-step Tsit5 with two trajectories per thread (direct schedule, TPT 2, FP32, final
+def test_paired_fixed_step_kernel_bit_identical(S, N, alg):
+    """Fixed-step Tsit5 and RK4 with two trajectories per thread (direct schedule, TPT 2, FP32, final
     state only: the paired instructions) gives every trajectory exactly the result, status
     and counters of the one-per-thread kernel: spans with different step counts (a lane
     idles while its partner finishes), zero-length spans, a last step shorter than dt, an
@@ -439,12 +440,12 @@ def test_paired_fixed_step_kernel_bit_identical(S, N):
                                 (2, 256, False), (2, 128, True)):
             if soa:  # structure-of-arrays inputs and output
                 o, st, stats = S["lorenz"].solve(d(P.T.copy()), d(U.T.copy()), d(T.T.copy()),
-                                                 alg="tsit5_fixed", dt=2e-3, layout="soa",
+                                                 alg=alg, dt=2e-3, layout="soa",
                                                  schedule="direct", tpt=tpt, block=block,
                                                  want_stats=True, **kw)
                 o = o.t()
             else:
-                o, st, stats = S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5_fixed", dt=2e-3,
+                o, st, stats = S["lorenz"].solve(d(P), d(U), d(T), alg=alg, dt=2e-3,
                                                  schedule="direct", tpt=tpt, block=block,
                                                  want_stats=True, **kw)
             outs.append((host(o), st.cpu().numpy(), stats.cpu().numpy()))
@@ -473,14 +474,14 @@ def test_paired_fixed_step_generic_rhs_and_oracle(S):
     np.testing.assert_array_equal(res[0][1], res[1][1])
     P, U, T = workloads.lorenz_random(2049, seed=79, t1=1.0)
     r = lambda a: a.astype(np.float32).astype(np.float64)
-    ref, _, _ = oracle.solve("lorenz", "tsit5_fixed", r(P), r(U), r(T), dt=1e-3,
-                             precision="f32")
-    o, st, _ = S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5_fixed", dt=1e-3,
-                                 schedule="direct", tpt=2)
-    g = host(o)
-    assert np.all(st.cpu().numpy() == 0)
-    e = np.abs(g - ref).max(axis=1) / np.maximum(np.abs(ref).max(axis=1), 1.0)
-    assert e.max() <= 1e-5, e.max()
+    for alg in ("tsit5_fixed", "rk4"):
+        ref, _, _ = oracle.solve("lorenz", alg, r(P), r(U), r(T), dt=1e-3, precision="f32")
+        o, st, _ = S["lorenz"].solve(d(P), d(U), d(T), alg=alg, dt=1e-3, schedule="direct",
+                                     tpt=2)
+        g = host(o)
+        assert np.all(st.cpu().numpy() == 0)
+        e = np.abs(g - ref).max(axis=1) / np.maximum(np.abs(ref).max(axis=1), 1.0)
+        assert e.max() <= 1e-5, (alg, e.max())
 
 
 def test_kernel_events_time_the_integrator_alone(S):
