@@ -56,7 +56,7 @@ LaunchCfg default_launch(const ens_opts* o, int sms) {
 
 // fixed-step Tsit5 / RK4 problems the paired direct kernel serves (FP32, final state only,
 // autonomous models without events)
-bool fixed_pairs(int rhs_id, const ens_opts* o) {
+static bool fixed_pairs(int rhs_id, const ens_opts* o) {
   return (o->alg == ENS_TSIT5_FIXED || o->alg == ENS_RK4) && o->dtype == ENS_F32 &&
          o->n_save == 0 &&
          (rhs_id == ENS_RHS_LORENZ || rhs_id == ENS_RHS_ROBERTSON || rhs_id == ENS_RHS_GBM ||
