@@ -500,9 +500,38 @@ class SolveRunner:
             n, mean, var = merge_moments(self.parts)
             extra["moments"] = {"n": int(n), "mean": [float(v) for v in mean],
                                 "var": [float(v) for v in var]}
+        eff = self.lane_efficiency(attempts)
+        if eff is not None:
+            extra["lane_efficiency"] = eff
         return attempts * OPS_PER_ATTEMPT[ops_key(self.w)] + save_ops, {
             "attempts_per_launch": attempts, "ops_per_attempt": OPS_PER_ATTEMPT[ops_key(self.w)],
             "trajectories_ok": ok, "autotuned_shape": self.tuned, **extra}
+
+    def lane_efficiency(self, attempts):
+        """Useful lane-attempts over the lane slots the persistent solve issued (its warps'
+        loop iterations x 32 x trajectories per thread): the same solve run once more as a
+        one-item batch plan, which counts the slots, at the launch shape the timed solves
+        used (outside the timed region).  Adaptive final-state solves of the batchable models
+        only."""
+        import torch
+
+        import paper_2304_06835_gb300 as ens
+        w, a = self.w, self.args
+        if (w["alg"] in ("tsit5_fixed", "rk4", "em", "siea") or w.get("saves") or
+                w.get("cap") or w.get("dtmax") or a.schedule == "direct" or
+                w["rhs"] not in ("lorenz", "robertson", "gbm")):
+            return None
+        shape = self.tuned or {"block": a.block, "tpt": a.tpt, "blocks_per_sm": a.bps}
+        item = dict(rhs=w["rhs"], params=self.Pd, u0=self.Ud, tspan=self.Td, alg=w["alg"],
+                    layout=self.layout, schedule="persistent", block=shape["block"],
+                    tpt=shape["tpt"], blocks_per_sm=shape["blocks_per_sm"],
+                    refill_min=a.refill, order=a.order, **self.kw)
+        plan = ens.EnsembleBatch([item], graph=False)
+        plan.run()
+        torch.cuda.synchronize()
+        slots = plan.info()[0]["lane_slots"]
+        plan.close()
+        return round(attempts / slots, 4) if slots else None
 
     def e2e(self, stream):
         """Trajectories/s through ens_solve_host: pinned host inputs copied to the device, the

@@ -151,10 +151,11 @@ typedef struct {
                              and takes at most 512 (more: ENS_ECUDA, too many resources). */
   int tpt;                /* trajectories per thread (1, 2 or 4); 0 = tuned / default.  The
                              Rosenbrock kernels, dense output and the step record run one.
-                             FP32 Tsit5 on the final-state output (adaptive, persistent
-                             schedule; fixed step, direct schedule) runs 2 as one lockstep
-                             pair on the paired FP32 instructions.  Every shape gives each
-                             trajectory the result of 1. */
+                             FP32 on the final-state output, adaptive Tsit5 (persistent
+                             schedule) and fixed-step Tsit5 / RK4 (direct schedule) run 2 as
+                             one lockstep pair on the paired FP32 instructions (the default
+                             for the fixed-step ones).  Every shape gives each trajectory the
+                             result of 1. */
   int refill_min;         /* persistent schedule: a warp refills its idle lanes once at least
                              this many are idle (1..32; 0 = default).  Batching refills trades
                              idle lanes for fewer divergent refill passes. */
