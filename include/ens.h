@@ -160,9 +160,11 @@ typedef struct {
                              this many are idle (1..32; 0 = default).  Batching refills trades
                              idle lanes for fewer divergent refill passes. */
   int order;              /* ENS_ORDER_* (persistent schedule only) */
-  int blocks_per_sm;      /* persistent schedule: resident blocks per SM (0 = as many as fit).
-                             Fewer resident lanes each take more trajectories from the queue,
-                             which shortens the drain at the end of the queue. */
+  int blocks_per_sm;      /* persistent schedule: resident blocks per SM (0 = as many as fit;
+                             -1, -2, -3 = that many quarters of them, as ens_autotune reports;
+                             otherwise <= 64).  Fewer resident lanes each take more
+                             trajectories from the queue, which shortens the drain at the end
+                             of the queue. */
   int dense;              /* TSIT5_ADAPTIVE with save times: 0 = the steps are cut to land on
                              each save time; 1 = the steps run to tf uncut and each save time
                              s in a step [t_n, t_n + h] takes the dense output

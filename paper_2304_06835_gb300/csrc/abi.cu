@@ -349,8 +349,8 @@ int validate_opts(int rhs_id, long long N, const void* params, const void* u0,
     return fail(ENS_EINVAL, "refill_min must be in [0, 32]");
   if (o->order < ENS_ORDER_AUTO || o->order > ENS_ORDER_COST)
     return fail(ENS_EINVAL, "unknown order");
-  if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64)
-    return fail(ENS_EINVAL, "blocks_per_sm must be in [0, 64]");
+  if (o->blocks_per_sm < -3 || o->blocks_per_sm > 64)
+    return fail(ENS_EINVAL, "blocks_per_sm must be in [-3, 64]");
   if (N > 0 && (!params || !u0 || !tspan || !out)) return fail(ENS_EINVAL, "null array");
   return ENS_OK;
 }

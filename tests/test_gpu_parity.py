@@ -484,6 +484,25 @@ def test_paired_fixed_step_generic_rhs_and_oracle(S):
         assert e.max() <= 1e-5, (alg, e.max())
 
 
+def test_fractional_blocks_per_sm_as_the_tuner_reports(S):
+    """blocks_per_sm = -1 .. -3 (that many quarters of the resident blocks, the codes
+    ens_autotune returns) is accepted and changes no result; -4 is refused."""
+    from paper_2304_06835_gb300 import EnsError
+    P, U, T = workloads.lorenz_random(20000, seed=81, t1=2.0)
+    d = lambda a: dev(a, torch.float32)
+    res = []
+    for f in (0, -1, -2, -3):
+        o, st, stats = S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5", abstol=1e-6,
+                                         reltol=1e-6, schedule="persistent", tpt=2,
+                                         blocks_per_sm=f, want_stats=True)
+        res.append((host(o), stats.cpu().numpy()))
+    for r in res[1:]:
+        np.testing.assert_array_equal(r[0], res[0][0])
+        np.testing.assert_array_equal(r[1], res[0][1])
+    with pytest.raises(EnsError):
+        S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5", blocks_per_sm=-4)
+
+
 def test_kernel_events_time_the_integrator_alone(S):
     """ens_opts.kernel_start / kernel_stop bracket the integrator kernel: a positive time no
     longer than the whole solve's (which adds the longest-first ordering kernels)."""
