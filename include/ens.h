@@ -139,7 +139,9 @@ typedef struct {
   double dt;              /* fixed-step size (TSIT5_FIXED, RK4, EM), > 0 */
   double abstol, reltol;  /* adaptive tolerances; abstol >= 1e-30, reltol >= 0 */
   double dt0;             /* adaptive first step; <= 0: Hairer-Norsett-Wanner starting step */
-  long long maxiters;     /* per-trajectory cap on step attempts (>= 1) */
+  long long maxiters;     /* per-trajectory cap on step attempts (>= 1); the fixed-step
+                             methods take at most 2^31 - 2 steps whatever the cap (a longer
+                             span stops there with ENS_TRAJ_MAXITERS) */
   const double* saveat;   /* HOST array of n_save ascending times, copied during the call;
                              NULL/0: only the final state is written (S = 1) */
   int n_save;             /* 0 .. ENS_MAX_SAVE */

@@ -571,6 +571,8 @@ struct DiagNoise : std::false_type {};
 template <class R>
 struct DiagNoise<R, std::void_t<decltype(&R::diag_b)>> : std::true_type {};
 
+constexpr long long kMaxFixedSteps = 0x7ffffffeLL;  // steps of one fixed-step trajectory
+
 template <class RHS, class T, int METH>
 struct Fixed {
   using Real = T;
@@ -590,11 +592,11 @@ struct Fixed {
   T u[D], fk[D], p[P];
   T h_reg, h_last, t0f;
   double t0, tf;
-  long long n, nrun, k, next_ks;
+  int n, nrun, k, next_ks;  // step counts in 32 bits (the 64-bit ones cost ~7 % on GBM EM)
   int si;
   long long idx;
 
-  __device__ __forceinline__ long long ks_of(const SolveArgs& a, int s) const {
+  __device__ __forceinline__ int ks_of(const SolveArgs& a, int s) const {
     const double sv = a.saveat[s];
     if (sv < t0 || sv > tf) return -1;
     long long ks = (sv <= t0) ? 0 : (long long)ceil((sv - t0) / a.dt - 1e-12);
@@ -623,11 +625,15 @@ struct Fixed {
     t0f = t0t;
     t0 = double(t0t);
     tf = double(tft);
-    n = (tf > t0) ? (long long)ceil((tf - t0) / a.dt - 1e-12) : 0;
-    if (n < 0) n = 0;
-    nrun = n < a.maxiters ? n : a.maxiters;
+    long long n64 = (tf > t0) ? (long long)ceil((tf - t0) / a.dt - 1e-12) : 0;
+    if (n64 < 0) n64 = 0;
+    // at most kMaxFixedSteps steps per trajectory: a longer span stops there, MAXITERS
+    long long r64 = n64 < a.maxiters ? n64 : a.maxiters;
+    r64 = r64 < kMaxFixedSteps ? r64 : kMaxFixedSteps;
+    n = int(n64 <= kMaxFixedSteps ? n64 : kMaxFixedSteps + 1);
+    nrun = int(r64);
     h_reg = T(a.dt);
-    h_last = n > 0 ? T(tf - (t0 + double(n - 1) * a.dt)) : T(0);
+    h_last = n64 > 0 ? T(tf - (t0 + double(n64 - 1) * a.dt)) : T(0);
     k = 0;
     if (METH == METH_FIX_TSIT5) RHS::f(u, p, t0t, fk);
     si = 0;
@@ -717,14 +723,14 @@ struct Fixed {
       const unsigned long long stream = (unsigned long long)(a.index_offset + idx);
       T z[kPC * kCalls];
       if (kCalls == 1) {
-        Normals<T>::draw(Philox::call(a.seed, stream, (unsigned long long)(k / kSub)), z);
+        Normals<T>::draw(Philox::call(a.seed, stream, (unsigned long long)(unsigned(k) / unsigned(kSub))), z);
 #pragma unroll
         for (int sub = 0; sub < kSub; ++sub)
           if (k < nrun) one_step(a, z + sub * kNW);
       } else {
 #pragma unroll
         for (int c = 0; c < kCalls; ++c)
-          Normals<T>::draw(Philox::call(a.seed, stream, (unsigned long long)(k * kCalls + c)),
+          Normals<T>::draw(Philox::call(a.seed, stream, (unsigned long long)k * kCalls + c),
                            z + c * kPC);
         one_step(a, z);
       }

@@ -113,17 +113,18 @@ __device__ __forceinline__ void tsit5_step2(const float2* u, const float2* p, fl
     unew[j] = fma2(h, s, u[j]);
   }
   F::f(unew, p, k7);
-  if constexpr (!WANT_ERR) return;
+  if constexpr (WANT_ERR) {
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    float2 s = mul2(bc2(float(Ts5::bt1)), k1[j]);
-    s = fma2(bc2(float(Ts5::bt2)), k2[j], s);
-    s = fma2(bc2(float(Ts5::bt3)), k3[j], s);
-    s = fma2(bc2(float(Ts5::bt4)), k4[j], s);
-    s = fma2(bc2(float(Ts5::bt5)), k5[j], s);
-    s = fma2(bc2(float(Ts5::bt6)), k6[j], s);
-    s = fma2(bc2(float(Ts5::bt7)), k7[j], s);
-    es[j] = s;
+    for (int j = 0; j < D; ++j) {
+      float2 s = mul2(bc2(float(Ts5::bt1)), k1[j]);
+      s = fma2(bc2(float(Ts5::bt2)), k2[j], s);
+      s = fma2(bc2(float(Ts5::bt3)), k3[j], s);
+      s = fma2(bc2(float(Ts5::bt4)), k4[j], s);
+      s = fma2(bc2(float(Ts5::bt5)), k5[j], s);
+      s = fma2(bc2(float(Ts5::bt6)), k6[j], s);
+      s = fma2(bc2(float(Ts5::bt7)), k7[j], s);
+      es[j] = s;
+    }
   }
 }
 
@@ -368,11 +369,11 @@ __global__ void k_direct_pair(const SolveArgs a) {
     }
 #pragma unroll
     for (int j = 0; j < P; ++j) p[j] = make_float2(s0.p[j], s1.p[j]);
-    const long long m0 = s0.nrun, m1 = two ? s1.nrun : 0;
-    const long long last0 = s0.n - 1, last1 = s1.n - 1;
+    const int m0 = s0.nrun, m1 = two ? s1.nrun : 0;
+    const int last0 = s0.n - 1, last1 = s1.n - 1;
     const float hr = s0.h_reg, hl0 = s0.h_last, hl1 = s1.h_last;
-    const long long mlo = m0 < m1 ? m0 : m1, mhi = m0 < m1 ? m1 : m0;
-    long long k = 0;
+    const int mlo = m0 < m1 ? m0 : m1, mhi = m0 < m1 ? m1 : m0;
+    int k = 0;
     for (; k < mlo; ++k) {  // both lanes step
       const float2 h = make_float2(k == last0 ? hl0 : hr, k == last1 ? hl1 : hr);
       float2 unew[D], k7[D];
