@@ -68,8 +68,11 @@ enum { ENS_OK = 0, ENS_EINVAL = 1, ENS_ENOTSUP = 2, ENS_ECUDA = 3, ENS_ENOMEM = 
  *             a constant printed in several equations is one parameter (Appendix, HIRES).
  *   POLLU     D=20 P=25  p=(k1..k25): the printed equations, which are exactly the sum over
  *             25 mass-action reactions ("k7 u9", "2 k18 u16" read as k7 y9, 2 k18 y16)
- *             (Appendix, POLLU).  HIRES and POLLU take ROS23 only: the 8x8 / 20x20 LU runs
- *             as loops over thread-local memory, one trajectory per thread. */
+ *             (Appendix, POLLU).  HIRES and POLLU take the Rosenbrock methods (ROS23,
+ *             RODAS4, RODAS5P), one trajectory per thread; their W is factored by a sparse
+ *             LU on the fixed Jacobian pattern (a minimum-degree order and its fill decided
+ *             at compile time; a column whose partial pivoting would exchange rows sends
+ *             the step to a dense LU with row exchanges). */
 enum { ENS_RHS_LORENZ = 1, ENS_RHS_ROBERTSON = 2, ENS_RHS_GBM = 3, ENS_RHS_CRN = 4,
        ENS_RHS_BALL = 5, ENS_RHS_OREGO = 6, ENS_RHS_HIRES = 7, ENS_RHS_POLLU = 8 };
 
