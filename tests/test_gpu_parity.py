@@ -484,6 +484,24 @@ def test_paired_fixed_step_generic_rhs_and_oracle(S):
         assert e.max() <= 1e-5, (alg, e.max())
 
 
+def test_fixed_step_span_beyond_32_bit_step_counts(S):
+    """A fixed-step span of 10^10 steps (past the 32-bit step counters) with a step cap of 50:
+    the trajectory stops after 50 steps with MAXITERS, in the oracle's state (FP64 1e-12;
+    FP32 paired kernel bit-identical to one per thread)."""
+    P, U, T = workloads.lorenz_random(65, seed=83, t1=1.0)
+    T[:, 1] = 1e7
+    ref, rst, _ = oracle.solve("lorenz", "tsit5_fixed", P, U, T, dt=1e-3, maxiters=50)
+    o, st, stats = S["lorenz"].solve(dev(P), dev(U), dev(T), alg="tsit5_fixed", dt=1e-3,
+                                     maxiters=50, want_stats=True)
+    assert np.all(st.cpu().numpy() == 1) and np.all(rst == 1)
+    assert np.all(stats.cpu().numpy()[0] == 50)
+    assert normwise(host(o), ref).max() <= 1e-12
+    d = lambda a: dev(a, torch.float32)
+    outs = [host(S["lorenz"].solve(d(P), d(U), d(T), alg="tsit5_fixed", dt=1e-3, maxiters=50,
+                                   schedule="direct", tpt=t)[0]) for t in (1, 2)]
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 def test_fractional_blocks_per_sm_as_the_tuner_reports(S):
     """blocks_per_sm = -1 .. -3 (that many quarters of the resident blocks, the codes
     ens_autotune returns) is accepted and changes no result; -4 is refused."""
