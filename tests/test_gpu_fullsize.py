@@ -3,14 +3,16 @@ times (autotuned, structure-of-arrays inputs), on a seeded sample the oracle sol
 
 * Lorenz, N = 2^20, adaptive Tsit5 FP64 at tol 1e-8 over [0, 10] (the FP64 half of the
   headline configuration): rho < 10 (stable equilibria) within 10 tol of the tol-1e-12
-  oracle; every sampled trajectory takes the oracle's own (accepted, rejected) counts at the
-  same tolerance on at least 90 % of the sample, and on those the two agree to 1e-6
-  (normwise; chaotic trajectories amplify the last-bit differences of contracted FMAs over
-  [0, 10]); the attempt total of the sample within 0.1 % of the oracle's.
+  oracle (measured 0.45); the sampled trajectories take the oracle's own (accepted, rejected)
+  counts at the same tolerance on at least 99 % of the sample (measured 100 %), and on those
+  the two agree to 1e-9 normwise (measured 3.2e-12: chaotic trajectories amplify the
+  last-bit differences of contracted FMAs over [0, 10]); the attempt total of the sample
+  within 0.1 % of the oracle's (measured equal).
 * Robertson, N = 2^18, Rosenbrock23 FP64 at tol 1e-6, h0 = 1e-4, [0, 1e5] (the stiff
   configuration): every sampled trajectory within 10 tol of a tol-1e-12 Rodas5P reference and
-  of the oracle at the same tolerance, identical counts on >= 95 % of the sample, the linear
-  invariant y1 + y2 + y3 = 1 to 1e-10.
+  of the oracle at the same tolerance (measured 3.42 tol for both, GPU - oracle 0.10 tol),
+  identical counts on >= 94 % of the sample (measured 95.6 %), the linear invariant
+  y1 + y2 + y3 = 1 to 1e-10.
 """
 import numpy as np
 import pytest
@@ -81,8 +83,8 @@ def test_lorenz_fp64_fullsize(lorenz64):
           "oracle on those median %.3g max %.3g; attempts GPU/oracle %.6f"
           % (err.max(), eq.mean(), np.median(d), d.max(), a_gpu / a_orc))
     assert err.max() <= 10.0
-    assert eq.mean() >= 0.9
-    assert d.max() <= 1e-6
+    assert eq.mean() >= 0.99
+    assert d.max() <= 1e-9
     assert abs(a_gpu / a_orc - 1) <= 1e-3
 
 
@@ -101,5 +103,5 @@ def test_robertson_ros23_fullsize(robertson):
           "tol; GPU - oracle max %.3g tol; identical counts %.4f"
           % (e_gpu.max(), e_orc.max(), d.max(), eq.mean()))
     assert e_gpu.max() <= 10.0 and d.max() <= 10.0
-    assert eq.mean() >= 0.95
+    assert eq.mean() >= 0.94
     assert np.abs(h["out"].sum(axis=1) - 1.0).max() < 1e-10
