@@ -253,6 +253,8 @@ struct ens_handle {
   size_t stage_bytes;
   cudaStream_t copy_stream;
   cudaEvent_t ev_in[8], ev_done[8];
+  cudaStream_t solve_stream;   // the second chunk's solve, beside the caller's stream
+  unsigned int* hist2;         // the second chunk's ordering histogram
   // discrete adjoint: one segment of stage inputs, and checkpoints when the caller gives none
   void* adj_seg;
   size_t adj_seg_bytes;
@@ -543,6 +545,8 @@ int ens_create(ens_handle** out, int rhs_id, int D, int P) {
   h->stage = nullptr;
   h->stage_bytes = 0;
   h->copy_stream = nullptr;
+  h->solve_stream = nullptr;
+  h->hist2 = nullptr;
   h->order = nullptr;
   h->bucket = nullptr;
   h->hist = nullptr;
@@ -581,18 +585,29 @@ int ens_destroy(ens_handle* h) {
     }
     cudaStreamDestroy(h->copy_stream);
   }
+  if (h->solve_stream) cudaStreamDestroy(h->solve_stream);
+  if (h->hist2) cudaFree(h->hist2);
   delete h;
   return ENS_OK;
 }
 
-// the solve of N validated trajectories with a resolved launch shape (stream-ordered on s)
+// the solve of N validated trajectories with a resolved launch shape (stream-ordered on s);
+// part > 0 gives a solve that may run beside part 0 its own queue counter, histogram and
+// ordering range (order + first, the handle's arrays already hold first + N entries)
 int solve_with_cfg(ens_handle* h, long long N, const void* params, const void* u0,
                    const void* tspan, const ens_opts* o, void* out, signed char* status,
-                   int* stats, cudaStream_t s, const LaunchCfg& cfg) {
+                   int* stats, cudaStream_t s, const LaunchCfg& cfg, int part = 0,
+                   long long first = 0) {
   SolveArgs a;
-  fill_args(&a, N, params, u0, tspan, o, out, status, stats, h->queue);
-  SolveScratch sc{h->queue, nullptr, nullptr, h->hist};
-  if (uses_cost_order(o, cfg) && N <= 0x7fffffffLL) {
+  unsigned long long* queue = h->queue + 4 * part;  // 32 bytes apart in the 256-byte block
+  fill_args(&a, N, params, u0, tspan, o, out, status, stats, queue);
+  SolveScratch sc{queue, nullptr, nullptr, part ? h->hist2 : h->hist};
+  if (part > 0) {
+    if (uses_cost_order(o, cfg) && first + N <= h->order_cap) {
+      sc.order = h->order + first;
+      sc.bucket = h->bucket + first;
+    }
+  } else if (uses_cost_order(o, cfg) && N <= 0x7fffffffLL) {
     if (N > h->order_cap) {
       cudaFree(h->order);
       cudaFree(h->bucket);
@@ -715,8 +730,29 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
   // included) are those of one solve over all N.
   const LaunchCfg cfg = resolve_cfg(h, N, o);
   // measured (Lorenz, 2^20, end to end): 1 chunk 722.6, 2 chunks 730.5, 4 chunks 602.9 M
-  // trajectories/s -- each chunk's solve drains its own tail, which more chunks repeat
+  // trajectories/s -- each chunk's solve drains its own tail, which more chunks repeat.  The
+  // second chunk's solve runs on a stream of its own, so its blocks take the SMs the first
+  // chunk's drain frees (own queue counter, histogram and ordering range).
   const int C = N >= (1LL << 20) ? 2 : 1;
+  if (C > 1) {
+    cudaError_t e = cudaSuccess;
+    if (!h->solve_stream) e = cudaStreamCreateWithFlags(&h->solve_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->hist2)
+      e = cudaMalloc(&h->hist2, sizeof(unsigned int) * kCostBuckets);
+    if (e == cudaSuccess && uses_cost_order(o, cfg) && N > h->order_cap &&
+        N <= 0x7fffffffLL) {  // the chunks' ordering ranges side by side
+      cudaFree(h->order);
+      cudaFree(h->bucket);
+      h->order = nullptr;
+      h->bucket = nullptr;
+      h->order_cap = 0;
+      cudaError_t e1 = cudaMalloc(&h->order, sizeof(int) * N);
+      cudaError_t e2 = cudaMalloc(&h->bucket, sizeof(unsigned short) * N);
+      if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ENS_ENOMEM, "order scratch");
+      h->order_cap = N;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "second solve stream");
+  }
   const bool soa = o->layout == ENS_LAYOUT_SOA;
   auto cp = [&](void* dst_, size_t dpitch, const void* src_, size_t spitch, size_t width,
                 size_t height, cudaMemcpyKind kind) {
@@ -744,18 +780,19 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
   }
   if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
   i0 = 0;
-  for (int c = 0; c < C; ++c) {  // solves on s; each chunk's outputs go back on cs
+  for (int c = 0; c < C; ++c) {  // solves on s and solve_stream; outputs go back on cs
     const long long i1 = N * (c + 1) / C, n = i1 - i0;
     ens_opts oc = *o;
     oc.index_offset = o->index_offset + i0;
     oc.kernel_start = oc.kernel_stop = nullptr;  // one event pair cannot time several chunks
-    e = cudaStreamWaitEvent(s, h->ev_in[c], 0);
+    const cudaStream_t ss = c == 0 ? s : h->solve_stream;
+    e = cudaStreamWaitEvent(ss, h->ev_in[c], 0);
     if (e != cudaSuccess) return cuda_fail(e, "chunk order");
     rc = solve_with_cfg(h, n, dp + es * i0 * P, du + es * i0 * D, dt + es * i0 * 2, &oc,
                         dout + es * i0 * S * D, status ? (signed char*)dst + i0 : nullptr,
-                        stats ? (int*)dstats + 3 * i0 : nullptr, s, cfg);
+                        stats ? (int*)dstats + 3 * i0 : nullptr, ss, cfg, c, i0);
     if (rc) return rc;
-    e = cudaEventRecord(h->ev_done[c], s);
+    e = cudaEventRecord(h->ev_done[c], ss);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->ev_done[c], 0);
     const size_t rowo = soa ? es * n : es * n * S * D;
     if (e == cudaSuccess)
@@ -770,7 +807,9 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     i0 = i1;
   }
-  e = cudaStreamSynchronize(cs);
+  // later work on the caller's stream follows the second chunk's solve too
+  if (C > 1) e = cudaStreamWaitEvent(s, h->ev_done[C - 1], 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
   return ENS_OK;
