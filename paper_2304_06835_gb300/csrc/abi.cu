@@ -785,12 +785,12 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
     ens_opts oc = *o;
     oc.index_offset = o->index_offset + i0;
     oc.kernel_start = oc.kernel_stop = nullptr;  // one event pair cannot time several chunks
-    const cudaStream_t ss = c == 0 ? s : h->solve_stream;
+    const cudaStream_t ss = c % 2 == 0 ? s : h->solve_stream;  // alternate: neighbours overlap
     e = cudaStreamWaitEvent(ss, h->ev_in[c], 0);
     if (e != cudaSuccess) return cuda_fail(e, "chunk order");
     rc = solve_with_cfg(h, n, dp + es * i0 * P, du + es * i0 * D, dt + es * i0 * 2, &oc,
                         dout + es * i0 * S * D, status ? (signed char*)dst + i0 : nullptr,
-                        stats ? (int*)dstats + 3 * i0 : nullptr, ss, cfg, c, i0);
+                        stats ? (int*)dstats + 3 * i0 : nullptr, ss, cfg, c % 2, i0);
     if (rc) return rc;
     e = cudaEventRecord(h->ev_done[c], ss);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->ev_done[c], 0);
@@ -807,8 +807,8 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     i0 = i1;
   }
-  // later work on the caller's stream follows the second chunk's solve too
-  if (C > 1) e = cudaStreamWaitEvent(s, h->ev_done[C - 1], 0);
+  // later work on the caller's stream follows the other stream's solves too
+  if (C > 1) e = cudaStreamWaitEvent(s, h->ev_done[C % 2 == 0 ? C - 1 : C - 2], 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
