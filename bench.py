@@ -967,7 +967,7 @@ class SurrogateRunner:
         N = w["N"]
         fwd_ms = self._time(lambda: self.net.forward(self.xi))
         flops = N * w["members"] * MLP_FLOPS_PER_SAMPLE
-        # held-out 1 %: judged by the plain solver (FP64, tol 1e-10)
+        # held-out 1 %: checked against the plain solver (FP64, tol 1e-10)
         idx = torch.tensor(np.random.default_rng(0).choice(N, N // 100, replace=False),
                            device=self.dev)
         ref, _ = lorenz_u1(self.solver, self.xi[idx])

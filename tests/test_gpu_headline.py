@@ -8,7 +8,7 @@ checked against the CPU oracle on the same float-rounded inputs:
 
 * rho < 10 (the solutions settle on a stable equilibrium, so the local tolerance bounds the
   global error): every component within 10 (abstol + reltol |u_ref|) of the FP64 oracle at
-  tolerance 1e-12 (the north_star's adaptive criterion);
+  tolerance 1e-12 (the adaptive parity criterion);
 * rho >= 10 (chaotic or long transients over [0,10]: a rounding-level difference of one step
   size grows like e^(0.9 t), so no tolerance-based bound holds): algorithmic parity against
   the oracle's FP32 mode at the same tolerance.  The kernel forms the controller's powers by
