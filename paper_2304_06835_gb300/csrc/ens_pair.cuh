@@ -167,6 +167,12 @@ struct AdaptivePair {
   int attempts[2], rejected[2], fev0[2], st[2];
   long long idx[2];
 
+  // k may be a run-time lane (the refill pass serves lane 0 of some threads and lane 1 of
+  // others at once): every write is then a select, never an indexed register array
+  __device__ __forceinline__ static void set2(int (&v)[2], int k, int x) {
+    v[0] = k ? v[0] : x;
+    v[1] = k ? x : v[1];
+  }
   __device__ __forceinline__ void init(int k, long long i, const SolveArgs& a) {
     Scalar s;
     s.template init<false>(i, a);
@@ -183,11 +189,12 @@ struct AdaptivePair {
     set_lane(thr, k, s.stop_thr);
     set_lane(h, k, s.h);
     set_lane(lq, k, s.lq);
-    attempts[k] = s.attempts;
-    rejected[k] = s.rejected;
-    fev0[k] = s.fev0;
-    st[k] = s.st;
-    idx[k] = s.idx;
+    set2(attempts, k, s.attempts);
+    set2(rejected, k, s.rejected);
+    set2(fev0, k, s.fev0);
+    set2(st, k, s.st);
+    idx[0] = k ? idx[0] : s.idx;
+    idx[1] = k ? s.idx : idx[1];
   }
 
   __device__ __forceinline__ void finish(int k, const SolveArgs& a) {
@@ -319,19 +326,25 @@ __device__ __forceinline__ void persistent_pair_loop(const SolveArgs& a) {
       if (busy == 0u) break;
       continue;
     }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const unsigned idle = __ballot_sync(0xffffffffu, !act[q]);
-      if (__popc(idle) >= a.refill_min) {
-        bool got = true;
-        if (!act[q]) {
-          const long long i = queue_next(a.queue);
-          act[q] = i < a.N;
-          got = act[q];
-          if (act[q]) s.init(q, a.order ? (long long)__ldg(a.order + i) : i, a);
+    // one refill pass over both lanes: once the warp's 64 slots hold refill_min idle ones,
+    // every thread with an idle slot fills one of them (lane 0 first), so the warp runs the
+    // initialisation once for both lanes' idle slots; a thread with both idle fills the
+    // other at a later pass
+    const unsigned idle0 = __ballot_sync(0xffffffffu, !act[0]);
+    const unsigned idle1 = __ballot_sync(0xffffffffu, !act[1]);
+    if (__popc(idle0) + __popc(idle1) >= a.refill_min) {
+      bool got = true;
+      if (!act[0] || !act[1]) {
+        const int q = act[0] ? 1 : 0;
+        const long long i = queue_next(a.queue);
+        got = i < a.N;
+        if (got) {
+          s.init(q, a.order ? (long long)__ldg(a.order + i) : i, a);
+          act[0] = act[0] || q == 0;
+          act[1] = act[1] || q == 1;
         }
-        drained = drained || __any_sync(0xffffffffu, !got);
       }
+      drained = drained || __any_sync(0xffffffffu, !got);
     }
   }
   count_slots(a.slots, (unsigned long long)iters * 2);
