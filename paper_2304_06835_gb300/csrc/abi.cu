@@ -102,7 +102,7 @@ __global__ void k_cost_scatter(long long N, long long chunk, const unsigned shor
 
 cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a,
                               unsigned short* bucket, unsigned int* hist, int* order,
-                              cudaStream_t stream) {
+                              void* h0, cudaStream_t stream) {
   DispatchFn f = table(rhs_id, dtype);
   if (!f) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kCostBuckets, stream);
@@ -110,6 +110,7 @@ cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a
   CostScratch cs;
   cs.bucket = bucket;
   cs.hist = hist;
+  cs.h0 = h0;
   cs.blocks = (int)std::min<long long>(kCostBlocks, std::max<long long>(1, (a.N + 1023) / 1024));
   cs.chunk = (a.N + cs.blocks - 1) / cs.blocks;
   LaunchCfg cfg{};
@@ -246,6 +247,7 @@ struct ens_handle {
   // longest-expected-first ordering scratch, grown on demand
   int* order;
   unsigned short* bucket;
+  void* h0;  // the starting steps kept by the ordering pre-pass (8 bytes a trajectory)
   unsigned int* hist;
   long long order_cap;
   // staging for ens_solve_host, and its copy stream and chunk events
@@ -484,12 +486,17 @@ cudaError_t prepare_solve(int rhs_id, const ens_opts* o, SolveArgs* a, const Lau
                           const SolveScratch& sc, cudaStream_t s) {
   a->queue = sc.queue;
   a->order = nullptr;
+  a->h0 = nullptr;
   if (cfg.schedule == ENS_SCHED_PERSISTENT) {
     if (uses_cost_order(o, cfg) && a->N <= 0x7fffffffLL && sc.order) {
+      // the pre-pass forms each trajectory's starting step for its key; with sc.h0 it keeps
+      // them, and the solve's initialisation reads them instead of forming them again
+      const bool keep_h0 = sc.h0 && !is_fixed(o->alg) && !(o->dt0 > 0);
       cudaError_t e = launch_cost_order(rhs_id, o->alg, o->dtype, *a, sc.bucket, sc.hist,
-                                        sc.order, s);
+                                        sc.order, keep_h0 ? sc.h0 : nullptr, s);
       if (e != cudaSuccess) return e;
       a->order = sc.order;
+      a->h0 = keep_h0 ? sc.h0 : nullptr;
     }
     cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
@@ -549,6 +556,7 @@ int ens_create(ens_handle** out, int rhs_id, int D, int P) {
   h->hist2 = nullptr;
   h->order = nullptr;
   h->bucket = nullptr;
+  h->h0 = nullptr;
   h->hist = nullptr;
   h->order_cap = 0;
   h->adj_seg = nullptr;
@@ -575,6 +583,7 @@ int ens_destroy(ens_handle* h) {
   cudaFree(h->hist);
   if (h->order) cudaFree(h->order);
   if (h->bucket) cudaFree(h->bucket);
+  if (h->h0) cudaFree(h->h0);
   if (h->stage) cudaFree(h->stage);
   if (h->adj_seg) cudaFree(h->adj_seg);
   if (h->adj_ckpt) cudaFree(h->adj_ckpt);
@@ -588,6 +597,26 @@ int ens_destroy(ens_handle* h) {
   if (h->solve_stream) cudaStreamDestroy(h->solve_stream);
   if (h->hist2) cudaFree(h->hist2);
   delete h;
+  return ENS_OK;
+}
+
+// The longest-first order's scratch for N trajectories: the order, the buckets and the
+// starting-step cache (8 bytes a trajectory, which serves either solve type).
+int ensure_order_scratch(ens_handle* h, long long N) {
+  if (N <= h->order_cap) return ENS_OK;
+  cudaFree(h->order);
+  cudaFree(h->bucket);
+  cudaFree(h->h0);
+  h->order = nullptr;
+  h->bucket = nullptr;
+  h->h0 = nullptr;
+  h->order_cap = 0;
+  cudaError_t e1 = cudaMalloc(&h->order, sizeof(int) * N);
+  cudaError_t e2 = cudaMalloc(&h->bucket, sizeof(unsigned short) * N);
+  cudaError_t e3 = cudaMalloc(&h->h0, sizeof(double) * N);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    return fail(ENS_ENOMEM, "order scratch");
+  h->order_cap = N;
   return ENS_OK;
 }
 
@@ -606,21 +635,14 @@ int solve_with_cfg(ens_handle* h, long long N, const void* params, const void* u
     if (uses_cost_order(o, cfg) && first + N <= h->order_cap) {
       sc.order = h->order + first;
       sc.bucket = h->bucket + first;
+      sc.h0 = (char*)h->h0 + elem_size(o->dtype) * first;
     }
   } else if (uses_cost_order(o, cfg) && N <= 0x7fffffffLL) {
-    if (N > h->order_cap) {
-      cudaFree(h->order);
-      cudaFree(h->bucket);
-      h->order = nullptr;
-      h->bucket = nullptr;
-      h->order_cap = 0;
-      cudaError_t e1 = cudaMalloc(&h->order, sizeof(int) * N);
-      cudaError_t e2 = cudaMalloc(&h->bucket, sizeof(unsigned short) * N);
-      if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ENS_ENOMEM, "order scratch");
-      h->order_cap = N;
-    }
+    const int rc = ensure_order_scratch(h, N);
+    if (rc) return rc;
     sc.order = h->order;
     sc.bucket = h->bucket;
+    sc.h0 = h->h0;
   }
   bool sup = false;
   cudaError_t e = enqueue_solve(h->rhs_id, o, a, cfg, sc, s, &sup);
@@ -647,20 +669,14 @@ int ens_autotune(ens_handle* h, long long N, const void* params, const void* u0,
   if (!block || !tpt || !blocks_per_sm || !best_ms) return fail(ENS_EINVAL, "null result pointer");
   if (N == 0) return fail(ENS_EINVAL, "nothing to tune (N = 0)");
   std::lock_guard<std::mutex> lock(h->mu);
-  if (N <= 0x7fffffffLL && N > h->order_cap) {
-    cudaFree(h->order);
-    cudaFree(h->bucket);
-    h->order = nullptr;
-    h->bucket = nullptr;
-    h->order_cap = 0;
-    cudaError_t e1 = cudaMalloc(&h->order, sizeof(int) * N);
-    cudaError_t e2 = cudaMalloc(&h->bucket, sizeof(unsigned short) * N);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ENS_ENOMEM, "order scratch");
-    h->order_cap = N;
+  if (N <= 0x7fffffffLL) {
+    rc = ensure_order_scratch(h, N);
+    if (rc) return rc;
   }
   SolveArgs a;
   fill_args(&a, N, params, u0, tspan, o, out, status, stats, h->queue);
-  SolveScratch sc{h->queue, N <= 0x7fffffffLL ? h->order : nullptr, h->bucket, h->hist};
+  SolveScratch sc{h->queue, N <= 0x7fffffffLL ? h->order : nullptr, h->bucket, h->hist,
+                  N <= 0x7fffffffLL ? h->h0 : nullptr};
   LaunchCfg best;
   rc = tune_problem(h->rhs_id, o, a, sc, h->num_sms, (cudaStream_t)stream, &best, best_ms);
   if (rc) return rc;
@@ -739,17 +755,10 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
     if (!h->solve_stream) e = cudaStreamCreateWithFlags(&h->solve_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !h->hist2)
       e = cudaMalloc(&h->hist2, sizeof(unsigned int) * kCostBuckets);
-    if (e == cudaSuccess && uses_cost_order(o, cfg) && N > h->order_cap &&
+    if (e == cudaSuccess && uses_cost_order(o, cfg) &&
         N <= 0x7fffffffLL) {  // the chunks' ordering ranges side by side
-      cudaFree(h->order);
-      cudaFree(h->bucket);
-      h->order = nullptr;
-      h->bucket = nullptr;
-      h->order_cap = 0;
-      cudaError_t e1 = cudaMalloc(&h->order, sizeof(int) * N);
-      cudaError_t e2 = cudaMalloc(&h->bucket, sizeof(unsigned short) * N);
-      if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ENS_ENOMEM, "order scratch");
-      h->order_cap = N;
+      rc = ensure_order_scratch(h, N);
+      if (rc) return rc;
     }
     if (e != cudaSuccess) return cuda_fail(e, "second solve stream");
   }

@@ -33,6 +33,8 @@ struct SolveArgs {
   long long index_offset;
   unsigned long long* queue;  // persistent-schedule counter (device), zeroed before launch
   const int* order;           // persistent schedule: queue slot -> trajectory index (or null)
+  const void* h0;             // with the order: each trajectory's starting step (T[N], by
+                              // trajectory index), formed by the ordering pre-pass; or null
   unsigned long long* slots;  // persistent schedule: adds the lane slots its warps issue (loop
                               // iterations x 32 x trajectories per thread), or null
   double saveat[ENS_MAX_SAVE];
@@ -66,6 +68,8 @@ int adjoint_stages(int alg);  // stages whose inputs the reverse pass stores (0:
 
 struct CostScratch {
   float* keys = nullptr;   // [N]: set to write the raw cost keys instead of the buckets
+  void* h0 = nullptr;      // [N] of the solve's type: the starting steps the keys are formed
+                           // from (adaptive methods without a given dt0), or null
   unsigned short* bucket;  // [N]
   unsigned int* hist;      // [kCostBuckets] bucket totals, then cursors
   int blocks;              // G <= kCostBlocks
@@ -92,7 +96,7 @@ constexpr int kCostBuckets = 1024;
 constexpr int kCostBlocks = 256;
 cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a,
                               unsigned short* bucket, unsigned int* hist, int* order,
-                              cudaStream_t stream);
+                              void* h0, cudaStream_t stream);
 // The cost keys themselves: keys[i] = the expected steps of trajectory i (the key the
 // longest-first order sorts by).
 cudaError_t launch_cost_keys(int rhs_id, int alg, int dtype, const SolveArgs& a, float* keys,
@@ -105,6 +109,8 @@ struct SolveScratch {
   int* order;               // null: index order
   unsigned short* bucket;
   unsigned int* hist;
+  void* h0 = nullptr;       // [N] of the solve's type, or null: the ordering pre-pass keeps the
+                            // starting steps here for the solve's initialisation
 };
 
 // Shared pieces of the solve entry points (abi.cu).

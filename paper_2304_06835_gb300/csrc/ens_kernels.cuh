@@ -290,8 +290,8 @@ struct Adaptive {
     fev0 = 1;
     if (Tol<T>::dt0(a) > T(0)) {
       h = Tol<T>::dt0(a);
-    } else {
-      h = initial_step(a, t0);
+    } else {  // the ordering pre-pass may have formed it already (the same arithmetic)
+      h = a.h0 ? ldg<T>(a.h0, i) : initial_step(a, t0);
       fev0 = 2;
     }
     lq = kLog2QoldInit;
@@ -550,12 +550,14 @@ struct Adaptive {
 
   // expected work of trajectory i: (tf - t0) / (starting step), the number of steps a solve
   // that kept the Hairer-Norsett-Wanner starting step would take
-  static __device__ __forceinline__ float cost_key(const SolveArgs& a, long long i) {
+  // (h0c: when not null, the starting step is kept there for the solve's initialisation)
+  static __device__ __forceinline__ float cost_key(const SolveArgs& a, long long i, void* h0c) {
     Adaptive s;
     T t0;
     load_problem<RHS, T>(a, i, s.p, s.u, t0, s.tf);
     RHS::f(s.u, s.p, t0, s.fk);
     const T h0 = s.initial_step(a, t0);
+    if (h0c) static_cast<T*>(h0c)[i] = h0;
     return float(s.tf - t0) / float(h0);
   }
 };
@@ -758,7 +760,7 @@ struct Fixed {
   }
 
   // expected work: the number of fixed steps
-  static __device__ __forceinline__ float cost_key(const SolveArgs& a, long long i) {
+  static __device__ __forceinline__ float cost_key(const SolveArgs& a, long long i, void*) {
     const double t0 = double(ldg<T>(a.tspan, in_idx(a.layout, i, 0, a.N, 2)));
     const double tf = double(ldg<T>(a.tspan, in_idx(a.layout, i, 1, a.N, 2)));
     return float((tf - t0) / a.dt);
@@ -807,14 +809,14 @@ __device__ __forceinline__ int cost_bucket(float key) {
 
 template <class I>
 __global__ void k_cost_keys(const SolveArgs a, long long chunk, unsigned short* bucket,
-                            unsigned int* tot) {
+                            unsigned int* tot, void* h0c) {
   __shared__ unsigned int sh[kCostBuckets];
   for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) sh[b] = 0u;
   __syncthreads();
   const long long lo = (long long)blockIdx.x * chunk;
   const long long hi = lo + chunk < a.N ? lo + chunk : a.N;
   for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const int b = cost_bucket(I::cost_key(a, i));
+    const int b = cost_bucket(I::cost_key(a, i, h0c));
     bucket[i] = (unsigned short)b;
     atomicAdd(&sh[b], 1u);
   }
@@ -828,7 +830,7 @@ template <class I>
 __global__ void k_cost_values(const SolveArgs a, float* keys) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.N;
        i += (long long)gridDim.x * blockDim.x)
-    keys[i] = I::cost_key(a, i);
+    keys[i] = I::cost_key(a, i, nullptr);
 }
 
 __global__ void k_cost_scan(unsigned int* tot);

@@ -89,18 +89,28 @@ def test_ragged_sizes_and_layouts_and_schedules(S, N):
 
 
 @pytest.mark.parametrize("N", [1, 37, 5000])
-def test_adaptive_schedules_and_orders_agree(S, N):
-    """Per-trajectory arithmetic does not depend on schedule, order, TPT or refill batching."""
-    P, U, T = workloads.lorenz_random(N, seed=100 + N, t1=2.0)
-    T[:, 1] = np.random.default_rng(N).uniform(0.1, 3.0, N)  # uneven lengths
-    s = S["lorenz"]
+@pytest.mark.parametrize("model,alg,dtype", [("lorenz", "tsit5", torch.float32),
+                                             ("lorenz", "tsit5", torch.float64),
+                                             ("robertson", "ros23", torch.float64)])
+def test_adaptive_schedules_and_orders_agree(S, N, model, alg, dtype):
+    """Per-trajectory arithmetic does not depend on schedule, order, TPT or refill batching
+    (the longest-first order's pre-pass keeps the starting steps it forms and the solve reads
+    them; the index order forms them in the solve)."""
+    if model == "lorenz":
+        P, U, T = workloads.lorenz_random(N, seed=100 + N, t1=2.0)
+        T[:, 1] = np.random.default_rng(N).uniform(0.1, 3.0, N)  # uneven lengths
+    else:
+        P, U, T = workloads.robertson_random(N, seed=100 + N)
+        T[:, 1] = np.random.default_rng(N).uniform(1.0, 100.0, N)
+    if N > 5:
+        P[3, 0] = np.nan  # a non-finite starting step in both forms
+    s = S[model]
     ref = None
     for kw in (dict(schedule="direct"), dict(schedule="persistent", order="index"),
                dict(schedule="persistent", order="cost"), dict(schedule="persistent", tpt=2),
                dict(schedule="persistent", refill_min=1), dict(schedule="persistent", refill_min=32)):
-        o, st, stats = s.solve(dev(P, torch.float32), dev(U, torch.float32),
-                               dev(T, torch.float32), alg="tsit5", abstol=1e-6, reltol=1e-6,
-                               want_stats=True, **kw)
+        o, st, stats = s.solve(dev(P, dtype), dev(U, dtype), dev(T, dtype), alg=alg,
+                               abstol=1e-6, reltol=1e-6, want_stats=True, **kw)
         cur = (host(o), st.cpu().numpy(), stats.cpu().numpy())
         if ref is None:
             ref = cur
