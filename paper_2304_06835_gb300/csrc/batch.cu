@@ -360,14 +360,16 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
                           "Tsit5, Robertson FP32 Rosenbrock23 and GBM FP32 Euler-Maruyama, "
                           "without save times or step records");
   }
-  // one scratch block: per item a 256-byte queue slot, the bucket cursors, order and keys
+  // one scratch block: per item a 256-byte queue slot, the bucket cursors, order, keys and
+  // the starting steps the ordering pre-pass keeps (8 bytes a trajectory)
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   std::vector<size_t> off(n_items);
   size_t total = 0;
   for (int i = 0; i < n_items; ++i) {
     off[i] = total;
     const long long N = items[i].N;
-    total += 256 + up(4 * (size_t)kCostBuckets) + up(4 * (size_t)N) + up(2 * (size_t)N);
+    total += 256 + up(4 * (size_t)kCostBuckets) + up(4 * (size_t)N) + up(2 * (size_t)N) +
+             up(8 * (size_t)N);
   }
   const size_t slots_off = total;
   total += up(sizeof(unsigned long long) * n_items);
@@ -400,6 +402,8 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
     it.sc.order = (int*)(base + 256 + up(4 * (size_t)kCostBuckets));
     it.sc.bucket = (unsigned short*)(base + 256 + up(4 * (size_t)kCostBuckets) +
                                      up(4 * (size_t)src.N));
+    it.sc.h0 = base + 256 + up(4 * (size_t)kCostBuckets) + up(4 * (size_t)src.N) +
+               up(2 * (size_t)src.N);
     if (cudaStreamCreateWithFlags(&it.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming) != cudaSuccess)
       return batch_fail(b, ENS_ECUDA, "stream / event creation");
