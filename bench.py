@@ -1215,6 +1215,8 @@ def main():
         "unit": "samples/s" if w["kind"] in ("surrogate", "mlp") else "trajectories/s",
         "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * launch_s,
+        # this rank's spread of the timed steps (the paper quotes the minimum of its runs)
+        "step_ms_spread": {"min": min(ms), "median": float(np.median(ms)), "max": max(ms)},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"],
         "data": "synthetic", "config": cfg, "wall_s": wall,
         "roofline": {**roofline, **extra},

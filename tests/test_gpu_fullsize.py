@@ -13,6 +13,12 @@ times (autotuned, structure-of-arrays inputs), on a seeded sample the oracle sol
   of the oracle at the same tolerance (measured 3.42 tol for both, GPU - oracle 0.10 tol),
   identical counts on >= 94 % of the sample (measured 95.6 %), the linear invariant
   y1 + y2 + y3 = 1 to 1e-10.
+* Robertson, the same 2^18 trajectories and tolerance under Rodas4 and Rodas5P (the stiff
+  solvers of the paper's GPU list): every sampled trajectory within 10 tol of the tol-1e-12
+  Rodas5P reference (measured 0.0027 / 0.012 tol) and of the oracle's own Rodas at the same
+  tolerance (measured 5.4e-8 / 8.0e-4 tol), identical counts on >= 94 % of the sample
+  (measured 100 % / 96.6 %), the linear invariant to 1e-10 (the Rodas stages keep it
+  exactly, as Rosenbrock23's do: c^T W = c^T when c^T J = 0).
 """
 import numpy as np
 import pytest
@@ -102,6 +108,27 @@ def test_robertson_ros23_fullsize(robertson):
     print("Robertson Rosenbrock23 full size: error vs reference GPU max %.3g, oracle max %.3g "
           "tol; GPU - oracle max %.3g tol; identical counts %.4f"
           % (e_gpu.max(), e_orc.max(), d.max(), eq.mean()))
+    assert e_gpu.max() <= 10.0 and d.max() <= 10.0
+    assert eq.mean() >= 0.94
+    assert np.abs(h["out"].sum(axis=1) - 1.0).max() < 1e-10
+
+
+@pytest.mark.parametrize("alg", ["rodas4", "rodas5p"])
+def test_robertson_rodas_fullsize(alg):
+    h = _solve_full("robertson_%s_f64" % alg, "robertson", alg)
+    tol = h["kw"]["abstol"]
+    assert np.all(h["status"] == 0)
+    same, sst, sstats = oracle.solve("robertson", alg, h["P"], h["U"], h["T"], **h["kw"])
+    fine, _, _ = oracle.solve("robertson", "rodas5p", h["P"], h["U"], h["T"], abstol=1e-12,
+                              reltol=1e-12, dt0=1e-8)
+    assert np.all(sst == 0)
+    unit = lambda x, r: (np.abs(x - r) / (tol + tol * np.abs(r))).max(axis=1)
+    e_gpu, e_orc, d = unit(h["out"], fine), unit(same, fine), unit(h["out"], same)
+    eq = np.all(h["stats"][:, :2] == sstats[:, :2], axis=1)
+    a_gpu, a_orc = int(h["stats"][:, :2].sum()), int(sstats[:, :2].sum())
+    print("Robertson %s full size: error vs reference GPU max %.3g, oracle max %.3g tol; "
+          "GPU - oracle max %.3g tol; identical counts %.4f; attempts GPU/oracle %.6f"
+          % (alg, e_gpu.max(), e_orc.max(), d.max(), eq.mean(), a_gpu / a_orc))
     assert e_gpu.max() <= 10.0 and d.max() <= 10.0
     assert eq.mean() >= 0.94
     assert np.abs(h["out"].sum(axis=1) - 1.0).max() < 1e-10
