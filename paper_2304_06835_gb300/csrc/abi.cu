@@ -67,34 +67,52 @@ cudaError_t launch_solve(int rhs_id, int alg, int dtype, const SolveArgs& a,
   return f(alg, &a, cfg, stream, supported, nullptr, nullptr, nullptr);
 }
 
-// exclusive scan of the kCostBuckets totals in place (one block of kCostBuckets threads)
-__global__ void k_cost_scan(unsigned int* tot) {
-  __shared__ unsigned int sh[kCostBuckets];
-  const int t = threadIdx.x;
-  sh[t] = tot[t];
-  __syncthreads();
-  for (int off = 1; off < kCostBuckets; off <<= 1) {
-    const unsigned int v = t >= off ? sh[t - off] : 0u;
-    __syncthreads();
-    sh[t] += v;
-    __syncthreads();
+// Pass 2 of the longest-first ordering (blocks of kScatterThreads).  hist[0, 1024): the
+// bucket totals of pass 1; hist[1024, 2048): the buckets' fill cursors, zero on entry.
+constexpr int kScatterThreads = 256;
+__global__ void __launch_bounds__(kScatterThreads)
+k_cost_scatter(long long N, long long chunk, const unsigned short* bucket, unsigned int* hist,
+               int* order, unsigned long long* queue) {
+  constexpr int E = kCostBuckets / kScatterThreads;  // totals per thread in the scan
+  __shared__ unsigned int start[kCostBuckets];       // first position of each bucket
+  __shared__ unsigned int base[kCostBuckets];        // this block's counts, then positions
+  __shared__ unsigned int wsum[kScatterThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  // exclusive scan of the totals (every block the same): E per thread, then the threads'
+  // sums by warp shuffles and one shared-memory pass over the warps
+  unsigned int v[E], run = 0u;
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    v[k] = hist[t * E + k];
+    run += v[k];
   }
-  tot[t] = t ? sh[t - 1] : 0u;
-}
-
-__global__ void k_cost_scatter(long long N, long long chunk, const unsigned short* bucket,
-                               unsigned int* cursor, int* order) {
-  __shared__ unsigned int base[kCostBuckets];
-  for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) base[b] = 0u;
+  unsigned int inc = run;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  for (int b = t; b < kCostBuckets; b += kScatterThreads) base[b] = 0u;
   __syncthreads();
+  unsigned int before = 0u;
+  for (int k = 0; k < w; ++k) before += wsum[k];
+  unsigned int acc = before + inc - run;  // exclusive prefix of this thread's first total
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    start[t * E + k] = acc;
+    acc += v[k];
+  }
+  if (queue && blockIdx.x == 0 && t == 0) *queue = 0ull;  // the persistent queue starts at 0
   const long long lo = (long long)blockIdx.x * chunk;
   const long long hi = lo + chunk < N ? lo + chunk : N;
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&base[bucket[i]], 1u);
+  for (long long i = lo + t; i < hi; i += kScatterThreads) atomicAdd(&base[bucket[i]], 1u);
   __syncthreads();
-  for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x)
-    if (base[b]) base[b] = atomicAdd(&cursor[b], base[b]);  // this block's range in bucket b
+  unsigned int* fill = hist + kCostBuckets;
+  for (int b = t; b < kCostBuckets; b += kScatterThreads)
+    if (base[b]) base[b] = start[b] + atomicAdd(&fill[b], base[b]);  // this block's range
   __syncthreads();
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+  for (long long i = lo + t; i < hi; i += kScatterThreads) {
     const unsigned int pos = atomicAdd(&base[bucket[i]], 1u);
     order[pos] = (int)i;
   }
@@ -102,23 +120,26 @@ __global__ void k_cost_scatter(long long N, long long chunk, const unsigned shor
 
 cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a,
                               unsigned short* bucket, unsigned int* hist, int* order,
-                              void* h0, cudaStream_t stream) {
+                              void* h0, unsigned long long* queue, int sms,
+                              cudaStream_t stream) {
   DispatchFn f = table(rhs_id, dtype);
   if (!f) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kCostBuckets, stream);
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kCostHistWords, stream);
   if (e != cudaSuccess) return e;
   CostScratch cs;
   cs.bucket = bucket;
   cs.hist = hist;
   cs.h0 = h0;
-  cs.blocks = (int)std::min<long long>(kCostBlocks, std::max<long long>(1, (a.N + 1023) / 1024));
-  cs.chunk = (a.N + cs.blocks - 1) / cs.blocks;
+  // the keys pass: 4 blocks of 256 per multiprocessor (its loads and the starting-step
+  // arithmetic want the warps), fewer for small ensembles
+  cs.blocks = (int)std::min<long long>(4LL * std::max(sms, 1), (a.N + 255) / 256);
   LaunchCfg cfg{};
   bool sup = false;
   e = f(alg, &a, cfg, stream, &sup, nullptr, nullptr, &cs);
   if (e != cudaSuccess || !sup) return sup ? e : cudaErrorInvalidValue;
-  k_cost_scan<<<1, kCostBuckets, 0, stream>>>(hist);
-  k_cost_scatter<<<cs.blocks, 256, 0, stream>>>(a.N, cs.chunk, bucket, hist, order);
+  const int G = (int)std::min<long long>(kCostBlocks, std::max<long long>(1, (a.N + 1023) / 1024));
+  const long long chunk = (a.N + G - 1) / G;
+  k_cost_scatter<<<G, kScatterThreads, 0, stream>>>(a.N, chunk, bucket, hist, order, queue);
   return cudaGetLastError();
 }
 
@@ -131,7 +152,6 @@ cudaError_t launch_cost_keys(int rhs_id, int alg, int dtype, const SolveArgs& a,
   cs.bucket = nullptr;
   cs.hist = nullptr;
   cs.blocks = (int)std::min<long long>(4 * 152, std::max<long long>(1, (a.N + 255) / 256));
-  cs.chunk = 0;
   LaunchCfg cfg{};
   bool sup = false;
   cudaError_t e = f(alg, &a, cfg, stream, &sup, nullptr, nullptr, &cs);
@@ -493,10 +513,12 @@ cudaError_t prepare_solve(int rhs_id, const ens_opts* o, SolveArgs* a, const Lau
       // them, and the solve's initialisation reads them instead of forming them again
       const bool keep_h0 = sc.h0 && !is_fixed(o->alg) && !(o->dt0 > 0);
       cudaError_t e = launch_cost_order(rhs_id, o->alg, o->dtype, *a, sc.bucket, sc.hist,
-                                        sc.order, keep_h0 ? sc.h0 : nullptr, s);
+                                        sc.order, keep_h0 ? sc.h0 : nullptr, sc.queue,
+                                        cfg.num_sms, s);
       if (e != cudaSuccess) return e;
       a->order = sc.order;
       a->h0 = keep_h0 ? sc.h0 : nullptr;
+      return cudaSuccess;  // the ordering's scatter pass zeroed the queue counter
     }
     cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
@@ -567,7 +589,7 @@ int ens_create(ens_handle** out, int rhs_id, int D, int P) {
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->queue, 256);
-  if (e == cudaSuccess) e = cudaMalloc(&h->hist, sizeof(unsigned int) * kCostBuckets);
+  if (e == cudaSuccess) e = cudaMalloc(&h->hist, sizeof(unsigned int) * kCostHistWords);
   if (e != cudaSuccess) {
     delete h;
     return cuda_fail(e, "ens_create");
@@ -754,7 +776,7 @@ int ens_solve_host(ens_handle* h, long long N, const void* params, const void* u
     cudaError_t e = cudaSuccess;
     if (!h->solve_stream) e = cudaStreamCreateWithFlags(&h->solve_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !h->hist2)
-      e = cudaMalloc(&h->hist2, sizeof(unsigned int) * kCostBuckets);
+      e = cudaMalloc(&h->hist2, sizeof(unsigned int) * kCostHistWords);
     if (e == cudaSuccess && uses_cost_order(o, cfg) &&
         N <= 0x7fffffffLL) {  // the chunks' ordering ranges side by side
       rc = ensure_order_scratch(h, N);

@@ -368,7 +368,7 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
   for (int i = 0; i < n_items; ++i) {
     off[i] = total;
     const long long N = items[i].N;
-    total += 256 + up(4 * (size_t)kCostBuckets) + up(4 * (size_t)N) + up(2 * (size_t)N) +
+    total += 256 + up(4 * (size_t)kCostHistWords) + up(4 * (size_t)N) + up(2 * (size_t)N) +
              up(8 * (size_t)N);
   }
   const size_t slots_off = total;
@@ -399,10 +399,10 @@ int ens_batch_create(ens_batch** out, const ens_batch_item* items, int n_items, 
     char* base = (char*)b->scratch + off[i];
     it.sc.queue = (unsigned long long*)base;
     it.sc.hist = (unsigned int*)(base + 256);
-    it.sc.order = (int*)(base + 256 + up(4 * (size_t)kCostBuckets));
-    it.sc.bucket = (unsigned short*)(base + 256 + up(4 * (size_t)kCostBuckets) +
+    it.sc.order = (int*)(base + 256 + up(4 * (size_t)kCostHistWords));
+    it.sc.bucket = (unsigned short*)(base + 256 + up(4 * (size_t)kCostHistWords) +
                                      up(4 * (size_t)src.N));
-    it.sc.h0 = base + 256 + up(4 * (size_t)kCostBuckets) + up(4 * (size_t)src.N) +
+    it.sc.h0 = base + 256 + up(4 * (size_t)kCostHistWords) + up(4 * (size_t)src.N) +
                up(2 * (size_t)src.N);
     if (cudaStreamCreateWithFlags(&it.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming) != cudaSuccess)

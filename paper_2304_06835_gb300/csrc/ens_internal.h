@@ -71,9 +71,8 @@ struct CostScratch {
   void* h0 = nullptr;      // [N] of the solve's type: the starting steps the keys are formed
                            // from (adaptive methods without a given dt0), or null
   unsigned short* bucket;  // [N]
-  unsigned int* hist;      // [kCostBuckets] bucket totals, then cursors
-  int blocks;              // G <= kCostBlocks
-  long long chunk;         // trajectories per block
+  unsigned int* hist;      // [kCostBuckets] bucket totals
+  int blocks;              // the keys pass's grid (it strides over all trajectories)
 };
 
 struct LaunchCfg {
@@ -91,12 +90,16 @@ cudaError_t launch_solve(int rhs_id, int alg, int dtype, const SolveArgs& a,
 
 // Longest-expected-first ordering for the persistent schedule: fills order[0..N) with the
 // trajectory indices sorted by decreasing cost key (counting sort over kCostBuckets
-// log-spaced buckets).  bucket: [N] scratch, hist: [kCostBuckets] scratch.
+// log-spaced buckets), and zeroes the persistent queue counter.  bucket: [N] scratch, hist:
+// [kCostHistWords] scratch (the bucket totals, then the buckets' fill cursors); h0: the
+// starting steps kept for the solve, or null; sms: the device's multiprocessors.
 constexpr int kCostBuckets = 1024;
-constexpr int kCostBlocks = 256;
+constexpr int kCostHistWords = 2 * kCostBuckets;
+constexpr int kCostBlocks = 256;  // blocks of the scatter pass (one range per block and bucket)
 cudaError_t launch_cost_order(int rhs_id, int alg, int dtype, const SolveArgs& a,
                               unsigned short* bucket, unsigned int* hist, int* order,
-                              void* h0, cudaStream_t stream);
+                              void* h0, unsigned long long* queue, int sms,
+                              cudaStream_t stream);
 // The cost keys themselves: keys[i] = the expected steps of trajectory i (the key the
 // longest-first order sorts by).
 cudaError_t launch_cost_keys(int rhs_id, int alg, int dtype, const SolveArgs& a, float* keys,

@@ -796,10 +796,11 @@ __global__ void k_direct(const SolveArgs a) {
 
 // ------------------------------------------------------------------------------------------
 // Longest-expected-first ordering: a counting sort of log2 cost keys (32 buckets per octave).
-// Block b of G owns trajectories [b*C, min((b+1)*C, N)).  Pass 1 computes each key's bucket
-// and adds the block's histogram into the bucket totals; a 1024-entry scan turns the totals
-// into bucket cursors; pass 2 reserves one contiguous range per (block, bucket) with a single
-// atomic and scatters with shared-memory atomics.  (Order inside a bucket is arbitrary: the
+// Pass 1 (a grid striding over all trajectories) computes each key's bucket and adds each
+// block's histogram into the bucket totals.  Pass 2: block b of G owns trajectories
+// [b*C, min((b+1)*C, N)); every block scans the 1024 totals itself (bucket starts), reserves
+// one contiguous range per (block, bucket) with a single atomic on that bucket's fill cursor
+// and scatters with shared-memory atomics.  (Order inside a bucket is arbitrary: the
 // result of every trajectory does not depend on the order.)
 __device__ __forceinline__ int cost_bucket(float key) {
   int b = (int)(log2f(fmaxf(key, 1.f)) * 32.f);  // NaN keys land in the cheapest bucket
@@ -808,14 +809,13 @@ __device__ __forceinline__ int cost_bucket(float key) {
 }
 
 template <class I>
-__global__ void k_cost_keys(const SolveArgs a, long long chunk, unsigned short* bucket,
-                            unsigned int* tot, void* h0c) {
+__global__ void k_cost_keys(const SolveArgs a, unsigned short* bucket, unsigned int* tot,
+                            void* h0c) {
   __shared__ unsigned int sh[kCostBuckets];
   for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) sh[b] = 0u;
   __syncthreads();
-  const long long lo = (long long)blockIdx.x * chunk;
-  const long long hi = lo + chunk < a.N ? lo + chunk : a.N;
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.N;
+       i += (long long)gridDim.x * blockDim.x) {
     const int b = cost_bucket(I::cost_key(a, i, h0c));
     bucket[i] = (unsigned short)b;
     atomicAdd(&sh[b], 1u);
@@ -833,9 +833,6 @@ __global__ void k_cost_values(const SolveArgs a, float* keys) {
     keys[i] = I::cost_key(a, i, nullptr);
 }
 
-__global__ void k_cost_scan(unsigned int* tot);
-__global__ void k_cost_scatter(long long N, long long chunk, const unsigned short* bucket,
-                               unsigned int* cursor, int* order);
 
 // Persistent schedule.  Every lane of a warp stays in the loop until the whole warp is done,
 // so warp-wide votes are safe.  A lane that finishes its trajectory writes it out and idles;

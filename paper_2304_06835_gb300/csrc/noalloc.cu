@@ -17,8 +17,8 @@ namespace {
 
 constexpr long long kMaxN = ENS_NOALLOC_MAX_N;
 constexpr size_t kQueueOff = 0;                                  // 8 B counter
-constexpr size_t kHistOff = 256;                                 // kCostBuckets x uint32
-constexpr size_t kOrderOff = kHistOff + 4 * kCostBuckets;        // kMaxN x int32
+constexpr size_t kHistOff = 256;                                 // kCostHistWords x uint32
+constexpr size_t kOrderOff = kHistOff + 4 * kCostHistWords;      // kMaxN x int32
 constexpr size_t kBucketOff = kOrderOff + 4 * (size_t)kMaxN;     // kMaxN x uint16
 constexpr size_t kScratchBytes = kBucketOff + 2 * (size_t)kMaxN;
 

@@ -148,7 +148,7 @@ cudaError_t cost_keys_integ(const SolveArgs& a, CostScratch* cs, cudaStream_t s)
   if (cs->keys)
     k_cost_values<I><<<cs->blocks, 256, 0, s>>>(a, cs->keys);
   else
-    k_cost_keys<I><<<cs->blocks, 256, 0, s>>>(a, cs->chunk, cs->bucket, cs->hist, cs->h0);
+    k_cost_keys<I><<<cs->blocks, 256, 0, s>>>(a, cs->bucket, cs->hist, cs->h0);
   return cudaGetLastError();
 }
 
