@@ -873,16 +873,45 @@ __device__ __forceinline__ void persistent_loop(const SolveArgs& a) {
       if (busy == 0u) break;
       continue;
     }
-#pragma unroll
-    for (int q = 0; q < TPT; ++q) {
-      const unsigned idle = __ballot_sync(0xffffffffu, !act[q]);
+    if constexpr (TPT == 1) {
+      const unsigned idle = __ballot_sync(0xffffffffu, !act[0]);
       if (__popc(idle) >= a.refill_min) {
         bool got = true;
-        if (!act[q]) {
+        if (!act[0]) {
           const long long i = queue_next(a.queue);
-          act[q] = i < a.N;
-          got = act[q];
-          if (act[q]) s[q].init(a.order ? (long long)__ldg(a.order + i) : i, a);
+          act[0] = i < a.N;
+          got = act[0];
+          if (act[0]) s[0].init(a.order ? (long long)__ldg(a.order + i) : i, a);
+        }
+        drained = drained || __any_sync(0xffffffffu, !got);
+      }
+    } else {
+      // one refill pass over all slots: once the warp's 32 x TPT slots hold refill_min idle
+      // ones, every thread with an idle slot fills its first idle one, so the warp runs the
+      // initialisation once for all slot indices (the new state is copied into its slot by
+      // selects, never through an indexed array)
+      int nidle = 0;
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) nidle += __popc(__ballot_sync(0xffffffffu, !act[q]));
+      if (nidle >= a.refill_min) {
+        bool got = true;
+        int qf = -1;
+#pragma unroll
+        for (int q = TPT - 1; q >= 0; --q) qf = act[q] ? qf : q;
+        if (qf >= 0) {
+          const long long i = queue_next(a.queue);
+          got = i < a.N;
+          if (got) {
+            I t;
+            t.init(a.order ? (long long)__ldg(a.order + i) : i, a);
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) {
+              if (q == qf) {
+                s[q] = t;
+                act[q] = true;
+              }
+            }
+          }
         }
         drained = drained || __any_sync(0xffffffffu, !got);
       }
