@@ -156,8 +156,9 @@ MLP_FLOPS_PER_SAMPLE = 2 * (6 * 256 + 2 * 256 * 256 + 256 * 3)  # 266,752 per me
 # traffic is the per-unit inputs and outputs, so it grows in proportion).  Used only while the
 # timed launch runs that same kernel.
 PROFILED_TRAFFIC = {
-    # k_persistent_pair, N = 393,216: 14.449 MB read + 0.269 MB written
-    "lorenz_adaptive_f32": dict(kernel="k_persistent_pair", per_unit=(14.449408e6 + 0.268800e6) / 393216),
+    # k_persistent_pair, N = 393,216: 16.022 MB read + 0.269 MB written (inputs, the order
+    # array and the starting steps the ordering pre-pass kept)
+    "lorenz_adaptive_f32": dict(kernel="k_persistent_pair", per_unit=(16.021504e6 + 0.268544e6) / 393216),
     # k_mlp_fused, 1,048,576 samples x 4 members: 34.80 MB read + 3.50 MB written
     "mlp_forward": dict(kernel="k_mlp_fused", per_unit=(34.7968e6 + 3.4967e6) / 1048576),
 }
