@@ -27,7 +27,12 @@ times (autotuned, structure-of-arrays inputs), on a seeded sample the oracle sol
   consecutive trajectories spread over the ensemble (each trajectory's noise stream is its
   global index) within 1e-5 normwise of the oracle run in FP64 on the FP32 normal stream
   (measured 3.4e-6 / 3.1e-6).
+* The bouncing ball, N = 2^20, adaptive Tsit5 FP32 at tol 1e-6 with dtmax 1 over [0, 15] (the
+  events workload): the sampled final states within 2e-3 of the closed form (the criterion
+  of the small-case FP32 test).
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -176,3 +181,27 @@ def test_gbm_fp32_fullsize(name, alg):
     print("GBM %s FP32 full size: max normwise error %.3g" % (alg, worst))
     assert worst <= 1e-5
     assert np.all(h["stats"][:, 0] == 1000)
+
+
+def _ball_exact(x0, g, e, t):
+    """Height and velocity at t of a ball dropped from x0 at rest, restitution e (closed
+    form: free fall between impacts, velocity -e v at each impact)."""
+    tk, xk, wk = 0.0, x0, 0.0
+    while True:
+        s = (wk + math.sqrt(wk * wk + 2 * g * xk)) / g
+        if tk + s > t:
+            d = t - tk
+            return xk + wk * d - 0.5 * g * d * d, wk - g * d
+        tk += s
+        wk, xk = e * (g * s - wk), 0.0
+
+
+def test_ball_events_fp32_fullsize():
+    h = _solve_full("ball_events_f32", "ball", "tsit5")
+    assert np.all(h["status"] == 0)
+    assert np.all(h["U"][:, 1] == 0.0)
+    err = max(max(abs(h["out"][i, 0] - x), abs(h["out"][i, 1] - v))
+              for i in range(len(h["P"]))
+              for x, v in [_ball_exact(h["U"][i, 0], h["P"][i, 0], h["P"][i, 1], h["T"][i, 1])])
+    print("ball events FP32 full size: max error against the closed form %.3g" % err)
+    assert err <= 2e-3
