@@ -161,9 +161,12 @@ typedef struct {
                              one lockstep pair on the paired FP32 instructions (the default
                              for the fixed-step ones).  Every shape gives each trajectory the
                              result of 1. */
-  int refill_min;         /* persistent schedule: a warp refills its idle lanes once at least
-                             this many are idle (1..32; 0 = default).  Batching refills trades
-                             idle lanes for fewer divergent refill passes. */
+  int refill_min;         /* persistent schedule: a warp refills its idle trajectory slots
+                             once at least this many of them are idle (1..32; 0 = default 4),
+                             counted over all the warp's slots (32 x trajectories per thread);
+                             one pass then gives each thread with an idle slot one new
+                             trajectory.  Batching refills trades idle slots for fewer
+                             divergent refill passes. */
   int order;              /* ENS_ORDER_* (persistent schedule only) */
   int blocks_per_sm;      /* persistent schedule: resident blocks per SM (0 = as many as fit;
                              -1, -2, -3 = that many quarters of them, as ens_autotune reports;
