@@ -1200,6 +1200,11 @@ def main():
                      "ms_per_step": 1e3 * t_s / n_s, "clocks": c2,
                      "note": "back-to-back steps after the timed region, no L2 flush"}
     e2e = None if args.no_e2e else runner.e2e(stream)
+    if e2e and world > 1:  # the whole job: every rank's units over the slowest rank's time
+        per_step = max_over_ranks(N / e2e["value"], world, dev)
+        e2e = dict(e2e, value=N * world / per_step,
+                   h2d_bytes_per_step=e2e["h2d_bytes_per_step"] * world,
+                   d2h_bytes_per_step=e2e["d2h_bytes_per_step"] * world)
     cfg = {"workload": args.workload, "rhs": w["rhs"], "alg": w["alg"], "N": N,
            "tspan": [0.0, w["t1"]],
            **{k: w[k] for k in ("tol", "dt", "dt0", "dtmax", "every", "seed", "saves", "dense")
