@@ -386,7 +386,24 @@ __global__ void k_direct_pair(const SolveArgs a) {
     const int last0 = s0.n - 1, last1 = s1.n - 1;
     const float hr = s0.h_reg, hl0 = s0.h_last, hl1 = s1.h_last;
     const int mlo = m0 < m1 ? m0 : m1, mhi = m0 < m1 ? m1 : m0;
+    // steps before either lane's last one take the regular step on both lanes: no per-step
+    // choice of h (and the step's constant multiples of h hoisted out of the loop)
+    const int lmin = last0 < last1 ? last0 : last1;
+    const int mreg = lmin < mlo ? (lmin > 0 ? lmin : 0) : mlo;
+    const float2 hreg = bc2(hr);
     int k = 0;
+    for (; k < mreg; ++k) {
+      float2 unew[D], k7[D];
+      if constexpr (METH == METH_FIX_TSIT5)
+        tsit5_step2<RHS, false>(u, p, hreg, fk, unew, nullptr, k7);
+      else
+        rk4_step2<RHS>(u, p, hreg, unew);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        u[j] = unew[j];
+        if constexpr (METH == METH_FIX_TSIT5) fk[j] = k7[j];
+      }
+    }
     for (; k < mlo; ++k) {  // both lanes step
       const float2 h = make_float2(k == last0 ? hl0 : hr, k == last1 ? hl1 : hr);
       float2 unew[D], k7[D];
