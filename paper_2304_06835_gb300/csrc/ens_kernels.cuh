@@ -593,6 +593,9 @@ struct Fixed {
 
   T u[D], fk[D], p[P];
   T h_reg, h_last, t0f;
+  // SDE steps: sqrt(h) and 1/(4 sqrt(h)) of the regular and of the last step, formed once per
+  // trajectory (the same values the steps would form)
+  T sq_reg, sq_last, q4_reg, q4_last;
   double t0, tf;
   int n, nrun, k, next_ks;  // step counts in 32 bits (the 64-bit ones cost ~7 % on GBM EM)
   int si;
@@ -636,6 +639,12 @@ struct Fixed {
     nrun = int(r64);
     h_reg = T(a.dt);
     h_last = n64 > 0 ? T(tf - (t0 + double(n64 - 1) * a.dt)) : T(0);
+    if constexpr (kSde) {
+      sq_reg = M<T>::sqrt(h_reg);
+      sq_last = M<T>::sqrt(h_last);
+      q4_reg = T(0.25) / sq_reg;
+      q4_last = T(0.25) / sq_last;
+    }
     k = 0;
     if (METH == METH_FIX_TSIT5) RHS::f(u, p, t0t, fk);
     si = 0;
@@ -646,7 +655,8 @@ struct Fixed {
   }
 
   __device__ __forceinline__ void one_step(const SolveArgs& a, const T* z) {
-    const T h = (k == n - 1) ? h_last : h_reg;
+    const bool lastk = k == n - 1;
+    const T h = lastk ? h_last : h_reg;
     const T tk = T(kSde || !RHS::autonomous ? t0f + T(k) * h_reg : T(0));
     T unew[D];
     if (METH == METH_FIX_TSIT5) {
@@ -657,9 +667,9 @@ struct Fixed {
     } else if (METH == METH_FIX_RK4) {
       rk4_step<RHS, T>(u, p, tk, h, unew);
     } else if (METH == METH_FIX_SIEA) {
-      siea_step(u, p, tk, h, z, unew);
+      siea_step(u, p, tk, h, lastk ? sq_last : sq_reg, lastk ? q4_last : q4_reg, z, unew);
     } else {
-      em_step(u, p, tk, h, z, unew);
+      em_step(u, p, tk, h, lastk ? sq_last : sq_reg, z, unew);
     }
 #pragma unroll
     for (int j = 0; j < D; ++j) u[j] = unew[j];
@@ -669,16 +679,16 @@ struct Fixed {
 
   template <class R = RHS>
   __device__ __forceinline__ typename std::enable_if<R::has_noise>::type em_step(
-      const T* uu, const T* pp, T tk, T h, const T* z, T* unew) {
+      const T* uu, const T* pp, T tk, T h, T sq, const T* z, T* unew) {  // sq = sqrt(h)
     T dr[D], nz[D];
-    RHS::sde(uu, pp, tk, M<T>::sqrt(h), z, dr, nz);
+    RHS::sde(uu, pp, tk, sq, z, dr, nz);
     // increment first (a h + sum_m b_m sqrt(h) Z_m), then one rounding at the scale of X
 #pragma unroll
     for (int j = 0; j < D; ++j) unew[j] = uu[j] + M<T>::fma(dr[j], h, nz[j]);
   }
   template <class R = RHS>
   __device__ __forceinline__ typename std::enable_if<!R::has_noise>::type em_step(
-      const T*, const T*, T, T, const T*, T*) {}
+      const T*, const T*, T, T, T, const T*, T*) {}
 
   // Weak order 2 stochastic Runge-Kutta step (GPUSIEA, Sec. 5.2.2; the improved-Euler-type
   // member of the SRK family of Sec. 3.3), diagonal noise, dW_j = sqrt(h) Z_j:
@@ -686,12 +696,11 @@ struct Fixed {
   //   X1 = X + (a(X) + a(Ybar)) h/2 + (b(Y+) + b(Y-) + 2 b(X)) dW/4
   //        + (b(Y+) - b(Y-)) (dW^2 - h) / (4 sqrt(h)).
   template <class R = RHS>
+  // (sq = sqrt(h) and q4 = 0.25 / sq, formed once per trajectory)
   __device__ __forceinline__ typename std::enable_if<DiagNoise<R>::value>::type siea_step(
-      const T* uu, const T* pp, T tk, T h, const T* z, T* unew) {
+      const T* uu, const T* pp, T tk, T h, T sq, T q4, const T* z, T* unew) {
     typedef M<T> m;
     T a0[D], a1[D], b0[D], bp[D], bm[D], Y[D], dW[D], ah[D];
-    const T sq = m::sqrt(h);
-    const T q4 = T(0.25) / sq;
     RHS::f(uu, pp, tk, a0);
     RHS::diag_b(uu, pp, tk, b0);
 #pragma unroll
@@ -717,7 +726,7 @@ struct Fixed {
   }
   template <class R = RHS>
   __device__ __forceinline__ typename std::enable_if<!DiagNoise<R>::value>::type siea_step(
-      const T*, const T*, T, T, const T*, T*) {}
+      const T*, const T*, T, T, T, T, const T*, T*) {}
 
   __device__ __forceinline__ bool advance(const SolveArgs& a) {
     if (k >= nrun) return true;
