@@ -654,8 +654,10 @@ struct Fixed {
     }
   }
 
+  // kReg: the caller knows this is not the trajectory's last step (h = h_reg)
+  template <bool kReg = false>
   __device__ __forceinline__ void one_step(const SolveArgs& a, const T* z) {
-    const bool lastk = k == n - 1;
+    const bool lastk = !kReg && k == n - 1;
     const T h = lastk ? h_last : h_reg;
     const T tk = T(kSde || !RHS::autonomous ? t0f + T(k) * h_reg : T(0));
     T unew[D];
@@ -735,9 +737,14 @@ struct Fixed {
       T z[kPC * kCalls];
       if (kCalls == 1) {
         Normals<T>::draw(Philox::call(a.seed, stream, (unsigned long long)(unsigned(k) / unsigned(kSub))), z);
+        if (k + kSub < n && k + kSub <= nrun) {  // all kSub steps run, none is the last
 #pragma unroll
-        for (int sub = 0; sub < kSub; ++sub)
-          if (k < nrun) one_step(a, z + sub * kNW);
+          for (int sub = 0; sub < kSub; ++sub) one_step<true>(a, z + sub * kNW);
+        } else {
+#pragma unroll
+          for (int sub = 0; sub < kSub; ++sub)
+            if (k < nrun) one_step(a, z + sub * kNW);
+        }
       } else {
 #pragma unroll
         for (int c = 0; c < kCalls; ++c)
