@@ -697,8 +697,8 @@ struct Fixed {
   //   Ybar = X + a h + b dW,  Y+- = X + a h +- b sqrt(h),
   //   X1 = X + (a(X) + a(Ybar)) h/2 + (b(Y+) + b(Y-) + 2 b(X)) dW/4
   //        + (b(Y+) - b(Y-)) (dW^2 - h) / (4 sqrt(h)).
-  template <class R = RHS>
   // (sq = sqrt(h) and q4 = 0.25 / sq, formed once per trajectory)
+  template <class R = RHS>
   __device__ __forceinline__ typename std::enable_if<DiagNoise<R>::value>::type siea_step(
       const T* uu, const T* pp, T tk, T h, T sq, T q4, const T* z, T* unew) {
     typedef M<T> m;
