@@ -260,6 +260,18 @@ def max_over_ranks(seconds, world, device=None):
     return float(t.item())
 
 
+def job_e2e(e2e, n_rank, world, device=None):
+    """The whole job's end-to-end figure from each rank's own: every rank's units (n_rank
+    each) over the slowest rank's time per step, and every rank's copied bytes (one MAX
+    all-reduce; at world = 1 the rank's own figure)."""
+    if not e2e or world <= 1:
+        return e2e
+    per_step = max_over_ranks(n_rank / e2e["value"], world, device)
+    return dict(e2e, value=n_rank * world / per_step,
+                h2d_bytes_per_step=e2e["h2d_bytes_per_step"] * world,
+                d2h_bytes_per_step=e2e["d2h_bytes_per_step"] * world)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -1199,12 +1211,7 @@ def main():
         sustained = {"seconds": t_s, "steps": n_s, "value": N * world * n_s / t_s,
                      "ms_per_step": 1e3 * t_s / n_s, "clocks": c2,
                      "note": "back-to-back steps after the timed region, no L2 flush"}
-    e2e = None if args.no_e2e else runner.e2e(stream)
-    if e2e and world > 1:  # the whole job: every rank's units over the slowest rank's time
-        per_step = max_over_ranks(N / e2e["value"], world, dev)
-        e2e = dict(e2e, value=N * world / per_step,
-                   h2d_bytes_per_step=e2e["h2d_bytes_per_step"] * world,
-                   d2h_bytes_per_step=e2e["d2h_bytes_per_step"] * world)
+    e2e = job_e2e(None if args.no_e2e else runner.e2e(stream), N, world, dev)
     cfg = {"workload": args.workload, "rhs": w["rhs"], "alg": w["alg"], "N": N,
            "tspan": [0.0, w["t1"]],
            **{k: w[k] for k in ("tol", "dt", "dt0", "dtmax", "every", "seed", "saves", "dense")

@@ -22,10 +22,13 @@ def _rank_main(rank, world, port, q):
     sys.path.insert(0, ROOT)
     import bench
     t = bench.max_over_ranks(1.0 + rank * 0.5, world)
+    # each rank's own end-to-end figure: 100 units/s on rank 0, 50 on rank 1, 10 units each
+    e = bench.job_e2e({"value": 100.0 / (1 + rank), "unit": "u/s", "h2d_bytes_per_step": 8,
+                       "d2h_bytes_per_step": 4}, 10, world)
     w = dict(bench.WORKLOADS["lorenz_adaptive_f32"], N=64)
     P, _, _ = bench.inputs_for(w, rank, world)
     wg = dict(bench.WORKLOADS["crn_em_f32"], N=64)
-    q.put((rank, t, P, bench.shard_start(wg, rank, world)))
+    q.put((rank, t, P, bench.shard_start(wg, rank, world), e))
     dist.destroy_process_group()
 
 
@@ -42,6 +45,10 @@ def test_max_over_ranks_and_shards_of_one_ensemble_gloo():
         assert p.exitcode == 0
     res.sort(key=lambda r: r[0])
     assert res[0][1] == res[1][1] == 1.5           # every rank sees the slowest rank's time
+    # the job's e2e: 20 units over the slower rank's 0.2 s per step, bytes of both ranks
+    for r in res:
+        assert r[4] == {"value": 100.0, "unit": "u/s", "h2d_bytes_per_step": 16,
+                        "d2h_bytes_per_step": 8}
     sys.path.insert(0, ROOT)
     import bench
     whole, _, _ = bench.inputs_for(dict(bench.WORKLOADS["lorenz_adaptive_f32"], N=128))
